@@ -1,0 +1,266 @@
+"""FP64 CPU oracle of sharing-ADMM with pixel elimination (SADMM / ASADMM).
+
+TEST INFRASTRUCTURE.  Only the tests, the smoke check and the CPU-baseline leg of
+the benchmark may import this module; the library never does.  It shares no code
+with the CUDA path.
+
+What it computes (Section III of the paper, Eq. 2, Eq. 3 and Algorithm 1), under
+the readings listed below.  Notation: B_q = [Re A_q; Im A_q] is the real form of
+the complex operator, so for real x, ||y - A x||^2 = ||[Re y; Im y] - B x||^2 and
+Re(A^H y) = B^T [Re y; Im y].
+
+Problem (Eq. 2 with the selectors equal to the identity):
+    min_{x_1..x_Q}  sum_q mu/2 ||y_q - A_q x_q||^2 + lambda ||x_G||_1,
+    x_G = sum_q x_q.
+This is the sharing problem of Boyd et al. (2011, Sec. 7.3), which the paper cites
+for its ADMM.  Internally the averaged variables are carried:
+x_bar = (1/Q) sum_q x_q, z_bar = x_G / Q, and the scaled dual s, so that the
+paper's dual is sigma = rho * s and its beta is rho.
+
+One iteration k -> k+1:
+  1. x-update (Eq. 3, first line), per sensor, on the active set J_q only:
+       v_J   = x_q - x_bar + z_bar - s           (restricted to J_q)
+       x_q,J = (rho I + mu B_J^T B_J)^{-1} (mu B_J^T y'_q + rho v_J)
+     Entries outside J_q keep their value (frozen).  y'_q is y_q minus the
+     contribution of the frozen pixels.
+  2. x_bar = (1/Q) sum_q x_q over all N pixels.
+  3. z_bar' = soft(x_bar + s, lambda/rho)        (Eq. 3, second line)
+  4. s'     = s + x_bar - z_bar'                 (Eq. 3, third line)
+  5. residuals: r_pri = sqrt(Q) ||x_bar - z_bar'||,
+       eps_pri  = sqrt(QN) eps_abs + eps_rel max(||X||_F, ||Z||_F),  Z_q = x_q - x_bar + z_bar',
+       d        = rho ||Z^{k+1} - Z^k||_F,
+       eps_dual = sqrt(QN) eps_abs + eps_rel rho sqrt(Q) ||s'||.
+  6. SSC (Algorithm 1): |x_q^{k+1} - x_q^k| is pushed into a ring of the last Kp
+     differences; if elimination is on, k+1 >= Kp and r_pri <= eps_pri, then
+     zeta = mean of the ring and J_q <- {i in J_q : zeta_i >= eps_p}.  Newly
+     removed pixels are frozen at their value and folded into y'_q
+     (y'_q -= A_q,E x_q,E), or, in zero mode, set to 0.
+  7. stop when k+1 = iters, or (mode 0) ||X^{k+1} - X^k||_F <= tol ||X^{k+1}||_F,
+     or (mode 1) r_pri <= eps_pri and d <= eps_dual.
+
+Readings where the paper is silent or garbled (each is a choice both this oracle
+and the CUDA path make): real x_q (Eq. 1 folds the phase into A_q); x_G is the sum
+of the x_q and the threshold on the averaged variable is lambda/rho; the x-update
+carries Boyd's x_q^k - x_bar^k + z_bar^k term that Eq. 3's garbled first line
+drops; the dual enters the x_G-update with the sign that makes the fixed point the
+optimum of Eq. 2; the primal/dual residuals follow Boyd Sec. 3.3.1 applied to the
+sharing form; Algorithm 1's window is the last Kp differences including the newest
+one and its gate uses the newest residual; ties zeta = eps_p are kept; the active
+set only shrinks; all iterates start at zero; the factor is refreshed whenever an
+active set changes.
+"""
+from dataclasses import dataclass, field
+import numpy as np
+import scipy.linalg as sla
+
+
+@dataclass
+class Criterion:
+    mu: float = 1.0
+    Kp: int = 5
+    eps_p: float = 1e-5
+    eps_abs: float = 1e-4
+    eps_rel: float = 1e-2
+    elim: int = 1          # 0: plain SADMM, 1: pixel elimination (Algorithm 1)
+    freeze_mode: int = 0   # 0: removed pixels keep their value, 1: set to zero
+    stop: int = 0          # 0: relative change of X, 1: primal and dual residuals
+
+
+def soft(v, t):
+    """Soft threshold: the closed-form minimiser of t|x| + 1/2 (x - v)^2 (Eq. 3, second line)."""
+    return np.sign(v) * np.maximum(np.abs(v) - t, 0.0)
+
+
+def real_form(Aq):
+    """B_q = [Re A_q; Im A_q] (2KM x N, float64) from a pixel-major (N, KM) operator."""
+    At = np.asarray(Aq).astype(np.complex128).T
+    return np.vstack([At.real, At.imag])
+
+
+def real_vec(y):
+    y = np.asarray(y).astype(np.complex128)
+    return np.concatenate([y.real, y.imag])
+
+
+def forward(Aq, x):
+    """A_q x for real x (Eq. 1), complex128."""
+    return np.asarray(Aq).astype(np.complex128).T @ np.asarray(x, dtype=np.float64)
+
+
+def adjoint_re(Aq, r):
+    """Re(A_q^H r), float64: the adjoint of the real-input forward map."""
+    return (np.asarray(Aq).astype(np.complex128).conj() @ np.asarray(r).astype(np.complex128)).real
+
+
+class RidgeSolver:
+    """Solves (rho I + mu B_J^T B_J) x = b for a fixed active set J (Eq. 3, first line).
+
+    The factor is a Cholesky decomposition of the smaller of the two Gram forms:
+    the |J| x |J| matrix itself, or, when |J| > 2KM, rho I + mu B_J B_J^T, used
+    through the Woodbury identity
+        (rho I + mu B^T B)^{-1} = (I - mu B^T (rho I + mu B B^T)^{-1} B) / rho.
+    """
+
+    def __init__(self, BJ, mu, rho):
+        self.BJ, self.mu, self.rho = BJ, mu, rho
+        m, n = BJ.shape
+        self.woodbury = n > m
+        if self.woodbury:
+            G = rho * np.eye(m) + mu * (BJ @ BJ.T)
+        else:
+            G = rho * np.eye(n) + mu * (BJ.T @ BJ)
+        self.cf = sla.cho_factor(G, lower=True)
+
+    def solve(self, b):
+        if self.woodbury:
+            t = sla.cho_solve(self.cf, self.BJ @ b)
+            return (b - self.mu * (self.BJ.T @ t)) / self.rho
+        return sla.cho_solve(self.cf, b)
+
+
+@dataclass
+class State:
+    k: int                      # iterations completed
+    x: np.ndarray               # (Q, N)
+    xbar: np.ndarray            # (N,)
+    zbar: np.ndarray            # (N,)
+    s: np.ndarray               # (N,)
+    ring: np.ndarray            # (Kp, Q, N) |x^{t+1} - x^t| for the last Kp iterations
+    J: list                     # Q sorted int arrays
+    yprime: list                # Q arrays (2KM,) real form of y'_q
+
+    def copy(self):
+        return State(self.k, self.x.copy(), self.xbar.copy(), self.zbar.copy(), self.s.copy(),
+                     self.ring.copy(), [j.copy() for j in self.J], [v.copy() for v in self.yprime])
+
+
+def initial_state(A, y, Kp):
+    Q, N = len(A), A[0].shape[0]
+    return State(0, np.zeros((Q, N)), np.zeros(N), np.zeros(N), np.zeros(N),
+                 np.zeros((Kp, Q, N)), [np.arange(N) for _ in range(Q)],
+                 [real_vec(v) for v in y])
+
+
+@dataclass
+class Result:
+    state: State
+    history: list = field(default_factory=list)
+    stop_reason: str = "iters"
+
+    @property
+    def xG(self):
+        return len(self.state.x) * self.state.zbar
+
+
+def sadmm(A, y, rho, lam, crit: Criterion, iters, tol=0.0, state: State = None, B=None):
+    """Run SADMM (crit.elim = 0) or ASADMM (crit.elim = 1) for at most `iters`
+    iterations from `state` (zeros if None).  Returns a Result whose history holds,
+    per iteration: r_pri, eps_pri, d, eps_dual, relchange, gate, sizes, and the
+    decision margins zeta_margin (min |zeta - eps_p| over tested pixels) and
+    gate_margin (|r_pri - eps_pri| / eps_pri)."""
+    Q = len(A)
+    mu = crit.mu
+    B = B if B is not None else [real_form(a) for a in A]
+    N = B[0].shape[1]
+    st = (state.copy() if state is not None else initial_state(A, y, crit.Kp))
+    solvers, cvec = [None] * Q, [None] * Q
+
+    def refresh(q):
+        J = st.J[q]
+        BJ = B[q] if len(J) == N else B[q][:, J]
+        solvers[q] = RidgeSolver(BJ, mu, rho)
+        cvec[q] = mu * (BJ.T @ st.yprime[q])
+
+    for q in range(Q):
+        refresh(q)
+    res = Result(st)
+    Zold = st.x - st.xbar[None, :] + st.zbar[None, :]
+    for it in range(iters):
+        x_old = st.x.copy()
+        # 1. x-update per sensor on its active set
+        for q in range(Q):
+            J = st.J[q]
+            v = st.x[q, J] - st.xbar[J] + st.zbar[J] - st.s[J]
+            st.x[q, J] = solvers[q].solve(cvec[q] + rho * v)
+        # 2-4. average, prox, dual
+        xbar_new = st.x.mean(axis=0)
+        zbar_new = soft(xbar_new + st.s, lam / rho)
+        s_new = st.s + xbar_new - zbar_new
+        # 5. residuals
+        Z = st.x - xbar_new[None, :] + zbar_new[None, :]
+        r_pri = np.sqrt(Q) * np.linalg.norm(xbar_new - zbar_new)
+        eps_pri = np.sqrt(Q * N) * crit.eps_abs + crit.eps_rel * max(np.linalg.norm(st.x),
+                                                                    np.linalg.norm(Z))
+        d = rho * np.linalg.norm(Z - Zold)
+        eps_dual = np.sqrt(Q * N) * crit.eps_abs + crit.eps_rel * rho * np.sqrt(Q) * np.linalg.norm(s_new)
+        nx = np.linalg.norm(st.x)
+        relchange = np.linalg.norm(st.x - x_old) / nx if nx > 0 else np.inf
+        st.xbar, st.zbar, st.s = xbar_new, zbar_new, s_new
+        # 6. SSC
+        slot = st.k % crit.Kp
+        st.ring[slot] = np.abs(st.x - x_old)
+        st.k += 1
+        rec = dict(k=st.k, r_pri=r_pri, eps_pri=eps_pri, d=d, eps_dual=eps_dual,
+                   relchange=relchange, gate=False, zeta_margin=np.inf, gate_margin=np.inf)
+        if crit.elim and st.k >= crit.Kp:
+            rec["gate_margin"] = abs(r_pri - eps_pri) / eps_pri
+            if r_pri <= eps_pri:
+                rec["gate"] = True
+                zeta = st.ring.mean(axis=0)
+                changed = False
+                for q in range(Q):
+                    J = st.J[q]
+                    zq = zeta[q, J]
+                    if len(zq):
+                        rec["zeta_margin"] = min(rec["zeta_margin"], float(np.min(np.abs(zq - crit.eps_p))))
+                    keep = zq >= crit.eps_p
+                    if keep.all():
+                        continue
+                    E = J[~keep]
+                    st.J[q] = J[keep]
+                    if crit.freeze_mode == 0:
+                        st.yprime[q] = st.yprime[q] - B[q][:, E] @ st.x[q, E]
+                    else:
+                        st.x[q, E] = 0.0
+                    changed = True
+                    refresh(q)
+                if changed and crit.freeze_mode == 1:
+                    st.xbar = st.x.mean(axis=0)
+        rec["sizes"] = [len(j) for j in st.J]
+        res.history.append(rec)
+        Zold = st.x - st.xbar[None, :] + st.zbar[None, :]
+        # 7. stop
+        if crit.stop == 0 and tol > 0 and relchange <= tol:
+            res.stop_reason = "tol"
+            break
+        if crit.stop == 1 and r_pri <= eps_pri and d <= eps_dual:
+            res.stop_reason = "residuals"
+            break
+    return res
+
+
+def objective(A, y, X, lam, mu=1.0, B=None):
+    """Eq. 2 objective with the selectors equal to the identity."""
+    B = B if B is not None else [real_form(a) for a in A]
+    f = sum(0.5 * mu * np.sum((real_vec(y[q]) - B[q] @ X[q]) ** 2) for q in range(len(A)))
+    return f + lam * np.sum(np.abs(np.sum(X, axis=0)))
+
+
+def kkt(A, y, X, s, rho, lam, mu=1.0, xG=None, B=None):
+    """Optimality conditions of Eq. 2 (selectors = identity) for the primal-dual
+    pair (X, nu = rho s):
+      stationarity  mu B_q^T (B_q x_q - y_q) + nu = 0 for every q,
+      subgradient   nu in lambda d||x_G||_1 (|nu_i| <= lambda; nu_i = lambda sign(x_G,i) on the support),
+      feasibility   x_G = sum_q x_q.
+    Returns the residuals normalised by lambda (and by max(1, ||x_G||_inf) for feasibility)."""
+    B = B if B is not None else [real_form(a) for a in A]
+    nu = rho * np.asarray(s)
+    xsum = np.sum(X, axis=0)
+    xG = xsum if xG is None else xG
+    stat = max(np.max(np.abs(mu * (B[q].T @ (B[q] @ X[q] - real_vec(y[q]))) + nu))
+               for q in range(len(A)))
+    sub = max(0.0, float(np.max(np.abs(nu))) - lam)
+    supp = np.abs(xG) > 0
+    sgn = float(np.max(np.abs(nu[supp] - lam * np.sign(xG[supp])))) if supp.any() else 0.0
+    feas = float(np.max(np.abs(xG - xsum))) / max(1.0, float(np.max(np.abs(xG))))
+    return dict(stationarity=stat / lam, subgradient=max(sub, sgn) / lam, feasibility=feas)

@@ -1,0 +1,10 @@
+"""Seeded synthetic inputs (operators, scenes, noise) shared by the oracle-side
+tests and the CUDA-side tests and bench.  No solver arithmetic lives here."""
+from .rng import Stream
+from .radar import (Geometry, Scene, operator, delays, pixel_centres, sensor_positions,
+                    point_targets, cluster_targets, measure, lambda_max)
+from .configs import GEOMS, Params, build_scene, resolve_lambda, random_problem
+
+__all__ = ["Stream", "Geometry", "Scene", "operator", "delays", "pixel_centres",
+           "sensor_positions", "point_targets", "cluster_targets", "measure", "lambda_max",
+           "GEOMS", "Params", "build_scene", "resolve_lambda", "random_problem"]

@@ -1,0 +1,373 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: an identity,
+a closed form, an independent solver, brute force, or an invariant of
+Algorithm 1.  The mutation tests at the end plant plausible mistakes in a copy of
+the oracle and check that the pins catch them.
+"""
+import inspect
+import sys
+import types
+
+import numpy as np
+import pytest
+
+import oracle
+import oracle.sharing_admm as osadmm
+import scenegen
+from scenegen import radar
+
+
+# ---------------------------------------------------------------- Eq. 1 products
+def test_forward_matches_elementwise_sum():
+    """A x computed one entry at a time (Eq. 1, with the pixel-major layout)."""
+    sc = scenegen.random_problem(1, 6, 5, seed=3)
+    A = sc.A[0]                       # (N, KM) pixel-major
+    x = scenegen.Stream(9, 1).normal(5)
+    ref = np.zeros(6, dtype=np.complex128)
+    for r in range(6):
+        for n in range(5):
+            ref[r] += complex(A[n, r]) * x[n]
+    assert np.allclose(oracle.forward(A, x), ref, rtol=1e-14, atol=1e-14)
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_adjoint_identity(seed):
+    """Re<A x, r> = <x, Re(A^H r)> for real x, complex r (Eq. 1 operator)."""
+    g = scenegen.GEOMS["small_point"]
+    A = radar.operator(g, seed % g.Q)
+    s = scenegen.Stream(seed, 7)
+    x = s.normal(g.N)
+    r = s.normal(g.KM) + 1j * s.normal(g.KM)
+    lhs = np.vdot(r, oracle.forward(A, x)).real
+    rhs = np.dot(x, oracle.adjoint_re(A, r))
+    scale = np.linalg.norm(oracle.forward(A, x)) * np.linalg.norm(r)
+    assert abs(lhs - rhs) <= 1e-12 * scale
+
+
+def test_real_form_consistent_with_complex_products():
+    """B = [Re A; Im A]: ||y - A x||^2 = ||[Re y; Im y] - B x||^2 and
+    Re(A^H y) = B^T [Re y; Im y] for real x."""
+    sc = scenegen.random_problem(1, 16, 12, seed=5)
+    A, y = sc.A[0], sc.y[0]
+    B = oracle.real_form(A)
+    x = scenegen.Stream(2, 2).normal(12)
+    lhs = np.sum(np.abs(y.astype(np.complex128) - oracle.forward(A, x)) ** 2)
+    rhs = np.sum((oracle.real_vec(y) - B @ x) ** 2)
+    assert abs(lhs - rhs) <= 1e-12 * lhs
+    assert np.allclose(B.T @ oracle.real_vec(y), oracle.adjoint_re(A, y), rtol=1e-13, atol=1e-12)
+
+
+# ------------------------------------------------------------ Eq. 3 ingredients
+def test_soft_threshold_is_the_prox():
+    """soft(v, t) minimises t|x| + (x - v)^2 / 2: brute force on a fine grid,
+    and the subgradient condition v - x in t d|x|."""
+    s = scenegen.Stream(4, 4)
+    v = s.uniform(200, -3, 3)
+    t = s.uniform(200, 0, 2)
+    x = oracle.soft(v, t)
+    grid = np.linspace(-4, 4, 80001)
+    for vi, ti, xi in zip(v[:40], t[:40], x[:40]):
+        f = ti * np.abs(grid) + 0.5 * (grid - vi) ** 2
+        assert abs(grid[np.argmin(f)] - xi) <= 1e-4
+    nz = x != 0
+    assert np.allclose(v[nz] - x[nz], t[nz] * np.sign(x[nz]), atol=1e-12)
+    assert np.all(np.abs(v[~nz]) <= t[~nz] + 1e-15)
+
+
+@pytest.mark.parametrize("nJ", [20, 200])
+def test_ridge_solver_residual_and_forms_agree(nJ):
+    """The x-update solve of Eq. 3: residual of (rho I + mu B_J^T B_J) x = b, for
+    the primal Cholesky (|J| <= 2KM) and the Woodbury form (|J| > 2KM)."""
+    sc = scenegen.random_problem(1, 32, 256, seed=11)
+    B = oracle.real_form(sc.A[0])                        # 64 x 256
+    J = np.sort(scenegen.Stream(1, 5).permutation(256)[:nJ])
+    BJ = B[:, J]
+    b = scenegen.Stream(2, 5).normal(nJ)
+    mu, rho = 0.7, 1.3
+    Hm = rho * np.eye(nJ) + mu * BJ.T @ BJ
+    solver = oracle.RidgeSolver(BJ, mu, rho)
+    assert solver.woodbury == (nJ > 64)
+    x = solver.solve(b)
+    assert np.linalg.norm(Hm @ x - b) <= 1e-12 * np.linalg.norm(b) * np.linalg.norm(Hm, 2)
+    # the other form of the same solve
+    x2 = np.linalg.solve(Hm, b)
+    assert np.allclose(x, x2, rtol=1e-10, atol=1e-12 * np.linalg.norm(x2))
+
+
+# ------------------------------------------------------- the whole iteration
+def _resolved(seed=1, snr=30.0):
+    sc = scenegen.build_scene("resolved_tiny", seed=seed, snr_db=snr)
+    lam = 0.05 * scenegen.lambda_max(sc.A, sc.y)
+    return sc, lam
+
+
+@pytest.fixture(scope="module")
+def converged_plain():
+    sc, lam = _resolved()
+    res = oracle.sadmm(sc.A, sc.y, 1.0, lam, oracle.Criterion(elim=0), iters=20000, tol=1e-15)
+    return sc, lam, res
+
+
+def test_kkt_at_the_limit(converged_plain):
+    """With elimination off the limit satisfies Eq. 2's optimality conditions to 1e-8."""
+    sc, lam, res = converged_plain
+    k = oracle.kkt(sc.A, sc.y, res.state.x, res.state.s, 1.0, lam, xG=res.xG)
+    assert k["stationarity"] <= 1e-8
+    assert k["subgradient"] <= 1e-8
+    assert k["feasibility"] <= 1e-8
+
+
+def test_fista_agrees(converged_plain):
+    """An independent proximal-gradient solve of Eq. 2 reaches the same minimiser
+    (unique here: every sensor resolves the grid, 2KM > N)."""
+    sc, lam, res = converged_plain
+    Xf, fval = oracle.fista(sc.A, sc.y, lam, iters=6000, tol=1e-14)
+    fa = oracle.objective(sc.A, sc.y, res.state.x, lam)
+    assert abs(fa - fval) <= 1e-10 * abs(fval)
+    assert np.max(np.abs(res.state.x - Xf)) <= 1e-6
+    assert np.max(np.abs(res.xG - Xf.sum(axis=0))) <= 1e-6
+
+
+@pytest.mark.parametrize("rho", [0.5, 4.0])
+def test_kkt_other_rho_random_operator(rho):
+    """Same optimality pin on unstructured operators and rho != 1, so that a
+    rho-scaling slip in the prox threshold or the dual cannot hide."""
+    sc = scenegen.random_problem(2, 24, 32, seed=21)
+    lam = 0.1 * scenegen.lambda_max(sc.A, sc.y)
+    res = oracle.sadmm(sc.A, sc.y, rho, lam, oracle.Criterion(elim=0, mu=0.8), iters=20000,
+                       tol=1e-15)
+    k = oracle.kkt(sc.A, sc.y, res.state.x, res.state.s, rho, lam, mu=0.8, xG=res.xG)
+    assert max(k.values()) <= 1e-8
+    Xf, fval = oracle.fista(sc.A, sc.y, lam, mu=0.8, iters=6000, tol=1e-14)
+    assert abs(oracle.objective(sc.A, sc.y, res.state.x, lam, mu=0.8) - fval) <= 1e-10 * abs(fval)
+
+
+def test_lasso_zero_above_lambda_max():
+    """Q = 1 is the LASSO; for lambda >= mu ||Re(A^H y)||_inf the minimiser is 0,
+    and the oracle stays at exactly zero."""
+    sc = scenegen.random_problem(1, 24, 40, seed=8)
+    lam = 1.0001 * scenegen.lambda_max(sc.A, sc.y)
+    res = oracle.sadmm(sc.A, sc.y, 1.0, lam, oracle.Criterion(elim=0), iters=3000, tol=1e-14)
+    assert np.all(res.xG == 0.0)
+    k = oracle.kkt(sc.A, sc.y, res.state.x, res.state.s, 1.0, lam, xG=res.xG)
+    assert max(k.values()) <= 1e-8
+
+
+@pytest.mark.parametrize("name,sensors", [("resolved_tiny", None), ("small_point", [0])])
+def test_single_point_target_recovered(name, sensors):
+    """A noiseless single point target: argmax |x_G| is its pixel, and its value
+    is the composite magnitude up to the l1 shrinkage bias."""
+    g = scenegen.GEOMS[name]
+    A = [radar.operator(g, q) for q in range(g.Q)]
+    n0 = g.N // 2 + g.nx // 3
+    x = np.zeros((g.Q, g.N))
+    x[:, n0] = 0.8
+    if sensors:
+        A, x = [A[q] for q in sensors], x[sensors]
+    y = radar.measure(A, x, None, 0)
+    lam = 0.01 * scenegen.lambda_max(A, y)
+    res = oracle.sadmm(A, y, 1.0, lam, oracle.Criterion(elim=0), iters=3000, tol=1e-12)
+    xG = res.xG
+    assert int(np.argmax(np.abs(xG))) == n0
+    truth = x.sum(axis=0)[n0]
+    assert truth * 0.95 <= xG[n0] <= truth
+    assert np.linalg.norm(np.delete(xG, n0)) <= 0.05 * truth
+
+
+# ------------------------------------------------------------- Algorithm 1
+def _elim_scene():
+    """A scene on which the gate opens near iteration 187 (rho = 1) and
+    Algorithm 1 then removes most pixels."""
+    sc, lam = _resolved(seed=2)
+    return sc, lam
+
+
+def test_eps_p_zero_is_plain_sadmm():
+    """zeta >= 0 always, so eps_p = 0 keeps every pixel: identical to SADMM."""
+    sc, lam = _elim_scene()
+    a = oracle.sadmm(sc.A, sc.y, 1.0, lam, oracle.Criterion(elim=0), iters=60)
+    b = oracle.sadmm(sc.A, sc.y, 1.0, lam, oracle.Criterion(elim=1, eps_p=0.0), iters=60)
+    assert np.array_equal(a.state.x, b.state.x)
+    assert np.array_equal(a.state.s, b.state.s)
+    assert all(len(j) == sc.geom.N for j in b.state.J)
+
+
+def _trajectory(sc, lam, crit, iters):
+    st = None
+    xs, Js, recs = [], [], []
+    for _ in range(iters):
+        r = oracle.sadmm(sc.A, sc.y, 1.0, lam, crit, iters=1, state=st)
+        st = r.state
+        xs.append(st.x.copy())
+        Js.append([j.copy() for j in st.J])
+        recs.append(r.history[-1])
+    return xs, Js, recs, st
+
+
+def test_ssc_window_and_monotone_sets():
+    """Recompute Algorithm 1 from the stored trajectory: at every gated
+    iteration J_q = {i in previous J_q : mean_{last Kp} |x^{t+1} - x^t| >= eps_p}.
+    Active sets only shrink, and frozen entries are bit-constant afterwards."""
+    sc, lam = _elim_scene()
+    crit = oracle.Criterion(elim=1, eps_p=1e-5, Kp=4)
+    x0 = np.zeros((sc.geom.Q, sc.geom.N))
+    xs, Js, recs, _ = _trajectory(sc, lam, crit, 200)
+    traj = [x0] + xs
+    prevJ = [np.arange(sc.geom.N)] * sc.geom.Q
+    removed_any = False
+    frozen_at = {}
+    for t, (J, rec) in enumerate(zip(Js, recs)):
+        k = t + 1
+        for q in range(sc.geom.Q):
+            assert set(J[q]) <= set(prevJ[q])
+            if rec["gate"]:
+                zeta = np.mean([np.abs(traj[u + 1][q] - traj[u][q]) for u in range(k - crit.Kp, k)],
+                               axis=0)
+                expect = prevJ[q][zeta[prevJ[q]] >= crit.eps_p]
+                assert np.array_equal(J[q], expect)
+            else:
+                assert np.array_equal(J[q], prevJ[q])
+            for i in set(prevJ[q]) - set(J[q]):
+                frozen_at[(q, i)] = (t, xs[t][q, i])
+                removed_any = True
+        prevJ = J
+    assert removed_any
+    for (q, i), (t, val) in frozen_at.items():
+        for u in range(t, len(xs)):
+            assert xs[u][q, i] == val
+
+
+def test_frozen_fold_is_the_restricted_problem():
+    """After elimination, y'_q = y_q - A_q,E x_q,E, and the next x-update equals the
+    minimiser of mu/2||y_q - A_q x||^2 + rho/2||x_J - v_J||^2 over x_J with the
+    frozen x_E held fixed (solved here by least squares on the stacked system)."""
+    sc, lam = _elim_scene()
+    crit = oracle.Criterion(elim=1, eps_p=1e-5, Kp=4)
+    r = oracle.sadmm(sc.A, sc.y, 1.0, lam, crit, iters=190)
+    st = r.state
+    q = int(np.argmin([len(j) for j in st.J]))
+    J = st.J[q]
+    E = np.setdiff1d(np.arange(sc.geom.N), J)
+    assert len(E) > 0
+    B = oracle.real_form(sc.A[q])
+    yq = oracle.real_vec(sc.y[q])
+    assert np.allclose(st.yprime[q], yq - B[:, E] @ st.x[q, E], rtol=0, atol=1e-12 * np.linalg.norm(yq))
+    nxt = oracle.sadmm(sc.A, sc.y, 1.0, lam, crit, iters=1, state=st).state
+    v = st.x[q, J] - st.xbar[J] + st.zbar[J] - st.s[J]
+    M = np.vstack([np.sqrt(crit.mu) * B[:, J], np.sqrt(1.0) * np.eye(len(J))])
+    rhs = np.concatenate([np.sqrt(crit.mu) * (yq - B[:, E] @ st.x[q, E]), np.sqrt(1.0) * v])
+    xJ = np.linalg.lstsq(M, rhs, rcond=None)[0]
+    assert np.allclose(nxt.x[q, J], xJ, rtol=1e-9, atol=1e-10)
+
+
+def test_residuals_follow_the_stacked_definitions():
+    """Residuals of Boyd Sec. 3.3.1 for the sharing problem written with copies
+    z_q (x_q - z_q = 0, z_q = x_q - x_bar + z_bar): recompute r_pri, eps_pri, d and
+    eps_dual from two consecutive states through the stacked vectors."""
+    sc, lam = _elim_scene()
+    crit = oracle.Criterion(elim=0)
+    rho = 1.0
+    a = oracle.sadmm(sc.A, sc.y, rho, lam, crit, iters=12).state
+    r = oracle.sadmm(sc.A, sc.y, rho, lam, crit, iters=1, state=a)
+    b, rec = r.state, r.history[-1]
+    Q, N = b.x.shape
+    Za = np.stack([a.x[q] - a.xbar + a.zbar for q in range(Q)]).ravel()
+    Zb = np.stack([b.x[q] - b.xbar + b.zbar for q in range(Q)]).ravel()
+    Xb = b.x.ravel()
+    assert np.isclose(rec["r_pri"], np.linalg.norm(Xb - Zb), rtol=1e-12)
+    assert np.isclose(rec["eps_pri"], np.sqrt(Xb.size) * crit.eps_abs
+                      + crit.eps_rel * max(np.linalg.norm(Xb), np.linalg.norm(Zb)), rtol=1e-12)
+    assert np.isclose(rec["d"], rho * np.linalg.norm(Zb - Za), rtol=1e-12)
+    U = np.tile(rho * b.s, Q)
+    assert np.isclose(rec["eps_dual"], np.sqrt(Xb.size) * crit.eps_abs
+                      + crit.eps_rel * np.linalg.norm(U), rtol=1e-12)
+    assert np.isclose(rec["relchange"], np.linalg.norm(b.x - a.x) / np.linalg.norm(b.x), rtol=1e-12)
+
+
+def test_resume_is_bit_exact():
+    """Running k1 then k2 iterations from the saved state equals k1 + k2 at once."""
+    sc, lam = _elim_scene()
+    crit = oracle.Criterion(elim=1, eps_p=1e-5, Kp=4)
+    full = oracle.sadmm(sc.A, sc.y, 1.0, lam, crit, iters=200)
+    half = oracle.sadmm(sc.A, sc.y, 1.0, lam, crit, iters=183)
+    rest = oracle.sadmm(sc.A, sc.y, 1.0, lam, crit, iters=17, state=half.state)
+    assert np.array_equal(full.state.x, rest.state.x)
+    assert [list(j) for j in full.state.J] == [list(j) for j in rest.state.J]
+
+
+def test_degenerate_sharing_certificate():
+    """When the per-sensor null spaces together span R^N (here: the 32x32 grid
+    seen by four 4-antenna sensors, 2KM = 512 < N = 1024), Eq. 2 is minimised with
+    x_G = 0: build a point with sum_q x_q = 0 that fits every sensor's data, and
+    check that its objective is far below that of the ground truth and below the
+    oracle's iterates."""
+    sc = scenegen.build_scene("small_point", seed=0)
+    lam = 0.05 * scenegen.lambda_max(sc.A, sc.y)
+    B = [oracle.real_form(a) for a in sc.A]
+    ys = [oracle.real_vec(v) for v in sc.y]
+    X0, nulls = [], []
+    for b, v in zip(B, ys):
+        U, S, Vt = np.linalg.svd(b)
+        r = int(np.sum(S > 1e-9 * S[0]))
+        X0.append(Vt[:r].T @ ((U[:, :r].T @ v) / S[:r]))
+        nulls.append(Vt[r:].T)
+    Nall = np.hstack(nulls)
+    c = np.linalg.lstsq(Nall, -np.sum(X0, axis=0), rcond=None)[0]
+    X, o = [], 0
+    for x0, nb in zip(X0, nulls):
+        X.append(x0 + nb @ c[o:o + nb.shape[1]])
+        o += nb.shape[1]
+    X = np.array(X)
+    assert np.max(np.abs(X.sum(axis=0))) <= 1e-8 * np.max(np.abs(X))
+    f_cert = oracle.objective(sc.A, sc.y, X, lam, B=B)
+    f_true = oracle.objective(sc.A, sc.y, sc.x_true, lam, B=B)
+    assert f_cert <= 1e-6 * f_true
+    it = oracle.sadmm(sc.A, sc.y, 1.0, lam, oracle.Criterion(elim=0), iters=50, B=B)
+    assert np.all(it.xG == 0.0)
+    assert oracle.objective(sc.A, sc.y, it.state.x, lam, B=B) >= f_cert
+
+
+# ------------------------------------------------------------ planted mistakes
+MUTANTS = {
+    "dual_sign": ("s_new = st.s + xbar_new - zbar_new", "s_new = st.s - xbar_new + zbar_new"),
+    "threshold_lambda": ("soft(xbar_new + st.s, lam / rho)", "soft(xbar_new + st.s, lam)"),
+    "paper_literal_x_update": ("v = st.x[q, J] - st.xbar[J] + st.zbar[J] - st.s[J]",
+                               "v = - st.xbar[J] * len(A) + st.zbar[J] - st.s[J]"),
+    "drop_rho_in_rhs": ("solvers[q].solve(cvec[q] + rho * v)", "solvers[q].solve(cvec[q] + v)"),
+    "mean_without_frozen": ("xbar_new = st.x.mean(axis=0)", "xbar_new = st.x.sum(axis=0)"),
+}
+
+
+def _mutant(name):
+    old, new = MUTANTS[name]
+    src = inspect.getsource(osadmm)
+    assert src.count(old) == 1, name
+    mod = types.ModuleType("oracle_mutant_" + name)
+    sys.modules[mod.__name__] = mod          # dataclasses look their module up here
+    try:
+        exec(compile(src.replace(old, new), osadmm.__file__, "exec"), mod.__dict__)
+    finally:
+        sys.modules.pop(mod.__name__, None)
+    return mod
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_catch_planted_mistakes(name):
+    sc = scenegen.random_problem(2, 24, 32, seed=21)
+    lam = 0.1 * scenegen.lambda_max(sc.A, sc.y)
+    rho = 2.0
+    m = _mutant(name)
+    with np.errstate(all="ignore"):
+        try:
+            res = m.sadmm(sc.A, sc.y, rho, lam, m.Criterion(elim=0), iters=3000, tol=1e-15)
+        except Exception:
+            return                     # blowing up is also caught
+        x, s = res.state.x, res.state.s
+        if not np.all(np.isfinite(x)):
+            return
+        k = oracle.kkt(sc.A, sc.y, x, s, rho, lam, xG=res.xG)
+        Xf, fval = oracle.fista(sc.A, sc.y, lam, iters=3000, tol=1e-13)
+        fa = oracle.objective(sc.A, sc.y, x, lam)
+    caught = (max(k.values()) > 1e-6) or abs(fa - fval) > 1e-8 * abs(fval)
+    assert caught, name
