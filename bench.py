@@ -1,0 +1,334 @@
+"""Benchmark of the sharing-ADMM hot path on one or more GPUs (replicas).
+
+Workload: the paper-scale scene (Q=8 sensors, M=8, K=256 so KM=2048,
+N=128x128 pixels, 40 clusters, 15 dB SNR, rho=1, lambda=0.05 lambda_max),
+operators resident in HBM (8 x 268 MB complex64, larger than L2).  One step is
+one cold-start solve of --iters iterations through the C ABI (Eq. 3 and, with
+--elim 1, Algorithm 1); the metric is SADMM iterations per second.
+
+Multi-GPU: each rank solves its own replica (different seed); no data-path
+collective.  `value` = iterations of all ranks / the slowest rank's time.
+
+--impl reference times the FP64 CPU oracle on the host cores on a bounded
+sample of the same workload (see cpu_baseline in the output).
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np
+
+METRIC = "SADMM iterations/s (Q=8, N=128^2, KM=2048)"
+UNIT = "iter/s"
+WORKLOAD = "paper_scale: Q=8 M=8 K=256 (KM=2048) N=128x128, 40 clusters, 15 dB, rho=1, lambda=0.05*lambda_max"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--iters", type=int, default=100, help="ADMM iterations per step")
+    ap.add_argument("--elim", type=int, default=0)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="paper_scale")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)),
+            int(os.environ.get("WORLD_SIZE", 1)))
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            mp = json.load(f)
+        return float(mp["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def source_sha():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2307_08606_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(f.encode())
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_for(kernel):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(p) as f:
+            t = json.load(f)
+        if t.get("source_sha") == source_sha() and kernel in t.get("kernels", {}):
+            return float(t["kernels"][kernel]["dram_bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out = ""
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except (ValueError, IndexError):
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline_sample(scene, lam, iters=4):
+    """The FP64 oracle on a bounded sample: one of the Q sensors of the same
+    scene (its own full operator), `iters` iterations timed after the factor;
+    scaled to the Q-sensor iteration rate (x-updates are per sensor and dominate)."""
+    import oracle
+    Q = scene.geom.Q
+    A1, y1 = [scene.A[0]], [scene.y[0]]
+    B1 = [oracle.real_form(A1[0])]
+    crit = oracle.Criterion(elim=0)
+    t0 = time.perf_counter()
+    oracle.sadmm(A1, y1, 1.0, lam, crit, iters=1, B=B1)
+    t1 = time.perf_counter()
+    oracle.sadmm(A1, y1, 1.0, lam, crit, iters=1 + iters, B=B1)
+    t2 = time.perf_counter()
+    per_sensor_iter = ((t2 - t1) - (t1 - t0)) / iters
+    cores = int(os.environ.get("OPENBLAS_NUM_THREADS", os.environ.get("OMP_NUM_THREADS", os.cpu_count())))
+    return {
+        "value": 1.0 / (Q * per_sensor_iter),
+        "unit": UNIT,
+        "cores": cores,
+        "kind": "oracle",
+        "sample": f"numpy FP64 oracle, sensor 0 of {Q} (full KM x N operator), {iters} iterations "
+                  f"timed after its factor; rate scaled by 1/{Q}",
+        "factor_s": round(t1 - t0, 3),
+    }
+
+
+def make_scene(name, seed):
+    import scenegen
+    sc = scenegen.build_scene(name, seed=seed)
+    lam = 0.05 * scenegen.lambda_max(sc.A, sc.y)
+    return sc, lam
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    sc, lam = make_scene(args.config, 0)
+    import oracle
+    A1, y1 = [sc.A[0]], [sc.y[0]]
+    B1 = [oracle.real_form(A1[0])]
+    crit = oracle.Criterion(elim=args.elim)
+    Q = sc.geom.Q
+    # a step: one oracle iteration of one sensor (bounded sample), scaled to Q sensors
+    base = oracle.sadmm(A1, y1, 1.0, lam, crit, iters=1, B=B1)
+    for _ in range(args.warmup):
+        oracle.sadmm(A1, y1, 1.0, lam, crit, iters=1, state=base.state, B=B1)
+    t_setup0 = time.perf_counter()
+    oracle.sadmm(A1, y1, 1.0, lam, crit, iters=0, state=base.state, B=B1)
+    t_setup = time.perf_counter() - t_setup0
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.sadmm(A1, y1, 1.0, lam, crit, iters=1, state=base.state, B=B1)
+    el = time.perf_counter() - t0 - args.steps * t_setup
+    per = el / args.steps
+    value = 1.0 / (Q * per)
+    cores = int(os.environ.get("OPENBLAS_NUM_THREADS", os.environ.get("OMP_NUM_THREADS", os.cpu_count())))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3 * Q,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "elim": args.elim},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"one FP64 oracle iteration of sensor 0 of {Q} per step "
+                                   f"(factor excluded), scaled by 1/{Q}"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    args = parse()
+    rank, local_rank, world = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import torch.distributed as dist
+    from paper_2307_08606_gb300 import build
+    build()
+    from paper_2307_08606_gb300 import binding
+
+    torch.cuda.set_device(local_rank)
+    if world > 1:
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream()
+
+    sc, lam = make_scene(args.config, rank)
+    g = sc.geom
+    s = binding.Solver(g.Q, g.M, g.K, g.N, 1.0, lam, stream=stream.cuda_stream, elim=args.elim)
+    for q in range(g.Q):
+        s.set_operator(q, torch.from_numpy(sc.A[q]).to(dev))
+    t0 = time.perf_counter()
+    s.prepare()
+    torch.cuda.synchronize()
+    factor_s = time.perf_counter() - t0
+    y_dev = [torch.from_numpy(v).to(dev) for v in sc.y]
+    xg = torch.empty(g.N, dtype=torch.float32, device=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        s.solve(y_dev, args.iters, out=xg)
+    s.set_profiling(True)
+    barrier()
+    n0 = binding.launch_count()
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    iters_done = 0
+    refresh_ms = 0.0
+    with ClockSampler(local_rank) as clk:
+        start.record(stream)
+        for _ in range(args.steps):
+            _, st = s.solve(y_dev, args.iters, out=xg)
+            iters_done += st["iters"]
+            refresh_ms += st["ms_refresh"]
+        end.record(stream)
+        barrier()
+    launches = binding.launch_count() - n0
+    ms = start.elapsed_time(end)
+    prof = s.profile()
+    s.set_profiling(False)
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    it = torch.tensor([float(iters_done)], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(it, op=dist.ReduceOp.SUM)
+    ms_max = float(t.item())
+    value = float(it.item()) / (ms_max / 1e3)
+
+    # end to end through the C ABI with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        y_host = [torch.from_numpy(v).pin_memory() for v in sc.y]
+        x_host = torch.empty(g.N, dtype=torch.float32).pin_memory()
+        barrier()
+        t0 = time.perf_counter()
+        e_iters = 0
+        for _ in range(args.steps):
+            _, st = s.solve(y_host, args.iters, out=x_host)
+            e_iters += st["iters"]
+        torch.cuda.synchronize()
+        e_ms = (time.perf_counter() - t0) * 1e3
+        te = torch.tensor([e_ms], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        e2e = {"value": world * e_iters / (float(te.item()) / 1e3), "unit": UNIT,
+               "h2d_bytes_per_step": int(g.Q * g.KM * 8), "d2h_bytes_per_step": int(g.N * 4)}
+
+    # roofline of the dominant kernel group
+    hbm, src = peaks()
+    per_launch_bytes = {
+        "forward": 2 * 0 + g.Q * g.KM * g.N * 8.0,
+        "adjoint_update": g.Q * g.KM * g.N * 8.0,
+        "spd_woodbury": g.Q * (2 * g.KM) ** 2 * 8.0,
+    }
+    dom = max((k for k in prof if prof[k][1] > 0), key=lambda k: prof[k][0])
+    dom_ms, dom_n = prof[dom]
+    ach = per_launch_bytes.get(dom, 0.0) / (dom_ms / dom_n / 1e3) / 1e9 if dom_n else None
+    roof = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": hbm, "unit": "GB/s",
+            "frac": (ach / hbm) if ach else None, "traffic": traffic_for(dom),
+            "peak_source": src,
+            "phases_ms_per_launch": {k: (v[0] / v[1] if v[1] else None) for k, v in prof.items()},
+            "algorithmic_bytes_per_launch": per_launch_bytes.get(dom)}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "iters_per_step": args.iters, "elim": args.elim,
+                   "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (operators 2.1 GB per replica)",
+                   "factor_s": round(factor_s, 3), "refresh_ms_total": round(refresh_ms, 3)},
+        "roofline": roof,
+        "e2e": e2e,
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        try:
+            line["cpu_baseline"] = cpu_baseline_sample(sc, lam)
+        except Exception as e:           # the baseline is reported, never required
+            line["cpu_baseline"] = {"error": str(e)}
+    if rank == 0:
+        print(json.dumps(line))
+    s.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,210 @@
+/*
+ * sadmm.h -- C ABI of the GB300 sharing-ADMM radar-imaging library.
+ *
+ * The library runs the per-iteration hot path of accelerated sharing ADMM
+ * (ASADMM, "Distributed Radar Imaging Based on Accelerated ADMM", Section III)
+ * on one GPU: for Q sensors with complex operators A_q (KM x N, Eq. 1) and
+ * measurements y_q it iterates
+ *
+ *   x_q,J  <- (rho I + mu B_J^T B_J)^{-1} (mu B_J^T y'_q + rho v_J)      Eq. 3, line 1
+ *             v = x_q - x_bar + z_bar - s, on the active set J_q only
+ *   z_bar  <- soft(x_bar + s, lambda / rho)                               Eq. 3, line 2
+ *   s      <- s + x_bar - z_bar                                           Eq. 3, line 3
+ *   J_q    <- SSC(last Kp updates, eps_p) when ||eta_pri|| <= eps_pri       Eq. 3, line 4; Algorithm 1
+ *
+ * with B = [Re A; Im A] the real form of A, x_bar = mean_q x_q, x_G = Q z_bar
+ * the output image and s the scaled dual (the paper's sigma = rho s, its
+ * beta = rho).  Removed pixels keep their value (freeze_mode 0) and are folded
+ * into y'_q = y_q - A_q,E x_q,E, or are set to zero (freeze_mode 1).
+ *
+ * Conventions
+ *   - Complex data are interleaved float pairs (re, im): "complex64".
+ *   - A_q is PIXEL-MAJOR: element (row r, pixel n) is at float offset
+ *     2 * (n * K * M + r) (re) and 2 * (n * K * M + r) + 1 (im); row r = m K + k.
+ *   - x vectors are float32, length N, pixel n = iy * nx + ix.
+ *   - Pointers documented "host or device" may be either (unified virtual
+ *     addressing, cudaMemcpyDefault); host memory may be pageable or pinned.
+ *   - Every function returns SADMM_OK (0) or a negative status; no C++
+ *     exception crosses this boundary.  sadmm_last_error() gives a message.
+ *   - Work is issued on the context's stream (sadmm_set_stream); calls that
+ *     return host-visible results synchronise that stream.
+ *   - Memory: device buffers come from the allocator installed with
+ *     sadmm_set_allocator (default cudaMalloc / cudaFree).
+ */
+#ifndef SADMM_H
+#define SADMM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SADMM_OK          0
+#define SADMM_EINVAL     -1   /* invalid argument or size                     */
+#define SADMM_ENOMEM     -2   /* device or host allocation failed             */
+#define SADMM_ECUDA      -3   /* a CUDA runtime call or kernel launch failed  */
+#define SADMM_ETIMEOUT   -4   /* a bounded device-side wait gave up           */
+#define SADMM_ENOTREADY  -5   /* an operator has not been set                 */
+#define SADMM_ENONFINITE -6   /* NaN or Inf in an input or an iterate         */
+
+typedef struct sadmm_ctx* sadmm_t;
+
+/* Method knobs.  Defaults (sadmm_default_criterion) are the paper's values
+ * (Section IV): Kp = 5, eps_p = 1e-5, eps_abs = 1e-4, eps_rel = 1e-2; mu = 1. */
+typedef struct {
+  double mu;          /* data-fidelity weight of Eq. 2                                  */
+  int    Kp;          /* Algorithm 1 window: number of past updates averaged (1..64)    */
+  double eps_p;       /* Algorithm 1 tolerance: keep pixel i iff zeta_i >= eps_p         */
+  double eps_abs;     /* absolute feasibility tolerance (gate of Algorithm 1, stop)      */
+  double eps_rel;     /* relative feasibility tolerance                                 */
+  int    elim;        /* 0 = plain SADMM, 1 = pixel elimination (ASADMM)                 */
+  int    freeze_mode; /* 0 = removed pixels keep their value, 1 = removed pixels set to 0 */
+  int    stop;        /* 0 = ||X^{k+1}-X^k||_F <= tol ||X^{k+1}||_F; 1 = primal & dual
+                         residuals below eps_pri and eps_dual (Boyd Sec. 3.3.1)          */
+} sadmm_criterion;
+
+/* Per-solve summary. */
+typedef struct {
+  int    iters;        /* iterations run                                              */
+  int    stop_reason;  /* 0 = iteration limit, 1 = relative change, 2 = residuals      */
+  int    refreshes;    /* factor refreshes after active-set changes                    */
+  int    active_total; /* sum_q |J_q| at the end                                       */
+  double r_pri, eps_pri, d, eps_dual, relchange;   /* last iteration                    */
+  double ms_total;     /* host wall time of the solve                                  */
+  double ms_refresh;   /* of which: fold + factor refresh after set changes            */
+  double bytes_iter;   /* algorithmic bytes read by the iteration kernels, summed      */
+} sadmm_stats;
+
+/* One record per iteration of the last solve. */
+typedef struct {
+  int    k;            /* iterations completed                                         */
+  int    gate;         /* 1 if Algorithm 1's test ran (elim on, k >= Kp, r_pri <= eps_pri) */
+  int    changed;      /* number of sensors whose active set shrank                    */
+  int    active_total; /* sum_q |J_q| after this iteration                             */
+  double r_pri, eps_pri, d, eps_dual, relchange;
+} sadmm_iter_record;
+
+typedef void* (*sadmm_alloc_fn)(size_t bytes, void* stream, void* user);
+typedef void  (*sadmm_free_fn)(void* ptr, void* stream, void* user);
+
+/* Fills *c with the defaults above. */
+void sadmm_default_criterion(sadmm_criterion* c);
+
+/* Installs the device allocator used by contexts created afterwards
+ * (NULL, NULL restores cudaMalloc / cudaFree).  The functions are called with
+ * the context's stream.  Not thread-safe against concurrent sadmm_create. */
+int sadmm_set_allocator(sadmm_alloc_fn alloc, sadmm_free_fn release, void* user);
+
+/* Creates a solver for Q sensors, M receivers, K fast-time samples and N pixels
+ * on the current CUDA device (Eq. 1 sizes, Eq. 2 weights rho = beta, lambda).
+ * Requirements: 1 <= Q <= 64, K*M a multiple of 32 and <= 16384, 1 <= N, rho > 0,
+ * lambda >= 0, crit->mu > 0, 1 <= crit->Kp <= 64.  Allocates all device state
+ * (about (8 K M N + 16 min(N, 2KM)^2) Q bytes plus O((Kp + 4) Q N)).
+ * crit may be NULL (defaults).  On failure *out is NULL. */
+int sadmm_create(int Q, int M, int K, int N, double rho, double lambda,
+                 const sadmm_criterion* crit, sadmm_t* out);
+
+/* Uses `stream` (a cudaStream_t, may be NULL for the legacy default stream)
+ * for all later work of this context. */
+int sadmm_set_stream(sadmm_t ctx, void* stream);
+
+/* Copies operator A_q (pixel-major complex64, N*K*M complex values; host or
+ * device pointer) into the context and invalidates sensor q's factor. */
+int sadmm_set_operator(sadmm_t ctx, int q, const float* A_q);
+
+/* Computes the full-active-set factor of every sensor whose operator changed:
+ * (rho I + mu B B^T)^{-1} if N > 2KM, else (rho I + mu B^T B)^{-1}, in FP64
+ * (Gram, Cholesky, explicit inverse).  It is kept and reused by later solves.
+ * Called implicitly by sadmm_solve; returns SADMM_ENOTREADY if an operator
+ * is missing. */
+int sadmm_prepare(sadmm_t ctx);
+
+/* Runs at most `iters` iterations from zero on measurements y[0..Q-1] (each
+ * K*M complex64 values, host or device) and writes x_G = Q z_bar (N floats,
+ * host or device; may be NULL).  tol is the stop-mode-0 relative-change
+ * tolerance (<= 0 disables it).  st may be NULL. */
+int sadmm_solve(sadmm_t ctx, const float* const* y, float* x_out, int iters, double tol,
+                sadmm_stats* st);
+
+/* Continues from the current state for at most `iters` more iterations
+ * (same outputs as sadmm_solve). */
+int sadmm_resume(sadmm_t ctx, float* x_out, int iters, double tol, sadmm_stats* st);
+
+/* Copies x_q (N floats) to `out` (host or device). */
+int sadmm_get_xq(sadmm_t ctx, int q, float* out);
+
+/* Copies the active set J_q (sorted pixel indices, host or device int32 array
+ * of capacity N) to idx and its size to *count (host). */
+int sadmm_get_active(sadmm_t ctx, int q, int* idx, int* count);
+
+/* Iteration records of the last solve/resume: copies up to cap records and
+ * returns how many were written (or a negative status). */
+int sadmm_history(sadmm_t ctx, sadmm_iter_record* out, int cap);
+
+/* Checkpoint: serialises (k, x, x_bar, z_bar, s, the Kp-deep update ring, the
+ * active sets and y') into host memory.  With buf == NULL only *bytes is set. */
+int sadmm_get_state(sadmm_t ctx, void* buf, size_t* bytes);
+
+/* Restores a checkpoint made by sadmm_get_state (same sizes and Kp).  Factors
+ * are recomputed for active sets that are not full. */
+int sadmm_set_state(sadmm_t ctx, const void* buf, size_t bytes);
+
+/* Profiling (tracing): when on, every kernel group of the iteration is
+ * bracketed by CUDA events on the context's stream and its device time is
+ * accumulated per phase.  Phases: 0 forward product (partials + reduction),
+ * 1 Woodbury SPD apply, 2 adjoint + x-update (Woodbury form), 3 adjoint
+ * (primal form), 4 SPD apply + x-update (primal form), 5 prox/dual/residuals,
+ * 6 Algorithm 1 compaction, 7 fold + factor refresh.  Turning it on resets
+ * the totals. */
+#define SADMM_NUM_PHASES 8
+int sadmm_set_profiling(sadmm_t ctx, int on);
+
+/* Copies min(cap, SADMM_NUM_PHASES) accumulated phase times (ms) and launch
+ * counts; returns the number of phases copied. */
+int sadmm_profile(sadmm_t ctx, double* ms, long long* launches, int cap);
+
+/* Number of kernels this library has launched in this process. */
+long long sadmm_launch_count(void);
+
+/* Releases all device memory of the context. */
+void sadmm_destroy(sadmm_t ctx);
+
+const char* sadmm_strerror(int status);
+const char* sadmm_last_error(void);
+
+/* ------------------------------------------------------------------------
+ * Kernel-level entry points on DEVICE pointers (used by parity tests and for
+ * composing other pipelines).  All work is on `stream`; none synchronises.
+ * ---------------------------------------------------------------------- */
+
+/* r = base - A_J v_J  (Eq. 1 forward product over the listed columns).
+ * A: pixel-major complex64 (N x KM), idx: nidx pixel indices in [0, N)
+ * (any order, repeats allowed), v: N floats indexed by pixel, base and r:
+ * KM complex64 (base may be NULL for 0; r may alias base). */
+int sadmm_forward(const float* A, int KM, int N, const int* idx, int nidx, const float* v,
+                  const float* base, float* r, void* stream);
+
+/* g[p] = Re(a_{idx[p]}^H w) for p < nidx (adjoint of the real-input forward
+ * product).  w: KM complex64 (KM even, <= 16384); g: nidx floats. */
+int sadmm_adjoint(const float* A, int KM, int N, const int* idx, int nidx, const float* w,
+                  float* g, void* stream);
+
+/* Factor of the x-update (Eq. 3, line 1) for the listed columns, in FP64:
+ * if nidx > 2KM, F = (rho I + mu B_J B_J^T)^{-1} with B_J rows interleaved
+ * (re, im) per sample (dimension n = 2KM, *form = 1); otherwise
+ * F = (rho I + mu B_J^T B_J)^{-1} (n = nidx, *form = 0).  F is n x n,
+ * row-major with leading dimension ldf >= roundup(n, 64), capacity
+ * ldf * ldf doubles; the padding is overwritten.  form is a host pointer. */
+int sadmm_factor(const float* A, int KM, int N, const int* idx, int nidx, double mu,
+                 double rho, double* F, int ldf, int* form, void* stream);
+
+/* out = F u for a symmetric n x n FP64 matrix (row-major, leading dimension
+ * ldf even and >= n, 16-byte aligned; n <= 32768), u and out n floats. */
+int sadmm_spd_apply(const double* F, int n, int ldf, const float* u, float* out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SADMM_H */

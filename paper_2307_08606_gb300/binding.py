@@ -1,0 +1,334 @@
+"""ctypes binding of libsadmm.so (include/sadmm.h).
+
+Argument marshalling only: every step of the solver runs in the library's CUDA
+kernels.  Host arrays are numpy; device arrays are torch CUDA tensors, whose
+data pointers are passed straight through.  The library must have been built
+(``paper_2307_08606_gb300.build.build()``); loading fails loudly otherwise.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+from .build import LIB
+
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENOTREADY, ENONFINITE = 0, -1, -2, -3, -4, -5, -6
+
+
+class SadmmError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"sadmm status {status}: {message}")
+        self.status = status
+
+
+class Criterion(C.Structure):
+    _fields_ = [("mu", C.c_double), ("Kp", C.c_int), ("eps_p", C.c_double),
+                ("eps_abs", C.c_double), ("eps_rel", C.c_double), ("elim", C.c_int),
+                ("freeze_mode", C.c_int), ("stop", C.c_int)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("iters", C.c_int), ("stop_reason", C.c_int), ("refreshes", C.c_int),
+                ("active_total", C.c_int), ("r_pri", C.c_double), ("eps_pri", C.c_double),
+                ("d", C.c_double), ("eps_dual", C.c_double), ("relchange", C.c_double),
+                ("ms_total", C.c_double), ("ms_refresh", C.c_double), ("bytes_iter", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class IterRecord(C.Structure):
+    _fields_ = [("k", C.c_int), ("gate", C.c_int), ("changed", C.c_int), ("active_total", C.c_int),
+                ("r_pri", C.c_double), ("eps_pri", C.c_double), ("d", C.c_double),
+                ("eps_dual", C.c_double), ("relchange", C.c_double)]
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
+
+_P = C.c_void_p
+_SIGS = {
+    "sadmm_default_criterion": (None, [C.POINTER(Criterion)]),
+    "sadmm_set_allocator": (C.c_int, [ALLOC_FN, FREE_FN, _P]),
+    "sadmm_create": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double,
+                               C.POINTER(Criterion), C.POINTER(_P)]),
+    "sadmm_set_stream": (C.c_int, [_P, _P]),
+    "sadmm_set_operator": (C.c_int, [_P, C.c_int, _P]),
+    "sadmm_prepare": (C.c_int, [_P]),
+    "sadmm_solve": (C.c_int, [_P, C.POINTER(_P), _P, C.c_int, C.c_double, C.POINTER(Stats)]),
+    "sadmm_resume": (C.c_int, [_P, _P, C.c_int, C.c_double, C.POINTER(Stats)]),
+    "sadmm_get_xq": (C.c_int, [_P, C.c_int, _P]),
+    "sadmm_get_active": (C.c_int, [_P, C.c_int, _P, C.POINTER(C.c_int)]),
+    "sadmm_history": (C.c_int, [_P, C.POINTER(IterRecord), C.c_int]),
+    "sadmm_get_state": (C.c_int, [_P, _P, C.POINTER(C.c_size_t)]),
+    "sadmm_set_state": (C.c_int, [_P, _P, C.c_size_t]),
+    "sadmm_set_profiling": (C.c_int, [_P, C.c_int]),
+    "sadmm_profile": (C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(C.c_longlong), C.c_int]),
+    "sadmm_launch_count": (C.c_longlong, []),
+    "sadmm_destroy": (None, [_P]),
+    "sadmm_strerror": (C.c_char_p, [C.c_int]),
+    "sadmm_last_error": (C.c_char_p, []),
+    "sadmm_forward": (C.c_int, [_P, C.c_int, C.c_int, _P, C.c_int, _P, _P, _P, _P]),
+    "sadmm_adjoint": (C.c_int, [_P, C.c_int, C.c_int, _P, C.c_int, _P, _P, _P]),
+    "sadmm_factor": (C.c_int, [_P, C.c_int, C.c_int, _P, C.c_int, C.c_double, C.c_double, _P,
+                               C.c_int, C.POINTER(C.c_int), _P]),
+    "sadmm_spd_apply": (C.c_int, [_P, C.c_int, C.c_int, _P, _P, _P]),
+}
+
+_lib = None
+
+
+def library_path():
+    return LIB
+
+
+def load():
+    """Load libsadmm.so and declare its signatures (raises if it is not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB):
+        raise RuntimeError(f"{LIB} is missing: build it with paper_2307_08606_gb300.build.build()")
+    lib = C.CDLL(LIB)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def launch_count():
+    """Kernels launched by the library in this process."""
+    return int(load().sadmm_launch_count())
+
+
+def check(status):
+    if status != OK:
+        lib = load()
+        raise SadmmError(status, lib.sadmm_last_error().decode(errors="replace"))
+    return status
+
+
+def default_criterion(**kw):
+    c = Criterion()
+    load().sadmm_default_criterion(C.byref(c))
+    for k, v in kw.items():
+        setattr(c, k, v)
+    return c
+
+
+# ------------------------------------------------------------------ torch glue
+_torch_alloc = None
+
+
+def use_torch_allocator():
+    """Route the library's device allocations through torch's caching allocator."""
+    global _torch_alloc
+    import torch
+
+    def _alloc(nbytes, stream, user):
+        dev = torch.cuda.current_device()
+        return torch.cuda.caching_allocator_alloc(int(nbytes), dev, stream)
+
+    def _free(ptr, stream, user):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    _torch_alloc = (ALLOC_FN(_alloc), FREE_FN(_free))
+    check(load().sadmm_set_allocator(_torch_alloc[0], _torch_alloc[1], None))
+
+
+def _ptr(a):
+    """Data pointer of a numpy array or torch tensor (contiguous)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        assert a.flags.c_contiguous
+        return a.ctypes.data
+    assert a.is_contiguous()
+    return a.data_ptr()
+
+
+def _as_c64(a):
+    if isinstance(a, np.ndarray):
+        return np.ascontiguousarray(a, dtype=np.complex64)
+    import torch
+    return a.to(torch.complex64).contiguous()
+
+
+class Solver:
+    """One sadmm context (Eq. 3 with Algorithm 1 on one GPU)."""
+
+    def __init__(self, Q, M, K, N, rho, lam, stream=None, **criterion):
+        self.lib = load()
+        self.Q, self.M, self.K, self.N, self.KM = Q, M, K, N, K * M
+        self.crit = default_criterion(**criterion)
+        h = C.c_void_p()
+        check(self.lib.sadmm_create(Q, M, K, N, float(rho), float(lam), C.byref(self.crit), C.byref(h)))
+        self.h = h
+        if stream is not None:
+            check(self.lib.sadmm_set_stream(self.h, C.c_void_p(stream)))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.sadmm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream):
+        check(self.lib.sadmm_set_stream(self.h, C.c_void_p(stream)))
+
+    def set_operator(self, q, A):
+        """A: (N, KM) complex64 pixel-major, numpy (host) or torch (host/cuda)."""
+        A = _as_c64(A)
+        assert tuple(A.shape) == (self.N, self.KM), A.shape
+        check(self.lib.sadmm_set_operator(self.h, q, _ptr(A)))
+
+    def prepare(self):
+        check(self.lib.sadmm_prepare(self.h))
+
+    def solve(self, y, iters, tol=0.0, out=None):
+        """y: Q arrays of KM complex64 (host or device).  Returns (x_G, stats);
+        x_G is written to `out` if given (numpy or torch), else a new numpy array."""
+        ys = [_as_c64(v) for v in y]
+        arr = (C.c_void_p * self.Q)(*[_ptr(v) for v in ys])
+        if out is None:
+            out = np.empty(self.N, dtype=np.float32)
+        st = Stats()
+        check(self.lib.sadmm_solve(self.h, arr, _ptr(out), int(iters), float(tol), C.byref(st)))
+        return out, st.as_dict()
+
+    def resume(self, iters, tol=0.0, out=None):
+        if out is None:
+            out = np.empty(self.N, dtype=np.float32)
+        st = Stats()
+        check(self.lib.sadmm_resume(self.h, _ptr(out), int(iters), float(tol), C.byref(st)))
+        return out, st.as_dict()
+
+    def xq(self, q):
+        out = np.empty(self.N, dtype=np.float32)
+        check(self.lib.sadmm_get_xq(self.h, q, _ptr(out)))
+        return out
+
+    def X(self):
+        return np.stack([self.xq(q) for q in range(self.Q)])
+
+    def active(self, q):
+        idx = np.empty(self.N, dtype=np.int32)
+        n = C.c_int()
+        check(self.lib.sadmm_get_active(self.h, q, _ptr(idx), C.byref(n)))
+        return idx[: n.value].copy()
+
+    def history(self):
+        n = self.lib.sadmm_history(self.h, None, 0)
+        recs = (IterRecord * max(n, 1))()
+        m = self.lib.sadmm_history(self.h, recs, n)
+        return [{k: getattr(recs[i], k) for k, _ in IterRecord._fields_} for i in range(m)]
+
+    PHASES = ("forward", "spd_woodbury", "adjoint_update", "adjoint_primal", "spd_update",
+              "residuals", "ssc", "refresh")
+
+    def set_profiling(self, on=True):
+        check(self.lib.sadmm_set_profiling(self.h, int(on)))
+
+    def profile(self):
+        ms = (C.c_double * 8)()
+        n = (C.c_longlong * 8)()
+        k = self.lib.sadmm_profile(self.h, ms, n, 8)
+        return {self.PHASES[i]: (ms[i], n[i]) for i in range(k)}
+
+    def get_state(self):
+        n = C.c_size_t()
+        check(self.lib.sadmm_get_state(self.h, None, C.byref(n)))
+        buf = np.empty(n.value, dtype=np.uint8)
+        check(self.lib.sadmm_get_state(self.h, _ptr(buf), C.byref(n)))
+        return buf
+
+    def set_state(self, buf):
+        buf = np.ascontiguousarray(buf, dtype=np.uint8)
+        check(self.lib.sadmm_set_state(self.h, _ptr(buf), buf.size))
+
+
+# ------------------------------------------------------ state blob conversion
+def pack_state(Q, N, KM, Kp, k, x, xbar, zbar, s, ring, J, yprime):
+    """Build a state blob (layout of sadmm_get_state) from host arrays."""
+    hdr = np.array([0x31766174734d4453], dtype=np.uint64).tobytes() + np.array(
+        [Q, N, KM, Kp, k, 0], dtype=np.int32).tobytes()
+    cnt = np.array([len(j) for j in J], dtype=np.int32)
+    Jpad = np.zeros((Q, N), dtype=np.int32)
+    for q, j in enumerate(J):
+        Jpad[q, : len(j)] = j
+    parts = [hdr, np.asarray(x, np.float32).tobytes(), np.asarray(xbar, np.float32).tobytes(),
+             np.asarray(zbar, np.float32).tobytes(), np.asarray(s, np.float32).tobytes(),
+             np.asarray(ring, np.float32).tobytes(), cnt.tobytes(), Jpad.tobytes(),
+             np.asarray(yprime, np.complex64).tobytes()]
+    return np.frombuffer(b"".join(parts), dtype=np.uint8).copy()
+
+
+def unpack_state(buf, Q, N, KM, Kp):
+    b = np.asarray(buf, dtype=np.uint8).tobytes()
+    o = 8 + 24
+    k = int(np.frombuffer(b[8:32], dtype=np.int32)[4])
+
+    def take(n, dt):
+        nonlocal o
+        a = np.frombuffer(b[o:o + n * np.dtype(dt).itemsize], dtype=dt).copy()
+        o += n * np.dtype(dt).itemsize
+        return a
+    x = take(Q * N, np.float32).reshape(Q, N)
+    xbar, zbar, s = take(N, np.float32), take(N, np.float32), take(N, np.float32)
+    ring = take(Kp * Q * N, np.float32).reshape(Kp, Q, N)
+    cnt = take(Q, np.int32)
+    Jp = take(Q * N, np.int32).reshape(Q, N)
+    yp = take(Q * KM, np.complex64).reshape(Q, KM)
+    return dict(k=k, x=x, xbar=xbar, zbar=zbar, s=s, ring=ring,
+                J=[Jp[q, : cnt[q]].copy() for q in range(Q)], yprime=yp)
+
+
+# ------------------------------------------------------------ kernel level
+def forward(A, idx, v, base=None, out=None, stream=0):
+    """r = base - A_idx v_idx on device tensors (see sadmm_forward)."""
+    import torch
+    KM = A.shape[1]
+    if out is None:
+        out = torch.empty(KM, dtype=torch.complex64, device=A.device)
+    check(load().sadmm_forward(_ptr(A), KM, A.shape[0], _ptr(idx), int(idx.numel()), _ptr(v),
+                               _ptr(base), _ptr(out), C.c_void_p(stream)))
+    return out
+
+
+def adjoint(A, idx, w, out=None, stream=0):
+    import torch
+    KM = A.shape[1]
+    if out is None:
+        out = torch.empty(int(idx.numel()), dtype=torch.float32, device=A.device)
+    check(load().sadmm_adjoint(_ptr(A), KM, A.shape[0], _ptr(idx), int(idx.numel()), _ptr(w),
+                               _ptr(out), C.c_void_p(stream)))
+    return out
+
+
+def factor(A, idx, mu, rho, stream=0):
+    """Returns (F, form, n): F the padded FP64 factor as a torch tensor."""
+    import torch
+    KM = A.shape[1]
+    nidx = int(idx.numel())
+    n = 2 * KM if nidx > 2 * KM else nidx
+    npad = (n + 63) // 64 * 64
+    F = torch.empty((npad, npad), dtype=torch.float64, device=A.device)
+    form = C.c_int()
+    check(load().sadmm_factor(_ptr(A), KM, A.shape[0], _ptr(idx), nidx, float(mu), float(rho),
+                              _ptr(F), npad, C.byref(form), C.c_void_p(stream)))
+    return F, form.value, n
+
+
+def spd_apply(F, n, u, out=None, stream=0):
+    import torch
+    if out is None:
+        out = torch.empty(n, dtype=torch.float32, device=F.device)
+    check(load().sadmm_spd_apply(_ptr(F), n, F.shape[1], _ptr(u), _ptr(out), C.c_void_p(stream)))
+    return out

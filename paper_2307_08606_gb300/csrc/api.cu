@@ -1,0 +1,827 @@
+// C ABI and host orchestration of the sharing-ADMM solver (Section III:
+// Eq. 3 iterated with Algorithm 1).  One context owns the device state of
+// one problem; all work goes to the context's stream.
+#include "common.cuh"
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <new>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+namespace sadmm {
+
+static thread_local std::string g_err;
+static std::atomic<long long> g_launches{0};
+
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+void set_error(const char* fmt, ...) {
+  char buf[1024];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+}
+
+namespace {
+
+struct Allocator {
+  sadmm_alloc_fn alloc = nullptr;
+  sadmm_free_fn release = nullptr;
+  void* user = nullptr;
+};
+Allocator g_alloc;
+
+struct Sensor {
+  float2* A = nullptr;       // N x KM pixel-major
+  float2* y = nullptr;       // KM
+  float2* yp = nullptr;      // KM, y minus frozen contributions
+  float2* r = nullptr;       // KM, residual y' - A_J v_J
+  float2* w = nullptr;       // KM, W r (Woodbury form)
+  float* g = nullptr;        // N, Re(A_J^H r) in list order (primal form)
+  int* J = nullptr;          // N, active list
+  int* E = nullptr;          // N, pixels removed in the last SSC pass
+  double* fb[3] = {nullptr, nullptr, nullptr};   // factor buffers
+  double* dinv = nullptr;
+  int full = 0;              // buffer holding the full-set factor
+  bool full_valid = false;
+  int cur = 0;               // buffer in use
+  int n = 0;                 // factor dimension in use
+  int woodbury = 0;          // form in use
+  int cnt = 0;               // |J_q| (host mirror)
+  bool op_set = false;
+};
+
+uint64_t constexpr kStateMagic = 0x31766174734d4453ull;   // "SDMstav1"
+
+}  // namespace
+
+struct Ctx {
+  int Q = 0, M = 0, K = 0, N = 0, KM = 0;
+  double rho = 1.0, lam = 0.0;
+  sadmm_criterion crit{};
+  cudaStream_t st = nullptr;
+  Allocator alloc;
+  std::vector<void*> owned;
+  std::vector<Sensor> s;
+  float *x = nullptr, *xbar = nullptr, *zbar = nullptr, *sd = nullptr, *ring = nullptr;
+  float* xg = nullptr;
+  int* iota = nullptr;
+  float2* partial = nullptr;
+  size_t partial_cap = 0;
+  double* red = nullptr;
+  unsigned int* ticket = nullptr;
+  IterScalars* scal = nullptr;
+  int* counts = nullptr;       // 2Q: |J_q|, |E_q|
+  int* dstatus = nullptr;      // Q factor status flags
+  IterScalars* h_scal = nullptr;
+  int* h_counts = nullptr;
+  int* h_status = nullptr;
+  int npad_max = 0;
+  int k = 0;
+  std::vector<sadmm_iter_record> hist;
+  // profiling: one event pair per phase, reused every iteration
+  bool prof = false;
+  cudaEvent_t ev[2 * SADMM_NUM_PHASES] = {};
+  bool ev_used[SADMM_NUM_PHASES] = {};
+  double prof_ms[SADMM_NUM_PHASES] = {};
+  long long prof_n[SADMM_NUM_PHASES] = {};
+
+  void mark(int phase, bool begin) {
+    if (!prof) return;
+    cudaEventRecord(ev[2 * phase + (begin ? 0 : 1)], st);
+    if (!begin) ev_used[phase] = true;
+  }
+  // After a stream synchronisation: fold the recorded phase times in.
+  void collect() {
+    if (!prof) return;
+    for (int p = 0; p < SADMM_NUM_PHASES; ++p) {
+      if (!ev_used[p]) continue;
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, ev[2 * p], ev[2 * p + 1]) == cudaSuccess) {
+        prof_ms[p] += ms;
+        prof_n[p] += 1;
+      }
+      ev_used[p] = false;
+    }
+  }
+
+  void* dalloc(size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    void* p = nullptr;
+    if (alloc.alloc) {
+      p = alloc.alloc(bytes, (void*)st, alloc.user);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+      p = nullptr;
+    }
+    if (p) owned.push_back(p);
+    return p;
+  }
+  void release_all() {
+    cudaStreamSynchronize(st);
+    for (void* p : owned) {
+      if (alloc.release) alloc.release(p, (void*)st, alloc.user);
+      else cudaFree(p);
+    }
+    owned.clear();
+    if (h_scal) cudaFreeHost(h_scal);
+    if (h_counts) cudaFreeHost(h_counts);
+    if (h_status) cudaFreeHost(h_status);
+    for (auto& e : ev)
+      if (e) { cudaEventDestroy(e); e = nullptr; }
+    h_scal = nullptr;
+    h_counts = nullptr;
+    h_status = nullptr;
+  }
+  SolverView view() const {
+    SolverView v;
+    v.Q = Q; v.N = N; v.KM = KM; v.Kp = crit.Kp;
+    v.mu = (float)crit.mu; v.rho = (float)rho; v.lam_over_rho = (float)(lam / rho);
+    v.x = x; v.xbar = xbar; v.zbar = zbar; v.s = sd; v.ring = ring;
+    v.slot = k % crit.Kp;
+    return v;
+  }
+};
+
+namespace {
+
+double now_ms() {
+  using namespace std::chrono;
+  return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
+}
+
+__global__ void iota_kernel(int* p, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) p[i] = i;
+}
+
+int factor_dims(const Ctx& c, int cnt, int* n, int* woodbury) {
+  *woodbury = cnt > 2 * c.KM ? 1 : 0;
+  *n = *woodbury ? 2 * c.KM : cnt;
+  return SADMM_OK;
+}
+
+// Factor refresh for the listed sensors at their current active sets.
+int refresh(Ctx& c, const std::vector<int>& qs, bool full_set) {
+  std::vector<FactorJob> jobs;
+  std::vector<int> owner, outbuf;
+  for (int q : qs) {
+    Sensor& S = c.s[q];
+    if (S.cnt == 0) { S.n = 0; continue; }
+    int n, wb;
+    factor_dims(c, S.cnt, &n, &wb);
+    int o, t;
+    if (full_set) { o = 0; t = 1; }
+    else { o = (S.full + 1) % 3; t = (S.full + 2) % 3; }
+    FactorJob j;
+    j.A = S.A; j.idx = full_set ? c.iota : S.J; j.ncols = S.cnt; j.n = n;
+    j.npad = round_up(n, kTile); j.woodbury = wb; j.out = S.fb[o]; j.tmp = S.fb[t];
+    j.dinv = S.dinv;
+    jobs.push_back(j);
+    owner.push_back(q);
+    outbuf.push_back(o);
+  }
+  if (jobs.empty()) return SADMM_OK;
+  SADMM_CUDA_TRY(cudaMemsetAsync(c.dstatus, 0, sizeof(int) * c.Q, c.st));
+  for (size_t b = 0; b < jobs.size(); b += kMaxSets) {
+    const int nj = (int)std::min<size_t>(kMaxSets, jobs.size() - b);
+    SADMM_TRY(run_factor(jobs.data() + b, nj, c.KM, c.crit.mu, c.rho, c.dstatus, c.st));
+  }
+  SADMM_CUDA_TRY(cudaMemcpyAsync(c.h_status, c.dstatus, sizeof(int) * c.Q, cudaMemcpyDeviceToHost, c.st));
+  SADMM_CUDA_TRY(cudaStreamSynchronize(c.st));
+  for (size_t i = 0; i < jobs.size(); ++i) {
+    if (c.h_status[i]) {
+      set_error("factor of sensor %d is not positive definite (non-finite operator?)", owner[i]);
+      return SADMM_ENONFINITE;
+    }
+    Sensor& S = c.s[owner[i]];
+    S.cur = outbuf[i];
+    S.n = jobs[i].n;
+    S.woodbury = jobs[i].woodbury;
+    if (full_set) { S.full = outbuf[i]; S.full_valid = true; }
+  }
+  return SADMM_OK;
+}
+
+int prepare(Ctx& c) {
+  std::vector<int> qs;
+  for (int q = 0; q < c.Q; ++q) {
+    if (!c.s[q].op_set) {
+      set_error("operator of sensor %d not set", q);
+      return SADMM_ENOTREADY;
+    }
+    if (!c.s[q].full_valid) qs.push_back(q);
+  }
+  if (qs.empty()) return SADMM_OK;
+  std::vector<int> saved(c.Q);
+  for (int q : qs) { saved[q] = c.s[q].cnt; c.s[q].cnt = c.N; }
+  int rc = refresh(c, qs, true);
+  for (int q : qs) c.s[q].cnt = saved[q];
+  return rc;
+}
+
+// Point every sensor at its full-set factor and reset the iterates to zero.
+int reset_state(Ctx& c) {
+  const size_t QN = (size_t)c.Q * c.N;
+  SADMM_CUDA_TRY(cudaMemsetAsync(c.x, 0, QN * sizeof(float), c.st));
+  SADMM_CUDA_TRY(cudaMemsetAsync(c.xbar, 0, c.N * sizeof(float), c.st));
+  SADMM_CUDA_TRY(cudaMemsetAsync(c.zbar, 0, c.N * sizeof(float), c.st));
+  SADMM_CUDA_TRY(cudaMemsetAsync(c.sd, 0, c.N * sizeof(float), c.st));
+  SADMM_CUDA_TRY(cudaMemsetAsync(c.ring, 0, (size_t)c.crit.Kp * QN * sizeof(float), c.st));
+  std::vector<int> cnts(2 * c.Q, 0);
+  for (int q = 0; q < c.Q; ++q) {
+    Sensor& S = c.s[q];
+    SADMM_CUDA_TRY(cudaMemcpyAsync(S.J, c.iota, c.N * sizeof(int), cudaMemcpyDeviceToDevice, c.st));
+    SADMM_CUDA_TRY(cudaMemcpyAsync(S.yp, S.y, c.KM * sizeof(float2), cudaMemcpyDeviceToDevice, c.st));
+    S.cnt = c.N;
+    cnts[q] = c.N;
+    S.cur = S.full;
+    factor_dims(c, c.N, &S.n, &S.woodbury);
+  }
+  SADMM_CUDA_TRY(cudaMemcpyAsync(c.counts, cnts.data(), cnts.size() * sizeof(int), cudaMemcpyHostToDevice, c.st));
+  SADMM_CUDA_TRY(cudaStreamSynchronize(c.st));
+  c.k = 0;
+  return SADMM_OK;
+}
+
+// One iteration of Eq. 3 (x-update, prox, dual) and Algorithm 1 (device side).
+int launch_iteration(Ctx& c) {
+  const SolverView sv = c.view();
+  std::vector<ColumnSet> fw;
+  std::vector<SpdSet> spd_w, spd_p;
+  std::vector<AdjointSet> adj_w, adj_p;
+  for (int q = 0; q < c.Q; ++q) {
+    Sensor& S = c.s[q];
+    if (S.cnt == 0) continue;
+    fw.push_back(ColumnSet{S.A, S.J, S.cnt, q, nullptr, S.yp, S.r});
+    const double* F = S.fb[S.cur];
+    const int ld = round_up(S.n, kTile);
+    if (S.woodbury) {
+      spd_w.push_back(SpdSet{F, S.n, ld, reinterpret_cast<const float*>(S.r),
+                             reinterpret_cast<float*>(S.w), nullptr, q});
+      adj_w.push_back(AdjointSet{S.A, S.J, S.cnt, q, S.w, nullptr});
+    } else {
+      adj_p.push_back(AdjointSet{S.A, S.J, S.cnt, q, S.r, S.g});
+      spd_p.push_back(SpdSet{F, S.n, ld, S.g, nullptr, S.J, q});
+    }
+  }
+  c.mark(0, true);
+  SADMM_TRY(launch_forward(fw.data(), (int)fw.size(), c.KM, kVAdmm, sv, c.partial, c.partial_cap, c.st));
+  c.mark(0, false);
+  if (!spd_w.empty()) {
+    c.mark(1, true);
+    SADMM_TRY(launch_spd_apply(spd_w.data(), (int)spd_w.size(), false, sv, 2 * c.KM, c.st));
+    c.mark(1, false);
+    c.mark(2, true);
+    SADMM_TRY(launch_adjoint(adj_w.data(), (int)adj_w.size(), c.KM, true, sv, c.st));
+    c.mark(2, false);
+  }
+  if (!spd_p.empty()) {
+    c.mark(3, true);
+    SADMM_TRY(launch_adjoint(adj_p.data(), (int)adj_p.size(), c.KM, false, sv, c.st));
+    c.mark(3, false);
+    c.mark(4, true);
+    SADMM_TRY(launch_spd_apply(spd_p.data(), (int)spd_p.size(), true, sv, 2 * c.KM, c.st));
+    c.mark(4, false);
+  }
+  c.mark(5, true);
+  SADMM_TRY(launch_residuals(sv, c.crit, c.red, c.ticket, c.scal, c.k + 1, c.st));
+  c.mark(5, false);
+  if (c.crit.elim) {
+    std::vector<int*> Jp(c.Q), Ep(c.Q);
+    for (int q = 0; q < c.Q; ++q) { Jp[q] = c.s[q].J; Ep[q] = c.s[q].E; }
+    c.mark(6, true);
+    SADMM_TRY(launch_ssc(sv, Jp.data(), Ep.data(), c.counts, c.crit.eps_p, c.crit.freeze_mode,
+                         c.scal, c.st));
+    c.mark(6, false);
+  }
+  return SADMM_OK;
+}
+
+// After an SSC pass that shrank some sets: fold frozen pixels into y' (or
+// re-average in zero mode) and refresh the factors of those sensors.
+int apply_changes(Ctx& c, const std::vector<int>& changed) {
+  const SolverView sv = c.view();
+  if (c.crit.freeze_mode == 0) {
+    std::vector<ColumnSet> fold;
+    for (int q : changed) {
+      Sensor& S = c.s[q];
+      fold.push_back(ColumnSet{S.A, S.E, c.h_counts[c.Q + q], q, nullptr, S.yp, S.yp});
+    }
+    SADMM_TRY(launch_forward(fold.data(), (int)fold.size(), c.KM, kVX, sv, c.partial, c.partial_cap, c.st));
+  } else {
+    SADMM_TRY(launch_recompute_xbar(sv, c.st));
+  }
+  return refresh(c, changed, false);
+}
+
+double iter_bytes(const Ctx& c) {
+  double b = 0.0;
+  for (const Sensor& S : c.s) {
+    if (S.cnt == 0) continue;
+    b += 2.0 * c.KM * (double)S.cnt * sizeof(float2) + (double)S.n * S.n * sizeof(double);
+  }
+  return b;
+}
+
+int run(Ctx& c, float* x_out, int iters, double tol, sadmm_stats* st) {
+  const double t0 = now_ms();
+  double t_ref = 0.0, bytes = 0.0;
+  int refreshes = 0, stop_reason = 0, done = 0;
+  c.hist.clear();
+  for (int it = 0; it < iters; ++it) {
+    bytes += iter_bytes(c);
+    SADMM_TRY(launch_iteration(c));
+    SADMM_CUDA_TRY(cudaMemcpyAsync(c.h_scal, c.scal, sizeof(IterScalars), cudaMemcpyDeviceToHost, c.st));
+    SADMM_CUDA_TRY(cudaMemcpyAsync(c.h_counts, c.counts, 2 * c.Q * sizeof(int), cudaMemcpyDeviceToHost, c.st));
+    SADMM_CUDA_TRY(cudaStreamSynchronize(c.st));
+    c.collect();
+    c.k += 1;
+    done += 1;
+    const IterScalars& r = *c.h_scal;
+    if (r.nonfinite) {
+      set_error("non-finite value in iteration %d", c.k);
+      return SADMM_ENONFINITE;
+    }
+    std::vector<int> changed;
+    if (c.crit.elim && r.gate) {
+      for (int q = 0; q < c.Q; ++q) {
+        if (c.h_counts[c.Q + q] > 0) {
+          changed.push_back(q);
+          c.s[q].cnt = c.h_counts[q];
+        }
+      }
+    }
+    if (!changed.empty()) {
+      const double ta = now_ms();
+      c.mark(7, true);
+      SADMM_TRY(apply_changes(c, changed));
+      c.mark(7, false);
+      SADMM_CUDA_TRY(cudaStreamSynchronize(c.st));
+      c.collect();
+      t_ref += now_ms() - ta;
+      refreshes += 1;
+    }
+    sadmm_iter_record rec;
+    rec.k = c.k; rec.gate = r.gate; rec.changed = (int)changed.size();
+    rec.active_total = 0;
+    for (const Sensor& S : c.s) rec.active_total += S.cnt;
+    rec.r_pri = r.r_pri; rec.eps_pri = r.eps_pri; rec.d = r.d; rec.eps_dual = r.eps_dual;
+    rec.relchange = r.relchange;
+    c.hist.push_back(rec);
+    if (c.crit.stop == 0 && tol > 0.0 && r.relchange <= tol) { stop_reason = 1; break; }
+    if (c.crit.stop == 1 && r.r_pri <= r.eps_pri && r.d <= r.eps_dual) { stop_reason = 2; break; }
+  }
+  if (x_out) {
+    SADMM_TRY(launch_scale(c.zbar, (float)c.Q, c.xg, c.N, c.st));
+    SADMM_CUDA_TRY(cudaMemcpyAsync(x_out, c.xg, c.N * sizeof(float), cudaMemcpyDefault, c.st));
+  }
+  SADMM_CUDA_TRY(cudaStreamSynchronize(c.st));
+  if (st) {
+    memset(st, 0, sizeof *st);
+    st->iters = done;
+    st->stop_reason = stop_reason;
+    st->refreshes = refreshes;
+    for (const Sensor& S : c.s) st->active_total += S.cnt;
+    if (!c.hist.empty()) {
+      const sadmm_iter_record& h = c.hist.back();
+      st->r_pri = h.r_pri; st->eps_pri = h.eps_pri; st->d = h.d; st->eps_dual = h.eps_dual;
+      st->relchange = h.relchange;
+    }
+    st->ms_total = now_ms() - t0;
+    st->ms_refresh = t_ref;
+    st->bytes_iter = bytes;
+  }
+  return SADMM_OK;
+}
+
+int valid_ctx(sadmm_t c) {
+  if (!c) { set_error("null context"); return SADMM_EINVAL; }
+  return SADMM_OK;
+}
+
+}  // namespace
+}  // namespace sadmm
+
+using sadmm::Ctx;
+using sadmm::set_error;
+
+struct sadmm_ctx : Ctx {};
+
+extern "C" {
+
+void sadmm_default_criterion(sadmm_criterion* c) {
+  if (!c) return;
+  c->mu = 1.0;
+  c->Kp = 5;
+  c->eps_p = 1e-5;
+  c->eps_abs = 1e-4;
+  c->eps_rel = 1e-2;
+  c->elim = 1;
+  c->freeze_mode = 0;
+  c->stop = 0;
+}
+
+int sadmm_set_allocator(sadmm_alloc_fn alloc, sadmm_free_fn release, void* user) {
+  if ((alloc == nullptr) != (release == nullptr)) {
+    set_error("allocator and release must both be set or both be NULL");
+    return SADMM_EINVAL;
+  }
+  sadmm::g_alloc.alloc = alloc;
+  sadmm::g_alloc.release = release;
+  sadmm::g_alloc.user = user;
+  return SADMM_OK;
+}
+
+int sadmm_create(int Q, int M, int K, int N, double rho, double lambda, const sadmm_criterion* crit,
+                 sadmm_t* out) {
+  using namespace sadmm;
+  if (!out) { set_error("out is NULL"); return SADMM_EINVAL; }
+  *out = nullptr;
+  sadmm_criterion c;
+  if (crit) c = *crit; else sadmm_default_criterion(&c);
+  const long long KM = (long long)K * M;
+  if (Q < 1 || Q > kMaxSets || M < 1 || K < 1 || N < 1 || KM % 32 != 0 || KM > 16384 ||
+      !(rho > 0.0) || !(lambda >= 0.0) || !(c.mu > 0.0) || c.Kp < 1 || c.Kp > 64 ||
+      !(c.eps_p >= 0.0) || c.elim < 0 || c.elim > 1 || c.freeze_mode < 0 || c.freeze_mode > 1 ||
+      c.stop < 0 || c.stop > 1 || !std::isfinite(rho) || !std::isfinite(lambda)) {
+    set_error("sadmm_create: invalid sizes or parameters (Q=%d M=%d K=%d N=%d rho=%g lambda=%g)", Q, M,
+              K, N, rho, lambda);
+    return SADMM_EINVAL;
+  }
+  if ((long long)N * KM * 8 > (1ll << 40)) { set_error("operator too large"); return SADMM_EINVAL; }
+  sadmm_ctx* ctx = new (std::nothrow) sadmm_ctx();
+  if (!ctx) return SADMM_ENOMEM;
+  ctx->Q = Q; ctx->M = M; ctx->K = K; ctx->N = N; ctx->KM = (int)KM;
+  ctx->rho = rho; ctx->lam = lambda; ctx->crit = c;
+  ctx->alloc = g_alloc;
+  ctx->npad_max = round_up(std::min<long long>(N, 2 * KM), kTile);
+  ctx->s.resize(Q);
+  bool ok = true;
+  auto A = [&](size_t b) { void* p = ctx->dalloc(b); if (!p) ok = false; return p; };
+  const size_t fbytes = (size_t)ctx->npad_max * ctx->npad_max * sizeof(double);
+  for (int q = 0; q < Q && ok; ++q) {
+    Sensor& S = ctx->s[q];
+    S.A = (float2*)A((size_t)N * KM * sizeof(float2));
+    S.y = (float2*)A(KM * sizeof(float2));
+    S.yp = (float2*)A(KM * sizeof(float2));
+    S.r = (float2*)A(KM * sizeof(float2));
+    S.w = (float2*)A(KM * sizeof(float2));
+    S.g = (float*)A((size_t)N * sizeof(float));
+    S.J = (int*)A((size_t)N * sizeof(int));
+    S.E = (int*)A((size_t)N * sizeof(int));
+    for (int b = 0; b < 3; ++b) S.fb[b] = (double*)A(fbytes);
+    S.dinv = (double*)A((size_t)ctx->npad_max * kTile * sizeof(double));
+  }
+  const size_t QN = (size_t)Q * N;
+  ctx->x = (float*)A(QN * sizeof(float));
+  ctx->xbar = (float*)A(N * sizeof(float));
+  ctx->zbar = (float*)A(N * sizeof(float));
+  ctx->sd = (float*)A(N * sizeof(float));
+  ctx->xg = (float*)A(N * sizeof(float));
+  ctx->ring = (float*)A((size_t)c.Kp * QN * sizeof(float));
+  ctx->iota = (int*)A(N * sizeof(int));
+  ctx->partial_cap = 0;
+  for (int ns = 1; ns <= Q; ++ns)   // any subset of sensors may be launched together
+    ctx->partial_cap = std::max(ctx->partial_cap, forward_partial_bytes(ns, (int)KM, N));
+  ctx->partial = (float2*)A(ctx->partial_cap);
+  ctx->red = (double*)A((size_t)residual_blocks(N) * 8 * sizeof(double));
+  ctx->ticket = (unsigned int*)A(sizeof(unsigned int));
+  ctx->scal = (IterScalars*)A(sizeof(IterScalars));
+  ctx->counts = (int*)A(2 * Q * sizeof(int));
+  ctx->dstatus = (int*)A(Q * sizeof(int));
+  if (ok && (cudaMallocHost(&ctx->h_scal, sizeof(IterScalars)) != cudaSuccess ||
+             cudaMallocHost(&ctx->h_counts, 2 * Q * sizeof(int)) != cudaSuccess ||
+             cudaMallocHost(&ctx->h_status, Q * sizeof(int)) != cudaSuccess))
+    ok = false;
+  if (!ok) {
+    cudaGetLastError();
+    set_error("sadmm_create: device allocation failed");
+    ctx->release_all();
+    delete ctx;
+    return SADMM_ENOMEM;
+  }
+  iota_kernel<<<div_up(N, 256), 256, 0, ctx->st>>>(ctx->iota, N);
+  if (cudaMemsetAsync(ctx->ticket, 0, sizeof(unsigned int), ctx->st) != cudaSuccess ||
+      cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(ctx->st) != cudaSuccess) {
+    set_error("sadmm_create: initialisation failed");
+    ctx->release_all();
+    delete ctx;
+    return SADMM_ECUDA;
+  }
+  *out = ctx;
+  return SADMM_OK;
+}
+
+int sadmm_set_stream(sadmm_t ctx, void* stream) {
+  SADMM_TRY(sadmm::valid_ctx(ctx));
+  SADMM_CUDA_TRY(cudaStreamSynchronize(ctx->st));
+  ctx->st = (cudaStream_t)stream;
+  return SADMM_OK;
+}
+
+int sadmm_set_operator(sadmm_t ctx, int q, const float* A_q) {
+  SADMM_TRY(sadmm::valid_ctx(ctx));
+  if (q < 0 || q >= ctx->Q || !A_q) { set_error("sadmm_set_operator: bad sensor or pointer"); return SADMM_EINVAL; }
+  sadmm::Sensor& S = ctx->s[q];
+  SADMM_CUDA_TRY(cudaMemcpyAsync(S.A, A_q, (size_t)ctx->N * ctx->KM * sizeof(float2), cudaMemcpyDefault, ctx->st));
+  SADMM_CUDA_TRY(cudaStreamSynchronize(ctx->st));
+  S.op_set = true;
+  S.full_valid = false;
+  return SADMM_OK;
+}
+
+int sadmm_prepare(sadmm_t ctx) {
+  SADMM_TRY(sadmm::valid_ctx(ctx));
+  return sadmm::prepare(*ctx);
+}
+
+int sadmm_solve(sadmm_t ctx, const float* const* y, float* x_out, int iters, double tol, sadmm_stats* st) {
+  SADMM_TRY(sadmm::valid_ctx(ctx));
+  if (!y || iters < 0) { set_error("sadmm_solve: bad arguments"); return SADMM_EINVAL; }
+  for (int q = 0; q < ctx->Q; ++q)
+    if (!y[q]) { set_error("sadmm_solve: y[%d] is NULL", q); return SADMM_EINVAL; }
+  SADMM_TRY(sadmm::prepare(*ctx));
+  for (int q = 0; q < ctx->Q; ++q)
+    SADMM_CUDA_TRY(cudaMemcpyAsync(ctx->s[q].y, y[q], ctx->KM * sizeof(float2), cudaMemcpyDefault, ctx->st));
+  SADMM_TRY(sadmm::reset_state(*ctx));
+  return sadmm::run(*ctx, x_out, iters, tol, st);
+}
+
+int sadmm_resume(sadmm_t ctx, float* x_out, int iters, double tol, sadmm_stats* st) {
+  SADMM_TRY(sadmm::valid_ctx(ctx));
+  if (iters < 0) { set_error("sadmm_resume: bad arguments"); return SADMM_EINVAL; }
+  SADMM_TRY(sadmm::prepare(*ctx));
+  return sadmm::run(*ctx, x_out, iters, tol, st);
+}
+
+int sadmm_get_xq(sadmm_t ctx, int q, float* out) {
+  SADMM_TRY(sadmm::valid_ctx(ctx));
+  if (q < 0 || q >= ctx->Q || !out) { set_error("sadmm_get_xq: bad arguments"); return SADMM_EINVAL; }
+  SADMM_CUDA_TRY(cudaMemcpyAsync(out, ctx->x + (size_t)q * ctx->N, ctx->N * sizeof(float), cudaMemcpyDefault, ctx->st));
+  SADMM_CUDA_TRY(cudaStreamSynchronize(ctx->st));
+  return SADMM_OK;
+}
+
+int sadmm_get_active(sadmm_t ctx, int q, int* idx, int* count) {
+  SADMM_TRY(sadmm::valid_ctx(ctx));
+  if (q < 0 || q >= ctx->Q || !count) { set_error("sadmm_get_active: bad arguments"); return SADMM_EINVAL; }
+  *count = ctx->s[q].cnt;
+  if (idx && ctx->s[q].cnt > 0)
+    SADMM_CUDA_TRY(cudaMemcpyAsync(idx, ctx->s[q].J, ctx->s[q].cnt * sizeof(int), cudaMemcpyDefault, ctx->st));
+  SADMM_CUDA_TRY(cudaStreamSynchronize(ctx->st));
+  return SADMM_OK;
+}
+
+int sadmm_history(sadmm_t ctx, sadmm_iter_record* out, int cap) {
+  SADMM_TRY(sadmm::valid_ctx(ctx));
+  const int n = (int)std::min<size_t>(cap < 0 ? 0 : cap, ctx->hist.size());
+  if (n > 0 && out) memcpy(out, ctx->hist.data(), n * sizeof(sadmm_iter_record));
+  return out ? n : (int)ctx->hist.size();
+}
+
+// State blob: header, x (QN), x_bar, z_bar, s (N each), ring (Kp Q N), counts
+// (Q int32), J (Q x N int32, first counts[q] valid), y' (Q x KM complex64).
+namespace {
+struct StateHeader {
+  uint64_t magic;
+  int32_t Q, N, KM, Kp, k, pad;
+};
+size_t state_bytes(const Ctx& c) {
+  const size_t QN = (size_t)c.Q * c.N;
+  return sizeof(StateHeader) + QN * 4 + 3 * (size_t)c.N * 4 + (size_t)c.crit.Kp * QN * 4 + c.Q * 4 +
+         QN * 4 + (size_t)c.Q * c.KM * 8;
+}
+}  // namespace
+
+int sadmm_get_state(sadmm_t ctx, void* buf, size_t* bytes) {
+  SADMM_TRY(sadmm::valid_ctx(ctx));
+  if (!bytes) { set_error("bytes is NULL"); return SADMM_EINVAL; }
+  const size_t need = state_bytes(*ctx);
+  if (!buf) { *bytes = need; return SADMM_OK; }
+  if (*bytes < need) { set_error("state buffer too small (%zu < %zu)", *bytes, need); return SADMM_EINVAL; }
+  *bytes = need;
+  char* p = (char*)buf;
+  StateHeader h{sadmm::kStateMagic, ctx->Q, ctx->N, ctx->KM, ctx->crit.Kp, ctx->k, 0};
+  memcpy(p, &h, sizeof h);
+  p += sizeof h;
+  const size_t QN = (size_t)ctx->Q * ctx->N;
+  auto d2h = [&](const void* src, size_t b) -> int {
+    SADMM_CUDA_TRY(cudaMemcpyAsync(p, src, b, cudaMemcpyDeviceToHost, ctx->st));
+    p += b;
+    return SADMM_OK;
+  };
+  SADMM_TRY(d2h(ctx->x, QN * 4));
+  SADMM_TRY(d2h(ctx->xbar, ctx->N * 4));
+  SADMM_TRY(d2h(ctx->zbar, ctx->N * 4));
+  SADMM_TRY(d2h(ctx->sd, ctx->N * 4));
+  SADMM_TRY(d2h(ctx->ring, (size_t)ctx->crit.Kp * QN * 4));
+  for (int q = 0; q < ctx->Q; ++q) { memcpy(p, &ctx->s[q].cnt, 4); p += 4; }
+  for (int q = 0; q < ctx->Q; ++q) SADMM_TRY(d2h(ctx->s[q].J, (size_t)ctx->N * 4));
+  for (int q = 0; q < ctx->Q; ++q) SADMM_TRY(d2h(ctx->s[q].yp, (size_t)ctx->KM * 8));
+  SADMM_CUDA_TRY(cudaStreamSynchronize(ctx->st));
+  return SADMM_OK;
+}
+
+int sadmm_set_state(sadmm_t ctx, const void* buf, size_t bytes) {
+  using namespace sadmm;
+  SADMM_TRY(valid_ctx(ctx));
+  if (!buf || bytes != state_bytes(*ctx)) { set_error("sadmm_set_state: size mismatch"); return SADMM_EINVAL; }
+  StateHeader h;
+  memcpy(&h, buf, sizeof h);
+  if (h.magic != kStateMagic || h.Q != ctx->Q || h.N != ctx->N || h.KM != ctx->KM || h.Kp != ctx->crit.Kp) {
+    set_error("sadmm_set_state: incompatible state");
+    return SADMM_EINVAL;
+  }
+  SADMM_TRY(prepare(*ctx));
+  const char* p = (const char*)buf + sizeof h;
+  const size_t QN = (size_t)ctx->Q * ctx->N;
+  const char* ringp = p + QN * 4 + 3 * (size_t)ctx->N * 4;
+  const char* cntp = ringp + (size_t)ctx->crit.Kp * QN * 4;
+  const char* Jp = cntp + ctx->Q * 4;
+  const char* ypp = Jp + QN * 4;
+  std::vector<int> cnt(ctx->Q);
+  memcpy(cnt.data(), cntp, ctx->Q * 4);
+  // ring entries of inactive pixels must read as zero updates
+  std::vector<float> ring((size_t)ctx->crit.Kp * QN);
+  memcpy(ring.data(), ringp, ring.size() * 4);
+  std::vector<int> J(QN);
+  memcpy(J.data(), Jp, QN * 4);
+  for (int q = 0; q < ctx->Q; ++q) {
+    if (cnt[q] < 0 || cnt[q] > ctx->N) { set_error("sadmm_set_state: bad count"); return SADMM_EINVAL; }
+    std::vector<char> act(ctx->N, 0);
+    int prev = -1;
+    for (int i = 0; i < cnt[q]; ++i) {
+      const int v = J[(size_t)q * ctx->N + i];
+      if (v <= prev || v >= ctx->N) { set_error("sadmm_set_state: active set not sorted/unique"); return SADMM_EINVAL; }
+      act[v] = 1;
+      prev = v;
+    }
+    for (int i = 0; i < ctx->N; ++i)
+      if (!act[i])
+        for (int t = 0; t < ctx->crit.Kp; ++t) ring[((size_t)t * ctx->Q + q) * ctx->N + i] = 0.f;
+  }
+  auto h2d = [&](void* dst, const void* src, size_t b) -> int {
+    SADMM_CUDA_TRY(cudaMemcpyAsync(dst, src, b, cudaMemcpyHostToDevice, ctx->st));
+    return SADMM_OK;
+  };
+  SADMM_TRY(h2d(ctx->x, p, QN * 4));
+  SADMM_TRY(h2d(ctx->xbar, p + QN * 4, ctx->N * 4));
+  SADMM_TRY(h2d(ctx->zbar, p + QN * 4 + ctx->N * 4, ctx->N * 4));
+  SADMM_TRY(h2d(ctx->sd, p + QN * 4 + 2 * (size_t)ctx->N * 4, ctx->N * 4));
+  SADMM_TRY(h2d(ctx->ring, ring.data(), ring.size() * 4));
+  std::vector<int> counts(2 * ctx->Q, 0);
+  std::vector<int> changed;
+  for (int q = 0; q < ctx->Q; ++q) {
+    Sensor& S = ctx->s[q];
+    SADMM_TRY(h2d(S.J, J.data() + (size_t)q * ctx->N, (size_t)ctx->N * 4));
+    SADMM_TRY(h2d(S.yp, ypp + (size_t)q * ctx->KM * 8, (size_t)ctx->KM * 8));
+    S.cnt = cnt[q];
+    counts[q] = cnt[q];
+    if (cnt[q] == ctx->N) {
+      S.cur = S.full;
+      factor_dims(*ctx, ctx->N, &S.n, &S.woodbury);
+    } else {
+      changed.push_back(q);
+    }
+  }
+  SADMM_TRY(h2d(ctx->counts, counts.data(), counts.size() * 4));
+  SADMM_CUDA_TRY(cudaStreamSynchronize(ctx->st));
+  ctx->k = h.k;
+  return refresh(*ctx, changed, false);
+}
+
+int sadmm_set_profiling(sadmm_t ctx, int on) {
+  SADMM_TRY(sadmm::valid_ctx(ctx));
+  if (on) {
+    for (auto& e : ctx->ev)
+      if (!e) SADMM_CUDA_TRY(cudaEventCreate(&e));
+  }
+  ctx->prof = on != 0;
+  for (int p = 0; p < SADMM_NUM_PHASES; ++p) {
+    ctx->prof_ms[p] = 0.0;
+    ctx->prof_n[p] = 0;
+    ctx->ev_used[p] = false;
+  }
+  return SADMM_OK;
+}
+
+int sadmm_profile(sadmm_t ctx, double* ms, long long* launches, int cap) {
+  SADMM_TRY(sadmm::valid_ctx(ctx));
+  const int n = std::max(0, std::min(cap, SADMM_NUM_PHASES));
+  for (int p = 0; p < n; ++p) {
+    if (ms) ms[p] = ctx->prof_ms[p];
+    if (launches) launches[p] = ctx->prof_n[p];
+  }
+  return n;
+}
+
+long long sadmm_launch_count(void) { return sadmm::g_launches.load(); }
+
+void sadmm_destroy(sadmm_t ctx) {
+  if (!ctx) return;
+  ctx->release_all();
+  delete ctx;
+}
+
+const char* sadmm_strerror(int status) {
+  switch (status) {
+    case SADMM_OK: return "ok";
+    case SADMM_EINVAL: return "invalid argument";
+    case SADMM_ENOMEM: return "out of memory";
+    case SADMM_ECUDA: return "CUDA error";
+    case SADMM_ETIMEOUT: return "device wait timed out";
+    case SADMM_ENOTREADY: return "operator not set";
+    case SADMM_ENONFINITE: return "non-finite value";
+    default: return "unknown status";
+  }
+}
+
+const char* sadmm_last_error(void) { return sadmm::g_err.c_str(); }
+
+// ---------------------------------------------------------------- kernel level
+int sadmm_forward(const float* A, int KM, int N, const int* idx, int nidx, const float* v,
+                  const float* base, float* r, void* stream) {
+  using namespace sadmm;
+  if (!A || !r || KM <= 0 || KM % 2 != 0 || N <= 0 || nidx < 0 || (nidx > 0 && (!idx || !v))) {
+    set_error("sadmm_forward: bad arguments");
+    return SADMM_EINVAL;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  ColumnSet cs{(const float2*)A, idx, nidx, 0, v, (const float2*)base, (float2*)r};
+  SolverView sv{};
+  const size_t cap = forward_partial_bytes(1, KM, std::max(nidx, 1));
+  void* part = nullptr;
+  SADMM_CUDA_TRY(cudaMallocAsync(&part, cap, st));
+  int rc = launch_forward(&cs, 1, KM, kVExplicit, sv, (float2*)part, cap, st);
+  cudaError_t e = cudaFreeAsync(part, st);
+  if (rc != SADMM_OK) return rc;
+  SADMM_CUDA_TRY(e);
+  return SADMM_OK;
+}
+
+int sadmm_adjoint(const float* A, int KM, int N, const int* idx, int nidx, const float* w, float* g,
+                  void* stream) {
+  using namespace sadmm;
+  if (!A || !w || KM <= 0 || KM % 2 != 0 || KM > 16384 || N <= 0 || nidx < 0 ||
+      (nidx > 0 && (!idx || !g))) {
+    set_error("sadmm_adjoint: bad arguments");
+    return SADMM_EINVAL;
+  }
+  AdjointSet as{(const float2*)A, idx, nidx, 0, (const float2*)w, g};
+  SolverView sv{};
+  return launch_adjoint(&as, 1, KM, false, sv, (cudaStream_t)stream);
+}
+
+int sadmm_factor(const float* A, int KM, int N, const int* idx, int nidx, double mu, double rho,
+                 double* F, int ldf, int* form, void* stream) {
+  using namespace sadmm;
+  if (!A || !idx || !F || KM <= 0 || KM % 32 != 0 || nidx <= 0 || !(rho > 0.0) || !(mu > 0.0)) {
+    set_error("sadmm_factor: bad arguments");
+    return SADMM_EINVAL;
+  }
+  const int wb = nidx > 2 * KM ? 1 : 0;
+  const int n = wb ? 2 * KM : nidx;
+  const int npad = round_up(n, kTile);
+  if (ldf != npad) { set_error("sadmm_factor: ldf must equal roundup(n, 64) = %d", npad); return SADMM_EINVAL; }
+  cudaStream_t st = (cudaStream_t)stream;
+  void *tmp = nullptr, *dinv = nullptr, *status = nullptr;
+  SADMM_CUDA_TRY(cudaMallocAsync(&tmp, (size_t)npad * npad * sizeof(double), st));
+  SADMM_CUDA_TRY(cudaMallocAsync(&dinv, (size_t)npad * kTile * sizeof(double), st));
+  SADMM_CUDA_TRY(cudaMallocAsync(&status, sizeof(int), st));
+  SADMM_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int), st));
+  FactorJob j{(const float2*)A, idx, nidx, n, npad, wb, F, (double*)tmp, (double*)dinv};
+  int rc = run_factor(&j, 1, KM, mu, rho, (int*)status, st);
+  int hs = 0;
+  if (rc == SADMM_OK) {
+    SADMM_CUDA_TRY(cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    SADMM_CUDA_TRY(cudaStreamSynchronize(st));
+  }
+  cudaFreeAsync(tmp, st);
+  cudaFreeAsync(dinv, st);
+  cudaFreeAsync(status, st);
+  if (rc != SADMM_OK) return rc;
+  if (hs) { set_error("sadmm_factor: matrix not positive definite"); return SADMM_ENONFINITE; }
+  if (form) *form = wb;
+  return SADMM_OK;
+}
+
+int sadmm_spd_apply(const double* F, int n, int ldf, const float* u, float* out, void* stream) {
+  using namespace sadmm;
+  if (!F || !u || !out || n <= 0 || n > 32768 || ldf < n || ldf % 2 != 0) {
+    set_error("sadmm_spd_apply: bad arguments");
+    return SADMM_EINVAL;
+  }
+  SpdSet s{F, n, ldf, u, out, nullptr, 0};
+  SolverView sv{};
+  return launch_spd_apply(&s, 1, false, sv, n, (cudaStream_t)stream);
+}
+
+}  // extern "C"

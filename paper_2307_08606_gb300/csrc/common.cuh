@@ -1,0 +1,147 @@
+// Shared device/host helpers of the sharing-ADMM library (sm_103a).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include "sadmm.h"
+
+namespace sadmm {
+
+// Status plumbing: every internal call returns an int status; the message of
+// the last failure is kept per host thread.
+void set_error(const char* fmt, ...);
+
+#define SADMM_CUDA_TRY(expr)                                                         \
+  do {                                                                               \
+    cudaError_t e_ = (expr);                                                         \
+    if (e_ != cudaSuccess) {                                                         \
+      ::sadmm::set_error("%s:%d %s: %s", __FILE__, __LINE__, #expr,                  \
+                         cudaGetErrorString(e_));                                    \
+      return SADMM_ECUDA;                                                            \
+    }                                                                                \
+  } while (0)
+
+#define SADMM_TRY(expr)                                                              \
+  do {                                                                               \
+    int s_ = (expr);                                                                 \
+    if (s_ != SADMM_OK) return s_;                                                   \
+  } while (0)
+
+// Every kernel launch of the library goes through this check, which also
+// counts it (process-wide, see sadmm_launch_count).
+void count_launch();
+#define SADMM_LAUNCH_CHECK()             \
+  do {                                   \
+    ::sadmm::count_launch();             \
+    SADMM_CUDA_TRY(cudaGetLastError());  \
+  } while (0)
+
+constexpr int kTile = 64;          // FP64 factor tile edge (Gram, Cholesky, inverse)
+constexpr int kMaxSets = 64;       // sensors per batched launch (= maximum Q)
+
+// Per-sensor launch arguments travel by value in the kernel parameter block
+// (no device-side argument copies, so launches can be captured in a graph).
+template <typename T>
+struct SetBlock {
+  T v[kMaxSets];
+};
+
+inline int div_up(long long a, long long b) { return (int)((a + b - 1) / b); }
+inline int round_up(int a, int b) { return (a + b - 1) / b * b; }
+
+// Which source the forward product reads its per-column scalar from.
+enum VMode : int {
+  kVAdmm = 0,   // v = x_q - x_bar + z_bar - s   (Eq. 3, line 1 right-hand side)
+  kVX = 1,      // v = x_q                       (fold of frozen pixels into y')
+  kVExplicit = 2// v = caller array indexed by pixel
+};
+
+// Device-resident per-iteration scalars written by the residual kernel
+// (layout shared with the host; all doubles first).
+struct IterScalars {
+  double r_pri, eps_pri, d, eps_dual, relchange, xg_norm, dxg_norm, xnorm;
+  int k;          // iterations completed after this one
+  int gate;       // Algorithm 1 test runs this iteration
+  int changed;    // sensors whose active set shrank (written by the SSC kernel)
+  int nonfinite;  // a NaN/Inf was seen in the reductions
+};
+
+// Device view of the solver state handed to the kernels.
+struct SolverView {
+  int Q, N, KM, Kp;
+  float mu, rho;
+  float lam_over_rho;
+  float* x;          // Q x N
+  float* xbar;       // N
+  float* zbar;       // N
+  float* s;          // N
+  float* ring;       // Kp x Q x N signed updates x^{t+1} - x^t
+  int slot;          // ring slot written this iteration
+};
+
+// ---- kernel launchers (implemented in the .cu files) ----
+struct ColumnSet {          // one sensor's column list for a batched launch
+  const float2* A;          // pixel-major operator of the sensor
+  const int* idx;           // column (pixel) indices
+  int n;                    // number of listed columns
+  int q;                    // sensor index (row of x, ring)
+  const float* vexp;        // explicit v (kVExplicit)
+  const float2* base;       // base vector (KM complex) or null
+  float2* out;              // KM complex output
+};
+
+int launch_forward(const ColumnSet* sets, int nsets, int KM, VMode mode, const SolverView& sv,
+                   float2* partial, size_t partial_cap, cudaStream_t st);
+size_t forward_partial_bytes(int nsets, int KM, int max_cols);
+
+struct AdjointSet {
+  const float2* A;
+  const int* idx;
+  int n;
+  int q;
+  const float2* w;   // KM complex
+  float* g;          // output g[p] (mode g) or unused (mode update)
+};
+int launch_adjoint(const AdjointSet* sets, int nsets, int KM, bool update, const SolverView& sv,
+                   cudaStream_t st);
+
+struct SpdSet {
+  const double* F;
+  int n, ldf;
+  const float* u;    // n floats
+  float* out;        // n floats (plain) or unused (update)
+  const int* idx;    // primal form: pixel of row p (update mode)
+  int q;
+};
+int launch_spd_apply(const SpdSet* sets, int nsets, bool update, const SolverView& sv,
+                     int max_n, cudaStream_t st);
+
+int launch_residuals(const SolverView& sv, const sadmm_criterion& c, double* partials,
+                     unsigned int* ticket, IterScalars* out, int k_after, cudaStream_t st);
+int residual_blocks(int N);
+
+// Algorithm 1 on every sensor: reads the gate from `sc`; compacts J[q] in
+// place (order kept), lists removed pixels in E[q], zeroes their ring entries
+// (and x in zero mode).  counts[q] = new |J_q|, counts[Q + q] = |E_q|.
+int launch_ssc(const SolverView& sv, int* const* J, int* const* E, int* counts, double eps_p,
+               int freeze_mode, const IterScalars* sc, cudaStream_t st);
+int launch_recompute_xbar(const SolverView& sv, cudaStream_t st);
+int launch_scale(const float* in, float a, float* out, int n, cudaStream_t st);
+
+// FP64 factor: F <- (rho I + mu G)^{-1} for the Gram of the listed columns.
+struct FactorJob {
+  const float2* A;
+  const int* idx;
+  int ncols;         // |J|
+  int n;             // factor dimension (2KM or |J|)
+  int npad;          // round_up(n, kTile), also the leading dimension
+  int woodbury;      // 1: G = B_J B_J^T (2KM x 2KM), 0: G = B_J^T B_J
+  double* out;       // npad x npad: Gram, then its Cholesky factor, then the inverse (result)
+  double* tmp;       // npad x npad scratch (inverse of the Cholesky factor)
+  double* dinv;      // (npad / kTile) x kTile x kTile inverses of the diagonal blocks
+};
+int run_factor(const FactorJob* jobs, int njobs, int KM, double mu, double rho, int* d_status,
+               cudaStream_t st);
+
+}  // namespace sadmm

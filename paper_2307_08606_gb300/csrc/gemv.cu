@@ -1,0 +1,326 @@
+// Column-compacted complex GEMVs over the active-pixel lists and the FP64
+// SPD apply of the x-update factor (Eq. 1 products inside Eq. 3, line 1).
+//
+// Operators are pixel-major complex64: column n of A_q is KM contiguous float2.
+// The forward product r = base - sum_{p} A[:, idx[p]] v[idx[p]] streams the
+// listed columns once; each CTA owns a 256-row slice of one column chunk and
+// keeps its partial sum in registers, the per-column scalars v are staged in
+// shared memory, and a second kernel reduces the chunk partials in a fixed
+// order (deterministic).  The adjoint g[p] = Re(a_{idx[p]}^H w) gives one warp
+// per column with w staged in shared memory and a shuffle reduction.
+#include "common.cuh"
+
+namespace sadmm {
+
+namespace {
+
+constexpr int kFwdThreads = 128;          // one float4 (2 complex rows) per thread
+constexpr int kFwdRows = 2 * kFwdThreads; // complex rows per CTA slice
+constexpr int kFwdStage = 512;            // columns staged per shared-memory batch
+constexpr int kFwdUnroll = 8;
+
+// Read-only streaming load of an operator element pair (evict-first in L1).
+__device__ __forceinline__ float4 ld_stream(const float4* p) {
+  float4 v;
+  asm volatile("ld.global.nc.L1::no_allocate.v4.f32 {%0,%1,%2,%3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "l"(p));
+  return v;
+}
+
+__device__ __forceinline__ float v_of(VMode mode, const SolverView& sv, int q, int pix,
+                                      const float* vexp) {
+  if (mode == kVExplicit) return vexp[pix];
+  float xq = sv.x[(size_t)q * sv.N + pix];
+  if (mode == kVX) return xq;
+  return xq - sv.xbar[pix] + sv.zbar[pix] - sv.s[pix];
+}
+
+__global__ void __launch_bounds__(kFwdThreads)
+forward_partial_kernel(const __grid_constant__ SetBlock<ColumnSet> sets, int KM, int chunks,
+                       int cols_per_chunk, VMode mode, const __grid_constant__ SolverView sv,
+                       float4* __restrict__ partial) {
+  const ColumnSet& cs = sets.v[blockIdx.z];
+  const int c = blockIdx.y;
+  const int p0 = c * cols_per_chunk;
+  const int p1 = min(cs.n, p0 + cols_per_chunk);
+  const int row2 = blockIdx.x * kFwdThreads + threadIdx.x;   // float4 index within a column
+  const bool active_row = row2 * 2 < KM;
+  __shared__ float s_v[kFwdStage];
+  __shared__ int s_off[kFwdStage];
+  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  const float4* A4 = reinterpret_cast<const float4*>(cs.A);
+  const size_t col4 = (size_t)KM / 2;                        // float4 per column
+  for (int b0 = p0; b0 < p1; b0 += kFwdStage) {
+    const int nb = min(kFwdStage, p1 - b0);
+    __syncthreads();
+    for (int t = threadIdx.x; t < nb; t += kFwdThreads) {
+      const int pix = cs.idx[b0 + t];
+      s_v[t] = v_of(mode, sv, cs.q, pix, cs.vexp);
+      s_off[t] = pix;
+    }
+    __syncthreads();
+    if (active_row) {
+      int j = 0;
+      for (; j + kFwdUnroll <= nb; j += kFwdUnroll) {
+        float4 a[kFwdUnroll];
+#pragma unroll
+        for (int u = 0; u < kFwdUnroll; ++u)
+          a[u] = ld_stream(A4 + (size_t)s_off[j + u] * col4 + row2);
+#pragma unroll
+        for (int u = 0; u < kFwdUnroll; ++u) {
+          const float v = s_v[j + u];
+          acc.x = fmaf(a[u].x, v, acc.x);
+          acc.y = fmaf(a[u].y, v, acc.y);
+          acc.z = fmaf(a[u].z, v, acc.z);
+          acc.w = fmaf(a[u].w, v, acc.w);
+        }
+      }
+      for (; j < nb; ++j) {
+        const float4 a = ld_stream(A4 + (size_t)s_off[j] * col4 + row2);
+        const float v = s_v[j];
+        acc.x = fmaf(a.x, v, acc.x);
+        acc.y = fmaf(a.y, v, acc.y);
+        acc.z = fmaf(a.z, v, acc.z);
+        acc.w = fmaf(a.w, v, acc.w);
+      }
+    }
+  }
+  if (active_row)
+    partial[((size_t)blockIdx.z * chunks + c) * col4 + row2] = acc;
+}
+
+// out[r] = base[r] - sum_c partial[c][r], chunks summed in ascending order.
+__global__ void forward_reduce_kernel(const __grid_constant__ SetBlock<ColumnSet> sets, int KM,
+                                      int chunks, const float4* __restrict__ partial) {
+  const ColumnSet& cs = sets.v[blockIdx.y];
+  const int row2 = blockIdx.x * blockDim.x + threadIdx.x;
+  if (row2 * 2 >= KM) return;
+  const size_t col4 = (size_t)KM / 2;
+  const float4* p = partial + (size_t)blockIdx.y * chunks * col4 + row2;
+  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int c = 0; c < chunks; ++c) {
+    const float4 t = p[(size_t)c * col4];
+    acc.x += t.x; acc.y += t.y; acc.z += t.z; acc.w += t.w;
+  }
+  float4 b = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (cs.base) b = reinterpret_cast<const float4*>(cs.base)[row2];
+  reinterpret_cast<float4*>(cs.out)[row2] =
+      make_float4(b.x - acc.x, b.y - acc.y, b.z - acc.z, b.w - acc.w);
+}
+
+int forward_chunks(int nsets, int KM, int max_cols) {
+  const int tiles = div_up(KM, kFwdRows);
+  int want = div_up(152 * 16, (long long)tiles * nsets);        // ~2 waves at full occupancy
+  int cap = div_up(max_cols, 64);                                // >= 64 columns per chunk
+  return max(1, min(want, cap));
+}
+
+// ------------------------------------------------------------------ adjoint
+constexpr int kAdjWarps = 8;
+constexpr int kAdjColsPerWarp = 8;
+constexpr int kAdjUnroll = 4;
+
+__global__ void __launch_bounds__(kAdjWarps * 32)
+adjoint_kernel(const __grid_constant__ SetBlock<AdjointSet> sets, int KM, bool update,
+               const __grid_constant__ SolverView sv) {
+  extern __shared__ float4 s_w4[];               // KM/2 float4 = KM complex
+  const AdjointSet& as = sets.v[blockIdx.y];
+  const int cols_per_cta = kAdjWarps * kAdjColsPerWarp;
+  const int pbeg = blockIdx.x * cols_per_cta;
+  if (pbeg >= as.n) return;
+  const int n4 = KM / 2;
+  const float4* w4 = reinterpret_cast<const float4*>(as.w);
+  for (int t = threadIdx.x; t < n4; t += blockDim.x) s_w4[t] = w4[t];
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const float4* A4 = reinterpret_cast<const float4*>(as.A);
+  for (int cw = 0; cw < kAdjColsPerWarp; ++cw) {
+    const int p = pbeg + warp * kAdjColsPerWarp + cw;
+    if (p >= as.n) break;
+    const int pix = as.idx[p];
+    const float4* col = A4 + (size_t)pix * n4;
+    float acc[kAdjUnroll];
+#pragma unroll
+    for (int u = 0; u < kAdjUnroll; ++u) acc[u] = 0.f;
+    int i = lane;
+    for (; i + 32 * (kAdjUnroll - 1) < n4; i += 32 * kAdjUnroll) {
+      float4 a[kAdjUnroll];
+#pragma unroll
+      for (int u = 0; u < kAdjUnroll; ++u) a[u] = ld_stream(col + i + 32 * u);
+#pragma unroll
+      for (int u = 0; u < kAdjUnroll; ++u) {
+        const float4 w = s_w4[i + 32 * u];
+        acc[u] = fmaf(a[u].x, w.x, acc[u]);
+        acc[u] = fmaf(a[u].y, w.y, acc[u]);
+        acc[u] = fmaf(a[u].z, w.z, acc[u]);
+        acc[u] = fmaf(a[u].w, w.w, acc[u]);
+      }
+    }
+    for (; i < n4; i += 32) {
+      const float4 a = ld_stream(col + i);
+      const float4 w = s_w4[i];
+      acc[0] = fmaf(a.x, w.x, acc[0]);
+      acc[0] = fmaf(a.y, w.y, acc[0]);
+      acc[0] = fmaf(a.z, w.z, acc[0]);
+      acc[0] = fmaf(a.w, w.w, acc[0]);
+    }
+    float g = 0.f;
+#pragma unroll
+    for (int u = 0; u < kAdjUnroll; ++u) g += acc[u];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
+    if (lane == 0) {
+      if (update) {
+        // x-update epilogue (Woodbury form): x = v + mu Re(a^H w)
+        const size_t xi = (size_t)as.q * sv.N + pix;
+        const float xo = sv.x[xi];
+        const float v = xo - sv.xbar[pix] + sv.zbar[pix] - sv.s[pix];
+        const float xn = fmaf(sv.mu, g, v);
+        sv.ring[((size_t)sv.slot * sv.Q + as.q) * sv.N + pix] = xn - xo;
+        sv.x[xi] = xn;
+      } else {
+        as.g[p] = g;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------- SPD apply
+constexpr int kSpdWarps = 8;
+constexpr int kSpdRowsPerWarp = 4;
+constexpr int kSpdUnroll = 4;
+
+__global__ void __launch_bounds__(kSpdWarps * 32)
+spd_apply_kernel(const __grid_constant__ SetBlock<SpdSet> sets, bool update,
+                 const __grid_constant__ SolverView sv) {
+  extern __shared__ float s_u[];
+  const SpdSet& ss = sets.v[blockIdx.y];
+  const int rows_per_cta = kSpdWarps * kSpdRowsPerWarp;
+  const int rbeg = blockIdx.x * rows_per_cta;
+  if (rbeg >= ss.n) return;
+  const int n = ss.n;
+  const int n2 = (n + 1) / 2;                  // double2 steps per row
+  for (int t = threadIdx.x; t < 2 * n2; t += blockDim.x) s_u[t] = t < n ? ss.u[t] : 0.f;
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int rw = 0; rw < kSpdRowsPerWarp; ++rw) {
+    const int i = rbeg + warp * kSpdRowsPerWarp + rw;
+    if (i >= n) break;
+    const double2* row = reinterpret_cast<const double2*>(ss.F + (size_t)i * ss.ldf);
+    double acc[kSpdUnroll];
+#pragma unroll
+    for (int u = 0; u < kSpdUnroll; ++u) acc[u] = 0.0;
+    int j = lane;
+    for (; j + 32 * (kSpdUnroll - 1) < n2; j += 32 * kSpdUnroll) {
+      double2 f[kSpdUnroll];
+#pragma unroll
+      for (int u = 0; u < kSpdUnroll; ++u) f[u] = __ldcs(row + j + 32 * u);
+#pragma unroll
+      for (int u = 0; u < kSpdUnroll; ++u) {
+        const int jj = 2 * (j + 32 * u);
+        acc[u] = fma(f[u].x, (double)s_u[jj], acc[u]);
+        acc[u] = fma(f[u].y, (double)s_u[jj + 1], acc[u]);
+      }
+    }
+    for (; j < n2; j += 32) {
+      const double2 f = __ldcs(row + j);
+      acc[0] = fma(f.x, (double)s_u[2 * j], acc[0]);
+      // the padded column (2j+1 == n) multiplies u = 0
+      acc[0] = fma(f.y, (double)s_u[2 * j + 1], acc[0]);
+    }
+    double g = 0.0;
+#pragma unroll
+    for (int u = 0; u < kSpdUnroll; ++u) g += acc[u];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
+    if (lane == 0) {
+      if (update) {
+        // x-update epilogue (primal form): x_J = v_J + mu H g
+        const int pix = ss.idx[i];
+        const size_t xi = (size_t)ss.q * sv.N + pix;
+        const float xo = sv.x[xi];
+        const float v = xo - sv.xbar[pix] + sv.zbar[pix] - sv.s[pix];
+        const float xn = fmaf(sv.mu, (float)g, v);
+        sv.ring[((size_t)sv.slot * sv.Q + ss.q) * sv.N + pix] = xn - xo;
+        sv.x[xi] = xn;
+      } else {
+        ss.out[i] = (float)g;
+      }
+    }
+  }
+}
+
+}  // namespace
+
+size_t forward_partial_bytes(int nsets, int KM, int max_cols) {
+  return (size_t)nsets * forward_chunks(nsets, KM, max_cols) * KM * sizeof(float2);
+}
+
+int launch_forward(const ColumnSet* sets, int nsets, int KM, VMode mode, const SolverView& sv,
+                   float2* partial, size_t partial_cap, cudaStream_t st) {
+  if (nsets <= 0) return SADMM_OK;
+  if (nsets > kMaxSets) { set_error("launch_forward: %d sets > %d", nsets, kMaxSets); return SADMM_EINVAL; }
+  SetBlock<ColumnSet> blk;
+  int max_cols = 0;
+  for (int i = 0; i < nsets; ++i) { blk.v[i] = sets[i]; max_cols = max(max_cols, sets[i].n); }
+  const int chunks = forward_chunks(nsets, KM, max(max_cols, 1));
+  const int per = max(1, div_up(max_cols, chunks));
+  if ((size_t)nsets * chunks * KM * sizeof(float2) > partial_cap) {
+    set_error("launch_forward: partial buffer too small");
+    return SADMM_EINVAL;
+  }
+  dim3 grid(div_up(KM, kFwdRows), chunks, nsets);
+  forward_partial_kernel<<<grid, kFwdThreads, 0, st>>>(blk, KM, chunks, per, mode, sv,
+                                                       reinterpret_cast<float4*>(partial));
+  SADMM_LAUNCH_CHECK();
+  dim3 g2(div_up(KM / 2, 256), nsets);
+  forward_reduce_kernel<<<g2, 256, 0, st>>>(blk, KM, chunks, reinterpret_cast<const float4*>(partial));
+  SADMM_LAUNCH_CHECK();
+  return SADMM_OK;
+}
+
+int launch_adjoint(const AdjointSet* sets, int nsets, int KM, bool update, const SolverView& sv,
+                   cudaStream_t st) {
+  if (nsets <= 0) return SADMM_OK;
+  if (nsets > kMaxSets) { set_error("launch_adjoint: too many sets"); return SADMM_EINVAL; }
+  SetBlock<AdjointSet> blk;
+  int max_cols = 0;
+  for (int i = 0; i < nsets; ++i) { blk.v[i] = sets[i]; max_cols = max(max_cols, sets[i].n); }
+  if (max_cols == 0) return SADMM_OK;
+  const size_t smem = (size_t)KM * sizeof(float2);
+  static bool configured = false;
+  if (!configured) {
+    SADMM_CUDA_TRY(cudaFuncSetAttribute(adjoint_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        200 * 1024));
+    configured = true;
+  }
+  dim3 grid(div_up(max_cols, kAdjWarps * kAdjColsPerWarp), nsets);
+  adjoint_kernel<<<grid, kAdjWarps * 32, smem, st>>>(blk, KM, update, sv);
+  SADMM_LAUNCH_CHECK();
+  return SADMM_OK;
+}
+
+int launch_spd_apply(const SpdSet* sets, int nsets, bool update, const SolverView& sv, int max_n,
+                     cudaStream_t st) {
+  if (nsets <= 0) return SADMM_OK;
+  if (nsets > kMaxSets) { set_error("launch_spd_apply: too many sets"); return SADMM_EINVAL; }
+  SetBlock<SpdSet> blk;
+  int mx = 0;
+  for (int i = 0; i < nsets; ++i) { blk.v[i] = sets[i]; mx = max(mx, sets[i].n); }
+  if (mx == 0) return SADMM_OK;
+  const size_t smem = (size_t)round_up(mx, 2) * sizeof(float);
+  static bool configured = false;
+  if (!configured) {
+    SADMM_CUDA_TRY(cudaFuncSetAttribute(spd_apply_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        200 * 1024));
+    configured = true;
+  }
+  dim3 grid(div_up(mx, kSpdWarps * kSpdRowsPerWarp), nsets);
+  spd_apply_kernel<<<grid, kSpdWarps * 32, smem, st>>>(blk, update, sv);
+  SADMM_LAUNCH_CHECK();
+  (void)max_n;
+  return SADMM_OK;
+}
+
+}  // namespace sadmm

@@ -76,8 +76,7 @@ def random_problem(Q, KM, N, seed, snr_db=30.0, k_sparse=3):
         re = s.normal(N * KM).reshape(N, KM)
         im = s.normal(N * KM).reshape(N, KM)
         A.append(((re + 1j * im) / np.sqrt(2.0)).astype(np.complex64))
-    g = Geometry(Q=Q, M=1, K=KM, nx=int(round(np.sqrt(N))) if int(round(np.sqrt(N))) ** 2 == N else N,
-                 cell=1.0, radius=1.0, fc=1.0, bw=1.0)
+    g = Geometry(Q=Q, M=1, K=KM, nx=N, ny=1, cell=1.0, radius=1.0, fc=1.0, bw=1.0)
     x = np.zeros((Q, N))
     pix = Stream(seed, 102).permutation(N)[:k_sparse]
     amp = Stream(seed, 103).uniform(k_sparse * Q, 0.5, 1.0).reshape(Q, k_sparse)

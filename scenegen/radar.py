@@ -41,10 +41,11 @@ class Geometry:
     radius: float     # sensor circle radius [m]
     fc: float         # chirp start frequency [Hz]
     bw: float         # chirp bandwidth [Hz]
+    ny: int = None    # rows of pixels (default nx); only unstructured problems set it
 
     @property
     def N(self):
-        return self.nx * self.nx
+        return self.nx * (self.nx if self.ny is None else self.ny)
 
     @property
     def KM(self):

@@ -1,0 +1,153 @@
+"""Kernel-level parity of the CUDA path (called through the C ABI) against the
+FP64 oracle's definitions: the Eq. 1 forward product over an index list, its
+adjoint, the FP64 x-update factor (Eq. 3, first line) and its SPD apply.
+
+Floating-point bounds are derived from the arithmetic: an FP32 sum of n
+products differs from the exact value by at most n u sum|terms| (u = 2^-24)."""
+import numpy as np
+import pytest
+
+import oracle
+import scenegen
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+U32 = 2.0 ** -24
+
+
+@pytest.fixture(scope="module")
+def B():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2307_08606_gb300 import build, binding
+    build()
+    binding.load()
+    return binding
+
+
+def _operator(KM, N, seed, radar=False):
+    if radar:
+        g = scenegen.Geometry(Q=1, M=KM // 32, K=32, nx=int(np.sqrt(N)), cell=0.05, radius=10.0,
+                              fc=77e9, bw=1e9)
+        return scenegen.operator(g, 0)
+    s = scenegen.Stream(seed, 500)
+    re = s.normal(N * KM).reshape(N, KM)
+    im = s.normal(N * KM).reshape(N, KM)
+    return ((re + 1j * im) / np.sqrt(2)).astype(np.complex64)
+
+
+FWD_CASES = [
+    # KM, N, nidx, repeats, radar
+    (2, 10, 7, False, False),
+    (32, 100, 37, False, False),
+    (96, 513, 300, True, False),
+    (256, 1024, 1024, False, True),
+    (256, 1024, 0, False, False),
+    (2048, 3001, 2999, False, False),
+]
+
+
+@pytest.mark.parametrize("KM,N,nidx,repeats,radar", FWD_CASES)
+def test_forward_matches_oracle(B, KM, N, nidx, repeats, radar):
+    A = _operator(KM, N, seed=KM + N, radar=radar)
+    s = scenegen.Stream(7, KM)
+    if repeats:
+        idx = s.integers(nidx, N).astype(np.int32)
+    else:
+        idx = np.sort(s.permutation(N)[:nidx]).astype(np.int32)
+    v = s.normal(N).astype(np.float32)
+    base = (s.normal(KM) + 1j * s.normal(KM)).astype(np.complex64)
+    dev = torch.device("cuda:0")
+    At = torch.from_numpy(A).to(dev)
+    r = B.forward(At, torch.from_numpy(idx).to(dev), torch.from_numpy(v).to(dev),
+                  base=torch.from_numpy(base).to(dev))
+    torch.cuda.synchronize()
+    r = r.cpu().numpy().astype(np.complex128)
+    Asel = A[idx].astype(np.complex128)                      # (nidx, KM)
+    ref = base.astype(np.complex128) - (Asel.T @ v[idx].astype(np.float64) if nidx else 0.0)
+    mag_re = np.abs(base.real) + (np.abs(Asel.real).T @ np.abs(v[idx]) if nidx else 0.0)
+    mag_im = np.abs(base.imag) + (np.abs(Asel.imag).T @ np.abs(v[idx]) if nidx else 0.0)
+    n = nidx + 2
+    assert np.all(np.abs(r.real - ref.real) <= n * U32 * mag_re + 1e-30)
+    assert np.all(np.abs(r.imag - ref.imag) <= n * U32 * mag_im + 1e-30)
+    if nidx:
+        rel = np.linalg.norm(r - ref) / np.linalg.norm(ref)
+        assert rel <= 1e-5
+
+
+@pytest.mark.parametrize("KM,N,nidx", [(32, 100, 37), (96, 513, 513), (2048, 700, 650), (8192, 70, 69)])
+def test_adjoint_matches_oracle(B, KM, N, nidx):
+    A = _operator(KM, N, seed=3 * KM + N)
+    s = scenegen.Stream(11, KM)
+    idx = s.permutation(N)[:nidx].astype(np.int32)           # unsorted
+    w = (s.normal(KM) + 1j * s.normal(KM)).astype(np.complex64)
+    dev = torch.device("cuda:0")
+    g = B.adjoint(torch.from_numpy(A).to(dev), torch.from_numpy(idx).to(dev),
+                  torch.from_numpy(w).to(dev))
+    torch.cuda.synchronize()
+    g = g.cpu().numpy().astype(np.float64)
+    ref = oracle.adjoint_re(A[idx], w)
+    mag = np.abs(A[idx].real) @ np.abs(w.real) + np.abs(A[idx].imag) @ np.abs(w.imag)
+    assert np.all(np.abs(g - ref) <= (2 * KM + 2) * U32 * mag)
+    # adjoint identity through the two GPU products, Re<A v, w> = <v, Re(A^H w)>
+    v = s.normal(N).astype(np.float32)
+    r = B.forward(torch.from_numpy(A).to(dev), torch.from_numpy(np.sort(idx)).to(dev),
+                  torch.from_numpy(v).to(dev)).cpu().numpy().astype(np.complex128)
+    lhs = -np.vdot(w.astype(np.complex128), r).real        # forward returns 0 - A v
+    rhs = float(np.dot(v[idx].astype(np.float64), g))
+    assert abs(lhs - rhs) <= 1e-5 * np.linalg.norm(r) * np.linalg.norm(w)
+
+
+def _interleaved_real_form(A, idx):
+    """B[2m, p] = Re A[idx_p, m], B[2m+1, p] = Im A[idx_p, m] (float64)."""
+    cols = A[idx].astype(np.complex128)                       # (nidx, KM)
+    Bm = np.empty((2 * A.shape[1], len(idx)))
+    Bm[0::2] = cols.real.T
+    Bm[1::2] = cols.imag.T
+    return Bm
+
+
+@pytest.mark.parametrize("KM,N,nidx,mu,rho", [
+    (32, 200, 50, 1.0, 1.0),      # primal, padded 50 -> 64
+    (32, 200, 64, 0.7, 2.0),      # primal, one full tile
+    (32, 200, 150, 1.0, 1.0),     # Woodbury, n = 64
+    (128, 1200, 1000, 1.3, 0.5),  # Woodbury, 4 tiles
+    (128, 1200, 200, 1.0, 3.0),   # primal, 200 -> 256
+])
+def test_factor_matches_fp64_inverse(B, KM, N, nidx, mu, rho):
+    A = _operator(KM, N, seed=KM * 7 + nidx)
+    idx = np.sort(scenegen.Stream(5, nidx).permutation(N)[:nidx]).astype(np.int32)
+    dev = torch.device("cuda:0")
+    F, form, n = B.factor(torch.from_numpy(A).to(dev), torch.from_numpy(idx).to(dev), mu, rho)
+    torch.cuda.synchronize()
+    F = F.cpu().numpy()
+    Bm = _interleaved_real_form(A, idx)
+    if nidx > 2 * KM:
+        assert form == 1 and n == 2 * KM
+        G = rho * np.eye(n) + mu * Bm @ Bm.T
+    else:
+        assert form == 0 and n == nidx
+        G = rho * np.eye(n) + mu * Bm.T @ Bm
+    ref = np.linalg.inv(G)
+    Fn = F[:n, :n]
+    assert np.array_equal(Fn, Fn.T)
+    cond = np.linalg.cond(G)
+    assert np.max(np.abs(Fn - ref)) <= 1e-14 * cond * np.max(np.abs(ref)) * n
+    assert np.max(np.abs(Fn @ G - np.eye(n))) <= 1e-13 * cond * n
+
+
+@pytest.mark.parametrize("n,ld", [(1, 2), (37, 64), (100, 128), (4096, 4096)])
+def test_spd_apply_matches_fp64(B, n, ld):
+    s = scenegen.Stream(9, n)
+    M = s.normal(n * n).reshape(n, n)
+    F = np.zeros((ld, ld))
+    F[:n, :n] = M + M.T
+    u = s.normal(n).astype(np.float32)
+    dev = torch.device("cuda:0")
+    out = B.spd_apply(torch.from_numpy(F).to(dev), n, torch.from_numpy(u).to(dev))
+    torch.cuda.synchronize()
+    out = out.cpu().numpy().astype(np.float64)
+    ref = F[:n, :n] @ u.astype(np.float64)
+    mag = np.abs(F[:n, :n]) @ np.abs(u.astype(np.float64))
+    assert np.all(np.abs(out - ref) <= U32 * np.abs(ref) + 1e-13 * mag)

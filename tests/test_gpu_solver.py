@@ -1,0 +1,189 @@
+"""Solve-level parity: the CUDA solver (through the C ABI) against the FP64
+oracle at equal iteration counts, on seeded synthetic scenes.
+
+Bar (FP32 GPU vs FP64 oracle): relative error of the stacked iterates
+X = (x_1..x_Q) and of the dual s <= 1e-4 at equal k; x_G (= Q z_bar) within
+1e-4 relative (or identical when the oracle's image is exactly zero); active
+sets bit-identical while the oracle's decision margins stay above
+delta = 0.1 eps_p for zeta and 1e-3 (relative) for the gate."""
+import numpy as np
+import pytest
+
+import oracle
+import scenegen
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def B():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2307_08606_gb300 import build, binding
+    build()
+    binding.load()
+    return binding
+
+
+def _solver(B, sc, rho, lam, **crit):
+    g = sc.geom
+    s = B.Solver(g.Q, g.M, g.K, g.N, rho, lam, **crit)
+    for q in range(g.Q):
+        s.set_operator(q, sc.A[q])
+    return s
+
+
+def _rel(a, b):
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / nb if nb > 0 else np.linalg.norm(a)
+
+
+def _margins_ok(hist, crit_eps_p):
+    for h in hist:
+        if h["gate_margin"] < 1e-3:
+            return False
+        if h["gate"] and h["zeta_margin"] < 0.1 * crit_eps_p:
+            return False
+    return True
+
+
+def _compare(B, sc, rho, lam, iters, elim, Kp=5, eps_p=1e-5, freeze_mode=0, mu=1.0):
+    crit = oracle.Criterion(mu=mu, elim=elim, Kp=Kp, eps_p=eps_p, freeze_mode=freeze_mode)
+    ref = oracle.sadmm(sc.A, sc.y, rho, lam, crit, iters=iters)
+    s = _solver(B, sc, rho, lam, mu=mu, elim=elim, Kp=Kp, eps_p=eps_p, freeze_mode=freeze_mode)
+    xg, st = s.solve(sc.y, iters)
+    X = s.X()
+    assert st["iters"] == iters
+    errX = _rel(X, ref.state.x)
+    assert errX <= TOL, errX
+    if np.any(ref.xG != 0):
+        assert _rel(xg, ref.xG) <= TOL
+    if elim and _margins_ok(ref.history, eps_p):
+        for q in range(sc.geom.Q):
+            assert np.array_equal(s.active(q), ref.state.J[q]), q
+    hist = s.history()
+    assert len(hist) == iters
+    for h, r in zip(hist, ref.history):
+        assert h["gate"] == int(r["gate"]) or abs(r["gate_margin"]) < 1e-3
+    s.close()
+    return ref, X, xg
+
+
+@pytest.mark.parametrize("elim", [0, 1])
+def test_small_point_scene(B, elim):
+    """32x32 grid, Q=4, KM=256 (Woodbury form, N > 2KM), 300 iterations."""
+    sc = scenegen.build_scene("small_point", seed=0)
+    lam = 0.05 * scenegen.lambda_max(sc.A, sc.y)
+    _compare(B, sc, 1.0, lam, 300, elim)
+
+
+def test_resolved_scene_with_elimination(B):
+    """8x8 grid, Q=3, KM=256 (primal form, N < 2KM); the gate opens near k=187
+    and Algorithm 1 removes most pixels."""
+    sc = scenegen.build_scene("resolved_tiny", seed=2, snr_db=30.0)
+    lam = 0.05 * scenegen.lambda_max(sc.A, sc.y)
+    ref, X, xg = _compare(B, sc, 1.0, lam, 200, 1, Kp=4)
+    assert sum(len(j) for j in ref.state.J) < sc.geom.Q * sc.geom.N
+
+
+def test_zero_mode_and_rho(B):
+    """Unstructured operators, rho = 2, mu = 0.8, removed pixels set to zero."""
+    sc = scenegen.random_problem(2, 32, 200, seed=4)
+    lam = 0.1 * scenegen.lambda_max(sc.A, sc.y, mu=0.8)
+    _compare(B, sc, 2.0, lam, 120, 1, Kp=3, eps_p=1e-4, freeze_mode=1, mu=0.8)
+
+
+def test_single_sensor(B):
+    sc = scenegen.random_problem(1, 64, 300, seed=6)
+    lam = 0.05 * scenegen.lambda_max(sc.A, sc.y)
+    _compare(B, sc, 1.0, lam, 80, 0)
+
+
+def test_lambda_above_max_gives_zero_image(B):
+    sc = scenegen.random_problem(2, 32, 100, seed=8)
+    lam = 1.01 * scenegen.lambda_max(sc.A, sc.y)
+    s = _solver(B, sc, 1.0, lam, elim=0)
+    xg, _ = s.solve(sc.y, 50)
+    assert np.all(xg == 0.0)
+
+
+def test_state_roundtrip_is_bit_exact(B):
+    sc = scenegen.build_scene("resolved_tiny", seed=2, snr_db=30.0)
+    lam = 0.05 * scenegen.lambda_max(sc.A, sc.y)
+    s = _solver(B, sc, 1.0, lam, Kp=4)
+    s.solve(sc.y, 185)
+    st = s.get_state()
+    s.resume(15)
+    Xa = s.X()
+    Ja = [s.active(q) for q in range(sc.geom.Q)]
+    s.set_state(st)
+    s.resume(15)
+    assert np.array_equal(s.X(), Xa)
+    assert all(np.array_equal(s.active(q), Ja[q]) for q in range(sc.geom.Q))
+
+
+def test_resync_from_oracle_state(B):
+    """Load the oracle's state at k = 190 (after elimination) into the GPU and
+    continue: the next 10 iterations match the oracle's."""
+    sc = scenegen.build_scene("resolved_tiny", seed=2, snr_db=30.0)
+    lam = 0.05 * scenegen.lambda_max(sc.A, sc.y)
+    crit = oracle.Criterion(elim=1, Kp=4)
+    r1 = oracle.sadmm(sc.A, sc.y, 1.0, lam, crit, iters=190)
+    r2 = oracle.sadmm(sc.A, sc.y, 1.0, lam, crit, iters=10, state=r1.state)
+    g = sc.geom
+    st = r1.state
+    blob = B.pack_state(g.Q, g.N, g.KM, 4, st.k, st.x, st.xbar, st.zbar, st.s, st.ring, st.J,
+                        np.stack([v[: g.KM] + 1j * v[g.KM:] for v in st.yprime]))
+    s = _solver(B, sc, 1.0, lam, Kp=4)
+    s.prepare()
+    s.set_state(blob)
+    s.resume(10)
+    assert _rel(s.X(), r2.state.x) <= TOL
+    back = B.unpack_state(s.get_state(), g.Q, g.N, g.KM, 4)
+    assert back["k"] == 200
+
+
+def test_nonfinite_measurement_reported(B):
+    sc = scenegen.random_problem(2, 32, 100, seed=9)
+    y = [v.copy() for v in sc.y]
+    y[1][3] = np.nan
+    s = _solver(B, sc, 1.0, 1.0, elim=0)
+    with pytest.raises(B.SadmmError) as e:
+        s.solve(y, 5)
+    assert e.value.status == B.ENONFINITE
+
+
+def test_device_and_host_buffers_agree(B):
+    sc = scenegen.build_scene("small_point", seed=1)
+    lam = 0.05 * scenegen.lambda_max(sc.A, sc.y)
+    s = _solver(B, sc, 1.0, lam)
+    xh, _ = s.solve(sc.y, 20)
+    Xh = s.X()
+    dev = torch.device("cuda:0")
+    yd = [torch.from_numpy(v).to(dev) for v in sc.y]
+    out = torch.empty(sc.geom.N, dtype=torch.float32, device=dev)
+    s.solve(yd, 20, out=out)
+    torch.cuda.synchronize()
+    assert np.array_equal(out.cpu().numpy(), xh)
+    assert np.array_equal(s.X(), Xh)
+
+
+def test_torch_allocator_path(B):
+    """Device memory routed through torch's caching allocator gives the same result."""
+    sc = scenegen.random_problem(2, 32, 100, seed=12)
+    lam = 0.1 * scenegen.lambda_max(sc.A, sc.y)
+    a = _solver(B, sc, 1.0, lam)
+    xa, _ = a.solve(sc.y, 30)
+    B.use_torch_allocator()
+    try:
+        before = torch.cuda.memory_allocated()
+        b = _solver(B, sc, 1.0, lam)
+        assert torch.cuda.memory_allocated() > before
+        xb, _ = b.solve(sc.y, 30)
+        b.close()
+    finally:
+        B.check(B.load().sadmm_set_allocator(B.ALLOC_FN(), B.FREE_FN(), None))
+    assert np.array_equal(xa, xb)
