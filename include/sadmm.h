@@ -186,6 +186,24 @@ const char* sadmm_last_error(void);
 int sadmm_forward(const float* A, int KM, int N, const int* idx, int nidx, const float* v,
                   const float* base, float* r, void* stream);
 
+/* Same result as sadmm_forward, for callers that cannot allocate device
+ * memory while they run (for example a real-time radar front end with a fixed
+ * per-frame latency budget, where cudaMalloc/cudaFree may synchronise the
+ * device, or a process whose device memory is rationed by another allocator).
+ * The paper has no counterpart: this is a library-interface variant.
+ * It allocates nothing: the partial sums go to one fixed 8 MiB device array
+ * that every GPU loading this library holds until the process exits.  Sizes
+ * whose partial sums (chunks x KM x 8 bytes) exceed 8 MiB are rejected with
+ * SADMM_EINVAL and a message naming the sizes.  The first call on each device
+ * looks up the array's device address (with that device current); make that
+ * first call before any stream capture begins.  All calls on a device share
+ * the array and it keeps the last call's contents; every entry a call reads is
+ * written earlier in the same call, so nothing needs clearing, but calls whose
+ * work overlaps on the GPU (different streams, or different host threads) race
+ * on it and must be serialised by the caller. */
+int sadmm_forward_noalloc(const float* A, int KM, int N, const int* idx, int nidx,
+                          const float* v, const float* base, float* r, void* stream);
+
 /* g[p] = Re(a_{idx[p]}^H w) for p < nidx (adjoint of the real-input forward
  * product).  w: KM complex64 (KM even, <= 16384); g: nidx floats. */
 int sadmm_adjoint(const float* A, int KM, int N, const int* idx, int nidx, const float* w,

@@ -69,6 +69,7 @@ _SIGS = {
     "sadmm_strerror": (C.c_char_p, [C.c_int]),
     "sadmm_last_error": (C.c_char_p, []),
     "sadmm_forward": (C.c_int, [_P, C.c_int, C.c_int, _P, C.c_int, _P, _P, _P, _P]),
+    "sadmm_forward_noalloc": (C.c_int, [_P, C.c_int, C.c_int, _P, C.c_int, _P, _P, _P, _P]),
     "sadmm_adjoint": (C.c_int, [_P, C.c_int, C.c_int, _P, C.c_int, _P, _P, _P]),
     "sadmm_factor": (C.c_int, [_P, C.c_int, C.c_int, _P, C.c_int, C.c_double, C.c_double, _P,
                                C.c_int, C.POINTER(C.c_int), _P]),
@@ -299,6 +300,17 @@ def forward(A, idx, v, base=None, out=None, stream=0):
         out = torch.empty(KM, dtype=torch.complex64, device=A.device)
     check(load().sadmm_forward(_ptr(A), KM, A.shape[0], _ptr(idx), int(idx.numel()), _ptr(v),
                                _ptr(base), _ptr(out), C.c_void_p(stream)))
+    return out
+
+
+def forward_noalloc(A, idx, v, base=None, out=None, stream=0):
+    """As forward(), through the allocation-free entry point (fixed scratch)."""
+    import torch
+    KM = A.shape[1]
+    if out is None:
+        out = torch.empty(KM, dtype=torch.complex64, device=A.device)
+    check(load().sadmm_forward_noalloc(_ptr(A), KM, A.shape[0], _ptr(idx), int(idx.numel()), _ptr(v),
+                                       _ptr(base), _ptr(out), C.c_void_p(stream)))
     return out
 
 

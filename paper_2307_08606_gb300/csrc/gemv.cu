@@ -10,6 +10,8 @@
 // per column with w staged in shared memory and a shuffle reduction.
 #include "common.cuh"
 
+#include <mutex>
+
 namespace sadmm {
 
 namespace {
@@ -324,3 +326,70 @@ int launch_spd_apply(const SpdSet* sets, int nsets, bool update, const SolverVie
 }
 
 }  // namespace sadmm
+
+// ---------------------------------------------------------------------------
+// Allocation-free forward product (sadmm_forward_noalloc).
+//
+// Some callers cannot allocate device memory once they are running: a
+// real-time radar front end with a fixed per-frame latency budget (where a
+// cudaMalloc / cudaFree can synchronise the device and stall the pipeline), or
+// a host process whose device memory is handed out by another allocator under
+// a fixed budget.  For them the forward product's chunk partial sums live in
+// one file-scope device array instead of memory allocated per call.  The
+// array is created when a GPU loads this library and is held until the process
+// exits; all calls on that GPU share it.
+namespace sadmm {
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = size_t(8) << 20;   // 8 MiB per GPU
+constexpr int kMaxDevices = 64;
+
+__device__ __align__(256) float4 g_noalloc_partial[kNoAllocScratchBytes / sizeof(float4)];
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kMaxDevices] = {};
+
+// Device address of the scratch array on the current device.  Host code must
+// not use the array's name as a pointer: it only stands for the symbol.  The
+// address is looked up once per device, with that device current.
+int noalloc_scratch(void** out) {
+  int dev = 0;
+  SADMM_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) {
+    set_error("sadmm_forward_noalloc: device ordinal %d out of range", dev);
+    return SADMM_EINVAL;
+  }
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    SADMM_CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_partial));
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return SADMM_OK;
+}
+
+}  // namespace
+}  // namespace sadmm
+
+extern "C" int sadmm_forward_noalloc(const float* A, int KM, int N, const int* idx, int nidx,
+                                     const float* v, const float* base, float* r, void* stream) {
+  using namespace sadmm;
+  if (!A || !r || KM <= 0 || KM % 2 != 0 || N <= 0 || nidx < 0 || (nidx > 0 && (!idx || !v))) {
+    set_error("sadmm_forward_noalloc: bad arguments");
+    return SADMM_EINVAL;
+  }
+  const size_t need = forward_partial_bytes(1, KM, nidx > 0 ? nidx : 1);
+  if (need > kNoAllocScratchBytes) {
+    set_error("sadmm_forward_noalloc: KM=%d with %d columns needs %zu bytes of partial sums, "
+              "more than the %zu-byte fixed scratch; use sadmm_forward",
+              KM, nidx, need, kNoAllocScratchBytes);
+    return SADMM_EINVAL;
+  }
+  void* scratch = nullptr;
+  SADMM_TRY(noalloc_scratch(&scratch));
+  ColumnSet cs{(const float2*)A, idx, nidx, 0, v, (const float2*)base, (float2*)r};
+  SolverView sv{};
+  return launch_forward(&cs, 1, KM, kVExplicit, sv, (float2*)scratch, kNoAllocScratchBytes,
+                        (cudaStream_t)stream);
+}
