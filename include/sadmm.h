@@ -6,11 +6,11 @@
  * on one GPU: for Q sensors with complex operators A_q (KM x N, Eq. 1) and
  * measurements y_q it iterates
  *
- *   x_q,J  <- (rho I + mu B_J^T B_J)^{-1} (mu B_J^T y'_q + rho v_J)      Eq. 3, line 1
+ *   x_q,J  <- (rho I + mu B_J^T B_J)^{-1} (mu B_J^T y'_q + rho v_J)      Eq. 3, x_q-update
  *             v = x_q - x_bar + z_bar - s, on the active set J_q only
- *   z_bar  <- soft(x_bar + s, lambda / rho)                               Eq. 3, line 2
- *   s      <- s + x_bar - z_bar                                           Eq. 3, line 3
- *   J_q    <- SSC(last Kp updates, eps_p) when ||eta_pri|| <= eps_pri       Eq. 3, line 4; Algorithm 1
+ *   z_bar  <- soft(x_bar + s, lambda / rho)                               Eq. 3, x_G-update
+ *   s      <- s + x_bar - z_bar                                           Eq. 3, dual update
+ *   J_q    <- SSC(last Kp updates, eps_p) when ||eta_pri|| <= eps_pri       Eq. 3, selector update; Algorithm 1
  *
  * with B = [Re A; Im A] the real form of A, x_bar = mean_q x_q, x_G = Q z_bar
  * the output image and s the scaled dual (the paper's sigma = rho s, its
@@ -209,7 +209,7 @@ int sadmm_forward_noalloc(const float* A, int KM, int N, const int* idx, int nid
 int sadmm_adjoint(const float* A, int KM, int N, const int* idx, int nidx, const float* w,
                   float* g, void* stream);
 
-/* Factor of the x-update (Eq. 3, line 1) for the listed columns, in FP64:
+/* Factor of the x-update (Eq. 3, x_q-update) for the listed columns, in FP64:
  * if nidx > 2KM, F = (rho I + mu B_J B_J^T)^{-1} with B_J rows interleaved
  * (re, im) per sample (dimension n = 2KM, *form = 1); otherwise
  * F = (rho I + mu B_J^T B_J)^{-1} (n = nidx, *form = 0).  F is n x n,

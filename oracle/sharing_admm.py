@@ -18,14 +18,14 @@ x_bar = (1/Q) sum_q x_q, z_bar = x_G / Q, and the scaled dual s, so that the
 paper's dual is sigma = rho * s and its beta is rho.
 
 One iteration k -> k+1:
-  1. x-update (Eq. 3, first line), per sensor, on the active set J_q only:
+  1. x-update (Eq. 3, x_q-update), per sensor, on the active set J_q only:
        v_J   = x_q - x_bar + z_bar - s           (restricted to J_q)
        x_q,J = (rho I + mu B_J^T B_J)^{-1} (mu B_J^T y'_q + rho v_J)
      Entries outside J_q keep their value (frozen).  y'_q is y_q minus the
      contribution of the frozen pixels.
   2. x_bar = (1/Q) sum_q x_q over all N pixels.
-  3. z_bar' = soft(x_bar + s, lambda/rho)        (Eq. 3, second line)
-  4. s'     = s + x_bar - z_bar'                 (Eq. 3, third line)
+  3. z_bar' = soft(x_bar + s, lambda/rho)        (Eq. 3, x_G-update)
+  4. s'     = s + x_bar - z_bar'                 (Eq. 3, dual update)
   5. residuals: r_pri = sqrt(Q) ||x_bar - z_bar'||,
        eps_pri  = sqrt(QN) eps_abs + eps_rel max(||X||_F, ||Z||_F),  Z_q = x_q - x_bar + z_bar',
        d        = rho ||Z^{k+1} - Z^k||_F,
@@ -41,7 +41,7 @@ One iteration k -> k+1:
 Readings where the paper is silent or garbled (each is a choice both this oracle
 and the CUDA path make): real x_q (Eq. 1 folds the phase into A_q); x_G is the sum
 of the x_q and the threshold on the averaged variable is lambda/rho; the x-update
-carries Boyd's x_q^k - x_bar^k + z_bar^k term that Eq. 3's garbled first line
+carries Boyd's x_q^k - x_bar^k + z_bar^k term that Eq. 3's garbled x_q-update
 drops; the dual enters the x_G-update with the sign that makes the fixed point the
 optimum of Eq. 2; the primal/dual residuals follow Boyd Sec. 3.3.1 applied to the
 sharing form; Algorithm 1's window is the last Kp differences including the newest
@@ -67,7 +67,7 @@ class Criterion:
 
 
 def soft(v, t):
-    """Soft threshold: the closed-form minimiser of t|x| + 1/2 (x - v)^2 (Eq. 3, second line)."""
+    """Soft threshold: the closed-form minimiser of t|x| + 1/2 (x - v)^2 (Eq. 3, x_G-update)."""
     return np.sign(v) * np.maximum(np.abs(v) - t, 0.0)
 
 
@@ -93,7 +93,7 @@ def adjoint_re(Aq, r):
 
 
 class RidgeSolver:
-    """Solves (rho I + mu B_J^T B_J) x = b for a fixed active set J (Eq. 3, first line).
+    """Solves (rho I + mu B_J^T B_J) x = b for a fixed active set J (Eq. 3, x_q-update).
 
     The factor is a Cholesky decomposition of the smaller of the two Gram forms:
     the |J| x |J| matrix itself, or, when |J| > 2KM, rho I + mu B_J B_J^T, used

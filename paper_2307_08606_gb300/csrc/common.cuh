@@ -52,7 +52,7 @@ inline int round_up(int a, int b) { return (a + b - 1) / b * b; }
 
 // Which source the forward product reads its per-column scalar from.
 enum VMode : int {
-  kVAdmm = 0,   // v = x_q - x_bar + z_bar - s   (Eq. 3, line 1 right-hand side)
+  kVAdmm = 0,   // v = x_q - x_bar + z_bar - s   (Eq. 3, x_q-update right-hand side)
   kVX = 1,      // v = x_q                       (fold of frozen pixels into y')
   kVExplicit = 2// v = caller array indexed by pixel
 };

@@ -1,4 +1,4 @@
-// FP64 factor of the x-update system (Eq. 3, first line):
+// FP64 factor of the x-update system (Eq. 3, x_q-update):
 //   F = (rho I + mu G)^{-1},  G = B_J B_J^T (Woodbury form, 2KM x 2KM) or
 //                             G = B_J^T B_J (primal form, |J| x |J|),
 // with B_J the real form of the active columns, rows interleaved (re, im) per

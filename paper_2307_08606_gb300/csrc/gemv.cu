@@ -1,5 +1,5 @@
 // Column-compacted complex GEMVs over the active-pixel lists and the FP64
-// SPD apply of the x-update factor (Eq. 1 products inside Eq. 3, line 1).
+// SPD apply of the x-update factor (Eq. 1 products inside Eq. 3, x_q-update).
 //
 // Operators are pixel-major complex64: column n of A_q is KM contiguous float2.
 // The forward product r = base - sum_{p} A[:, idx[p]] v[idx[p]] streams the

@@ -1,6 +1,6 @@
 """Kernel-level parity of the CUDA path (called through the C ABI) against the
 FP64 oracle's definitions: the Eq. 1 forward product over an index list, its
-adjoint, the FP64 x-update factor (Eq. 3, first line) and its SPD apply.
+adjoint, the FP64 x-update factor (Eq. 3, x_q-update) and its SPD apply.
 
 Floating-point bounds are derived from the arithmetic: an FP32 sum of n
 products differs from the exact value by at most n u sum|terms| (u = 2^-24)."""
