@@ -41,6 +41,8 @@ def parse():
     ap.add_argument("--elim", type=int, default=0)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="paper_scale")
+    ap.add_argument("--sensors", type=int, default=0,
+                    help="keep only the first S sensors (smaller case for profiler captures)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -160,9 +162,13 @@ def cpu_baseline_sample(scene, lam, iters=4):
     }
 
 
-def make_scene(name, seed):
+def make_scene(name, seed, sensors=0):
+    import dataclasses
     import scenegen
     sc = scenegen.build_scene(name, seed=seed)
+    if sensors and sensors < sc.geom.Q:
+        sc = scenegen.Scene(geom=dataclasses.replace(sc.geom, Q=sensors), A=sc.A[:sensors],
+                            y=sc.y[:sensors], x_true=sc.x_true[:sensors], seed=sc.seed, meta=sc.meta)
     lam = 0.05 * scenegen.lambda_max(sc.A, sc.y)
     return sc, lam
 
@@ -224,7 +230,7 @@ def main():
     dev = torch.device("cuda", local_rank)
     stream = torch.cuda.current_stream()
 
-    sc, lam = make_scene(args.config, rank)
+    sc, lam = make_scene(args.config, rank, args.sensors)
     g = sc.geom
     s = binding.Solver(g.Q, g.M, g.K, g.N, 1.0, lam, stream=stream.cuda_stream, elim=args.elim)
     for q in range(g.Q):
@@ -291,9 +297,9 @@ def main():
     # roofline of the dominant kernel group
     hbm, src = peaks()
     per_launch_bytes = {
-        "forward": 2 * 0 + g.Q * g.KM * g.N * 8.0,
+        "forward": g.Q * g.KM * g.N * 8.0,
         "adjoint_update": g.Q * g.KM * g.N * 8.0,
-        "spd_woodbury": g.Q * (2 * g.KM) ** 2 * 8.0,
+        "spd_woodbury": g.Q * ((2 * g.KM // 64) * (2 * g.KM // 64 + 1) // 2) * 64 * 64 * 4.0,
     }
     dom = max((k for k in prof if prof[k][1] > 0), key=lambda k: prof[k][0])
     dom_ms, dom_n = prof[dom]
@@ -308,7 +314,8 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "iters_per_step": args.iters, "elim": args.elim,
+        "config": {"workload": WORKLOAD if not args.sensors else WORKLOAD + f", first {g.Q} sensors",
+                   "iters_per_step": args.iters, "elim": args.elim,
                    "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (operators 2.1 GB per replica)",
                    "factor_s": round(factor_s, 3), "refresh_ms_total": round(refresh_ms, 3)},

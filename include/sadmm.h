@@ -218,8 +218,10 @@ int sadmm_adjoint(const float* A, int KM, int N, const int* idx, int nidx, const
 int sadmm_factor(const float* A, int KM, int N, const int* idx, int nidx, double mu,
                  double rho, double* F, int ldf, int* form, void* stream);
 
-/* out = F u for a symmetric n x n FP64 matrix (row-major, leading dimension
- * ldf even and >= n, 16-byte aligned; n <= 32768), u and out n floats. */
+/* out = F u for an n x n FP64 matrix (row-major, leading dimension ldf even
+ * and >= n, F 16-byte aligned, n <= 24576), computed with FP64 products and
+ * sums from FP32 u; out rounded to FP32.  This is how the solver applies its
+ * factor each iteration. */
 int sadmm_spd_apply(const double* F, int n, int ldf, const float* u, float* out, void* stream);
 
 #ifdef __cplusplus

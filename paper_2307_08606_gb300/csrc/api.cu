@@ -48,7 +48,7 @@ struct Sensor {
   float* g = nullptr;        // N, Re(A_J^H r) in list order (primal form)
   int* J = nullptr;          // N, active list
   int* E = nullptr;          // N, pixels removed in the last SSC pass
-  double* fb[3] = {nullptr, nullptr, nullptr};   // factor buffers
+  double* fb[3] = {nullptr, nullptr, nullptr};   // FP64 factor buffers
   double* dinv = nullptr;
   int full = 0;              // buffer holding the full-set factor
   bool full_valid = false;
@@ -87,31 +87,50 @@ struct Ctx {
   int npad_max = 0;
   int k = 0;
   std::vector<sadmm_iter_record> hist;
-  // profiling: one event pair per phase, reused every iteration
+  // profiling: one event pair per (slot, phase); a slot is an iteration not
+  // yet collected (one per iteration when the host synchronises each
+  // iteration, one per iteration of the whole run otherwise)
   bool prof = false;
-  cudaEvent_t ev[2 * SADMM_NUM_PHASES] = {};
-  bool ev_used[SADMM_NUM_PHASES] = {};
+  std::vector<cudaEvent_t> ev;
+  std::vector<char> ev_used;
+  int prof_slot = 0;
   double prof_ms[SADMM_NUM_PHASES] = {};
   long long prof_n[SADMM_NUM_PHASES] = {};
 
+  int ensure_events(int slots) {
+    const size_t need = (size_t)slots * SADMM_NUM_PHASES * 2;
+    while (ev.size() < need) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) return SADMM_ECUDA;
+      ev.push_back(e);
+    }
+    ev_used.resize(ev.size() / 2, 0);
+    return SADMM_OK;
+  }
   void mark(int phase, bool begin) {
     if (!prof) return;
-    cudaEventRecord(ev[2 * phase + (begin ? 0 : 1)], st);
-    if (!begin) ev_used[phase] = true;
+    if (ensure_events(prof_slot + 1) != SADMM_OK) { prof = false; return; }
+    const size_t pair = (size_t)prof_slot * SADMM_NUM_PHASES + phase;
+    cudaEventRecord(ev[2 * pair + (begin ? 0 : 1)], st);
+    if (!begin) ev_used[pair] = 1;
   }
   // After a stream synchronisation: fold the recorded phase times in.
   void collect() {
-    if (!prof) return;
-    for (int p = 0; p < SADMM_NUM_PHASES; ++p) {
-      if (!ev_used[p]) continue;
+    if (!prof) { prof_slot = 0; return; }
+    for (size_t pair = 0; pair < ev_used.size(); ++pair) {
+      if (!ev_used[pair]) continue;
       float ms = 0.f;
-      if (cudaEventElapsedTime(&ms, ev[2 * p], ev[2 * p + 1]) == cudaSuccess) {
-        prof_ms[p] += ms;
-        prof_n[p] += 1;
+      if (cudaEventElapsedTime(&ms, ev[2 * pair], ev[2 * pair + 1]) == cudaSuccess) {
+        prof_ms[pair % SADMM_NUM_PHASES] += ms;
+        prof_n[pair % SADMM_NUM_PHASES] += 1;
       }
-      ev_used[p] = false;
+      ev_used[pair] = 0;
     }
+    prof_slot = 0;
   }
+  // device history of per-iteration scalars for runs without per-iteration sync
+  IterScalars* hist_dev = nullptr;
+  int hist_cap = 0;
 
   void* dalloc(size_t bytes) {
     if (bytes == 0) bytes = 16;
@@ -134,8 +153,9 @@ struct Ctx {
     if (h_scal) cudaFreeHost(h_scal);
     if (h_counts) cudaFreeHost(h_counts);
     if (h_status) cudaFreeHost(h_status);
-    for (auto& e : ev)
-      if (e) { cudaEventDestroy(e); e = nullptr; }
+    for (auto& e : ev) cudaEventDestroy(e);
+    ev.clear();
+    ev_used.clear();
     h_scal = nullptr;
     h_counts = nullptr;
     h_status = nullptr;
@@ -252,7 +272,7 @@ int reset_state(Ctx& c) {
 }
 
 // One iteration of Eq. 3 (x-update, prox, dual) and Algorithm 1 (device side).
-int launch_iteration(Ctx& c) {
+int launch_iteration(Ctx& c, IterScalars* out) {
   const SolverView sv = c.view();
   std::vector<ColumnSet> fw;
   std::vector<SpdSet> spd_w, spd_p;
@@ -277,7 +297,7 @@ int launch_iteration(Ctx& c) {
   c.mark(0, false);
   if (!spd_w.empty()) {
     c.mark(1, true);
-    SADMM_TRY(launch_spd_apply(spd_w.data(), (int)spd_w.size(), false, sv, 2 * c.KM, c.st));
+    SADMM_TRY(launch_spd_apply(spd_w.data(), (int)spd_w.size(), false, sv, c.st));
     c.mark(1, false);
     c.mark(2, true);
     SADMM_TRY(launch_adjoint(adj_w.data(), (int)adj_w.size(), c.KM, true, sv, c.st));
@@ -288,18 +308,18 @@ int launch_iteration(Ctx& c) {
     SADMM_TRY(launch_adjoint(adj_p.data(), (int)adj_p.size(), c.KM, false, sv, c.st));
     c.mark(3, false);
     c.mark(4, true);
-    SADMM_TRY(launch_spd_apply(spd_p.data(), (int)spd_p.size(), true, sv, 2 * c.KM, c.st));
+    SADMM_TRY(launch_spd_apply(spd_p.data(), (int)spd_p.size(), true, sv, c.st));
     c.mark(4, false);
   }
   c.mark(5, true);
-  SADMM_TRY(launch_residuals(sv, c.crit, c.red, c.ticket, c.scal, c.k + 1, c.st));
+  SADMM_TRY(launch_residuals(sv, c.crit, c.red, c.ticket, out, c.k + 1, c.st));
   c.mark(5, false);
   if (c.crit.elim) {
     std::vector<int*> Jp(c.Q), Ep(c.Q);
     for (int q = 0; q < c.Q; ++q) { Jp[q] = c.s[q].J; Ep[q] = c.s[q].E; }
     c.mark(6, true);
     SADMM_TRY(launch_ssc(sv, Jp.data(), Ep.data(), c.counts, c.crit.eps_p, c.crit.freeze_mode,
-                         c.scal, c.st));
+                         out, c.st));
     c.mark(6, false);
   }
   return SADMM_OK;
@@ -331,53 +351,88 @@ double iter_bytes(const Ctx& c) {
   return b;
 }
 
+sadmm_iter_record make_record(const Ctx& c, const IterScalars& r, int changed) {
+  sadmm_iter_record rec;
+  rec.k = r.k; rec.gate = r.gate; rec.changed = changed;
+  rec.active_total = 0;
+  for (const Sensor& S : c.s) rec.active_total += S.cnt;
+  rec.r_pri = r.r_pri; rec.eps_pri = r.eps_pri; rec.d = r.d; rec.eps_dual = r.eps_dual;
+  rec.relchange = r.relchange;
+  return rec;
+}
+
 int run(Ctx& c, float* x_out, int iters, double tol, sadmm_stats* st) {
   const double t0 = now_ms();
   double t_ref = 0.0, bytes = 0.0;
   int refreshes = 0, stop_reason = 0, done = 0;
   c.hist.clear();
-  for (int it = 0; it < iters; ++it) {
-    bytes += iter_bytes(c);
-    SADMM_TRY(launch_iteration(c));
-    SADMM_CUDA_TRY(cudaMemcpyAsync(c.h_scal, c.scal, sizeof(IterScalars), cudaMemcpyDeviceToHost, c.st));
-    SADMM_CUDA_TRY(cudaMemcpyAsync(c.h_counts, c.counts, 2 * c.Q * sizeof(int), cudaMemcpyDeviceToHost, c.st));
+  // Without elimination and without a residual-based stop nothing decided on
+  // the host depends on an iteration's scalars: run the iterations back to
+  // back and read all scalars once at the end.
+  const bool nosync = !c.crit.elim && !(c.crit.stop == 0 && tol > 0.0) && c.crit.stop != 1;
+  if (nosync && iters > 0) {
+    if (c.hist_cap < iters) {
+      void* p = c.dalloc((size_t)iters * sizeof(IterScalars));
+      if (!p) { set_error("history buffer allocation failed"); return SADMM_ENOMEM; }
+      c.hist_dev = (IterScalars*)p;
+      c.hist_cap = iters;
+    }
+    for (int it = 0; it < iters; ++it) {
+      bytes += iter_bytes(c);
+      c.prof_slot = it;
+      SADMM_TRY(launch_iteration(c, c.hist_dev + it));
+      c.k += 1;
+    }
+    std::vector<IterScalars> h(iters);
+    SADMM_CUDA_TRY(cudaMemcpyAsync(h.data(), c.hist_dev, iters * sizeof(IterScalars), cudaMemcpyDeviceToHost, c.st));
     SADMM_CUDA_TRY(cudaStreamSynchronize(c.st));
     c.collect();
-    c.k += 1;
-    done += 1;
-    const IterScalars& r = *c.h_scal;
-    if (r.nonfinite) {
-      set_error("non-finite value in iteration %d", c.k);
-      return SADMM_ENONFINITE;
-    }
-    std::vector<int> changed;
-    if (c.crit.elim && r.gate) {
-      for (int q = 0; q < c.Q; ++q) {
-        if (c.h_counts[c.Q + q] > 0) {
-          changed.push_back(q);
-          c.s[q].cnt = c.h_counts[q];
-        }
+    done = iters;
+    for (int it = 0; it < iters; ++it) {
+      if (h[it].nonfinite) {
+        set_error("non-finite value in iteration %d", h[it].k);
+        return SADMM_ENONFINITE;
       }
+      c.hist.push_back(make_record(c, h[it], 0));
     }
-    if (!changed.empty()) {
-      const double ta = now_ms();
-      c.mark(7, true);
-      SADMM_TRY(apply_changes(c, changed));
-      c.mark(7, false);
+  } else {
+    for (int it = 0; it < iters; ++it) {
+      bytes += iter_bytes(c);
+      SADMM_TRY(launch_iteration(c, c.scal));
+      SADMM_CUDA_TRY(cudaMemcpyAsync(c.h_scal, c.scal, sizeof(IterScalars), cudaMemcpyDeviceToHost, c.st));
+      SADMM_CUDA_TRY(cudaMemcpyAsync(c.h_counts, c.counts, 2 * c.Q * sizeof(int), cudaMemcpyDeviceToHost, c.st));
       SADMM_CUDA_TRY(cudaStreamSynchronize(c.st));
       c.collect();
-      t_ref += now_ms() - ta;
-      refreshes += 1;
+      c.k += 1;
+      done += 1;
+      const IterScalars& r = *c.h_scal;
+      if (r.nonfinite) {
+        set_error("non-finite value in iteration %d", c.k);
+        return SADMM_ENONFINITE;
+      }
+      std::vector<int> changed;
+      if (c.crit.elim && r.gate) {
+        for (int q = 0; q < c.Q; ++q) {
+          if (c.h_counts[c.Q + q] > 0) {
+            changed.push_back(q);
+            c.s[q].cnt = c.h_counts[q];
+          }
+        }
+      }
+      if (!changed.empty()) {
+        const double ta = now_ms();
+        c.mark(7, true);
+        SADMM_TRY(apply_changes(c, changed));
+        c.mark(7, false);
+        SADMM_CUDA_TRY(cudaStreamSynchronize(c.st));
+        c.collect();
+        t_ref += now_ms() - ta;
+        refreshes += 1;
+      }
+      c.hist.push_back(make_record(c, r, (int)changed.size()));
+      if (c.crit.stop == 0 && tol > 0.0 && r.relchange <= tol) { stop_reason = 1; break; }
+      if (c.crit.stop == 1 && r.r_pri <= r.eps_pri && r.d <= r.eps_dual) { stop_reason = 2; break; }
     }
-    sadmm_iter_record rec;
-    rec.k = c.k; rec.gate = r.gate; rec.changed = (int)changed.size();
-    rec.active_total = 0;
-    for (const Sensor& S : c.s) rec.active_total += S.cnt;
-    rec.r_pri = r.r_pri; rec.eps_pri = r.eps_pri; rec.d = r.d; rec.eps_dual = r.eps_dual;
-    rec.relchange = r.relchange;
-    c.hist.push_back(rec);
-    if (c.crit.stop == 0 && tol > 0.0 && r.relchange <= tol) { stop_reason = 1; break; }
-    if (c.crit.stop == 1 && r.r_pri <= r.eps_pri && r.d <= r.eps_dual) { stop_reason = 2; break; }
   }
   if (x_out) {
     SADMM_TRY(launch_scale(c.zbar, (float)c.Q, c.xg, c.N, c.st));
@@ -700,16 +755,14 @@ int sadmm_set_state(sadmm_t ctx, const void* buf, size_t bytes) {
 
 int sadmm_set_profiling(sadmm_t ctx, int on) {
   SADMM_TRY(sadmm::valid_ctx(ctx));
-  if (on) {
-    for (auto& e : ctx->ev)
-      if (!e) SADMM_CUDA_TRY(cudaEventCreate(&e));
-  }
+  SADMM_CUDA_TRY(cudaStreamSynchronize(ctx->st));
   ctx->prof = on != 0;
   for (int p = 0; p < SADMM_NUM_PHASES; ++p) {
     ctx->prof_ms[p] = 0.0;
     ctx->prof_n[p] = 0;
-    ctx->ev_used[p] = false;
   }
+  std::fill(ctx->ev_used.begin(), ctx->ev_used.end(), 0);
+  ctx->prof_slot = 0;
   return SADMM_OK;
 }
 
@@ -815,13 +868,14 @@ int sadmm_factor(const float* A, int KM, int N, const int* idx, int nidx, double
 
 int sadmm_spd_apply(const double* F, int n, int ldf, const float* u, float* out, void* stream) {
   using namespace sadmm;
-  if (!F || !u || !out || n <= 0 || n > 32768 || ldf < n || ldf % 2 != 0) {
+  if (!F || !u || !out || n <= 0 || n > 24576 || ldf < round_up(n, 2) || ldf % 2 != 0 ||
+      ((uintptr_t)F & 15) != 0) {
     set_error("sadmm_spd_apply: bad arguments");
     return SADMM_EINVAL;
   }
   SpdSet s{F, n, ldf, u, out, nullptr, 0};
   SolverView sv{};
-  return launch_spd_apply(&s, 1, false, sv, n, (cudaStream_t)stream);
+  return launch_spd_apply(&s, 1, false, sv, (cudaStream_t)stream);
 }
 
 }  // extern "C"

@@ -107,7 +107,7 @@ int launch_adjoint(const AdjointSet* sets, int nsets, int KM, bool update, const
                    cudaStream_t st);
 
 struct SpdSet {
-  const double* F;
+  const double* F;   // symmetric FP64 factor, row-major
   int n, ldf;
   const float* u;    // n floats
   float* out;        // n floats (plain) or unused (update)
@@ -115,7 +115,7 @@ struct SpdSet {
   int q;
 };
 int launch_spd_apply(const SpdSet* sets, int nsets, bool update, const SolverView& sv,
-                     int max_n, cudaStream_t st);
+                     cudaStream_t st);
 
 int launch_residuals(const SolverView& sv, const sadmm_criterion& c, double* partials,
                      unsigned int* ticket, IterScalars* out, int k_after, cudaStream_t st);

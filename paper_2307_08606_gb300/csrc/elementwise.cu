@@ -3,6 +3,8 @@
 // (Algorithm 1) of the sharing-ADMM iteration.
 #include "common.cuh"
 
+#include <algorithm>
+
 namespace sadmm {
 
 namespace {

@@ -189,6 +189,12 @@ adjoint_kernel(const __grid_constant__ SetBlock<AdjointSet> sets, int KM, bool u
 }
 
 // ---------------------------------------------------------------- SPD apply
+// out = F u for the FP64 factor F.  FP64 is required here: the residual lies
+// mostly where F is small, so |F u| is far below sum |F||u| and FP32 storage or
+// accumulation loses several digits.  One warp per row streams the row as
+// double2; u is staged in shared memory already converted to double so that
+// every matrix element costs exactly one DFMA (the kernel is bound by the
+// FP64 pipe on GB300, not by HBM).
 constexpr int kSpdWarps = 8;
 constexpr int kSpdRowsPerWarp = 4;
 constexpr int kSpdUnroll = 4;
@@ -196,15 +202,16 @@ constexpr int kSpdUnroll = 4;
 __global__ void __launch_bounds__(kSpdWarps * 32)
 spd_apply_kernel(const __grid_constant__ SetBlock<SpdSet> sets, bool update,
                  const __grid_constant__ SolverView sv) {
-  extern __shared__ float s_u[];
+  extern __shared__ double s_ud[];
   const SpdSet& ss = sets.v[blockIdx.y];
   const int rows_per_cta = kSpdWarps * kSpdRowsPerWarp;
   const int rbeg = blockIdx.x * rows_per_cta;
   if (rbeg >= ss.n) return;
   const int n = ss.n;
   const int n2 = (n + 1) / 2;                  // double2 steps per row
-  for (int t = threadIdx.x; t < 2 * n2; t += blockDim.x) s_u[t] = t < n ? ss.u[t] : 0.f;
+  for (int t = threadIdx.x; t < 2 * n2; t += blockDim.x) s_ud[t] = t < n ? (double)ss.u[t] : 0.0;
   __syncthreads();
+  const double2* u2 = reinterpret_cast<const double2*>(s_ud);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int rw = 0; rw < kSpdRowsPerWarp; ++rw) {
     const int i = rbeg + warp * kSpdRowsPerWarp + rw;
@@ -220,16 +227,16 @@ spd_apply_kernel(const __grid_constant__ SetBlock<SpdSet> sets, bool update,
       for (int u = 0; u < kSpdUnroll; ++u) f[u] = __ldcs(row + j + 32 * u);
 #pragma unroll
       for (int u = 0; u < kSpdUnroll; ++u) {
-        const int jj = 2 * (j + 32 * u);
-        acc[u] = fma(f[u].x, (double)s_u[jj], acc[u]);
-        acc[u] = fma(f[u].y, (double)s_u[jj + 1], acc[u]);
+        const double2 x = u2[j + 32 * u];
+        acc[u] = fma(f[u].x, x.x, acc[u]);
+        acc[u] = fma(f[u].y, x.y, acc[u]);
       }
     }
     for (; j < n2; j += 32) {
       const double2 f = __ldcs(row + j);
-      acc[0] = fma(f.x, (double)s_u[2 * j], acc[0]);
-      // the padded column (2j+1 == n) multiplies u = 0
-      acc[0] = fma(f.y, (double)s_u[2 * j + 1], acc[0]);
+      const double2 x = u2[j];            // the padded column (2j+1 == n) multiplies u = 0
+      acc[0] = fma(f.x, x.x, acc[0]);
+      acc[0] = fma(f.y, x.y, acc[0]);
     }
     double g = 0.0;
 #pragma unroll
@@ -303,15 +310,22 @@ int launch_adjoint(const AdjointSet* sets, int nsets, int KM, bool update, const
   return SADMM_OK;
 }
 
-int launch_spd_apply(const SpdSet* sets, int nsets, bool update, const SolverView& sv, int max_n,
+int launch_spd_apply(const SpdSet* sets, int nsets, bool update, const SolverView& sv,
                      cudaStream_t st) {
   if (nsets <= 0) return SADMM_OK;
   if (nsets > kMaxSets) { set_error("launch_spd_apply: too many sets"); return SADMM_EINVAL; }
   SetBlock<SpdSet> blk;
   int mx = 0;
-  for (int i = 0; i < nsets; ++i) { blk.v[i] = sets[i]; mx = max(mx, sets[i].n); }
+  for (int i = 0; i < nsets; ++i) {
+    blk.v[i] = sets[i];
+    mx = max(mx, sets[i].n);
+    if (sets[i].ldf < round_up(sets[i].n, 2) || sets[i].ldf % 2 != 0) {
+      set_error("launch_spd_apply: leading dimension must be even and >= n");
+      return SADMM_EINVAL;
+    }
+  }
   if (mx == 0) return SADMM_OK;
-  const size_t smem = (size_t)round_up(mx, 2) * sizeof(float);
+  const size_t smem = (size_t)round_up(mx, 2) * sizeof(double);
   static bool configured = false;
   if (!configured) {
     SADMM_CUDA_TRY(cudaFuncSetAttribute(spd_apply_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -321,7 +335,6 @@ int launch_spd_apply(const SpdSet* sets, int nsets, bool update, const SolverVie
   dim3 grid(div_up(mx, kSpdWarps * kSpdRowsPerWarp), nsets);
   spd_apply_kernel<<<grid, kSpdWarps * 32, smem, st>>>(blk, update, sv);
   SADMM_LAUNCH_CHECK();
-  (void)max_n;
   return SADMM_OK;
 }
 

@@ -137,7 +137,7 @@ def test_factor_matches_fp64_inverse(B, KM, N, nidx, mu, rho):
     assert np.max(np.abs(Fn @ G - np.eye(n))) <= 1e-13 * cond * n
 
 
-@pytest.mark.parametrize("n,ld", [(1, 2), (37, 64), (100, 128), (4096, 4096)])
+@pytest.mark.parametrize("n,ld", [(1, 2), (37, 64), (101, 102), (4096, 4096)])
 def test_spd_apply_matches_fp64(B, n, ld):
     s = scenegen.Stream(9, n)
     M = s.normal(n * n).reshape(n, n)
@@ -150,4 +150,5 @@ def test_spd_apply_matches_fp64(B, n, ld):
     out = out.cpu().numpy().astype(np.float64)
     ref = F[:n, :n] @ u.astype(np.float64)
     mag = np.abs(F[:n, :n]) @ np.abs(u.astype(np.float64))
-    assert np.all(np.abs(out - ref) <= U32 * np.abs(ref) + 1e-13 * mag)
+    # FP64 sums of exact products, rounded once to FP32
+    assert np.all(np.abs(out - ref) <= U32 * np.abs(ref) + (n + 2) * 2.0 ** -53 * mag)

@@ -187,3 +187,25 @@ def test_torch_allocator_path(B):
     finally:
         B.check(B.load().sadmm_set_allocator(B.ALLOC_FN(), B.FREE_FN(), None))
     assert np.array_equal(xa, xb)
+
+
+@pytest.mark.parametrize("elim", [0, 1])
+def test_profiling_counts_every_phase_launch(B, elim):
+    """Tracing: with profiling on, each iteration records one forward, one
+    factor apply, one adjoint and one residual phase (elimination adds the
+    compaction phase); turning it on again resets the totals."""
+    sc = scenegen.build_scene("small_point", seed=3)
+    lam = 0.05 * scenegen.lambda_max(sc.A, sc.y)
+    s = _solver(B, sc, 1.0, lam, elim=elim)
+    s.set_profiling(True)
+    s.solve(sc.y, 12)
+    p = s.profile()
+    assert p["forward"][1] == 12 and p["spd_woodbury"][1] == 12 and p["adjoint_update"][1] == 12
+    assert p["residuals"][1] == 12
+    assert p["ssc"][1] == (12 if elim else 0)
+    assert all(ms >= 0.0 for ms, _ in p.values())
+    s.set_profiling(True)
+    assert all(n == 0 for _, n in s.profile().values())
+    s.set_profiling(False)
+    s.solve(sc.y, 3)
+    assert all(n == 0 for _, n in s.profile().values())
