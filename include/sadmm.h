@@ -218,6 +218,16 @@ int sadmm_adjoint(const float* A, int KM, int N, const int* idx, int nidx, const
 int sadmm_factor(const float* A, int KM, int N, const int* idx, int nidx, double mu,
                  double rho, double* F, int ldf, int* form, void* stream);
 
+/* In-place rank-e downdate of a Woodbury-form factor after removing the e
+ * columns E (pixel indices) from its active set (Eq. 3, x_q-update, with those
+ * pixels frozen): W <- (W^{-1} - mu B_E B_E^T)^{-1} = W + mu T T^T with
+ * P = W B_E, S = I - mu B_E^T P = L L^T, T = P L^{-T} (Woodbury identity),
+ * in FP64, in passes of at most 32 columns.  W: 2KM x 2KM row-major FP64
+ * (leading dimension 2KM), rows interleaved (re, im) as in sadmm_factor.
+ * Returns SADMM_ENONFINITE if S is not numerically positive definite. */
+int sadmm_factor_downdate(const float* A, int KM, const int* E, int e, double mu, double* W,
+                          void* stream);
+
 /* out = F u for an n x n FP64 matrix (row-major, leading dimension ldf even
  * and >= n, F 16-byte aligned, n <= 24576), computed with FP64 products and
  * sums from FP32 u; out rounded to FP32.  This is how the solver applies its

@@ -146,18 +146,21 @@ class Result:
     state: State
     history: list = field(default_factory=list)
     stop_reason: str = "iters"
+    snapshots: dict = field(default_factory=dict)   # k -> State copy (requested k only)
 
     @property
     def xG(self):
         return len(self.state.x) * self.state.zbar
 
 
-def sadmm(A, y, rho, lam, crit: Criterion, iters, tol=0.0, state: State = None, B=None):
+def sadmm(A, y, rho, lam, crit: Criterion, iters, tol=0.0, state: State = None, B=None,
+          snapshots=()):
     """Run SADMM (crit.elim = 0) or ASADMM (crit.elim = 1) for at most `iters`
     iterations from `state` (zeros if None).  Returns a Result whose history holds,
     per iteration: r_pri, eps_pri, d, eps_dual, relchange, gate, sizes, and the
     decision margins zeta_margin (min |zeta - eps_p| over tested pixels) and
-    gate_margin (|r_pri - eps_pri| / eps_pri)."""
+    gate_margin (|r_pri - eps_pri| / eps_pri).  A copy of the state after
+    iteration k is kept in Result.snapshots for every k in `snapshots`."""
     Q = len(A)
     mu = crit.mu
     B = B if B is not None else [real_form(a) for a in A]
@@ -228,6 +231,8 @@ def sadmm(A, y, rho, lam, crit: Criterion, iters, tol=0.0, state: State = None, 
                     st.xbar = st.x.mean(axis=0)
         rec["sizes"] = [len(j) for j in st.J]
         res.history.append(rec)
+        if st.k in snapshots:
+            res.snapshots[st.k] = st.copy()
         Zold = st.x - st.xbar[None, :] + st.zbar[None, :]
         # 7. stop
         if crit.stop == 0 and tol > 0 and relchange <= tol:

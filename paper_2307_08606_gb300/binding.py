@@ -74,6 +74,7 @@ _SIGS = {
     "sadmm_factor": (C.c_int, [_P, C.c_int, C.c_int, _P, C.c_int, C.c_double, C.c_double, _P,
                                C.c_int, C.POINTER(C.c_int), _P]),
     "sadmm_spd_apply": (C.c_int, [_P, C.c_int, C.c_int, _P, _P, _P]),
+    "sadmm_factor_downdate": (C.c_int, [_P, C.c_int, _P, C.c_int, C.c_double, _P, _P]),
 }
 
 _lib = None
@@ -336,6 +337,14 @@ def factor(A, idx, mu, rho, stream=0):
     check(load().sadmm_factor(_ptr(A), KM, A.shape[0], _ptr(idx), nidx, float(mu), float(rho),
                               _ptr(F), npad, C.byref(form), C.c_void_p(stream)))
     return F, form.value, n
+
+
+def factor_downdate(A, E, mu, W, stream=0):
+    """In place: W <- factor of the active set without the columns E (Woodbury form)."""
+    KM = A.shape[1]
+    check(load().sadmm_factor_downdate(_ptr(A), KM, _ptr(E), int(E.numel()), float(mu), _ptr(W),
+                                       C.c_void_p(stream)))
+    return W
 
 
 def spd_apply(F, n, u, out=None, stream=0):

@@ -49,7 +49,9 @@ struct Sensor {
   int* J = nullptr;          // N, active list
   int* E = nullptr;          // N, pixels removed in the last SSC pass
   double* fb[3] = {nullptr, nullptr, nullptr};   // FP64 factor buffers
-  double* dinv = nullptr;
+  double* dinv = nullptr;      // diagonal-block inverses; also the downdate's n x 32 scratch
+  double* dd = nullptr;        // downdate scratch (partial sums and the small factor)
+  int cum_dd = 0;              // columns downdated since the last full factorisation
   int full = 0;              // buffer holding the full-set factor
   bool full_valid = false;
   int cur = 0;               // buffer in use
@@ -226,6 +228,49 @@ int refresh(Ctx& c, const std::vector<int>& qs, bool full_set) {
     S.n = jobs[i].n;
     S.woodbury = jobs[i].woodbury;
     if (full_set) { S.full = outbuf[i]; S.full_valid = true; }
+    S.cum_dd = 0;
+  }
+  return SADMM_OK;
+}
+
+// Rank-|E| downdate of Woodbury-form factors (see run_downdate), in passes of
+// at most kDowndateMax removed columns.  Sensors whose downdate fails (the
+// small system is not numerically positive definite) are returned in `failed`.
+int downdate(Ctx& c, const std::vector<int>& qs, std::vector<int>* failed) {
+  if (qs.empty()) return SADMM_OK;
+  std::vector<int> dst(c.Q), etot(c.Q);
+  int max_e = 0;
+  for (int q : qs) {
+    Sensor& S = c.s[q];
+    dst[q] = (S.cur == S.full) ? (S.full + 1) % 3 : S.cur;
+    etot[q] = c.h_counts[c.Q + q];
+    max_e = std::max(max_e, etot[q]);
+  }
+  SADMM_CUDA_TRY(cudaMemsetAsync(c.dstatus, 0, sizeof(int) * c.Q, c.st));
+  const int n = 2 * c.KM;
+  const size_t nblk = div_up(n, 256);
+  for (int off = 0; off < max_e; off += kDowndateMax) {
+    std::vector<DowndateJob> jobs;
+    for (int q : qs) {
+      Sensor& S = c.s[q];
+      if (etot[q] <= off) continue;
+      DowndateJob j;
+      j.A = S.A; j.E = S.E + off; j.e = std::min(kDowndateMax, etot[q] - off); j.n = n;
+      j.Wsrc = (off == 0) ? S.fb[S.cur] : S.fb[dst[q]];
+      j.Wdst = S.fb[dst[q]];
+      j.P = S.dinv; j.Spart = S.dd; j.S = S.dd + nblk * kDowndateMax * kDowndateMax;
+      j.slot = q;
+      jobs.push_back(j);
+    }
+    SADMM_TRY(run_downdate(jobs.data(), (int)jobs.size(), c.KM, c.crit.mu, c.dstatus, c.st));
+  }
+  SADMM_CUDA_TRY(cudaMemcpyAsync(c.h_status, c.dstatus, sizeof(int) * c.Q, cudaMemcpyDeviceToHost, c.st));
+  SADMM_CUDA_TRY(cudaStreamSynchronize(c.st));
+  for (int q : qs) {
+    Sensor& S = c.s[q];
+    if (c.h_status[q]) { failed->push_back(q); continue; }
+    S.cur = dst[q];
+    S.cum_dd += etot[q];
   }
   return SADMM_OK;
 }
@@ -263,6 +308,7 @@ int reset_state(Ctx& c) {
     S.cnt = c.N;
     cnts[q] = c.N;
     S.cur = S.full;
+    S.cum_dd = 0;
     factor_dims(c, c.N, &S.n, &S.woodbury);
   }
   SADMM_CUDA_TRY(cudaMemcpyAsync(c.counts, cnts.data(), cnts.size() * sizeof(int), cudaMemcpyHostToDevice, c.st));
@@ -339,7 +385,18 @@ int apply_changes(Ctx& c, const std::vector<int>& changed) {
   } else {
     SADMM_TRY(launch_recompute_xbar(sv, c.st));
   }
-  return refresh(c, changed, false);
+  // A Woodbury-form factor that stays in Woodbury form is downdated by the
+  // removed columns; a form change, a primal-form factor, or too many
+  // accumulated downdates (rounding) refactor from scratch.
+  std::vector<int> dd, full;
+  for (int q : changed) {
+    const Sensor& S = c.s[q];
+    const int e = c.h_counts[c.Q + q];
+    if (S.woodbury && S.cnt > 2 * c.KM && S.cum_dd + e <= std::max(kDowndateMax, c.KM / 2)) dd.push_back(q);
+    else full.push_back(q);
+  }
+  SADMM_TRY(downdate(c, dd, &full));
+  return refresh(c, full, false);
 }
 
 double iter_bytes(const Ctx& c) {
@@ -534,6 +591,7 @@ int sadmm_create(int Q, int M, int K, int N, double rho, double lambda, const sa
     S.E = (int*)A((size_t)N * sizeof(int));
     for (int b = 0; b < 3; ++b) S.fb[b] = (double*)A(fbytes);
     S.dinv = (double*)A((size_t)ctx->npad_max * kTile * sizeof(double));
+    S.dd = (double*)A(downdate_scratch_doubles(2 * (int)KM) * sizeof(double));
   }
   const size_t QN = (size_t)Q * N;
   ctx->x = (float*)A(QN * sizeof(float));
@@ -742,6 +800,7 @@ int sadmm_set_state(sadmm_t ctx, const void* buf, size_t bytes) {
     counts[q] = cnt[q];
     if (cnt[q] == ctx->N) {
       S.cur = S.full;
+      S.cum_dd = 0;
       factor_dims(*ctx, ctx->N, &S.n, &S.woodbury);
     } else {
       changed.push_back(q);
@@ -863,6 +922,40 @@ int sadmm_factor(const float* A, int KM, int N, const int* idx, int nidx, double
   if (rc != SADMM_OK) return rc;
   if (hs) { set_error("sadmm_factor: matrix not positive definite"); return SADMM_ENONFINITE; }
   if (form) *form = wb;
+  return SADMM_OK;
+}
+
+int sadmm_factor_downdate(const float* A, int KM, const int* E, int e, double mu, double* W,
+                          void* stream) {
+  using namespace sadmm;
+  if (!A || !W || KM <= 0 || KM % 32 != 0 || e < 0 || (e > 0 && !E) || !(mu > 0.0)) {
+    set_error("sadmm_factor_downdate: bad arguments");
+    return SADMM_EINVAL;
+  }
+  if (e == 0) return SADMM_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int n = 2 * KM;
+  void *P = nullptr, *dd = nullptr, *status = nullptr;
+  SADMM_CUDA_TRY(cudaMallocAsync(&P, (size_t)n * kDowndateMax * sizeof(double), st));
+  SADMM_CUDA_TRY(cudaMallocAsync(&dd, downdate_scratch_doubles(n) * sizeof(double), st));
+  SADMM_CUDA_TRY(cudaMallocAsync(&status, sizeof(int), st));
+  SADMM_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int), st));
+  int rc = SADMM_OK;
+  for (int off = 0; off < e && rc == SADMM_OK; off += kDowndateMax) {
+    DowndateJob j{(const float2*)A, E + off, std::min(kDowndateMax, e - off), n, W, W, (double*)P,
+                  (double*)dd, (double*)dd + (size_t)div_up(n, 256) * kDowndateMax * kDowndateMax, 0};
+    rc = run_downdate(&j, 1, KM, mu, (int*)status, st);
+  }
+  int hs = 0;
+  if (rc == SADMM_OK) {
+    SADMM_CUDA_TRY(cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    SADMM_CUDA_TRY(cudaStreamSynchronize(st));
+  }
+  cudaFreeAsync(P, st);
+  cudaFreeAsync(dd, st);
+  cudaFreeAsync(status, st);
+  if (rc != SADMM_OK) return rc;
+  if (hs) { set_error("sadmm_factor_downdate: downdated system not positive definite"); return SADMM_ENONFINITE; }
   return SADMM_OK;
 }
 

@@ -144,4 +144,24 @@ struct FactorJob {
 int run_factor(const FactorJob* jobs, int njobs, int KM, double mu, double rho, int* d_status,
                cudaStream_t st);
 
+// Rank-e downdate of a Woodbury-form factor after removing e <= kDowndateMax
+// columns E from the active set (Eq. 3's system without those pixels):
+//   (G - mu U U^T)^{-1} = W + mu T T^T,  P = W U,  S = I - mu U^T P = L L^T,
+//   T = P L^{-T},  U = B_E (interleaved real form of the removed columns).
+constexpr int kDowndateMax = 32;
+struct DowndateJob {
+  const float2* A;
+  const int* E;          // removed pixels of this pass
+  int e;                 // 1..kDowndateMax
+  int n;                 // factor dimension 2KM (leading dimension too)
+  const double* Wsrc;    // current factor
+  double* Wdst;          // updated factor (may alias Wsrc)
+  double* P;             // n x kDowndateMax scratch: W U, then T
+  double* Spart;         // ceil(n/256) x kDowndateMax^2 partial sums of U^T P
+  double* S;             // kDowndateMax^2: the inverse Cholesky factor of S
+  int slot;              // index of this job's failure flag in the status array
+};
+int run_downdate(const DowndateJob* jobs, int njobs, int KM, double mu, int* d_status, cudaStream_t st);
+size_t downdate_scratch_doubles(int n);
+
 }  // namespace sadmm

@@ -323,7 +323,243 @@ inverse_kernel(const __grid_constant__ JobBlock jobs) {
     }
 }
 
+// ---------------------------------------------------------------- downdate
+constexpr int DM = kDowndateMax;          // 32
+constexpr int kDdWarps = 8;
+constexpr int kDdChunk = 512;             // rows of U staged per shared-memory pass
+using DdBlock = SetBlock<DowndateJob>;
+
+// P = W U: one warp per row of W, lanes stride the row; U (the removed
+// columns of B as doubles) is staged in shared memory column by column in
+// chunks of rows (consecutive lanes read consecutive rows: no bank conflicts).
+template <int EB>
+struct DdShape {
+  static constexpr int rows = EB <= 8 ? 4 : (EB <= 16 ? 2 : 1);   // rows per warp
+};
+
+template <int EB>
+__global__ void __launch_bounds__(kDdWarps * 32)
+dd_p_kernel(const __grid_constant__ DdBlock jobs, int KM) {
+  constexpr int RPW = DdShape<EB>::rows;
+  extern __shared__ double s_u[];                 // [EB][kDdChunk]
+  const DowndateJob& jb = jobs.v[blockIdx.y];
+  const int n = jb.n, e = jb.e;
+  const int rbeg = blockIdx.x * kDdWarps * RPW;
+  if (rbeg >= n) return;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const float* Af = reinterpret_cast<const float*>(jb.A);
+  const size_t twoKM = 2 * (size_t)KM;
+  double acc[RPW][EB];
+#pragma unroll
+  for (int r = 0; r < RPW; ++r)
+#pragma unroll
+    for (int c = 0; c < EB; ++c) acc[r][c] = 0.0;
+  for (int j0 = 0; j0 < n; j0 += kDdChunk) {
+    const int nj = min(kDdChunk, n - j0);
+    __syncthreads();
+    for (int t = threadIdx.x; t < kDdChunk * EB; t += blockDim.x) {
+      const int c = t / kDdChunk, jj = t % kDdChunk;
+      double v = 0.0;
+      if (c < e && jj < nj) v = (double)Af[(size_t)jb.E[c] * twoKM + j0 + jj];
+      s_u[c * kDdChunk + jj] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < RPW; ++r) {
+      const int i = rbeg + warp * RPW + r;
+      if (i >= n) break;
+      const double* row = jb.Wsrc + (size_t)i * n + j0;
+      for (int jj = lane; jj < nj; jj += 32) {
+        const double w = __ldcs(row + jj);
+#pragma unroll
+        for (int c = 0; c < EB; ++c) acc[r][c] = fma(w, s_u[c * kDdChunk + jj], acc[r][c]);
+      }
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < RPW; ++r) {
+    const int i = rbeg + warp * RPW + r;
+#pragma unroll
+    for (int c = 0; c < EB; ++c) {
+      double v = acc[r][c];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (i < n && lane == c) jb.P[(size_t)i * DM + c] = (c < e) ? v : 0.0;
+    }
+  }
+  // columns EB..DM-1 of P are never written by this kernel: zero them
+  if constexpr (EB < DM) {
+    for (int t = threadIdx.x; t < kDdWarps * RPW * (DM - EB); t += blockDim.x) {
+      const int i = rbeg + t / (DM - EB), c = EB + t % (DM - EB);
+      if (i < n) jb.P[(size_t)i * DM + c] = 0.0;
+    }
+  }
+}
+
+// Spart[blk][a][b] = sum over 256 rows of U[i][a] P[i][b] (fixed order per thread).
+__global__ void dd_s_kernel(const __grid_constant__ DdBlock jobs, int KM) {
+  const DowndateJob& jb = jobs.v[blockIdx.y];
+  const int a = threadIdx.x / DM, b = threadIdx.x % DM;
+  const int i0 = blockIdx.x * 256;
+  if (i0 >= jb.n) return;
+  double acc = 0.0;
+  if (a < jb.e && b < jb.e) {
+    const float* col = reinterpret_cast<const float*>(jb.A) + (size_t)jb.E[a] * 2 * KM;
+    const int i1 = min(jb.n, i0 + 256);
+    for (int i = i0; i < i1; ++i) acc = fma((double)col[i], jb.P[(size_t)i * DM + b], acc);
+  }
+  jb.Spart[((size_t)blockIdx.x * DM + a) * DM + b] = acc;
+}
+
+// S = I - mu sum_blk Spart[blk]; Cholesky S = L L^T and L^{-1} in shared memory
+// (identity beyond e); writes L^{-1} to jb.S.
+__global__ void __launch_bounds__(DM * DM)
+dd_chol_kernel(const __grid_constant__ DdBlock jobs, double mu, int* status) {
+  const DowndateJob& jb = jobs.v[blockIdx.x];
+  __shared__ double L[DM][DM + 1], Li[DM][DM + 1];
+  const int a = threadIdx.x / DM, b = threadIdx.x % DM;
+  const int nblk = (jb.n + 255) / 256;
+  double sum = 0.0;
+  for (int k = 0; k < nblk; ++k) sum += jb.Spart[((size_t)k * DM + a) * DM + b];
+  L[a][b] = (a < jb.e && b < jb.e) ? ((a == b ? 1.0 : 0.0) - mu * sum) : (a == b ? 1.0 : 0.0);
+  __syncthreads();
+  for (int j = 0; j < DM; ++j) {
+    double d = L[j][j];
+    __syncthreads();
+    if (!(d > 0.0) || !isfinite(d)) {
+      if (threadIdx.x == 0) status[jb.slot] = 1;
+      d = 1.0;
+    }
+    d = sqrt(d);
+    if (b == j && a >= j) L[a][j] = (a == j) ? d : L[a][j] / d;
+    __syncthreads();
+    if (b > j && a >= b) L[a][b] = fma(-L[a][j], L[b][j], L[a][b]);
+    __syncthreads();
+  }
+  for (int i = 0; i < DM; ++i) {
+    if (threadIdx.x < DM) {
+      const int c = threadIdx.x;
+      double v = 0.0;
+      if (c <= i) {
+        double s = (c == i) ? 1.0 : 0.0;
+        for (int k = c; k < i; ++k) s = fma(-L[i][k], Li[k][c], s);
+        v = s / L[i][i];
+      }
+      Li[i][c] = v;
+    }
+    __syncthreads();
+  }
+  jb.S[a * DM + b] = Li[a][b];
+}
+
+// T = P L^{-T} row by row, in place in P.
+__global__ void dd_t_kernel(const __grid_constant__ DdBlock jobs) {
+  const DowndateJob& jb = jobs.v[blockIdx.y];
+  __shared__ double Li[DM][DM];
+  for (int t = threadIdx.x; t < DM * DM; t += blockDim.x) Li[t / DM][t % DM] = jb.S[t];
+  __syncthreads();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= jb.n) return;
+  double p[DM];
+#pragma unroll
+  for (int c = 0; c < DM; ++c) p[c] = jb.P[(size_t)i * DM + c];
+#pragma unroll
+  for (int c = 0; c < DM; ++c) {
+    double t = 0.0;
+#pragma unroll
+    for (int k = 0; k <= c; ++k) t = fma(p[k], Li[c][k], t);
+    jb.P[(size_t)i * DM + c] = t;
+  }
+}
+
+// Wdst = Wsrc + mu T T^T on the lower 64x64 tiles, written to both triangles.
+__global__ void __launch_bounds__(kThreads)
+dd_w_kernel(const __grid_constant__ DdBlock jobs, double mu) {
+  const DowndateJob& jb = jobs.v[blockIdx.y];
+  const int Tn = jb.n / T;
+  if ((int)blockIdx.x >= Tn * (Tn + 1) / 2) return;
+  int bi, bj;
+  tri_decode(blockIdx.x, bi, bj);
+  __shared__ double Ti[DM][T], Tj[DM][T];
+  const int tid = threadIdx.x, ty = tid / 16, tx = tid % 16;
+  for (int t = tid; t < DM * T; t += kThreads) {
+    const int r = t / DM, c = t % DM;
+    Ti[c][r] = jb.P[(size_t)(bi * T + r) * DM + c];
+    Tj[c][r] = jb.P[(size_t)(bj * T + r) * DM + c];
+  }
+  __syncthreads();
+  double acc[4][4];
+  zero_acc(acc);
+  for (int c = 0; c < jb.e; ++c) {
+    double x[4], y[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) { x[u] = Ti[c][ty + 16 * u]; y[u] = Tj[c][tx + 16 * u]; }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) acc[u][v] = fma(x[u], y[v], acc[u][v]);
+  }
+  const size_t n = jb.n;
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const size_t i = bi * T + ty + 16 * u, j = bj * T + tx + 16 * v;
+      const double val = jb.Wsrc[i * n + j] + mu * acc[u][v];
+      jb.Wdst[i * n + j] = val;
+      if (bi != bj) jb.Wdst[j * n + i] = val;
+    }
+}
+
+template <int EB>
+int launch_dd_p(const DdBlock& blk, int njobs, int n_max, int KM, cudaStream_t st) {
+  const size_t smem = (size_t)kDdChunk * EB * sizeof(double);
+  static bool configured = false;
+  if (!configured) {
+    SADMM_CUDA_TRY(cudaFuncSetAttribute(dd_p_kernel<EB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)smem));
+    configured = true;
+  }
+  dd_p_kernel<EB><<<dim3(div_up(n_max, kDdWarps * DdShape<EB>::rows), njobs), kDdWarps * 32, smem, st>>>(blk, KM);
+  SADMM_LAUNCH_CHECK();
+  return SADMM_OK;
+}
+
 }  // namespace
+
+size_t downdate_scratch_doubles(int n) {
+  return (size_t)(div_up(n, 256) + 1) * DM * DM;
+}
+
+int run_downdate(const DowndateJob* jobs, int njobs, int KM, double mu, int* d_status, cudaStream_t st) {
+  if (njobs <= 0) return SADMM_OK;
+  if (njobs > kMaxSets) { set_error("run_downdate: too many jobs"); return SADMM_EINVAL; }
+  DdBlock blk;
+  int n_max = 0, e_max = 0;
+  for (int i = 0; i < njobs; ++i) {
+    blk.v[i] = jobs[i];
+    if (jobs[i].e < 1 || jobs[i].e > DM || jobs[i].n % T != 0) {
+      set_error("run_downdate: bad job (e=%d n=%d)", jobs[i].e, jobs[i].n);
+      return SADMM_EINVAL;
+    }
+    n_max = max(n_max, jobs[i].n);
+    e_max = max(e_max, jobs[i].e);
+  }
+  if (e_max <= 4) SADMM_TRY(launch_dd_p<4>(blk, njobs, n_max, KM, st));
+  else if (e_max <= 8) SADMM_TRY(launch_dd_p<8>(blk, njobs, n_max, KM, st));
+  else if (e_max <= 16) SADMM_TRY(launch_dd_p<16>(blk, njobs, n_max, KM, st));
+  else SADMM_TRY(launch_dd_p<32>(blk, njobs, n_max, KM, st));
+  dd_s_kernel<<<dim3(div_up(n_max, 256), njobs), DM * DM, 0, st>>>(blk, KM);
+  SADMM_LAUNCH_CHECK();
+  dd_chol_kernel<<<njobs, DM * DM, 0, st>>>(blk, mu, d_status);
+  SADMM_LAUNCH_CHECK();
+  dd_t_kernel<<<dim3(div_up(n_max, 128), njobs), 128, 0, st>>>(blk);
+  SADMM_LAUNCH_CHECK();
+  const int Tn = n_max / T;
+  dd_w_kernel<<<dim3(Tn * (Tn + 1) / 2, njobs), kThreads, 0, st>>>(blk, mu);
+  SADMM_LAUNCH_CHECK();
+  return SADMM_OK;
+}
 
 int run_factor(const FactorJob* jobs, int njobs, int KM, double mu, double rho, int* d_status,
                cudaStream_t st) {

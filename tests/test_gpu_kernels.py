@@ -152,3 +152,28 @@ def test_spd_apply_matches_fp64(B, n, ld):
     mag = np.abs(F[:n, :n]) @ np.abs(u.astype(np.float64))
     # FP64 sums of exact products, rounded once to FP32
     assert np.all(np.abs(out - ref) <= U32 * np.abs(ref) + (n + 2) * 2.0 ** -53 * mag)
+
+
+@pytest.mark.parametrize("KM,N,e", [(32, 300, 1), (32, 300, 7), (128, 700, 40), (256, 1024, 3)])
+def test_factor_downdate_matches_fresh_inverse(B, KM, N, e):
+    """Rank-e downdate of the Woodbury factor equals the FP64 inverse of the
+    Gram without the removed columns."""
+    A = _operator(KM, N, seed=KM + 3 * N + e, radar=(KM == 256))
+    mu, rho = 1.0, 1.0
+    s = scenegen.Stream(13, e)
+    J = np.arange(N, dtype=np.int32)
+    E = np.sort(s.permutation(N)[:e]).astype(np.int32)
+    dev = torch.device("cuda:0")
+    At = torch.from_numpy(A).to(dev)
+    W, form, n = B.factor(At, torch.from_numpy(J).to(dev), mu, rho)
+    assert form == 1
+    B.factor_downdate(At, torch.from_numpy(E).to(dev), mu, W)
+    torch.cuda.synchronize()
+    Wd = W.cpu().numpy()[:n, :n]
+    keep = np.setdiff1d(J, E)
+    Bm = _interleaved_real_form(A, keep)
+    G = rho * np.eye(n) + mu * Bm @ Bm.T
+    ref = np.linalg.inv(G)
+    cond = np.linalg.cond(G)
+    assert np.max(np.abs(Wd - ref)) <= 1e-14 * cond * n * np.max(np.abs(ref))
+    assert np.array_equal(Wd, Wd.T)
