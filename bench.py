@@ -39,6 +39,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--iters", type=int, default=100, help="ADMM iterations per step")
     ap.add_argument("--elim", type=int, default=0)
+    ap.add_argument("--precision", type=int, default=0,
+                    help="0 FP32, 1/2 BF16/FP16 hi+lo pairs, 3/4 BF16/FP16 hi plane + lo refresh")
+    ap.add_argument("--correct-every", type=int, default=4)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="paper_scale")
     ap.add_argument("--sensors", type=int, default=0,
@@ -232,7 +235,8 @@ def main():
 
     sc, lam = make_scene(args.config, rank, args.sensors)
     g = sc.geom
-    s = binding.Solver(g.Q, g.M, g.K, g.N, 1.0, lam, stream=stream.cuda_stream, elim=args.elim)
+    s = binding.Solver(g.Q, g.M, g.K, g.N, 1.0, lam, stream=stream.cuda_stream, elim=args.elim,
+                       precision=args.precision, correct_every=args.correct_every)
     for q in range(g.Q):
         s.set_operator(q, torch.from_numpy(sc.A[q]).to(dev))
     t0 = time.perf_counter()
@@ -296,9 +300,11 @@ def main():
 
     # roofline of the dominant kernel group
     hbm, src = peaks()
+    # operator bytes per entry: complex64 or hi+lo pairs 8; hi plane 4 (+4 on refresh iterations)
+    bpe = 8.0 if args.precision in (0, 1, 2) else 4.0 * (1.0 + 1.0 / args.correct_every)
     per_launch_bytes = {
-        "forward": g.Q * g.KM * g.N * 8.0,
-        "adjoint_update": g.Q * g.KM * g.N * 8.0,
+        "forward": g.Q * g.KM * g.N * bpe,
+        "adjoint_update": g.Q * g.KM * g.N * bpe,
         "spd_woodbury": g.Q * ((2 * g.KM // 64) * (2 * g.KM // 64 + 1) // 2) * 64 * 64 * 4.0,
     }
     dom = max((k for k in prof if prof[k][1] > 0), key=lambda k: prof[k][0])
@@ -313,9 +319,12 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {0: "f32", 1: "bf16x2/f32", 2: "f16x2/f32", 3: "bf16/f32", 4: "f16/f32"}[args.precision],
+        "data": "synthetic",
         "config": {"workload": WORKLOAD if not args.sensors else WORKLOAD + f", first {g.Q} sensors",
-                   "iters_per_step": args.iters, "elim": args.elim,
+                   "iters_per_step": args.iters, "elim": args.elim, "precision": args.precision,
+                   "correct_every": args.correct_every if args.precision >= 3 else None,
                    "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (operators 2.1 GB per replica)",
                    "factor_s": round(factor_s, 3), "refresh_ms_total": round(refresh_ms, 3)},

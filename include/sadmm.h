@@ -63,6 +63,12 @@ typedef struct {
   int    freeze_mode; /* 0 = removed pixels keep their value, 1 = removed pixels set to 0 */
   int    stop;        /* 0 = ||X^{k+1}-X^k||_F <= tol ||X^{k+1}||_F; 1 = primal & dual
                          residuals below eps_pri and eps_dual (Boyd Sec. 3.3.1)          */
+  int    precision;   /* operator used by the per-iteration products:
+                         0 = complex64 (FP32), 1 = BF16 hi/lo pairs, 2 = FP16 hi/lo pairs,
+                         3 = BF16 hi plane with the lo-plane products refreshed every
+                         correct_every iterations, 4 = the same with FP16 planes.  The
+                         factor, its refreshes and the fold always use the FP32 operator. */
+  int    correct_every; /* precision 3/4: lo-plane refresh period (>= 1)                    */
 } sadmm_criterion;
 
 /* Per-solve summary. */
@@ -218,6 +224,21 @@ int sadmm_adjoint(const float* A, int KM, int N, const int* idx, int nidx, const
 int sadmm_factor(const float* A, int KM, int N, const int* idx, int nidx, double mu,
                  double rho, double* F, int ldf, int* form, void* stream);
 
+/* Split-precision operator planes: for each of the 2 n_complex floats a of A,
+ * hi = round(a) and lo = round(a - hi) in BF16 (kind 1) or FP16 (kind 2),
+ * round-to-nearest; hi + lo is exact in FP32.  hi and lo: device arrays of
+ * 2 n_complex 16-bit values in A's layout (pixel-major (re, im) pairs). */
+int sadmm_split_operator(const float* A, size_t n_complex, int kind, void* hi, void* lo, void* stream);
+
+/* r = base - P_idx v_idx with P = hi (planes 1), lo (planes 2) or hi + lo
+ * (planes 3), FP32 accumulation (as sadmm_forward; KM a multiple of 4). */
+int sadmm_forward_split(const void* hi, const void* lo, int kind, int planes, int KM, int N, const int* idx,
+                        int nidx, const float* v, const float* base, float* r, void* stream);
+
+/* g[p] = Re(P[:, idx[p]]^H w) with P as in sadmm_forward_split (KM <= 16384). */
+int sadmm_adjoint_split(const void* hi, const void* lo, int kind, int planes, int KM, int N, const int* idx,
+                        int nidx, const float* w, float* g, void* stream);
+
 /* In-place rank-e downdate of a Woodbury-form factor after removing the e
  * columns E (pixel indices) from its active set (Eq. 3, x_q-update, with those
  * pixels frozen): W <- (W^{-1} - mu B_E B_E^T)^{-1} = W + mu T T^T with
@@ -229,9 +250,10 @@ int sadmm_factor_downdate(const float* A, int KM, const int* E, int e, double mu
                           void* stream);
 
 /* out = F u for an n x n FP64 matrix (row-major, leading dimension ldf even
- * and >= n, F 16-byte aligned, n <= 24576), computed with FP64 products and
- * sums from FP32 u; out rounded to FP32.  This is how the solver applies its
- * factor each iteration. */
+ * and >= n, n <= 49152) and FP32 u; out rounded to FP32.  As in the solver, F
+ * is first split into FP32 pairs (hi, lo) and the products are formed exactly
+ * and summed as FP32 pairs with the error-free two-sum (about 48 significant
+ * bits).  Allocates a temporary n x ldf pair copy on `stream`. */
 int sadmm_spd_apply(const double* F, int n, int ldf, const float* u, float* out, void* stream);
 
 #ifdef __cplusplus

@@ -24,7 +24,8 @@ class SadmmError(RuntimeError):
 class Criterion(C.Structure):
     _fields_ = [("mu", C.c_double), ("Kp", C.c_int), ("eps_p", C.c_double),
                 ("eps_abs", C.c_double), ("eps_rel", C.c_double), ("elim", C.c_int),
-                ("freeze_mode", C.c_int), ("stop", C.c_int)]
+                ("freeze_mode", C.c_int), ("stop", C.c_int), ("precision", C.c_int),
+                ("correct_every", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -75,6 +76,11 @@ _SIGS = {
                                C.c_int, C.POINTER(C.c_int), _P]),
     "sadmm_spd_apply": (C.c_int, [_P, C.c_int, C.c_int, _P, _P, _P]),
     "sadmm_factor_downdate": (C.c_int, [_P, C.c_int, _P, C.c_int, C.c_double, _P, _P]),
+    "sadmm_split_operator": (C.c_int, [_P, C.c_size_t, C.c_int, _P, _P, _P]),
+    "sadmm_forward_split": (C.c_int, [_P, _P, C.c_int, C.c_int, C.c_int, C.c_int, _P, C.c_int, _P, _P,
+                                      _P, _P]),
+    "sadmm_adjoint_split": (C.c_int, [_P, _P, C.c_int, C.c_int, C.c_int, C.c_int, _P, C.c_int, _P, _P,
+                                      _P]),
 }
 
 _lib = None
@@ -345,6 +351,36 @@ def factor_downdate(A, E, mu, W, stream=0):
     check(load().sadmm_factor_downdate(_ptr(A), KM, _ptr(E), int(E.numel()), float(mu), _ptr(W),
                                        C.c_void_p(stream)))
     return W
+
+
+BF16, FP16 = 1, 2
+
+
+def split_operator(A, kind, stream=0):
+    """(hi, lo) int16 tensors holding the 16-bit planes of the complex64 operator A."""
+    import torch
+    hi = torch.empty(A.shape + (2,), dtype=torch.int16, device=A.device)
+    lo = torch.empty_like(hi)
+    check(load().sadmm_split_operator(_ptr(A), A.numel(), int(kind), _ptr(hi), _ptr(lo), C.c_void_p(stream)))
+    return hi, lo
+
+
+def forward_split(hi, lo, kind, planes, idx, v, base=None, stream=0):
+    import torch
+    N, KM = hi.shape[0], hi.shape[1]
+    out = torch.empty(KM, dtype=torch.complex64, device=hi.device)
+    check(load().sadmm_forward_split(_ptr(hi), _ptr(lo), int(kind), int(planes), KM, N, _ptr(idx),
+                                     int(idx.numel()), _ptr(v), _ptr(base), _ptr(out), C.c_void_p(stream)))
+    return out
+
+
+def adjoint_split(hi, lo, kind, planes, idx, w, stream=0):
+    import torch
+    N, KM = hi.shape[0], hi.shape[1]
+    out = torch.empty(int(idx.numel()), dtype=torch.float32, device=hi.device)
+    check(load().sadmm_adjoint_split(_ptr(hi), _ptr(lo), int(kind), int(planes), KM, N, _ptr(idx),
+                                     int(idx.numel()), _ptr(w), _ptr(out), C.c_void_p(stream)))
+    return out
 
 
 def spd_apply(F, n, u, out=None, stream=0):

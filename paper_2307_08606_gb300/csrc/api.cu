@@ -49,9 +49,14 @@ struct Sensor {
   int* J = nullptr;          // N, active list
   int* E = nullptr;          // N, pixels removed in the last SSC pass
   double* fb[3] = {nullptr, nullptr, nullptr};   // FP64 factor buffers
+  float2* fhl[3] = {nullptr, nullptr, nullptr};  // their (hi, lo) FP32-pair copies, used every iteration
   double* dinv = nullptr;      // diagonal-block inverses; also the downdate's n x 32 scratch
   double* dd = nullptr;        // downdate scratch (partial sums and the small factor)
   int cum_dd = 0;              // columns downdated since the last full factorisation
+  uint16_t* hi = nullptr;      // split-precision planes (precision > 0)
+  uint16_t* lo = nullptr;
+  float2* base_corr = nullptr; // y' - A_lo,J v at the last lo refresh (precision 3/4)
+  float* gcorr = nullptr;      // Re(a_lo^H w) per pixel at the last lo refresh
   int full = 0;              // buffer holding the full-set factor
   bool full_valid = false;
   int cur = 0;               // buffer in use
@@ -89,6 +94,10 @@ struct Ctx {
   int npad_max = 0;
   int k = 0;
   std::vector<sadmm_iter_record> hist;
+  bool corr_due = true;        // precision 3/4: refresh the lo-plane products next iteration
+  int last_corr_k = 0;
+  int split_kind() const { return (crit.precision == 1 || crit.precision == 3) ? kSplitBF16 : kSplitFP16; }
+  bool periodic() const { return crit.precision >= 3; }
   // profiling: one event pair per (slot, phase); a slot is an iteration not
   // yet collected (one per iteration when the host synchronises each
   // iteration, one per iteration of the whole run otherwise)
@@ -229,6 +238,8 @@ int refresh(Ctx& c, const std::vector<int>& qs, bool full_set) {
     S.woodbury = jobs[i].woodbury;
     if (full_set) { S.full = outbuf[i]; S.full_valid = true; }
     S.cum_dd = 0;
+    const size_t np = (size_t)jobs[i].npad;
+    SADMM_TRY(launch_split_f64(S.fb[S.cur], S.fhl[S.cur], np * np, c.st));
   }
   return SADMM_OK;
 }
@@ -271,6 +282,7 @@ int downdate(Ctx& c, const std::vector<int>& qs, std::vector<int>* failed) {
     if (c.h_status[q]) { failed->push_back(q); continue; }
     S.cur = dst[q];
     S.cum_dd += etot[q];
+    SADMM_TRY(launch_split_f64(S.fb[S.cur], S.fhl[S.cur], (size_t)n * n, c.st));
   }
   return SADMM_OK;
 }
@@ -314,12 +326,55 @@ int reset_state(Ctx& c) {
   SADMM_CUDA_TRY(cudaMemcpyAsync(c.counts, cnts.data(), cnts.size() * sizeof(int), cudaMemcpyHostToDevice, c.st));
   SADMM_CUDA_TRY(cudaStreamSynchronize(c.st));
   c.k = 0;
+  c.corr_due = true;
+  c.last_corr_k = 0;
   return SADMM_OK;
 }
 
 // One iteration of Eq. 3 (x-update, prox, dual) and Algorithm 1 (device side).
+int launch_split_products_fwd(Ctx& c, const SolverView& sv, bool corr);
+int launch_split_products_adj(Ctx& c, const SolverView& sv, bool corr);
+
 int launch_iteration(Ctx& c, IterScalars* out) {
   const SolverView sv = c.view();
+  if (c.crit.precision > 0) {
+    const bool corr = c.periodic() && (c.corr_due || c.k - c.last_corr_k >= c.crit.correct_every);
+    c.mark(0, true);
+    SADMM_TRY(launch_split_products_fwd(c, sv, corr));
+    c.mark(0, false);
+    std::vector<SpdSet> spd_w, spd_p;
+    for (int q = 0; q < c.Q; ++q) {
+      Sensor& S = c.s[q];
+      if (S.cnt == 0) continue;
+      const float2* F = S.fhl[S.cur];
+      const int ld = round_up(S.n, kTile);
+      if (S.woodbury)
+        spd_w.push_back(SpdSet{F, S.n, ld, reinterpret_cast<const float*>(S.r), reinterpret_cast<float*>(S.w), nullptr, q});
+      else
+        spd_p.push_back(SpdSet{F, S.n, ld, S.g, nullptr, S.J, q});
+    }
+    c.mark(1, true);
+    SADMM_TRY(launch_spd_apply(spd_w.data(), (int)spd_w.size(), false, sv, c.st));
+    c.mark(1, false);
+    c.mark(2, true);
+    SADMM_TRY(launch_split_products_adj(c, sv, corr));
+    c.mark(2, false);
+    c.mark(4, true);
+    SADMM_TRY(launch_spd_apply(spd_p.data(), (int)spd_p.size(), true, sv, c.st));
+    c.mark(4, false);
+    if (corr) { c.corr_due = false; c.last_corr_k = c.k; }
+    c.mark(5, true);
+    SADMM_TRY(launch_residuals(sv, c.crit, c.red, c.ticket, out, c.k + 1, c.st));
+    c.mark(5, false);
+    if (c.crit.elim) {
+      std::vector<int*> Jp(c.Q), Ep(c.Q);
+      for (int q = 0; q < c.Q; ++q) { Jp[q] = c.s[q].J; Ep[q] = c.s[q].E; }
+      c.mark(6, true);
+      SADMM_TRY(launch_ssc(sv, Jp.data(), Ep.data(), c.counts, c.crit.eps_p, c.crit.freeze_mode, out, c.st));
+      c.mark(6, false);
+    }
+    return SADMM_OK;
+  }
   std::vector<ColumnSet> fw;
   std::vector<SpdSet> spd_w, spd_p;
   std::vector<AdjointSet> adj_w, adj_p;
@@ -327,7 +382,7 @@ int launch_iteration(Ctx& c, IterScalars* out) {
     Sensor& S = c.s[q];
     if (S.cnt == 0) continue;
     fw.push_back(ColumnSet{S.A, S.J, S.cnt, q, nullptr, S.yp, S.r});
-    const double* F = S.fb[S.cur];
+    const float2* F = S.fhl[S.cur];
     const int ld = round_up(S.n, kTile);
     if (S.woodbury) {
       spd_w.push_back(SpdSet{F, S.n, ld, reinterpret_cast<const float*>(S.r),
@@ -371,6 +426,65 @@ int launch_iteration(Ctx& c, IterScalars* out) {
   return SADMM_OK;
 }
 
+// Split-precision forward product r = y' - (A_hi + A_lo) v.  Pairs read both
+// planes every iteration; the periodic modes read hi every iteration and
+// refresh base_corr = y' - A_lo v only on correction iterations.
+int launch_split_products_fwd(Ctx& c, const SolverView& sv, bool corr) {
+  std::vector<SplitSet> a, b;
+  for (int q = 0; q < c.Q; ++q) {
+    Sensor& S = c.s[q];
+    if (S.cnt == 0) continue;
+    SplitSet x{};
+    x.hi = S.hi; x.lo = S.lo; x.idx = S.J; x.n = S.cnt; x.q = q;
+    if (!c.periodic()) {
+      x.base = S.yp; x.out = S.r;
+      a.push_back(x);
+    } else {
+      if (corr) {
+        SplitSet l = x;
+        l.base = S.yp; l.out = S.base_corr;
+        b.push_back(l);
+      }
+      x.base = S.base_corr; x.out = S.r;
+      a.push_back(x);
+    }
+  }
+  const int kind = c.split_kind();
+  if (!b.empty())
+    SADMM_TRY(launch_split_forward(b.data(), (int)b.size(), c.KM, kind, 2, kVAdmm, sv, c.partial, c.partial_cap, c.st));
+  return launch_split_forward(a.data(), (int)a.size(), c.KM, kind, c.periodic() ? 1 : 3, kVAdmm, sv,
+                              c.partial, c.partial_cap, c.st);
+}
+
+// Split-precision adjoint g = Re((A_hi + A_lo)^H w): with the x-update epilogue
+// for Woodbury-form sensors, into S.g for primal-form sensors.
+int launch_split_products_adj(Ctx& c, const SolverView& sv, bool corr) {
+  std::vector<SplitSet> lo_pass, upd, gout;
+  for (int q = 0; q < c.Q; ++q) {
+    Sensor& S = c.s[q];
+    if (S.cnt == 0) continue;
+    SplitSet x{};
+    x.hi = S.hi; x.lo = S.lo; x.idx = S.J; x.n = S.cnt; x.q = q;
+    x.w = S.woodbury ? S.w : S.r;
+    if (c.periodic()) {
+      if (corr) {
+        SplitSet l = x;
+        l.gcorr_out = S.gcorr;
+        lo_pass.push_back(l);
+      }
+      x.gcorr_in = S.gcorr;
+    }
+    if (S.woodbury) upd.push_back(x);
+    else { x.g = S.g; gout.push_back(x); }
+  }
+  const int kind = c.split_kind();
+  const int planes = c.periodic() ? 1 : 3;
+  if (!lo_pass.empty())
+    SADMM_TRY(launch_split_adjoint(lo_pass.data(), (int)lo_pass.size(), c.KM, kind, 2, false, sv, c.st));
+  SADMM_TRY(launch_split_adjoint(upd.data(), (int)upd.size(), c.KM, kind, planes, true, sv, c.st));
+  return launch_split_adjoint(gout.data(), (int)gout.size(), c.KM, kind, planes, false, sv, c.st);
+}
+
 // After an SSC pass that shrank some sets: fold frozen pixels into y' (or
 // re-average in zero mode) and refresh the factors of those sensors.
 int apply_changes(Ctx& c, const std::vector<int>& changed) {
@@ -396,6 +510,7 @@ int apply_changes(Ctx& c, const std::vector<int>& changed) {
     else full.push_back(q);
   }
   SADMM_TRY(downdate(c, dd, &full));
+  c.corr_due = true;        // y' and the active sets changed: refresh the lo-plane products
   return refresh(c, full, false);
 }
 
@@ -403,7 +518,8 @@ double iter_bytes(const Ctx& c) {
   double b = 0.0;
   for (const Sensor& S : c.s) {
     if (S.cnt == 0) continue;
-    b += 2.0 * c.KM * (double)S.cnt * sizeof(float2) + (double)S.n * S.n * sizeof(double);
+    const double per_entry = c.crit.precision == 0 ? 8.0 : (c.periodic() ? 4.0 : 8.0);
+    b += 2.0 * c.KM * (double)S.cnt * per_entry + (double)S.n * S.n * sizeof(double);
   }
   return b;
 }
@@ -539,6 +655,8 @@ void sadmm_default_criterion(sadmm_criterion* c) {
   c->elim = 1;
   c->freeze_mode = 0;
   c->stop = 0;
+  c->precision = 0;
+  c->correct_every = 4;
 }
 
 int sadmm_set_allocator(sadmm_alloc_fn alloc, sadmm_free_fn release, void* user) {
@@ -563,7 +681,8 @@ int sadmm_create(int Q, int M, int K, int N, double rho, double lambda, const sa
   if (Q < 1 || Q > kMaxSets || M < 1 || K < 1 || N < 1 || KM % 32 != 0 || KM > 16384 ||
       !(rho > 0.0) || !(lambda >= 0.0) || !(c.mu > 0.0) || c.Kp < 1 || c.Kp > 64 ||
       !(c.eps_p >= 0.0) || c.elim < 0 || c.elim > 1 || c.freeze_mode < 0 || c.freeze_mode > 1 ||
-      c.stop < 0 || c.stop > 1 || !std::isfinite(rho) || !std::isfinite(lambda)) {
+      c.stop < 0 || c.stop > 1 || !std::isfinite(rho) || !std::isfinite(lambda) ||
+      c.precision < 0 || c.precision > 4 || c.correct_every < 1) {
     set_error("sadmm_create: invalid sizes or parameters (Q=%d M=%d K=%d N=%d rho=%g lambda=%g)", Q, M,
               K, N, rho, lambda);
     return SADMM_EINVAL;
@@ -590,8 +709,15 @@ int sadmm_create(int Q, int M, int K, int N, double rho, double lambda, const sa
     S.J = (int*)A((size_t)N * sizeof(int));
     S.E = (int*)A((size_t)N * sizeof(int));
     for (int b = 0; b < 3; ++b) S.fb[b] = (double*)A(fbytes);
+    for (int b = 0; b < 3; ++b) S.fhl[b] = (float2*)A(fbytes);
     S.dinv = (double*)A((size_t)ctx->npad_max * kTile * sizeof(double));
     S.dd = (double*)A(downdate_scratch_doubles(2 * (int)KM) * sizeof(double));
+    if (c.precision > 0) {
+      S.hi = (uint16_t*)A((size_t)N * KM * 2 * sizeof(uint16_t));
+      S.lo = (uint16_t*)A((size_t)N * KM * 2 * sizeof(uint16_t));
+      S.base_corr = (float2*)A(KM * sizeof(float2));
+      S.gcorr = (float*)A((size_t)N * sizeof(float));
+    }
   }
   const size_t QN = (size_t)Q * N;
   ctx->x = (float*)A(QN * sizeof(float));
@@ -602,8 +728,10 @@ int sadmm_create(int Q, int M, int K, int N, double rho, double lambda, const sa
   ctx->ring = (float*)A((size_t)c.Kp * QN * sizeof(float));
   ctx->iota = (int*)A(N * sizeof(int));
   ctx->partial_cap = 0;
-  for (int ns = 1; ns <= Q; ++ns)   // any subset of sensors may be launched together
+  for (int ns = 1; ns <= Q; ++ns) {  // any subset of sensors may be launched together
     ctx->partial_cap = std::max(ctx->partial_cap, forward_partial_bytes(ns, (int)KM, N));
+    if (c.precision > 0) ctx->partial_cap = std::max(ctx->partial_cap, split_partial_bytes(ns, (int)KM, N));
+  }
   ctx->partial = (float2*)A(ctx->partial_cap);
   ctx->red = (double*)A((size_t)residual_blocks(N) * 8 * sizeof(double));
   ctx->ticket = (unsigned int*)A(sizeof(unsigned int));
@@ -645,6 +773,9 @@ int sadmm_set_operator(sadmm_t ctx, int q, const float* A_q) {
   if (q < 0 || q >= ctx->Q || !A_q) { set_error("sadmm_set_operator: bad sensor or pointer"); return SADMM_EINVAL; }
   sadmm::Sensor& S = ctx->s[q];
   SADMM_CUDA_TRY(cudaMemcpyAsync(S.A, A_q, (size_t)ctx->N * ctx->KM * sizeof(float2), cudaMemcpyDefault, ctx->st));
+  if (ctx->crit.precision > 0)
+    SADMM_TRY(sadmm::launch_split_convert(reinterpret_cast<const float*>(S.A), (size_t)ctx->N * ctx->KM * 2,
+                                          ctx->split_kind(), S.hi, S.lo, ctx->st));
   SADMM_CUDA_TRY(cudaStreamSynchronize(ctx->st));
   S.op_set = true;
   S.full_valid = false;
@@ -809,6 +940,7 @@ int sadmm_set_state(sadmm_t ctx, const void* buf, size_t bytes) {
   SADMM_TRY(h2d(ctx->counts, counts.data(), counts.size() * 4));
   SADMM_CUDA_TRY(cudaStreamSynchronize(ctx->st));
   ctx->k = h.k;
+  ctx->corr_due = true;
   return refresh(*ctx, changed, false);
 }
 
@@ -959,16 +1091,71 @@ int sadmm_factor_downdate(const float* A, int KM, const int* E, int e, double mu
   return SADMM_OK;
 }
 
+int sadmm_split_operator(const float* A, size_t n_complex, int kind, void* hi, void* lo, void* stream) {
+  using namespace sadmm;
+  if (!A || !hi || !lo || (kind != kSplitBF16 && kind != kSplitFP16)) {
+    set_error("sadmm_split_operator: bad arguments");
+    return SADMM_EINVAL;
+  }
+  return launch_split_convert(A, 2 * n_complex, kind, (uint16_t*)hi, (uint16_t*)lo, (cudaStream_t)stream);
+}
+
+int sadmm_forward_split(const void* hi, const void* lo, int kind, int planes, int KM, int N, const int* idx,
+                        int nidx, const float* v, const float* base, float* r, void* stream) {
+  using namespace sadmm;
+  if (!r || KM <= 0 || KM % 4 != 0 || N <= 0 || nidx < 0 || (nidx > 0 && (!idx || !v)) ||
+      planes < 1 || planes > 3 || ((planes & 1) && !hi) || ((planes & 2) && !lo)) {
+    set_error("sadmm_forward_split: bad arguments");
+    return SADMM_EINVAL;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  SplitSet cs{};
+  cs.hi = hi; cs.lo = lo; cs.idx = idx; cs.n = nidx; cs.vexp = v; cs.base = (const float2*)base;
+  cs.out = (float2*)r;
+  SolverView sv{};
+  const size_t cap = split_partial_bytes(1, KM, std::max(nidx, 1));
+  void* part = nullptr;
+  SADMM_CUDA_TRY(cudaMallocAsync(&part, cap, st));
+  int rc = launch_split_forward(&cs, 1, KM, kind, planes, kVExplicit, sv, (float2*)part, cap, st);
+  cudaError_t e = cudaFreeAsync(part, st);
+  if (rc != SADMM_OK) return rc;
+  SADMM_CUDA_TRY(e);
+  return SADMM_OK;
+}
+
+int sadmm_adjoint_split(const void* hi, const void* lo, int kind, int planes, int KM, int N, const int* idx,
+                        int nidx, const float* w, float* g, void* stream) {
+  using namespace sadmm;
+  if (!w || KM <= 0 || KM % 4 != 0 || KM > 16384 || N <= 0 || nidx < 0 || (nidx > 0 && (!idx || !g)) ||
+      planes < 1 || planes > 3 || ((planes & 1) && !hi) || ((planes & 2) && !lo)) {
+    set_error("sadmm_adjoint_split: bad arguments");
+    return SADMM_EINVAL;
+  }
+  SplitSet as{};
+  as.hi = hi; as.lo = lo; as.idx = idx; as.n = nidx; as.w = (const float2*)w; as.g = g;
+  SolverView sv{};
+  return launch_split_adjoint(&as, 1, KM, kind, planes, false, sv, (cudaStream_t)stream);
+}
+
 int sadmm_spd_apply(const double* F, int n, int ldf, const float* u, float* out, void* stream) {
   using namespace sadmm;
-  if (!F || !u || !out || n <= 0 || n > 24576 || ldf < round_up(n, 2) || ldf % 2 != 0 ||
-      ((uintptr_t)F & 15) != 0) {
+  if (!F || !u || !out || n <= 0 || n > 49152 || ldf < round_up(n, 2) || ldf % 2 != 0) {
     set_error("sadmm_spd_apply: bad arguments");
     return SADMM_EINVAL;
   }
-  SpdSet s{F, n, ldf, u, out, nullptr, 0};
-  SolverView sv{};
-  return launch_spd_apply(&s, 1, false, sv, (cudaStream_t)stream);
+  cudaStream_t st = (cudaStream_t)stream;
+  void* Fhl = nullptr;
+  SADMM_CUDA_TRY(cudaMallocAsync(&Fhl, (size_t)n * ldf * sizeof(float2), st));
+  int rc = launch_split_f64(F, (float2*)Fhl, (size_t)n * ldf, st);
+  if (rc == SADMM_OK) {
+    SpdSet s{(const float2*)Fhl, n, ldf, u, out, nullptr, 0};
+    SolverView sv{};
+    rc = launch_spd_apply(&s, 1, false, sv, st);
+  }
+  cudaError_t e = cudaFreeAsync(Fhl, st);
+  if (rc != SADMM_OK) return rc;
+  SADMM_CUDA_TRY(e);
+  return SADMM_OK;
 }
 
 }  // extern "C"

@@ -107,7 +107,7 @@ int launch_adjoint(const AdjointSet* sets, int nsets, int KM, bool update, const
                    cudaStream_t st);
 
 struct SpdSet {
-  const double* F;   // symmetric FP64 factor, row-major
+  const float2* F;   // factor as double-float pairs (hi, lo), row-major
   int n, ldf;
   const float* u;    // n floats
   float* out;        // n floats (plain) or unused (update)
@@ -116,6 +116,8 @@ struct SpdSet {
 };
 int launch_spd_apply(const SpdSet* sets, int nsets, bool update, const SolverView& sv,
                      cudaStream_t st);
+// (hi, lo) = (fl32(x), fl32(x - hi)) for n doubles.
+int launch_split_f64(const double* in, float2* out, size_t n, cudaStream_t st);
 
 int launch_residuals(const SolverView& sv, const sadmm_criterion& c, double* partials,
                      unsigned int* ticket, IterScalars* out, int k_after, cudaStream_t st);
@@ -128,6 +130,32 @@ int launch_ssc(const SolverView& sv, int* const* J, int* const* E, int* counts, 
                int freeze_mode, const IterScalars* sc, cudaStream_t st);
 int launch_recompute_xbar(const SolverView& sv, cudaStream_t st);
 int launch_scale(const float* in, float a, float* out, int n, cudaStream_t st);
+
+// ---- split-precision operator planes (split.cu) ----
+constexpr int kSplitBF16 = 1;
+constexpr int kSplitFP16 = 2;
+struct SplitSet {
+  const void* hi;            // 16-bit (re, im) plane, pixel-major
+  const void* lo;            // 16-bit residual plane
+  const int* idx;            // column (pixel) list
+  int n;                     // listed columns
+  int q;                     // sensor (row of x and the ring)
+  const float* vexp;         // forward, kVExplicit: v by pixel
+  const float2* base;        // forward: out = base - product (null: 0)
+  float2* out;               // forward: base - product (may be null)
+  float2* out2;              // forward: the product itself (may be null)
+  const float2* w;           // adjoint input (KM complex)
+  float* g;                  // adjoint output in list order (+ gcorr_in when set)
+  const float* gcorr_in;     // per-pixel correction added to the adjoint
+  float* gcorr_out;          // adjoint: per-pixel store of the product
+};
+int launch_split_forward(const SplitSet* sets, int nsets, int KM, int kind, int planes, VMode mode,
+                         const SolverView& sv, float2* partial, size_t partial_cap, cudaStream_t st);
+int launch_split_adjoint(const SplitSet* sets, int nsets, int KM, int kind, int planes, bool update,
+                         const SolverView& sv, cudaStream_t st);
+int launch_split_convert(const float* A, size_t nfloats, int kind, uint16_t* hi, uint16_t* lo,
+                         cudaStream_t st);
+size_t split_partial_bytes(int nsets, int KM, int max_cols);
 
 // FP64 factor: F <- (rho I + mu G)^{-1} for the Gram of the listed columns.
 struct FactorJob {

@@ -150,8 +150,9 @@ def test_spd_apply_matches_fp64(B, n, ld):
     out = out.cpu().numpy().astype(np.float64)
     ref = F[:n, :n] @ u.astype(np.float64)
     mag = np.abs(F[:n, :n]) @ np.abs(u.astype(np.float64))
-    # FP64 sums of exact products, rounded once to FP32
-    assert np.all(np.abs(out - ref) <= U32 * np.abs(ref) + (n + 2) * 2.0 ** -53 * mag)
+    # exact products summed as FP32 pairs (about 48 bits), rounded once to FP32;
+    # the pair split of F itself costs 2^-48 relative per element
+    assert np.all(np.abs(out - ref) <= U32 * np.abs(ref) + (2 * n + 8) * 2.0 ** -47 * mag)
 
 
 @pytest.mark.parametrize("KM,N,e", [(32, 300, 1), (32, 300, 7), (128, 700, 40), (256, 1024, 3)])
