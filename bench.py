@@ -48,6 +48,8 @@ def parse():
                     help="keep only the first S sensors (smaller case for profiler captures)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the 16-scene batched measurement (Q=8, KM=2048, N=96x96)")
     return ap.parse_args()
 
 
@@ -163,6 +165,51 @@ def cpu_baseline_sample(scene, lam, iters=4):
                   f"timed after its factor; rate scaled by 1/{Q}",
         "factor_s": round(t1 - t0, 3),
     }
+
+
+def batched_measure(args, dev, stream, rank):
+    """16 scenes sharing one geometry (Q=8, M=8, K=256, N=96x96), iterated together;
+    scene-iterations per second and the operator-GEMM roofline."""
+    import torch
+    import scenegen
+    from scenegen import radar
+    from paper_2307_08606_gb300 import binding
+    g = scenegen.Geometry(Q=8, M=8, K=256, nx=96, cell=0.05, radius=10.0, fc=77e9, bw=1e9)
+    A = [radar.operator(g, q) for q in range(g.Q)]
+    At = [torch.from_numpy(a).to(dev) for a in A]
+    ys, lams = [], []
+    for s in range(16):
+        x = radar.cluster_targets(g, 1000 * (rank + 1) + s, 5 + (s * 7) % 56, p_vis=0.5 + 0.025 * s)
+        y = radar.measure(A, x, 10.0 + s, 1000 * (rank + 1) + s)
+        ys.append(np.stack(y))
+        lams.append(0.05 * scenegen.lambda_max(A, y))
+    Y = torch.from_numpy(np.stack(ys)).to(dev)
+    bs = binding.BatchSolver(g.Q, g.M, g.K, g.N, 1.0, lams, stream=stream.cuda_stream)
+    for q in range(g.Q):
+        bs.set_operator(q, At[q])
+    out = torch.empty((16, g.N), dtype=torch.float32, device=dev)
+    iters = 100
+    for _ in range(2):
+        bs.solve(Y, iters, out=out)
+    torch.cuda.synchronize()
+    n0 = binding.launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    reps = 3
+    for _ in range(reps):
+        bs.solve(Y, iters, out=out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    launches = binding.launch_count() - n0
+    bs.close()
+    scene_its = 16 * iters * reps / (ms / 1e3)
+    op_bytes = 2.0 * g.Q * g.KM * g.N * 8.0            # forward + adjoint, read once for 16 scenes
+    return {"metric": "batched scene-iterations/s", "value": scene_its, "unit": "scene-iter/s",
+            "workload": "16 scenes sharing Q=8 M=8 K=256 (KM=2048) N=96x96; plain SADMM, 100 iterations per solve",
+            "ms_per_iteration": ms / (iters * reps), "operator_bytes_per_iteration": op_bytes,
+            "operator_GBps_effective": op_bytes / (ms / (iters * reps) / 1e3) / 1e9,
+            "gpu_launches": int(launches)}
 
 
 def make_scene(name, seed, sensors=0):
@@ -333,6 +380,8 @@ def main():
         "gpu_launches": int(launches),
         "clocks": clk.summary(),
     }
+    if not args.no_batched:
+        line["batched"] = batched_measure(args, dev, stream, rank)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
             line["cpu_baseline"] = cpu_baseline_sample(sc, lam)

@@ -181,6 +181,28 @@ const char* sadmm_strerror(int status);
 const char* sadmm_last_error(void);
 
 /* ------------------------------------------------------------------------
+ * Batched form: S = 16 scenes sharing one geometry (the operators A_q, hence
+ * the factors) iterate together; the forward and adjoint products become
+ * GEMMs with 16 right-hand sides, so each operator byte read serves 16
+ * scenes.  Plain SADMM (Eq. 3 without pixel elimination: every scene keeps
+ * the full active set and the shared full-set factor), fixed iteration
+ * count, one captured CUDA graph replayed per iteration.
+ * ---------------------------------------------------------------------- */
+typedef struct sadmm_batch_ctx* sadmm_batch_t;
+
+/* S must be 16; lambda: S per-scene l1 weights; criterion as for
+ * sadmm_create (elim and precision are ignored). */
+int sadmm_batch_create(int Q, int M, int K, int N, int S, double rho, const double* lambda,
+                       const sadmm_criterion* crit, sadmm_batch_t* out);
+int sadmm_batch_set_stream(sadmm_batch_t b, void* stream);
+int sadmm_batch_set_operator(sadmm_batch_t b, int q, const float* A_q);
+/* y: S x Q x KM complex64 (scene-major, host or device); x_out: S x N floats
+ * (x_G of each scene, host or device, may be NULL). */
+int sadmm_batch_solve(sadmm_batch_t b, const float* y, float* x_out, int iters, sadmm_stats* st);
+int sadmm_batch_get_xq(sadmm_batch_t b, int scene, int q, float* out);
+void sadmm_batch_destroy(sadmm_batch_t b);
+
+/* ------------------------------------------------------------------------
  * Kernel-level entry points on DEVICE pointers (used by parity tests and for
  * composing other pipelines).  All work is on `stream`; none synchronises.
  * ---------------------------------------------------------------------- */

@@ -76,6 +76,13 @@ _SIGS = {
                                C.c_int, C.POINTER(C.c_int), _P]),
     "sadmm_spd_apply": (C.c_int, [_P, C.c_int, C.c_int, _P, _P, _P]),
     "sadmm_factor_downdate": (C.c_int, [_P, C.c_int, _P, C.c_int, C.c_double, _P, _P]),
+    "sadmm_batch_create": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double,
+                                     C.POINTER(C.c_double), C.POINTER(Criterion), C.POINTER(_P)]),
+    "sadmm_batch_set_stream": (C.c_int, [_P, _P]),
+    "sadmm_batch_set_operator": (C.c_int, [_P, C.c_int, _P]),
+    "sadmm_batch_solve": (C.c_int, [_P, _P, _P, C.c_int, C.POINTER(Stats)]),
+    "sadmm_batch_get_xq": (C.c_int, [_P, C.c_int, C.c_int, _P]),
+    "sadmm_batch_destroy": (None, [_P]),
     "sadmm_split_operator": (C.c_int, [_P, C.c_size_t, C.c_int, _P, _P, _P]),
     "sadmm_forward_split": (C.c_int, [_P, _P, C.c_int, C.c_int, C.c_int, C.c_int, _P, C.c_int, _P, _P,
                                       _P, _P]),
@@ -260,6 +267,52 @@ class Solver:
     def set_state(self, buf):
         buf = np.ascontiguousarray(buf, dtype=np.uint8)
         check(self.lib.sadmm_set_state(self.h, _ptr(buf), buf.size))
+
+
+class BatchSolver:
+    """16 scenes sharing one geometry, iterated together (sadmm_batch_*)."""
+    S = 16
+
+    def __init__(self, Q, M, K, N, rho, lams, stream=None, **criterion):
+        self.lib = load()
+        self.Q, self.M, self.K, self.N, self.KM = Q, M, K, N, K * M
+        lam = (C.c_double * self.S)(*[float(v) for v in lams])
+        crit = default_criterion(**criterion)
+        h = C.c_void_p()
+        check(self.lib.sadmm_batch_create(Q, M, K, N, self.S, float(rho), lam, C.byref(crit), C.byref(h)))
+        self.h = h
+        if stream is not None:
+            check(self.lib.sadmm_batch_set_stream(self.h, C.c_void_p(stream)))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.sadmm_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_operator(self, q, A):
+        A = _as_c64(A)
+        assert tuple(A.shape) == (self.N, self.KM)
+        check(self.lib.sadmm_batch_set_operator(self.h, q, _ptr(A)))
+
+    def solve(self, y, iters, out=None):
+        """y: (S, Q, KM) complex64 (numpy or torch); returns (x_G (S, N), stats)."""
+        y = _as_c64(y)
+        if out is None:
+            out = np.empty((self.S, self.N), dtype=np.float32)
+        st = Stats()
+        check(self.lib.sadmm_batch_solve(self.h, _ptr(y), _ptr(out), int(iters), C.byref(st)))
+        return out, st.as_dict()
+
+    def xq(self, scene, q):
+        out = np.empty(self.N, dtype=np.float32)
+        check(self.lib.sadmm_batch_get_xq(self.h, scene, q, _ptr(out)))
+        return out
 
 
 # ------------------------------------------------------ state blob conversion

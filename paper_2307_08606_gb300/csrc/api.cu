@@ -643,6 +643,25 @@ using sadmm::set_error;
 
 struct sadmm_ctx : Ctx {};
 
+namespace sadmm {
+// Operator and current factor of sensor q (for the batched form, which keeps
+// every pixel active and so uses the full-set factor).
+int single_export(sadmm_t h, int q, const float2** A, const float2** Fhl, int* n, int* ld, int* woodbury) {
+  if (!h || q < 0 || q >= h->Q) return SADMM_EINVAL;
+  const sadmm::Sensor& S = h->s[q];
+  if (!S.full_valid) { set_error("factor of sensor %d not prepared", q); return SADMM_ENOTREADY; }
+  *A = S.A;
+  *Fhl = S.fhl[S.full];
+  int nn, wb;
+  factor_dims(*h, h->N, &nn, &wb);
+  *n = nn;
+  *ld = round_up(nn, kTile);
+  *woodbury = wb;
+  return SADMM_OK;
+}
+}  // namespace sadmm
+
+
 extern "C" {
 
 void sadmm_default_criterion(sadmm_criterion* c) {

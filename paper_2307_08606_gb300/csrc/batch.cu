@@ -1,0 +1,649 @@
+// Batched sharing ADMM: S scenes that share one geometry (the operators A_q
+// and therefore the factors) iterate together, so every operator byte read
+// from HBM serves S scenes.  The per-iteration products become GEMMs with S
+// right-hand sides (Eq. 3, x_q-update, for all scenes at once):
+//   R_q (KM x S) = Y'_q - A_q V_q          V_q[j][s] = x - x_bar + z_bar - s  (scene s)
+//   U_q (n x S)  = F_q R_q                 (factor, double-float pairs)
+//   X_q[j][s]    = V_q[j][s] + mu Re(a_j^H U_q[:, s])
+// followed by the per-scene prox / dual / residual step (Eq. 3, x_G- and dual
+// updates).  Pixel elimination is not used in this form (every scene keeps
+// the full active set, so the shared factor stays valid).
+//
+// Layout: scene index fastest everywhere: X_q [pixel][scene], x_bar / z_bar /
+// s [pixel][scene], Y'_q, R_q, U_q [row][scene] (complex as float2).
+#include "common.cuh"
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+namespace sadmm {
+
+namespace {
+
+constexpr int kBS = 16;              // scenes per batch (fixed tile width)
+
+// ------------------------------------------------------------------ forward
+// Output tile: 128 complex rows x 16 scenes; thread tile 4 rows x 4 scenes
+// (16 complex accumulators).  K loop over pixel slabs of 16 staged in shared
+// memory (operator slab 128 x 16 complex, V slab 16 x 16).
+constexpr int kBfRows = 128;
+constexpr int kBfSlab = 16;
+constexpr int kBfThreads = 128;
+
+struct BatchDev {
+  int Q, N, KM, S;
+  float mu, rho;
+  const float* lam_over_rho;     // S
+  float* X;                      // Q x N x S
+  float* dX;                     // Q x N x S  (x^{k+1} - x^k)
+  float* xbar;                   // N x S
+  float* zbar;                   // N x S
+  float* sd;                     // N x S
+};
+
+__global__ void __launch_bounds__(kBfThreads)
+bfwd_partial_kernel(const float2* const* __restrict__ Aq, BatchDev b, int chunks, int cols_per_chunk,
+                    float2* __restrict__ partial) {
+  const int q = blockIdx.z, c = blockIdx.y;
+  const int r0 = blockIdx.x * kBfRows;
+  const int KM = b.KM, N = b.N;
+  const int p0 = c * cols_per_chunk, p1 = min(N, p0 + cols_per_chunk);
+  __shared__ float2 sA[kBfSlab][kBfRows];
+  __shared__ float sV[kBfSlab][kBS];
+  const int tid = threadIdx.x;
+  const int tr = tid / 4, ts = tid % 4;            // 32 row groups x 4 scene groups
+  float2 acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int s = 0; s < 4; ++s) acc[i][s] = make_float2(0.f, 0.f);
+  const float2* A = Aq[q];
+  const float* X = b.X + (size_t)q * N * kBS;
+  for (int j0 = p0; j0 < p1; j0 += kBfSlab) {
+    __syncthreads();
+    for (int e = tid; e < kBfSlab * kBfRows; e += kBfThreads) {
+      const int jj = e / kBfRows, rr = e % kBfRows;
+      const int j = j0 + jj, r = r0 + rr;
+      sA[jj][rr] = (j < p1 && r < KM) ? A[(size_t)j * KM + r] : make_float2(0.f, 0.f);
+    }
+    for (int e = tid; e < kBfSlab * kBS; e += kBfThreads) {
+      const int jj = e / kBS, s = e % kBS, j = j0 + jj;
+      float v = 0.f;
+      if (j < p1) {
+        const size_t o = (size_t)j * kBS + s;
+        v = X[o] - b.xbar[o] + b.zbar[o] - b.sd[o];
+      }
+      sV[jj][s] = v;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int jj = 0; jj < kBfSlab; ++jj) {
+      float2 a[4];
+      float v[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = sA[jj][tr + 32 * i];
+#pragma unroll
+      for (int s = 0; s < 4; ++s) v[s] = sV[jj][ts + 4 * s];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+          acc[i][s].x = fmaf(a[i].x, v[s], acc[i][s].x);
+          acc[i][s].y = fmaf(a[i].y, v[s], acc[i][s].y);
+        }
+    }
+  }
+  float2* out = partial + ((size_t)q * chunks + c) * KM * kBS;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int r = r0 + tr + 32 * i;
+    if (r >= KM) continue;
+#pragma unroll
+    for (int s = 0; s < 4; ++s) out[(size_t)r * kBS + ts + 4 * s] = acc[i][s];
+  }
+}
+
+// R_q[r][s] = Y'_q[r][s] - sum_c partial[q][c][r][s]
+__global__ void bfwd_reduce_kernel(const float2* __restrict__ partial, const float2* const* __restrict__ Yq,
+                                   float2* const* __restrict__ Rq, int KM, int chunks) {
+  const int q = blockIdx.y;
+  const size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (e >= (size_t)KM * kBS) return;
+  const float2* p = partial + (size_t)q * chunks * KM * kBS + e;
+  float2 acc = make_float2(0.f, 0.f);
+  for (int c = 0; c < chunks; ++c) {
+    const float2 t = p[(size_t)c * KM * kBS];
+    acc.x += t.x;
+    acc.y += t.y;
+  }
+  const float2 y = Yq[q][e];
+  Rq[q][e] = make_float2(y.x - acc.x, y.y - acc.y);
+}
+
+// ------------------------------------------------------------ factor apply
+// U[i][s] = sum_j F[i][j] u_s[j] for the 16 scenes, F as double-float pairs,
+// exact products and two-sum accumulation (as the single-scene apply).  One
+// warp per row of F; lane l takes the columns j = l (mod 32) and keeps a
+// double-float accumulator for every scene; lanes combine in FP64.
+// u (and U in mode 0) use the interleaved real index of a complex [row][scene]
+// array: real row j = 2m + c lives at float (m * 16 + s) * 2 + c.
+__device__ __forceinline__ void df2(float& sh, float& sl, float wh, float wl, float u) {
+  const float p = wh * u;
+  float e = fmaf(wh, u, -p);
+  e = fmaf(wl, u, e);
+  const float t = sh + p;
+  const float bp = t - sh;
+  sl += ((sh - (t - bp)) + (p - bp)) + e;
+  sh = t;
+}
+
+constexpr int kBsWarps = 8;
+constexpr int kBsChunk = 256;        // rows of u staged per pass
+
+__device__ __forceinline__ size_t cidx(int j, int s) { return ((size_t)(j >> 1) * kBS + s) * 2 + (j & 1); }
+
+// mode 0 (Woodbury): u from R (complex [row][scene]), U written as complex [row][scene]
+// mode 1 (primal):   u from G ([pixel][scene]); x-update X = V + mu U
+__global__ void __launch_bounds__(kBsWarps * 32)
+bspd_kernel(const float2* const* __restrict__ Fq, const float* const* __restrict__ uq, float* const* __restrict__ outq,
+            int n, int ld, int mode, BatchDev b) {
+  extern __shared__ float s_u[];                   // [kBsChunk][kBS]
+  const int q = blockIdx.y;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i = blockIdx.x * kBsWarps + warp;      // one row per warp
+  const float2* F = Fq[q];
+  const float* u = uq[q];
+  float sh[kBS], sl[kBS];
+#pragma unroll
+  for (int s = 0; s < kBS; ++s) { sh[s] = 0.f; sl[s] = 0.f; }
+  for (int j0 = 0; j0 < n; j0 += kBsChunk) {
+    const int nj = min(kBsChunk, n - j0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < kBsChunk * kBS; e += blockDim.x) {
+      const int jj = e / kBS, s = e % kBS;
+      float v = 0.f;
+      if (jj < nj) v = mode == 0 ? u[cidx(j0 + jj, s)] : u[(size_t)(j0 + jj) * kBS + s];
+      s_u[e] = v;
+    }
+    __syncthreads();
+    if (i < n) {
+      const float2* row = F + (size_t)i * ld + j0;
+      for (int jj = lane; jj < nj; jj += 32) {
+        const float2 f = row[jj];
+        const float4* uu = reinterpret_cast<const float4*>(s_u + jj * kBS);
+#pragma unroll
+        for (int s4 = 0; s4 < kBS / 4; ++s4) {
+          const float4 x = uu[s4];
+          df2(sh[4 * s4 + 0], sl[4 * s4 + 0], f.x, f.y, x.x);
+          df2(sh[4 * s4 + 1], sl[4 * s4 + 1], f.x, f.y, x.y);
+          df2(sh[4 * s4 + 2], sl[4 * s4 + 2], f.x, f.y, x.z);
+          df2(sh[4 * s4 + 3], sl[4 * s4 + 3], f.x, f.y, x.w);
+        }
+      }
+    }
+  }
+  if (i >= n) return;
+#pragma unroll
+  for (int s = 0; s < kBS; ++s) {
+    double g = (double)sh[s] + (double)sl[s];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
+    if (lane != s) continue;
+    if (mode == 0) {
+      outq[q][cidx(i, s)] = (float)g;
+    } else {
+      // primal form: row i is pixel i (the full active set, in pixel order)
+      const size_t o = ((size_t)q * b.N + i) * kBS + s;
+      const size_t p = (size_t)i * kBS + s;
+      const float xo = b.X[o];
+      const float v = xo - b.xbar[p] + b.zbar[p] - b.sd[p];
+      const float xn = fmaf(b.mu, (float)g, v);
+      b.dX[o] = xn - xo;
+      b.X[o] = xn;
+    }
+  }
+}
+
+// ------------------------------------------------------------------ adjoint
+// G[j][s] = Re(a_j^H w_s): output tile 128 pixels x 16 scenes, thread tile
+// 4 pixels x 4 scenes; K loop over complex rows in slabs of 16.
+constexpr int kBaPix = 128;
+constexpr int kBaSlab = 16;
+constexpr int kBaThreads = 128;
+
+// mode 0: x-update epilogue (Woodbury form); mode 1: G into gq [pixel][scene]
+__global__ void __launch_bounds__(kBaThreads)
+badj_kernel(const float2* const* __restrict__ Aq, const float2* const* __restrict__ Wq, float* const* __restrict__ gq,
+            int mode, BatchDev b) {
+  const int q = blockIdx.y;
+  const int j0 = blockIdx.x * kBaPix;
+  const int KM = b.KM, N = b.N;
+  __shared__ float2 sA[kBaPix][kBaSlab + 1];
+  __shared__ float2 sW[kBaSlab][kBS];
+  const int tid = threadIdx.x;
+  const int tp = tid / 4, ts = tid % 4;            // 32 pixel groups x 4 scene groups
+  float acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int s = 0; s < 4; ++s) acc[i][s] = 0.f;
+  const float2* A = Aq[q];
+  const float2* W = Wq[q];
+  for (int r0 = 0; r0 < KM; r0 += kBaSlab) {
+    __syncthreads();
+    for (int e = tid; e < kBaPix * kBaSlab; e += kBaThreads) {
+      const int pp = e / kBaSlab, rr = e % kBaSlab;
+      const int j = j0 + pp, r = r0 + rr;
+      sA[pp][rr] = (j < N && r < KM) ? A[(size_t)j * KM + r] : make_float2(0.f, 0.f);
+    }
+    for (int e = tid; e < kBaSlab * kBS; e += kBaThreads) {
+      const int rr = e / kBS, s = e % kBS, r = r0 + rr;
+      sW[rr][s] = r < KM ? W[(size_t)r * kBS + s] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int rr = 0; rr < kBaSlab; ++rr) {
+      float2 a[4], w[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = sA[tp + 32 * i][rr];
+#pragma unroll
+      for (int s = 0; s < 4; ++s) w[s] = sW[rr][ts + 4 * s];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int s = 0; s < 4; ++s) acc[i][s] = fmaf(a[i].x, w[s].x, fmaf(a[i].y, w[s].y, acc[i][s]));
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int j = j0 + tp + 32 * i;
+    if (j >= N) continue;
+#pragma unroll
+    for (int s4 = 0; s4 < 4; ++s4) {
+      const int s = ts + 4 * s4;
+      if (mode == 1) {
+        gq[q][(size_t)j * kBS + s] = acc[i][s4];
+      } else {
+        const size_t o = ((size_t)q * N + j) * kBS + s;
+        const size_t p = (size_t)j * kBS + s;
+        const float xo = b.X[o];
+        const float v = xo - b.xbar[p] + b.zbar[p] - b.sd[p];
+        const float xn = fmaf(b.mu, acc[i][s4], v);
+        b.dX[o] = xn - xo;
+        b.X[o] = xn;
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------- prox / residuals
+// Per (pixel, scene): x_bar, z_bar = soft(x_bar + s, lambda_s / rho), s update,
+// and per-scene FP64 partial sums (same eight sums as the single-scene path).
+constexpr int kBrThreads = 256;   // 16 pixels x 16 scenes
+constexpr int kBrSums = 8;
+
+__global__ void __launch_bounds__(kBrThreads)
+bresid_kernel(BatchDev b, double* __restrict__ partials) {
+  const int s = threadIdx.x % kBS, pl = threadIdx.x / kBS;
+  const int j = blockIdx.x * (kBrThreads / kBS) + pl;
+  double acc[kBrSums];
+#pragma unroll
+  for (int k = 0; k < kBrSums; ++k) acc[k] = 0.0;
+  if (j < b.N) {
+    const size_t p = (size_t)j * kBS + s;
+    float sx = 0.f;
+    for (int q = 0; q < b.Q; ++q) sx += b.X[((size_t)q * b.N + j) * kBS + s];
+    const float xb = sx / (float)b.Q;
+    const float xo = b.xbar[p], zo = b.zbar[p], so = b.sd[p];
+    const float t = xb + so;
+    const float zb = copysignf(fmaxf(fabsf(t) - b.lam_over_rho[s], 0.f), t);
+    const float sn = (so + xb) - zb;
+    const double dxb = (double)xb - xo, dzb = (double)zb - zo, e = (double)xb - zb;
+    acc[0] = e * e;
+    for (int q = 0; q < b.Q; ++q) {
+      const size_t o = ((size_t)q * b.N + j) * kBS + s;
+      const double xq = b.X[o], dx = b.dX[o];
+      const double zq = xq - (double)xb + (double)zb, dz = dx - dxb + dzb;
+      acc[1] += xq * xq;
+      acc[2] += zq * zq;
+      acc[3] += dz * dz;
+      acc[5] += dx * dx;
+    }
+    acc[4] = (double)sn * sn;
+    acc[6] = (double)zb * zb;
+    acc[7] = dzb * dzb;
+    b.xbar[p] = xb;
+    b.zbar[p] = zb;
+    b.sd[p] = sn;
+  }
+  // reduce over the 16 pixels of this block for each scene (fixed order)
+  __shared__ double red[kBrThreads / kBS][kBS][kBrSums];
+#pragma unroll
+  for (int k = 0; k < kBrSums; ++k) red[pl][s][k] = acc[k];
+  __syncthreads();
+  if (pl == 0) {
+    for (int k = 0; k < kBrSums; ++k) {
+      double t = 0.0;
+      for (int r = 0; r < kBrThreads / kBS; ++r) t += red[r][s][k];
+      partials[((size_t)blockIdx.x * kBS + s) * kBrSums + k] = t;
+    }
+  }
+}
+
+__global__ void bresid_final_kernel(const double* __restrict__ partials, int nblk, BatchDev b, double eps_abs,
+                                    double eps_rel, int k_after, IterScalars* __restrict__ out) {
+  const int s = threadIdx.x;
+  if (s >= kBS) return;
+  double tot[kBrSums];
+  for (int k = 0; k < kBrSums; ++k) tot[k] = 0.0;
+  for (int blk = 0; blk < nblk; ++blk)
+    for (int k = 0; k < kBrSums; ++k) tot[k] += partials[((size_t)blk * kBS + s) * kBrSums + k];
+  const double Q = b.Q, QN = (double)b.Q * b.N;
+  IterScalars r;
+  r.r_pri = sqrt(Q) * sqrt(tot[0]);
+  const double xn = sqrt(tot[1]), zn = sqrt(tot[2]);
+  r.eps_pri = sqrt(QN) * eps_abs + eps_rel * fmax(xn, zn);
+  r.d = (double)b.rho * sqrt(tot[3]);
+  r.eps_dual = sqrt(QN) * eps_abs + eps_rel * (double)b.rho * sqrt(Q) * sqrt(tot[4]);
+  r.relchange = xn > 0.0 ? sqrt(tot[5]) / xn : INFINITY;
+  r.xg_norm = Q * sqrt(tot[6]);
+  r.dxg_norm = Q * sqrt(tot[7]);
+  r.xnorm = xn;
+  r.k = k_after;
+  r.gate = 0;
+  r.changed = 0;
+  double chk = 0.0;
+  for (int k = 0; k < kBrSums; ++k) chk += tot[k];
+  r.nonfinite = isfinite(chk) ? 0 : 1;
+  out[s] = r;
+}
+
+__global__ void bscale_kernel(const float* __restrict__ zbar, float Q, float* __restrict__ out, int N) {
+  // out[s][j] = Q z_bar[j][s] (scene-major output)
+  const size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (e >= (size_t)N * kBS) return;
+  const int j = (int)(e / kBS), s = (int)(e % kBS);
+  out[(size_t)s * N + j] = Q * zbar[e];
+}
+
+// interleave per-scene measurement vectors y[s][q] (KM complex) -> Y'_q [row][scene]
+__global__ void bload_y_kernel(const float2* __restrict__ y, float2* const* __restrict__ Yq, int Q, int KM) {
+  const int q = blockIdx.y;
+  const size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (e >= (size_t)KM * kBS) return;
+  const int r = (int)(e / kBS), s = (int)(e % kBS);
+  Yq[q][e] = y[((size_t)s * Q + q) * KM + r];
+}
+
+// X_q [pixel][scene] -> out [pixel] for one scene
+__global__ void bget_x_kernel(const float* __restrict__ X, int N, int scene, float* __restrict__ out) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < N) out[j] = X[(size_t)j * kBS + scene];
+}
+
+int batch_chunks(int Q, int KM, int N) {
+  const int tiles = div_up(KM, kBfRows);
+  const int want = div_up(152 * 8, (long long)tiles * Q);
+  return std::max(1, std::min(want, div_up(N, 256)));
+}
+
+}  // namespace
+
+struct BatchCtx {
+  int Q = 0, M = 0, K = 0, N = 0, KM = 0, S = kBS;
+  double rho = 1.0, mu = 1.0;
+  sadmm_criterion crit{};
+  cudaStream_t st = nullptr;
+  sadmm_t single = nullptr;        // owns the operators and the FP64 factors
+  std::vector<void*> owned;
+  float *X = nullptr, *dX = nullptr, *xbar = nullptr, *zbar = nullptr, *sd = nullptr, *lor = nullptr;
+  float2 **dA = nullptr, **dY = nullptr, **dR = nullptr, **dF = nullptr;
+  float **dU = nullptr, **dG = nullptr;
+  float2* partial = nullptr;
+  double* rpart = nullptr;
+  IterScalars* scal = nullptr;
+  float2* ybuf = nullptr;
+  float* xout = nullptr;
+  int chunks = 1, n = 0, ld = 0, woodbury = 1;
+  cudaGraphExec_t graph = nullptr;
+  bool graph_valid = false;
+  int kernels_per_iter = 0;
+  int k = 0;
+
+  void* dalloc(size_t bytes) {
+    void* p = nullptr;
+    if (cudaMalloc(&p, bytes ? bytes : 16) != cudaSuccess) return nullptr;
+    owned.push_back(p);
+    return p;
+  }
+  BatchDev view() const {
+    return BatchDev{Q, N, KM, S, (float)mu, (float)rho, lor, X, dX, xbar, zbar, sd};
+  }
+};
+
+// Accessors implemented in api.cu (the batch form reuses a single-scene
+// context for operator storage and the FP64 factor pipeline).
+int single_export(sadmm_t h, int q, const float2** A, const float2** Fhl, int* n, int* ld, int* woodbury);
+
+namespace {
+
+int batch_launch_iteration(BatchCtx& c) {
+  const BatchDev bv = c.view();
+  dim3 gf(div_up(c.KM, kBfRows), c.chunks, c.Q);
+  const int per = div_up(c.N, c.chunks);
+  bfwd_partial_kernel<<<gf, kBfThreads, 0, c.st>>>(c.dA, bv, c.chunks, per, c.partial);
+  SADMM_LAUNCH_CHECK();
+  bfwd_reduce_kernel<<<dim3(div_up((long long)c.KM * kBS, 256), c.Q), 256, 0, c.st>>>(c.partial, c.dY, c.dR, c.KM,
+                                                                                     c.chunks);
+  SADMM_LAUNCH_CHECK();
+  const size_t smem = (size_t)kBsChunk * kBS * sizeof(float);
+  if (c.woodbury) {
+    bspd_kernel<<<dim3(div_up(c.n, kBsWarps), c.Q), kBsWarps * 32, smem, c.st>>>(
+        c.dF, (const float* const*)c.dR, c.dU, c.n, c.ld, 0, bv);
+    SADMM_LAUNCH_CHECK();
+    badj_kernel<<<dim3(div_up(c.N, kBaPix), c.Q), kBaThreads, 0, c.st>>>(c.dA, (const float2* const*)c.dU, c.dG, 0, bv);
+    SADMM_LAUNCH_CHECK();
+  } else {
+    badj_kernel<<<dim3(div_up(c.N, kBaPix), c.Q), kBaThreads, 0, c.st>>>(c.dA, c.dR, c.dG, 1, bv);
+    SADMM_LAUNCH_CHECK();
+    bspd_kernel<<<dim3(div_up(c.n, kBsWarps), c.Q), kBsWarps * 32, smem, c.st>>>(
+        c.dF, (const float* const*)c.dG, nullptr, c.n, c.ld, 1, bv);
+    SADMM_LAUNCH_CHECK();
+  }
+  const int nblk = div_up(c.N, kBrThreads / kBS);
+  bresid_kernel<<<nblk, kBrThreads, 0, c.st>>>(bv, c.rpart);
+  SADMM_LAUNCH_CHECK();
+  bresid_final_kernel<<<1, 32, 0, c.st>>>(c.rpart, nblk, bv, c.crit.eps_abs, c.crit.eps_rel, 0, c.scal);
+  SADMM_LAUNCH_CHECK();
+  return SADMM_OK;
+}
+
+}  // namespace
+}  // namespace sadmm
+
+struct sadmm_batch_ctx : sadmm::BatchCtx {};
+
+extern "C" {
+
+int sadmm_batch_create(int Q, int M, int K, int N, int S, double rho, const double* lambda,
+                       const sadmm_criterion* crit, sadmm_batch_t* out) {
+  using namespace sadmm;
+  if (!out || !lambda || S != kBS) {
+    set_error("sadmm_batch_create: S must be %d and lambda / out non-NULL", kBS);
+    return SADMM_EINVAL;
+  }
+  *out = nullptr;
+  sadmm_criterion c;
+  if (crit) c = *crit; else sadmm_default_criterion(&c);
+  c.elim = 0;
+  c.precision = 0;
+  for (int s = 0; s < S; ++s)
+    if (!(lambda[s] >= 0.0) || !std::isfinite(lambda[s])) { set_error("sadmm_batch_create: bad lambda"); return SADMM_EINVAL; }
+  sadmm_t single = nullptr;
+  SADMM_TRY(sadmm_create(Q, M, K, N, rho, lambda[0], &c, &single));
+  sadmm_batch_ctx* b = new (std::nothrow) sadmm_batch_ctx();
+  if (!b) { sadmm_destroy(single); return SADMM_ENOMEM; }
+  b->Q = Q; b->M = M; b->K = K; b->N = N; b->KM = K * M; b->S = S;
+  b->rho = rho; b->mu = c.mu; b->crit = c; b->single = single;
+  bool ok = true;
+  auto A = [&](size_t bytes) { void* p = b->dalloc(bytes); if (!p) ok = false; return p; };
+  const size_t QNS = (size_t)Q * N * kBS, NS = (size_t)N * kBS, KS = (size_t)b->KM * kBS;
+  b->X = (float*)A(QNS * 4); b->dX = (float*)A(QNS * 4);
+  b->xbar = (float*)A(NS * 4); b->zbar = (float*)A(NS * 4); b->sd = (float*)A(NS * 4);
+  b->lor = (float*)A(kBS * 4);
+  b->dA = (float2**)A(Q * sizeof(void*)); b->dY = (float2**)A(Q * sizeof(void*));
+  b->dR = (float2**)A(Q * sizeof(void*)); b->dF = (float2**)A(Q * sizeof(void*));
+  b->dU = (float**)A(Q * sizeof(void*)); b->dG = (float**)A(Q * sizeof(void*));
+  b->chunks = batch_chunks(Q, b->KM, N);
+  b->partial = (float2*)A((size_t)Q * b->chunks * KS * sizeof(float2));
+  b->rpart = (double*)A((size_t)div_up(N, kBrThreads / kBS) * kBS * kBrSums * sizeof(double));
+  b->scal = (IterScalars*)A(kBS * sizeof(IterScalars));
+  b->ybuf = (float2*)A((size_t)S * Q * b->KM * sizeof(float2));
+  b->xout = (float*)A((size_t)S * N * 4);
+  std::vector<void*> Y(Q), R(Q), U(Q), G(Q);
+  for (int q = 0; q < Q && ok; ++q) {
+    Y[q] = A(KS * sizeof(float2));
+    R[q] = A(KS * sizeof(float2));
+    U[q] = A(2 * KS * sizeof(float));
+    G[q] = A(NS * sizeof(float));
+  }
+  if (!ok) {
+    for (void* p : b->owned) cudaFree(p);
+    sadmm_destroy(single);
+    delete b;
+    set_error("sadmm_batch_create: device allocation failed");
+    return SADMM_ENOMEM;
+  }
+  std::vector<float> lor(kBS);
+  for (int s = 0; s < kBS; ++s) lor[s] = (float)(lambda[s] / rho);
+  if (cudaMemcpy(b->lor, lor.data(), kBS * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(b->dY, Y.data(), Q * sizeof(void*), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(b->dR, R.data(), Q * sizeof(void*), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(b->dU, U.data(), Q * sizeof(void*), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(b->dG, G.data(), Q * sizeof(void*), cudaMemcpyHostToDevice) != cudaSuccess) {
+    for (void* p : b->owned) cudaFree(p);
+    sadmm_destroy(single);
+    delete b;
+    set_error("sadmm_batch_create: initialisation failed");
+    return SADMM_ECUDA;
+  }
+  *out = b;
+  return SADMM_OK;
+}
+
+int sadmm_batch_set_stream(sadmm_batch_t b, void* stream) {
+  using namespace sadmm;
+  if (!b) return SADMM_EINVAL;
+  SADMM_CUDA_TRY(cudaStreamSynchronize(b->st));
+  b->st = (cudaStream_t)stream;
+  if (b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; }
+  b->graph_valid = false;
+  return sadmm_set_stream(b->single, stream);
+}
+
+int sadmm_batch_set_operator(sadmm_batch_t b, int q, const float* A_q) {
+  using namespace sadmm;
+  if (!b) return SADMM_EINVAL;
+  b->graph_valid = false;
+  return sadmm_set_operator(b->single, q, A_q);
+}
+
+int sadmm_batch_solve(sadmm_batch_t b, const float* y, float* x_out, int iters, sadmm_stats* st) {
+  using namespace sadmm;
+  if (!b || !y || iters < 0) { set_error("sadmm_batch_solve: bad arguments"); return SADMM_EINVAL; }
+  const auto t0 = std::chrono::steady_clock::now();
+  SADMM_TRY(sadmm_prepare(b->single));
+  if (!b->graph_valid) {
+    std::vector<void*> Ap(b->Q), Fp(b->Q);
+    for (int q = 0; q < b->Q; ++q) {
+      const float2 *A = nullptr, *F = nullptr;
+      SADMM_TRY(single_export(b->single, q, &A, &F, &b->n, &b->ld, &b->woodbury));
+      Ap[q] = (void*)A;
+      Fp[q] = (void*)F;
+    }
+    SADMM_CUDA_TRY(cudaMemcpyAsync(b->dA, Ap.data(), b->Q * sizeof(void*), cudaMemcpyHostToDevice, b->st));
+    SADMM_CUDA_TRY(cudaMemcpyAsync(b->dF, Fp.data(), b->Q * sizeof(void*), cudaMemcpyHostToDevice, b->st));
+    SADMM_CUDA_TRY(cudaStreamSynchronize(b->st));
+    if (b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; }
+    // capture one iteration; replay it `iters` times
+    cudaStream_t cap;
+    SADMM_CUDA_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    cudaStream_t saved = b->st;
+    b->st = cap;
+    cudaGraph_t g;
+    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    const long long n0 = sadmm_launch_count();
+    int rc = e == cudaSuccess ? batch_launch_iteration(*b) : SADMM_ECUDA;
+    b->kernels_per_iter = (int)(sadmm_launch_count() - n0);
+    cudaError_t e2 = cudaStreamEndCapture(cap, &g);
+    b->st = saved;
+    cudaStreamDestroy(cap);
+    if (rc != SADMM_OK) return rc;
+    SADMM_CUDA_TRY(e);
+    SADMM_CUDA_TRY(e2);
+    e = cudaGraphInstantiate(&b->graph, g, 0);
+    cudaGraphDestroy(g);
+    SADMM_CUDA_TRY(e);
+    b->graph_valid = true;
+  }
+  // reset and load measurements
+  const size_t QNS = (size_t)b->Q * b->N * kBS, NS = (size_t)b->N * kBS;
+  SADMM_CUDA_TRY(cudaMemsetAsync(b->X, 0, QNS * 4, b->st));
+  SADMM_CUDA_TRY(cudaMemsetAsync(b->dX, 0, QNS * 4, b->st));
+  SADMM_CUDA_TRY(cudaMemsetAsync(b->xbar, 0, NS * 4, b->st));
+  SADMM_CUDA_TRY(cudaMemsetAsync(b->zbar, 0, NS * 4, b->st));
+  SADMM_CUDA_TRY(cudaMemsetAsync(b->sd, 0, NS * 4, b->st));
+  SADMM_CUDA_TRY(cudaMemcpyAsync(b->ybuf, y, (size_t)kBS * b->Q * b->KM * sizeof(float2), cudaMemcpyDefault, b->st));
+  bload_y_kernel<<<dim3(div_up((long long)b->KM * kBS, 256), b->Q), 256, 0, b->st>>>(b->ybuf, b->dY, b->Q, b->KM);
+  SADMM_LAUNCH_CHECK();
+  for (int it = 0; it < iters; ++it) {
+    SADMM_CUDA_TRY(cudaGraphLaunch(b->graph, b->st));
+    for (int kk = 0; kk < b->kernels_per_iter; ++kk) count_launch();
+  }
+  if (x_out) {
+    bscale_kernel<<<div_up(NS, 256), 256, 0, b->st>>>(b->zbar, (float)b->Q, b->xout, b->N);
+    SADMM_LAUNCH_CHECK();
+    SADMM_CUDA_TRY(cudaMemcpyAsync(x_out, b->xout, NS * 4, cudaMemcpyDefault, b->st));
+  }
+  IterScalars h[kBS];
+  SADMM_CUDA_TRY(cudaMemcpyAsync(h, b->scal, sizeof h, cudaMemcpyDeviceToHost, b->st));
+  SADMM_CUDA_TRY(cudaStreamSynchronize(b->st));
+  b->k = iters;
+  for (int s = 0; s < kBS; ++s)
+    if (iters > 0 && h[s].nonfinite) { set_error("non-finite value in scene %d", s); return SADMM_ENONFINITE; }
+  if (st) {
+    memset(st, 0, sizeof *st);
+    st->iters = iters;
+    st->active_total = b->Q * b->N * kBS;
+    st->r_pri = h[0].r_pri; st->eps_pri = h[0].eps_pri; st->d = h[0].d; st->eps_dual = h[0].eps_dual;
+    st->relchange = h[0].relchange;
+    st->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    st->bytes_iter = (double)iters * ((double)b->Q * b->KM * b->N * 16.0 + (double)b->Q * b->n * b->ld * 8.0);
+  }
+  return SADMM_OK;
+}
+
+int sadmm_batch_get_xq(sadmm_batch_t b, int scene, int q, float* out) {
+  using namespace sadmm;
+  if (!b || scene < 0 || scene >= b->S || q < 0 || q >= b->Q || !out) return SADMM_EINVAL;
+  bget_x_kernel<<<div_up(b->N, 256), 256, 0, b->st>>>(b->X + (size_t)q * b->N * kBS, b->N, scene, b->xout);
+  SADMM_LAUNCH_CHECK();
+  SADMM_CUDA_TRY(cudaMemcpyAsync(out, b->xout, b->N * 4, cudaMemcpyDefault, b->st));
+  SADMM_CUDA_TRY(cudaStreamSynchronize(b->st));
+  return SADMM_OK;
+}
+
+void sadmm_batch_destroy(sadmm_batch_t b) {
+  if (!b) return;
+  cudaStreamSynchronize(b->st);
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  for (void* p : b->owned) cudaFree(p);
+  sadmm_destroy(b->single);
+  delete b;
+}
+
+}  // extern "C"
