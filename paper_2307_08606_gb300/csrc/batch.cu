@@ -26,12 +26,24 @@ namespace {
 
 constexpr int kBS = 16;              // scenes per batch (fixed tile width)
 
+// Asynchronous 16-byte global -> shared copies (zero fill when !valid), so a
+// whole operator slab is in flight at once and the next slab loads while the
+// current one is used.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool valid) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  const int sz = valid ? 16 : 0;
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(sa), "l"(gmem), "r"(sz) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
 // ------------------------------------------------------------------ forward
 // Output tile: 128 complex rows x 16 scenes; thread tile 4 rows x 4 scenes
 // (16 complex accumulators).  K loop over pixel slabs of 16 staged in shared
 // memory (operator slab 128 x 16 complex, V slab 16 x 16).
 constexpr int kBfRows = 128;
-constexpr int kBfSlab = 16;
+constexpr int kBfSlab = 32;
 constexpr int kBfThreads = 128;
 
 struct BatchDev {
@@ -52,7 +64,8 @@ bfwd_partial_kernel(const float2* const* __restrict__ Aq, BatchDev b, int chunks
   const int r0 = blockIdx.x * kBfRows;
   const int KM = b.KM, N = b.N;
   const int p0 = c * cols_per_chunk, p1 = min(N, p0 + cols_per_chunk);
-  __shared__ float2 sA[kBfSlab][kBfRows];
+  extern __shared__ float4 smem4[];
+  float2 (*sA)[kBfSlab][kBfRows] = reinterpret_cast<float2 (*)[kBfSlab][kBfRows]>(smem4);   // [2][slab][rows]
   __shared__ float sV[kBfSlab][kBS];
   const int tid = threadIdx.x;
   const int tr = tid / 4, ts = tid % 4;            // 32 row groups x 4 scene groups
@@ -63,13 +76,21 @@ bfwd_partial_kernel(const float2* const* __restrict__ Aq, BatchDev b, int chunks
     for (int s = 0; s < 4; ++s) acc[i][s] = make_float2(0.f, 0.f);
   const float2* A = Aq[q];
   const float* X = b.X + (size_t)q * N * kBS;
-  for (int j0 = p0; j0 < p1; j0 += kBfSlab) {
-    __syncthreads();
-    for (int e = tid; e < kBfSlab * kBfRows; e += kBfThreads) {
-      const int jj = e / kBfRows, rr = e % kBfRows;
-      const int j = j0 + jj, r = r0 + rr;
-      sA[jj][rr] = (j < p1 && r < KM) ? A[(size_t)j * KM + r] : make_float2(0.f, 0.f);
+  auto stage = [&](int buf, int j0) {
+    // kBfSlab pixels x kBfRows rows of complex = kBfSlab * kBfRows / 2 chunks of 16 bytes
+    for (int e = tid; e < kBfSlab * kBfRows / 2; e += kBfThreads) {
+      const int jj = e / (kBfRows / 2), r2 = e % (kBfRows / 2);
+      const int j = j0 + jj, r = r0 + 2 * r2;
+      const bool ok = j < p1 && r < KM;
+      cp_async16(&sA[buf][jj][2 * r2], ok ? (const void*)(A + (size_t)j * KM + r) : (const void*)A, ok);
     }
+    cp_async_commit();
+  };
+  if (p0 < p1) stage(0, p0);
+  int buf = 0;
+  for (int j0 = p0; j0 < p1; j0 += kBfSlab, buf ^= 1) {
+    const bool more = j0 + kBfSlab < p1;
+    if (more) stage(buf ^ 1, j0 + kBfSlab);
     for (int e = tid; e < kBfSlab * kBS; e += kBfThreads) {
       const int jj = e / kBS, s = e % kBS, j = j0 + jj;
       float v = 0.f;
@@ -79,13 +100,14 @@ bfwd_partial_kernel(const float2* const* __restrict__ Aq, BatchDev b, int chunks
       }
       sV[jj][s] = v;
     }
+    if (more) cp_async_wait<1>(); else cp_async_wait<0>();
     __syncthreads();
-#pragma unroll 4
+#pragma unroll 8
     for (int jj = 0; jj < kBfSlab; ++jj) {
       float2 a[4];
       float v[4];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = sA[jj][tr + 32 * i];
+      for (int i = 0; i < 4; ++i) a[i] = sA[buf][jj][tr + 32 * i];
 #pragma unroll
       for (int s = 0; s < 4; ++s) v[s] = sV[jj][ts + 4 * s];
 #pragma unroll
@@ -96,6 +118,7 @@ bfwd_partial_kernel(const float2* const* __restrict__ Aq, BatchDev b, int chunks
           acc[i][s].y = fmaf(a[i].y, v[s], acc[i][s].y);
         }
     }
+    __syncthreads();
   }
   float2* out = partial + ((size_t)q * chunks + c) * KM * kBS;
 #pragma unroll
@@ -151,7 +174,7 @@ __device__ __forceinline__ size_t cidx(int j, int s) { return ((size_t)(j >> 1) 
 __global__ void __launch_bounds__(kBsWarps * 32)
 bspd_kernel(const float2* const* __restrict__ Fq, const float* const* __restrict__ uq, float* const* __restrict__ outq,
             int n, int ld, int mode, BatchDev b) {
-  extern __shared__ float s_u[];                   // [kBsChunk][kBS]
+  extern __shared__ float s_u[];                   // [kBsChunk + 1][kBS]
   const int q = blockIdx.y;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int i = blockIdx.x * kBsWarps + warp;      // one row per warp
@@ -163,7 +186,7 @@ bspd_kernel(const float2* const* __restrict__ Fq, const float* const* __restrict
   for (int j0 = 0; j0 < n; j0 += kBsChunk) {
     const int nj = min(kBsChunk, n - j0);
     __syncthreads();
-    for (int e = threadIdx.x; e < kBsChunk * kBS; e += blockDim.x) {
+    for (int e = threadIdx.x; e < (kBsChunk + 1) * kBS; e += blockDim.x) {
       const int jj = e / kBS, s = e % kBS;
       float v = 0.f;
       if (jj < nj) v = mode == 0 ? u[cidx(j0 + jj, s)] : u[(size_t)(j0 + jj) * kBS + s];
@@ -171,17 +194,33 @@ bspd_kernel(const float2* const* __restrict__ Fq, const float* const* __restrict
     }
     __syncthreads();
     if (i < n) {
-      const float2* row = F + (size_t)i * ld + j0;
-      for (int jj = lane; jj < nj; jj += 32) {
-        const float2 f = row[jj];
-        const float4* uu = reinterpret_cast<const float4*>(s_u + jj * kBS);
+      // two (hi, lo) elements per float4; two float4 in flight per lane
+      const float4* row = reinterpret_cast<const float4*>(F + (size_t)i * ld + j0);
+      for (int jj0 = 2 * lane; jj0 < nj; jj0 += 2 * 32 * 2) {
+        float4 f[2];
 #pragma unroll
-        for (int s4 = 0; s4 < kBS / 4; ++s4) {
-          const float4 x = uu[s4];
-          df2(sh[4 * s4 + 0], sl[4 * s4 + 0], f.x, f.y, x.x);
-          df2(sh[4 * s4 + 1], sl[4 * s4 + 1], f.x, f.y, x.y);
-          df2(sh[4 * s4 + 2], sl[4 * s4 + 2], f.x, f.y, x.z);
-          df2(sh[4 * s4 + 3], sl[4 * s4 + 3], f.x, f.y, x.w);
+        for (int u2 = 0; u2 < 2; ++u2) {
+          const int jj = jj0 + 64 * u2;
+          f[u2] = jj < nj ? __ldcs(row + jj / 2) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int u2 = 0; u2 < 2; ++u2) {
+          const int jj = jj0 + 64 * u2;
+          if (jj >= nj) break;
+          const float4* ua = reinterpret_cast<const float4*>(s_u + jj * kBS);
+          const float4* ub = reinterpret_cast<const float4*>(s_u + (jj + 1) * kBS);
+#pragma unroll
+          for (int s4 = 0; s4 < kBS / 4; ++s4) {
+            const float4 x = ua[s4], y = ub[s4];
+            df2(sh[4 * s4 + 0], sl[4 * s4 + 0], f[u2].x, f[u2].y, x.x);
+            df2(sh[4 * s4 + 1], sl[4 * s4 + 1], f[u2].x, f[u2].y, x.y);
+            df2(sh[4 * s4 + 2], sl[4 * s4 + 2], f[u2].x, f[u2].y, x.z);
+            df2(sh[4 * s4 + 3], sl[4 * s4 + 3], f[u2].x, f[u2].y, x.w);
+            df2(sh[4 * s4 + 0], sl[4 * s4 + 0], f[u2].z, f[u2].w, y.x);
+            df2(sh[4 * s4 + 1], sl[4 * s4 + 1], f[u2].z, f[u2].w, y.y);
+            df2(sh[4 * s4 + 2], sl[4 * s4 + 2], f[u2].z, f[u2].w, y.z);
+            df2(sh[4 * s4 + 3], sl[4 * s4 + 3], f[u2].z, f[u2].w, y.w);
+          }
         }
       }
     }
@@ -215,14 +254,20 @@ constexpr int kBaPix = 128;
 constexpr int kBaSlab = 16;
 constexpr int kBaThreads = 128;
 
-// mode 0: x-update epilogue (Woodbury form); mode 1: G into gq [pixel][scene]
+// Partial G over the rows [r_begin, r_end) of split blockIdx.z, written to
+// gpart[q][split][pixel][scene]; badj_reduce_kernel adds the splits in order.
+constexpr int kBaPad = kBaSlab + 2;   // row stride 144 bytes: 16-byte aligned, conflict-free reads
+
 __global__ void __launch_bounds__(kBaThreads)
-badj_kernel(const float2* const* __restrict__ Aq, const float2* const* __restrict__ Wq, float* const* __restrict__ gq,
-            int mode, BatchDev b) {
+badj_kernel(const float2* const* __restrict__ Aq, const float2* const* __restrict__ Wq, float* __restrict__ gpart,
+            int splits, BatchDev b) {
   const int q = blockIdx.y;
   const int j0 = blockIdx.x * kBaPix;
   const int KM = b.KM, N = b.N;
-  __shared__ float2 sA[kBaPix][kBaSlab + 1];
+  const int rows_per = (KM / splits + kBaSlab - 1) / kBaSlab * kBaSlab;
+  const int rb = blockIdx.z * rows_per, re = min(KM, rb + rows_per);
+  extern __shared__ float4 smem4[];
+  float2 (*sA)[kBaPix][kBaPad] = reinterpret_cast<float2 (*)[kBaPix][kBaPad]>(smem4);      // [2][pix][pad]
   __shared__ float2 sW[kBaSlab][kBS];
   const int tid = threadIdx.x;
   const int tp = tid / 4, ts = tid % 4;            // 32 pixel groups x 4 scene groups
@@ -233,23 +278,31 @@ badj_kernel(const float2* const* __restrict__ Aq, const float2* const* __restric
     for (int s = 0; s < 4; ++s) acc[i][s] = 0.f;
   const float2* A = Aq[q];
   const float2* W = Wq[q];
-  for (int r0 = 0; r0 < KM; r0 += kBaSlab) {
-    __syncthreads();
-    for (int e = tid; e < kBaPix * kBaSlab; e += kBaThreads) {
-      const int pp = e / kBaSlab, rr = e % kBaSlab;
-      const int j = j0 + pp, r = r0 + rr;
-      sA[pp][rr] = (j < N && r < KM) ? A[(size_t)j * KM + r] : make_float2(0.f, 0.f);
+  auto stage = [&](int buf, int r0) {
+    for (int e = tid; e < kBaPix * kBaSlab / 2; e += kBaThreads) {
+      const int pp = e / (kBaSlab / 2), r2 = e % (kBaSlab / 2);
+      const int j = j0 + pp, r = r0 + 2 * r2;
+      const bool ok = j < N && r < re;
+      cp_async16(&sA[buf][pp][2 * r2], ok ? (const void*)(A + (size_t)j * KM + r) : (const void*)A, ok);
     }
+    cp_async_commit();
+  };
+  if (rb < re) stage(0, rb);
+  int buf = 0;
+  for (int r0 = rb; r0 < re; r0 += kBaSlab, buf ^= 1) {
+    const bool more = r0 + kBaSlab < re;
+    if (more) stage(buf ^ 1, r0 + kBaSlab);
     for (int e = tid; e < kBaSlab * kBS; e += kBaThreads) {
       const int rr = e / kBS, s = e % kBS, r = r0 + rr;
-      sW[rr][s] = r < KM ? W[(size_t)r * kBS + s] : make_float2(0.f, 0.f);
+      sW[rr][s] = r < re ? W[(size_t)r * kBS + s] : make_float2(0.f, 0.f);
     }
+    if (more) cp_async_wait<1>(); else cp_async_wait<0>();
     __syncthreads();
 #pragma unroll 4
     for (int rr = 0; rr < kBaSlab; ++rr) {
       float2 a[4], w[4];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = sA[tp + 32 * i][rr];
+      for (int i = 0; i < 4; ++i) a[i] = sA[buf][tp + 32 * i][rr];
 #pragma unroll
       for (int s = 0; s < 4; ++s) w[s] = sW[rr][ts + 4 * s];
 #pragma unroll
@@ -257,26 +310,38 @@ badj_kernel(const float2* const* __restrict__ Aq, const float2* const* __restric
 #pragma unroll
         for (int s = 0; s < 4; ++s) acc[i][s] = fmaf(a[i].x, w[s].x, fmaf(a[i].y, w[s].y, acc[i][s]));
     }
+    __syncthreads();
   }
+  float* out = gpart + ((size_t)q * splits + blockIdx.z) * N * kBS;
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     const int j = j0 + tp + 32 * i;
     if (j >= N) continue;
 #pragma unroll
-    for (int s4 = 0; s4 < 4; ++s4) {
-      const int s = ts + 4 * s4;
-      if (mode == 1) {
-        gq[q][(size_t)j * kBS + s] = acc[i][s4];
-      } else {
-        const size_t o = ((size_t)q * N + j) * kBS + s;
-        const size_t p = (size_t)j * kBS + s;
-        const float xo = b.X[o];
-        const float v = xo - b.xbar[p] + b.zbar[p] - b.sd[p];
-        const float xn = fmaf(b.mu, acc[i][s4], v);
-        b.dX[o] = xn - xo;
-        b.X[o] = xn;
-      }
-    }
+    for (int s4 = 0; s4 < 4; ++s4) out[(size_t)j * kBS + ts + 4 * s4] = acc[i][s4];
+  }
+}
+
+// G = sum of the split partials (split order).  mode 0: x-update epilogue
+// (Woodbury form); mode 1: G into gq [pixel][scene] (primal form).
+__global__ void badj_reduce_kernel(const float* __restrict__ gpart, int splits, float* const* __restrict__ gq,
+                                   int mode, BatchDev b) {
+  const int q = blockIdx.y;
+  const size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  const size_t NS = (size_t)b.N * kBS;
+  if (e >= NS) return;
+  const float* p = gpart + (size_t)q * splits * NS + e;
+  float g = 0.f;
+  for (int k = 0; k < splits; ++k) g += p[(size_t)k * NS];
+  if (mode == 1) {
+    gq[q][e] = g;
+  } else {
+    const size_t o = (size_t)q * NS + e;
+    const float xo = b.X[o];
+    const float v = xo - b.xbar[e] + b.zbar[e] - b.sd[e];
+    const float xn = fmaf(b.mu, g, v);
+    b.dX[o] = xn - xo;
+    b.X[o] = xn;
   }
 }
 
@@ -334,14 +399,19 @@ bresid_kernel(BatchDev b, double* __restrict__ partials) {
   }
 }
 
-__global__ void bresid_final_kernel(const double* __restrict__ partials, int nblk, BatchDev b, double eps_abs,
-                                    double eps_rel, int k_after, IterScalars* __restrict__ out) {
-  const int s = threadIdx.x;
-  if (s >= kBS) return;
-  double tot[kBrSums];
-  for (int k = 0; k < kBrSums; ++k) tot[k] = 0.0;
-  for (int blk = 0; blk < nblk; ++blk)
-    for (int k = 0; k < kBrSums; ++k) tot[k] += partials[((size_t)blk * kBS + s) * kBrSums + k];
+__global__ void __launch_bounds__(kBrSums * 32)
+bresid_final_kernel(const double* __restrict__ partials, int nblk, BatchDev b, double eps_abs,
+                    double eps_rel, int k_after, IterScalars* __restrict__ out) {
+  const int s = blockIdx.x;                        // scene
+  const int k = threadIdx.x >> 5, lane = threadIdx.x & 31;   // warp k reduces sum k
+  __shared__ double tot[kBrSums];
+  double t = 0.0;
+  for (int blk = lane; blk < nblk; blk += 32) t += partials[((size_t)blk * kBS + s) * kBrSums + k];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  if (lane == 0) tot[k] = t;
+  __syncthreads();
+  if (threadIdx.x != 0) return;
   const double Q = b.Q, QN = (double)b.Q * b.N;
   IterScalars r;
   r.r_pri = sqrt(Q) * sqrt(tot[0]);
@@ -357,7 +427,7 @@ __global__ void bresid_final_kernel(const double* __restrict__ partials, int nbl
   r.gate = 0;
   r.changed = 0;
   double chk = 0.0;
-  for (int k = 0; k < kBrSums; ++k) chk += tot[k];
+  for (int j = 0; j < kBrSums; ++j) chk += tot[j];
   r.nonfinite = isfinite(chk) ? 0 : 1;
   out[s] = r;
 }
@@ -409,6 +479,8 @@ struct BatchCtx {
   float2* ybuf = nullptr;
   float* xout = nullptr;
   int chunks = 1, n = 0, ld = 0, woodbury = 1;
+  int asplits = 1;                 // row splits of the adjoint GEMM
+  float* gpart = nullptr;          // Q x asplits x N x 16 partial adjoint sums
   cudaGraphExec_t graph = nullptr;
   bool graph_valid = false;
   int kernels_per_iter = 0;
@@ -435,20 +507,33 @@ int batch_launch_iteration(BatchCtx& c) {
   const BatchDev bv = c.view();
   dim3 gf(div_up(c.KM, kBfRows), c.chunks, c.Q);
   const int per = div_up(c.N, c.chunks);
-  bfwd_partial_kernel<<<gf, kBfThreads, 0, c.st>>>(c.dA, bv, c.chunks, per, c.partial);
+  const size_t fsmem = 2 * sizeof(float2) * kBfSlab * kBfRows;
+  static bool fconf = false;
+  if (!fconf) {
+    SADMM_CUDA_TRY(cudaFuncSetAttribute(bfwd_partial_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem));
+    fconf = true;
+  }
+  bfwd_partial_kernel<<<gf, kBfThreads, fsmem, c.st>>>(c.dA, bv, c.chunks, per, c.partial);
   SADMM_LAUNCH_CHECK();
   bfwd_reduce_kernel<<<dim3(div_up((long long)c.KM * kBS, 256), c.Q), 256, 0, c.st>>>(c.partial, c.dY, c.dR, c.KM,
                                                                                      c.chunks);
   SADMM_LAUNCH_CHECK();
-  const size_t smem = (size_t)kBsChunk * kBS * sizeof(float);
+  const size_t smem = (size_t)(kBsChunk + 1) * kBS * sizeof(float);
+  const dim3 ga(div_up(c.N, kBaPix), c.Q, c.asplits);
+  const size_t asmem = 2 * sizeof(float2) * kBaPix * kBaPad;
+  const dim3 gr(div_up((long long)c.N * kBS, 256), c.Q);
   if (c.woodbury) {
     bspd_kernel<<<dim3(div_up(c.n, kBsWarps), c.Q), kBsWarps * 32, smem, c.st>>>(
         c.dF, (const float* const*)c.dR, c.dU, c.n, c.ld, 0, bv);
     SADMM_LAUNCH_CHECK();
-    badj_kernel<<<dim3(div_up(c.N, kBaPix), c.Q), kBaThreads, 0, c.st>>>(c.dA, (const float2* const*)c.dU, c.dG, 0, bv);
+    badj_kernel<<<ga, kBaThreads, asmem, c.st>>>(c.dA, (const float2* const*)c.dU, c.gpart, c.asplits, bv);
+    SADMM_LAUNCH_CHECK();
+    badj_reduce_kernel<<<gr, 256, 0, c.st>>>(c.gpart, c.asplits, c.dG, 0, bv);
     SADMM_LAUNCH_CHECK();
   } else {
-    badj_kernel<<<dim3(div_up(c.N, kBaPix), c.Q), kBaThreads, 0, c.st>>>(c.dA, c.dR, c.dG, 1, bv);
+    badj_kernel<<<ga, kBaThreads, asmem, c.st>>>(c.dA, c.dR, c.gpart, c.asplits, bv);
+    SADMM_LAUNCH_CHECK();
+    badj_reduce_kernel<<<gr, 256, 0, c.st>>>(c.gpart, c.asplits, c.dG, 1, bv);
     SADMM_LAUNCH_CHECK();
     bspd_kernel<<<dim3(div_up(c.n, kBsWarps), c.Q), kBsWarps * 32, smem, c.st>>>(
         c.dF, (const float* const*)c.dG, nullptr, c.n, c.ld, 1, bv);
@@ -457,7 +542,7 @@ int batch_launch_iteration(BatchCtx& c) {
   const int nblk = div_up(c.N, kBrThreads / kBS);
   bresid_kernel<<<nblk, kBrThreads, 0, c.st>>>(bv, c.rpart);
   SADMM_LAUNCH_CHECK();
-  bresid_final_kernel<<<1, 32, 0, c.st>>>(c.rpart, nblk, bv, c.crit.eps_abs, c.crit.eps_rel, 0, c.scal);
+  bresid_final_kernel<<<kBS, kBrSums * 32, 0, c.st>>>(c.rpart, nblk, bv, c.crit.eps_abs, c.crit.eps_rel, 0, c.scal);
   SADMM_LAUNCH_CHECK();
   return SADMM_OK;
 }
@@ -499,6 +584,8 @@ int sadmm_batch_create(int Q, int M, int K, int N, int S, double rho, const doub
   b->dR = (float2**)A(Q * sizeof(void*)); b->dF = (float2**)A(Q * sizeof(void*));
   b->dU = (float**)A(Q * sizeof(void*)); b->dG = (float**)A(Q * sizeof(void*));
   b->chunks = batch_chunks(Q, b->KM, N);
+  b->asplits = std::max(1, std::min(div_up(152 * 8, (long long)div_up(N, kBaPix) * Q), b->KM / 256));
+  b->gpart = (float*)A((size_t)Q * b->asplits * NS * sizeof(float));
   b->partial = (float2*)A((size_t)Q * b->chunks * KS * sizeof(float2));
   b->rpart = (double*)A((size_t)div_up(N, kBrThreads / kBS) * kBS * kBrSums * sizeof(double));
   b->scal = (IterScalars*)A(kBS * sizeof(IterScalars));
