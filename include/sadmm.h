@@ -203,6 +203,34 @@ int sadmm_batch_get_xq(sadmm_batch_t b, int scene, int q, float* out);
 void sadmm_batch_destroy(sadmm_batch_t b);
 
 /* ------------------------------------------------------------------------
+ * Learned elimination proposal (an extension; the paper has no counterpart):
+ * a CNN over the H x W pixel grid with five 3x3 convolutions (6 -> 32, then
+ * 32 -> 32, zero padding), GELU after each, a 1x1 head (32 -> 1) and a
+ * sigmoid.  Weights are BF16-rounded copies of FP32 master parameters; sums
+ * are FP32.  Flat parameter order: W1[32][6][3][3] b1[32] W2[32][32][3][3]
+ * b2[32] ... W5 b5 Wh[32] bh[1] (sadmm_cnn_num_params() = 38785 floats).
+ * Inputs are NCHW float32 (6 feature channels), outputs H x W probabilities.
+ * ---------------------------------------------------------------------- */
+typedef struct sadmm_cnn_ctx* sadmm_cnn_t;
+int sadmm_cnn_create(int H, int W, int max_batch, sadmm_cnn_t* out);
+int sadmm_cnn_num_params(void);
+/* params: host or device FP32; resets the Adam state. */
+int sadmm_cnn_set_params(sadmm_cnn_t c, const float* params);
+/* rounded = 1: the BF16-rounded weights the kernels use; 0: FP32 masters. */
+int sadmm_cnn_get_params(sadmm_cnn_t c, float* params, int rounded);
+/* prob (device, B x H x W) = CNN(in) for in (device, B x 6 x H x W). */
+int sadmm_cnn_forward(sadmm_cnn_t c, const float* in, int B, float* prob, void* stream);
+/* Gradient (device, num_params floats) of the mean weighted binary
+ * cross-entropy  -mean(w_i [y_i log p_i + (1-y_i) log(1-p_i)]),  w_i = pos_weight
+ * for y_i = 1 else 1, with respect to the (rounded) weights; *loss (host) the
+ * loss, may be NULL.  labels: device, B x H x W in {0, 1}. */
+int sadmm_cnn_backward(sadmm_cnn_t c, const float* in, const float* labels, int B, double pos_weight,
+                       float* grad, double* loss, void* stream);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) on the FP32 masters. */
+int sadmm_cnn_adam_step(sadmm_cnn_t c, const float* grad, double lr, void* stream);
+void sadmm_cnn_destroy(sadmm_cnn_t c);
+
+/* ------------------------------------------------------------------------
  * Kernel-level entry points on DEVICE pointers (used by parity tests and for
  * composing other pipelines).  All work is on `stream`; none synchronises.
  * ---------------------------------------------------------------------- */

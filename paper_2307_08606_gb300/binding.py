@@ -83,6 +83,14 @@ _SIGS = {
     "sadmm_batch_solve": (C.c_int, [_P, _P, _P, C.c_int, C.POINTER(Stats)]),
     "sadmm_batch_get_xq": (C.c_int, [_P, C.c_int, C.c_int, _P]),
     "sadmm_batch_destroy": (None, [_P]),
+    "sadmm_cnn_create": (C.c_int, [C.c_int, C.c_int, C.c_int, C.POINTER(_P)]),
+    "sadmm_cnn_num_params": (C.c_int, []),
+    "sadmm_cnn_set_params": (C.c_int, [_P, _P]),
+    "sadmm_cnn_get_params": (C.c_int, [_P, _P, C.c_int]),
+    "sadmm_cnn_forward": (C.c_int, [_P, _P, C.c_int, _P, _P]),
+    "sadmm_cnn_backward": (C.c_int, [_P, _P, _P, C.c_int, C.c_double, _P, C.POINTER(C.c_double), _P]),
+    "sadmm_cnn_adam_step": (C.c_int, [_P, _P, C.c_double, _P]),
+    "sadmm_cnn_destroy": (None, [_P]),
     "sadmm_split_operator": (C.c_int, [_P, C.c_size_t, C.c_int, _P, _P, _P]),
     "sadmm_forward_split": (C.c_int, [_P, _P, C.c_int, C.c_int, C.c_int, C.c_int, _P, C.c_int, _P, _P,
                                       _P, _P]),
@@ -313,6 +321,56 @@ class BatchSolver:
         out = np.empty(self.N, dtype=np.float32)
         check(self.lib.sadmm_batch_get_xq(self.h, scene, q, _ptr(out)))
         return out
+
+
+class CNN:
+    """The learned elimination proposal network (sadmm_cnn_*); device tensors in and out."""
+
+    def __init__(self, H, W, max_batch=1):
+        self.lib = load()
+        self.H, self.W, self.maxB = H, W, max_batch
+        h = C.c_void_p()
+        check(self.lib.sadmm_cnn_create(H, W, max_batch, C.byref(h)))
+        self.h = h
+        self.n = int(self.lib.sadmm_cnn_num_params())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.sadmm_cnn_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32) if isinstance(p, np.ndarray) else p.contiguous()
+        check(self.lib.sadmm_cnn_set_params(self.h, _ptr(p)))
+
+    def params(self, rounded=False):
+        out = np.empty(self.n, dtype=np.float32)
+        check(self.lib.sadmm_cnn_get_params(self.h, _ptr(out), int(rounded)))
+        return out
+
+    def forward(self, x, stream=0):
+        import torch
+        B = x.shape[0]
+        out = torch.empty((B, self.H, self.W), dtype=torch.float32, device=x.device)
+        check(self.lib.sadmm_cnn_forward(self.h, _ptr(x), B, _ptr(out), C.c_void_p(stream)))
+        return out
+
+    def backward(self, x, labels, pos_weight=1.0, stream=0):
+        import torch
+        g = torch.empty(self.n, dtype=torch.float32, device=x.device)
+        loss = C.c_double()
+        check(self.lib.sadmm_cnn_backward(self.h, _ptr(x), _ptr(labels), x.shape[0], float(pos_weight), _ptr(g),
+                                          C.byref(loss), C.c_void_p(stream)))
+        return g, loss.value
+
+    def adam_step(self, grad, lr, stream=0):
+        check(self.lib.sadmm_cnn_adam_step(self.h, _ptr(grad), float(lr), C.c_void_p(stream)))
 
 
 # ------------------------------------------------------ state blob conversion
