@@ -59,7 +59,8 @@ typedef struct {
   double eps_p;       /* Algorithm 1 tolerance: keep pixel i iff zeta_i >= eps_p         */
   double eps_abs;     /* absolute feasibility tolerance (gate of Algorithm 1, stop)      */
   double eps_rel;     /* relative feasibility tolerance                                 */
-  int    elim;        /* 0 = plain SADMM, 1 = pixel elimination (ASADMM)                 */
+  int    elim;        /* 0 = plain SADMM, 1 = pixel elimination (ASADMM), 2 = ASADMM plus
+                         the learned proposal and re-admission (sadmm_set_eliminator)   */
   int    freeze_mode; /* 0 = removed pixels keep their value, 1 = removed pixels set to 0 */
   int    stop;        /* 0 = ||X^{k+1}-X^k||_F <= tol ||X^{k+1}||_F; 1 = primal & dual
                          residuals below eps_pri and eps_dual (Boyd Sec. 3.3.1)          */
@@ -69,6 +70,21 @@ typedef struct {
                          correct_every iterations, 4 = the same with FP16 planes.  The
                          factor, its refreshes and the fold always use the FP32 operator. */
   int    correct_every; /* precision 3/4: lo-plane refresh period (>= 1)                    */
+  /* elim = 2 (an extension; the paper has no counterpart).  Every learn_every
+     iterations (once k >= max(Kp, 4)), before Algorithm 1's pass:
+       - re-admission: a pixel i frozen in sensor q re-enters J_q when the step
+         |mu Re(a_qi^H (A_q x_q - y_q)) + rho s_i| / (mu ||a_qi||^2 + rho) that a
+         single-coordinate x-update would take exceeds readmit * eps_p (the pixel's
+         entry of the optimality condition of Eq. 2 is then far from zero);
+       - proposal: the network set by sadmm_set_eliminator maps six per-pixel
+         features (sadmm_features) to p_i; p_i > learn_theta drops pixel i from
+         every J_q, in addition to (and independently of the gate of) Algorithm 1.
+     Re-admitted pixels are unfolded from y', their last Kp updates are set to
+     2 eps_p, and the factors gain their columns.  Without a network, elim = 2
+     runs as elim = 1. */
+  int    learn_every;   /* default 10                                                   */
+  double learn_theta;   /* default 0.5, in [0, 1]                                       */
+  double readmit;       /* default 10 (>= 0); elim = 2 also needs eps_p > 0               */
 } sadmm_criterion;
 
 /* Per-solve summary. */
@@ -77,6 +93,8 @@ typedef struct {
   int    stop_reason;  /* 0 = iteration limit, 1 = relative change, 2 = residuals      */
   int    refreshes;    /* factor refreshes after active-set changes                    */
   int    active_total; /* sum_q |J_q| at the end                                       */
+  int    learned_steps;/* learned proposal steps run (elim = 2)                        */
+  int    readmitted;   /* (sensor, pixel) pairs re-admitted over the solve (elim = 2)  */
   double r_pri, eps_pri, d, eps_dual, relchange;   /* last iteration                    */
   double ms_total;     /* host wall time of the solve                                  */
   double ms_refresh;   /* of which: fold + factor refresh after set changes            */
@@ -89,6 +107,8 @@ typedef struct {
   int    gate;         /* 1 if Algorithm 1's test ran (elim on, k >= Kp, r_pri <= eps_pri) */
   int    changed;      /* number of sensors whose active set shrank                    */
   int    active_total; /* sum_q |J_q| after this iteration                             */
+  int    learned;      /* 1 if the learned proposal ran in this iteration (elim = 2)   */
+  int    readmitted;   /* (sensor, pixel) pairs re-admitted in this iteration          */
   double r_pri, eps_pri, d, eps_dual, relchange;
 } sadmm_iter_record;
 
@@ -157,12 +177,29 @@ int sadmm_get_state(sadmm_t ctx, void* buf, size_t* bytes);
  * are recomputed for active sets that are not full. */
 int sadmm_set_state(sadmm_t ctx, const void* buf, size_t bytes);
 
+/* Learned proposal network for elim = 2 (an extension; the paper has no
+ * counterpart): params are sadmm_cnn_num_params() FP32 values (host or
+ * device) in the flat layout of sadmm_cnn_set_params, for the H x W pixel grid
+ * (H * W = N, pixel i at row i / W, column i % W).  The context keeps its own
+ * copy (allocated with cudaMalloc, not the allocator hooks).  params = NULL
+ * removes the network. */
+int sadmm_set_eliminator(sadmm_t ctx, const float* params, int H, int W);
+
+/* The six per-pixel features the network reads, at the current state after k
+ * iterations: out (host or device) is 6 x N floats (NCHW with one image):
+ *   c0 = log(1 + sum_q |x_qi|),  c1 = log(1 + max_q |x_qi|),
+ *   c(2+j) = log10(||dx_i^(k-j)||_2 / eps_p + 1e-4) / 4,  j = 0..3,
+ * dx^(t) being the update of iteration t over the sensors (zero when t < 1 or
+ * j >= Kp; frozen pixels' updates are zero). */
+int sadmm_features(sadmm_t ctx, float* out);
+
 /* Profiling (tracing): when on, every kernel group of the iteration is
  * bracketed by CUDA events on the context's stream and its device time is
  * accumulated per phase.  Phases: 0 forward product (partials + reduction),
  * 1 Woodbury SPD apply, 2 adjoint + x-update (Woodbury form), 3 adjoint
  * (primal form), 4 SPD apply + x-update (primal form), 5 prox/dual/residuals,
- * 6 Algorithm 1 compaction, 7 fold + factor refresh.  Turning it on resets
+ * 6 Algorithm 1 compaction (with the learned step's re-admission test and
+ * network), 7 fold + factor refresh (and re-admission).  Turning it on resets
  * the totals. */
 #define SADMM_NUM_PHASES 8
 int sadmm_set_profiling(sadmm_t ctx, int on);
@@ -298,6 +335,14 @@ int sadmm_adjoint_split(const void* hi, const void* lo, int kind, int planes, in
  * Returns SADMM_ENONFINITE if S is not numerically positive definite. */
 int sadmm_factor_downdate(const float* A, int KM, const int* E, int e, double mu, double* W,
                           void* stream);
+
+/* In-place rank-e update of a Woodbury-form factor.  sign = +1 removes the e
+ * columns E (exactly sadmm_factor_downdate); sign = -1 adds them (pixels
+ * re-admitted to the active set): W <- (W^{-1} + mu B_E B_E^T)^{-1} = W - mu T T^T
+ * with P = W B_E, S = I + mu B_E^T P = L L^T, T = P L^{-T} (Woodbury identity).
+ * Same layout, passes and errors as sadmm_factor_downdate. */
+int sadmm_factor_update(const float* A, int KM, const int* E, int e, double mu, int sign, double* W,
+                        void* stream);
 
 /* out = F u for an n x n FP64 matrix (row-major, leading dimension ldf even
  * and >= n, n <= 49152) and FP32 u; out rounded to FP32.  As in the solver, F

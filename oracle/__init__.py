@@ -4,9 +4,9 @@ TEST INFRASTRUCTURE: imported only by tests/, by the smoke check and by the
 CPU-baseline leg of bench.py.  The CUDA library never imports, links or calls
 anything here, and nothing here imports the library.
 """
-from .sharing_admm import (Criterion, State, Result, RidgeSolver, sadmm, soft, real_form, real_vec,
-                    forward, adjoint_re, objective, kkt, initial_state)
+from .sharing_admm import (Criterion, Eliminator, State, Result, RidgeSolver, sadmm, soft, real_form,
+                           real_vec, forward, adjoint_re, objective, kkt, initial_state)
 from .fista import fista
 
-__all__ = ["Criterion", "State", "Result", "RidgeSolver", "sadmm", "soft", "real_form",
+__all__ = ["Criterion", "Eliminator", "State", "Result", "RidgeSolver", "sadmm", "soft", "real_form",
            "real_vec", "forward", "adjoint_re", "objective", "kkt", "initial_state", "fista"]

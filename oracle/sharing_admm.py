@@ -53,6 +53,9 @@ from dataclasses import dataclass, field
 import numpy as np
 import scipy.linalg as sla
 
+from . import cnn as _cnn
+from . import learned as _learned
+
 
 @dataclass
 class Criterion:
@@ -61,9 +64,12 @@ class Criterion:
     eps_p: float = 1e-5
     eps_abs: float = 1e-4
     eps_rel: float = 1e-2
-    elim: int = 1          # 0: plain SADMM, 1: pixel elimination (Algorithm 1)
+    elim: int = 1          # 0: plain SADMM, 1: pixel elimination (Algorithm 1), 2: plus learned step
     freeze_mode: int = 0   # 0: removed pixels keep their value, 1: set to zero
     stop: int = 0          # 0: relative change of X, 1: primal and dual residuals
+    learn_every: int = 10  # elim 2: period of the learned step
+    learn_theta: float = 0.5   # elim 2: drop pixel i when the network's p_i > learn_theta
+    readmit: float = 10.0  # elim 2: re-admit when the coordinate step exceeds readmit * eps_p
 
 
 def soft(v, t):
@@ -153,14 +159,37 @@ class Result:
         return len(self.state.x) * self.state.zbar
 
 
+@dataclass
+class Eliminator:
+    """Proposal network of the learned step: FP32 master parameters (flat layout
+    of oracle.cnn) for an H x W pixel grid (pixel i at row i // W, column i % W).
+    The network is evaluated with the parameters rounded to BF16."""
+    params: np.ndarray
+    H: int
+    W: int
+
+
 def sadmm(A, y, rho, lam, crit: Criterion, iters, tol=0.0, state: State = None, B=None,
-          snapshots=()):
-    """Run SADMM (crit.elim = 0) or ASADMM (crit.elim = 1) for at most `iters`
+          snapshots=(), eliminator: Eliminator = None):
+    """Run SADMM (crit.elim = 0), ASADMM (crit.elim = 1) or ASADMM with the
+    learned step (crit.elim = 2 with an eliminator) for at most `iters`
     iterations from `state` (zeros if None).  Returns a Result whose history holds,
     per iteration: r_pri, eps_pri, d, eps_dual, relchange, gate, sizes, and the
     decision margins zeta_margin (min |zeta - eps_p| over tested pixels) and
-    gate_margin (|r_pri - eps_pri| / eps_pri).  A copy of the state after
-    iteration k is kept in Result.snapshots for every k in `snapshots`."""
+    gate_margin (|r_pri - eps_pri| / eps_pri); learned steps add learned,
+    readmitted, prob_margin (min |p_i - learn_theta| over pixels active in some
+    sensor) and readmit_margin (min |step - thr| / thr over frozen pixels).  A
+    copy of the state after iteration k is kept in Result.snapshots for every k
+    in `snapshots`.
+
+    The learned step (an extension; the paper has no counterpart) runs after
+    iteration k when k is a multiple of learn_every and k >= max(Kp, 4): the
+    re-admission test (oracle.learned) marks frozen pixels against the sets
+    before this pass, the network maps the features to p, Algorithm 1's pass
+    also drops every pixel with p_i > learn_theta (whether or not its gate
+    passed), and the marked pixels then re-enter their sets: unfolded from y',
+    their last Kp updates set to 2 eps_p.  Removed pixels' window entries are
+    cleared at every pass."""
     Q = len(A)
     mu = crit.mu
     B = B if B is not None else [real_form(a) for a in A]
@@ -176,6 +205,10 @@ def sadmm(A, y, rho, lam, crit: Criterion, iters, tol=0.0, state: State = None, 
 
     for q in range(Q):
         refresh(q)
+    pr = None
+    if crit.elim == 2 and eliminator is not None:
+        assert eliminator.H * eliminator.W == N and crit.eps_p > 0
+        pr = _learned.round_bf16(eliminator.params)
     res = Result(st)
     Zold = st.x - st.xbar[None, :] + st.zbar[None, :]
     for it in range(iters):
@@ -205,30 +238,71 @@ def sadmm(A, y, rho, lam, crit: Criterion, iters, tol=0.0, state: State = None, 
         st.k += 1
         rec = dict(k=st.k, r_pri=r_pri, eps_pri=eps_pri, d=d, eps_dual=eps_dual,
                    relchange=relchange, gate=False, zeta_margin=np.inf, gate_margin=np.inf)
+        gate = False
         if crit.elim and st.k >= crit.Kp:
-            rec["gate_margin"] = abs(r_pri - eps_pri) / eps_pri
-            if r_pri <= eps_pri:
-                rec["gate"] = True
-                zeta = st.ring.mean(axis=0)
-                changed = False
-                for q in range(Q):
-                    J = st.J[q]
-                    zq = zeta[q, J]
+            rec["gate_margin"] = abs(r_pri - eps_pri) / eps_pri if eps_pri > 0 else np.inf
+            gate = r_pri <= eps_pri
+        rec["gate"] = gate
+        learned = (pr is not None and st.k % crit.learn_every == 0 and st.k >= max(crit.Kp, 4))
+        readd, prob = None, None
+        if learned:
+            # re-admission test against the sets before this pass
+            thr = crit.readmit * crit.eps_p
+            readd, rmargin = [], np.inf
+            for q in range(Q):
+                F, step = _learned.readmission_steps(B[q], st.yprime[q], st.x[q], st.J[q], st.s, mu, rho)
+                readd.append(F[step > thr])
+                if len(F) and thr > 0:
+                    rmargin = min(rmargin, float(np.min(np.abs(step - thr))) / thr)
+            feats = _learned.features(st.x, st.ring, st.k, crit.eps_p)
+            p, _ = _cnn.forward(pr, feats.reshape(1, _learned.NFEAT, eliminator.H, eliminator.W))
+            prob = p.reshape(N)
+            act = np.zeros(N, dtype=bool)
+            for J in st.J:
+                act[J] = True
+            rec["prob_margin"] = (float(np.min(np.abs(prob[act] - crit.learn_theta))) if act.any() else np.inf)
+            rec["readmit_margin"] = rmargin
+        rec["learned"] = learned
+        if gate or learned:
+            zeta = st.ring.mean(axis=0)
+            changed = False
+            for q in range(Q):
+                J = st.J[q]
+                zq = zeta[q, J]
+                if gate:
                     if len(zq):
                         rec["zeta_margin"] = min(rec["zeta_margin"], float(np.min(np.abs(zq - crit.eps_p))))
                     keep = zq >= crit.eps_p
-                    if keep.all():
-                        continue
-                    E = J[~keep]
-                    st.J[q] = J[keep]
-                    if crit.freeze_mode == 0:
-                        st.yprime[q] = st.yprime[q] - B[q][:, E] @ st.x[q, E]
-                    else:
-                        st.x[q, E] = 0.0
-                    changed = True
-                    refresh(q)
-                if changed and crit.freeze_mode == 1:
-                    st.xbar = st.x.mean(axis=0)
+                else:
+                    keep = np.ones(len(J), dtype=bool)
+                if learned:
+                    keep &= ~(prob[J] > crit.learn_theta)
+                if keep.all():
+                    continue
+                E = J[~keep]
+                st.J[q] = J[keep]
+                st.ring[:, q, E] = 0.0
+                if crit.freeze_mode == 0:
+                    st.yprime[q] = st.yprime[q] - B[q][:, E] @ st.x[q, E]
+                else:
+                    st.x[q, E] = 0.0
+                changed = True
+                refresh(q)
+            if changed and crit.freeze_mode == 1:
+                st.xbar = st.x.mean(axis=0)
+        if learned:
+            total = 0
+            for q in range(Q):
+                R = readd[q]
+                if len(R) == 0:
+                    continue
+                total += len(R)
+                st.J[q] = np.union1d(st.J[q], R)
+                st.ring[:, q, R] = 2.0 * crit.eps_p
+                if crit.freeze_mode == 0:
+                    st.yprime[q] = st.yprime[q] + B[q][:, R] @ st.x[q, R]
+                refresh(q)
+            rec["readmitted"] = total
         rec["sizes"] = [len(j) for j in st.J]
         res.history.append(rec)
         if st.k in snapshots:

@@ -25,12 +25,14 @@ class Criterion(C.Structure):
     _fields_ = [("mu", C.c_double), ("Kp", C.c_int), ("eps_p", C.c_double),
                 ("eps_abs", C.c_double), ("eps_rel", C.c_double), ("elim", C.c_int),
                 ("freeze_mode", C.c_int), ("stop", C.c_int), ("precision", C.c_int),
-                ("correct_every", C.c_int)]
+                ("correct_every", C.c_int), ("learn_every", C.c_int), ("learn_theta", C.c_double),
+                ("readmit", C.c_double)]
 
 
 class Stats(C.Structure):
     _fields_ = [("iters", C.c_int), ("stop_reason", C.c_int), ("refreshes", C.c_int),
-                ("active_total", C.c_int), ("r_pri", C.c_double), ("eps_pri", C.c_double),
+                ("active_total", C.c_int), ("learned_steps", C.c_int), ("readmitted", C.c_int),
+                ("r_pri", C.c_double), ("eps_pri", C.c_double),
                 ("d", C.c_double), ("eps_dual", C.c_double), ("relchange", C.c_double),
                 ("ms_total", C.c_double), ("ms_refresh", C.c_double), ("bytes_iter", C.c_double)]
 
@@ -40,7 +42,7 @@ class Stats(C.Structure):
 
 class IterRecord(C.Structure):
     _fields_ = [("k", C.c_int), ("gate", C.c_int), ("changed", C.c_int), ("active_total", C.c_int),
-                ("r_pri", C.c_double), ("eps_pri", C.c_double), ("d", C.c_double),
+                ("learned", C.c_int), ("readmitted", C.c_int), ("r_pri", C.c_double), ("eps_pri", C.c_double), ("d", C.c_double),
                 ("eps_dual", C.c_double), ("relchange", C.c_double)]
 
 
@@ -64,6 +66,8 @@ _SIGS = {
     "sadmm_get_state": (C.c_int, [_P, _P, C.POINTER(C.c_size_t)]),
     "sadmm_set_state": (C.c_int, [_P, _P, C.c_size_t]),
     "sadmm_set_profiling": (C.c_int, [_P, C.c_int]),
+    "sadmm_set_eliminator": (C.c_int, [_P, _P, C.c_int, C.c_int]),
+    "sadmm_features": (C.c_int, [_P, _P]),
     "sadmm_profile": (C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(C.c_longlong), C.c_int]),
     "sadmm_launch_count": (C.c_longlong, []),
     "sadmm_destroy": (None, [_P]),
@@ -76,6 +80,7 @@ _SIGS = {
                                C.c_int, C.POINTER(C.c_int), _P]),
     "sadmm_spd_apply": (C.c_int, [_P, C.c_int, C.c_int, _P, _P, _P]),
     "sadmm_factor_downdate": (C.c_int, [_P, C.c_int, _P, C.c_int, C.c_double, _P, _P]),
+    "sadmm_factor_update": (C.c_int, [_P, C.c_int, _P, C.c_int, C.c_double, C.c_int, _P, _P]),
     "sadmm_batch_create": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double,
                                      C.POINTER(C.c_double), C.POINTER(Criterion), C.POINTER(_P)]),
     "sadmm_batch_set_stream": (C.c_int, [_P, _P]),
@@ -136,7 +141,10 @@ def check(status):
 def default_criterion(**kw):
     c = Criterion()
     load().sadmm_default_criterion(C.byref(c))
+    names = {f for f, _ in Criterion._fields_}
     for k, v in kw.items():
+        if k not in names:
+            raise TypeError(f"unknown criterion field {k!r}")
         setattr(c, k, v)
     return c
 
@@ -264,6 +272,22 @@ class Solver:
         n = (C.c_longlong * 8)()
         k = self.lib.sadmm_profile(self.h, ms, n, 8)
         return {self.PHASES[i]: (ms[i], n[i]) for i in range(k)}
+
+    def set_eliminator(self, params, H, W):
+        """Proposal network for elim = 2: flat FP32 parameters (numpy or torch), or None."""
+        if params is None:
+            check(self.lib.sadmm_set_eliminator(self.h, None, 0, 0))
+            return
+        if isinstance(params, np.ndarray):
+            params = np.ascontiguousarray(params, dtype=np.float32)
+        check(self.lib.sadmm_set_eliminator(self.h, _ptr(params), int(H), int(W)))
+
+    def features(self, out=None):
+        """(6, N) features of the current state (numpy, or into `out`)."""
+        if out is None:
+            out = np.empty((6, self.N), dtype=np.float32)
+        check(self.lib.sadmm_features(self.h, _ptr(out)))
+        return out
 
     def get_state(self):
         n = C.c_size_t()
@@ -454,6 +478,14 @@ def factor(A, idx, mu, rho, stream=0):
     check(load().sadmm_factor(_ptr(A), KM, A.shape[0], _ptr(idx), nidx, float(mu), float(rho),
                               _ptr(F), npad, C.byref(form), C.c_void_p(stream)))
     return F, form.value, n
+
+
+def factor_update(A, E, mu, sign, W, stream=0):
+    """In place: W <- factor with the columns E removed (sign +1) or added (sign -1)."""
+    KM = A.shape[1]
+    check(load().sadmm_factor_update(_ptr(A), KM, _ptr(E), int(E.numel()), float(mu), int(sign), _ptr(W),
+                                     C.c_void_p(stream)))
+    return W
 
 
 def factor_downdate(A, E, mu, W, stream=0):

@@ -48,6 +48,8 @@ struct Sensor {
   float* g = nullptr;        // N, Re(A_J^H r) in list order (primal form)
   int* J = nullptr;          // N, active list
   int* E = nullptr;          // N, pixels removed in the last SSC pass
+  int* F = nullptr;          // N, frozen pixels at the last learned step (elim = 2)
+  int* R = nullptr;          // N, pixels re-admitted at the last learned step (elim = 2)
   double* fb[3] = {nullptr, nullptr, nullptr};   // FP64 factor buffers
   float2* fhl[3] = {nullptr, nullptr, nullptr};  // their (hi, lo) FP32-pair copies, used every iteration
   double* dinv = nullptr;      // diagonal-block inverses; also the downdate's n x 32 scratch
@@ -86,13 +88,23 @@ struct Ctx {
   double* red = nullptr;
   unsigned int* ticket = nullptr;
   IterScalars* scal = nullptr;
-  int* counts = nullptr;       // 2Q: |J_q|, |E_q|
+  int* counts = nullptr;       // 4Q: |J_q|, |E_q|, |F_q|, |R_q|
   int* dstatus = nullptr;      // Q factor status flags
   IterScalars* h_scal = nullptr;
   int* h_counts = nullptr;
   int* h_status = nullptr;
   int npad_max = 0;
   int k = 0;
+  // learned proposal and re-admission (elim = 2)
+  sadmm_cnn_t cnn = nullptr;   // owned
+  int cnn_H = 0, cnn_W = 0;
+  float* feat = nullptr;       // 6 x N features
+  float* prob = nullptr;       // N proposal probabilities
+  uint8_t* mask = nullptr;     // Q x 2N: active flags, re-admission flags
+  bool learned_now = false;    // the iteration last launched ran the learned step
+  bool learned_due() const {
+    return crit.elim == 2 && cnn != nullptr && (k + 1) % crit.learn_every == 0 && k + 1 >= std::max(crit.Kp, 4);
+  }
   std::vector<sadmm_iter_record> hist;
   bool corr_due = true;        // precision 3/4: refresh the lo-plane products next iteration
   int last_corr_k = 0;
@@ -164,6 +176,8 @@ struct Ctx {
     if (h_scal) cudaFreeHost(h_scal);
     if (h_counts) cudaFreeHost(h_counts);
     if (h_status) cudaFreeHost(h_status);
+    if (cnn) sadmm_cnn_destroy(cnn);
+    cnn = nullptr;
     for (auto& e : ev) cudaEventDestroy(e);
     ev.clear();
     ev_used.clear();
@@ -245,16 +259,17 @@ int refresh(Ctx& c, const std::vector<int>& qs, bool full_set) {
 }
 
 // Rank-|E| downdate of Woodbury-form factors (see run_downdate), in passes of
-// at most kDowndateMax removed columns.  Sensors whose downdate fails (the
-// small system is not numerically positive definite) are returned in `failed`.
-int downdate(Ctx& c, const std::vector<int>& qs, std::vector<int>* failed) {
+// at most kDowndateMax removed columns; with `add` the rank-|R| update for the
+// re-admitted columns instead.  Sensors whose downdate fails (the small system
+// is not numerically positive definite) are returned in `failed`.
+int downdate(Ctx& c, const std::vector<int>& qs, std::vector<int>* failed, bool add = false) {
   if (qs.empty()) return SADMM_OK;
   std::vector<int> dst(c.Q), etot(c.Q);
   int max_e = 0;
   for (int q : qs) {
     Sensor& S = c.s[q];
     dst[q] = (S.cur == S.full) ? (S.full + 1) % 3 : S.cur;
-    etot[q] = c.h_counts[c.Q + q];
+    etot[q] = c.h_counts[(add ? 3 : 1) * c.Q + q];
     max_e = std::max(max_e, etot[q]);
   }
   SADMM_CUDA_TRY(cudaMemsetAsync(c.dstatus, 0, sizeof(int) * c.Q, c.st));
@@ -266,11 +281,12 @@ int downdate(Ctx& c, const std::vector<int>& qs, std::vector<int>* failed) {
       Sensor& S = c.s[q];
       if (etot[q] <= off) continue;
       DowndateJob j;
-      j.A = S.A; j.E = S.E + off; j.e = std::min(kDowndateMax, etot[q] - off); j.n = n;
+      j.A = S.A; j.E = (add ? S.R : S.E) + off; j.e = std::min(kDowndateMax, etot[q] - off); j.n = n;
       j.Wsrc = (off == 0) ? S.fb[S.cur] : S.fb[dst[q]];
       j.Wdst = S.fb[dst[q]];
       j.P = S.dinv; j.Spart = S.dd; j.S = S.dd + nblk * kDowndateMax * kDowndateMax;
       j.slot = q;
+      j.sign = add ? -1 : 1;
       jobs.push_back(j);
     }
     SADMM_TRY(run_downdate(jobs.data(), (int)jobs.size(), c.KM, c.crit.mu, c.dstatus, c.st));
@@ -335,6 +351,39 @@ int reset_state(Ctx& c) {
 int launch_split_products_fwd(Ctx& c, const SolverView& sv, bool corr);
 int launch_split_products_adj(Ctx& c, const SolverView& sv, bool corr);
 
+// Algorithm 1 on the device.  At a learned iteration (elim = 2) it is preceded
+// by the re-admission test of the pixels frozen before this pass (flags in the
+// second half of each sensor's mask row) and by the proposal network, whose
+// probabilities the SSC pass uses to drop pixels in addition to Algorithm 1.
+int launch_elimination(Ctx& c, const SolverView& sv, IterScalars* out) {
+  c.learned_now = c.learned_due();
+  std::vector<int*> Jp(c.Q), Ep(c.Q), Fp(c.Q);
+  for (int q = 0; q < c.Q; ++q) { Jp[q] = c.s[q].J; Ep[q] = c.s[q].E; Fp[q] = c.s[q].F; }
+  c.mark(6, true);
+  if (c.learned_now) {
+    // residual of the whole model, y' - A_J x_J = y - A x, into r (free until the next iteration)
+    std::vector<ColumnSet> fw;
+    std::vector<ReadmitSet> rs;
+    for (int q = 0; q < c.Q; ++q) {
+      Sensor& S = c.s[q];
+      if (S.cnt > 0) fw.push_back(ColumnSet{S.A, S.J, S.cnt, q, nullptr, S.yp, S.r});
+      else SADMM_CUDA_TRY(cudaMemcpyAsync(S.r, S.yp, c.KM * sizeof(float2), cudaMemcpyDeviceToDevice, c.st));
+      if (S.cnt < c.N) rs.push_back(ReadmitSet{S.A, S.F, c.N - S.cnt, q, S.r});
+    }
+    if (!fw.empty())
+      SADMM_TRY(launch_forward(fw.data(), (int)fw.size(), c.KM, kVX, sv, c.partial, c.partial_cap, c.st));
+    SADMM_TRY(launch_frozen_lists(sv, Jp.data(), c.counts, c.mask, Fp.data(), c.counts + 2 * c.Q, c.st));
+    SADMM_TRY(launch_readmit_check(rs.data(), (int)rs.size(), c.KM, sv, c.crit.readmit * c.crit.eps_p, c.mask,
+                                   c.st));
+    SADMM_TRY(launch_features(sv, c.k + 1, c.crit.eps_p, c.feat, c.st));
+    SADMM_TRY(sadmm_cnn_forward(c.cnn, c.feat, 1, c.prob, (void*)c.st));
+  }
+  SADMM_TRY(launch_ssc(sv, Jp.data(), Ep.data(), c.counts, c.crit.eps_p, c.crit.freeze_mode, out, c.prob,
+                       (float)c.crit.learn_theta, c.learned_now ? 1 : 0, c.st));
+  c.mark(6, false);
+  return SADMM_OK;
+}
+
 int launch_iteration(Ctx& c, IterScalars* out) {
   const SolverView sv = c.view();
   if (c.crit.precision > 0) {
@@ -366,13 +415,7 @@ int launch_iteration(Ctx& c, IterScalars* out) {
     c.mark(5, true);
     SADMM_TRY(launch_residuals(sv, c.crit, c.red, c.ticket, out, c.k + 1, c.st));
     c.mark(5, false);
-    if (c.crit.elim) {
-      std::vector<int*> Jp(c.Q), Ep(c.Q);
-      for (int q = 0; q < c.Q; ++q) { Jp[q] = c.s[q].J; Ep[q] = c.s[q].E; }
-      c.mark(6, true);
-      SADMM_TRY(launch_ssc(sv, Jp.data(), Ep.data(), c.counts, c.crit.eps_p, c.crit.freeze_mode, out, c.st));
-      c.mark(6, false);
-    }
+    if (c.crit.elim) SADMM_TRY(launch_elimination(c, sv, out));
     return SADMM_OK;
   }
   std::vector<ColumnSet> fw;
@@ -415,14 +458,7 @@ int launch_iteration(Ctx& c, IterScalars* out) {
   c.mark(5, true);
   SADMM_TRY(launch_residuals(sv, c.crit, c.red, c.ticket, out, c.k + 1, c.st));
   c.mark(5, false);
-  if (c.crit.elim) {
-    std::vector<int*> Jp(c.Q), Ep(c.Q);
-    for (int q = 0; q < c.Q; ++q) { Jp[q] = c.s[q].J; Ep[q] = c.s[q].E; }
-    c.mark(6, true);
-    SADMM_TRY(launch_ssc(sv, Jp.data(), Ep.data(), c.counts, c.crit.eps_p, c.crit.freeze_mode,
-                         out, c.st));
-    c.mark(6, false);
-  }
+  if (c.crit.elim) SADMM_TRY(launch_elimination(c, sv, out));
   return SADMM_OK;
 }
 
@@ -514,6 +550,45 @@ int apply_changes(Ctx& c, const std::vector<int>& changed) {
   return refresh(c, full, false);
 }
 
+// After a learned SSC pass: rebuild each J_q as the ordered union of the kept
+// and the re-admitted pixels (flags set by the re-admission test), unfold the
+// re-admitted pixels from y' (freeze mode 0) and add their columns to the
+// factors (rank update of a Woodbury form, otherwise a refresh).
+int readmit(Ctx& c, int* total) {
+  *total = 0;
+  const SolverView sv = c.view();
+  std::vector<int*> Jp(c.Q), Rp(c.Q);
+  for (int q = 0; q < c.Q; ++q) { Jp[q] = c.s[q].J; Rp[q] = c.s[q].R; }
+  SADMM_TRY(launch_rebuild_lists(sv, Jp.data(), Rp.data(), c.mask, c.counts, c.counts + 3 * c.Q,
+                                 2.0 * c.crit.eps_p, c.st));
+  SADMM_CUDA_TRY(cudaMemcpyAsync(c.h_counts, c.counts, 4 * c.Q * sizeof(int), cudaMemcpyDeviceToHost, c.st));
+  SADMM_CUDA_TRY(cudaStreamSynchronize(c.st));
+  std::vector<int> added;
+  std::vector<ColumnSet> unfold;
+  for (int q = 0; q < c.Q; ++q) {
+    Sensor& S = c.s[q];
+    const int nr = c.h_counts[3 * c.Q + q];
+    if (nr == 0) continue;
+    added.push_back(q);
+    S.cnt = c.h_counts[q];
+    *total += nr;
+    unfold.push_back(ColumnSet{S.A, S.R, nr, q, nullptr, S.yp, S.yp});
+  }
+  if (added.empty()) return SADMM_OK;
+  if (c.crit.freeze_mode == 0)
+    SADMM_TRY(launch_forward(unfold.data(), (int)unfold.size(), c.KM, kVNegX, sv, c.partial, c.partial_cap, c.st));
+  std::vector<int> up, full;
+  for (int q : added) {
+    const Sensor& S = c.s[q];
+    const int e = c.h_counts[3 * c.Q + q];
+    if (S.woodbury && S.cum_dd + e <= std::max(kDowndateMax, c.KM / 2)) up.push_back(q);
+    else full.push_back(q);
+  }
+  SADMM_TRY(downdate(c, up, &full, true));
+  c.corr_due = true;
+  return refresh(c, full, false);
+}
+
 double iter_bytes(const Ctx& c) {
   double b = 0.0;
   for (const Sensor& S : c.s) {
@@ -524,9 +599,11 @@ double iter_bytes(const Ctx& c) {
   return b;
 }
 
-sadmm_iter_record make_record(const Ctx& c, const IterScalars& r, int changed) {
+sadmm_iter_record make_record(const Ctx& c, const IterScalars& r, int changed, int learned = 0,
+                              int readmitted = 0) {
   sadmm_iter_record rec;
   rec.k = r.k; rec.gate = r.gate; rec.changed = changed;
+  rec.learned = learned; rec.readmitted = readmitted;
   rec.active_total = 0;
   for (const Sensor& S : c.s) rec.active_total += S.cnt;
   rec.r_pri = r.r_pri; rec.eps_pri = r.eps_pri; rec.d = r.d; rec.eps_dual = r.eps_dual;
@@ -537,7 +614,7 @@ sadmm_iter_record make_record(const Ctx& c, const IterScalars& r, int changed) {
 int run(Ctx& c, float* x_out, int iters, double tol, sadmm_stats* st) {
   const double t0 = now_ms();
   double t_ref = 0.0, bytes = 0.0;
-  int refreshes = 0, stop_reason = 0, done = 0;
+  int refreshes = 0, stop_reason = 0, done = 0, learned_steps = 0, readmitted = 0;
   c.hist.clear();
   // Without elimination and without a residual-based stop nothing decided on
   // the host depends on an iteration's scalars: run the iterations back to
@@ -573,7 +650,7 @@ int run(Ctx& c, float* x_out, int iters, double tol, sadmm_stats* st) {
       bytes += iter_bytes(c);
       SADMM_TRY(launch_iteration(c, c.scal));
       SADMM_CUDA_TRY(cudaMemcpyAsync(c.h_scal, c.scal, sizeof(IterScalars), cudaMemcpyDeviceToHost, c.st));
-      SADMM_CUDA_TRY(cudaMemcpyAsync(c.h_counts, c.counts, 2 * c.Q * sizeof(int), cudaMemcpyDeviceToHost, c.st));
+      SADMM_CUDA_TRY(cudaMemcpyAsync(c.h_counts, c.counts, 4 * c.Q * sizeof(int), cudaMemcpyDeviceToHost, c.st));
       SADMM_CUDA_TRY(cudaStreamSynchronize(c.st));
       c.collect();
       c.k += 1;
@@ -584,7 +661,7 @@ int run(Ctx& c, float* x_out, int iters, double tol, sadmm_stats* st) {
         return SADMM_ENONFINITE;
       }
       std::vector<int> changed;
-      if (c.crit.elim && r.gate) {
+      if (c.crit.elim && (r.gate || c.learned_now)) {
         for (int q = 0; q < c.Q; ++q) {
           if (c.h_counts[c.Q + q] > 0) {
             changed.push_back(q);
@@ -602,7 +679,19 @@ int run(Ctx& c, float* x_out, int iters, double tol, sadmm_stats* st) {
         t_ref += now_ms() - ta;
         refreshes += 1;
       }
-      c.hist.push_back(make_record(c, r, (int)changed.size()));
+      int nre = 0;
+      if (c.learned_now) {
+        const double ta = now_ms();
+        c.mark(7, true);
+        SADMM_TRY(readmit(c, &nre));
+        c.mark(7, false);
+        SADMM_CUDA_TRY(cudaStreamSynchronize(c.st));
+        c.collect();
+        t_ref += now_ms() - ta;
+        learned_steps += 1;
+        readmitted += nre;
+      }
+      c.hist.push_back(make_record(c, r, (int)changed.size(), c.learned_now ? 1 : 0, nre));
       if (c.crit.stop == 0 && tol > 0.0 && r.relchange <= tol) { stop_reason = 1; break; }
       if (c.crit.stop == 1 && r.r_pri <= r.eps_pri && r.d <= r.eps_dual) { stop_reason = 2; break; }
     }
@@ -617,6 +706,8 @@ int run(Ctx& c, float* x_out, int iters, double tol, sadmm_stats* st) {
     st->iters = done;
     st->stop_reason = stop_reason;
     st->refreshes = refreshes;
+    st->learned_steps = learned_steps;
+    st->readmitted = readmitted;
     for (const Sensor& S : c.s) st->active_total += S.cnt;
     if (!c.hist.empty()) {
       const sadmm_iter_record& h = c.hist.back();
@@ -676,6 +767,9 @@ void sadmm_default_criterion(sadmm_criterion* c) {
   c->stop = 0;
   c->precision = 0;
   c->correct_every = 4;
+  c->learn_every = 10;
+  c->learn_theta = 0.5;
+  c->readmit = 10.0;
 }
 
 int sadmm_set_allocator(sadmm_alloc_fn alloc, sadmm_free_fn release, void* user) {
@@ -699,7 +793,9 @@ int sadmm_create(int Q, int M, int K, int N, double rho, double lambda, const sa
   const long long KM = (long long)K * M;
   if (Q < 1 || Q > kMaxSets || M < 1 || K < 1 || N < 1 || KM % 32 != 0 || KM > 16384 ||
       !(rho > 0.0) || !(lambda >= 0.0) || !(c.mu > 0.0) || c.Kp < 1 || c.Kp > 64 ||
-      !(c.eps_p >= 0.0) || c.elim < 0 || c.elim > 1 || c.freeze_mode < 0 || c.freeze_mode > 1 ||
+      !(c.eps_p >= 0.0) || c.elim < 0 || c.elim > 2 || c.freeze_mode < 0 || c.freeze_mode > 1 ||
+      (c.elim == 2 && (c.learn_every < 1 || !(c.eps_p > 0.0) || !(c.learn_theta >= 0.0 && c.learn_theta <= 1.0) ||
+                       !(c.readmit >= 0.0))) ||
       c.stop < 0 || c.stop > 1 || !std::isfinite(rho) || !std::isfinite(lambda) ||
       c.precision < 0 || c.precision > 4 || c.correct_every < 1) {
     set_error("sadmm_create: invalid sizes or parameters (Q=%d M=%d K=%d N=%d rho=%g lambda=%g)", Q, M,
@@ -727,6 +823,8 @@ int sadmm_create(int Q, int M, int K, int N, double rho, double lambda, const sa
     S.g = (float*)A((size_t)N * sizeof(float));
     S.J = (int*)A((size_t)N * sizeof(int));
     S.E = (int*)A((size_t)N * sizeof(int));
+    S.F = (int*)A((size_t)N * sizeof(int));
+    S.R = (int*)A((size_t)N * sizeof(int));
     for (int b = 0; b < 3; ++b) S.fb[b] = (double*)A(fbytes);
     for (int b = 0; b < 3; ++b) S.fhl[b] = (float2*)A(fbytes);
     S.dinv = (double*)A((size_t)ctx->npad_max * kTile * sizeof(double));
@@ -755,10 +853,13 @@ int sadmm_create(int Q, int M, int K, int N, double rho, double lambda, const sa
   ctx->red = (double*)A((size_t)residual_blocks(N) * 8 * sizeof(double));
   ctx->ticket = (unsigned int*)A(sizeof(unsigned int));
   ctx->scal = (IterScalars*)A(sizeof(IterScalars));
-  ctx->counts = (int*)A(2 * Q * sizeof(int));
+  ctx->counts = (int*)A(4 * Q * sizeof(int));
+  ctx->feat = (float*)A((size_t)6 * N * sizeof(float));
+  ctx->prob = (float*)A((size_t)N * sizeof(float));
+  ctx->mask = (uint8_t*)A((size_t)Q * 2 * N);
   ctx->dstatus = (int*)A(Q * sizeof(int));
   if (ok && (cudaMallocHost(&ctx->h_scal, sizeof(IterScalars)) != cudaSuccess ||
-             cudaMallocHost(&ctx->h_counts, 2 * Q * sizeof(int)) != cudaSuccess ||
+             cudaMallocHost(&ctx->h_counts, 4 * Q * sizeof(int)) != cudaSuccess ||
              cudaMallocHost(&ctx->h_status, Q * sizeof(int)) != cudaSuccess))
     ok = false;
   if (!ok) {
@@ -963,6 +1064,39 @@ int sadmm_set_state(sadmm_t ctx, const void* buf, size_t bytes) {
   return refresh(*ctx, changed, false);
 }
 
+int sadmm_set_eliminator(sadmm_t ctx, const float* params, int H, int W) {
+  SADMM_TRY(sadmm::valid_ctx(ctx));
+  SADMM_CUDA_TRY(cudaStreamSynchronize(ctx->st));
+  if (!params) {
+    if (ctx->cnn) sadmm_cnn_destroy(ctx->cnn);
+    ctx->cnn = nullptr;
+    return SADMM_OK;
+  }
+  if (H < 1 || W < 1 || (long long)H * W != ctx->N) {
+    set_error("sadmm_set_eliminator: grid %d x %d does not hold N = %d pixels", H, W, ctx->N);
+    return SADMM_EINVAL;
+  }
+  if (ctx->cnn && (ctx->cnn_H != H || ctx->cnn_W != W)) {
+    sadmm_cnn_destroy(ctx->cnn);
+    ctx->cnn = nullptr;
+  }
+  if (!ctx->cnn) {
+    SADMM_TRY(sadmm_cnn_create(H, W, 1, &ctx->cnn));
+    ctx->cnn_H = H;
+    ctx->cnn_W = W;
+  }
+  return sadmm_cnn_set_params(ctx->cnn, params);
+}
+
+int sadmm_features(sadmm_t ctx, float* out) {
+  SADMM_TRY(sadmm::valid_ctx(ctx));
+  if (!out) { set_error("sadmm_features: out is NULL"); return SADMM_EINVAL; }
+  SADMM_TRY(sadmm::launch_features(ctx->view(), ctx->k, ctx->crit.eps_p, ctx->feat, ctx->st));
+  SADMM_CUDA_TRY(cudaMemcpyAsync(out, ctx->feat, (size_t)6 * ctx->N * sizeof(float), cudaMemcpyDefault, ctx->st));
+  SADMM_CUDA_TRY(cudaStreamSynchronize(ctx->st));
+  return SADMM_OK;
+}
+
 int sadmm_set_profiling(sadmm_t ctx, int on) {
   SADMM_TRY(sadmm::valid_ctx(ctx));
   SADMM_CUDA_TRY(cudaStreamSynchronize(ctx->st));
@@ -1078,9 +1212,15 @@ int sadmm_factor(const float* A, int KM, int N, const int* idx, int nidx, double
 
 int sadmm_factor_downdate(const float* A, int KM, const int* E, int e, double mu, double* W,
                           void* stream) {
+  return sadmm_factor_update(A, KM, E, e, mu, 1, W, stream);
+}
+
+int sadmm_factor_update(const float* A, int KM, const int* E, int e, double mu, int sign, double* W,
+                        void* stream) {
   using namespace sadmm;
-  if (!A || !W || KM <= 0 || KM % 32 != 0 || e < 0 || (e > 0 && !E) || !(mu > 0.0)) {
-    set_error("sadmm_factor_downdate: bad arguments");
+  if (!A || !W || KM <= 0 || KM % 32 != 0 || e < 0 || (e > 0 && !E) || !(mu > 0.0) ||
+      (sign != 1 && sign != -1)) {
+    set_error("sadmm_factor_update: bad arguments");
     return SADMM_EINVAL;
   }
   if (e == 0) return SADMM_OK;
@@ -1094,7 +1234,7 @@ int sadmm_factor_downdate(const float* A, int KM, const int* E, int e, double mu
   int rc = SADMM_OK;
   for (int off = 0; off < e && rc == SADMM_OK; off += kDowndateMax) {
     DowndateJob j{(const float2*)A, E + off, std::min(kDowndateMax, e - off), n, W, W, (double*)P,
-                  (double*)dd, (double*)dd + (size_t)div_up(n, 256) * kDowndateMax * kDowndateMax, 0};
+                  (double*)dd, (double*)dd + (size_t)div_up(n, 256) * kDowndateMax * kDowndateMax, 0, sign};
     rc = run_downdate(&j, 1, KM, mu, (int*)status, st);
   }
   int hs = 0;
@@ -1106,7 +1246,7 @@ int sadmm_factor_downdate(const float* A, int KM, const int* E, int e, double mu
   cudaFreeAsync(dd, st);
   cudaFreeAsync(status, st);
   if (rc != SADMM_OK) return rc;
-  if (hs) { set_error("sadmm_factor_downdate: downdated system not positive definite"); return SADMM_ENONFINITE; }
+  if (hs) { set_error("sadmm_factor_update: updated system not positive definite"); return SADMM_ENONFINITE; }
   return SADMM_OK;
 }
 

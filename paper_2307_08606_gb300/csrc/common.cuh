@@ -54,7 +54,8 @@ inline int round_up(int a, int b) { return (a + b - 1) / b * b; }
 enum VMode : int {
   kVAdmm = 0,   // v = x_q - x_bar + z_bar - s   (Eq. 3, x_q-update right-hand side)
   kVX = 1,      // v = x_q                       (fold of frozen pixels into y')
-  kVExplicit = 2// v = caller array indexed by pixel
+  kVExplicit = 2,// v = caller array indexed by pixel
+  kVNegX = 3     // v = -x_q                      (unfold of re-admitted pixels)
 };
 
 // Device-resident per-iteration scalars written by the residual kernel
@@ -127,7 +128,23 @@ int residual_blocks(int N);
 // place (order kept), lists removed pixels in E[q], zeroes their ring entries
 // (and x in zero mode).  counts[q] = new |J_q|, counts[Q + q] = |E_q|.
 int launch_ssc(const SolverView& sv, int* const* J, int* const* E, int* counts, double eps_p,
-               int freeze_mode, const IterScalars* sc, cudaStream_t st);
+               int freeze_mode, const IterScalars* sc, const float* prob, float theta, int learned_now,
+               cudaStream_t st);
+// Learned proposal and re-admission (learned.cu)
+int launch_features(const SolverView& sv, int k_done, double eps_p, float* out, cudaStream_t st);
+int launch_frozen_lists(const SolverView& sv, int* const* J, const int* counts, uint8_t* mask, int* const* F,
+                        int* fcounts, cudaStream_t st);
+struct ReadmitSet {
+  const float2* A;
+  const int* F;        // frozen pixels of the sensor
+  int n;
+  int q;
+  const float2* r;     // y'_q - A_J x_J
+};
+int launch_readmit_check(const ReadmitSet* sets, int nsets, int KM, const SolverView& sv, double thr,
+                         uint8_t* mask, cudaStream_t st);
+int launch_rebuild_lists(const SolverView& sv, int* const* J, int* const* R, uint8_t* mask, int* counts,
+                         int* rcounts, double ring_fill, cudaStream_t st);
 int launch_recompute_xbar(const SolverView& sv, cudaStream_t st);
 int launch_scale(const float* in, float a, float* out, int n, cudaStream_t st);
 
@@ -175,7 +192,9 @@ int run_factor(const FactorJob* jobs, int njobs, int KM, double mu, double rho, 
 // Rank-e downdate of a Woodbury-form factor after removing e <= kDowndateMax
 // columns E from the active set (Eq. 3's system without those pixels):
 //   (G - mu U U^T)^{-1} = W + mu T T^T,  P = W U,  S = I - mu U^T P = L L^T,
-//   T = P L^{-T},  U = B_E (interleaved real form of the removed columns).
+//   T = P L^{-T},  U = B_E (interleaved real form of the removed columns);
+// with sign = -1 the rank-e update after adding columns back:
+//   (G + mu U U^T)^{-1} = W - mu T T^T,  S = I + mu U^T P.
 constexpr int kDowndateMax = 32;
 struct DowndateJob {
   const float2* A;
@@ -188,6 +207,7 @@ struct DowndateJob {
   double* Spart;         // ceil(n/256) x kDowndateMax^2 partial sums of U^T P
   double* S;             // kDowndateMax^2: the inverse Cholesky factor of S
   int slot;              // index of this job's failure flag in the status array
+  int sign;              // +1 remove the columns, -1 add them
 };
 int run_downdate(const DowndateJob* jobs, int njobs, int KM, double mu, int* d_status, cudaStream_t st);
 size_t downdate_scratch_doubles(int n);

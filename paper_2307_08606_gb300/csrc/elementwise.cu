@@ -143,9 +143,11 @@ struct SscSet {
 // to 0.
 __global__ void __launch_bounds__(kSscThreads)
 ssc_kernel(const __grid_constant__ SetBlock<SscSet> sets, const __grid_constant__ SolverView sv,
-           int* __restrict__ counts, double eps_p, int freeze_mode, const IterScalars* sc) {
+           int* __restrict__ counts, double eps_p, int freeze_mode, const IterScalars* sc,
+           const float* __restrict__ prob, float theta, int learned_now) {
   const int q = blockIdx.x;
-  if (!sc->gate) {
+  const int gate = sc->gate;
+  if (!gate && !learned_now) {
     if (threadIdx.x == 0) counts[sv.Q + q] = 0;
     return;
   }
@@ -167,7 +169,9 @@ ssc_kernel(const __grid_constant__ SetBlock<SscSet> sets, const __grid_constant_
       double z = 0.0;
       for (int t = 0; t < sv.Kp; ++t) z += fabs((double)sv.ring[((size_t)t * sv.Q + q) * N + pix]);
       z /= (double)sv.Kp;
-      keep = z >= eps_p;
+      keep = gate ? (z >= eps_p) : true;
+      // learned proposal: drop pixels the network marks as converged
+      if (learned_now && prob[pix] > theta) keep = false;
     }
     const bool rem = valid && !keep;
     const unsigned bk = __ballot_sync(0xffffffffu, keep);
@@ -238,11 +242,13 @@ int launch_residuals(const SolverView& sv, const sadmm_criterion& c, double* par
 }
 
 int launch_ssc(const SolverView& sv, int* const* J, int* const* E, int* counts, double eps_p,
-               int freeze_mode, const IterScalars* sc, cudaStream_t st) {
+               int freeze_mode, const IterScalars* sc, const float* prob, float theta, int learned_now,
+               cudaStream_t st) {
   if (sv.Q > kMaxSets) return SADMM_EINVAL;
   SetBlock<SscSet> blk;
   for (int q = 0; q < sv.Q; ++q) blk.v[q] = SscSet{J[q], E[q]};
-  ssc_kernel<<<sv.Q, kSscThreads, 0, st>>>(blk, sv, counts, eps_p, freeze_mode, sc);
+  ssc_kernel<<<sv.Q, kSscThreads, 0, st>>>(blk, sv, counts, eps_p, freeze_mode, sc, prob, theta,
+                                           learned_now && prob ? 1 : 0);
   SADMM_LAUNCH_CHECK();
   return SADMM_OK;
 }

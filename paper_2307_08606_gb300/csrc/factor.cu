@@ -421,7 +421,7 @@ dd_chol_kernel(const __grid_constant__ DdBlock jobs, double mu, int* status) {
   const int nblk = (jb.n + 255) / 256;
   double sum = 0.0;
   for (int k = 0; k < nblk; ++k) sum += jb.Spart[((size_t)k * DM + a) * DM + b];
-  L[a][b] = (a < jb.e && b < jb.e) ? ((a == b ? 1.0 : 0.0) - mu * sum) : (a == b ? 1.0 : 0.0);
+  L[a][b] = (a < jb.e && b < jb.e) ? ((a == b ? 1.0 : 0.0) - jb.sign * mu * sum) : (a == b ? 1.0 : 0.0);
   __syncthreads();
   for (int j = 0; j < DM; ++j) {
     double d = L[j][j];
@@ -505,7 +505,7 @@ dd_w_kernel(const __grid_constant__ DdBlock jobs, double mu) {
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
       const size_t i = bi * T + ty + 16 * u, j = bj * T + tx + 16 * v;
-      const double val = jb.Wsrc[i * n + j] + mu * acc[u][v];
+      const double val = jb.Wsrc[i * n + j] + jb.sign * mu * acc[u][v];
       jb.Wdst[i * n + j] = val;
       if (bi != bj) jb.Wdst[j * n + i] = val;
     }

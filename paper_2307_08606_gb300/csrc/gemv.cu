@@ -36,6 +36,7 @@ __device__ __forceinline__ float v_of(VMode mode, const SolverView& sv, int q, i
   if (mode == kVExplicit) return vexp[pix];
   float xq = sv.x[(size_t)q * sv.N + pix];
   if (mode == kVX) return xq;
+  if (mode == kVNegX) return -xq;
   return xq - sv.xbar[pix] + sv.zbar[pix] - sv.s[pix];
 }
 

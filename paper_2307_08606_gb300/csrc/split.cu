@@ -52,6 +52,7 @@ __device__ __forceinline__ float v_split(VMode mode, const SolverView& sv, int q
   if (mode == kVExplicit) return vexp[pix];
   const float xq = sv.x[(size_t)q * sv.N + pix];
   if (mode == kVX) return xq;
+  if (mode == kVNegX) return -xq;
   return xq - sv.xbar[pix] + sv.zbar[pix] - sv.s[pix];
 }
 

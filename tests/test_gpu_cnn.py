@@ -6,6 +6,7 @@ import numpy as np
 import pytest
 
 import oracle.cnn as ocnn
+import oracle.learned as ol
 import scenegen
 
 pytestmark = pytest.mark.gpu
@@ -35,7 +36,9 @@ def test_forward_and_gradient_match_fp64(B, Bn, H, W):
     net = B.CNN(H, W, max_batch=Bn)
     p = scenegen.cnn_init(11, scale=0.9, head_bias=-0.5)
     net.set_params(p)
-    pr = net.params(rounded=True).astype(np.float64)
+    pr = ol.round_bf16(p)
+    # the weights the kernels use are exactly the round-to-nearest-even BF16 values
+    assert np.array_equal(net.params(rounded=True).astype(np.float64), pr)
     x, y = _batch(H + W, Bn, H, W)
     xt, yt = torch.from_numpy(x).to(dev), torch.from_numpy(y).to(dev)
     prob = net.forward(xt).cpu().numpy()

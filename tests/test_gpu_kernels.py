@@ -178,3 +178,27 @@ def test_factor_downdate_matches_fresh_inverse(B, KM, N, e):
     cond = np.linalg.cond(G)
     assert np.max(np.abs(Wd - ref)) <= 1e-14 * cond * n * np.max(np.abs(ref))
     assert np.array_equal(Wd, Wd.T)
+
+
+@pytest.mark.parametrize("KM,N,e", [(32, 300, 5), (128, 700, 40), (256, 1024, 33)])
+def test_factor_rank_update_adds_columns(B, KM, N, e):
+    """Rank-e update with sign -1 (columns re-admitted) of the Woodbury factor of
+    a reduced set equals the FP64 inverse of the Gram of the enlarged set."""
+    A = _operator(KM, N, seed=KM + 5 * N + e, radar=(KM == 256))
+    mu, rho = 0.8, 1.3
+    s = scenegen.Stream(17, e)
+    R = np.sort(s.permutation(N)[:e]).astype(np.int32)
+    J = np.setdiff1d(np.arange(N), R).astype(np.int32)
+    dev = torch.device("cuda:0")
+    At = torch.from_numpy(A).to(dev)
+    W, form, n = B.factor(At, torch.from_numpy(J).to(dev), mu, rho)
+    assert form == 1
+    B.factor_update(At, torch.from_numpy(R).to(dev), mu, -1, W)
+    torch.cuda.synchronize()
+    Wu = W.cpu().numpy()[:n, :n]
+    Bm = _interleaved_real_form(A, np.arange(N))
+    G = rho * np.eye(n) + mu * Bm @ Bm.T
+    ref = np.linalg.inv(G)
+    cond = np.linalg.cond(G)
+    assert np.max(np.abs(Wu - ref)) <= 1e-14 * cond * n * np.max(np.abs(ref))
+    assert np.array_equal(Wu, Wu.T)

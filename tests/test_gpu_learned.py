@@ -1,0 +1,236 @@
+"""Learned elimination step (elim = 2) on the GPU against the FP64 oracle:
+features, the proposal-and-re-admission step one iteration at a time from the
+oracle's state, a free run, and the C ABI's argument checks.
+
+Decision bar: the stacked iterate within 1e-4 of the oracle's at equal k; the
+active sets after a learned step equal to the oracle's except at pixels whose
+decision is marginal in the oracle: |p_i - learn_theta| < 0.05 (FP32 features
+of tiny updates differ from FP64 by up to ~1e-2 in the log channels),
+|zeta - eps_p| < 0.1 eps_p when the gate is open, or a re-admission step within
+5 % of its threshold (the step is a difference of two FP32 sums)."""
+import dataclasses
+
+import numpy as np
+import pytest
+
+import oracle
+import oracle.cnn as ocnn
+import oracle.learned as ol
+import scenegen
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+TOL = 1e-4
+DP, DR = 0.05, 0.05
+
+
+@pytest.fixture(scope="module")
+def B():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2307_08606_gb300 import build, binding
+    build()
+    binding.load()
+    return binding
+
+
+def _solver(B, sc, rho, lam, **crit):
+    g = sc.geom
+    s = B.Solver(g.Q, g.M, g.K, g.N, rho, lam, **crit)
+    for q in range(g.Q):
+        s.set_operator(q, sc.A[q])
+    return s
+
+
+def _pack(B, sc, st, Kp):
+    g = sc.geom
+    return B.pack_state(g.Q, g.N, g.KM, Kp, st.k, st.x, st.xbar, st.zbar, st.s, st.ring, st.J,
+                        np.stack([v[: g.KM] + 1j * v[g.KM:] for v in st.yprime]))
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def _scene():
+    sc = scenegen.build_scene("small_point", seed=0)
+    return sc, 0.05 * scenegen.lambda_max(sc.A, sc.y)
+
+
+def _prepass(sc, lam, crit, st):
+    """The oracle's state one iteration after st, before any elimination pass."""
+    return oracle.sadmm(sc.A, sc.y, 1.0, lam, dataclasses.replace(crit, elim=0), iters=1, state=st).state
+
+
+def _prob(el, st, eps_p):
+    f = ol.features(st.x, st.ring, st.k, eps_p)
+    p, _ = ocnn.forward(ol.round_bf16(el.params), f.reshape(1, 6, el.H, el.W))
+    return p.reshape(-1)
+
+
+def _choose_theta(sc, lam, el, crit, k_first):
+    """A threshold in a wide gap of the oracle's probabilities at the first
+    learned step, dropping roughly a third of the pixels."""
+    st = oracle.sadmm(sc.A, sc.y, 1.0, lam, dataclasses.replace(crit, elim=0), iters=k_first).state
+    p = np.sort(_prob(el, st, crit.eps_p))
+    lo, hi = int(0.55 * len(p)), int(0.8 * len(p))
+    i = lo + int(np.argmax(np.diff(p[lo:hi + 1])))
+    return float(0.5 * (p[i] + p[i + 1]))
+
+
+def test_features_match_oracle(B):
+    sc, lam = _scene()
+    g = sc.geom
+    for Kp, k in ((5, 12), (3, 2)):
+        crit = oracle.Criterion(elim=0, Kp=Kp)
+        st = oracle.sadmm(sc.A, sc.y, 1.0, lam, crit, iters=k).state
+        s = _solver(B, sc, 1.0, lam, elim=0, Kp=Kp)
+        s.prepare()
+        s.set_state(_pack(B, sc, st, Kp))
+        got = s.features()
+        ref = ol.features(st.x, st.ring, k, crit.eps_p)
+        assert np.max(np.abs(got - ref)) <= 1e-5, (Kp, k)
+        s.close()
+
+
+def test_learned_steps_synced(B):
+    """small_point scene (Q=4, KM=256, Woodbury form): from the oracle's state at
+    k, one GPU iteration that runs the learned step (re-admission test, network,
+    Algorithm 1 with proposals, fold, downdate, unfold, rank update) against the
+    oracle at k+1."""
+    sc, lam = _scene()
+    g = sc.geom
+    el = oracle.Eliminator(scenegen.cnn_init(21), g.nx, g.nx)
+    base = oracle.Criterion(elim=2, Kp=5, learn_every=5, readmit=10.0)
+    theta = _choose_theta(sc, lam, el, base, 5)
+    crit = dataclasses.replace(base, learn_theta=theta)
+    ks = [4, 9, 14, 19, 29, 39]
+    ref = oracle.sadmm(sc.A, sc.y, 1.0, lam, crit, iters=40, snapshots=set(ks) | {k + 1 for k in ks},
+                       eliminator=el)
+    s = _solver(B, sc, 1.0, lam, elim=2, Kp=5, learn_every=5, learn_theta=theta, readmit=10.0)
+    s.set_eliminator(el.params, g.nx, g.nx)
+    s.prepare()
+    thr = crit.readmit * crit.eps_p
+    dropped = readmitted = marginal = 0
+    for k in ks:
+        s.set_state(_pack(B, sc, ref.snapshots[k], crit.Kp))
+        s.resume(1)
+        h = s.history()[-1]
+        assert h["learned"] == 1 and h["k"] == k + 1
+        want = ref.snapshots[k + 1]
+        assert _rel(s.X(), want.x) <= TOL, k
+        before = ref.snapshots[k]
+        pre = _prepass(sc, lam, crit, before)
+        prob = _prob(el, pre, crit.eps_p)
+        zeta = pre.ring.mean(axis=0)
+        gate = ref.history[k]["gate"]
+        Bq = [oracle.real_form(a) for a in sc.A]
+        for q in range(g.Q):
+            F, step = ol.readmission_steps(Bq[q], before.yprime[q], pre.x[q], before.J[q], pre.s, crit.mu, 1.0)
+            near_r = set(F[np.abs(step - thr) < DR * thr].tolist())
+            got = set(s.active(q).tolist())
+            exp = set(want.J[q].tolist())
+            dropped += len(set(before.J[q].tolist()) - exp)
+            readmitted += len(exp - set(before.J[q].tolist()))
+            for i in got ^ exp:
+                ok = (abs(prob[i] - theta) < DP or (gate and abs(zeta[q, i] - crit.eps_p) < 0.1 * crit.eps_p)
+                      or i in near_r)
+                assert ok, (k, q, i, prob[i], zeta[q, i], gate)
+                marginal += 1
+    print(f"learned steps: dropped {dropped}, re-admitted {readmitted}, marginal differences {marginal}")
+    assert dropped > 0 and readmitted > 0
+    s.close()
+
+
+def test_learned_free_run(B):
+    """400 free-running iterations on the well-posed 8x8 scene (Q=3, primal
+    form), learned steps every 5 with an untrained network that drops about a
+    third of the pixels each time: marginal decisions make the GPU and oracle
+    trajectories differ, but re-admission brings both to the optimum, so the
+    final iterates are compared with the plain oracle's (2e-3) and x_G (1e-3)."""
+    sc = scenegen.build_scene("resolved_tiny", seed=2, snr_db=30.0)
+    lam = 0.05 * scenegen.lambda_max(sc.A, sc.y)
+    g = sc.geom
+    el = oracle.Eliminator(scenegen.cnn_init(21), g.nx, g.nx)
+    base = oracle.Criterion(elim=2, Kp=4, learn_every=5, readmit=10.0)
+    theta = _choose_theta(sc, lam, el, base, 5)
+    crit = dataclasses.replace(base, learn_theta=theta)
+    plain = oracle.sadmm(sc.A, sc.y, 1.0, lam, oracle.Criterion(elim=0, Kp=4), iters=400)
+    ref = oracle.sadmm(sc.A, sc.y, 1.0, lam, crit, iters=400, eliminator=el)
+    s = _solver(B, sc, 1.0, lam, elim=2, Kp=4, learn_every=5, learn_theta=theta, readmit=10.0)
+    s.set_eliminator(el.params, g.nx, g.nx)
+    xg, st = s.solve(sc.y, 400)
+    assert st["learned_steps"] == sum(h["learned"] for h in ref.history) == 80
+    rr = sum(h.get("readmitted", 0) for h in ref.history)
+    print(f"re-admitted: GPU {st['readmitted']}, oracle {rr}; X vs plain: GPU {_rel(s.X(), plain.state.x):.2e}, "
+          f"oracle {_rel(ref.state.x, plain.state.x):.2e}")
+    assert st["readmitted"] > 0
+    assert _rel(s.X(), plain.state.x) <= 2e-3
+    assert _rel(xg, plain.xG) <= 1e-3
+    s.close()
+
+
+def test_without_network_learned_mode_is_algorithm_1(B):
+    sc, lam = _scene()
+    a = _solver(B, sc, 1.0, lam, elim=1)
+    b = _solver(B, sc, 1.0, lam, elim=2)
+    xa, _ = a.solve(sc.y, 120)
+    xb, st = b.solve(sc.y, 120)
+    assert st["learned_steps"] == 0
+    assert np.array_equal(a.X(), b.X())
+    assert all(np.array_equal(a.active(q), b.active(q)) for q in range(sc.geom.Q))
+
+
+def test_eliminator_arguments_checked(B):
+    sc, lam = _scene()
+    g = sc.geom
+    s = _solver(B, sc, 1.0, lam, elim=2)
+    with pytest.raises(B.SadmmError):
+        s.set_eliminator(scenegen.cnn_init(1), g.nx, g.nx + 1)
+    s.set_eliminator(scenegen.cnn_init(1), g.nx, g.nx)
+    s.set_eliminator(None, 0, 0)
+    with pytest.raises(B.SadmmError):
+        B.Solver(g.Q, g.M, g.K, g.N, 1.0, lam, elim=2, eps_p=0.0)
+    with pytest.raises(B.SadmmError):
+        B.Solver(g.Q, g.M, g.K, g.N, 1.0, lam, elim=2, learn_theta=1.5)
+
+
+def test_trained_proposal_on_held_out_scene(B):
+    """Train the network on plain runs of three 32x32 scenes, then solve a
+    held-out scene with Algorithm 1 alone and with the learned step.  Reported:
+    the active-set work sum_k sum_q |J_q|, the deviation of the final iterates
+    from the plain run, and the re-admissions (false eliminations caught).
+    Required: the loss falls, and the learned mode's final iterates stay as
+    close to the plain run as 5x Algorithm 1's deviation (plus 1e-3)."""
+    from paper_2307_08606_gb300 import eliminator as E
+    lam_of = lambda sc: 0.05 * scenegen.lambda_max(sc.A, sc.y)
+    train = [scenegen.build_scene("small_point", seed=s) for s in (10, 11, 12)]
+    g = train[0].geom
+    smp = E.collect(train, lam_of, g.nx, g.nx, iters=200, learn_every=10, horizon=50)
+    net = B.CNN(g.nx, g.nx, max_batch=8)
+    net.set_params(scenegen.cnn_init(5))
+    losses = E.train(net, smp, steps=300, lr=2e-3, batch=8)
+    print(f"samples {len(smp.ks)}, droppable fraction {smp.labels.mean():.3f}, "
+          f"loss {np.mean(losses[:20]):.4f} -> {np.mean(losses[-20:]):.4f}")
+    assert np.mean(losses[-20:]) < np.mean(losses[:20])
+    params = net.params()
+    sc = scenegen.build_scene("small_point", seed=13)
+    lam = lam_of(sc)
+    iters = 300
+    p = _solver(B, sc, 1.0, lam, elim=0)
+    p.solve(sc.y, iters)
+    Xp = p.X()
+    out = {}
+    for mode in (1, 2):
+        s = _solver(B, sc, 1.0, lam, elim=mode, learn_every=10, learn_theta=0.5)
+        if mode == 2:
+            s.set_eliminator(params, g.nx, g.nx)
+        _, st = s.solve(sc.y, iters)
+        work = sum(h["active_total"] for h in s.history())
+        out[mode] = dict(work=work, dev=_rel(s.X(), Xp), readmitted=st["readmitted"],
+                         active=st["active_total"], ms=st["ms_total"])
+        s.close()
+    print(f"Algorithm 1: {out[1]}")
+    print(f"learned:     {out[2]}")
+    assert out[2]["dev"] <= 5 * out[1]["dev"] + 1e-3

@@ -344,6 +344,7 @@ def _mutant(name):
     src = inspect.getsource(osadmm)
     assert src.count(old) == 1, name
     mod = types.ModuleType("oracle_mutant_" + name)
+    mod.__package__ = "oracle"               # its relative imports resolve in the oracle package
     sys.modules[mod.__name__] = mod          # dataclasses look their module up here
     try:
         exec(compile(src.replace(old, new), osadmm.__file__, "exec"), mod.__dict__)
