@@ -48,6 +48,8 @@ def parse():
                     help="keep only the first S sensors (smaller case for profiler captures)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-learned", action="store_true",
+                    help="skip the learned-step cost measurement (elim 2 on the bench scene)")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the 16-scene batched measurement (Q=8, KM=2048, N=96x96)")
     return ap.parse_args()
@@ -210,6 +212,64 @@ def batched_measure(args, dev, stream, rank):
             "ms_per_iteration": ms / (iters * reps), "operator_bytes_per_iteration": op_bytes,
             "operator_GBps_effective": op_bytes / (ms / (iters * reps) / 1e3) / 1e9,
             "gpu_launches": int(launches)}
+
+
+def learned_measure(sc, lam, dev, stream):
+    """Cost of the learned step (features, re-admission test, network, SSC with
+    proposals) on the bench workload: 40-iteration solves with elim = 2 and a
+    network whose proposals and re-admissions never fire (learn_theta = 1,
+    readmit huge), against the same solver without a network (elim = 1
+    behaviour), plus the network's forward alone on the pixel grid."""
+    import torch
+    import scenegen
+    from paper_2307_08606_gb300 import binding
+    g = sc.geom
+    s = binding.Solver(g.Q, g.M, g.K, g.N, 1.0, lam, stream=stream.cuda_stream, elim=2, learn_every=10,
+                       learn_theta=1.0, readmit=1e30)
+    for q in range(g.Q):
+        s.set_operator(q, torch.from_numpy(sc.A[q]).to(dev))
+    s.prepare()
+    y_dev = [torch.from_numpy(v).to(dev) for v in sc.y]
+    params = scenegen.cnn_init(0)
+    iters, reps = 40, 3
+    res = {}
+    for label, net in (("without", None), ("with", params)):
+        s.set_eliminator(net, g.nx, g.nx)
+        s.solve(y_dev, iters)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            _, st = s.solve(y_dev, iters)
+        torch.cuda.synchronize()
+        res[label] = (time.perf_counter() - t0) * 1e3 / reps
+        res[label + "_steps"] = st["learned_steps"]
+    s.close()
+    net = binding.CNN(g.nx, g.nx, max_batch=1)
+    net.set_params(params)
+    feat = torch.randn((1, 6, g.nx, g.nx), device=dev)
+    for _ in range(3):
+        net.forward(feat)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n = 20
+    e0.record()
+    for _ in range(n):
+        net.forward(feat)
+    e1.record()
+    torch.cuda.synchronize()
+    cnn_ms = e0.elapsed_time(e1) / n
+    net.close()
+    flops = 2.0 * g.N * (6 * 32 * 9 + 4 * 32 * 32 * 9 + 32)
+    steps = max(res["with_steps"], 1)
+    step_ms = (res["with"] - res["without"]) / steps
+    per_iter_ms = res["without"] / iters
+    return {"workload": f"elim 2 on the bench scene, {iters} iterations per solve, learned step every 10",
+            "learned_steps_per_solve": res["with_steps"],
+            "solve_ms_without_network": res["without"], "solve_ms_with_network": res["with"],
+            "learned_step_ms": step_ms, "iteration_ms_elim1": per_iter_ms,
+            "learned_step_fraction_of_iteration_amortised": step_ms / (10 * per_iter_ms),
+            "cnn_forward_ms": cnn_ms, "cnn_forward_gflop": flops / 1e9,
+            "cnn_forward_tflops": flops / (cnn_ms / 1e3) / 1e12}
 
 
 def make_scene(name, seed, sensors=0):
@@ -382,6 +442,8 @@ def main():
     }
     if not args.no_batched:
         line["batched"] = batched_measure(args, dev, stream, rank)
+    if not args.no_learned:
+        line["learned"] = learned_measure(sc, lam, dev, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
             line["cpu_baseline"] = cpu_baseline_sample(sc, lam)

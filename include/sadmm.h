@@ -344,11 +344,13 @@ int sadmm_factor_downdate(const float* A, int KM, const int* E, int e, double mu
 int sadmm_factor_update(const float* A, int KM, const int* E, int e, double mu, int sign, double* W,
                         void* stream);
 
-/* out = F u for an n x n FP64 matrix (row-major, leading dimension ldf even
- * and >= n, n <= 49152) and FP32 u; out rounded to FP32.  As in the solver, F
- * is first split into FP32 pairs (hi, lo) and the products are formed exactly
- * and summed as FP32 pairs with the error-free two-sum (about 48 significant
- * bits).  Allocates a temporary n x ldf pair copy on `stream`. */
+/* out = F u for a symmetric n x n FP64 matrix (row-major, leading dimension
+ * ldf even and >= n, n <= 49152; only the upper triangle is read) and FP32 u;
+ * out rounded to FP32.  As in the solver, the upper triangle is first packed
+ * into 64 x 64 tiles of FP32 pairs (hi, lo), and the products are formed
+ * exactly and summed as FP32 pairs with the error-free two-sum (about 48
+ * significant bits).  Allocates the packed copy and partial sums on `stream`
+ * and synchronises it.  SADMM_ETIMEOUT if a tile copy did not complete. */
 int sadmm_spd_apply(const double* F, int n, int ldf, const float* u, float* out, void* stream);
 
 #ifdef __cplusplus

@@ -51,7 +51,7 @@ struct Sensor {
   int* F = nullptr;          // N, frozen pixels at the last learned step (elim = 2)
   int* R = nullptr;          // N, pixels re-admitted at the last learned step (elim = 2)
   double* fb[3] = {nullptr, nullptr, nullptr};   // FP64 factor buffers
-  float2* fhl[3] = {nullptr, nullptr, nullptr};  // their (hi, lo) FP32-pair copies, used every iteration
+  float2* fhl[3] = {nullptr, nullptr, nullptr};  // their packed symmetric (hi, lo) pair copies, used every iteration
   double* dinv = nullptr;      // diagonal-block inverses; also the downdate's n x 32 scratch
   double* dd = nullptr;        // downdate scratch (partial sums and the small factor)
   int cum_dd = 0;              // columns downdated since the last full factorisation
@@ -85,6 +85,9 @@ struct Ctx {
   int* iota = nullptr;
   float2* partial = nullptr;
   size_t partial_cap = 0;
+  float2* spd_part = nullptr;  // per-sensor partial sums of the symmetric factor apply
+  size_t spd_part_stride = 0;
+  int* spd_err = nullptr;      // set by the factor apply if a tile copy timed out
   double* red = nullptr;
   unsigned int* ticket = nullptr;
   IterScalars* scal = nullptr;
@@ -252,8 +255,7 @@ int refresh(Ctx& c, const std::vector<int>& qs, bool full_set) {
     S.woodbury = jobs[i].woodbury;
     if (full_set) { S.full = outbuf[i]; S.full_valid = true; }
     S.cum_dd = 0;
-    const size_t np = (size_t)jobs[i].npad;
-    SADMM_TRY(launch_split_f64(S.fb[S.cur], S.fhl[S.cur], np * np, c.st));
+    SADMM_TRY(launch_pack_sym(S.fb[S.cur], jobs[i].npad, jobs[i].n, S.fhl[S.cur], c.st));
   }
   return SADMM_OK;
 }
@@ -298,7 +300,7 @@ int downdate(Ctx& c, const std::vector<int>& qs, std::vector<int>* failed, bool 
     if (c.h_status[q]) { failed->push_back(q); continue; }
     S.cur = dst[q];
     S.cum_dd += etot[q];
-    SADMM_TRY(launch_split_f64(S.fb[S.cur], S.fhl[S.cur], (size_t)n * n, c.st));
+    SADMM_TRY(launch_pack_sym(S.fb[S.cur], n, n, S.fhl[S.cur], c.st));
   }
   return SADMM_OK;
 }
@@ -396,20 +398,21 @@ int launch_iteration(Ctx& c, IterScalars* out) {
       Sensor& S = c.s[q];
       if (S.cnt == 0) continue;
       const float2* F = S.fhl[S.cur];
-      const int ld = round_up(S.n, kTile);
+      float2* part = c.spd_part + (size_t)q * c.spd_part_stride;
       if (S.woodbury)
-        spd_w.push_back(SpdSet{F, S.n, ld, reinterpret_cast<const float*>(S.r), reinterpret_cast<float*>(S.w), nullptr, q});
+        spd_w.push_back(SpdSet{F, S.n, reinterpret_cast<const float*>(S.r), reinterpret_cast<float*>(S.w), nullptr, q,
+                               part, 0});
       else
-        spd_p.push_back(SpdSet{F, S.n, ld, S.g, nullptr, S.J, q});
+        spd_p.push_back(SpdSet{F, S.n, S.g, nullptr, S.J, q, part, 0});
     }
     c.mark(1, true);
-    SADMM_TRY(launch_spd_apply(spd_w.data(), (int)spd_w.size(), false, sv, c.st));
+    SADMM_TRY(launch_spd_apply(spd_w.data(), (int)spd_w.size(), false, sv, c.spd_err, c.st));
     c.mark(1, false);
     c.mark(2, true);
     SADMM_TRY(launch_split_products_adj(c, sv, corr));
     c.mark(2, false);
     c.mark(4, true);
-    SADMM_TRY(launch_spd_apply(spd_p.data(), (int)spd_p.size(), true, sv, c.st));
+    SADMM_TRY(launch_spd_apply(spd_p.data(), (int)spd_p.size(), true, sv, c.spd_err, c.st));
     c.mark(4, false);
     if (corr) { c.corr_due = false; c.last_corr_k = c.k; }
     c.mark(5, true);
@@ -426,14 +429,14 @@ int launch_iteration(Ctx& c, IterScalars* out) {
     if (S.cnt == 0) continue;
     fw.push_back(ColumnSet{S.A, S.J, S.cnt, q, nullptr, S.yp, S.r});
     const float2* F = S.fhl[S.cur];
-    const int ld = round_up(S.n, kTile);
+    float2* part = c.spd_part + (size_t)q * c.spd_part_stride;
     if (S.woodbury) {
-      spd_w.push_back(SpdSet{F, S.n, ld, reinterpret_cast<const float*>(S.r),
-                             reinterpret_cast<float*>(S.w), nullptr, q});
+      spd_w.push_back(SpdSet{F, S.n, reinterpret_cast<const float*>(S.r), reinterpret_cast<float*>(S.w), nullptr, q,
+                             part, 0});
       adj_w.push_back(AdjointSet{S.A, S.J, S.cnt, q, S.w, nullptr});
     } else {
       adj_p.push_back(AdjointSet{S.A, S.J, S.cnt, q, S.r, S.g});
-      spd_p.push_back(SpdSet{F, S.n, ld, S.g, nullptr, S.J, q});
+      spd_p.push_back(SpdSet{F, S.n, S.g, nullptr, S.J, q, part, 0});
     }
   }
   c.mark(0, true);
@@ -441,7 +444,7 @@ int launch_iteration(Ctx& c, IterScalars* out) {
   c.mark(0, false);
   if (!spd_w.empty()) {
     c.mark(1, true);
-    SADMM_TRY(launch_spd_apply(spd_w.data(), (int)spd_w.size(), false, sv, c.st));
+    SADMM_TRY(launch_spd_apply(spd_w.data(), (int)spd_w.size(), false, sv, c.spd_err, c.st));
     c.mark(1, false);
     c.mark(2, true);
     SADMM_TRY(launch_adjoint(adj_w.data(), (int)adj_w.size(), c.KM, true, sv, c.st));
@@ -452,7 +455,7 @@ int launch_iteration(Ctx& c, IterScalars* out) {
     SADMM_TRY(launch_adjoint(adj_p.data(), (int)adj_p.size(), c.KM, false, sv, c.st));
     c.mark(3, false);
     c.mark(4, true);
-    SADMM_TRY(launch_spd_apply(spd_p.data(), (int)spd_p.size(), true, sv, c.st));
+    SADMM_TRY(launch_spd_apply(spd_p.data(), (int)spd_p.size(), true, sv, c.spd_err, c.st));
     c.mark(4, false);
   }
   c.mark(5, true);
@@ -700,7 +703,14 @@ int run(Ctx& c, float* x_out, int iters, double tol, sadmm_stats* st) {
     SADMM_TRY(launch_scale(c.zbar, (float)c.Q, c.xg, c.N, c.st));
     SADMM_CUDA_TRY(cudaMemcpyAsync(x_out, c.xg, c.N * sizeof(float), cudaMemcpyDefault, c.st));
   }
+  int spd_err = 0;
+  SADMM_CUDA_TRY(cudaMemcpyAsync(&spd_err, c.spd_err, sizeof(int), cudaMemcpyDeviceToHost, c.st));
   SADMM_CUDA_TRY(cudaStreamSynchronize(c.st));
+  if (spd_err) {
+    SADMM_CUDA_TRY(cudaMemsetAsync(c.spd_err, 0, sizeof(int), c.st));
+    set_error("factor apply: a tile copy did not complete within the wait limit");
+    return SADMM_ETIMEOUT;
+  }
   if (st) {
     memset(st, 0, sizeof *st);
     st->iters = done;
@@ -737,12 +747,12 @@ struct sadmm_ctx : Ctx {};
 namespace sadmm {
 // Operator and current factor of sensor q (for the batched form, which keeps
 // every pixel active and so uses the full-set factor).
-int single_export(sadmm_t h, int q, const float2** A, const float2** Fhl, int* n, int* ld, int* woodbury) {
+int single_export(sadmm_t h, int q, const float2** A, const double** F, int* n, int* ld, int* woodbury) {
   if (!h || q < 0 || q >= h->Q) return SADMM_EINVAL;
   const sadmm::Sensor& S = h->s[q];
   if (!S.full_valid) { set_error("factor of sensor %d not prepared", q); return SADMM_ENOTREADY; }
   *A = S.A;
-  *Fhl = S.fhl[S.full];
+  *F = S.fb[S.full];
   int nn, wb;
   factor_dims(*h, h->N, &nn, &wb);
   *n = nn;
@@ -813,6 +823,7 @@ int sadmm_create(int Q, int M, int K, int N, double rho, double lambda, const sa
   bool ok = true;
   auto A = [&](size_t b) { void* p = ctx->dalloc(b); if (!p) ok = false; return p; };
   const size_t fbytes = (size_t)ctx->npad_max * ctx->npad_max * sizeof(double);
+  const size_t pbytes = sym_packed_pairs(ctx->npad_max) * sizeof(float2);
   for (int q = 0; q < Q && ok; ++q) {
     Sensor& S = ctx->s[q];
     S.A = (float2*)A((size_t)N * KM * sizeof(float2));
@@ -826,7 +837,7 @@ int sadmm_create(int Q, int M, int K, int N, double rho, double lambda, const sa
     S.F = (int*)A((size_t)N * sizeof(int));
     S.R = (int*)A((size_t)N * sizeof(int));
     for (int b = 0; b < 3; ++b) S.fb[b] = (double*)A(fbytes);
-    for (int b = 0; b < 3; ++b) S.fhl[b] = (float2*)A(fbytes);
+    for (int b = 0; b < 3; ++b) S.fhl[b] = (float2*)A(pbytes);
     S.dinv = (double*)A((size_t)ctx->npad_max * kTile * sizeof(double));
     S.dd = (double*)A(downdate_scratch_doubles(2 * (int)KM) * sizeof(double));
     if (c.precision > 0) {
@@ -850,6 +861,9 @@ int sadmm_create(int Q, int M, int K, int N, double rho, double lambda, const sa
     if (c.precision > 0) ctx->partial_cap = std::max(ctx->partial_cap, split_partial_bytes(ns, (int)KM, N));
   }
   ctx->partial = (float2*)A(ctx->partial_cap);
+  ctx->spd_part_stride = sym_part_pairs(ctx->npad_max);
+  ctx->spd_part = (float2*)A((size_t)Q * ctx->spd_part_stride * sizeof(float2));
+  ctx->spd_err = (int*)A(sizeof(int));
   ctx->red = (double*)A((size_t)residual_blocks(N) * 8 * sizeof(double));
   ctx->ticket = (unsigned int*)A(sizeof(unsigned int));
   ctx->scal = (IterScalars*)A(sizeof(IterScalars));
@@ -871,6 +885,7 @@ int sadmm_create(int Q, int M, int K, int N, double rho, double lambda, const sa
   }
   iota_kernel<<<div_up(N, 256), 256, 0, ctx->st>>>(ctx->iota, N);
   if (cudaMemsetAsync(ctx->ticket, 0, sizeof(unsigned int), ctx->st) != cudaSuccess ||
+      cudaMemsetAsync(ctx->spd_err, 0, sizeof(int), ctx->st) != cudaSuccess ||
       cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(ctx->st) != cudaSuccess) {
     set_error("sadmm_create: initialisation failed");
     ctx->release_all();
@@ -1303,17 +1318,28 @@ int sadmm_spd_apply(const double* F, int n, int ldf, const float* u, float* out,
     return SADMM_EINVAL;
   }
   cudaStream_t st = (cudaStream_t)stream;
-  void* Fhl = nullptr;
-  SADMM_CUDA_TRY(cudaMallocAsync(&Fhl, (size_t)n * ldf * sizeof(float2), st));
-  int rc = launch_split_f64(F, (float2*)Fhl, (size_t)n * ldf, st);
+  void *P = nullptr, *part = nullptr, *err = nullptr;
+  SADMM_CUDA_TRY(cudaMallocAsync(&P, sym_packed_pairs(n) * sizeof(float2), st));
+  SADMM_CUDA_TRY(cudaMallocAsync(&part, sym_part_pairs(n) * sizeof(float2), st));
+  SADMM_CUDA_TRY(cudaMallocAsync(&err, sizeof(int), st));
+  int rc = cudaMemsetAsync(err, 0, sizeof(int), st) == cudaSuccess ? SADMM_OK : SADMM_ECUDA;
+  if (rc == SADMM_OK) rc = launch_pack_sym(F, ldf, n, (float2*)P, st);
   if (rc == SADMM_OK) {
-    SpdSet s{(const float2*)Fhl, n, ldf, u, out, nullptr, 0};
+    SpdSet s{(const float2*)P, n, u, out, nullptr, 0, (float2*)part, 0};
     SolverView sv{};
-    rc = launch_spd_apply(&s, 1, false, sv, st);
+    rc = launch_spd_apply(&s, 1, false, sv, (int*)err, st);
   }
-  cudaError_t e = cudaFreeAsync(Fhl, st);
+  int herr = 0;
+  if (rc == SADMM_OK) {
+    SADMM_CUDA_TRY(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    SADMM_CUDA_TRY(cudaStreamSynchronize(st));
+  }
+  cudaFreeAsync(P, st);
+  cudaFreeAsync(part, st);
+  cudaError_t e = cudaFreeAsync(err, st);
   if (rc != SADMM_OK) return rc;
   SADMM_CUDA_TRY(e);
+  if (herr) { set_error("sadmm_spd_apply: a tile copy did not complete within the wait limit"); return SADMM_ETIMEOUT; }
   return SADMM_OK;
 }
 

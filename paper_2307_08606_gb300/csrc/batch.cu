@@ -472,6 +472,7 @@ struct BatchCtx {
   std::vector<void*> owned;
   float *X = nullptr, *dX = nullptr, *xbar = nullptr, *zbar = nullptr, *sd = nullptr, *lor = nullptr;
   float2 **dA = nullptr, **dY = nullptr, **dR = nullptr, **dF = nullptr;
+  std::vector<float2*> fpair;      // full-factor (hi, lo) pairs, one per sensor
   float **dU = nullptr, **dG = nullptr;
   float2* partial = nullptr;
   double* rpart = nullptr;
@@ -499,7 +500,7 @@ struct BatchCtx {
 
 // Accessors implemented in api.cu (the batch form reuses a single-scene
 // context for operator storage and the FP64 factor pipeline).
-int single_export(sadmm_t h, int q, const float2** A, const float2** Fhl, int* n, int* ld, int* woodbury);
+int single_export(sadmm_t h, int q, const float2** A, const double** F, int* n, int* ld, int* woodbury);
 
 namespace {
 
@@ -646,11 +647,19 @@ int sadmm_batch_solve(sadmm_batch_t b, const float* y, float* x_out, int iters, 
   SADMM_TRY(sadmm_prepare(b->single));
   if (!b->graph_valid) {
     std::vector<void*> Ap(b->Q), Fp(b->Q);
+    if (b->fpair.empty()) b->fpair.assign(b->Q, nullptr);
     for (int q = 0; q < b->Q; ++q) {
-      const float2 *A = nullptr, *F = nullptr;
+      const float2* A = nullptr;
+      const double* F = nullptr;
       SADMM_TRY(single_export(b->single, q, &A, &F, &b->n, &b->ld, &b->woodbury));
+      // the batched apply reads the full factor as (hi, lo) pairs
+      if (!b->fpair[q]) {
+        b->fpair[q] = (float2*)b->dalloc((size_t)b->n * b->ld * sizeof(float2));
+        if (!b->fpair[q]) { set_error("sadmm_batch_solve: factor allocation failed"); return SADMM_ENOMEM; }
+      }
+      SADMM_TRY(launch_split_f64(F, b->fpair[q], (size_t)b->n * b->ld, b->st));
       Ap[q] = (void*)A;
-      Fp[q] = (void*)F;
+      Fp[q] = (void*)b->fpair[q];
     }
     SADMM_CUDA_TRY(cudaMemcpyAsync(b->dA, Ap.data(), b->Q * sizeof(void*), cudaMemcpyHostToDevice, b->st));
     SADMM_CUDA_TRY(cudaMemcpyAsync(b->dF, Fp.data(), b->Q * sizeof(void*), cudaMemcpyHostToDevice, b->st));

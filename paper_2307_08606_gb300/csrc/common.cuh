@@ -107,15 +107,27 @@ struct AdjointSet {
 int launch_adjoint(const AdjointSet* sets, int nsets, int KM, bool update, const SolverView& sv,
                    cudaStream_t st);
 
+// Symmetric factors are stored as packed upper-triangular 64 x 64 tiles of
+// double-float pairs (spd.cu).
+constexpr int kSymTile = 64;
+size_t sym_packed_pairs(int n);      // float2 elements of the packed factor
+size_t sym_part_pairs(int n);        // float2 elements of the apply's partial sums
+// P (packed pairs) <- the upper triangle of the n x n FP64 matrix F (leading dimension ld)
+int launch_pack_sym(const double* F, int ld, int n, float2* P, cudaStream_t st);
+
 struct SpdSet {
-  const float2* F;   // factor as double-float pairs (hi, lo), row-major
-  int n, ldf;
+  const float2* P;   // packed factor (launch_pack_sym)
+  int n;
   const float* u;    // n floats
   float* out;        // n floats (plain) or unused (update)
   const int* idx;    // primal form: pixel of row p (update mode)
   int q;
+  float2* part;      // sym_part_pairs(n) scratch
+  int tile0;         // set by launch_spd_apply
 };
-int launch_spd_apply(const SpdSet* sets, int nsets, bool update, const SolverView& sv,
+// out = F u for every set (or, with update, the primal x-update epilogue).
+// *err is set to 1 if a tile copy did not complete within the wait limit.
+int launch_spd_apply(const SpdSet* sets, int nsets, bool update, const SolverView& sv, int* err,
                      cudaStream_t st);
 // (hi, lo) = (fl32(x), fl32(x - hi)) for n doubles.
 int launch_split_f64(const double* in, float2* out, size_t n, cudaStream_t st);

@@ -190,95 +190,6 @@ adjoint_kernel(const __grid_constant__ SetBlock<AdjointSet> sets, int KM, bool u
   }
 }
 
-// ---------------------------------------------------------------- SPD apply
-// out = F u for the factor F held as double-float pairs (hi, lo) with
-// hi = fl32(F), lo = fl32(F - hi).  The residual lies mostly where F is small,
-// so |F u| is far below sum |F||u| and plain FP32 loses several digits; FP64
-// arithmetic is exact enough but GB300's FP64 pipe makes it the bottleneck.
-// Here every product is formed exactly in FP32 (p + e = hi u via FMA, plus the
-// small lo u term) and accumulated as an unevaluated FP32 pair with the
-// error-free two-sum (Knuth), about 48 significant bits; lanes combine in FP64.
-// One warp per row streams (hi, lo) pairs as float4 (two elements).
-constexpr int kSpdWarps = 8;
-constexpr int kSpdRowsPerWarp = 4;
-constexpr int kSpdUnroll = 4;
-
-struct DF {
-  float hi, lo;
-};
-
-__device__ __forceinline__ void df_acc(DF& s, float w_hi, float w_lo, float u) {
-  const float p = w_hi * u;
-  float e = fmaf(w_hi, u, -p);          // w_hi u = p + e exactly
-  e = fmaf(w_lo, u, e);
-  const float t = s.hi + p;             // two-sum s.hi + p = t + err
-  const float bp = t - s.hi;
-  const float err = (s.hi - (t - bp)) + (p - bp);
-  s.hi = t;
-  s.lo += err + e;
-}
-
-__global__ void __launch_bounds__(kSpdWarps * 32)
-spd_apply_kernel(const __grid_constant__ SetBlock<SpdSet> sets, bool update,
-                 const __grid_constant__ SolverView sv) {
-  extern __shared__ float s_u[];
-  const SpdSet& ss = sets.v[blockIdx.y];
-  const int rows_per_cta = kSpdWarps * kSpdRowsPerWarp;
-  const int rbeg = blockIdx.x * rows_per_cta;
-  if (rbeg >= ss.n) return;
-  const int n = ss.n;
-  const int n2 = (n + 1) / 2;                  // float4 (two elements) steps per row
-  for (int t = threadIdx.x; t < 2 * n2; t += blockDim.x) s_u[t] = t < n ? ss.u[t] : 0.f;
-  __syncthreads();
-  const float2* u2 = reinterpret_cast<const float2*>(s_u);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int rw = 0; rw < kSpdRowsPerWarp; ++rw) {
-    const int i = rbeg + warp * kSpdRowsPerWarp + rw;
-    if (i >= n) break;
-    const float4* row = reinterpret_cast<const float4*>(ss.F + (size_t)i * ss.ldf);
-    DF acc[kSpdUnroll];
-#pragma unroll
-    for (int u = 0; u < kSpdUnroll; ++u) acc[u] = DF{0.f, 0.f};
-    int j = lane;
-    for (; j + 32 * (kSpdUnroll - 1) < n2; j += 32 * kSpdUnroll) {
-      float4 f[kSpdUnroll];
-#pragma unroll
-      for (int u = 0; u < kSpdUnroll; ++u) f[u] = __ldcs(row + j + 32 * u);
-#pragma unroll
-      for (int u = 0; u < kSpdUnroll; ++u) {
-        const float2 x = u2[j + 32 * u];
-        df_acc(acc[u], f[u].x, f[u].y, x.x);
-        df_acc(acc[u], f[u].z, f[u].w, x.y);
-      }
-    }
-    for (; j < n2; j += 32) {
-      const float4 f = __ldcs(row + j);
-      const float2 x = u2[j];             // the padded column (2j+1 == n) multiplies u = 0
-      df_acc(acc[0], f.x, f.y, x.x);
-      df_acc(acc[0], f.z, f.w, x.y);
-    }
-    double g = 0.0;
-#pragma unroll
-    for (int u = 0; u < kSpdUnroll; ++u) g += (double)acc[u].hi + (double)acc[u].lo;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
-    if (lane == 0) {
-      if (update) {
-        // x-update epilogue (primal form): x_J = v_J + mu H g
-        const int pix = ss.idx[i];
-        const size_t xi = (size_t)ss.q * sv.N + pix;
-        const float xo = sv.x[xi];
-        const float v = xo - sv.xbar[pix] + sv.zbar[pix] - sv.s[pix];
-        const float xn = fmaf(sv.mu, (float)g, v);
-        sv.ring[((size_t)sv.slot * sv.Q + ss.q) * sv.N + pix] = xn - xo;
-        sv.x[xi] = xn;
-      } else {
-        ss.out[i] = (float)g;
-      }
-    }
-  }
-}
-
 __global__ void split_f64_kernel(const double* __restrict__ in, float2* __restrict__ out, size_t n) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
     const double x = in[i];
@@ -340,34 +251,6 @@ int launch_adjoint(const AdjointSet* sets, int nsets, int KM, bool update, const
 int launch_split_f64(const double* in, float2* out, size_t n, cudaStream_t st) {
   if (n == 0) return SADMM_OK;
   split_f64_kernel<<<(int)std::min<size_t>(div_up((long long)n, 256), 152 * 32), 256, 0, st>>>(in, out, n);
-  SADMM_LAUNCH_CHECK();
-  return SADMM_OK;
-}
-
-int launch_spd_apply(const SpdSet* sets, int nsets, bool update, const SolverView& sv,
-                     cudaStream_t st) {
-  if (nsets <= 0) return SADMM_OK;
-  if (nsets > kMaxSets) { set_error("launch_spd_apply: too many sets"); return SADMM_EINVAL; }
-  SetBlock<SpdSet> blk;
-  int mx = 0;
-  for (int i = 0; i < nsets; ++i) {
-    blk.v[i] = sets[i];
-    mx = max(mx, sets[i].n);
-    if (sets[i].ldf < round_up(sets[i].n, 2) || sets[i].ldf % 2 != 0) {
-      set_error("launch_spd_apply: leading dimension must be even and >= n");
-      return SADMM_EINVAL;
-    }
-  }
-  if (mx == 0) return SADMM_OK;
-  const size_t smem = (size_t)round_up(mx, 2) * sizeof(float);
-  static bool configured = false;
-  if (!configured) {
-    SADMM_CUDA_TRY(cudaFuncSetAttribute(spd_apply_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        200 * 1024));
-    configured = true;
-  }
-  dim3 grid(div_up(mx, kSpdWarps * kSpdRowsPerWarp), nsets);
-  spd_apply_kernel<<<grid, kSpdWarps * 32, smem, st>>>(blk, update, sv);
   SADMM_LAUNCH_CHECK();
   return SADMM_OK;
 }

@@ -1,0 +1,309 @@
+// Symmetric factor apply out = F u (Eq. 3, x_q-update: the Woodbury matrix W
+// or the primal inverse H), for F symmetric positive definite held as
+// double-float pairs (hi, lo) with hi = fl32(F), lo = fl32(F - hi).
+//
+// Precision.  The residual u lies mostly where F is small, so |F u| is far
+// below sum |F||u| and plain FP32 loses several digits, while GB300's FP64
+// pipe is too slow for a per-iteration pass.  Every product is formed exactly
+// in FP32 (p + e = hi u via FMA, plus the small lo u term) and accumulated as
+// an unevaluated FP32 pair with the error-free two-sum (Knuth), about 48
+// significant bits.
+//
+// Layout and traffic.  Only the upper triangle is stored, in 64 x 64 tiles
+// (I <= J, row-block-major; each tile row-major and contiguous, zero-padded
+// past n), so one iteration streams n^2/2 pairs instead of n^2.  A tile (I, J)
+// contributes F_IJ u_J to block row I and, off the diagonal, F_IJ^T u_I to
+// block row J.  Persistent CTAs pull tiles with one bulk asynchronous copy
+// each (cp.async.bulk into shared memory, completion on an mbarrier, two
+// stages), then 64 threads form the row sums and 64 the column sums of the
+// tile, reading it along diagonals so that shared-memory accesses do not
+// conflict.  Per-tile partial sums (pairs) go to a scratch buffer; a second
+// kernel adds them in a fixed order and applies the epilogue.
+#include "common.cuh"
+
+namespace sadmm {
+namespace {
+
+constexpr int kT = kSymTile;                  // tile side
+constexpr int kTileBytes = kT * kT * (int)sizeof(float2);
+constexpr int kSpdThreads = 2 * kT;           // 64 row threads + 64 column threads
+constexpr long long kWaitLimit = 1ll << 26;   // bounded mbarrier wait (far beyond any copy time)
+
+struct DF {
+  float hi, lo;
+};
+
+__device__ __forceinline__ void df_acc(DF& s, float w_hi, float w_lo, float u) {
+  const float p = w_hi * u;
+  float e = fmaf(w_hi, u, -p);          // w_hi u = p + e exactly
+  e = fmaf(w_lo, u, e);
+  const float t = s.hi + p;             // two-sum s.hi + p = t + err
+  const float bp = t - s.hi;
+  const float err = (s.hi - (t - bp)) + (p - bp);
+  s.hi = t;
+  s.lo += err + e;
+}
+
+__device__ __forceinline__ void df_add(DF& s, DF b) {
+  const float t = s.hi + b.hi;
+  const float bp = t - s.hi;
+  const float err = (s.hi - (t - bp)) + (b.hi - bp);
+  s.hi = t;
+  s.lo += err + b.lo;
+}
+
+__device__ __forceinline__ DF df_norm(DF s) {
+  const float t = s.hi + s.lo;
+  return DF{t, s.lo - (t - s.hi)};
+}
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Waits for phase `parity` of the barrier; false after kWaitLimit polls.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+  for (long long it = 0; it < kWaitLimit; ++it) {
+    unsigned ok;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+__host__ __device__ __forceinline__ int ntiles_side(int n) { return (n + kT - 1) / kT; }
+
+// tile number t of an nt x nt upper triangle -> (I, J)
+__device__ __forceinline__ void tile_ij(int t, int nt, int& I, int& J) {
+  I = 0;
+  while (t >= nt - I) { t -= nt - I; ++I; }
+  J = I + t;
+}
+
+// item -> (set, tile): items are numbered set after set
+__device__ __forceinline__ int item_set(const SetBlock<SpdSet>& sets, int nsets, int item, int& t) {
+  int s = 0;
+  while (s + 1 < nsets && item >= sets.v[s + 1].tile0) ++s;
+  t = item - sets.v[s].tile0;
+  return s;
+}
+
+__global__ void __launch_bounds__(kSpdThreads)
+spd_tile_kernel(const __grid_constant__ SetBlock<SpdSet> sets, int nsets, int items, int* __restrict__ err) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  float2* buf = reinterpret_cast<float2*>(smem_raw);            // 2 stages x 64 x 64 pairs
+  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ float s_u[2][2][kT];                                // stage, (u_I, u_J), 64
+  const int tid = threadIdx.x;
+  const int lt = tid;                                            // < 64: row lt, else column lt - 64
+  int item = blockIdx.x;
+  if (item >= items) return;
+  if (tid == 0) {
+    mbar_init(&bar[0]);
+    mbar_init(&bar[1]);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+
+  // stage the first tile
+  int t0, s0 = item_set(sets, nsets, item, t0);
+  int I0, J0;
+  tile_ij(t0, ntiles_side(sets.v[s0].n), I0, J0);
+  if (tid == 0) bulk_load(buf, sets.v[s0].P + (size_t)t0 * kT * kT, kTileBytes, &bar[0]);
+  {
+    const SpdSet& ss = sets.v[s0];
+    const int blk = lt < kT ? I0 : J0;
+    const int i = blk * kT + (lt & (kT - 1));
+    s_u[0][lt >> 6][lt & (kT - 1)] = i < ss.n ? ss.u[i] : 0.f;
+  }
+  unsigned phase = 0u;                               // bit s: parity to wait for on stage s
+  unsigned issued = 1u;                              // bit s: a copy into stage s is outstanding
+  for (int k = 0; item < items; ++k, item += gridDim.x) {
+    const int st = k & 1;
+    int t, s = item_set(sets, nsets, item, t);
+    const SpdSet& ss = sets.v[s];
+    const int nt = ntiles_side(ss.n);
+    int I, J;
+    tile_ij(t, nt, I, J);
+    // issue the next tile into the other stage (freed by the barrier that
+    // closed the previous iteration) and fetch its u slices into registers
+    const int nitem = item + gridDim.x;
+    float u_next = 0.f;
+    if (nitem < items) {
+      int tn, sn = item_set(sets, nsets, nitem, tn);
+      const SpdSet& sn_ = sets.v[sn];
+      int In, Jn;
+      tile_ij(tn, ntiles_side(sn_.n), In, Jn);
+      if (tid == 0) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        bulk_load(buf + (size_t)(st ^ 1) * kT * kT, sn_.P + (size_t)tn * kT * kT, kTileBytes, &bar[st ^ 1]);
+      }
+      issued |= 2u >> st;
+      const int blk = lt < kT ? In : Jn;
+      const int i = blk * kT + (lt & (kT - 1));
+      u_next = i < sn_.n ? sn_.u[i] : 0.f;
+    }
+    __syncthreads();                                   // s_u[st] written
+    const bool ok = mbar_wait(&bar[st], (phase >> st) & 1u);
+    if (!__syncthreads_and(ok)) {
+      // give up on this launch: flag it, wait (bounded) for the other copy in
+      // flight so that no transfer targets the CTA's memory after it exits
+      if (tid == 0) atomicExch(err, 1);
+      if ((issued >> (st ^ 1)) & 1u) mbar_wait(&bar[st ^ 1], (phase >> (st ^ 1)) & 1u);
+      return;
+    }
+    issued &= ~(1u << st);
+    phase ^= 1u << st;
+    const float2* tile = buf + (size_t)st * kT * kT;
+    DF acc0{0.f, 0.f}, acc1{0.f, 0.f};
+    const int r = lt & (kT - 1);
+    if (lt < kT) {
+      // row r of F_IJ times u_J, read along the diagonal (r, (r + c) mod 64)
+      const float* uJ = s_u[st][1];
+#pragma unroll 8
+      for (int c = 0; c < kT; c += 2) {
+        const int c0 = (r + c) & (kT - 1), c1 = (r + c + 1) & (kT - 1);
+        const float2 f0 = tile[r * kT + c0], f1 = tile[r * kT + c1];
+        df_acc(acc0, f0.x, f0.y, uJ[c0]);
+        df_acc(acc1, f1.x, f1.y, uJ[c1]);
+      }
+    } else if (I != J) {
+      // column r of F_IJ times u_I (the transposed contribution to block row J)
+      const float* uI = s_u[st][0];
+#pragma unroll 8
+      for (int c = 0; c < kT; c += 2) {
+        const int r0 = (r + c) & (kT - 1), r1 = (r + c + 1) & (kT - 1);
+        const float2 f0 = tile[r0 * kT + r], f1 = tile[r1 * kT + r];
+        df_acc(acc0, f0.x, f0.y, uI[r0]);
+        df_acc(acc1, f1.x, f1.y, uI[r1]);
+      }
+    }
+    df_add(acc0, acc1);
+    const DF o = df_norm(acc0);
+    ss.part[(size_t)t * 2 * kT + lt] = make_float2(o.hi, o.lo);
+    s_u[st ^ 1][lt >> 6][r] = u_next;
+    __syncthreads();                                   // stage st consumed; s_u[st ^ 1] ready
+  }
+}
+
+// out_I[i] = sum_{J >= I} row part of tile (I, J) + sum_{J < I} column part of
+// tile (J, I), in a fixed order; then the epilogue.
+__global__ void __launch_bounds__(kT)
+spd_reduce_kernel(const __grid_constant__ SetBlock<SpdSet> sets, bool update, const __grid_constant__ SolverView sv) {
+  const SpdSet& ss = sets.v[blockIdx.y];
+  const int nt = ntiles_side(ss.n);
+  const int I = blockIdx.x;
+  if (I >= nt) return;
+  const int i = I * kT + threadIdx.x;
+  DF acc{0.f, 0.f};
+  constexpr int kB = 8;                 // loads issued ahead of their sums
+  for (int J0 = 0; J0 < nt; J0 += kB) {
+    float2 p[kB];
+#pragma unroll
+    for (int u = 0; u < kB; ++u) {
+      const int J = J0 + u;
+      p[u] = make_float2(0.f, 0.f);
+      if (J < nt) {
+        const int a = min(I, J), b = max(I, J);
+        const int t = a * nt - a * (a - 1) / 2 + (b - a);
+        p[u] = ss.part[(size_t)t * 2 * kT + (J >= I ? 0 : kT) + threadIdx.x];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kB; ++u) df_add(acc, DF{p[u].x, p[u].y});
+  }
+  if (i >= ss.n) return;
+  const float g = acc.hi + acc.lo;
+  if (update) {
+    // x-update epilogue (primal form): x_J = v_J + mu H g
+    const int pix = ss.idx[i];
+    const size_t xi = (size_t)ss.q * sv.N + pix;
+    const float xo = sv.x[xi];
+    const float v = xo - sv.xbar[pix] + sv.zbar[pix] - sv.s[pix];
+    const float xn = fmaf(sv.mu, g, v);
+    sv.ring[((size_t)sv.slot * sv.Q + ss.q) * sv.N + pix] = xn - xo;
+    sv.x[xi] = xn;
+  } else {
+    ss.out[i] = g;
+  }
+}
+
+__global__ void pack_sym_kernel(const double* __restrict__ F, int ld, int n, float2* __restrict__ P) {
+  const int I = blockIdx.y, J = blockIdx.x;
+  if (I > J) return;
+  const int nt = ntiles_side(n);
+  const size_t t = (size_t)I * nt - (size_t)I * (I - 1) / 2 + (J - I);
+  float2* out = P + t * kT * kT;
+  for (int e = threadIdx.x; e < kT * kT; e += blockDim.x) {
+    const int r = I * kT + e / kT, c = J * kT + e % kT;
+    const double x = (r < n && c < n) ? F[(size_t)r * ld + c] : 0.0;
+    const float h = (float)x;
+    out[e] = make_float2(h, (float)(x - (double)h));
+  }
+}
+
+}  // namespace
+
+size_t sym_packed_pairs(int n) {
+  const size_t nt = ntiles_side(n);
+  return nt * (nt + 1) / 2 * kT * kT;
+}
+
+size_t sym_part_pairs(int n) {
+  const size_t nt = ntiles_side(n);
+  return nt * (nt + 1) / 2 * 2 * kT;
+}
+
+int launch_pack_sym(const double* F, int ld, int n, float2* P, cudaStream_t st) {
+  if (n <= 0) return SADMM_OK;
+  const int nt = ntiles_side(n);
+  pack_sym_kernel<<<dim3(nt, nt), 256, 0, st>>>(F, ld, n, P);
+  SADMM_LAUNCH_CHECK();
+  return SADMM_OK;
+}
+
+int launch_spd_apply(const SpdSet* sets, int nsets, bool update, const SolverView& sv, int* err, cudaStream_t st) {
+  if (nsets <= 0) return SADMM_OK;
+  if (nsets > kMaxSets) { set_error("launch_spd_apply: too many sets"); return SADMM_EINVAL; }
+  SetBlock<SpdSet> blk;
+  int items = 0, nt_max = 0;
+  for (int i = 0; i < nsets; ++i) {
+    blk.v[i] = sets[i];
+    blk.v[i].tile0 = items;
+    const int nt = ntiles_side(sets[i].n);
+    items += nt * (nt + 1) / 2;
+    nt_max = max(nt_max, nt);
+  }
+  if (items == 0) return SADMM_OK;
+  const int smem = 2 * kTileBytes;
+  static bool configured = false;
+  if (!configured) {
+    SADMM_CUDA_TRY(cudaFuncSetAttribute(spd_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    configured = true;
+  }
+  const int grid = min(items, 152 * 3);
+  spd_tile_kernel<<<grid, kSpdThreads, smem, st>>>(blk, nsets, items, err);
+  SADMM_LAUNCH_CHECK();
+  spd_reduce_kernel<<<dim3(nt_max, nsets), kT, 0, st>>>(blk, update, sv);
+  SADMM_LAUNCH_CHECK();
+  return SADMM_OK;
+}
+
+}  // namespace sadmm

@@ -37,6 +37,9 @@ GEOMS = {
     "small_point": Geometry(Q=4, M=4, K=64, nx=32, cell=2.0 / 32, radius=10.0, fc=77e9, bw=1e9),
     "paper_scale": Geometry(Q=8, M=8, K=256, nx=128, cell=0.05, radius=10.0, fc=77e9, bw=1e9),
     "resolved_tiny": Geometry(Q=3, M=16, K=16, nx=8, cell=0.10, radius=0.6, fc=60e9, bw=4e9),
+    # 32x32 grid that every sensor resolves on its own (2KM = 2N, condition ~300):
+    # Eq. 2 is well posed, so the iterates converge to a nonzero image
+    "resolved_32": Geometry(Q=4, M=32, K=32, nx=32, cell=0.08, radius=2.0, fc=60e9, bw=4e9),
 }
 
 
@@ -47,6 +50,9 @@ def build_scene(name: str, seed: int = 0, geom: Geometry = None, snr_db="default
     if name == "paper_scale":
         x = cluster_targets(g, seed, n_targets or 40, amp=(0.3, 1.0), p_vis=0.7)
         snr = 15.0
+    elif name == "resolved_32":
+        x = cluster_targets(g, seed, n_targets or 10, amp=(0.3, 1.0), p_vis=0.7)
+        snr = 25.0
     elif name == "resolved_tiny":
         x = point_targets(g, seed, n_targets or 3, amp=(0.5, 1.0), p_vis=0.8)
         snr = 30.0

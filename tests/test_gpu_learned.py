@@ -197,40 +197,49 @@ def test_eliminator_arguments_checked(B):
 
 
 def test_trained_proposal_on_held_out_scene(B):
-    """Train the network on plain runs of three 32x32 scenes, then solve a
-    held-out scene with Algorithm 1 alone and with the learned step.  Reported:
-    the active-set work sum_k sum_q |J_q|, the deviation of the final iterates
-    from the plain run, and the re-admissions (false eliminations caught).
-    Required: the loss falls, and the learned mode's final iterates stay as
-    close to the plain run as 5x Algorithm 1's deviation (plus 1e-3)."""
+    """Well-posed 32x32 scenes (Q=4, KM=1024, primal form, rho = 100): train the
+    network on plain runs of three scenes, then solve a held-out scene with
+    Algorithm 1 alone and with the learned step.  Reported: the active-set work
+    sum_k sum_q |J_q| relative to the plain run's, the deviation of x_G from the
+    plain run's, the re-admissions (false eliminations caught) and the
+    eliminations.  Required: the loss falls, the labels are not all of one
+    class, and the learned mode's x_G stays within max(5x Algorithm 1's
+    deviation, 1e-3) of the plain run's."""
     from paper_2307_08606_gb300 import eliminator as E
+    rho = 100.0
     lam_of = lambda sc: 0.05 * scenegen.lambda_max(sc.A, sc.y)
-    train = [scenegen.build_scene("small_point", seed=s) for s in (10, 11, 12)]
+    train = [scenegen.build_scene("resolved_32", seed=s) for s in (10, 11, 12)]
     g = train[0].geom
-    smp = E.collect(train, lam_of, g.nx, g.nx, iters=200, learn_every=10, horizon=50)
+    smp = E.collect(train, lam_of, g.nx, g.nx, iters=200, learn_every=10, horizon=50, rho=rho)
+    frac = float(smp.labels.mean())
+    assert 0.0 < frac < 1.0
     net = B.CNN(g.nx, g.nx, max_batch=8)
     net.set_params(scenegen.cnn_init(5))
-    losses = E.train(net, smp, steps=300, lr=2e-3, batch=8)
-    print(f"samples {len(smp.ks)}, droppable fraction {smp.labels.mean():.3f}, "
+    losses = E.train(net, smp, steps=400, lr=2e-3, batch=8)
+    print(f"samples {len(smp.ks)}, droppable fraction {frac:.3f}, "
           f"loss {np.mean(losses[:20]):.4f} -> {np.mean(losses[-20:]):.4f}")
-    assert np.mean(losses[-20:]) < np.mean(losses[:20])
+    assert np.mean(losses[-20:]) < 0.5 * np.mean(losses[:20])
     params = net.params()
-    sc = scenegen.build_scene("small_point", seed=13)
+    net.close()
+    sc = scenegen.build_scene("resolved_32", seed=13)
     lam = lam_of(sc)
-    iters = 300
-    p = _solver(B, sc, 1.0, lam, elim=0)
-    p.solve(sc.y, iters)
-    Xp = p.X()
+    iters = 200
+    p = _solver(B, sc, rho, lam, elim=0)
+    xp, _ = p.solve(sc.y, iters)
+    p.close()
+    full = iters * g.Q * g.N
     out = {}
     for mode in (1, 2):
-        s = _solver(B, sc, 1.0, lam, elim=mode, learn_every=10, learn_theta=0.5)
+        s = _solver(B, sc, rho, lam, elim=mode, learn_every=10, learn_theta=0.5)
         if mode == 2:
             s.set_eliminator(params, g.nx, g.nx)
-        _, st = s.solve(sc.y, iters)
-        work = sum(h["active_total"] for h in s.history())
-        out[mode] = dict(work=work, dev=_rel(s.X(), Xp), readmitted=st["readmitted"],
-                         active=st["active_total"], ms=st["ms_total"])
+        xg, st = s.solve(sc.y, iters)
+        h = s.history()
+        out[mode] = dict(work=round(sum(r["active_total"] for r in h) / full, 4),
+                         dev=float(np.linalg.norm(xg - xp) / np.linalg.norm(xp)),
+                         readmitted=st["readmitted"], learned_steps=st["learned_steps"],
+                         active=st["active_total"], ms=round(st["ms_total"], 1))
         s.close()
     print(f"Algorithm 1: {out[1]}")
     print(f"learned:     {out[2]}")
-    assert out[2]["dev"] <= 5 * out[1]["dev"] + 1e-3
+    assert out[2]["dev"] <= max(5 * out[1]["dev"], 1e-3)
