@@ -12,6 +12,7 @@
 // Layout: scene index fastest everywhere: X_q [pixel][scene], x_bar / z_bar /
 // s [pixel][scene], Y'_q, R_q, U_q [row][scene] (complex as float2).
 #include "common.cuh"
+#include "symtile.cuh"
 
 #include <algorithm>
 #include <chrono>
@@ -148,99 +149,217 @@ __global__ void bfwd_reduce_kernel(const float2* __restrict__ partial, const flo
 }
 
 // ------------------------------------------------------------ factor apply
-// U[i][s] = sum_j F[i][j] u_s[j] for the 16 scenes, F as double-float pairs,
-// exact products and two-sum accumulation (as the single-scene apply).  One
-// warp per row of F; lane l takes the columns j = l (mod 32) and keeps a
-// double-float accumulator for every scene; lanes combine in FP64.
+// U[i][s] = sum_j F[i][j] u_s[j] for the 16 scenes with F symmetric, packed
+// as upper-triangular 64 x 64 tiles of double-float pairs (as the
+// single-scene apply): exact products, two-sum accumulation, about 48 bits.
+// A tile (I, J) is a pair of small GEMMs, OUT_I += F_IJ U_J and (off the
+// diagonal) OUT_J += F_IJ^T U_I, with 64 x 16 right-hand sides.  Persistent
+// CTAs pull tiles by bulk asynchronous copy (two stages, mbarrier, bounded
+// waits); 64 threads hold 4 rows x 4 scenes of F_IJ U_J and 64 threads 4
+// columns x 4 scenes of F_IJ^T U_I, stepping along skewed diagonals so that
+// shared-memory reads do not conflict.  Per-tile partials go to a scratch
+// buffer that bspd_reduce_kernel adds in a fixed order.
 // u (and U in mode 0) use the interleaved real index of a complex [row][scene]
 // array: real row j = 2m + c lives at float (m * 16 + s) * 2 + c.
-__device__ __forceinline__ void df2(float& sh, float& sl, float wh, float wl, float u) {
-  const float p = wh * u;
-  float e = fmaf(wh, u, -p);
-  e = fmaf(wl, u, e);
-  const float t = sh + p;
-  const float bp = t - sh;
-  sl += ((sh - (t - bp)) + (p - bp)) + e;
-  sh = t;
-}
+using namespace symtile;
 
-constexpr int kBsWarps = 8;
-constexpr int kBsChunk = 256;        // rows of u staged per pass
+constexpr int kBtThreads = 128;
+constexpr int kBtTileBytes = kT * kT * (int)sizeof(float2);
+constexpr int kBtPart = 2 * kT * kBS;          // float2 partials per tile (row part, column part)
 
 __device__ __forceinline__ size_t cidx(int j, int s) { return ((size_t)(j >> 1) * kBS + s) * 2 + (j & 1); }
 
-// mode 0 (Woodbury): u from R (complex [row][scene]), U written as complex [row][scene]
-// mode 1 (primal):   u from G ([pixel][scene]); x-update X = V + mu U
-__global__ void __launch_bounds__(kBsWarps * 32)
-bspd_kernel(const float2* const* __restrict__ Fq, const float* const* __restrict__ uq, float* const* __restrict__ outq,
-            int n, int ld, int mode, BatchDev b) {
-  extern __shared__ float s_u[];                   // [kBsChunk + 1][kBS]
-  const int q = blockIdx.y;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int i = blockIdx.x * kBsWarps + warp;      // one row per warp
-  const float2* F = Fq[q];
-  const float* u = uq[q];
-  float sh[kBS], sl[kBS];
+// The 16 values of u this thread stages for tile (I, J): thread t covers
+// slice t / 64 (u_I, then u_J) and, in mode 1, row t % 64 of it; in mode 0 the
+// complex row (t % 64) / 2 and scenes 8 (t % 2) .. 8 (t % 2) + 7 of both its
+// real rows.
+__device__ __forceinline__ void bt_load_u(const float* __restrict__ u, int n, int mode, int I, int J, int t,
+                                          float (&v)[16]) {
+  const int blk = (t >> 6) ? J : I;
+  const int l = t & 63;
+  if (mode == 1) {
+    const int j = blk * kT + l;
 #pragma unroll
-  for (int s = 0; s < kBS; ++s) { sh[s] = 0.f; sl[s] = 0.f; }
-  for (int j0 = 0; j0 < n; j0 += kBsChunk) {
-    const int nj = min(kBsChunk, n - j0);
-    __syncthreads();
-    for (int e = threadIdx.x; e < (kBsChunk + 1) * kBS; e += blockDim.x) {
-      const int jj = e / kBS, s = e % kBS;
-      float v = 0.f;
-      if (jj < nj) v = mode == 0 ? u[cidx(j0 + jj, s)] : u[(size_t)(j0 + jj) * kBS + s];
-      s_u[e] = v;
+    for (int e = 0; e < 4; ++e) {
+      const float4 x = j < n ? reinterpret_cast<const float4*>(u + (size_t)j * kBS)[e] : make_float4(0.f, 0.f, 0.f, 0.f);
+      v[4 * e] = x.x; v[4 * e + 1] = x.y; v[4 * e + 2] = x.z; v[4 * e + 3] = x.w;
     }
-    __syncthreads();
-    if (i < n) {
-      // two (hi, lo) elements per float4; two float4 in flight per lane
-      const float4* row = reinterpret_cast<const float4*>(F + (size_t)i * ld + j0);
-      for (int jj0 = 2 * lane; jj0 < nj; jj0 += 2 * 32 * 2) {
-        float4 f[2];
+  } else {
+    const int m = blk * (kT / 2) + (l >> 1), h = l & 1;
+    const bool ok = 2 * m < n;
 #pragma unroll
-        for (int u2 = 0; u2 < 2; ++u2) {
-          const int jj = jj0 + 64 * u2;
-          f[u2] = jj < nj ? __ldcs(row + jj / 2) : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
+    for (int e = 0; e < 4; ++e) {
+      const float4 x = ok ? reinterpret_cast<const float4*>(u + ((size_t)m * kBS + 8 * h) * 2)[e]
+                          : make_float4(0.f, 0.f, 0.f, 0.f);
+      // (re, im) of scenes 8h + 2e, 8h + 2e + 1
+      v[2 * e] = x.x; v[8 + 2 * e] = x.y; v[2 * e + 1] = x.z; v[8 + 2 * e + 1] = x.w;
+    }
+  }
+}
+
+// ... and writes them to the staged slices su[2][64][16].
+__device__ __forceinline__ void bt_store_u(float* su, int mode, int t, const float (&v)[16]) {
+  const int slice = t >> 6, l = t & 63;
+  float* base = su + (size_t)slice * kT * kBS;
+  if (mode == 1) {
 #pragma unroll
-        for (int u2 = 0; u2 < 2; ++u2) {
-          const int jj = jj0 + 64 * u2;
-          if (jj >= nj) break;
-          const float4* ua = reinterpret_cast<const float4*>(s_u + jj * kBS);
-          const float4* ub = reinterpret_cast<const float4*>(s_u + (jj + 1) * kBS);
+    for (int e = 0; e < 4; ++e)
+      reinterpret_cast<float4*>(base + l * kBS)[e] = make_float4(v[4 * e], v[4 * e + 1], v[4 * e + 2], v[4 * e + 3]);
+  } else {
+    const int r = (l >> 1) * 2, h = l & 1;     // real rows r (re) and r + 1 (im), scenes 8h..8h+7
 #pragma unroll
-          for (int s4 = 0; s4 < kBS / 4; ++s4) {
-            const float4 x = ua[s4], y = ub[s4];
-            df2(sh[4 * s4 + 0], sl[4 * s4 + 0], f[u2].x, f[u2].y, x.x);
-            df2(sh[4 * s4 + 1], sl[4 * s4 + 1], f[u2].x, f[u2].y, x.y);
-            df2(sh[4 * s4 + 2], sl[4 * s4 + 2], f[u2].x, f[u2].y, x.z);
-            df2(sh[4 * s4 + 3], sl[4 * s4 + 3], f[u2].x, f[u2].y, x.w);
-            df2(sh[4 * s4 + 0], sl[4 * s4 + 0], f[u2].z, f[u2].w, y.x);
-            df2(sh[4 * s4 + 1], sl[4 * s4 + 1], f[u2].z, f[u2].w, y.y);
-            df2(sh[4 * s4 + 2], sl[4 * s4 + 2], f[u2].z, f[u2].w, y.z);
-            df2(sh[4 * s4 + 3], sl[4 * s4 + 3], f[u2].z, f[u2].w, y.w);
-          }
+    for (int e = 0; e < 2; ++e) {
+      reinterpret_cast<float4*>(base + r * kBS + 8 * h)[e] = make_float4(v[4 * e], v[4 * e + 1], v[4 * e + 2], v[4 * e + 3]);
+      reinterpret_cast<float4*>(base + (r + 1) * kBS + 8 * h)[e] =
+          make_float4(v[8 + 4 * e], v[8 + 4 * e + 1], v[8 + 4 * e + 2], v[8 + 4 * e + 3]);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kBtThreads)
+bspd_tile_kernel(const float2* const* __restrict__ Pq, const float* const* __restrict__ uq, float2* __restrict__ part,
+                 size_t part_stride, int n, int mode, int items, int* __restrict__ err) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  float2* buf = reinterpret_cast<float2*>(smem_raw);                         // 2 x 64 x 64 pairs
+  float* su = reinterpret_cast<float*>(smem_raw + 2 * kBtTileBytes);        // 2 stages x (u_I, u_J) x 64 x 16
+  __shared__ __align__(8) uint64_t bar[2];
+  const int tid = threadIdx.x;
+  const int nt = ntiles_side(n);
+  const int tiles = nt * (nt + 1) / 2;
+  int item = blockIdx.x;
+  if (item >= items) return;
+  if (tid == 0) {
+    mbar_init(&bar[0]);
+    mbar_init(&bar[1]);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  {
+    const int q = item / tiles, t = item % tiles;
+    int I, J;
+    tile_ij(t, nt, I, J);
+    if (tid == 0) bulk_load(buf, Pq[q] + (size_t)t * kT * kT, kBtTileBytes, &bar[0]);
+    float v[16];
+    bt_load_u(uq[q], n, mode, I, J, tid, v);
+    bt_store_u(su, mode, tid, v);
+  }
+  unsigned phase = 0u, issued = 1u;
+  const bool rowpart = tid < 64;
+  const int grp = (tid & 63) >> 2;        // row group (rows 4 grp..) or column group
+  const int g = tid & 3;                  // scenes 4g .. 4g + 3
+  for (int k = 0; item < items; ++k, item += gridDim.x) {
+    const int st = k & 1;
+    const int q = item / tiles, t = item % tiles;
+    int I, J;
+    tile_ij(t, nt, I, J);
+    const int nitem = item + gridDim.x;
+    float vn[16];
+    if (nitem < items) {
+      const int qn = nitem / tiles, tn = nitem % tiles;
+      int In, Jn;
+      tile_ij(tn, nt, In, Jn);
+      if (tid == 0) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        bulk_load(buf + (size_t)(st ^ 1) * kT * kT, Pq[qn] + (size_t)tn * kT * kT, kBtTileBytes, &bar[st ^ 1]);
+      }
+      issued |= 2u >> st;
+      bt_load_u(uq[qn], n, mode, In, Jn, tid, vn);
+    }
+    __syncthreads();                                        // su[st] written
+    const bool ok = mbar_wait(&bar[st], (phase >> st) & 1u);
+    if (!__syncthreads_and(ok)) {
+      if (tid == 0) atomicExch(err, 1);
+      if ((issued >> (st ^ 1)) & 1u) mbar_wait(&bar[st ^ 1], (phase >> (st ^ 1)) & 1u);
+      return;
+    }
+    issued &= ~(1u << st);
+    phase ^= 1u << st;
+    const float2* tile = buf + (size_t)st * kT * kT;
+    const float* uI = su + (size_t)st * 2 * kT * kBS;
+    const float* uJ = uI + kT * kBS;
+    DF acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc[a][b] = DF{0.f, 0.f};
+    if (rowpart) {
+      // OUT_I[4 grp + a][4 g + b] += F[4 grp + a][k'] u_J[k'][4 g + b]
+#pragma unroll 4
+      for (int k0 = 0; k0 < kT; ++k0) {
+        const int kk = (k0 + grp) & (kT - 1);
+        const float4 u4 = reinterpret_cast<const float4*>(uJ + kk * kBS)[g];
+        const float uv[4] = {u4.x, u4.y, u4.z, u4.w};
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          const float2 f = tile[(4 * grp + a) * kT + kk];
+#pragma unroll
+          for (int b = 0; b < 4; ++b) df_acc(acc[a][b], f.x, f.y, uv[b]);
         }
       }
+    } else if (I != J) {
+      // OUT_J[4 grp + a][4 g + b] += F[i'][4 grp + a] u_I[i'][4 g + b]
+#pragma unroll 4
+      for (int k0 = 0; k0 < kT; ++k0) {
+        const int ii = (k0 + grp) & (kT - 1);
+        const float4 u4 = reinterpret_cast<const float4*>(uI + ii * kBS)[g];
+        const float uv[4] = {u4.x, u4.y, u4.z, u4.w};
+        const float4 f01 = reinterpret_cast<const float4*>(tile + ii * kT + 4 * grp)[0];
+        const float4 f23 = reinterpret_cast<const float4*>(tile + ii * kT + 4 * grp)[1];
+        const float fh[4] = {f01.x, f01.z, f23.x, f23.z}, fl[4] = {f01.y, f01.w, f23.y, f23.w};
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) df_acc(acc[a][b], fh[a], fl[a], uv[b]);
+      }
     }
+    float2* pt = part + (size_t)q * part_stride + (size_t)t * kBtPart + (rowpart ? 0 : kT * kBS);
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const DF o0 = df_norm(acc[a][0]), o1 = df_norm(acc[a][1]), o2 = df_norm(acc[a][2]), o3 = df_norm(acc[a][3]);
+      float4* dst = reinterpret_cast<float4*>(pt + (4 * grp + a) * kBS + 4 * g);
+      dst[0] = make_float4(o0.hi, o0.lo, o1.hi, o1.lo);
+      dst[1] = make_float4(o2.hi, o2.lo, o3.hi, o3.lo);
+    }
+    if (nitem < items) bt_store_u(su + (size_t)(st ^ 1) * 2 * kT * kBS, mode, tid, vn);
+    __syncthreads();                                        // stage st consumed; su[st ^ 1] ready
+  }
+}
+
+// OUT[i][s] = sum_{J >= I} row part of tile (I, J) + sum_{J < I} column part of
+// tile (J, I), in a fixed order, then the epilogue:
+// mode 0 (Woodbury): U written as complex [row][scene]
+// mode 1 (primal):   x-update X = V + mu U (row i is pixel i: the full active set)
+__global__ void __launch_bounds__(256)
+bspd_reduce_kernel(const float2* __restrict__ part, size_t part_stride, float* const* __restrict__ outq, int n,
+                   int mode, BatchDev b) {
+  const int q = blockIdx.y, I = blockIdx.x;
+  const int nt = ntiles_side(n);
+  const int i = I * kT + (threadIdx.x >> 2), s0 = 4 * (threadIdx.x & 3);
+  DF acc[4] = {DF{0.f, 0.f}, DF{0.f, 0.f}, DF{0.f, 0.f}, DF{0.f, 0.f}};
+  const float2* pq = part + (size_t)q * part_stride;
+  for (int J = 0; J < nt; ++J) {
+    const int a = min(I, J), c = max(I, J);
+    const float2* p = pq + (size_t)tile_index(a, c, nt) * kBtPart + (J >= I ? 0 : kT * kBS) +
+                      (threadIdx.x >> 2) * kBS + s0;
+    const float4 x = reinterpret_cast<const float4*>(p)[0], y = reinterpret_cast<const float4*>(p)[1];
+    df_add(acc[0], DF{x.x, x.y});
+    df_add(acc[1], DF{x.z, x.w});
+    df_add(acc[2], DF{y.x, y.y});
+    df_add(acc[3], DF{y.z, y.w});
   }
   if (i >= n) return;
 #pragma unroll
-  for (int s = 0; s < kBS; ++s) {
-    double g = (double)sh[s] + (double)sl[s];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
-    if (lane != s) continue;
+  for (int e = 0; e < 4; ++e) {
+    const int s = s0 + e;
+    const float g = acc[e].hi + acc[e].lo;
     if (mode == 0) {
-      outq[q][cidx(i, s)] = (float)g;
+      outq[q][cidx(i, s)] = g;
     } else {
-      // primal form: row i is pixel i (the full active set, in pixel order)
       const size_t o = ((size_t)q * b.N + i) * kBS + s;
-      const size_t p = (size_t)i * kBS + s;
+      const size_t pp = (size_t)i * kBS + s;
       const float xo = b.X[o];
-      const float v = xo - b.xbar[p] + b.zbar[p] - b.sd[p];
-      const float xn = fmaf(b.mu, (float)g, v);
+      const float v = xo - b.xbar[pp] + b.zbar[pp] - b.sd[pp];
+      const float xn = fmaf(b.mu, g, v);
       b.dX[o] = xn - xo;
       b.X[o] = xn;
     }
@@ -472,7 +591,10 @@ struct BatchCtx {
   std::vector<void*> owned;
   float *X = nullptr, *dX = nullptr, *xbar = nullptr, *zbar = nullptr, *sd = nullptr, *lor = nullptr;
   float2 **dA = nullptr, **dY = nullptr, **dR = nullptr, **dF = nullptr;
-  std::vector<float2*> fpair;      // full-factor (hi, lo) pairs, one per sensor
+  std::vector<float2*> fpair;      // packed symmetric factor pairs, one per sensor
+  float2* bpart = nullptr;         // per-tile partial sums of the factor apply
+  size_t bpart_stride = 0;
+  int* berr = nullptr;             // set if a factor tile copy timed out
   float **dU = nullptr, **dG = nullptr;
   float2* partial = nullptr;
   double* rpart = nullptr;
@@ -504,6 +626,22 @@ int single_export(sadmm_t h, int q, const float2** A, const double** F, int* n, 
 
 namespace {
 
+int launch_bspd(BatchCtx& c, const float* const* u, float* const* out, int mode, const BatchDev& bv) {
+  const int nt = div_up(c.n, kT), items = c.Q * nt * (nt + 1) / 2;
+  const int smem = 2 * kBtTileBytes + 2 * 2 * kT * kBS * (int)sizeof(float);
+  static bool conf = false;
+  if (!conf) {
+    SADMM_CUDA_TRY(cudaFuncSetAttribute(bspd_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    conf = true;
+  }
+  bspd_tile_kernel<<<std::min(items, 152 * 2), kBtThreads, smem, c.st>>>(
+      (const float2* const*)c.dF, u, c.bpart, c.bpart_stride, c.n, mode, items, c.berr);
+  SADMM_LAUNCH_CHECK();
+  bspd_reduce_kernel<<<dim3(nt, c.Q), 256, 0, c.st>>>(c.bpart, c.bpart_stride, out, c.n, mode, bv);
+  SADMM_LAUNCH_CHECK();
+  return SADMM_OK;
+}
+
 int batch_launch_iteration(BatchCtx& c) {
   const BatchDev bv = c.view();
   dim3 gf(div_up(c.KM, kBfRows), c.chunks, c.Q);
@@ -519,14 +657,11 @@ int batch_launch_iteration(BatchCtx& c) {
   bfwd_reduce_kernel<<<dim3(div_up((long long)c.KM * kBS, 256), c.Q), 256, 0, c.st>>>(c.partial, c.dY, c.dR, c.KM,
                                                                                      c.chunks);
   SADMM_LAUNCH_CHECK();
-  const size_t smem = (size_t)(kBsChunk + 1) * kBS * sizeof(float);
   const dim3 ga(div_up(c.N, kBaPix), c.Q, c.asplits);
   const size_t asmem = 2 * sizeof(float2) * kBaPix * kBaPad;
   const dim3 gr(div_up((long long)c.N * kBS, 256), c.Q);
   if (c.woodbury) {
-    bspd_kernel<<<dim3(div_up(c.n, kBsWarps), c.Q), kBsWarps * 32, smem, c.st>>>(
-        c.dF, (const float* const*)c.dR, c.dU, c.n, c.ld, 0, bv);
-    SADMM_LAUNCH_CHECK();
+    SADMM_TRY(launch_bspd(c, (const float* const*)c.dR, c.dU, 0, bv));
     badj_kernel<<<ga, kBaThreads, asmem, c.st>>>(c.dA, (const float2* const*)c.dU, c.gpart, c.asplits, bv);
     SADMM_LAUNCH_CHECK();
     badj_reduce_kernel<<<gr, 256, 0, c.st>>>(c.gpart, c.asplits, c.dG, 0, bv);
@@ -536,9 +671,7 @@ int batch_launch_iteration(BatchCtx& c) {
     SADMM_LAUNCH_CHECK();
     badj_reduce_kernel<<<gr, 256, 0, c.st>>>(c.gpart, c.asplits, c.dG, 1, bv);
     SADMM_LAUNCH_CHECK();
-    bspd_kernel<<<dim3(div_up(c.n, kBsWarps), c.Q), kBsWarps * 32, smem, c.st>>>(
-        c.dF, (const float* const*)c.dG, nullptr, c.n, c.ld, 1, bv);
-    SADMM_LAUNCH_CHECK();
+    SADMM_TRY(launch_bspd(c, (const float* const*)c.dG, nullptr, 1, bv));
   }
   const int nblk = div_up(c.N, kBrThreads / kBS);
   bresid_kernel<<<nblk, kBrThreads, 0, c.st>>>(bv, c.rpart);
@@ -590,6 +723,7 @@ int sadmm_batch_create(int Q, int M, int K, int N, int S, double rho, const doub
   b->partial = (float2*)A((size_t)Q * b->chunks * KS * sizeof(float2));
   b->rpart = (double*)A((size_t)div_up(N, kBrThreads / kBS) * kBS * kBrSums * sizeof(double));
   b->scal = (IterScalars*)A(kBS * sizeof(IterScalars));
+  b->berr = (int*)A(sizeof(int));
   b->ybuf = (float2*)A((size_t)S * Q * b->KM * sizeof(float2));
   b->xout = (float*)A((size_t)S * N * 4);
   std::vector<void*> Y(Q), R(Q), U(Q), G(Q);
@@ -612,7 +746,8 @@ int sadmm_batch_create(int Q, int M, int K, int N, int S, double rho, const doub
       cudaMemcpy(b->dY, Y.data(), Q * sizeof(void*), cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(b->dR, R.data(), Q * sizeof(void*), cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(b->dU, U.data(), Q * sizeof(void*), cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemcpy(b->dG, G.data(), Q * sizeof(void*), cudaMemcpyHostToDevice) != cudaSuccess) {
+      cudaMemcpy(b->dG, G.data(), Q * sizeof(void*), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemset(b->berr, 0, sizeof(int)) != cudaSuccess) {
     for (void* p : b->owned) cudaFree(p);
     sadmm_destroy(single);
     delete b;
@@ -652,14 +787,20 @@ int sadmm_batch_solve(sadmm_batch_t b, const float* y, float* x_out, int iters, 
       const float2* A = nullptr;
       const double* F = nullptr;
       SADMM_TRY(single_export(b->single, q, &A, &F, &b->n, &b->ld, &b->woodbury));
-      // the batched apply reads the full factor as (hi, lo) pairs
+      // the batched apply reads the packed symmetric factor as (hi, lo) pairs
       if (!b->fpair[q]) {
-        b->fpair[q] = (float2*)b->dalloc((size_t)b->n * b->ld * sizeof(float2));
+        b->fpair[q] = (float2*)b->dalloc(sym_packed_pairs(b->n) * sizeof(float2));
         if (!b->fpair[q]) { set_error("sadmm_batch_solve: factor allocation failed"); return SADMM_ENOMEM; }
       }
-      SADMM_TRY(launch_split_f64(F, b->fpair[q], (size_t)b->n * b->ld, b->st));
+      SADMM_TRY(launch_pack_sym(F, b->ld, b->n, b->fpair[q], b->st));
       Ap[q] = (void*)A;
       Fp[q] = (void*)b->fpair[q];
+    }
+    if (!b->bpart) {
+      const size_t nt = div_up(b->n, kT);
+      b->bpart_stride = nt * (nt + 1) / 2 * kBtPart;
+      b->bpart = (float2*)b->dalloc((size_t)b->Q * b->bpart_stride * sizeof(float2));
+      if (!b->bpart) { set_error("sadmm_batch_solve: scratch allocation failed"); return SADMM_ENOMEM; }
     }
     SADMM_CUDA_TRY(cudaMemcpyAsync(b->dA, Ap.data(), b->Q * sizeof(void*), cudaMemcpyHostToDevice, b->st));
     SADMM_CUDA_TRY(cudaMemcpyAsync(b->dF, Fp.data(), b->Q * sizeof(void*), cudaMemcpyHostToDevice, b->st));
@@ -706,9 +847,16 @@ int sadmm_batch_solve(sadmm_batch_t b, const float* y, float* x_out, int iters, 
     SADMM_CUDA_TRY(cudaMemcpyAsync(x_out, b->xout, NS * 4, cudaMemcpyDefault, b->st));
   }
   IterScalars h[kBS];
+  int herr = 0;
   SADMM_CUDA_TRY(cudaMemcpyAsync(h, b->scal, sizeof h, cudaMemcpyDeviceToHost, b->st));
+  SADMM_CUDA_TRY(cudaMemcpyAsync(&herr, b->berr, sizeof(int), cudaMemcpyDeviceToHost, b->st));
   SADMM_CUDA_TRY(cudaStreamSynchronize(b->st));
   b->k = iters;
+  if (herr) {
+    SADMM_CUDA_TRY(cudaMemset(b->berr, 0, sizeof(int)));
+    set_error("batched factor apply: a tile copy did not complete within the wait limit");
+    return SADMM_ETIMEOUT;
+  }
   for (int s = 0; s < kBS; ++s)
     if (iters > 0 && h[s].nonfinite) { set_error("non-finite value in scene %d", s); return SADMM_ENONFINITE; }
   if (st) {
@@ -718,7 +866,7 @@ int sadmm_batch_solve(sadmm_batch_t b, const float* y, float* x_out, int iters, 
     st->r_pri = h[0].r_pri; st->eps_pri = h[0].eps_pri; st->d = h[0].d; st->eps_dual = h[0].eps_dual;
     st->relchange = h[0].relchange;
     st->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-    st->bytes_iter = (double)iters * ((double)b->Q * b->KM * b->N * 16.0 + (double)b->Q * b->n * b->ld * 8.0);
+    st->bytes_iter = (double)iters * ((double)b->Q * b->KM * b->N * 16.0 + (double)b->Q * sym_packed_pairs(b->n) * 8.0);
   }
   return SADMM_OK;
 }

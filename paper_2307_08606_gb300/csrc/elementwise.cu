@@ -9,7 +9,7 @@ namespace sadmm {
 
 namespace {
 
-constexpr int kResThreads = 256;
+constexpr int kResThreads = 128;
 constexpr int kNumSums = 8;
 constexpr int kSscThreads = 1024;
 
@@ -59,6 +59,8 @@ residual_kernel(const __grid_constant__ SolverView sv, double* __restrict__ part
 #pragma unroll
   for (int j = 0; j < kNumSums; ++j) acc[j] = 0.0;
   if (i < sv.N) {
+    // per-pixel terms in FP32 (a handful per thread; GB300's FP64 pipe is
+    // narrow), cross-thread sums in FP64
     const size_t N = sv.N;
     float sx = 0.f;
     for (int q = 0; q < sv.Q; ++q) sx += sv.x[q * N + i];
@@ -66,24 +68,29 @@ residual_kernel(const __grid_constant__ SolverView sv, double* __restrict__ part
     const float xb_old = sv.xbar[i], zb_old = sv.zbar[i], s_old = sv.s[i];
     const float zb = soft_threshold(xb + s_old, sv.lam_over_rho);
     const float sn = (s_old + xb) - zb;
-    const double dxb = (double)xb - (double)xb_old;
-    const double dzb = (double)zb - (double)zb_old;
-    const double e = (double)xb - (double)zb;
-    acc[0] = e * e;
+    const float dxb = xb - xb_old;
+    const float dzb = zb - zb_old;
+    const float e = xb - zb;
+    float a1 = 0.f, a2 = 0.f, a3 = 0.f, a5 = 0.f;
     const float* ring = sv.ring + (size_t)sv.slot * sv.Q * N;
     for (int q = 0; q < sv.Q; ++q) {
-      const double xq = sv.x[q * N + i];
-      const double dx = ring[q * N + i];
-      const double zq = xq - (double)xb + (double)zb;
-      const double dz = dx - dxb + dzb;
-      acc[1] += xq * xq;
-      acc[2] += zq * zq;
-      acc[3] += dz * dz;
-      acc[5] += dx * dx;
+      const float xq = sv.x[q * N + i];
+      const float dx = ring[q * N + i];
+      const float zq = (xq - xb) + zb;
+      const float dz = (dx - dxb) + dzb;
+      a1 = fmaf(xq, xq, a1);
+      a2 = fmaf(zq, zq, a2);
+      a3 = fmaf(dz, dz, a3);
+      a5 = fmaf(dx, dx, a5);
     }
+    acc[0] = (double)e * e;
+    acc[1] = a1;
+    acc[2] = a2;
+    acc[3] = a3;
+    acc[5] = a5;
     acc[4] = (double)sn * sn;
     acc[6] = (double)zb * zb;
-    acc[7] = dzb * dzb;
+    acc[7] = (double)dzb * dzb;
     sv.xbar[i] = xb;
     sv.zbar[i] = zb;
     sv.s[i] = sn;

@@ -20,82 +20,14 @@
 // conflict.  Per-tile partial sums (pairs) go to a scratch buffer; a second
 // kernel adds them in a fixed order and applies the epilogue.
 #include "common.cuh"
+#include "symtile.cuh"
 
 namespace sadmm {
 namespace {
 
-constexpr int kT = kSymTile;                  // tile side
+using namespace symtile;
 constexpr int kTileBytes = kT * kT * (int)sizeof(float2);
 constexpr int kSpdThreads = 2 * kT;           // 64 row threads + 64 column threads
-constexpr long long kWaitLimit = 1ll << 26;   // bounded mbarrier wait (far beyond any copy time)
-
-struct DF {
-  float hi, lo;
-};
-
-__device__ __forceinline__ void df_acc(DF& s, float w_hi, float w_lo, float u) {
-  const float p = w_hi * u;
-  float e = fmaf(w_hi, u, -p);          // w_hi u = p + e exactly
-  e = fmaf(w_lo, u, e);
-  const float t = s.hi + p;             // two-sum s.hi + p = t + err
-  const float bp = t - s.hi;
-  const float err = (s.hi - (t - bp)) + (p - bp);
-  s.hi = t;
-  s.lo += err + e;
-}
-
-__device__ __forceinline__ void df_add(DF& s, DF b) {
-  const float t = s.hi + b.hi;
-  const float bp = t - s.hi;
-  const float err = (s.hi - (t - bp)) + (b.hi - bp);
-  s.hi = t;
-  s.lo += err + b.lo;
-}
-
-__device__ __forceinline__ DF df_norm(DF s) {
-  const float t = s.hi + s.lo;
-  return DF{t, s.lo - (t - s.hi)};
-}
-
-__device__ __forceinline__ unsigned smem_u32(const void* p) {
-  return (unsigned)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
-}
-
-__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-               : "memory");
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar))
-      : "memory");
-}
-
-// Waits for phase `parity` of the barrier; false after kWaitLimit polls.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
-  for (long long it = 0; it < kWaitLimit; ++it) {
-    unsigned ok;
-    asm volatile(
-        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    if (ok) return true;
-  }
-  return false;
-}
-
-__host__ __device__ __forceinline__ int ntiles_side(int n) { return (n + kT - 1) / kT; }
-
-// tile number t of an nt x nt upper triangle -> (I, J)
-__device__ __forceinline__ void tile_ij(int t, int nt, int& I, int& J) {
-  I = 0;
-  while (t >= nt - I) { t -= nt - I; ++I; }
-  J = I + t;
-}
 
 // item -> (set, tile): items are numbered set after set
 __device__ __forceinline__ int item_set(const SetBlock<SpdSet>& sets, int nsets, int item, int& t) {
@@ -222,7 +154,7 @@ spd_reduce_kernel(const __grid_constant__ SetBlock<SpdSet> sets, bool update, co
       p[u] = make_float2(0.f, 0.f);
       if (J < nt) {
         const int a = min(I, J), b = max(I, J);
-        const int t = a * nt - a * (a - 1) / 2 + (b - a);
+        const int t = tile_index(a, b, nt);
         p[u] = ss.part[(size_t)t * 2 * kT + (J >= I ? 0 : kT) + threadIdx.x];
       }
     }
@@ -249,7 +181,7 @@ __global__ void pack_sym_kernel(const double* __restrict__ F, int ld, int n, flo
   const int I = blockIdx.y, J = blockIdx.x;
   if (I > J) return;
   const int nt = ntiles_side(n);
-  const size_t t = (size_t)I * nt - (size_t)I * (I - 1) / 2 + (J - I);
+  const size_t t = tile_index(I, J, nt);
   float2* out = P + t * kT * kT;
   for (int e = threadIdx.x; e < kT * kT; e += blockDim.x) {
     const int r = I * kT + e / kT, c = J * kT + e % kT;

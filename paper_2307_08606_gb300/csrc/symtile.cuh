@@ -1,0 +1,86 @@
+// Device helpers shared by the symmetric factor applies (spd.cu, batch.cu):
+// double-float accumulation with exact products, bulk asynchronous copies
+// completing on an mbarrier (with bounded waits), and the packed
+// upper-triangular tile numbering.
+#pragma once
+#include "common.cuh"
+
+namespace sadmm {
+namespace symtile {
+
+constexpr int kT = kSymTile;
+constexpr long long kWaitLimit = 1ll << 26;   // mbarrier polls before giving up
+
+struct DF {
+  float hi, lo;
+};
+
+__device__ __forceinline__ void df_acc(DF& s, float w_hi, float w_lo, float u) {
+  const float p = w_hi * u;
+  float e = fmaf(w_hi, u, -p);          // w_hi u = p + e exactly
+  e = fmaf(w_lo, u, e);
+  const float t = s.hi + p;             // two-sum s.hi + p = t + err
+  const float bp = t - s.hi;
+  const float err = (s.hi - (t - bp)) + (p - bp);
+  s.hi = t;
+  s.lo += err + e;
+}
+
+__device__ __forceinline__ void df_add(DF& s, DF b) {
+  const float t = s.hi + b.hi;
+  const float bp = t - s.hi;
+  const float err = (s.hi - (t - bp)) + (b.hi - bp);
+  s.hi = t;
+  s.lo += err + b.lo;
+}
+
+__device__ __forceinline__ DF df_norm(DF s) {
+  const float t = s.hi + s.lo;
+  return DF{t, s.lo - (t - s.hi)};
+}
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Waits for phase `parity` of the barrier; false after kWaitLimit polls.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+  for (long long it = 0; it < kWaitLimit; ++it) {
+    unsigned ok;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+__host__ __device__ __forceinline__ int ntiles_side(int n) { return (n + kT - 1) / kT; }
+
+__host__ __device__ __forceinline__ int tile_index(int I, int J, int nt) { return I * nt - I * (I - 1) / 2 + (J - I); }
+
+// tile number t of an nt x nt upper triangle -> (I, J)
+__device__ __forceinline__ void tile_ij(int t, int nt, int& I, int& J) {
+  I = 0;
+  while (t >= nt - I) { t -= nt - I; ++I; }
+  J = I + t;
+}
+
+
+}  // namespace symtile
+}  // namespace sadmm
