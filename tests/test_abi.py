@@ -57,3 +57,18 @@ def test_invalid_sizes_rejected_before_any_device_work():
     # rho <= 0
     assert lib.sadmm_create(2, 4, 8, 16, 0.0, 0.1, ctypes.byref(crit), ctypes.byref(h)) == binding.EINVAL
     assert b"invalid" in lib.sadmm_last_error()
+
+
+def test_default_criterion_matches_the_paper_setup(lib):
+    """The library's Algorithm 1 defaults are the values Section IV prints
+    (tests/golden/simulation_parameters.json)."""
+    import json
+    import os
+    from paper_2307_08606_gb300 import binding
+    with open(os.path.join(os.path.dirname(__file__), "golden", "simulation_parameters.json")) as f:
+        gold = json.load(f)
+    c = binding.default_criterion()
+    assert c.Kp == gold["Kp"]
+    assert c.eps_p == gold["eps_p"]
+    assert c.eps_abs == gold["eps_abs"]
+    assert c.eps_rel == gold["eps_rel"]
