@@ -48,6 +48,8 @@ def parse():
                     help="keep only the first S sensors (smaller case for profiler captures)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the chosen-form comparison (precision 3 and elimination vs plain FP32)")
     ap.add_argument("--no-learned", action="store_true",
                     help="skip the learned-step cost measurement (elim 2 on the bench scene)")
     ap.add_argument("--no-batched", action="store_true",
@@ -212,6 +214,52 @@ def batched_measure(args, dev, stream, rank):
             "ms_per_iteration": ms / (iters * reps), "operator_bytes_per_iteration": op_bytes,
             "operator_GBps_effective": op_bytes / (ms / (iters * reps) / 1e3) / 1e9,
             "gpu_launches": int(launches)}
+
+
+def forms_measure(sc, lam, dev, stream, iters=400):
+    """The chosen forms against plain FP32 on the bench scene, from the same
+    cold start for the same number of iterations:
+      - precision 3 (BF16 hi plane every iteration, lo-plane products refreshed
+        every 4 iterations and after every set change);
+      - elimination (Algorithm 1) with the per-iteration host decisions and the
+        factor downdates it needs, with the active-set fraction at the end and
+        the HBM rate of its iterations alone.
+    x_G is identically zero on this scene (Eq. 2 is degenerate there), so the
+    forms are compared on the stacked iterate X: |X_form - X_plain| / |X_plain|."""
+    import torch
+    from paper_2307_08606_gb300 import binding
+    g = sc.geom
+    At = [torch.from_numpy(a).to(dev) for a in sc.A]
+    y_dev = [torch.from_numpy(v).to(dev) for v in sc.y]
+    out, Xp = {}, None
+    for name, kw in (("plain_fp32", dict(elim=0)), ("bf16_hi_corr4", dict(elim=0, precision=3, correct_every=4)),
+                     ("elim_fp32", dict(elim=1))):
+        s = binding.Solver(g.Q, g.M, g.K, g.N, 1.0, lam, stream=stream.cuda_stream, **kw)
+        for q in range(g.Q):
+            s.set_operator(q, At[q])
+        s.prepare()
+        s.solve(y_dev, 20)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        xg, st = s.solve(y_dev, iters)
+        torch.cuda.synchronize()
+        ms = (time.perf_counter() - t0) * 1e3
+        X = s.X()
+        s.close()
+        if Xp is None:
+            Xp = X
+        it_ms = ms - st["ms_refresh"]
+        out[name] = {"ms": round(ms, 2), "iters_per_s": iters / (ms / 1e3),
+                     "rel_diff_X_vs_plain": float(np.linalg.norm(X - Xp) / np.linalg.norm(Xp)),
+                     "xg_max_abs": float(np.max(np.abs(xg))),
+                     "active_fraction_end": st["active_total"] / (g.Q * g.N),
+                     "refresh_ms": round(st["ms_refresh"], 2), "refreshes": st["refreshes"],
+                     "iteration_GBps": st["bytes_iter"] / (it_ms / 1e3) / 1e9 if it_ms > 0 else None}
+    base = out["plain_fp32"]["ms"]
+    for v in out.values():
+        v["speedup_vs_plain_fp32"] = base / v["ms"]
+    out["workload"] = f"bench scene, {iters} iterations from zero per form"
+    return out
 
 
 def learned_measure(sc, lam, dev, stream):
@@ -444,6 +492,8 @@ def main():
         line["batched"] = batched_measure(args, dev, stream, rank)
     if not args.no_learned:
         line["learned"] = learned_measure(sc, lam, dev, stream)
+    if not args.no_forms:
+        line["forms"] = forms_measure(sc, lam, dev, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
             line["cpu_baseline"] = cpu_baseline_sample(sc, lam)

@@ -353,6 +353,17 @@ int sadmm_factor_update(const float* A, int KM, const int* E, int e, double mu, 
  * and synchronises it.  SADMM_ETIMEOUT if a tile copy did not complete. */
 int sadmm_spd_apply(const double* F, int n, int ldf, const float* u, float* out, void* stream);
 
+/* G = Re(A^H W) for one sensor and 16 right-hand sides on the tensor cores:
+ * the adjoint product of the batched form (Eq. 3, x_q-update for 16 scenes),
+ * the paper has no batched form.  A: device complex64, N x KM pixel-major (as
+ * sadmm_set_operator); W: device complex64, KM x 16 ([row][scene]); G: device
+ * float, N x 16 ([pixel][scene]).  Each operand is split into TF32 hi + lo and
+ * hi*hi + hi*lo + lo*hi is accumulated in FP32 (tcgen05.mma kind::tf32), which
+ * is within a few FP32 roundings of the FP32 product.  2KM must be a multiple
+ * of 32.  Allocates a few bytes of scratch on `stream` and synchronises it;
+ * SADMM_ETIMEOUT if a tensor-core wait timed out. */
+int sadmm_adjoint16_tc(const float* A, int KM, int N, const float* W, float* G, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

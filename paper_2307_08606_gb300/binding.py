@@ -81,6 +81,7 @@ _SIGS = {
     "sadmm_spd_apply": (C.c_int, [_P, C.c_int, C.c_int, _P, _P, _P]),
     "sadmm_factor_downdate": (C.c_int, [_P, C.c_int, _P, C.c_int, C.c_double, _P, _P]),
     "sadmm_factor_update": (C.c_int, [_P, C.c_int, _P, C.c_int, C.c_double, C.c_int, _P, _P]),
+    "sadmm_adjoint16_tc": (C.c_int, [_P, C.c_int, C.c_int, _P, _P, _P]),
     "sadmm_batch_create": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double,
                                      C.POINTER(C.c_double), C.POINTER(Criterion), C.POINTER(_P)]),
     "sadmm_batch_set_stream": (C.c_int, [_P, _P]),
@@ -478,6 +479,15 @@ def factor(A, idx, mu, rho, stream=0):
     check(load().sadmm_factor(_ptr(A), KM, A.shape[0], _ptr(idx), nidx, float(mu), float(rho),
                               _ptr(F), npad, C.byref(form), C.c_void_p(stream)))
     return F, form.value, n
+
+
+def adjoint16_tc(A, W, stream=0):
+    """G (N x 16 float) = Re(A^H W) on the tensor cores; A (N, KM) complex64, W (KM, 16) complex64."""
+    import torch
+    N, KM = A.shape
+    G = torch.empty((N, 16), dtype=torch.float32, device=A.device)
+    check(load().sadmm_adjoint16_tc(_ptr(A), KM, N, _ptr(W), _ptr(G), C.c_void_p(stream)))
+    return G
 
 
 def factor_update(A, E, mu, sign, W, stream=0):

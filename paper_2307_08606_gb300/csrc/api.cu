@@ -524,6 +524,12 @@ int launch_split_products_adj(Ctx& c, const SolverView& sv, bool corr) {
   return launch_split_adjoint(gout.data(), (int)gout.size(), c.KM, kind, planes, false, sv, c.st);
 }
 
+// Columns a Woodbury factor may gain or lose by rank updates before it is
+// rebuilt from scratch.  Each pass applies the Woodbury identity exactly in
+// FP64, so rounding grows with the number of passes only; 2n columns (n = 2KM)
+// keeps it far below the FP32 iteration's own rounding.
+int refactor_after(const Ctx& c) { return 4 * c.KM; }
+
 // After an SSC pass that shrank some sets: fold frozen pixels into y' (or
 // re-average in zero mode) and refresh the factors of those sensors.
 int apply_changes(Ctx& c, const std::vector<int>& changed) {
@@ -545,7 +551,7 @@ int apply_changes(Ctx& c, const std::vector<int>& changed) {
   for (int q : changed) {
     const Sensor& S = c.s[q];
     const int e = c.h_counts[c.Q + q];
-    if (S.woodbury && S.cnt > 2 * c.KM && S.cum_dd + e <= std::max(kDowndateMax, c.KM / 2)) dd.push_back(q);
+    if (S.woodbury && S.cnt > 2 * c.KM && S.cum_dd + e <= refactor_after(c)) dd.push_back(q);
     else full.push_back(q);
   }
   SADMM_TRY(downdate(c, dd, &full));
@@ -584,7 +590,7 @@ int readmit(Ctx& c, int* total) {
   for (int q : added) {
     const Sensor& S = c.s[q];
     const int e = c.h_counts[3 * c.Q + q];
-    if (S.woodbury && S.cum_dd + e <= std::max(kDowndateMax, c.KM / 2)) up.push_back(q);
+    if (S.woodbury && S.cum_dd + e <= refactor_after(c)) up.push_back(q);
     else full.push_back(q);
   }
   SADMM_TRY(downdate(c, up, &full, true));
@@ -597,7 +603,7 @@ double iter_bytes(const Ctx& c) {
   for (const Sensor& S : c.s) {
     if (S.cnt == 0) continue;
     const double per_entry = c.crit.precision == 0 ? 8.0 : (c.periodic() ? 4.0 : 8.0);
-    b += 2.0 * c.KM * (double)S.cnt * per_entry + (double)S.n * S.n * sizeof(double);
+    b += 2.0 * c.KM * (double)S.cnt * per_entry + (double)sym_packed_pairs(S.n) * sizeof(float2);
   }
   return b;
 }

@@ -367,82 +367,9 @@ bspd_reduce_kernel(const float2* __restrict__ part, size_t part_stride, float* c
 }
 
 // ------------------------------------------------------------------ adjoint
-// G[j][s] = Re(a_j^H w_s): output tile 128 pixels x 16 scenes, thread tile
-// 4 pixels x 4 scenes; K loop over complex rows in slabs of 16.
-constexpr int kBaPix = 128;
-constexpr int kBaSlab = 16;
-constexpr int kBaThreads = 128;
-
-// Partial G over the rows [r_begin, r_end) of split blockIdx.z, written to
-// gpart[q][split][pixel][scene]; badj_reduce_kernel adds the splits in order.
-constexpr int kBaPad = kBaSlab + 2;   // row stride 144 bytes: 16-byte aligned, conflict-free reads
-
-__global__ void __launch_bounds__(kBaThreads)
-badj_kernel(const float2* const* __restrict__ Aq, const float2* const* __restrict__ Wq, float* __restrict__ gpart,
-            int splits, BatchDev b) {
-  const int q = blockIdx.y;
-  const int j0 = blockIdx.x * kBaPix;
-  const int KM = b.KM, N = b.N;
-  const int rows_per = (KM / splits + kBaSlab - 1) / kBaSlab * kBaSlab;
-  const int rb = blockIdx.z * rows_per, re = min(KM, rb + rows_per);
-  extern __shared__ float4 smem4[];
-  float2 (*sA)[kBaPix][kBaPad] = reinterpret_cast<float2 (*)[kBaPix][kBaPad]>(smem4);      // [2][pix][pad]
-  __shared__ float2 sW[kBaSlab][kBS];
-  const int tid = threadIdx.x;
-  const int tp = tid / 4, ts = tid % 4;            // 32 pixel groups x 4 scene groups
-  float acc[4][4];
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int s = 0; s < 4; ++s) acc[i][s] = 0.f;
-  const float2* A = Aq[q];
-  const float2* W = Wq[q];
-  auto stage = [&](int buf, int r0) {
-    for (int e = tid; e < kBaPix * kBaSlab / 2; e += kBaThreads) {
-      const int pp = e / (kBaSlab / 2), r2 = e % (kBaSlab / 2);
-      const int j = j0 + pp, r = r0 + 2 * r2;
-      const bool ok = j < N && r < re;
-      cp_async16(&sA[buf][pp][2 * r2], ok ? (const void*)(A + (size_t)j * KM + r) : (const void*)A, ok);
-    }
-    cp_async_commit();
-  };
-  if (rb < re) stage(0, rb);
-  int buf = 0;
-  for (int r0 = rb; r0 < re; r0 += kBaSlab, buf ^= 1) {
-    const bool more = r0 + kBaSlab < re;
-    if (more) stage(buf ^ 1, r0 + kBaSlab);
-    for (int e = tid; e < kBaSlab * kBS; e += kBaThreads) {
-      const int rr = e / kBS, s = e % kBS, r = r0 + rr;
-      sW[rr][s] = r < re ? W[(size_t)r * kBS + s] : make_float2(0.f, 0.f);
-    }
-    if (more) cp_async_wait<1>(); else cp_async_wait<0>();
-    __syncthreads();
-#pragma unroll 4
-    for (int rr = 0; rr < kBaSlab; ++rr) {
-      float2 a[4], w[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = sA[buf][tp + 32 * i][rr];
-#pragma unroll
-      for (int s = 0; s < 4; ++s) w[s] = sW[rr][ts + 4 * s];
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int s = 0; s < 4; ++s) acc[i][s] = fmaf(a[i].x, w[s].x, fmaf(a[i].y, w[s].y, acc[i][s]));
-    }
-    __syncthreads();
-  }
-  float* out = gpart + ((size_t)q * splits + blockIdx.z) * N * kBS;
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int j = j0 + tp + 32 * i;
-    if (j >= N) continue;
-#pragma unroll
-    for (int s4 = 0; s4 < 4; ++s4) out[(size_t)j * kBS + ts + 4 * s4] = acc[i][s4];
-  }
-}
-
-// G = sum of the split partials (split order).  mode 0: x-update epilogue
-// (Woodbury form); mode 1: G into gq [pixel][scene] (primal form).
+// G_q = Re(A_q^H W_q) for the 16 scenes runs on the tensor cores (tc.cu,
+// 3xTF32 tcgen05 GEMM into gpart[q][split][pixel][scene]); the splits of the
+// row range are added here in order, followed by the x-update epilogue.
 __global__ void badj_reduce_kernel(const float* __restrict__ gpart, int splits, float* const* __restrict__ gq,
                                    int mode, BatchDev b) {
   const int q = blockIdx.y;
@@ -657,18 +584,14 @@ int batch_launch_iteration(BatchCtx& c) {
   bfwd_reduce_kernel<<<dim3(div_up((long long)c.KM * kBS, 256), c.Q), 256, 0, c.st>>>(c.partial, c.dY, c.dR, c.KM,
                                                                                      c.chunks);
   SADMM_LAUNCH_CHECK();
-  const dim3 ga(div_up(c.N, kBaPix), c.Q, c.asplits);
-  const size_t asmem = 2 * sizeof(float2) * kBaPix * kBaPad;
   const dim3 gr(div_up((long long)c.N * kBS, 256), c.Q);
   if (c.woodbury) {
     SADMM_TRY(launch_bspd(c, (const float* const*)c.dR, c.dU, 0, bv));
-    badj_kernel<<<ga, kBaThreads, asmem, c.st>>>(c.dA, (const float2* const*)c.dU, c.gpart, c.asplits, bv);
-    SADMM_LAUNCH_CHECK();
+    SADMM_TRY(launch_tc_adjoint(c.dA, (const float2* const*)c.dU, c.gpart, c.Q, c.N, c.KM, c.asplits, c.berr, c.st));
     badj_reduce_kernel<<<gr, 256, 0, c.st>>>(c.gpart, c.asplits, c.dG, 0, bv);
     SADMM_LAUNCH_CHECK();
   } else {
-    badj_kernel<<<ga, kBaThreads, asmem, c.st>>>(c.dA, c.dR, c.gpart, c.asplits, bv);
-    SADMM_LAUNCH_CHECK();
+    SADMM_TRY(launch_tc_adjoint(c.dA, c.dR, c.gpart, c.Q, c.N, c.KM, c.asplits, c.berr, c.st));
     badj_reduce_kernel<<<gr, 256, 0, c.st>>>(c.gpart, c.asplits, c.dG, 1, bv);
     SADMM_LAUNCH_CHECK();
     SADMM_TRY(launch_bspd(c, (const float* const*)c.dG, nullptr, 1, bv));
@@ -718,7 +641,7 @@ int sadmm_batch_create(int Q, int M, int K, int N, int S, double rho, const doub
   b->dR = (float2**)A(Q * sizeof(void*)); b->dF = (float2**)A(Q * sizeof(void*));
   b->dU = (float**)A(Q * sizeof(void*)); b->dG = (float**)A(Q * sizeof(void*));
   b->chunks = batch_chunks(Q, b->KM, N);
-  b->asplits = std::max(1, std::min(div_up(152 * 8, (long long)div_up(N, kBaPix) * Q), b->KM / 256));
+  b->asplits = tc_adjoint_splits(Q, N, b->KM);
   b->gpart = (float*)A((size_t)Q * b->asplits * NS * sizeof(float));
   b->partial = (float2*)A((size_t)Q * b->chunks * KS * sizeof(float2));
   b->rpart = (double*)A((size_t)div_up(N, kBrThreads / kBS) * kBS * kBrSums * sizeof(double));

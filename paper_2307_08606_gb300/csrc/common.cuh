@@ -107,6 +107,12 @@ struct AdjointSet {
 int launch_adjoint(const AdjointSet* sets, int nsets, int KM, bool update, const SolverView& sv,
                    cudaStream_t st);
 
+// Batched adjoint on the tensor cores (tc.cu): gpart[q][split][p][s] =
+// sum over the split's real rows of B_q[r][p] W_q[r][s] (16 scenes).
+int tc_adjoint_splits(int Q, int N, int KM);
+int launch_tc_adjoint(const float2* const* Aq, const float2* const* Wq, float* gpart, int Q, int N, int KM, int splits,
+                      int* err, cudaStream_t st);
+
 // Symmetric factors are stored as packed upper-triangular 64 x 64 tiles of
 // double-float pairs (spd.cu).
 constexpr int kSymTile = 64;

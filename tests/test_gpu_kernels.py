@@ -202,3 +202,23 @@ def test_factor_rank_update_adds_columns(B, KM, N, e):
     cond = np.linalg.cond(G)
     assert np.max(np.abs(Wu - ref)) <= 1e-14 * cond * n * np.max(np.abs(ref))
     assert np.array_equal(Wu, Wu.T)
+
+
+@pytest.mark.parametrize("KM,N", [(16, 128), (32, 200), (256, 1024), (2048, 300)])
+def test_tensor_core_adjoint16_matches_fp64(B, KM, N):
+    """Batched adjoint on tcgen05 (3xTF32 split, FP32 accumulation) against the
+    FP64 product: each of the 2KM terms is within 2^-21 of its exact value and
+    the FP32 accumulation adds at most 2KM roundings (or truncations, 2^-23) of
+    the running magnitude, so |G - G64| <= (2KM 2^-23 + 2^-20) sum |a||w|."""
+    A = _operator(KM, N, seed=KM + N, radar=(KM == 256))
+    s = scenegen.Stream(31, N)
+    W = (s.normal(KM * 16) + 1j * s.normal(KM * 16)).reshape(KM, 16).astype(np.complex64)
+    dev = torch.device("cuda:0")
+    G = B.adjoint16_tc(torch.from_numpy(A).to(dev), torch.from_numpy(W).to(dev)).cpu().numpy().astype(np.float64)
+    A64, W64 = A.astype(np.complex128), W.astype(np.complex128)
+    ref = (A64.conj() @ W64).real
+    mag = np.abs(A64.real) @ np.abs(W64.real) + np.abs(A64.imag) @ np.abs(W64.imag)
+    bound = (2 * KM * 2.0 ** -23 + 2.0 ** -20) * mag
+    err = np.abs(G - ref)
+    print(f"KM={KM} N={N}: max |G - G64| / bound = {np.max(err / bound):.3f}")
+    assert np.all(err <= bound)
