@@ -519,6 +519,7 @@ struct BatchCtx {
   float *X = nullptr, *dX = nullptr, *xbar = nullptr, *zbar = nullptr, *sd = nullptr, *lor = nullptr;
   float2 **dA = nullptr, **dY = nullptr, **dR = nullptr, **dF = nullptr;
   std::vector<float2*> fpair;      // packed symmetric factor pairs, one per sensor
+  std::vector<const float2*> hA, hR, hU;   // host copies of the per-sensor device pointers
   float2* bpart = nullptr;         // per-tile partial sums of the factor apply
   size_t bpart_stride = 0;
   int* berr = nullptr;             // set if a factor tile copy timed out
@@ -587,11 +588,11 @@ int batch_launch_iteration(BatchCtx& c) {
   const dim3 gr(div_up((long long)c.N * kBS, 256), c.Q);
   if (c.woodbury) {
     SADMM_TRY(launch_bspd(c, (const float* const*)c.dR, c.dU, 0, bv));
-    SADMM_TRY(launch_tc_adjoint(c.dA, (const float2* const*)c.dU, c.gpart, c.Q, c.N, c.KM, c.asplits, c.berr, c.st));
+    SADMM_TRY(launch_tc_adjoint(c.hA.data(), c.hU.data(), c.gpart, c.Q, c.N, c.KM, c.asplits, c.berr, c.st));
     badj_reduce_kernel<<<gr, 256, 0, c.st>>>(c.gpart, c.asplits, c.dG, 0, bv);
     SADMM_LAUNCH_CHECK();
   } else {
-    SADMM_TRY(launch_tc_adjoint(c.dA, c.dR, c.gpart, c.Q, c.N, c.KM, c.asplits, c.berr, c.st));
+    SADMM_TRY(launch_tc_adjoint(c.hA.data(), c.hR.data(), c.gpart, c.Q, c.N, c.KM, c.asplits, c.berr, c.st));
     badj_reduce_kernel<<<gr, 256, 0, c.st>>>(c.gpart, c.asplits, c.dG, 1, bv);
     SADMM_LAUNCH_CHECK();
     SADMM_TRY(launch_bspd(c, (const float* const*)c.dG, nullptr, 1, bv));
@@ -656,6 +657,10 @@ int sadmm_batch_create(int Q, int M, int K, int N, int S, double rho, const doub
     U[q] = A(2 * KS * sizeof(float));
     G[q] = A(NS * sizeof(float));
   }
+  for (int q = 0; q < Q; ++q) {
+    b->hR.push_back((const float2*)R[q]);
+    b->hU.push_back((const float2*)U[q]);
+  }
   if (!ok) {
     for (void* p : b->owned) cudaFree(p);
     sadmm_destroy(single);
@@ -706,6 +711,7 @@ int sadmm_batch_solve(sadmm_batch_t b, const float* y, float* x_out, int iters, 
   if (!b->graph_valid) {
     std::vector<void*> Ap(b->Q), Fp(b->Q);
     if (b->fpair.empty()) b->fpair.assign(b->Q, nullptr);
+    b->hA.assign(b->Q, nullptr);
     for (int q = 0; q < b->Q; ++q) {
       const float2* A = nullptr;
       const double* F = nullptr;
@@ -718,6 +724,7 @@ int sadmm_batch_solve(sadmm_batch_t b, const float* y, float* x_out, int iters, 
       SADMM_TRY(launch_pack_sym(F, b->ld, b->n, b->fpair[q], b->st));
       Ap[q] = (void*)A;
       Fp[q] = (void*)b->fpair[q];
+      b->hA[q] = A;
     }
     if (!b->bpart) {
       const size_t nt = div_up(b->n, kT);

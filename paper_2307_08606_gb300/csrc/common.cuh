@@ -108,7 +108,8 @@ int launch_adjoint(const AdjointSet* sets, int nsets, int KM, bool update, const
                    cudaStream_t st);
 
 // Batched adjoint on the tensor cores (tc.cu): gpart[q][split][p][s] =
-// sum over the split's real rows of B_q[r][p] W_q[r][s] (16 scenes).
+// sum over the split's real rows of B_q[r][p] W_q[r][s] (16 scenes).  Aq and
+// Wq are HOST arrays of Q device pointers (the tensor maps are built on the host).
 int tc_adjoint_splits(int Q, int N, int KM);
 int launch_tc_adjoint(const float2* const* Aq, const float2* const* Wq, float* gpart, int Q, int N, int KM, int splits,
                       int* err, cudaStream_t st);

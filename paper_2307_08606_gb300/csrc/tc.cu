@@ -12,18 +12,22 @@
 // FP32 one, the dropped lo*lo term is below 2^-22, and the sum over K rounds
 // as an FP32 accumulation does.
 //
-// Tile: M = 128 pixels per CTA (TMEM lanes), N = 16 scenes (TMEM columns), K
-// slabs of 32 real rows.  Per slab every thread converts one pixel's 32 floats
-// (and 4 values of W) into hi and lo operand tiles in shared memory, in the
-// canonical K-major no-swizzle layout (core matrices of 8 rows x 16 bytes;
-// K-adjacent cores LBO bytes apart, M/N-adjacent cores SBO bytes apart); one
-// thread then issues 4 k-steps x 3 products of tcgen05.mma kind::tf32
-// (M128 N16 K8) and commits them to an mbarrier.  Two operand buffers let the
-// conversion of slab i+1 overlap the MMAs of slab i.  The accumulator is read
-// back with tcgen05.ld (32 lanes x 16 columns per warp).  Every wait is
-// bounded; on a timeout the CTA flags *err, waits (bounded) for its
-// outstanding MMAs, frees its tensor memory and exits.
+// Tile: M = 128 pixels (TMEM lanes), N = 16 scenes (TMEM columns), K slabs of
+// 32 real rows.  A slab of A arrives by TMA (tensor map over the pixel-major
+// operand, 128-byte swizzle: exactly the SW128 K-major operand layout of the
+// MMA); W's slab (2 KB) by a bulk copy.  The tile is split in place into its
+// TF32 hi part plus a lo tile of the same layout; W goes to hi/lo tiles in the
+// no-swizzle K-major layout (core matrices of 8 rows x 16 bytes, K-adjacent
+// cores LBO bytes apart, N-adjacent cores SBO bytes apart).  One thread issues
+// 4 k-steps x 3 products of tcgen05.mma kind::tf32 (M128 N16 K8) per slab; the
+// accumulator is read back with tcgen05.ld (32 lanes x 16 columns per warp).
+// The pipeline structure is described at tc_adjoint_kernel.  Every wait is
+// bounded; on a timeout the CTA flags *err, waits (bounded) for its copies in
+// flight, frees its tensor memory and exits.
 #include "common.cuh"
+
+#include <cuda.h>
+#include <cstring>
 
 namespace sadmm {
 namespace {
@@ -31,7 +35,6 @@ namespace {
 constexpr int kTcM = 128;              // pixels per CTA
 constexpr int kTcN = 16;               // scenes
 constexpr int kTcK = 32;               // real rows per slab
-constexpr int kTcThreads = 128;
 constexpr int kTmemCols = 32;          // power of two >= 32, >= kTcN
 constexpr long long kTcWaitLimit = 1ll << 26;
 
@@ -40,12 +43,8 @@ constexpr int kABytes = kTcM * kTcK * 4;          // 16 KB
 constexpr int kBBytes = kTcN * kTcK * 4;          // 2 KB
 // canonical K-major layout strides (bytes)
 constexpr int kCore = 128;                         // 8 rows x 16 bytes
-constexpr int kA_SBO = kCore;                      // next 8 pixels
-constexpr int kA_LBO = (kTcM / 8) * kCore;         // next 4 k-elements (2048)
 constexpr int kB_SBO = kCore;                      // next 8 scenes
 constexpr int kB_LBO = (kTcN / 8) * kCore;         // next 4 k-elements (256)
-constexpr int kBufBytes = 2 * kABytes + 2 * kBBytes;   // A hi, A lo, B hi, B lo
-constexpr int kTcSmem = 2 * kBufBytes;
 
 __device__ __forceinline__ unsigned su32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 
@@ -94,149 +93,241 @@ __device__ __forceinline__ float tf32_rn(float x) {
   return __uint_as_float(r);
 }
 
-__global__ void __launch_bounds__(kTcThreads)
-tc_adjoint_kernel(const float2* const* __restrict__ Aq, const float2* const* __restrict__ Wq, float* __restrict__ gpart,
-                  int N, int KM, int splits, int* __restrict__ err) {
-  extern __shared__ __align__(1024) unsigned char smem[];
-  __shared__ __align__(8) uint64_t bar[2];
-  __shared__ unsigned s_tmem;
-  const int tid = threadIdx.x, warp = tid >> 5;
-  const int q = blockIdx.y, split = blockIdx.z;
-  const int p0 = blockIdx.x * kTcM;
-  const int R = 2 * KM;                                    // real rows
-  const int rows_per = (R / splits + kTcK - 1) / kTcK * kTcK;
-  const int rb = split * rows_per, re = min(R, rb + rows_per);
-  const int nslab = max(0, (re - rb) / kTcK);
-  const float* A = reinterpret_cast<const float*>(Aq[q]);
-  const float* W = reinterpret_cast<const float*>(Wq[q]);
+struct TmapSet {
+  CUtensorMap m[kMaxSets];     // A_q as a 2-D FP32 tensor: x = real row (2KM), y = pixel (N)
+};
+struct PtrSet {
+  const float* w[kMaxSets];    // W_q as floats
+};
 
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(bar)), "r"(bytes) : "memory");
+}
+
+// Persistent, warp-specialised pipeline over work items (sensor, 128-pixel
+// tile, row split), kS shared-memory stages deep:
+//   warp 0      producer: per slab one TMA tile load of A (128 pixels x 32
+//               real rows, 128-byte swizzle) and one bulk copy of the W slab;
+//   warp 1      MMA issuer: 4 k-steps x 3 tcgen05.mma per slab into one of two
+//               TMEM accumulators (alternating per item), commits free the
+//               stage and, at the end of an item, publish the accumulator;
+//   warps 2-5   converters: split the landed A tile in place into its TF32 hi
+//               part plus a lo tile (same swizzled layout) and W into hi/lo
+//               operand tiles; after an item, read its accumulator (each warp
+//               its 32-lane quarter of TMEM) and store the 128 x 16 result.
+// Barriers: full (TMA landed), conv (operands ready), empty (stage free),
+// accfull / accempty (accumulator handoff).  All waits are bounded.
+constexpr int kS = 5;
+constexpr int kPipeThreads = 192;
+constexpr int kStageBytes = 2 * kABytes + 3 * kBBytes;        // A hi, A lo, B hi, B lo, W raw
+constexpr int kPipeSmem = kS * kStageBytes + 1024;            // + alignment slack
+
+// SW128 K-major descriptor: 8-row atoms of 128-byte rows, atoms 1024 bytes apart
+__device__ __forceinline__ uint64_t sw128_desc(unsigned addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr >> 4) & 0x3FFF);
+  d |= (uint64_t)1 << 16;                                      // leading offset: unused for swizzled K-major
+  d |= (uint64_t)((1024 >> 4) & 0x3FFF) << 32;                 // stride offset: next 8 rows
+  d |= (uint64_t)1 << 46;                                      // descriptor version for tcgen05
+  d |= (uint64_t)2 << 61;                                      // 128-byte swizzle
+  return d;
+}
+
+__global__ void __launch_bounds__(kPipeThreads, 1)
+tc_adjoint_kernel(const __grid_constant__ TmapSet tmaps, const __grid_constant__ PtrSet wq, float* __restrict__ gpart,
+                  int Q, int N, int KM, int splits, int* __restrict__ err) {
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t full[kS], conv[kS], empty[kS], accfull[2], accempty[2];
+  __shared__ unsigned s_tmem;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int R = 2 * KM;
+  const int mtiles = (N + kTcM - 1) / kTcM;
+  const int items = Q * mtiles * splits;
+  const int rows_per = (R / splits + kTcK - 1) / kTcK * kTcK;
+  auto item_of = [&](int it, int& q, int& mt, int& sp, int& rb, int& ns) {
+    sp = it % splits;
+    const int qm = it / splits;
+    mt = qm % mtiles;
+    q = qm / mtiles;
+    rb = sp * rows_per;
+    ns = max(0, (min(R, rb + rows_per) - rb) / kTcK);
+  };
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&s_tmem)),
                  "r"(kTmemCols)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
-  if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&bar[0])) : "memory");
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&bar[1])) : "memory");
+  if (tid == 32) {
+    for (int s = 0; s < kS; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&conv[s], 128);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&accfull[b], 1);
+      mbar_init(&accempty[b], 128);
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const unsigned tmem = s_tmem;
-
-  // this thread's pixel and its W quad (complex row m_l, scenes 2 (tid % 8), +1)
-  const int p = p0 + tid;
-  const bool pv = p < N;
-  const float4* arow = reinterpret_cast<const float4*>(A + (size_t)(pv ? p : 0) * R);
-  const int wm = tid >> 3, ws = 2 * (tid & 7);
-  // two register sets: the loads of slab i + 2 are in flight while slabs i
-  // and i + 1 are converted and multiplied
-  float4 raA[kTcK / 4], raB[kTcK / 4];
-  float4 rwA, rwB;
-  auto load = [&](int slab, float4 (&ra)[kTcK / 4], float4& rw) {
-    const int r0 = rb + slab * kTcK;
-#pragma unroll
-    for (int e = 0; e < kTcK / 4; ++e) ra[e] = pv ? __ldcs(arow + r0 / 4 + e) : make_float4(0.f, 0.f, 0.f, 0.f);
-    rw = reinterpret_cast<const float4*>(W + ((size_t)(r0 / 2 + wm) * kTcN + ws) * 2)[0];
-  };
-  unsigned phase = 0u;          // bit b: parity to wait for on buffer b
-  unsigned pending = 0u;        // bit b: a commit on buffer b is outstanding
   bool ok = true;
-  // convert slab `slab` from registers into operand buffer slab & 1, refill
-  // the registers with slab + 2, and issue the slab's MMAs
-  auto step = [&](int slab, float4 (&ra)[kTcK / 4], float4& rw) -> bool {
-    const int b = slab & 1;
-    unsigned char* base = smem + b * kBufBytes;
-    float* Ahi = reinterpret_cast<float*>(base);
-    float* Alo = reinterpret_cast<float*>(base + kABytes);
-    float* Bhi = reinterpret_cast<float*>(base + 2 * kABytes);
-    float* Blo = reinterpret_cast<float*>(base + 2 * kABytes + kBBytes);
-    // the MMAs that last read this buffer (slab - 2) must be done
-    if ((pending >> b) & 1u) {
-      ok = bar_wait(&bar[b], (phase >> b) & 1u);
-      phase ^= 1u << b;
-      pending &= ~(1u << b);
-      if (!__syncthreads_and(ok)) return false;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------------------------------------------------------- producer
+      int t = 0;
+      for (int it = blockIdx.x; it < items && ok; it += gridDim.x) {
+        int q, mt, sp, rb, ns;
+        item_of(it, q, mt, sp, rb, ns);
+        for (int sl = 0; sl < ns && ok; ++sl, ++t) {
+          const int s = t % kS;
+          if (t >= kS) ok = bar_wait(&empty[s], ((t / kS) - 1) & 1);
+          if (!ok) break;
+          unsigned char* st = smem + s * kStageBytes;
+          mbar_expect_tx(&full[s], kABytes + kBBytes);
+          const int x = rb + sl * kTcK, y = mt * kTcM;
+          asm volatile(
+              "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+                  su32(st)),
+              "l"(reinterpret_cast<uint64_t>(&tmaps.m[q])), "r"(x), "r"(y), "r"(su32(&full[s]))
+              : "memory");
+          const float* wsrc = wq.w[q] + (size_t)x * kTcN;       // real rows x .. x+31 = complex rows x/2 ..
+          asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                           su32(st + 2 * kABytes + 2 * kBBytes)),
+                       "l"(wsrc), "r"(kBBytes), "r"(su32(&full[s]))
+                       : "memory");
+        }
+      }
+      // copies still in flight when stopping early: wait for them (bounded)
+      if (!ok)
+        for (int u = max(0, t - kS); u < t; ++u) bar_wait(&full[u % kS], (u / kS) & 1);
     }
-    // A: element (m = tid, k = 4e + j) -> core (tid / 8, e), row tid % 8
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ------------------------------------------------------------- MMA issuer
+      int t = 0, i = 0;                 // i counts the non-empty items (accumulator alternation)
+      for (int it = blockIdx.x; it < items && ok; it += gridDim.x) {
+        int q, mt, sp, rb, ns;
+        item_of(it, q, mt, sp, rb, ns);
+        if (ns == 0) continue;
+        const int ab = i & 1;
+        if (i >= 2) ok = bar_wait(&accempty[ab], ((i / 2) - 1) & 1);
+        if (!ok) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const unsigned d = tmem + ab * kTcN;
+        for (int sl = 0; sl < ns && ok; ++sl, ++t) {
+          const int s = t % kS;
+          ok = bar_wait(&conv[s], (t / kS) & 1);
+          if (!ok) break;
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const unsigned st = su32(smem + s * kStageBytes);
+          const unsigned a_hi = st, a_lo = st + kABytes, b_hi = st + 2 * kABytes, b_lo = b_hi + kBBytes;
 #pragma unroll
-    for (int e = 0; e < kTcK / 4; ++e) {
-      const float4 x = ra[e];
-      const float4 h = make_float4(tf32_rn(x.x), tf32_rn(x.y), tf32_rn(x.z), tf32_rn(x.w));
-      const float4 l = make_float4(x.x - h.x, x.y - h.y, x.z - h.z, x.w - h.w);
-      const int off = (e * kA_LBO + tid * 16) / 4;
-      reinterpret_cast<float4*>(Ahi + off)[0] = h;
-      reinterpret_cast<float4*>(Alo + off)[0] = l;
-    }
-    // B: W real rows 2 wm (re), 2 wm + 1 (im) for scenes ws, ws + 1
-    {
-      const float v[4] = {rw.x, rw.y, rw.z, rw.w};       // (ws re, ws im, ws+1 re, ws+1 im)
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int s = ws + (u >> 1), k = 2 * wm + (u & 1);
-        const int off = ((k >> 2) * kB_LBO + (s >> 3) * kB_SBO + (s & 7) * 16 + (k & 3) * 4) / 4;
-        const float h = tf32_rn(v[u]);
-        Bhi[off] = h;
-        Blo[off] = v[u] - h;
+          for (int ks = 0; ks < kTcK / 8; ++ks) {
+            const unsigned acc0 = (sl > 0 || ks > 0) ? 1u : 0u;
+            const uint64_t dah = sw128_desc(a_hi + ks * 32), dal = sw128_desc(a_lo + ks * 32);
+            const uint64_t dbh = smem_desc(b_hi + ks * 2 * kB_LBO, kB_LBO, kB_SBO);
+            const uint64_t dbl = smem_desc(b_lo + ks * 2 * kB_LBO, kB_LBO, kB_SBO);
+            mma_tf32(d, dah, dbh, acc0);
+            mma_tf32(d, dah, dbl, 1u);
+            mma_tf32(d, dal, dbh, 1u);
+          }
+          mma_commit(&empty[s]);
+        }
+        if (ok) mma_commit(&accfull[ab]);
+        ++i;
       }
     }
-    if (slab + 2 < nslab) load(slab + 2, ra, rw);
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    if (tid == 0) {
+  } else {
+    // --------------------------------------------------------- converters
+    const int ct = tid - 64;                        // 0..127
+    const int quarter = warp & 3;                   // TMEM lanes 32 quarter .. +31
+    int t = 0, i = 0;                   // i counts the non-empty items
+    for (int it = blockIdx.x; it < items && ok; it += gridDim.x) {
+      int q, mt, sp, rb, ns;
+      item_of(it, q, mt, sp, rb, ns);
+      if (ns == 0) {
+        // an empty row split contributes zeros
+        const int p = mt * kTcM + quarter * 32 + lane;
+        if (p < N) {
+          float4* out = reinterpret_cast<float4*>(gpart + (((size_t)q * splits + sp) * N + p) * kTcN);
+#pragma unroll
+          for (int e = 0; e < 4; ++e) out[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        continue;
+      }
+      for (int sl = 0; sl < ns && ok; ++sl, ++t) {
+        const int s = t % kS;
+        ok = bar_wait(&full[s], (t / kS) & 1);
+        if (!ok) break;
+        unsigned char* st = smem + s * kStageBytes;
+        float4* ahi = reinterpret_cast<float4*>(st);
+        float4* alo = reinterpret_cast<float4*>(st + kABytes);
+#pragma unroll
+        for (int c = 0; c < kABytes / 16 / 128; ++c) {
+          const int e = ct + 128 * c;
+          const float4 x = ahi[e];
+          const float4 h = make_float4(tf32_rn(x.x), tf32_rn(x.y), tf32_rn(x.z), tf32_rn(x.w));
+          ahi[e] = h;
+          alo[e] = make_float4(x.x - h.x, x.y - h.y, x.z - h.z, x.w - h.w);
+        }
+        float* bhi = reinterpret_cast<float*>(st + 2 * kABytes);
+        float* blo = bhi + kBBytes / 4;
+        const float4 rw = reinterpret_cast<const float4*>(st + 2 * kABytes + 2 * kBBytes)[ct];
+        const int wm = ct >> 3, ws = 2 * (ct & 7);
+        const float v[4] = {rw.x, rw.y, rw.z, rw.w};       // (ws re, ws im, ws+1 re, ws+1 im)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int sc = ws + (u >> 1), k = 2 * wm + (u & 1);
+          const int off = ((k >> 2) * kB_LBO + (sc >> 3) * kB_SBO + (sc & 7) * 16 + (k & 3) * 4) / 4;
+          const float h = tf32_rn(v[u]);
+          bhi[off] = h;
+          blo[off] = v[u] - h;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive(&conv[s]);
+      }
+      if (!ok) break;
+      // epilogue of this item
+      const int ii = i++;
+      const int ab = ii & 1;
+      ok = bar_wait(&accfull[ab], (ii / 2) & 1);
+      ok = __all_sync(0xffffffffu, ok);          // tcgen05.ld below is warp-collective
+      if (!ok) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const unsigned a_hi = su32(Ahi), a_lo = su32(Alo), b_hi = su32(Bhi), b_lo = su32(Blo);
+      unsigned r[16];
+      const unsigned taddr = tmem + ((unsigned)(quarter * 32) << 16) + ab * kTcN;
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+          : "r"(taddr)
+          : "memory");
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      const int p = mt * kTcM + quarter * 32 + lane;
+      if (p < N) {
+        float4* out = reinterpret_cast<float4*>(gpart + (((size_t)q * splits + sp) * N + p) * kTcN);
 #pragma unroll
-      for (int ks = 0; ks < kTcK / 8; ++ks) {
-        const int ao = ks * 2 * kA_LBO, bo = ks * 2 * kB_LBO;
-        const unsigned acc0 = (slab > 0 || ks > 0) ? 1u : 0u;
-        mma_tf32(tmem, smem_desc(a_hi + ao, kA_LBO, kA_SBO), smem_desc(b_hi + bo, kB_LBO, kB_SBO), acc0);
-        mma_tf32(tmem, smem_desc(a_hi + ao, kA_LBO, kA_SBO), smem_desc(b_lo + bo, kB_LBO, kB_SBO), 1u);
-        mma_tf32(tmem, smem_desc(a_lo + ao, kA_LBO, kA_SBO), smem_desc(b_hi + bo, kB_LBO, kB_SBO), 1u);
+        for (int e = 0; e < 4; ++e)
+          out[e] = make_float4(__uint_as_float(r[4 * e]), __uint_as_float(r[4 * e + 1]),
+                               __uint_as_float(r[4 * e + 2]), __uint_as_float(r[4 * e + 3]));
       }
-      mma_commit(&bar[b]);
-    }
-    pending |= 1u << b;
-    return true;
-  };
-  if (nslab > 0) load(0, raA, rwA);
-  if (nslab > 1) load(1, raB, rwB);
-  for (int slab = 0; slab < nslab; slab += 2) {
-    if (!step(slab, raA, rwA)) break;
-    if (slab + 1 < nslab && !step(slab + 1, raB, rwB)) break;
-  }
-  // drain: wait for every outstanding commit (bounded)
-  for (int b = 0; b < 2; ++b) {
-    if ((pending >> b) & 1u) {
-      const bool w = bar_wait(&bar[b], (phase >> b) & 1u);
-      ok = ok && w;
-      phase ^= 1u << b;
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      mbar_arrive(&accempty[ab]);
     }
   }
-  ok = __syncthreads_and(ok);
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (ok && nslab > 0) {
-    unsigned r[16];
-    const unsigned taddr = tmem + ((unsigned)(warp * 32) << 16);
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr)
-        : "memory");
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-    if (pv) {
-      float4* out = reinterpret_cast<float4*>(gpart + (((size_t)q * splits + split) * N + p) * kTcN);
-#pragma unroll
-      for (int e = 0; e < 4; ++e)
-        out[e] = make_float4(__uint_as_float(r[4 * e]), __uint_as_float(r[4 * e + 1]), __uint_as_float(r[4 * e + 2]),
-                             __uint_as_float(r[4 * e + 3]));
-    }
-  } else if (!ok && tid == 0) {
-    atomicExch(err, 1);
-  }
+  if (!ok) atomicExch(err, 1);
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0)
@@ -245,21 +336,64 @@ tc_adjoint_kernel(const float2* const* __restrict__ Aq, const float2* const* __r
 
 }  // namespace
 
+namespace {
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// The tensor-map encoder comes from the driver through the runtime, so the
+// library needs no link-time dependency on libcuda.
+EncodeTiledFn tensor_map_encoder() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult qr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &qr) == cudaSuccess &&
+        qr == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+}  // namespace
+
 int tc_adjoint_splits(int Q, int N, int KM) {
-  const int ctas = div_up(N, kTcM) * Q;
-  const int want = div_up(152 * 3 * 4, ctas);          // about four waves of resident CTAs
+  const int tiles = div_up(N, kTcM) * Q;
+  const int want = div_up(152 * 4, tiles);                  // about four items per persistent CTA
   return std::max(1, std::min(want, (2 * KM) / (4 * kTcK)));
 }
 
 int launch_tc_adjoint(const float2* const* Aq, const float2* const* Wq, float* gpart, int Q, int N, int KM, int splits,
                       int* err, cudaStream_t st) {
-  if ((2 * KM) % kTcK != 0 || splits < 1) { set_error("launch_tc_adjoint: bad sizes"); return SADMM_EINVAL; }
+  if (Q < 1 || Q > kMaxSets || N < 1 || (2 * KM) % kTcK != 0 || splits < 1) {
+    set_error("launch_tc_adjoint: bad sizes");
+    return SADMM_EINVAL;
+  }
+  EncodeTiledFn enc = tensor_map_encoder();
+  if (!enc) { set_error("launch_tc_adjoint: cuTensorMapEncodeTiled unavailable"); return SADMM_ECUDA; }
+  TmapSet tm;
+  PtrSet ws;
+  memset(&tm, 0, sizeof tm);
+  memset(&ws, 0, sizeof ws);
+  for (int q = 0; q < Q; ++q) {
+    const cuuint64_t dims[2] = {(cuuint64_t)2 * KM, (cuuint64_t)N};
+    const cuuint64_t strides[1] = {(cuuint64_t)2 * KM * sizeof(float)};
+    const cuuint32_t box[2] = {(cuuint32_t)kTcK, (cuuint32_t)kTcM};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = enc(&tm.m[q], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float2*>(Aq[q]), dims, strides, box,
+                           estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) { set_error("launch_tc_adjoint: tensor map of sensor %d rejected (%d)", q, (int)r); return SADMM_ECUDA; }
+    ws.w[q] = reinterpret_cast<const float*>(Wq[q]);
+  }
   static bool conf = false;
   if (!conf) {
-    SADMM_CUDA_TRY(cudaFuncSetAttribute(tc_adjoint_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem));
+    SADMM_CUDA_TRY(cudaFuncSetAttribute(tc_adjoint_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kPipeSmem));
     conf = true;
   }
-  tc_adjoint_kernel<<<dim3(div_up(N, kTcM), Q, splits), kTcThreads, kTcSmem, st>>>(Aq, Wq, gpart, N, KM, splits, err);
+  const int items = Q * div_up(N, kTcM) * splits;
+  tc_adjoint_kernel<<<std::min(items, 152), kPipeThreads, kPipeSmem, st>>>(tm, ws, gpart, Q, N, KM, splits, err);
   SADMM_LAUNCH_CHECK();
   return SADMM_OK;
 }
@@ -273,24 +407,19 @@ extern "C" int sadmm_adjoint16_tc(const float* A, int KM, int N, const float* W,
     return SADMM_EINVAL;
   }
   cudaStream_t st = (cudaStream_t)stream;
-  void *ptrs = nullptr, *err = nullptr;
-  SADMM_CUDA_TRY(cudaMallocAsync(&ptrs, 2 * sizeof(void*), st));
+  void* err = nullptr;
   SADMM_CUDA_TRY(cudaMallocAsync(&err, sizeof(int), st));
-  const void* hp[2] = {A, W};
-  int rc = cudaMemcpyAsync(ptrs, hp, sizeof hp, cudaMemcpyHostToDevice, st) == cudaSuccess &&
-                   cudaMemsetAsync(err, 0, sizeof(int), st) == cudaSuccess
-               ? SADMM_OK
-               : SADMM_ECUDA;
-  if (rc == SADMM_OK)
-    rc = launch_tc_adjoint((const float2* const*)ptrs, (const float2* const*)ptrs + 1, G, 1, N, KM, 1, (int*)err, st);
+  int rc = cudaMemsetAsync(err, 0, sizeof(int), st) == cudaSuccess ? SADMM_OK : SADMM_ECUDA;
+  const float2* a = reinterpret_cast<const float2*>(A);
+  const float2* w = reinterpret_cast<const float2*>(W);
+  if (rc == SADMM_OK) rc = launch_tc_adjoint(&a, &w, G, 1, N, KM, 1, (int*)err, st);
   int herr = 0;
   if (rc == SADMM_OK) {
     SADMM_CUDA_TRY(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
     SADMM_CUDA_TRY(cudaStreamSynchronize(st));
   }
-  cudaFreeAsync(ptrs, st);
   cudaFreeAsync(err, st);
   if (rc != SADMM_OK) return rc;
-  if (herr) { set_error("sadmm_adjoint16_tc: a tensor-core wait timed out"); return SADMM_ETIMEOUT; }
+  if (herr) { set_error("sadmm_adjoint16_tc: a tensor-core pipeline wait timed out"); return SADMM_ETIMEOUT; }
   return SADMM_OK;
 }
