@@ -154,8 +154,8 @@ __global__ void bfwd_reduce_kernel(const float2* __restrict__ partial, const flo
 // single-scene apply): exact products, two-sum accumulation, about 48 bits.
 // A tile (I, J) is a pair of small GEMMs, OUT_I += F_IJ U_J and (off the
 // diagonal) OUT_J += F_IJ^T U_I, with 64 x 16 right-hand sides.  Persistent
-// CTAs pull tiles by bulk asynchronous copy (two stages, mbarrier, bounded
-// waits); 64 threads hold 4 rows x 4 scenes of F_IJ U_J and 64 threads 4
+// CTAs (five per SM, so that copies overlap other CTAs' arithmetic) pull tiles
+// by bulk asynchronous copy (mbarrier, bounded waits); 64 threads hold 4 rows x 4 scenes of F_IJ U_J and 64 threads 4
 // columns x 4 scenes of F_IJ^T U_I, stepping along skewed diagonals so that
 // shared-memory reads do not conflict.  Per-tile partials go to a scratch
 // buffer that bspd_reduce_kernel adds in a fixed order.
@@ -220,62 +220,44 @@ __global__ void __launch_bounds__(kBtThreads)
 bspd_tile_kernel(const float2* const* __restrict__ Pq, const float* const* __restrict__ uq, float2* __restrict__ part,
                  size_t part_stride, int n, int mode, int items, int* __restrict__ err) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  float2* buf = reinterpret_cast<float2*>(smem_raw);                         // 2 x 64 x 64 pairs
-  float* su = reinterpret_cast<float*>(smem_raw + 2 * kBtTileBytes);        // 2 stages x (u_I, u_J) x 64 x 16
-  __shared__ __align__(8) uint64_t bar[2];
+  float2* tile = reinterpret_cast<float2*>(smem_raw);                        // 64 x 64 pairs
+  float* su = reinterpret_cast<float*>(smem_raw + kBtTileBytes);            // (u_I, u_J) x 64 x 16
+  __shared__ __align__(8) uint64_t bar;
   const int tid = threadIdx.x;
   const int nt = ntiles_side(n);
   const int tiles = nt * (nt + 1) / 2;
-  int item = blockIdx.x;
-  if (item >= items) return;
+  if ((int)blockIdx.x >= items) return;
   if (tid == 0) {
-    mbar_init(&bar[0]);
-    mbar_init(&bar[1]);
+    mbar_init(&bar);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  {
-    const int q = item / tiles, t = item % tiles;
-    int I, J;
-    tile_ij(t, nt, I, J);
-    if (tid == 0) bulk_load(buf, Pq[q] + (size_t)t * kT * kT, kBtTileBytes, &bar[0]);
-    float v[16];
-    bt_load_u(uq[q], n, mode, I, J, tid, v);
-    bt_store_u(su, mode, tid, v);
-  }
-  unsigned phase = 0u, issued = 1u;
+  unsigned phase = 0u;
   const bool rowpart = tid < 64;
   const int grp = (tid & 63) >> 2;        // row group (rows 4 grp..) or column group
   const int g = tid & 3;                  // scenes 4g .. 4g + 3
-  for (int k = 0; item < items; ++k, item += gridDim.x) {
-    const int st = k & 1;
+  for (int item = blockIdx.x; item < items; item += gridDim.x) {
     const int q = item / tiles, t = item % tiles;
     int I, J;
     tile_ij(t, nt, I, J);
-    const int nitem = item + gridDim.x;
-    float vn[16];
-    if (nitem < items) {
-      const int qn = nitem / tiles, tn = nitem % tiles;
-      int In, Jn;
-      tile_ij(tn, nt, In, Jn);
-      if (tid == 0) {
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        bulk_load(buf + (size_t)(st ^ 1) * kT * kT, Pq[qn] + (size_t)tn * kT * kT, kBtTileBytes, &bar[st ^ 1]);
-      }
-      issued |= 2u >> st;
-      bt_load_u(uq[qn], n, mode, In, Jn, tid, vn);
+    // the previous tile and u slices are consumed (closing barrier)
+    if (tid == 0) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      bulk_load(tile, Pq[q] + (size_t)t * kT * kT, kBtTileBytes, &bar);
     }
-    __syncthreads();                                        // su[st] written
-    const bool ok = mbar_wait(&bar[st], (phase >> st) & 1u);
+    {
+      float v[16];
+      bt_load_u(uq[q], n, mode, I, J, tid, v);
+      bt_store_u(su, mode, tid, v);
+    }
+    __syncthreads();                                        // su written
+    const bool ok = mbar_wait(&bar, phase);
+    phase ^= 1u;
     if (!__syncthreads_and(ok)) {
       if (tid == 0) atomicExch(err, 1);
-      if ((issued >> (st ^ 1)) & 1u) mbar_wait(&bar[st ^ 1], (phase >> (st ^ 1)) & 1u);
       return;
     }
-    issued &= ~(1u << st);
-    phase ^= 1u << st;
-    const float2* tile = buf + (size_t)st * kT * kT;
-    const float* uI = su + (size_t)st * 2 * kT * kBS;
+    const float* uI = su;
     const float* uJ = uI + kT * kBS;
     DF acc[4][4];
 #pragma unroll
@@ -320,8 +302,7 @@ bspd_tile_kernel(const float2* const* __restrict__ Pq, const float* const* __res
       dst[0] = make_float4(o0.hi, o0.lo, o1.hi, o1.lo);
       dst[1] = make_float4(o2.hi, o2.lo, o3.hi, o3.lo);
     }
-    if (nitem < items) bt_store_u(su + (size_t)(st ^ 1) * 2 * kT * kBS, mode, tid, vn);
-    __syncthreads();                                        // stage st consumed; su[st ^ 1] ready
+    __syncthreads();                                        // tile and su consumed
   }
 }
 
@@ -556,13 +537,13 @@ namespace {
 
 int launch_bspd(BatchCtx& c, const float* const* u, float* const* out, int mode, const BatchDev& bv) {
   const int nt = div_up(c.n, kT), items = c.Q * nt * (nt + 1) / 2;
-  const int smem = 2 * kBtTileBytes + 2 * 2 * kT * kBS * (int)sizeof(float);
+  const int smem = kBtTileBytes + 2 * kT * kBS * (int)sizeof(float);
   static bool conf = false;
   if (!conf) {
     SADMM_CUDA_TRY(cudaFuncSetAttribute(bspd_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     conf = true;
   }
-  bspd_tile_kernel<<<std::min(items, 152 * 2), kBtThreads, smem, c.st>>>(
+  bspd_tile_kernel<<<std::min(items, 152 * 5), kBtThreads, smem, c.st>>>(
       (const float2* const*)c.dF, u, c.bpart, c.bpart_stride, c.n, mode, items, c.berr);
   SADMM_LAUNCH_CHECK();
   bspd_reduce_kernel<<<dim3(nt, c.Q), 256, 0, c.st>>>(c.bpart, c.bpart_stride, out, c.n, mode, bv);

@@ -13,9 +13,10 @@
 // (I <= J, row-block-major; each tile row-major and contiguous, zero-padded
 // past n), so one iteration streams n^2/2 pairs instead of n^2.  A tile (I, J)
 // contributes F_IJ u_J to block row I and, off the diagonal, F_IJ^T u_I to
-// block row J.  Persistent CTAs pull tiles with one bulk asynchronous copy
-// each (cp.async.bulk into shared memory, completion on an mbarrier, two
-// stages), then 64 threads form the row sums and 64 the column sums of the
+// block row J.  Persistent CTAs (six per SM, so that one CTA's copy overlaps
+// the others' arithmetic) pull tiles with one bulk asynchronous copy each
+// (cp.async.bulk into shared memory, completion on an mbarrier), then 64
+// threads form the row sums and 64 the column sums of the
 // tile, reading it along diagonals so that shared-memory accesses do not
 // conflict.  Per-tile partial sums (pairs) go to a scratch buffer; a second
 // kernel adds them in a fixed order and applies the epilogue.
@@ -40,75 +41,46 @@ __device__ __forceinline__ int item_set(const SetBlock<SpdSet>& sets, int nsets,
 __global__ void __launch_bounds__(kSpdThreads)
 spd_tile_kernel(const __grid_constant__ SetBlock<SpdSet> sets, int nsets, int items, int* __restrict__ err) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  float2* buf = reinterpret_cast<float2*>(smem_raw);            // 2 stages x 64 x 64 pairs
-  __shared__ __align__(8) uint64_t bar[2];
-  __shared__ float s_u[2][2][kT];                                // stage, (u_I, u_J), 64
+  float2* tile = reinterpret_cast<float2*>(smem_raw);           // 64 x 64 pairs
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ float s_u[2][kT];                                  // u_I, u_J
   const int tid = threadIdx.x;
   const int lt = tid;                                            // < 64: row lt, else column lt - 64
-  int item = blockIdx.x;
-  if (item >= items) return;
+  if ((int)blockIdx.x >= items) return;
   if (tid == 0) {
-    mbar_init(&bar[0]);
-    mbar_init(&bar[1]);
+    mbar_init(&bar);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-
-  // stage the first tile
-  int t0, s0 = item_set(sets, nsets, item, t0);
-  int I0, J0;
-  tile_ij(t0, ntiles_side(sets.v[s0].n), I0, J0);
-  if (tid == 0) bulk_load(buf, sets.v[s0].P + (size_t)t0 * kT * kT, kTileBytes, &bar[0]);
-  {
-    const SpdSet& ss = sets.v[s0];
-    const int blk = lt < kT ? I0 : J0;
-    const int i = blk * kT + (lt & (kT - 1));
-    s_u[0][lt >> 6][lt & (kT - 1)] = i < ss.n ? ss.u[i] : 0.f;
-  }
-  unsigned phase = 0u;                               // bit s: parity to wait for on stage s
-  unsigned issued = 1u;                              // bit s: a copy into stage s is outstanding
-  for (int k = 0; item < items; ++k, item += gridDim.x) {
-    const int st = k & 1;
+  unsigned phase = 0u;
+  const int r = lt & (kT - 1);
+  for (int item = blockIdx.x; item < items; item += gridDim.x) {
     int t, s = item_set(sets, nsets, item, t);
     const SpdSet& ss = sets.v[s];
     const int nt = ntiles_side(ss.n);
     int I, J;
     tile_ij(t, nt, I, J);
-    // issue the next tile into the other stage (freed by the barrier that
-    // closed the previous iteration) and fetch its u slices into registers
-    const int nitem = item + gridDim.x;
-    float u_next = 0.f;
-    if (nitem < items) {
-      int tn, sn = item_set(sets, nsets, nitem, tn);
-      const SpdSet& sn_ = sets.v[sn];
-      int In, Jn;
-      tile_ij(tn, ntiles_side(sn_.n), In, Jn);
-      if (tid == 0) {
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        bulk_load(buf + (size_t)(st ^ 1) * kT * kT, sn_.P + (size_t)tn * kT * kT, kTileBytes, &bar[st ^ 1]);
-      }
-      issued |= 2u >> st;
-      const int blk = lt < kT ? In : Jn;
-      const int i = blk * kT + (lt & (kT - 1));
-      u_next = i < sn_.n ? sn_.u[i] : 0.f;
+    // the previous tile is consumed (closing barrier): reuse the buffer
+    if (tid == 0) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      bulk_load(tile, ss.P + (size_t)t * kT * kT, kTileBytes, &bar);
     }
-    __syncthreads();                                   // s_u[st] written
-    const bool ok = mbar_wait(&bar[st], (phase >> st) & 1u);
+    {
+      const int blk = lt < kT ? I : J;
+      const int i = blk * kT + r;
+      s_u[lt >> 6][r] = i < ss.n ? ss.u[i] : 0.f;
+    }
+    __syncthreads();                                   // s_u written
+    const bool ok = mbar_wait(&bar, phase);
+    phase ^= 1u;
     if (!__syncthreads_and(ok)) {
-      // give up on this launch: flag it, wait (bounded) for the other copy in
-      // flight so that no transfer targets the CTA's memory after it exits
-      if (tid == 0) atomicExch(err, 1);
-      if ((issued >> (st ^ 1)) & 1u) mbar_wait(&bar[st ^ 1], (phase >> (st ^ 1)) & 1u);
+      if (tid == 0) atomicExch(err, 1);              // the one copy in flight is the one that timed out
       return;
     }
-    issued &= ~(1u << st);
-    phase ^= 1u << st;
-    const float2* tile = buf + (size_t)st * kT * kT;
     DF acc0{0.f, 0.f}, acc1{0.f, 0.f};
-    const int r = lt & (kT - 1);
     if (lt < kT) {
       // row r of F_IJ times u_J, read along the diagonal (r, (r + c) mod 64)
-      const float* uJ = s_u[st][1];
+      const float* uJ = s_u[1];
 #pragma unroll 8
       for (int c = 0; c < kT; c += 2) {
         const int c0 = (r + c) & (kT - 1), c1 = (r + c + 1) & (kT - 1);
@@ -118,7 +90,7 @@ spd_tile_kernel(const __grid_constant__ SetBlock<SpdSet> sets, int nsets, int it
       }
     } else if (I != J) {
       // column r of F_IJ times u_I (the transposed contribution to block row J)
-      const float* uI = s_u[st][0];
+      const float* uI = s_u[0];
 #pragma unroll 8
       for (int c = 0; c < kT; c += 2) {
         const int r0 = (r + c) & (kT - 1), r1 = (r + c + 1) & (kT - 1);
@@ -130,8 +102,7 @@ spd_tile_kernel(const __grid_constant__ SetBlock<SpdSet> sets, int nsets, int it
     df_add(acc0, acc1);
     const DF o = df_norm(acc0);
     ss.part[(size_t)t * 2 * kT + lt] = make_float2(o.hi, o.lo);
-    s_u[st ^ 1][lt >> 6][r] = u_next;
-    __syncthreads();                                   // stage st consumed; s_u[st ^ 1] ready
+    __syncthreads();                                   // tile and s_u consumed
   }
 }
 
@@ -224,13 +195,13 @@ int launch_spd_apply(const SpdSet* sets, int nsets, bool update, const SolverVie
     nt_max = max(nt_max, nt);
   }
   if (items == 0) return SADMM_OK;
-  const int smem = 2 * kTileBytes;
+  const int smem = kTileBytes;
   static bool configured = false;
   if (!configured) {
     SADMM_CUDA_TRY(cudaFuncSetAttribute(spd_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     configured = true;
   }
-  const int grid = min(items, 152 * 3);
+  const int grid = min(items, 152 * 6);           // six 32 KB tiles in flight per SM
   spd_tile_kernel<<<grid, kSpdThreads, smem, st>>>(blk, nsets, items, err);
   SADMM_LAUNCH_CHECK();
   spd_reduce_kernel<<<dim3(nt_max, nsets), kT, 0, st>>>(blk, update, sv);
