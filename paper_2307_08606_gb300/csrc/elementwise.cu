@@ -1,4 +1,4 @@
-// Fused prox + dual + residual reductions (Eq. 3, lines 2-3, and the primal /
+// Fused prox + dual + residual reductions (Eq. 3, x_G- and dual updates, and the primal /
 // dual residuals that gate Algorithm 1) and the SSC stream compaction
 // (Algorithm 1) of the sharing-ADMM iteration.
 #include "common.cuh"
