@@ -208,11 +208,26 @@ def batched_measure(args, dev, stream, rank):
     launches = binding.launch_count() - n0
     bs.close()
     scene_its = 16 * iters * reps / (ms / 1e3)
+    # the same geometry solved one scene at a time (plain FP32 single-scene form)
+    one = binding.Solver(g.Q, g.M, g.K, g.N, 1.0, lams[0], stream=stream.cuda_stream, elim=0)
+    for q in range(g.Q):
+        one.set_operator(q, At[q])
+    one.prepare()
+    y0 = [torch.from_numpy(v).to(dev) for v in ys[0]]
+    one.solve(y0, iters)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    one.solve(y0, iters)
+    torch.cuda.synchronize()
+    single_its = iters / (time.perf_counter() - t0)
+    one.close()
     op_bytes = 2.0 * g.Q * g.KM * g.N * 8.0            # forward + adjoint, read once for 16 scenes
     return {"metric": "batched scene-iterations/s", "value": scene_its, "unit": "scene-iter/s",
             "workload": "16 scenes sharing Q=8 M=8 K=256 (KM=2048) N=96x96; plain SADMM, 100 iterations per solve",
             "ms_per_iteration": ms / (iters * reps), "operator_bytes_per_iteration": op_bytes,
             "operator_GBps_effective": op_bytes / (ms / (iters * reps) / 1e3) / 1e9,
+            "single_scene_iters_per_s_same_geometry": single_its,
+            "speedup_vs_single_scene": scene_its / single_its,
             "gpu_launches": int(launches)}
 
 
