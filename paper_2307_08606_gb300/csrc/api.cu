@@ -86,6 +86,7 @@ struct Ctx {
   float2* partial = nullptr;
   size_t partial_cap = 0;
   float2* spd_part = nullptr;  // per-sensor partial sums of the symmetric factor apply
+  float2* dd_part = nullptr;   // partial sums of the factor updates' applies (64 columns)
   size_t spd_part_stride = 0;
   int* spd_err = nullptr;      // set by the factor apply if a tile copy timed out
   double* red = nullptr;
@@ -260,38 +261,51 @@ int refresh(Ctx& c, const std::vector<int>& qs, bool full_set) {
   return SADMM_OK;
 }
 
-// Rank-|E| downdate of Woodbury-form factors (see run_downdate), in passes of
-// at most kDowndateMax removed columns; with `add` the rank-|R| update for the
-// re-admitted columns instead.  Sensors whose downdate fails (the small system
-// is not numerically positive definite) are returned in `failed`.
+// Rank-|E| downdate of Woodbury-form factors, in passes of at most
+// kDowndateMax removed columns; with `add` the rank-|R| update for the
+// re-admitted columns instead.  The update is applied to the packed (hi, lo)
+// pair copy the iteration reads (run_downdate_pairs: W U by the double-float
+// symmetric apply, the small system in FP64, the rank correction in
+// double-float), so the FP64 factor is only rebuilt on a full refresh.
+// Sensors whose update fails (the small system is not numerically positive
+// definite) are returned in `failed`.
 int downdate(Ctx& c, const std::vector<int>& qs, std::vector<int>* failed, bool add = false) {
   if (qs.empty()) return SADMM_OK;
   std::vector<int> dst(c.Q), etot(c.Q);
+  std::vector<std::vector<int>> Eh(c.Q);
   int max_e = 0;
   for (int q : qs) {
     Sensor& S = c.s[q];
     dst[q] = (S.cur == S.full) ? (S.full + 1) % 3 : S.cur;
     etot[q] = c.h_counts[(add ? 3 : 1) * c.Q + q];
     max_e = std::max(max_e, etot[q]);
+    Eh[q].resize(etot[q]);
+    if (etot[q] > 0)
+      SADMM_CUDA_TRY(cudaMemcpyAsync(Eh[q].data(), add ? S.R : S.E, etot[q] * sizeof(int), cudaMemcpyDeviceToHost,
+                                     c.st));
   }
   SADMM_CUDA_TRY(cudaMemsetAsync(c.dstatus, 0, sizeof(int) * c.Q, c.st));
+  SADMM_CUDA_TRY(cudaStreamSynchronize(c.st));
   const int n = 2 * c.KM;
   const size_t nblk = div_up(n, 256);
   for (int off = 0; off < max_e; off += kDowndateMax) {
     std::vector<DowndateJob> jobs;
+    std::vector<const int*> eh;
     for (int q : qs) {
       Sensor& S = c.s[q];
       if (etot[q] <= off) continue;
-      DowndateJob j;
+      DowndateJob j{};
       j.A = S.A; j.E = (add ? S.R : S.E) + off; j.e = std::min(kDowndateMax, etot[q] - off); j.n = n;
-      j.Wsrc = (off == 0) ? S.fb[S.cur] : S.fb[dst[q]];
-      j.Wdst = S.fb[dst[q]];
+      j.Fsrc = (off == 0) ? S.fhl[S.cur] : S.fhl[dst[q]];
+      j.Fdst = S.fhl[dst[q]];
       j.P = S.dinv; j.Spart = S.dd; j.S = S.dd + nblk * kDowndateMax * kDowndateMax;
       j.slot = q;
       j.sign = add ? -1 : 1;
       jobs.push_back(j);
+      eh.push_back(Eh[q].data() + off);
     }
-    SADMM_TRY(run_downdate(jobs.data(), (int)jobs.size(), c.KM, c.crit.mu, c.dstatus, c.st));
+    SADMM_TRY(run_downdate_pairs(jobs.data(), eh.data(), (int)jobs.size(), c.KM, c.crit.mu, c.dd_part, c.dstatus,
+                                 c.spd_err, c.st));
   }
   SADMM_CUDA_TRY(cudaMemcpyAsync(c.h_status, c.dstatus, sizeof(int) * c.Q, cudaMemcpyDeviceToHost, c.st));
   SADMM_CUDA_TRY(cudaStreamSynchronize(c.st));
@@ -300,7 +314,6 @@ int downdate(Ctx& c, const std::vector<int>& qs, std::vector<int>* failed, bool 
     if (c.h_status[q]) { failed->push_back(q); continue; }
     S.cur = dst[q];
     S.cum_dd += etot[q];
-    SADMM_TRY(launch_pack_sym(S.fb[S.cur], n, n, S.fhl[S.cur], c.st));
   }
   return SADMM_OK;
 }
@@ -870,6 +883,8 @@ int sadmm_create(int Q, int M, int K, int N, double rho, double lambda, const sa
   ctx->spd_part_stride = sym_part_pairs(ctx->npad_max);
   ctx->spd_part = (float2*)A((size_t)Q * ctx->spd_part_stride * sizeof(float2));
   ctx->spd_err = (int*)A(sizeof(int));
+  if (c.elim > 0 && ctx->npad_max == 2 * KM)     // Woodbury-form factors get rank updates
+    ctx->dd_part = (float2*)A((size_t)kMaxSets * ctx->spd_part_stride * sizeof(float2));
   ctx->red = (double*)A((size_t)residual_blocks(N) * 8 * sizeof(double));
   ctx->ticket = (unsigned int*)A(sizeof(unsigned int));
   ctx->scal = (IterScalars*)A(sizeof(IterScalars));

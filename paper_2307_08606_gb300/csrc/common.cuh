@@ -131,6 +131,8 @@ struct SpdSet {
   int q;
   float2* part;      // sym_part_pairs(n) scratch
   int tile0;         // set by launch_spd_apply
+  double* outd;      // optional: out written as hi + lo in FP64, element i at outd[i * ldd]
+  int ldd;
 };
 // out = F u for every set (or, with update, the primal x-update epilogue).
 // *err is set to 1 if a tile copy did not complete within the wait limit.
@@ -227,8 +229,18 @@ struct DowndateJob {
   double* S;             // kDowndateMax^2: the inverse Cholesky factor of S
   int slot;              // index of this job's failure flag in the status array
   int sign;              // +1 remove the columns, -1 add them
+  // double-float path (run_downdate_pairs): the packed pair copies of W
+  const float2* Fsrc;
+  float2* Fdst;          // may alias Fsrc
 };
 int run_downdate(const DowndateJob* jobs, int njobs, int KM, double mu, int* d_status, cudaStream_t st);
+// The same rank update applied to the packed (hi, lo) pair copy of W only
+// (Fsrc -> Fdst), with W U formed by the double-float symmetric apply and the
+// rank-e correction accumulated in double-float arithmetic; the FP64 Wsrc/Wdst
+// are not used.  E_host: the removed pixels of every job (host copies).
+// part: scratch of 64 x sym_part_pairs(n) float2.
+int run_downdate_pairs(const DowndateJob* jobs, const int* const* E_host, int njobs, int KM, double mu,
+                       float2* part, int* d_status, int* err, cudaStream_t st);
 size_t downdate_scratch_doubles(int n);
 
 }  // namespace sadmm

@@ -11,6 +11,9 @@
 #include "common.cuh"
 #include <math.h>
 
+#include <algorithm>
+#include <vector>
+
 namespace sadmm {
 
 namespace {
@@ -511,6 +514,82 @@ dd_w_kernel(const __grid_constant__ DdBlock jobs, double mu) {
     }
 }
 
+// Fdst = Fsrc + sign mu T T^T on the packed upper-triangular 64x64 tiles of
+// (hi, lo) pairs.  T (n x 32 FP64, columns >= e zero) is split into pairs in
+// shared memory; each element accumulates its e products T_ik T_jk in
+// double-float arithmetic (hi*hi exactly by FMA, plus the two cross terms),
+// is scaled by sign mu (a pair) and added to the stored pair with a two-sum.
+__device__ __forceinline__ void dfp_add(float& sh, float& sl, float p, float e) {
+  const float t = sh + p;
+  const float bp = t - sh;
+  sl += ((sh - (t - bp)) + (p - bp)) + e;
+  sh = t;
+}
+
+__global__ void __launch_bounds__(kThreads)
+ddw_pairs_kernel(const __grid_constant__ DdBlock jobs, double mu) {
+  const DowndateJob& jb = jobs.v[blockIdx.y];
+  const int nt = jb.n / T;
+  const int ntile = nt * (nt + 1) / 2;
+  if ((int)blockIdx.x >= ntile) return;
+  // tile number -> (I, J), I <= J, row-block-major (the packed order)
+  int I = 0, t = blockIdx.x;
+  while (t >= nt - I) { t -= nt - I; ++I; }
+  const int J = I + t;
+  __shared__ float Ih[DM][T], Il[DM][T], Jh[DM][T], Jl[DM][T];
+  const int tid = threadIdx.x, ty = tid / 16, tx = tid % 16;
+  for (int q = tid; q < DM * T; q += kThreads) {
+    const int r = q / DM, c = q % DM;
+    const double a = jb.P[(size_t)(I * T + r) * DM + c], b = jb.P[(size_t)(J * T + r) * DM + c];
+    const float ah = (float)a, bh = (float)b;
+    Ih[c][r] = ah; Il[c][r] = (float)(a - (double)ah);
+    Jh[c][r] = bh; Jl[c][r] = (float)(b - (double)bh);
+  }
+  __syncthreads();
+  float sh[4][4], sl[4][4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) { sh[u][v] = 0.f; sl[u][v] = 0.f; }
+  for (int c = 0; c < jb.e; ++c) {
+    float xh[4], xl[4], yh[4], yl[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      xh[u] = Ih[c][ty + 16 * u]; xl[u] = Il[c][ty + 16 * u];
+      yh[u] = Jh[c][tx + 16 * u]; yl[u] = Jl[c][tx + 16 * u];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        const float p = xh[u] * yh[v];
+        float e = fmaf(xh[u], yh[v], -p);
+        e = fmaf(xh[u], yl[v], fmaf(xl[u], yh[v], e));
+        dfp_add(sh[u][v], sl[u][v], p, e);
+      }
+  }
+  const double smu = jb.sign * mu;
+  const float mh = (float)smu, ml = (float)(smu - (double)mh);
+  const size_t tile = (size_t)I * nt - (size_t)I * (I - 1) / 2 + (J - I);
+  const float2* src = jb.Fsrc + tile * T * T;
+  float2* dst = jb.Fdst + tile * T * T;
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int e = (ty + 16 * u) * T + tx + 16 * v;
+      // (mh + ml) (sh + sl), then added to the stored pair
+      const float p = mh * sh[u][v];
+      float err = fmaf(mh, sh[u][v], -p);
+      err = fmaf(mh, sl[u][v], fmaf(ml, sh[u][v], err));
+      const float2 w = src[e];
+      float h = w.x, l = w.y;
+      dfp_add(h, l, p, err);
+      const float hn = h + l;
+      dst[e] = make_float2(hn, l - (hn - h));
+    }
+}
+
 template <int EB>
 int launch_dd_p(const DdBlock& blk, int njobs, int n_max, int KM, cudaStream_t st) {
   const size_t smem = (size_t)kDdChunk * EB * sizeof(double);
@@ -557,6 +636,53 @@ int run_downdate(const DowndateJob* jobs, int njobs, int KM, double mu, int* d_s
   SADMM_LAUNCH_CHECK();
   const int Tn = n_max / T;
   dd_w_kernel<<<dim3(Tn * (Tn + 1) / 2, njobs), kThreads, 0, st>>>(blk, mu);
+  SADMM_LAUNCH_CHECK();
+  return SADMM_OK;
+}
+
+int run_downdate_pairs(const DowndateJob* jobs, const int* const* E_host, int njobs, int KM, double mu,
+                       float2* part, int* d_status, int* err, cudaStream_t st) {
+  if (njobs <= 0) return SADMM_OK;
+  if (njobs > kMaxSets) { set_error("run_downdate_pairs: too many jobs"); return SADMM_EINVAL; }
+  DdBlock blk;
+  int n_max = 0;
+  for (int i = 0; i < njobs; ++i) {
+    blk.v[i] = jobs[i];
+    if (jobs[i].e < 1 || jobs[i].e > DM || jobs[i].n % T != 0 || !jobs[i].Fsrc || !jobs[i].Fdst) {
+      set_error("run_downdate_pairs: bad job (e=%d n=%d)", jobs[i].e, jobs[i].n);
+      return SADMM_EINVAL;
+    }
+    n_max = max(n_max, jobs[i].n);
+    // columns e..31 of P must be zero for the kernels below
+    SADMM_CUDA_TRY(cudaMemsetAsync(jobs[i].P, 0, (size_t)jobs[i].n * DM * sizeof(double), st));
+  }
+  // P = W U, one symmetric apply per removed column (u = that pixel's column of B)
+  std::vector<SpdSet> sets;
+  const size_t stride = sym_part_pairs(n_max);
+  for (int i = 0; i < njobs; ++i)
+    for (int c = 0; c < jobs[i].e; ++c) {
+      SpdSet s{};
+      s.P = jobs[i].Fsrc;
+      s.n = jobs[i].n;
+      s.u = reinterpret_cast<const float*>(jobs[i].A) + (size_t)E_host[i][c] * 2 * KM;
+      s.outd = jobs[i].P + c;
+      s.ldd = DM;
+      sets.push_back(s);
+    }
+  SolverView sv{};
+  for (size_t b = 0; b < sets.size(); b += kMaxSets) {
+    const int ns = (int)std::min<size_t>(kMaxSets, sets.size() - b);
+    for (int k = 0; k < ns; ++k) sets[b + k].part = part + (size_t)k * stride;
+    SADMM_TRY(launch_spd_apply(sets.data() + b, ns, false, sv, err, st));
+  }
+  dd_s_kernel<<<dim3(div_up(n_max, 256), njobs), DM * DM, 0, st>>>(blk, KM);
+  SADMM_LAUNCH_CHECK();
+  dd_chol_kernel<<<njobs, DM * DM, 0, st>>>(blk, mu, d_status);
+  SADMM_LAUNCH_CHECK();
+  dd_t_kernel<<<dim3(div_up(n_max, 128), njobs), 128, 0, st>>>(blk);
+  SADMM_LAUNCH_CHECK();
+  const int Tn = n_max / T;
+  ddw_pairs_kernel<<<dim3(Tn * (Tn + 1) / 2, njobs), kThreads, 0, st>>>(blk, mu);
   SADMM_LAUNCH_CHECK();
   return SADMM_OK;
 }
