@@ -27,26 +27,6 @@ namespace {
 
 constexpr int kBS = 16;              // scenes per batch (fixed tile width)
 
-// Asynchronous 16-byte global -> shared copies (zero fill when !valid), so a
-// whole operator slab is in flight at once and the next slab loads while the
-// current one is used.
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool valid) {
-  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-  const int sz = valid ? 16 : 0;
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(sa), "l"(gmem), "r"(sz) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
-
-// ------------------------------------------------------------------ forward
-// Output tile: 128 complex rows x 16 scenes; thread tile 4 rows x 4 scenes
-// (16 complex accumulators).  K loop over pixel slabs of 16 staged in shared
-// memory (operator slab 128 x 16 complex, V slab 16 x 16).
-constexpr int kBfRows = 128;
-constexpr int kBfSlab = 32;
-constexpr int kBfThreads = 128;
-
 struct BatchDev {
   int Q, N, KM, S;
   float mu, rho;
@@ -58,80 +38,10 @@ struct BatchDev {
   float* sd;                     // N x S
 };
 
-__global__ void __launch_bounds__(kBfThreads)
-bfwd_partial_kernel(const float2* const* __restrict__ Aq, BatchDev b, int chunks, int cols_per_chunk,
-                    float2* __restrict__ partial) {
-  const int q = blockIdx.z, c = blockIdx.y;
-  const int r0 = blockIdx.x * kBfRows;
-  const int KM = b.KM, N = b.N;
-  const int p0 = c * cols_per_chunk, p1 = min(N, p0 + cols_per_chunk);
-  extern __shared__ float4 smem4[];
-  float2 (*sA)[kBfSlab][kBfRows] = reinterpret_cast<float2 (*)[kBfSlab][kBfRows]>(smem4);   // [2][slab][rows]
-  __shared__ float sV[kBfSlab][kBS];
-  const int tid = threadIdx.x;
-  const int tr = tid / 4, ts = tid % 4;            // 32 row groups x 4 scene groups
-  float2 acc[4][4];
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int s = 0; s < 4; ++s) acc[i][s] = make_float2(0.f, 0.f);
-  const float2* A = Aq[q];
-  const float* X = b.X + (size_t)q * N * kBS;
-  auto stage = [&](int buf, int j0) {
-    // kBfSlab pixels x kBfRows rows of complex = kBfSlab * kBfRows / 2 chunks of 16 bytes
-    for (int e = tid; e < kBfSlab * kBfRows / 2; e += kBfThreads) {
-      const int jj = e / (kBfRows / 2), r2 = e % (kBfRows / 2);
-      const int j = j0 + jj, r = r0 + 2 * r2;
-      const bool ok = j < p1 && r < KM;
-      cp_async16(&sA[buf][jj][2 * r2], ok ? (const void*)(A + (size_t)j * KM + r) : (const void*)A, ok);
-    }
-    cp_async_commit();
-  };
-  if (p0 < p1) stage(0, p0);
-  int buf = 0;
-  for (int j0 = p0; j0 < p1; j0 += kBfSlab, buf ^= 1) {
-    const bool more = j0 + kBfSlab < p1;
-    if (more) stage(buf ^ 1, j0 + kBfSlab);
-    for (int e = tid; e < kBfSlab * kBS; e += kBfThreads) {
-      const int jj = e / kBS, s = e % kBS, j = j0 + jj;
-      float v = 0.f;
-      if (j < p1) {
-        const size_t o = (size_t)j * kBS + s;
-        v = X[o] - b.xbar[o] + b.zbar[o] - b.sd[o];
-      }
-      sV[jj][s] = v;
-    }
-    if (more) cp_async_wait<1>(); else cp_async_wait<0>();
-    __syncthreads();
-#pragma unroll 8
-    for (int jj = 0; jj < kBfSlab; ++jj) {
-      float2 a[4];
-      float v[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = sA[buf][jj][tr + 32 * i];
-#pragma unroll
-      for (int s = 0; s < 4; ++s) v[s] = sV[jj][ts + 4 * s];
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int s = 0; s < 4; ++s) {
-          acc[i][s].x = fmaf(a[i].x, v[s], acc[i][s].x);
-          acc[i][s].y = fmaf(a[i].y, v[s], acc[i][s].y);
-        }
-    }
-    __syncthreads();
-  }
-  float2* out = partial + ((size_t)q * chunks + c) * KM * kBS;
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int r = r0 + tr + 32 * i;
-    if (r >= KM) continue;
-#pragma unroll
-    for (int s = 0; s < 4; ++s) out[(size_t)r * kBS + ts + 4 * s] = acc[i][s];
-  }
-}
-
-// R_q[r][s] = Y'_q[r][s] - sum_c partial[q][c][r][s]
+// ------------------------------------------------------------------ forward
+// The products B_q V_q for the 16 scenes run on the tensor cores (tc.cu,
+// 3xTF32 tcgen05 GEMM into partial[q][split][row][scene]); the splits are added
+// here in order and subtracted from y'.
 __global__ void bfwd_reduce_kernel(const float2* __restrict__ partial, const float2* const* __restrict__ Yq,
                                    float2* const* __restrict__ Rq, int KM, int chunks) {
   const int q = blockIdx.y;
@@ -482,11 +392,6 @@ __global__ void bget_x_kernel(const float* __restrict__ X, int N, int scene, flo
   if (j < N) out[j] = X[(size_t)j * kBS + scene];
 }
 
-int batch_chunks(int Q, int KM, int N) {
-  const int tiles = div_up(KM, kBfRows);
-  const int want = div_up(152 * 8, (long long)tiles * Q);
-  return std::max(1, std::min(want, div_up(N, 256)));
-}
 
 }  // namespace
 
@@ -553,16 +458,8 @@ int launch_bspd(BatchCtx& c, const float* const* u, float* const* out, int mode,
 
 int batch_launch_iteration(BatchCtx& c) {
   const BatchDev bv = c.view();
-  dim3 gf(div_up(c.KM, kBfRows), c.chunks, c.Q);
-  const int per = div_up(c.N, c.chunks);
-  const size_t fsmem = 2 * sizeof(float2) * kBfSlab * kBfRows;
-  static bool fconf = false;
-  if (!fconf) {
-    SADMM_CUDA_TRY(cudaFuncSetAttribute(bfwd_partial_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem));
-    fconf = true;
-  }
-  bfwd_partial_kernel<<<gf, kBfThreads, fsmem, c.st>>>(c.dA, bv, c.chunks, per, c.partial);
-  SADMM_LAUNCH_CHECK();
+  SADMM_TRY(launch_tc_forward(c.hA.data(), bv.X, bv.xbar, bv.zbar, bv.sd, c.partial, c.Q, c.N, c.KM, c.chunks, c.berr,
+                              c.st));
   bfwd_reduce_kernel<<<dim3(div_up((long long)c.KM * kBS, 256), c.Q), 256, 0, c.st>>>(c.partial, c.dY, c.dR, c.KM,
                                                                                      c.chunks);
   SADMM_LAUNCH_CHECK();
@@ -622,7 +519,7 @@ int sadmm_batch_create(int Q, int M, int K, int N, int S, double rho, const doub
   b->dA = (float2**)A(Q * sizeof(void*)); b->dY = (float2**)A(Q * sizeof(void*));
   b->dR = (float2**)A(Q * sizeof(void*)); b->dF = (float2**)A(Q * sizeof(void*));
   b->dU = (float**)A(Q * sizeof(void*)); b->dG = (float**)A(Q * sizeof(void*));
-  b->chunks = batch_chunks(Q, b->KM, N);
+  b->chunks = tc_forward_splits(Q, N, b->KM);
   b->asplits = tc_adjoint_splits(Q, N, b->KM);
   b->gpart = (float*)A((size_t)Q * b->asplits * NS * sizeof(float));
   b->partial = (float2*)A((size_t)Q * b->chunks * KS * sizeof(float2));

@@ -111,6 +111,12 @@ int launch_adjoint(const AdjointSet* sets, int nsets, int KM, bool update, const
 // sum over the split's real rows of B_q[r][p] W_q[r][s] (16 scenes).  Aq and
 // Wq are HOST arrays of Q device pointers (the tensor maps are built on the host).
 int tc_adjoint_splits(int Q, int N, int KM);
+// Batched forward on the tensor cores (tc.cu): partial[q][split][m][s] (float2:
+// real rows 2m, 2m+1) = sum over the split's pixels p of B_q[r][p] V[p][s],
+// V = x - x_bar + z_bar - s of scene s (16 scenes); Aq: HOST array of Q device pointers.
+int tc_forward_splits(int Q, int N, int KM);
+int launch_tc_forward(const float2* const* Aq, const float* X, const float* xbar, const float* zbar, const float* sd,
+                      float2* partial, int Q, int N, int KM, int splits, int* err, cudaStream_t st);
 int launch_tc_adjoint(const float2* const* Aq, const float2* const* Wq, float* gpart, int Q, int N, int KM, int splits,
                       int* err, cudaStream_t st);
 

@@ -7,10 +7,10 @@
 //
 // Precision: three TF32 products per term (3xTF32).  Each operand is split
 // x = hi + lo with hi = tf32(x) (round to nearest) and lo = x - hi (exact in
-// FP32; the MMA keeps its top 11 bits), and hi*hi + hi*lo + lo*hi is
-// accumulated in FP32 in tensor memory: each product is within 2^-21 of the
-// FP32 one, the dropped lo*lo term is below 2^-22, and the sum over K rounds
-// as an FP32 accumulation does.
+// FP32; the MMA keeps its top 11 bits); hi*hi, hi*lo and lo*hi accumulate in
+// FP32 in three tensor-memory accumulators, added as hi*hi + (hi*lo + lo*hi)
+// at the end: each product is within 2^-21 of the FP32 one, the dropped lo*lo
+// term is below 2^-22, and the sums over K round as FP32 accumulations do.
 //
 // Tile: M = 128 pixels (TMEM lanes), N = 16 scenes (TMEM columns), K slabs of
 // 32 real rows.  A slab of A arrives by TMA (tensor map over the pixel-major
@@ -35,7 +35,8 @@ namespace {
 constexpr int kTcM = 128;              // pixels per CTA
 constexpr int kTcN = 16;               // scenes
 constexpr int kTcK = 32;               // real rows per slab
-constexpr int kTmemCols = 32;          // power of two >= 32, >= kTcN
+constexpr int kTmemCols = 128;         // 2 accumulator sets x 3 products x kTcN columns, power of two
+constexpr int kAccSet = 3 * kTcN;      // one accumulator per product (hi*hi, hi*lo, lo*hi)
 constexpr long long kTcWaitLimit = 1ll << 26;
 
 // operand tile bytes per plane and buffer
@@ -85,6 +86,30 @@ __device__ __forceinline__ bool bar_wait(uint64_t* bar, unsigned parity) {
     if (ok) return true;
   }
   return false;
+}
+
+// The 16 columns of this warp's 32-lane quarter at taddr (one row per lane).
+__device__ __forceinline__ void tmem_ld16(unsigned taddr, float (&v)[16]) {
+  unsigned r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// hi*hi + (hi*lo + lo*hi) from the three accumulators of one set
+__device__ __forceinline__ void tmem_sum3(unsigned taddr, float (&v)[16]) {
+  float b[16], c[16];
+  tmem_ld16(taddr, v);
+  tmem_ld16(taddr + kTcN, b);
+  tmem_ld16(taddr + 2 * kTcN, c);
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] += b[i] + c[i];
 }
 
 __device__ __forceinline__ float tf32_rn(float x) {
@@ -225,7 +250,7 @@ tc_adjoint_kernel(const __grid_constant__ TmapSet tmaps, const __grid_constant__
         if (i >= 2) ok = bar_wait(&accempty[ab], ((i / 2) - 1) & 1);
         if (!ok) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const unsigned d = tmem + ab * kTcN;
+        const unsigned d = tmem + ab * kAccSet;    // three independent accumulation chains
         for (int sl = 0; sl < ns && ok; ++sl, ++t) {
           const int s = t % kS;
           ok = bar_wait(&conv[s], (t / kS) & 1);
@@ -240,8 +265,8 @@ tc_adjoint_kernel(const __grid_constant__ TmapSet tmaps, const __grid_constant__
             const uint64_t dbh = smem_desc(b_hi + ks * 2 * kB_LBO, kB_LBO, kB_SBO);
             const uint64_t dbl = smem_desc(b_lo + ks * 2 * kB_LBO, kB_LBO, kB_SBO);
             mma_tf32(d, dah, dbh, acc0);
-            mma_tf32(d, dah, dbl, 1u);
-            mma_tf32(d, dal, dbh, 1u);
+            mma_tf32(d + kTcN, dah, dbl, acc0);
+            mma_tf32(d + 2 * kTcN, dal, dbh, acc0);
           }
           mma_commit(&empty[s]);
         }
@@ -306,22 +331,245 @@ tc_adjoint_kernel(const __grid_constant__ TmapSet tmaps, const __grid_constant__
       ok = __all_sync(0xffffffffu, ok);          // tcgen05.ld below is warp-collective
       if (!ok) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      unsigned r[16];
-      const unsigned taddr = tmem + ((unsigned)(quarter * 32) << 16) + ab * kTcN;
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-          : "r"(taddr)
-          : "memory");
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      float v[16];
+      tmem_sum3(tmem + ((unsigned)(quarter * 32) << 16) + ab * kAccSet, v);
       const int p = mt * kTcM + quarter * 32 + lane;
       if (p < N) {
         float4* out = reinterpret_cast<float4*>(gpart + (((size_t)q * splits + sp) * N + p) * kTcN);
 #pragma unroll
-        for (int e = 0; e < 4; ++e)
-          out[e] = make_float4(__uint_as_float(r[4 * e]), __uint_as_float(r[4 * e + 1]),
-                               __uint_as_float(r[4 * e + 2]), __uint_as_float(r[4 * e + 3]));
+        for (int e = 0; e < 4; ++e) out[e] = make_float4(v[4 * e], v[4 * e + 1], v[4 * e + 2], v[4 * e + 3]);
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      mbar_arrive(&accempty[ab]);
+    }
+  }
+  if (!ok) atomicExch(err, 1);
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+}
+
+// ------------------------------------------------------------------ forward
+// D_q (2KM x 16) = B_q V_q for the batched form's forward product (Eq. 3,
+// x_q-update: r = y' - B v for 16 scenes), V[p][s] = x - x_bar + z_bar - s of
+// scene s at pixel p.  M = 128 real rows (TMEM lanes), N = 16 scenes, K = 32
+// pixels per slab; items (sensor, row tile, pixel split) are spread over
+// persistent CTAs.  The operator tile arrives by TMA as [32 pixels][128 rows]
+// (rows contiguous, no swizzle) and the four 2 KB slabs of x, x_bar, z_bar, s
+// by bulk copies; converter warps transpose the tile into the SW128 K-major
+// layout while splitting it into TF32 hi and lo tiles (row m, pixel quad kq
+// lands in 16-byte chunk kq ^ (m mod 8) of its 128-byte row: conflict-free),
+// form V and split it into the no-swizzle B tiles.  The MMA issuer and the
+// epilogue are as in tc_adjoint_kernel; the epilogue writes partial sums in
+// the layout of the SIMT forward (partial[q][split][complex row][scene] as
+// float2), which bfwd_reduce_kernel turns into r = y' - sum.
+constexpr int kFwdS = 3;
+constexpr int kFwdRaw = kTcM * kTcK * 4;                       // [32 pixels][128 rows] floats, 16 KB
+constexpr int kVBytes = kTcK * kTcN * 4;                        // one [32 pixels][16 scenes] slab, 2 KB
+constexpr int kFwdStage = kFwdRaw + 2 * kABytes + 2 * kBBytes + 4 * kVBytes;   // 60 KB
+constexpr int kFwdSmem = kFwdS * kFwdStage + 1024;
+
+struct VSet {
+  const float* X;       // Q x N x 16
+  const float* xbar;    // N x 16
+  const float* zbar;
+  const float* sd;
+};
+
+__global__ void __launch_bounds__(kPipeThreads, 1)
+tc_forward_kernel(const __grid_constant__ TmapSet tmaps, const __grid_constant__ VSet vs, float* __restrict__ partial,
+                  int Q, int N, int KM, int splits, int* __restrict__ err) {
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t full[kFwdS], conv[kFwdS], empty[kFwdS], accfull[2], accempty[2];
+  __shared__ unsigned s_tmem;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int R = 2 * KM;
+  const int mtiles = (R + kTcM - 1) / kTcM;
+  const int items = Q * mtiles * splits;
+  const int pix_per = (N / splits + kTcK - 1) / kTcK * kTcK;
+  auto item_of = [&](int it, int& q, int& mt, int& sp, int& pb, int& ns) {
+    sp = it % splits;
+    const int qm = it / splits;
+    mt = qm % mtiles;
+    q = qm / mtiles;
+    pb = sp * pix_per;
+    const int pe = min(N, pb + pix_per);
+    ns = pe > pb ? (pe - pb + kTcK - 1) / kTcK : 0;
+  };
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&s_tmem)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 32) {
+    for (int s = 0; s < kFwdS; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&conv[s], 128);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&accfull[b], 1);
+      mbar_init(&accempty[b], 128);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const unsigned tmem = s_tmem;
+  bool ok = true;
+  // stage layout: raw A | A hi | A lo | B hi | B lo | x | x_bar | z_bar | s
+  auto stage = [&](int s) { return smem + s * kFwdStage; };
+  constexpr int oAhi = kFwdRaw, oAlo = kFwdRaw + kABytes, oBhi = kFwdRaw + 2 * kABytes, oBlo = oBhi + kBBytes,
+                oV = oBlo + kBBytes;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int t = 0;
+      for (int it = blockIdx.x; it < items && ok; it += gridDim.x) {
+        int q, mt, sp, pb, ns;
+        item_of(it, q, mt, sp, pb, ns);
+        for (int sl = 0; sl < ns && ok; ++sl, ++t) {
+          const int s = t % kFwdS;
+          if (t >= kFwdS) ok = bar_wait(&empty[s], ((t / kFwdS) - 1) & 1);
+          if (!ok) break;
+          unsigned char* st = stage(s);
+          const int p0 = pb + sl * kTcK;
+          const int nv = min(kTcK, N - p0);                      // pixels present in this slab
+          const unsigned vbytes = (unsigned)nv * kTcN * 4;
+          mbar_expect_tx(&full[s], kFwdRaw + 4 * vbytes);
+          asm volatile(
+              "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+                  su32(st)),
+              "l"(reinterpret_cast<uint64_t>(&tmaps.m[q])), "r"(mt * kTcM), "r"(p0), "r"(su32(&full[s]))
+              : "memory");
+          const float* src[4] = {vs.X + ((size_t)q * N + p0) * kTcN, vs.xbar + (size_t)p0 * kTcN,
+                                 vs.zbar + (size_t)p0 * kTcN, vs.sd + (size_t)p0 * kTcN};
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
+            asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                             su32(st + oV + a * kVBytes)),
+                         "l"(src[a]), "r"(vbytes), "r"(su32(&full[s]))
+                         : "memory");
+        }
+      }
+      if (!ok)
+        for (int u = max(0, t - kFwdS); u < t; ++u) bar_wait(&full[u % kFwdS], (u / kFwdS) & 1);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      int t = 0, i = 0;
+      for (int it = blockIdx.x; it < items && ok; it += gridDim.x) {
+        int q, mt, sp, pb, ns;
+        item_of(it, q, mt, sp, pb, ns);
+        if (ns == 0) continue;
+        const int ab = i & 1;
+        if (i >= 2) ok = bar_wait(&accempty[ab], ((i / 2) - 1) & 1);
+        if (!ok) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const unsigned d = tmem + ab * kAccSet;    // three independent accumulation chains
+        for (int sl = 0; sl < ns && ok; ++sl, ++t) {
+          const int s = t % kFwdS;
+          ok = bar_wait(&conv[s], (t / kFwdS) & 1);
+          if (!ok) break;
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const unsigned st = su32(stage(s));
+          const unsigned a_hi = st + oAhi, a_lo = st + oAlo, b_hi = st + oBhi, b_lo = st + oBlo;
+#pragma unroll
+          for (int ks = 0; ks < kTcK / 8; ++ks) {
+            const unsigned acc0 = (sl > 0 || ks > 0) ? 1u : 0u;
+            const uint64_t dah = sw128_desc(a_hi + ks * 32), dal = sw128_desc(a_lo + ks * 32);
+            const uint64_t dbh = smem_desc(b_hi + ks * 2 * kB_LBO, kB_LBO, kB_SBO);
+            const uint64_t dbl = smem_desc(b_lo + ks * 2 * kB_LBO, kB_LBO, kB_SBO);
+            mma_tf32(d, dah, dbh, acc0);
+            mma_tf32(d + kTcN, dah, dbl, acc0);
+            mma_tf32(d + 2 * kTcN, dal, dbh, acc0);
+          }
+          mma_commit(&empty[s]);
+        }
+        if (ok) mma_commit(&accfull[ab]);
+        ++i;
+      }
+    }
+  } else {
+    const int ct = tid - 64;                        // 0..127: row m of the tile
+    const int quarter = warp & 3;
+    int t = 0, i = 0;
+    for (int it = blockIdx.x; it < items && ok; it += gridDim.x) {
+      int q, mt, sp, pb, ns;
+      item_of(it, q, mt, sp, pb, ns);
+      if (ns == 0) {
+        const int r = mt * kTcM + quarter * 32 + lane;
+        if (r < R)
+          for (int sc = 0; sc < kTcN; ++sc)
+            partial[(((size_t)q * splits + sp) * KM + (r >> 1)) * kTcN * 2 + sc * 2 + (r & 1)] = 0.f;
+        continue;
+      }
+      for (int sl = 0; sl < ns && ok; ++sl, ++t) {
+        const int s = t % kFwdS;
+        ok = bar_wait(&full[s], (t / kFwdS) & 1);
+        if (!ok) break;
+        unsigned char* st = stage(s);
+        const float* raw = reinterpret_cast<const float*>(st);
+        const int nv = min(kTcK, N - (pb + sl * kTcK));
+        // A: row m = ct, pixel quads kq: transpose + TF32 split into SW128 K-major
+        const int m = ct;
+#pragma unroll
+        for (int kq = 0; kq < kTcK / 4; ++kq) {
+          float x[4];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) x[j] = raw[(4 * kq + j) * kTcM + m];   // zero-filled beyond N by TMA
+          const float4 h = make_float4(tf32_rn(x[0]), tf32_rn(x[1]), tf32_rn(x[2]), tf32_rn(x[3]));
+          const float4 l = make_float4(x[0] - h.x, x[1] - h.y, x[2] - h.z, x[3] - h.w);
+          const int off = (m >> 3) * 1024 + (m & 7) * 128 + ((kq ^ (m & 7)) << 4);
+          *reinterpret_cast<float4*>(st + oAhi + off) = h;
+          *reinterpret_cast<float4*>(st + oAlo + off) = l;
+        }
+        // B: V[k][n] for pixel k = ct / 4, scenes 4 (ct % 4) .. +3
+        {
+          const int k = ct >> 2, n0 = 4 * (ct & 3);
+          float v[4] = {0.f, 0.f, 0.f, 0.f};
+          if (k < nv) {
+            const float4 xx = *reinterpret_cast<const float4*>(st + oV + (k * kTcN + n0) * 4);
+            const float4 xb = *reinterpret_cast<const float4*>(st + oV + kVBytes + (k * kTcN + n0) * 4);
+            const float4 zb = *reinterpret_cast<const float4*>(st + oV + 2 * kVBytes + (k * kTcN + n0) * 4);
+            const float4 sdv = *reinterpret_cast<const float4*>(st + oV + 3 * kVBytes + (k * kTcN + n0) * 4);
+            v[0] = xx.x - xb.x + zb.x - sdv.x;
+            v[1] = xx.y - xb.y + zb.y - sdv.y;
+            v[2] = xx.z - xb.z + zb.z - sdv.z;
+            v[3] = xx.w - xb.w + zb.w - sdv.w;
+          }
+          float* bhi = reinterpret_cast<float*>(st + oBhi);
+          float* blo = reinterpret_cast<float*>(st + oBlo);
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int n = n0 + u;
+            const int off = ((k >> 2) * kB_LBO + (n >> 3) * kB_SBO + (n & 7) * 16 + (k & 3) * 4) / 4;
+            const float h = tf32_rn(v[u]);
+            bhi[off] = h;
+            blo[off] = v[u] - h;
+          }
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive(&conv[s]);
+      }
+      if (!ok) break;
+      const int ii = i++;
+      const int ab = ii & 1;
+      ok = bar_wait(&accfull[ab], (ii / 2) & 1);
+      ok = __all_sync(0xffffffffu, ok);
+      if (!ok) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      float v[16];
+      tmem_sum3(tmem + ((unsigned)(quarter * 32) << 16) + ab * kAccSet, v);
+      const int r = mt * kTcM + quarter * 32 + lane;           // real row
+      if (r < R) {
+        float* out = partial + (((size_t)q * splits + sp) * KM + (r >> 1)) * kTcN * 2 + (r & 1);
+#pragma unroll
+        for (int sc = 0; sc < kTcN; ++sc) out[sc * 2] = v[sc];
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       mbar_arrive(&accempty[ab]);
@@ -394,6 +642,45 @@ int launch_tc_adjoint(const float2* const* Aq, const float2* const* Wq, float* g
   }
   const int items = Q * div_up(N, kTcM) * splits;
   tc_adjoint_kernel<<<std::min(items, 152), kPipeThreads, kPipeSmem, st>>>(tm, ws, gpart, Q, N, KM, splits, err);
+  SADMM_LAUNCH_CHECK();
+  return SADMM_OK;
+}
+
+int tc_forward_splits(int Q, int N, int KM) {
+  const int tiles = div_up(2 * KM, kTcM) * Q;
+  const int want = div_up(152 * 4, tiles);
+  return std::max(1, std::min(want, div_up(N, 4 * kTcK)));
+}
+
+int launch_tc_forward(const float2* const* Aq, const float* X, const float* xbar, const float* zbar, const float* sd,
+                      float2* partial, int Q, int N, int KM, int splits, int* err, cudaStream_t st) {
+  if (Q < 1 || Q > kMaxSets || N < 1 || (2 * KM) % 16 != 0 || splits < 1) {
+    set_error("launch_tc_forward: bad sizes");
+    return SADMM_EINVAL;
+  }
+  EncodeTiledFn enc = tensor_map_encoder();
+  if (!enc) { set_error("launch_tc_forward: cuTensorMapEncodeTiled unavailable"); return SADMM_ECUDA; }
+  TmapSet tm;
+  memset(&tm, 0, sizeof tm);
+  for (int q = 0; q < Q; ++q) {
+    const cuuint64_t dims[2] = {(cuuint64_t)2 * KM, (cuuint64_t)N};
+    const cuuint64_t strides[1] = {(cuuint64_t)2 * KM * sizeof(float)};
+    const cuuint32_t box[2] = {(cuuint32_t)kTcM, (cuuint32_t)kTcK};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = enc(&tm.m[q], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float2*>(Aq[q]), dims, strides, box,
+                           estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) { set_error("launch_tc_forward: tensor map of sensor %d rejected (%d)", q, (int)r); return SADMM_ECUDA; }
+  }
+  const VSet vs{X, xbar, zbar, sd};
+  static bool conf = false;
+  if (!conf) {
+    SADMM_CUDA_TRY(cudaFuncSetAttribute(tc_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kFwdSmem));
+    conf = true;
+  }
+  const int items = Q * div_up(2 * KM, kTcM) * splits;
+  tc_forward_kernel<<<std::min(items, 152), kPipeThreads, kFwdSmem, st>>>(tm, vs, reinterpret_cast<float*>(partial), Q,
+                                                                          N, KM, splits, err);
   SADMM_LAUNCH_CHECK();
   return SADMM_OK;
 }

@@ -201,10 +201,11 @@ def test_trained_proposal_on_held_out_scene(B):
     network on plain runs of three scenes, then solve a held-out scene with
     Algorithm 1 alone and with the learned step.  Reported: the active-set work
     sum_k sum_q |J_q| relative to the plain run's, the deviation of x_G from the
-    plain run's, the re-admissions (false eliminations caught) and the
-    eliminations.  Required: the loss falls, the labels are not all of one
-    class, and the learned mode's x_G stays within max(5x Algorithm 1's
-    deviation, 1e-3) of the plain run's."""
+    plain run's, the re-admissions (false eliminations caught), for
+    Algorithm 1 alone, the learned step with a network that never proposes
+    (re-admission only) and the trained network.  Required: the loss falls,
+    the labels are not all of one class, and the trained mode's x_G ends
+    closer to the plain run's than Algorithm 1's does (and within 1e-3)."""
     from paper_2307_08606_gb300 import eliminator as E
     rho = 100.0
     lam_of = lambda sc: 0.05 * scenegen.lambda_max(sc.A, sc.y)
@@ -229,17 +230,21 @@ def test_trained_proposal_on_held_out_scene(B):
     p.close()
     full = iters * g.Q * g.N
     out = {}
-    for mode in (1, 2):
-        s = _solver(B, sc, rho, lam, elim=mode, learn_every=10, learn_theta=0.5)
+    # Algorithm 1 alone; the learned step with a network that never proposes
+    # (theta = 1: re-admission only); the trained network
+    for name, mode, theta in (("algorithm1", 1, 0.5), ("readmission", 2, 1.0), ("learned", 2, 0.5)):
+        s = _solver(B, sc, rho, lam, elim=mode, learn_every=10, learn_theta=theta)
         if mode == 2:
             s.set_eliminator(params, g.nx, g.nx)
         xg, st = s.solve(sc.y, iters)
         h = s.history()
-        out[mode] = dict(work=round(sum(r["active_total"] for r in h) / full, 4),
+        out[name] = dict(work=round(sum(r["active_total"] for r in h) / full, 4),
                          dev=float(np.linalg.norm(xg - xp) / np.linalg.norm(xp)),
                          readmitted=st["readmitted"], learned_steps=st["learned_steps"],
                          active=st["active_total"], ms=round(st["ms_total"], 1))
         s.close()
-    print(f"Algorithm 1: {out[1]}")
-    print(f"learned:     {out[2]}")
-    assert out[2]["dev"] <= max(5 * out[1]["dev"], 1e-3)
+    for k, v in out.items():
+        print(f"{k:12s} {v}")
+    # the learned step ends closer to the plain solution than Algorithm 1 alone
+    assert out["learned"]["dev"] < out["algorithm1"]["dev"]
+    assert out["learned"]["dev"] <= 1e-3
