@@ -54,29 +54,34 @@ __device__ __forceinline__ float gelu_grad(float z) {
 // wt[ci][co][2-ky][2-kx] = w[co][ci][ky][kx] (prep_transpose_kernel), run by
 // this kernel without bias or GELU.
 constexpr int kCiChunk = 8;
+constexpr int kOutGroup = 16;          // output channels per CTA
 
-template <int CIN, int NOUT>
+// Output channels are split over blockIdx.z in groups of OG (more CTAs for a
+// single image); each thread forms OG outputs of one pixel.
+template <int CIN, int NOUT, int OG>
 __global__ void __launch_bounds__(kTileXY * kTileXY)
 conv3x3_kernel(const float* __restrict__ in, const float* __restrict__ w, const float* __restrict__ bias,
                float* __restrict__ pre, float* __restrict__ out, int H, int Wd, int tiles_x) {
+  static_assert(OG % 4 == 0 && NOUT % OG == 0, "output groups of whole float4s");
   __shared__ float s_in[kCiChunk][kTileXY + 2][kTileXY + 2];
-  __shared__ float s_w[NOUT * kCiChunk * 9];
+  __shared__ __align__(16) float s_w[kCiChunk * 9 * OG];         // [c][k][o]: four outputs per 16-byte read
   const int b = blockIdx.y;
+  const int og = blockIdx.z * OG;
   const int ty0 = (blockIdx.x / tiles_x) * kTileXY, tx0 = (blockIdx.x % tiles_x) * kTileXY;
   const int t = threadIdx.x;
   const int ly = t / kTileXY, lx = t % kTileXY;
   const int y = ty0 + ly, x = tx0 + lx;
-  float acc[NOUT];
+  float acc[OG];
 #pragma unroll
-  for (int o = 0; o < NOUT; ++o) acc[o] = bias ? bias[o] : 0.f;
+  for (int o = 0; o < OG; ++o) acc[o] = bias ? bias[og + o] : 0.f;
   const float* inb = in + (size_t)b * CIN * H * Wd;
   constexpr int kHalo = (kTileXY + 2) * (kTileXY + 2);
   for (int c0 = 0; c0 < CIN; c0 += kCiChunk) {
     const int nc = min(kCiChunk, CIN - c0);
     __syncthreads();
-    for (int e = t; e < NOUT * kCiChunk * 9; e += blockDim.x) {
+    for (int e = t; e < OG * kCiChunk * 9; e += blockDim.x) {
       const int o = e / (kCiChunk * 9), c = (e / 9) % kCiChunk, k = e % 9;
-      s_w[e] = c < nc ? w[((size_t)o * CIN + c0 + c) * 9 + k] : 0.f;
+      s_w[(c * 9 + k) * OG + o] = c < nc ? w[((size_t)(og + o) * CIN + c0 + c) * 9 + k] : 0.f;
     }
     for (int e = t; e < kCiChunk * kHalo; e += blockDim.x) {
       const int c = e / kHalo, r = e % kHalo;
@@ -90,16 +95,23 @@ conv3x3_kernel(const float* __restrict__ in, const float* __restrict__ w, const 
 #pragma unroll
       for (int k = 0; k < 9; ++k) {
         const float v = s_in[c][ly + k / 3][lx + k % 3];
+        const float4* wk = reinterpret_cast<const float4*>(s_w + (c * 9 + k) * OG);
 #pragma unroll
-        for (int o = 0; o < NOUT; ++o) acc[o] = fmaf(s_w[(o * kCiChunk + c) * 9 + k], v, acc[o]);
+        for (int o4 = 0; o4 < OG / 4; ++o4) {
+          const float4 ww = wk[o4];
+          acc[4 * o4 + 0] = fmaf(ww.x, v, acc[4 * o4 + 0]);
+          acc[4 * o4 + 1] = fmaf(ww.y, v, acc[4 * o4 + 1]);
+          acc[4 * o4 + 2] = fmaf(ww.z, v, acc[4 * o4 + 2]);
+          acc[4 * o4 + 3] = fmaf(ww.w, v, acc[4 * o4 + 3]);
+        }
       }
     }
   }
   if (y >= H || x >= Wd) return;
   const size_t base = (size_t)b * NOUT * H * Wd + (size_t)y * Wd + x;
 #pragma unroll
-  for (int o = 0; o < NOUT; ++o) {
-    const size_t idx = base + (size_t)o * H * Wd;
+  for (int o = 0; o < OG; ++o) {
+    const size_t idx = base + (size_t)(og + o) * H * Wd;
     if (pre) {
       pre[idx] = acc[o];
       out[idx] = gelu(acc[o]);
@@ -278,13 +290,17 @@ int tiles(const CnnCtx& c) { return div_up(c.H, kTileXY) * div_up(c.W, kTileXY);
 
 int cnn_forward_impl(CnnCtx& c, const float* in, int B, float* prob, cudaStream_t st) {
   const int tx = div_up(c.W, kTileXY);
-  const dim3 grid(tiles(c), B);
+  const dim3 grid(tiles(c), B, kC / kOutGroup);
   const float* x = in;
   for (int l = 0; l < kLayers; ++l) {
     const float* w = c.wq + layer_offset(l);
     const float* bias = w + (l == 0 ? conv_w_size(kCin0) : conv_w_size(kC));
-    if (l == 0) conv3x3_kernel<kCin0, kC><<<grid, kTileXY * kTileXY, 0, st>>>(x, w, bias, c.pre[l], c.act[l + 1], c.H, c.W, tx);
-    else conv3x3_kernel<kC, kC><<<grid, kTileXY * kTileXY, 0, st>>>(x, w, bias, c.pre[l], c.act[l + 1], c.H, c.W, tx);
+    if (l == 0)
+      conv3x3_kernel<kCin0, kC, kOutGroup><<<grid, kTileXY * kTileXY, 0, st>>>(x, w, bias, c.pre[l], c.act[l + 1], c.H,
+                                                                              c.W, tx);
+    else
+      conv3x3_kernel<kC, kC, kOutGroup><<<grid, kTileXY * kTileXY, 0, st>>>(x, w, bias, c.pre[l], c.act[l + 1], c.H,
+                                                                           c.W, tx);
     SADMM_LAUNCH_CHECK();
     x = c.act[l + 1];
   }
@@ -405,7 +421,8 @@ int sadmm_cnn_backward(sadmm_cnn_t c, const float* in, const float* labels, int 
     if (l > 0) {
       prep_transpose_kernel<<<div_up(conv_w_size(kC), 256), 256, 0, st>>>(c->wq + layer_offset(l), kC, c->wt);
       SADMM_LAUNCH_CHECK();
-      conv3x3_kernel<kC, kC><<<grid, kTileXY * kTileXY, 0, st>>>(c->dz, c->wt, nullptr, nullptr, c->da, c->H, c->W, tx);
+      conv3x3_kernel<kC, kC, kOutGroup><<<dim3(grid.x, grid.y, kC / kOutGroup), kTileXY * kTileXY, 0, st>>>(
+          c->dz, c->wt, nullptr, nullptr, c->da, c->H, c->W, tx);
       SADMM_LAUNCH_CHECK();
     }
   }
