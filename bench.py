@@ -335,6 +335,21 @@ def learned_measure(sc, lam, dev, stream):
             "cnn_forward_tflops": flops / (cnn_ms / 1e3) / 1e12}
 
 
+def reduce_over_ranks(ms, iters, world, device):
+    """Whole-job rate of independent replicas: the slowest rank's time and the
+    iterations of all ranks (the only collectives of the run; the solver itself
+    has no data-path exchange).  Returns (max ms, iterations / max time)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    it = torch.tensor([float(iters)], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(it, op=dist.ReduceOp.SUM)
+    ms_max = float(t.item())
+    return ms_max, float(it.item()) / (ms_max / 1e3)
+
+
 def make_scene(name, seed, sensors=0):
     import dataclasses
     import scenegen
@@ -441,13 +456,7 @@ def main():
     ms = start.elapsed_time(end)
     prof = s.profile()
     s.set_profiling(False)
-    t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    it = torch.tensor([float(iters_done)], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dist.all_reduce(it, op=dist.ReduceOp.SUM)
-    ms_max = float(t.item())
-    value = float(it.item()) / (ms_max / 1e3)
+    ms_max, value = reduce_over_ranks(ms, iters_done, world, dev)
 
     # end to end through the C ABI with pinned host buffers
     e2e = None
@@ -462,10 +471,8 @@ def main():
             e_iters += st["iters"]
         torch.cuda.synchronize()
         e_ms = (time.perf_counter() - t0) * 1e3
-        te = torch.tensor([e_ms], dtype=torch.float64, device=dev)
-        if world > 1:
-            dist.all_reduce(te, op=dist.ReduceOp.MAX)
-        e2e = {"value": world * e_iters / (float(te.item()) / 1e3), "unit": UNIT,
+        _, e_value = reduce_over_ranks(e_ms, e_iters, world, dev)
+        e2e = {"value": e_value, "unit": UNIT,
                "h2d_bytes_per_step": int(g.Q * g.KM * 8), "d2h_bytes_per_step": int(g.N * 4)}
 
     # roofline of the dominant kernel group
