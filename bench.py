@@ -238,7 +238,9 @@ def forms_measure(sc, lam, dev, stream, iters=400):
         every 4 iterations and after every set change);
       - elimination (Algorithm 1) with the per-iteration host decisions and the
         factor downdates it needs, with the active-set fraction at the end and
-        the HBM rate of its iterations alone.
+        the HBM rate of its iterations alone;
+      - elimination with Algorithm 1's pass every 16 iterations (batched factor
+        updates) on the BF16 hi-plane operator.
     x_G is identically zero on this scene (Eq. 2 is degenerate there), so the
     forms are compared on the stacked iterate X: |X_form - X_plain| / |X_plain|."""
     import torch
@@ -248,7 +250,8 @@ def forms_measure(sc, lam, dev, stream, iters=400):
     y_dev = [torch.from_numpy(v).to(dev) for v in sc.y]
     out, Xp = {}, None
     for name, kw in (("plain_fp32", dict(elim=0)), ("bf16_hi_corr4", dict(elim=0, precision=3, correct_every=4)),
-                     ("elim_fp32", dict(elim=1))):
+                     ("elim_fp32", dict(elim=1)),
+                     ("elim_every16_bf16_hi_corr4", dict(elim=1, ssc_every=16, precision=3, correct_every=4))):
         s = binding.Solver(g.Q, g.M, g.K, g.N, 1.0, lam, stream=stream.cuda_stream, **kw)
         for q in range(g.Q):
             s.set_operator(q, At[q])

@@ -85,6 +85,10 @@ typedef struct {
   int    learn_every;   /* default 10                                                   */
   double learn_theta;   /* default 0.5, in [0, 1]                                       */
   double readmit;       /* default 10 (>= 0); elim = 2 also needs eps_p > 0               */
+  /* Removal policy (an extension; the paper runs Algorithm 1 every iteration):
+     Algorithm 1's pass runs after iteration k only when k is a multiple of
+     ssc_every (default 1), so that each factor update takes a batch of columns. */
+  int    ssc_every;
 } sadmm_criterion;
 
 /* Per-solve summary. */
@@ -104,7 +108,8 @@ typedef struct {
 /* One record per iteration of the last solve. */
 typedef struct {
   int    k;            /* iterations completed                                         */
-  int    gate;         /* 1 if Algorithm 1's test ran (elim on, k >= Kp, r_pri <= eps_pri) */
+  int    gate;         /* 1 if Algorithm 1's test ran (elim on, k >= Kp, k a multiple of
+                          ssc_every, r_pri <= eps_pri)                                  */
   int    changed;      /* number of sensors whose active set shrank                    */
   int    active_total; /* sum_q |J_q| after this iteration                             */
   int    learned;      /* 1 if the learned proposal ran in this iteration (elim = 2)   */

@@ -70,6 +70,7 @@ class Criterion:
     learn_every: int = 10  # elim 2: period of the learned step
     learn_theta: float = 0.5   # elim 2: drop pixel i when the network's p_i > learn_theta
     readmit: float = 10.0  # elim 2: re-admit when the coordinate step exceeds readmit * eps_p
+    ssc_every: int = 1     # Algorithm 1's pass after iteration k only when ssc_every divides k
 
 
 def soft(v, t):
@@ -241,7 +242,7 @@ def sadmm(A, y, rho, lam, crit: Criterion, iters, tol=0.0, state: State = None, 
         gate = False
         if crit.elim and st.k >= crit.Kp:
             rec["gate_margin"] = abs(r_pri - eps_pri) / eps_pri if eps_pri > 0 else np.inf
-            gate = r_pri <= eps_pri
+            gate = r_pri <= eps_pri and st.k % crit.ssc_every == 0
         rec["gate"] = gate
         learned = (pr is not None and st.k % crit.learn_every == 0 and st.k >= max(crit.Kp, 4))
         readd, prob = None, None

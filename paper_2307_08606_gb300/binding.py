@@ -26,7 +26,7 @@ class Criterion(C.Structure):
                 ("eps_abs", C.c_double), ("eps_rel", C.c_double), ("elim", C.c_int),
                 ("freeze_mode", C.c_int), ("stop", C.c_int), ("precision", C.c_int),
                 ("correct_every", C.c_int), ("learn_every", C.c_int), ("learn_theta", C.c_double),
-                ("readmit", C.c_double)]
+                ("readmit", C.c_double), ("ssc_every", C.c_int)]
 
 
 class Stats(C.Structure):

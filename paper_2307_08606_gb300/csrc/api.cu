@@ -86,7 +86,7 @@ struct Ctx {
   float2* partial = nullptr;
   size_t partial_cap = 0;
   float2* spd_part = nullptr;  // per-sensor partial sums of the symmetric factor apply
-  float2* dd_part = nullptr;   // partial sums of the factor updates' applies (64 columns)
+  DdScratch dd{};              // scratch of the factor updates' 16-column applies
   size_t spd_part_stride = 0;
   int* spd_err = nullptr;      // set by the factor apply if a tile copy timed out
   double* red = nullptr;
@@ -272,25 +272,18 @@ int refresh(Ctx& c, const std::vector<int>& qs, bool full_set) {
 int downdate(Ctx& c, const std::vector<int>& qs, std::vector<int>* failed, bool add = false) {
   if (qs.empty()) return SADMM_OK;
   std::vector<int> dst(c.Q), etot(c.Q);
-  std::vector<std::vector<int>> Eh(c.Q);
   int max_e = 0;
   for (int q : qs) {
     Sensor& S = c.s[q];
     dst[q] = (S.cur == S.full) ? (S.full + 1) % 3 : S.cur;
     etot[q] = c.h_counts[(add ? 3 : 1) * c.Q + q];
     max_e = std::max(max_e, etot[q]);
-    Eh[q].resize(etot[q]);
-    if (etot[q] > 0)
-      SADMM_CUDA_TRY(cudaMemcpyAsync(Eh[q].data(), add ? S.R : S.E, etot[q] * sizeof(int), cudaMemcpyDeviceToHost,
-                                     c.st));
   }
   SADMM_CUDA_TRY(cudaMemsetAsync(c.dstatus, 0, sizeof(int) * c.Q, c.st));
-  SADMM_CUDA_TRY(cudaStreamSynchronize(c.st));
   const int n = 2 * c.KM;
   const size_t nblk = div_up(n, 256);
   for (int off = 0; off < max_e; off += kDowndateMax) {
     std::vector<DowndateJob> jobs;
-    std::vector<const int*> eh;
     for (int q : qs) {
       Sensor& S = c.s[q];
       if (etot[q] <= off) continue;
@@ -302,10 +295,8 @@ int downdate(Ctx& c, const std::vector<int>& qs, std::vector<int>* failed, bool 
       j.slot = q;
       j.sign = add ? -1 : 1;
       jobs.push_back(j);
-      eh.push_back(Eh[q].data() + off);
     }
-    SADMM_TRY(run_downdate_pairs(jobs.data(), eh.data(), (int)jobs.size(), c.KM, c.crit.mu, c.dd_part, c.dstatus,
-                                 c.spd_err, c.st));
+    SADMM_TRY(run_downdate_pairs(jobs.data(), (int)jobs.size(), c.KM, c.crit.mu, c.dd, c.dstatus, c.spd_err, c.st));
   }
   SADMM_CUDA_TRY(cudaMemcpyAsync(c.h_status, c.dstatus, sizeof(int) * c.Q, cudaMemcpyDeviceToHost, c.st));
   SADMM_CUDA_TRY(cudaStreamSynchronize(c.st));
@@ -799,6 +790,7 @@ void sadmm_default_criterion(sadmm_criterion* c) {
   c->learn_every = 10;
   c->learn_theta = 0.5;
   c->readmit = 10.0;
+  c->ssc_every = 1;
 }
 
 int sadmm_set_allocator(sadmm_alloc_fn alloc, sadmm_free_fn release, void* user) {
@@ -826,7 +818,7 @@ int sadmm_create(int Q, int M, int K, int N, double rho, double lambda, const sa
       (c.elim == 2 && (c.learn_every < 1 || !(c.eps_p > 0.0) || !(c.learn_theta >= 0.0 && c.learn_theta <= 1.0) ||
                        !(c.readmit >= 0.0))) ||
       c.stop < 0 || c.stop > 1 || !std::isfinite(rho) || !std::isfinite(lambda) ||
-      c.precision < 0 || c.precision > 4 || c.correct_every < 1) {
+      c.precision < 0 || c.precision > 4 || c.correct_every < 1 || c.ssc_every < 1) {
     set_error("sadmm_create: invalid sizes or parameters (Q=%d M=%d K=%d N=%d rho=%g lambda=%g)", Q, M,
               K, N, rho, lambda);
     return SADMM_EINVAL;
@@ -883,8 +875,12 @@ int sadmm_create(int Q, int M, int K, int N, double rho, double lambda, const sa
   ctx->spd_part_stride = sym_part_pairs(ctx->npad_max);
   ctx->spd_part = (float2*)A((size_t)Q * ctx->spd_part_stride * sizeof(float2));
   ctx->spd_err = (int*)A(sizeof(int));
-  if (c.elim > 0 && ctx->npad_max == 2 * KM)     // Woodbury-form factors get rank updates
-    ctx->dd_part = (float2*)A((size_t)kMaxSets * ctx->spd_part_stride * sizeof(float2));
+  if (c.elim > 0 && ctx->npad_max == 2 * KM) {   // Woodbury-form factors get rank updates
+    const int n = 2 * (int)KM;
+    ctx->dd.U = (float*)A((size_t)Q * n * 16 * sizeof(float));
+    ctx->dd.dptrs = (void**)A((size_t)2 * Q * sizeof(void*));
+    ctx->dd.part = (float2*)A((size_t)Q * multi_apply_part_pairs(n) * sizeof(float2));
+  }
   ctx->red = (double*)A((size_t)residual_blocks(N) * 8 * sizeof(double));
   ctx->ticket = (unsigned int*)A(sizeof(unsigned int));
   ctx->scal = (IterScalars*)A(sizeof(IterScalars));

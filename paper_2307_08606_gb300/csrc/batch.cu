@@ -393,6 +393,56 @@ __global__ void bget_x_kernel(const float* __restrict__ X, int N, int scene, flo
 }
 
 
+// ------------------------------------------- multi-column apply (factor updates)
+// P[:, c] = F B[:, E_c] for up to 16 columns at a time (the W U product of a
+// rank update of the factor, Eq. 3, x_q-update with changed active sets):
+// the columns are gathered into a [row][16] block and pushed through the same
+// packed-tile 16-RHS kernel as the batched apply; the reduction writes FP64.
+struct ColJob {
+  const float2* A;      // operator of the sensor (pixel-major)
+  const int* E;         // columns (pixels), device
+  int e;                // columns in this call's window [c0, c0 + 16)
+  float* U;             // n x 16 staging
+  double* P;            // n x 32 output (row-major), columns c0 .. c0 + 15 written
+};
+
+__global__ void gather_cols_kernel(const __grid_constant__ SetBlock<ColJob> jobs, int n, int c0) {
+  const ColJob& jb = jobs.v[blockIdx.y];
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n * kBS) return;
+  const int j = idx / kBS, c = idx % kBS;
+  float v = 0.f;
+  if (c < jb.e) v = reinterpret_cast<const float*>(jb.A)[(size_t)jb.E[c0 + c] * n + j];
+  jb.U[idx] = v;
+}
+
+__global__ void __launch_bounds__(256)
+bspd_reduce_cols_kernel(const float2* __restrict__ part, size_t part_stride, const __grid_constant__ SetBlock<ColJob> jobs,
+                        int n, int c0) {
+  const int q = blockIdx.y, I = blockIdx.x;
+  const ColJob& jb = jobs.v[q];
+  const int nt = ntiles_side(n);
+  const int i = I * kT + (threadIdx.x >> 2), s0 = 4 * (threadIdx.x & 3);
+  DF acc[4] = {DF{0.f, 0.f}, DF{0.f, 0.f}, DF{0.f, 0.f}, DF{0.f, 0.f}};
+  const float2* pq = part + (size_t)q * part_stride;
+  for (int J = 0; J < nt; ++J) {
+    const int a = min(I, J), c = max(I, J);
+    const float2* p = pq + (size_t)tile_index(a, c, nt) * kBtPart + (J >= I ? 0 : kT * kBS) +
+                      (threadIdx.x >> 2) * kBS + s0;
+    const float4 x = reinterpret_cast<const float4*>(p)[0], y = reinterpret_cast<const float4*>(p)[1];
+    df_add(acc[0], DF{x.x, x.y});
+    df_add(acc[1], DF{x.z, x.w});
+    df_add(acc[2], DF{y.x, y.y});
+    df_add(acc[3], DF{y.z, y.w});
+  }
+  if (i >= n) return;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const int c = s0 + e;
+    if (c < jb.e) jb.P[(size_t)i * kDowndateMax + c0 + c] = (double)acc[e].hi + (double)acc[e].lo;
+  }
+}
+
 }  // namespace
 
 struct BatchCtx {
@@ -484,6 +534,43 @@ int batch_launch_iteration(BatchCtx& c) {
 }
 
 }  // namespace
+
+size_t multi_apply_part_pairs(int n) {
+  const size_t nt = ntiles_side(n);
+  return nt * (nt + 1) / 2 * kBtPart;
+}
+
+int launch_multi_apply_cols(const float2* const* F, const float2* const* A, const int* const* E, const int* e, double* const* P,
+                            int njobs, int n, int c0, float* U, void** dptrs, float2* part, int* err, cudaStream_t st) {
+  if (njobs <= 0) return SADMM_OK;
+  if (njobs > kMaxSets || n % kT != 0) { set_error("launch_multi_apply_cols: bad sizes"); return SADMM_EINVAL; }
+  SetBlock<ColJob> blk;
+  std::vector<const void*> hp(2 * njobs);
+  for (int j = 0; j < njobs; ++j) {
+    blk.v[j] = ColJob{A[j], E[j], std::max(0, std::min(kBS, e[j] - c0)), U + (size_t)j * n * kBS, P[j]};
+    hp[j] = F[j];
+    hp[njobs + j] = blk.v[j].U;
+  }
+  SADMM_CUDA_TRY(cudaMemcpyAsync(dptrs, hp.data(), hp.size() * sizeof(void*), cudaMemcpyHostToDevice, st));
+  gather_cols_kernel<<<dim3(div_up(n * kBS, 256), njobs), 256, 0, st>>>(blk, n, c0);
+  SADMM_LAUNCH_CHECK();
+  const int nt = div_up(n, kT), items = njobs * nt * (nt + 1) / 2;
+  const int smem = kBtTileBytes + 2 * kT * kBS * (int)sizeof(float);
+  static bool conf = false;
+  if (!conf) {
+    SADMM_CUDA_TRY(cudaFuncSetAttribute(bspd_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    conf = true;
+  }
+  const size_t stride = multi_apply_part_pairs(n);
+  bspd_tile_kernel<<<std::min(items, 152 * 5), kBtThreads, smem, st>>>(
+      reinterpret_cast<const float2* const*>(dptrs), reinterpret_cast<const float* const*>(dptrs + njobs), part, stride,
+      n, 1, items, err);
+  SADMM_LAUNCH_CHECK();
+  bspd_reduce_cols_kernel<<<dim3(nt, njobs), 256, 0, st>>>(part, stride, blk, n, c0);
+  SADMM_LAUNCH_CHECK();
+  return SADMM_OK;
+}
+
 }  // namespace sadmm
 
 struct sadmm_batch_ctx : sadmm::BatchCtx {};

@@ -137,8 +137,6 @@ struct SpdSet {
   int q;
   float2* part;      // sym_part_pairs(n) scratch
   int tile0;         // set by launch_spd_apply
-  double* outd;      // optional: out written as hi + lo in FP64, element i at outd[i * ldd]
-  int ldd;
 };
 // out = F u for every set (or, with update, the primal x-update epilogue).
 // *err is set to 1 if a tile copy did not complete within the wait limit.
@@ -240,13 +238,27 @@ struct DowndateJob {
   float2* Fdst;          // may alias Fsrc
 };
 int run_downdate(const DowndateJob* jobs, int njobs, int KM, double mu, int* d_status, cudaStream_t st);
+
+// P[:, c0 + c] = F B[:, E[c0 + c]] for c < min(16, e - c0), per job (batch.cu):
+// the 16-column packed-tile apply used by the factor updates.  F, A, E, P:
+// HOST arrays of per-job device pointers; U: njobs x n x 16 floats of scratch;
+// dptrs: 2 x njobs device pointers of scratch; part: njobs x
+// multi_apply_part_pairs(n) float2 of scratch.
+size_t multi_apply_part_pairs(int n);
+int launch_multi_apply_cols(const float2* const* F, const float2* const* A, const int* const* E, const int* e, double* const* P,
+                            int njobs, int n, int c0, float* U, void** dptrs, float2* part, int* err, cudaStream_t st);
+
 // The same rank update applied to the packed (hi, lo) pair copy of W only
-// (Fsrc -> Fdst), with W U formed by the double-float symmetric apply and the
-// rank-e correction accumulated in double-float arithmetic; the FP64 Wsrc/Wdst
-// are not used.  E_host: the removed pixels of every job (host copies).
-// part: scratch of 64 x sym_part_pairs(n) float2.
-int run_downdate_pairs(const DowndateJob* jobs, const int* const* E_host, int njobs, int KM, double mu,
-                       float2* part, int* d_status, int* err, cudaStream_t st);
+// (Fsrc -> Fdst), with W U formed by the 16-column double-float packed-tile
+// apply and the rank-e correction accumulated in double-float arithmetic; the
+// FP64 Wsrc/Wdst are not used.  All jobs share n.
+struct DdScratch {
+  float* U;          // jobs x n x 16
+  void** dptrs;      // 2 x jobs device pointers
+  float2* part;      // jobs x multi_apply_part_pairs(n)
+};
+int run_downdate_pairs(const DowndateJob* jobs, int njobs, int KM, double mu, const DdScratch& scr, int* d_status,
+                       int* err, cudaStream_t st);
 size_t downdate_scratch_doubles(int n);
 
 }  // namespace sadmm

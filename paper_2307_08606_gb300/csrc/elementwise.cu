@@ -51,7 +51,7 @@ __device__ __forceinline__ float soft_threshold(float t, float thr) {
 __global__ void __launch_bounds__(kResThreads)
 residual_kernel(const __grid_constant__ SolverView sv, double* __restrict__ partials,
                 unsigned int* ticket, IterScalars* __restrict__ out, int k_after, double eps_abs,
-                double eps_rel, int elim, int Kp) {
+                double eps_rel, int elim, int Kp, int ssc_every) {
   __shared__ double s_red[kResThreads / 32][kNumSums];
   __shared__ bool s_last;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -127,7 +127,7 @@ residual_kernel(const __grid_constant__ SolverView sv, double* __restrict__ part
     r.dxg_norm = Q * sqrt(tot[7]);
     r.xnorm = xn;
     r.k = k_after;
-    r.gate = (elim && k_after >= Kp && r.r_pri <= r.eps_pri) ? 1 : 0;
+    r.gate = (elim && k_after >= Kp && k_after % ssc_every == 0 && r.r_pri <= r.eps_pri) ? 1 : 0;
     r.changed = 0;
     double chk = 0.0;
 #pragma unroll
@@ -243,7 +243,7 @@ int residual_blocks(int N) { return div_up(N, kResThreads); }
 int launch_residuals(const SolverView& sv, const sadmm_criterion& c, double* partials,
                      unsigned int* ticket, IterScalars* out, int k_after, cudaStream_t st) {
   residual_kernel<<<residual_blocks(sv.N), kResThreads, 0, st>>>(
-      sv, partials, ticket, out, k_after, c.eps_abs, c.eps_rel, c.elim, c.Kp);
+      sv, partials, ticket, out, k_after, c.eps_abs, c.eps_rel, c.elim, c.Kp, c.ssc_every);
   SADMM_LAUNCH_CHECK();
   return SADMM_OK;
 }

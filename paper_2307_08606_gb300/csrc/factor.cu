@@ -640,41 +640,33 @@ int run_downdate(const DowndateJob* jobs, int njobs, int KM, double mu, int* d_s
   return SADMM_OK;
 }
 
-int run_downdate_pairs(const DowndateJob* jobs, const int* const* E_host, int njobs, int KM, double mu,
-                       float2* part, int* d_status, int* err, cudaStream_t st) {
+int run_downdate_pairs(const DowndateJob* jobs, int njobs, int KM, double mu, const DdScratch& scr, int* d_status,
+                       int* err, cudaStream_t st) {
   if (njobs <= 0) return SADMM_OK;
   if (njobs > kMaxSets) { set_error("run_downdate_pairs: too many jobs"); return SADMM_EINVAL; }
   DdBlock blk;
-  int n_max = 0;
+  int n_max = 0, e_max = 0;
+  std::vector<const float2*> F(njobs), A(njobs);
+  std::vector<const int*> E(njobs);
+  std::vector<int> e(njobs);
+  std::vector<double*> P(njobs);
   for (int i = 0; i < njobs; ++i) {
     blk.v[i] = jobs[i];
-    if (jobs[i].e < 1 || jobs[i].e > DM || jobs[i].n % T != 0 || !jobs[i].Fsrc || !jobs[i].Fdst) {
+    if (jobs[i].e < 1 || jobs[i].e > DM || jobs[i].n % T != 0 || !jobs[i].Fsrc || !jobs[i].Fdst ||
+        (i > 0 && jobs[i].n != jobs[0].n)) {
       set_error("run_downdate_pairs: bad job (e=%d n=%d)", jobs[i].e, jobs[i].n);
       return SADMM_EINVAL;
     }
     n_max = max(n_max, jobs[i].n);
+    e_max = max(e_max, jobs[i].e);
+    F[i] = jobs[i].Fsrc; A[i] = jobs[i].A; E[i] = jobs[i].E; e[i] = jobs[i].e; P[i] = jobs[i].P;
     // columns e..31 of P must be zero for the kernels below
     SADMM_CUDA_TRY(cudaMemsetAsync(jobs[i].P, 0, (size_t)jobs[i].n * DM * sizeof(double), st));
   }
-  // P = W U, one symmetric apply per removed column (u = that pixel's column of B)
-  std::vector<SpdSet> sets;
-  const size_t stride = sym_part_pairs(n_max);
-  for (int i = 0; i < njobs; ++i)
-    for (int c = 0; c < jobs[i].e; ++c) {
-      SpdSet s{};
-      s.P = jobs[i].Fsrc;
-      s.n = jobs[i].n;
-      s.u = reinterpret_cast<const float*>(jobs[i].A) + (size_t)E_host[i][c] * 2 * KM;
-      s.outd = jobs[i].P + c;
-      s.ldd = DM;
-      sets.push_back(s);
-    }
-  SolverView sv{};
-  for (size_t b = 0; b < sets.size(); b += kMaxSets) {
-    const int ns = (int)std::min<size_t>(kMaxSets, sets.size() - b);
-    for (int k = 0; k < ns; ++k) sets[b + k].part = part + (size_t)k * stride;
-    SADMM_TRY(launch_spd_apply(sets.data() + b, ns, false, sv, err, st));
-  }
+  // P = W U, sixteen columns of U (removed pixels' columns of B) per packed-tile pass
+  for (int c0 = 0; c0 < e_max; c0 += 16)
+    SADMM_TRY(launch_multi_apply_cols(F.data(), A.data(), E.data(), e.data(), P.data(), njobs, n_max, c0, scr.U,
+                                      scr.dptrs, scr.part, err, st));
   dd_s_kernel<<<dim3(div_up(n_max, 256), njobs), DM * DM, 0, st>>>(blk, KM);
   SADMM_LAUNCH_CHECK();
   dd_chol_kernel<<<njobs, DM * DM, 0, st>>>(blk, mu, d_status);

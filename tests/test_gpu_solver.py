@@ -294,3 +294,23 @@ def test_downdated_factor_matches_fresh_factorisation(B):
     a.resume(1)
     c.resume(1)
     assert _rel(c.X(), a.X()) <= 1e-6
+
+
+def test_batched_removal_policy(B):
+    """ssc_every = 3: Algorithm 1's pass runs only after iterations 3, 6, ...;
+    on the resolved 8x8 scene the GPU run matches the oracle's iterate (1e-4)
+    and, while the decision margins allow, its active sets."""
+    sc = scenegen.build_scene("resolved_tiny", seed=2, snr_db=30.0)
+    lam = 0.05 * scenegen.lambda_max(sc.A, sc.y)
+    crit = oracle.Criterion(elim=1, Kp=4, ssc_every=3)
+    ref = oracle.sadmm(sc.A, sc.y, 1.0, lam, crit, iters=220)
+    s = _solver(B, sc, 1.0, lam, elim=1, Kp=4, ssc_every=3)
+    s.solve(sc.y, 220)
+    assert _rel(s.X(), ref.state.x) <= TOL
+    hist = s.history()
+    assert all(h["gate"] == 0 for h in hist if h["k"] % 3)
+    assert any(h["gate"] for h in hist)
+    if _margins_ok(ref.history, crit.eps_p):
+        for q in range(sc.geom.Q):
+            assert np.array_equal(s.active(q), ref.state.J[q])
+    s.close()

@@ -205,12 +205,14 @@ def _trajectory(sc, lam, crit, iters):
     return xs, Js, recs, st
 
 
-def test_ssc_window_and_monotone_sets():
+@pytest.mark.parametrize("ssc_every", [1, 3])
+def test_ssc_window_and_monotone_sets(ssc_every):
     """Recompute Algorithm 1 from the stored trajectory: at every gated
     iteration J_q = {i in previous J_q : mean_{last Kp} |x^{t+1} - x^t| >= eps_p}.
-    Active sets only shrink, and frozen entries are bit-constant afterwards."""
+    Active sets only shrink, and frozen entries are bit-constant afterwards.
+    With the batched removal policy the test runs only when ssc_every divides k."""
     sc, lam = _elim_scene()
-    crit = oracle.Criterion(elim=1, eps_p=1e-5, Kp=4)
+    crit = oracle.Criterion(elim=1, eps_p=1e-5, Kp=4, ssc_every=ssc_every)
     x0 = np.zeros((sc.geom.Q, sc.geom.N))
     xs, Js, recs, _ = _trajectory(sc, lam, crit, 200)
     traj = [x0] + xs
@@ -219,6 +221,8 @@ def test_ssc_window_and_monotone_sets():
     frozen_at = {}
     for t, (J, rec) in enumerate(zip(Js, recs)):
         k = t + 1
+        if k % ssc_every:
+            assert not rec["gate"]
         for q in range(sc.geom.Q):
             assert set(J[q]) <= set(prevJ[q])
             if rec["gate"]:
