@@ -879,7 +879,8 @@ int sadmm_create(int Q, int M, int K, int N, double rho, double lambda, const sa
     const int n = 2 * (int)KM;
     ctx->dd.U = (float*)A((size_t)Q * n * 16 * sizeof(float));
     ctx->dd.dptrs = (void**)A((size_t)2 * Q * sizeof(void*));
-    ctx->dd.part = (float2*)A((size_t)Q * multi_apply_part_pairs(n) * sizeof(float2));
+    ctx->dd.part = (float2*)A(std::max((size_t)Q * multi_apply_part_pairs(n), (size_t)kMaxSets * sym_part_pairs(n)) *
+                              sizeof(float2));
   }
   ctx->red = (double*)A((size_t)residual_blocks(N) * 8 * sizeof(double));
   ctx->ticket = (unsigned int*)A(sizeof(unsigned int));

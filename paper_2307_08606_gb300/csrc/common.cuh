@@ -137,6 +137,8 @@ struct SpdSet {
   int q;
   float2* part;      // sym_part_pairs(n) scratch
   int tile0;         // set by launch_spd_apply
+  double* outd;      // optional: out written as hi + lo in FP64, element i at outd[i * ldd]
+  int ldd;
 };
 // out = F u for every set (or, with update, the primal x-update epilogue).
 // *err is set to 1 if a tile copy did not complete within the wait limit.
@@ -255,7 +257,7 @@ int launch_multi_apply_cols(const float2* const* F, const float2* const* A, cons
 struct DdScratch {
   float* U;          // jobs x n x 16
   void** dptrs;      // 2 x jobs device pointers
-  float2* part;      // jobs x multi_apply_part_pairs(n)
+  float2* part;      // jobs x multi_apply_part_pairs(n); also 64 x sym_part_pairs(n) for single-column applies
 };
 int run_downdate_pairs(const DowndateJob* jobs, int njobs, int KM, double mu, const DdScratch& scr, int* d_status,
                        int* err, cudaStream_t st);

@@ -328,6 +328,7 @@ inverse_kernel(const __grid_constant__ JobBlock jobs) {
 
 // ---------------------------------------------------------------- downdate
 constexpr int DM = kDowndateMax;          // 32
+constexpr int kFewColumns = 6;            // single-column applies up to this many columns per job
 constexpr int kDdWarps = 8;
 constexpr int kDdChunk = 512;             // rows of U staged per shared-memory pass
 using DdBlock = SetBlock<DowndateJob>;
@@ -663,10 +664,36 @@ int run_downdate_pairs(const DowndateJob* jobs, int njobs, int KM, double mu, co
     // columns e..31 of P must be zero for the kernels below
     SADMM_CUDA_TRY(cudaMemsetAsync(jobs[i].P, 0, (size_t)jobs[i].n * DM * sizeof(double), st));
   }
-  // P = W U, sixteen columns of U (removed pixels' columns of B) per packed-tile pass
-  for (int c0 = 0; c0 < e_max; c0 += 16)
-    SADMM_TRY(launch_multi_apply_cols(F.data(), A.data(), E.data(), e.data(), P.data(), njobs, n_max, c0, scr.U,
-                                      scr.dptrs, scr.part, err, st));
+  // P = W U.  A few columns: one single-column symmetric apply each (its
+  // arithmetic is one product per element); more: sixteen columns per
+  // packed-tile pass (one read of W for all of them).
+  if (e_max <= kFewColumns) {
+    std::vector<int> Eh((size_t)njobs * DM);
+    for (int i = 0; i < njobs; ++i)
+      SADMM_CUDA_TRY(cudaMemcpyAsync(Eh.data() + (size_t)i * DM, jobs[i].E, jobs[i].e * sizeof(int),
+                                     cudaMemcpyDeviceToHost, st));
+    SADMM_CUDA_TRY(cudaStreamSynchronize(st));
+    std::vector<SpdSet> sets;
+    const size_t stride = sym_part_pairs(n_max);
+    for (int i = 0; i < njobs; ++i)
+      for (int c = 0; c < jobs[i].e; ++c) {
+        SpdSet s{};
+        s.P = jobs[i].Fsrc;
+        s.n = jobs[i].n;
+        s.u = reinterpret_cast<const float*>(jobs[i].A) + (size_t)Eh[(size_t)i * DM + c] * 2 * KM;
+        s.part = scr.part + (size_t)(sets.size() % kMaxSets) * stride;
+        s.outd = jobs[i].P + c;
+        s.ldd = DM;
+        sets.push_back(s);
+      }
+    SolverView sv{};
+    for (size_t b = 0; b < sets.size(); b += kMaxSets)
+      SADMM_TRY(launch_spd_apply(sets.data() + b, (int)std::min<size_t>(kMaxSets, sets.size() - b), false, sv, err, st));
+  } else {
+    for (int c0 = 0; c0 < e_max; c0 += 16)
+      SADMM_TRY(launch_multi_apply_cols(F.data(), A.data(), E.data(), e.data(), P.data(), njobs, n_max, c0, scr.U,
+                                        scr.dptrs, scr.part, err, st));
+  }
   dd_s_kernel<<<dim3(div_up(n_max, 256), njobs), DM * DM, 0, st>>>(blk, KM);
   SADMM_LAUNCH_CHECK();
   dd_chol_kernel<<<njobs, DM * DM, 0, st>>>(blk, mu, d_status);

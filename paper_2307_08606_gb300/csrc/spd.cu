@@ -143,6 +143,8 @@ spd_reduce_kernel(const __grid_constant__ SetBlock<SpdSet> sets, bool update, co
     const float xn = fmaf(sv.mu, g, v);
     sv.ring[((size_t)sv.slot * sv.Q + ss.q) * sv.N + pix] = xn - xo;
     sv.x[xi] = xn;
+  } else if (ss.outd) {
+    ss.outd[(size_t)i * ss.ldd] = (double)acc.hi + (double)acc.lo;
   } else {
     ss.out[i] = g;
   }
