@@ -453,7 +453,7 @@ struct BatchCtx {
   sadmm_t single = nullptr;        // owns the operators and the FP64 factors
   std::vector<void*> owned;
   float *X = nullptr, *dX = nullptr, *xbar = nullptr, *zbar = nullptr, *sd = nullptr, *lor = nullptr;
-  float2 **dA = nullptr, **dY = nullptr, **dR = nullptr, **dF = nullptr;
+  float2 **dY = nullptr, **dR = nullptr, **dF = nullptr;
   std::vector<float2*> fpair;      // packed symmetric factor pairs, one per sensor
   std::vector<const float2*> hA, hR, hU;   // host copies of the per-sensor device pointers
   float2* bpart = nullptr;         // per-tile partial sums of the factor apply
@@ -603,7 +603,7 @@ int sadmm_batch_create(int Q, int M, int K, int N, int S, double rho, const doub
   b->X = (float*)A(QNS * 4); b->dX = (float*)A(QNS * 4);
   b->xbar = (float*)A(NS * 4); b->zbar = (float*)A(NS * 4); b->sd = (float*)A(NS * 4);
   b->lor = (float*)A(kBS * 4);
-  b->dA = (float2**)A(Q * sizeof(void*)); b->dY = (float2**)A(Q * sizeof(void*));
+  b->dY = (float2**)A(Q * sizeof(void*));
   b->dR = (float2**)A(Q * sizeof(void*)); b->dF = (float2**)A(Q * sizeof(void*));
   b->dU = (float**)A(Q * sizeof(void*)); b->dG = (float**)A(Q * sizeof(void*));
   b->chunks = tc_forward_splits(Q, N, b->KM);
@@ -697,7 +697,6 @@ int sadmm_batch_solve(sadmm_batch_t b, const float* y, float* x_out, int iters, 
       b->bpart = (float2*)b->dalloc((size_t)b->Q * b->bpart_stride * sizeof(float2));
       if (!b->bpart) { set_error("sadmm_batch_solve: scratch allocation failed"); return SADMM_ENOMEM; }
     }
-    SADMM_CUDA_TRY(cudaMemcpyAsync(b->dA, Ap.data(), b->Q * sizeof(void*), cudaMemcpyHostToDevice, b->st));
     SADMM_CUDA_TRY(cudaMemcpyAsync(b->dF, Fp.data(), b->Q * sizeof(void*), cudaMemcpyHostToDevice, b->st));
     SADMM_CUDA_TRY(cudaStreamSynchronize(b->st));
     if (b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; }

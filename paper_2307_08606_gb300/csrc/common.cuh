@@ -144,8 +144,6 @@ struct SpdSet {
 // *err is set to 1 if a tile copy did not complete within the wait limit.
 int launch_spd_apply(const SpdSet* sets, int nsets, bool update, const SolverView& sv, int* err,
                      cudaStream_t st);
-// (hi, lo) = (fl32(x), fl32(x - hi)) for n doubles.
-int launch_split_f64(const double* in, float2* out, size_t n, cudaStream_t st);
 
 int launch_residuals(const SolverView& sv, const sadmm_criterion& c, double* partials,
                      unsigned int* ticket, IterScalars* out, int k_after, cudaStream_t st);

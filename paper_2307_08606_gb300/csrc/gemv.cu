@@ -190,14 +190,6 @@ adjoint_kernel(const __grid_constant__ SetBlock<AdjointSet> sets, int KM, bool u
   }
 }
 
-__global__ void split_f64_kernel(const double* __restrict__ in, float2* __restrict__ out, size_t n) {
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    const double x = in[i];
-    const float h = (float)x;
-    out[i] = make_float2(h, (float)(x - (double)h));
-  }
-}
-
 }  // namespace
 
 size_t forward_partial_bytes(int nsets, int KM, int max_cols) {
@@ -244,13 +236,6 @@ int launch_adjoint(const AdjointSet* sets, int nsets, int KM, bool update, const
   }
   dim3 grid(div_up(max_cols, kAdjWarps * kAdjColsPerWarp), nsets);
   adjoint_kernel<<<grid, kAdjWarps * 32, smem, st>>>(blk, KM, update, sv);
-  SADMM_LAUNCH_CHECK();
-  return SADMM_OK;
-}
-
-int launch_split_f64(const double* in, float2* out, size_t n, cudaStream_t st) {
-  if (n == 0) return SADMM_OK;
-  split_f64_kernel<<<(int)std::min<size_t>(div_up((long long)n, 256), 152 * 32), 256, 0, st>>>(in, out, n);
   SADMM_LAUNCH_CHECK();
   return SADMM_OK;
 }

@@ -314,3 +314,25 @@ def test_batched_removal_policy(B):
         for q in range(sc.geom.Q):
             assert np.array_equal(s.active(q), ref.state.J[q])
     s.close()
+
+
+def test_full_size_first_iteration_matches_oracle(B):
+    """Paper-scale workload at its full size (Q=8, KM=2048, N=128x128), in the
+    benchmark's configuration: the first iteration from zero for sensors 0 and
+    7, x_q = (rho I + mu B_q^T B_q)^{-1} mu B_q^T y_q, against the FP64 oracle's
+    x-update of those sensors (the oracle computes them one sensor at a time)."""
+    sc = scenegen.build_scene("paper_scale", seed=0)
+    lam = 0.05 * scenegen.lambda_max(sc.A, sc.y)
+    g = sc.geom
+    dev = torch.device("cuda:0")
+    s = B.Solver(g.Q, g.M, g.K, g.N, 1.0, lam, elim=0)
+    for q in range(g.Q):
+        s.set_operator(q, torch.from_numpy(sc.A[q]).to(dev))
+    s.solve([torch.from_numpy(v).to(dev) for v in sc.y], 1)
+    for q in (0, g.Q - 1):
+        Bq = oracle.real_form(sc.A[q])
+        solver = oracle.RidgeSolver(Bq, 1.0, 1.0)
+        ref = solver.solve(1.0 * (Bq.T @ oracle.real_vec(sc.y[q])))
+        got = s.xq(q).astype(np.float64)
+        assert _rel(got, ref) <= TOL, q
+    s.close()
