@@ -54,6 +54,8 @@ def parse():
                     help="skip the learned-step cost measurement (elim 2 on the bench scene)")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the 16-scene batched measurement (Q=8, KM=2048, N=96x96)")
+    ap.add_argument("--group-geoms", type=int, default=32,
+                    help="geometries in the mixed-geometry batch group (16 scenes each); 0 skips it")
     return ap.parse_args()
 
 
@@ -71,10 +73,11 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def source_sha():
+def source_sha(files):
+    """Hash of the named kernel source files (under the package's csrc/)."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2307_08606_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
+    for f in sorted(files):
         with open(os.path.join(d, f), "rb") as fh:
             h.update(f.encode())
             h.update(fh.read())
@@ -83,13 +86,13 @@ def source_sha():
 
 def traffic_for(kernel):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel sources."""
+    on the current sources of that kernel (the files each entry names)."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(p) as f:
-            t = json.load(f)
-        if t.get("source_sha") == source_sha() and kernel in t.get("kernels", {}):
-            return float(t["kernels"][kernel]["dram_bytes_per_launch"])
+            e = json.load(f)["kernels"][kernel]
+        if e["source_sha"] == source_sha(e["files"]):
+            return float(e["dram_bytes_per_launch"])
     except Exception:
         pass
     return None
@@ -229,6 +232,94 @@ def batched_measure(args, dev, stream, rank):
             "single_scene_iters_per_s_same_geometry": single_its,
             "speedup_vs_single_scene": scene_its / single_its,
             "gpu_launches": int(launches)}
+
+
+def group_measure(args, dev, stream, rank):
+    """Mixed-geometry batched workload: args.group_geoms geometries drawn by seed
+    from the 48 combinations of Q in {2,4,6,8}, M in {4,8}, K in {128,256},
+    N in {48^2, 64^2, 96^2}, 16 scenes each, every batch's work decomposition
+    chosen by the autotuner, all batches iterated together as one batch group
+    (one graph launch per iteration).  Reports scene-iterations/s, the
+    operator bytes per iteration, and the same batches solved one after
+    another for comparison."""
+    import torch
+    import scenegen
+    from scenegen import radar
+    from paper_2307_08606_gb300 import binding
+    from concurrent.futures import ThreadPoolExecutor
+    t0 = time.perf_counter()
+    geoms = scenegen.batch_geometries(rank, args.group_geoms)
+    batches, ys = [], []
+    with ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 1)) as pool:
+        ops = [pool.map(lambda gq: radar.operator(*gq), [(g, q) for q in range(g.Q)]) for g in geoms]
+        ops = [list(o) for o in ops]
+    for gi, g in enumerate(geoms):
+        A = ops[gi]
+        Y, lams = scenegen.batch_scenes(g, A, seed=100 * rank + gi)
+        bs = binding.BatchSolver(g.Q, g.M, g.K, g.N, 1.0, lams, stream=stream.cuda_stream)
+        for q in range(g.Q):
+            bs.set_operator(q, A[q])
+        batches.append(bs)
+        ys.append(torch.from_numpy(Y).to(dev))
+    gen_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    tunings = [b.tune(reps=3) for b in batches]
+    torch.cuda.synchronize()
+    tune_s = time.perf_counter() - t0
+    grp = binding.BatchGroup(batches, stream=stream.cuda_stream)
+    outs = [torch.empty((16, g.N), dtype=torch.float32, device=dev) for g in geoms]
+    iters, reps = 50, 3
+    grp.solve(ys, iters, outs)                       # graph capture, factors
+    torch.cuda.synchronize()
+    n0 = binding.launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        grp.solve(ys, iters, outs)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    launches = binding.launch_count() - n0
+    for b, y, o in zip(batches, ys, outs):           # each batch's own graph, for the comparison
+        b.solve(y, iters, out=o)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for b, y, o in zip(batches, ys, outs):
+        b.solve(y, iters, out=o)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_seq = e0.elapsed_time(e1)
+    grp.close()
+    for b in batches:
+        b.close()
+    scenes = 16 * len(geoms)
+    op_bytes = sum(2.0 * g.Q * g.KM * g.N * 8.0 for g in geoms)
+    ms_it = ms / (iters * reps)
+    return {"metric": "mixed-geometry batched scene-iterations/s", "value": scenes * iters * reps / (ms / 1e3),
+            "unit": "scene-iter/s",
+            "workload": f"{len(geoms)} geometries drawn by seed from Q{{2,4,6,8}} x M{{4,8}} x K{{128,256}} x "
+                        f"N{{48^2,64^2,96^2}}, 16 scenes each ({scenes} scenes); plain SADMM, {iters} iterations "
+                        "per solve, one batch group",
+            "ms_per_iteration": ms_it, "operator_bytes_per_iteration": op_bytes,
+            "operator_GBps_effective": op_bytes / (ms_it / 1e3) / 1e9,
+            "sequential_batches_scene_iters_per_s": scenes * iters / (ms_seq / 1e3),
+            "group_speedup_vs_sequential": (ms_seq / iters) / ms_it,
+            "tuned_splits": [[t["forward_splits"], t["adjoint_splits"]] for t in tunings],
+            "tuning_gain_fraction": _tuning_gain(tunings),
+            "setup_s": round(gen_s, 1), "tune_s": round(tune_s, 2),
+            "gpu_launches": int(launches)}
+
+
+def _tuning_gain(tunings):
+    """Mean over batches of (time at the default splits - time at the chosen
+    splits) / time at the default splits, forward and adjoint launches summed."""
+    gains = []
+    for t in tunings:
+        f, a = t["forward"], t["adjoint"]
+        base = f[t["forward_default"]] + a[t["adjoint_default"]]
+        best = f[t["forward_splits"]] + a[t["adjoint_splits"]]
+        gains.append((base - best) / base)
+    return float(np.mean(gains)) if gains else None
 
 
 def forms_measure(sc, lam, dev, stream, iters=400):
@@ -515,6 +606,8 @@ def main():
     }
     if not args.no_batched:
         line["batched"] = batched_measure(args, dev, stream, rank)
+    if args.group_geoms > 0:
+        line["group"] = group_measure(args, dev, stream, rank)
     if not args.no_learned:
         line["learned"] = learned_measure(sc, lam, dev, stream)
     if not args.no_forms:

@@ -244,6 +244,42 @@ int sadmm_batch_solve(sadmm_batch_t b, const float* y, float* x_out, int iters, 
 int sadmm_batch_get_xq(sadmm_batch_t b, int scene, int q, float* out);
 void sadmm_batch_destroy(sadmm_batch_t b);
 
+/* Autotuner for the batched products' work decomposition (an extension; the
+ * paper has no batched form).  The tensor-core GEMM tiles are fixed (128
+ * operator rows or pixels x 16 scenes x 32-row K slabs); what is tuned is
+ * how each GEMM's K range is split across persistent CTAs: the forward
+ * product's pixel splits and the adjoint's real-row splits.  Each candidate
+ * (up to eight per product, from a quarter to four times the default) is
+ * launched `reps` times on the batch's stream with CUDA events around the
+ * launches; the fastest is kept for every later solve and the captured graph
+ * is rebuilt.  The operators must be set; the batch's state is reset by the
+ * next solve.  out (may be NULL) receives the candidates, their mean times
+ * per launch and the choice.  Errors: SADMM_EINVAL for reps < 1. */
+typedef struct {
+  int n_fwd, n_adj;              /* candidates tried */
+  int fwd_splits[8], adj_splits[8];
+  double fwd_ms[8], adj_ms[8];   /* mean time per launch (GEMM + its reduction) */
+  int fwd_choice, adj_choice;    /* the splits kept */
+  int fwd_default, adj_default;  /* the splits a batch starts with (always among the candidates) */
+} sadmm_batch_tuning;
+int sadmm_batch_tune(sadmm_batch_t b, int reps, sadmm_batch_tuning* out);
+
+/* A group of batches with different geometries (Q, M, K, N may all differ),
+ * iterated together: one CUDA graph holds one iteration of every batch, each
+ * batch on its own branch, so the GPU runs the batches' kernels side by side
+ * and one graph launch advances every scene of every geometry by one
+ * iteration.  The caller keeps ownership of the batches and must not destroy
+ * one while the group exists; changing a batch (operator, stream, tuning)
+ * makes the group rebuild its graph at the next solve.  At most 64 batches. */
+typedef struct sadmm_batch_group_ctx* sadmm_batch_group_t;
+int sadmm_batch_group_create(const sadmm_batch_t* batches, int n, sadmm_batch_group_t* out);
+int sadmm_batch_group_set_stream(sadmm_batch_group_t g, void* stream);
+/* y[i], x_out[i] and st[i] as for sadmm_batch_solve of batch i (x_out and st
+ * may be NULL, and so may any x_out[i]); every batch runs `iters` iterations. */
+int sadmm_batch_group_solve(sadmm_batch_group_t g, const float* const* y, float* const* x_out, int iters,
+                            sadmm_stats* st);
+void sadmm_batch_group_destroy(sadmm_batch_group_t g);
+
 /* ------------------------------------------------------------------------
  * Learned elimination proposal (an extension; the paper has no counterpart):
  * a CNN over the H x W pixel grid with five 3x3 convolutions (6 -> 32, then
@@ -291,8 +327,8 @@ int sadmm_forward(const float* A, int KM, int N, const int* idx, int nidx, const
  * The paper has no counterpart: this is a library-interface variant.
  * It allocates nothing: the partial sums go to one fixed 8 MiB device array
  * that every GPU loading this library holds until the process exits.  Sizes
- * whose partial sums (chunks x KM x 8 bytes) exceed 8 MiB are rejected with
- * SADMM_EINVAL and a message naming the sizes.  The first call on each device
+ * whose partial sums (chunks x KM x 16 bytes: double-float pairs) exceed
+ * 8 MiB are rejected with SADMM_EINVAL and a message naming the sizes.  The first call on each device
  * looks up the array's device address (with that device current); make that
  * first call before any stream capture begins.  All calls on a device share
  * the array and it keeps the last call's contents; every entry a call reads is

@@ -46,6 +46,20 @@ class IterRecord(C.Structure):
                 ("eps_dual", C.c_double), ("relchange", C.c_double)]
 
 
+class BatchTuning(C.Structure):
+    _fields_ = [("n_fwd", C.c_int), ("n_adj", C.c_int),
+                ("fwd_splits", C.c_int * 8), ("adj_splits", C.c_int * 8),
+                ("fwd_ms", C.c_double * 8), ("adj_ms", C.c_double * 8),
+                ("fwd_choice", C.c_int), ("adj_choice", C.c_int),
+                ("fwd_default", C.c_int), ("adj_default", C.c_int)]
+
+    def as_dict(self):
+        return {"forward": {int(self.fwd_splits[i]): float(self.fwd_ms[i]) for i in range(self.n_fwd)},
+                "adjoint": {int(self.adj_splits[i]): float(self.adj_ms[i]) for i in range(self.n_adj)},
+                "forward_splits": int(self.fwd_choice), "adjoint_splits": int(self.adj_choice),
+                "forward_default": int(self.fwd_default), "adjoint_default": int(self.adj_default)}
+
+
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
 
@@ -89,6 +103,11 @@ _SIGS = {
     "sadmm_batch_solve": (C.c_int, [_P, _P, _P, C.c_int, C.POINTER(Stats)]),
     "sadmm_batch_get_xq": (C.c_int, [_P, C.c_int, C.c_int, _P]),
     "sadmm_batch_destroy": (None, [_P]),
+    "sadmm_batch_tune": (C.c_int, [_P, C.c_int, C.POINTER(BatchTuning)]),
+    "sadmm_batch_group_create": (C.c_int, [C.POINTER(_P), C.c_int, C.POINTER(_P)]),
+    "sadmm_batch_group_set_stream": (C.c_int, [_P, _P]),
+    "sadmm_batch_group_solve": (C.c_int, [_P, C.POINTER(_P), C.POINTER(_P), C.c_int, C.POINTER(Stats)]),
+    "sadmm_batch_group_destroy": (None, [_P]),
     "sadmm_cnn_create": (C.c_int, [C.c_int, C.c_int, C.c_int, C.POINTER(_P)]),
     "sadmm_cnn_num_params": (C.c_int, []),
     "sadmm_cnn_set_params": (C.c_int, [_P, _P]),
@@ -346,6 +365,51 @@ class BatchSolver:
         out = np.empty(self.N, dtype=np.float32)
         check(self.lib.sadmm_batch_get_xq(self.h, scene, q, _ptr(out)))
         return out
+
+    def tune(self, reps=5):
+        """Time the candidate work splits of the two tensor-core products and keep
+        the fastest (sadmm_batch_tune); returns the candidates' times and the choice."""
+        t = BatchTuning()
+        check(self.lib.sadmm_batch_tune(self.h, int(reps), C.byref(t)))
+        return t.as_dict()
+
+
+class BatchGroup:
+    """Batches of different geometries iterated together, one graph branch per
+    batch (sadmm_batch_group_*).  The batches stay owned by the caller."""
+
+    def __init__(self, batches, stream=None):
+        self.lib = load()
+        self.batches = list(batches)
+        hs = (_P * len(self.batches))(*[b.h for b in self.batches])
+        h = C.c_void_p()
+        check(self.lib.sadmm_batch_group_create(hs, len(self.batches), C.byref(h)))
+        self.h = h
+        if stream is not None:
+            check(self.lib.sadmm_batch_group_set_stream(self.h, C.c_void_p(stream)))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.sadmm_batch_group_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def solve(self, ys, iters, outs=None):
+        """ys: one (S, Q_i, KM_i) complex64 array per batch; returns ([x_G (S, N_i)], [stats])."""
+        n = len(self.batches)
+        ys = [_as_c64(y) for y in ys]
+        if outs is None:
+            outs = [np.empty((b.S, b.N), dtype=np.float32) for b in self.batches]
+        yp = (_P * n)(*[_ptr(y) for y in ys])
+        xp = (_P * n)(*[_ptr(o) for o in outs])
+        st = (Stats * n)()
+        check(self.lib.sadmm_batch_group_solve(self.h, yp, xp, int(iters), st))
+        return outs, [st[i].as_dict() for i in range(n)]
 
 
 class CNN:

@@ -456,6 +456,7 @@ struct BatchCtx {
   float2 **dY = nullptr, **dR = nullptr, **dF = nullptr;
   std::vector<float2*> fpair;      // packed symmetric factor pairs, one per sensor
   std::vector<const float2*> hA, hR, hU;   // host copies of the per-sensor device pointers
+  std::vector<void*> hY, hG;
   float2* bpart = nullptr;         // per-tile partial sums of the factor apply
   size_t bpart_stride = 0;
   int* berr = nullptr;             // set if a factor tile copy timed out
@@ -467,11 +468,17 @@ struct BatchCtx {
   float* xout = nullptr;
   int chunks = 1, n = 0, ld = 0, woodbury = 1;
   int asplits = 1;                 // row splits of the adjoint GEMM
+  int chunks0 = 1, asplits0 = 1;   // the default splits (the tuner's starting points)
+  int chunks_cap = 1, asplits_cap = 1;     // the largest splits the scratch holds
   float* gpart = nullptr;          // Q x asplits x N x 16 partial adjoint sums
   cudaGraphExec_t graph = nullptr;
   bool graph_valid = false;
+  bool ready = false;              // factors exported and packed for the current operators
+  unsigned epoch = 0;              // changes whenever the work one iteration launches changes
   int kernels_per_iter = 0;
   int k = 0;
+  IterScalars h_scal[kBS];         // last iteration's per-scene scalars (host copy)
+  int h_err = 0;
 
   void* dalloc(size_t bytes) {
     void* p = nullptr;
@@ -481,6 +488,11 @@ struct BatchCtx {
   }
   BatchDev view() const {
     return BatchDev{Q, N, KM, S, (float)mu, (float)rho, lor, X, dX, xbar, zbar, sd};
+  }
+  void invalidate() {
+    ready = false;
+    graph_valid = false;
+    ++epoch;
   }
 };
 
@@ -506,23 +518,32 @@ int launch_bspd(BatchCtx& c, const float* const* u, float* const* out, int mode,
   return SADMM_OK;
 }
 
-int batch_launch_iteration(BatchCtx& c) {
-  const BatchDev bv = c.view();
-  SADMM_TRY(launch_tc_forward(c.hA.data(), bv.X, bv.xbar, bv.zbar, bv.sd, c.partial, c.Q, c.N, c.KM, c.chunks, c.berr,
+int launch_forward_products(BatchCtx& c, int chunks, const BatchDev& bv) {
+  SADMM_TRY(launch_tc_forward(c.hA.data(), bv.X, bv.xbar, bv.zbar, bv.sd, c.partial, c.Q, c.N, c.KM, chunks, c.berr,
                               c.st));
   bfwd_reduce_kernel<<<dim3(div_up((long long)c.KM * kBS, 256), c.Q), 256, 0, c.st>>>(c.partial, c.dY, c.dR, c.KM,
-                                                                                     c.chunks);
+                                                                                     chunks);
   SADMM_LAUNCH_CHECK();
-  const dim3 gr(div_up((long long)c.N * kBS, 256), c.Q);
+  return SADMM_OK;
+}
+
+// mode 0: x-update epilogue from W R (Woodbury form); mode 1: G = Re(A^H R) only
+int launch_adjoint_products(BatchCtx& c, int splits, const float2* const* in, int mode, const BatchDev& bv) {
+  SADMM_TRY(launch_tc_adjoint(c.hA.data(), in, c.gpart, c.Q, c.N, c.KM, splits, c.berr, c.st));
+  badj_reduce_kernel<<<dim3(div_up((long long)c.N * kBS, 256), c.Q), 256, 0, c.st>>>(c.gpart, splits, c.dG, mode,
+                                                                                    bv);
+  SADMM_LAUNCH_CHECK();
+  return SADMM_OK;
+}
+
+int batch_launch_iteration(BatchCtx& c) {
+  const BatchDev bv = c.view();
+  SADMM_TRY(launch_forward_products(c, c.chunks, bv));
   if (c.woodbury) {
     SADMM_TRY(launch_bspd(c, (const float* const*)c.dR, c.dU, 0, bv));
-    SADMM_TRY(launch_tc_adjoint(c.hA.data(), c.hU.data(), c.gpart, c.Q, c.N, c.KM, c.asplits, c.berr, c.st));
-    badj_reduce_kernel<<<gr, 256, 0, c.st>>>(c.gpart, c.asplits, c.dG, 0, bv);
-    SADMM_LAUNCH_CHECK();
+    SADMM_TRY(launch_adjoint_products(c, c.asplits, c.hU.data(), 0, bv));
   } else {
-    SADMM_TRY(launch_tc_adjoint(c.hA.data(), c.hR.data(), c.gpart, c.Q, c.N, c.KM, c.asplits, c.berr, c.st));
-    badj_reduce_kernel<<<gr, 256, 0, c.st>>>(c.gpart, c.asplits, c.dG, 1, bv);
-    SADMM_LAUNCH_CHECK();
+    SADMM_TRY(launch_adjoint_products(c, c.asplits, c.hR.data(), 1, bv));
     SADMM_TRY(launch_bspd(c, (const float* const*)c.dG, nullptr, 1, bv));
   }
   const int nblk = div_up(c.N, kBrThreads / kBS);
@@ -531,6 +552,127 @@ int batch_launch_iteration(BatchCtx& c) {
   bresid_final_kernel<<<kBS, kBrSums * 32, 0, c.st>>>(c.rpart, nblk, bv, c.crit.eps_abs, c.crit.eps_rel, 0, c.scal);
   SADMM_LAUNCH_CHECK();
   return SADMM_OK;
+}
+
+// Factors for the current operators (FP64, from the single-scene context),
+// packed as double-float pairs; the apply's scratch.  Synchronises b.st.
+int batch_setup(BatchCtx& b) {
+  SADMM_TRY(sadmm_prepare(b.single));
+  if (b.ready) return SADMM_OK;
+  std::vector<void*> Fp(b.Q);
+  if (b.fpair.empty()) b.fpair.assign(b.Q, nullptr);
+  b.hA.assign(b.Q, nullptr);
+  for (int q = 0; q < b.Q; ++q) {
+    const float2* A = nullptr;
+    const double* F = nullptr;
+    SADMM_TRY(single_export(b.single, q, &A, &F, &b.n, &b.ld, &b.woodbury));
+    if (!b.fpair[q]) {
+      b.fpair[q] = (float2*)b.dalloc(sym_packed_pairs(b.n) * sizeof(float2));
+      if (!b.fpair[q]) { set_error("batched form: factor allocation failed"); return SADMM_ENOMEM; }
+    }
+    SADMM_TRY(launch_pack_sym(F, b.ld, b.n, b.fpair[q], b.st));
+    Fp[q] = (void*)b.fpair[q];
+    b.hA[q] = A;
+  }
+  if (!b.bpart) {
+    const size_t nt = div_up(b.n, kT);
+    b.bpart_stride = nt * (nt + 1) / 2 * kBtPart;
+    b.bpart = (float2*)b.dalloc((size_t)b.Q * b.bpart_stride * sizeof(float2));
+    if (!b.bpart) { set_error("batched form: scratch allocation failed"); return SADMM_ENOMEM; }
+  }
+  SADMM_CUDA_TRY(cudaMemcpyAsync(b.dF, Fp.data(), b.Q * sizeof(void*), cudaMemcpyHostToDevice, b.st));
+  SADMM_CUDA_TRY(cudaStreamSynchronize(b.st));
+  b.ready = true;
+  return SADMM_OK;
+}
+
+// One iteration captured as a graph, replayed once per iteration.
+int batch_capture(BatchCtx& b) {
+  if (b.graph) { cudaGraphExecDestroy(b.graph); b.graph = nullptr; }
+  b.graph_valid = false;
+  cudaStream_t cap;
+  SADMM_CUDA_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+  cudaStream_t saved = b.st;
+  b.st = cap;
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+  const long long n0 = sadmm_launch_count();
+  int rc = e == cudaSuccess ? batch_launch_iteration(b) : SADMM_ECUDA;
+  b.kernels_per_iter = (int)(sadmm_launch_count() - n0);
+  cudaError_t e2 = e == cudaSuccess ? cudaStreamEndCapture(cap, &g) : cudaSuccess;
+  b.st = saved;
+  cudaStreamDestroy(cap);
+  if (rc != SADMM_OK) { if (g) cudaGraphDestroy(g); return rc; }
+  SADMM_CUDA_TRY(e);
+  SADMM_CUDA_TRY(e2);
+  e = cudaGraphInstantiate(&b.graph, g, 0);
+  cudaGraphDestroy(g);
+  SADMM_CUDA_TRY(e);
+  b.graph_valid = true;
+  return SADMM_OK;
+}
+
+// Zero state, measurements y (S x Q x KM complex, host or device) into Y'.
+int batch_reset(BatchCtx& b, const float* y, cudaStream_t st) {
+  const size_t QNS = (size_t)b.Q * b.N * kBS, NS = (size_t)b.N * kBS;
+  SADMM_CUDA_TRY(cudaMemsetAsync(b.X, 0, QNS * 4, st));
+  SADMM_CUDA_TRY(cudaMemsetAsync(b.dX, 0, QNS * 4, st));
+  SADMM_CUDA_TRY(cudaMemsetAsync(b.xbar, 0, NS * 4, st));
+  SADMM_CUDA_TRY(cudaMemsetAsync(b.zbar, 0, NS * 4, st));
+  SADMM_CUDA_TRY(cudaMemsetAsync(b.sd, 0, NS * 4, st));
+  SADMM_CUDA_TRY(cudaMemcpyAsync(b.ybuf, y, (size_t)kBS * b.Q * b.KM * sizeof(float2), cudaMemcpyDefault, st));
+  bload_y_kernel<<<dim3(div_up((long long)b.KM * kBS, 256), b.Q), 256, 0, st>>>(b.ybuf, b.dY, b.Q, b.KM);
+  SADMM_LAUNCH_CHECK();
+  return SADMM_OK;
+}
+
+// x_G of every scene to x_out (may be NULL); the last iteration's scalars and
+// the error flag to the host copies (read after the stream is synchronised).
+int batch_collect(BatchCtx& b, float* x_out, cudaStream_t st) {
+  const size_t NS = (size_t)b.N * kBS;
+  if (x_out) {
+    bscale_kernel<<<div_up(NS, 256), 256, 0, st>>>(b.zbar, (float)b.Q, b.xout, b.N);
+    SADMM_LAUNCH_CHECK();
+    SADMM_CUDA_TRY(cudaMemcpyAsync(x_out, b.xout, NS * 4, cudaMemcpyDefault, st));
+  }
+  SADMM_CUDA_TRY(cudaMemcpyAsync(b.h_scal, b.scal, sizeof b.h_scal, cudaMemcpyDeviceToHost, st));
+  SADMM_CUDA_TRY(cudaMemcpyAsync(&b.h_err, b.berr, sizeof(int), cudaMemcpyDeviceToHost, st));
+  return SADMM_OK;
+}
+
+int batch_finish(BatchCtx& b, int iters, sadmm_stats* st, double ms) {
+  b.k = iters;
+  if (b.h_err) {
+    SADMM_CUDA_TRY(cudaMemset(b.berr, 0, sizeof(int)));
+    b.h_err = 0;
+    set_error("batched form: a tile copy or tensor-core pipeline wait did not complete within its limit");
+    return SADMM_ETIMEOUT;
+  }
+  for (int s = 0; s < kBS; ++s)
+    if (iters > 0 && b.h_scal[s].nonfinite) { set_error("non-finite value in scene %d", s); return SADMM_ENONFINITE; }
+  if (st) {
+    const IterScalars& h = b.h_scal[0];
+    memset(st, 0, sizeof *st);
+    st->iters = iters;
+    st->active_total = b.Q * b.N * kBS;
+    st->r_pri = h.r_pri; st->eps_pri = h.eps_pri; st->d = h.d; st->eps_dual = h.eps_dual;
+    st->relchange = h.relchange;
+    st->ms_total = ms;
+    st->bytes_iter = (double)iters * ((double)b.Q * b.KM * b.N * 16.0 + (double)b.Q * sym_packed_pairs(b.n) * 8.0);
+  }
+  return SADMM_OK;
+}
+
+// Up to eight split counts from a quarter to four times the default, in [1, cap].
+std::vector<int> split_candidates(int base, int cap) {
+  std::vector<int> v;
+  const int f[8] = {base / 4, base / 2, (3 * base) / 4, base, (3 * base) / 2, 2 * base, 3 * base, 4 * base};
+  for (int x : f) {
+    x = std::max(1, std::min(x, cap));
+    if (std::find(v.begin(), v.end(), x) == v.end()) v.push_back(x);
+  }
+  std::sort(v.begin(), v.end());
+  return v;
 }
 
 }  // namespace
@@ -575,6 +717,16 @@ int launch_multi_apply_cols(const float2* const* F, const float2* const* A, cons
 
 struct sadmm_batch_ctx : sadmm::BatchCtx {};
 
+struct sadmm_batch_group_ctx {
+  std::vector<sadmm::BatchCtx*> b;
+  std::vector<unsigned> epochs;
+  std::vector<cudaStream_t> side;  // one capture branch per batch
+  std::vector<cudaEvent_t> ev;     // fork, then one join per batch
+  cudaStream_t st = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  int kernels_per_iter = 0;
+};
+
 extern "C" {
 
 int sadmm_batch_create(int Q, int M, int K, int N, int S, double rho, const double* lambda,
@@ -606,21 +758,25 @@ int sadmm_batch_create(int Q, int M, int K, int N, int S, double rho, const doub
   b->dY = (float2**)A(Q * sizeof(void*));
   b->dR = (float2**)A(Q * sizeof(void*)); b->dF = (float2**)A(Q * sizeof(void*));
   b->dU = (float**)A(Q * sizeof(void*)); b->dG = (float**)A(Q * sizeof(void*));
-  b->chunks = tc_forward_splits(Q, N, b->KM);
-  b->asplits = tc_adjoint_splits(Q, N, b->KM);
-  b->gpart = (float*)A((size_t)Q * b->asplits * NS * sizeof(float));
-  b->partial = (float2*)A((size_t)Q * b->chunks * KS * sizeof(float2));
+  b->chunks = b->chunks0 = tc_forward_splits(Q, N, b->KM);
+  b->asplits = b->asplits0 = tc_adjoint_splits(Q, N, b->KM);
+  b->chunks_cap = std::min(4 * b->chunks0, tc_forward_max_splits(N));
+  b->asplits_cap = std::min(4 * b->asplits0, tc_adjoint_max_splits(b->KM));
+  b->gpart = (float*)A((size_t)Q * b->asplits_cap * NS * sizeof(float));
+  b->partial = (float2*)A((size_t)Q * b->chunks_cap * KS * sizeof(float2));
   b->rpart = (double*)A((size_t)div_up(N, kBrThreads / kBS) * kBS * kBrSums * sizeof(double));
   b->scal = (IterScalars*)A(kBS * sizeof(IterScalars));
   b->berr = (int*)A(sizeof(int));
   b->ybuf = (float2*)A((size_t)S * Q * b->KM * sizeof(float2));
   b->xout = (float*)A((size_t)S * N * 4);
-  std::vector<void*> Y(Q), R(Q), U(Q), G(Q);
+  std::vector<void*> R(Q), U(Q);
+  b->hY.assign(Q, nullptr);
+  b->hG.assign(Q, nullptr);
   for (int q = 0; q < Q && ok; ++q) {
-    Y[q] = A(KS * sizeof(float2));
+    b->hY[q] = A(KS * sizeof(float2));
     R[q] = A(KS * sizeof(float2));
     U[q] = A(2 * KS * sizeof(float));
-    G[q] = A(NS * sizeof(float));
+    b->hG[q] = A(NS * sizeof(float));
   }
   for (int q = 0; q < Q; ++q) {
     b->hR.push_back((const float2*)R[q]);
@@ -636,10 +792,10 @@ int sadmm_batch_create(int Q, int M, int K, int N, int S, double rho, const doub
   std::vector<float> lor(kBS);
   for (int s = 0; s < kBS; ++s) lor[s] = (float)(lambda[s] / rho);
   if (cudaMemcpy(b->lor, lor.data(), kBS * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemcpy(b->dY, Y.data(), Q * sizeof(void*), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(b->dY, b->hY.data(), Q * sizeof(void*), cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(b->dR, R.data(), Q * sizeof(void*), cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(b->dU, U.data(), Q * sizeof(void*), cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemcpy(b->dG, G.data(), Q * sizeof(void*), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(b->dG, b->hG.data(), Q * sizeof(void*), cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemset(b->berr, 0, sizeof(int)) != cudaSuccess) {
     for (void* p : b->owned) cudaFree(p);
     sadmm_destroy(single);
@@ -664,7 +820,7 @@ int sadmm_batch_set_stream(sadmm_batch_t b, void* stream) {
 int sadmm_batch_set_operator(sadmm_batch_t b, int q, const float* A_q) {
   using namespace sadmm;
   if (!b) return SADMM_EINVAL;
-  b->graph_valid = false;
+  b->invalidate();
   return sadmm_set_operator(b->single, q, A_q);
 }
 
@@ -672,96 +828,89 @@ int sadmm_batch_solve(sadmm_batch_t b, const float* y, float* x_out, int iters, 
   using namespace sadmm;
   if (!b || !y || iters < 0) { set_error("sadmm_batch_solve: bad arguments"); return SADMM_EINVAL; }
   const auto t0 = std::chrono::steady_clock::now();
-  SADMM_TRY(sadmm_prepare(b->single));
-  if (!b->graph_valid) {
-    std::vector<void*> Ap(b->Q), Fp(b->Q);
-    if (b->fpair.empty()) b->fpair.assign(b->Q, nullptr);
-    b->hA.assign(b->Q, nullptr);
-    for (int q = 0; q < b->Q; ++q) {
-      const float2* A = nullptr;
-      const double* F = nullptr;
-      SADMM_TRY(single_export(b->single, q, &A, &F, &b->n, &b->ld, &b->woodbury));
-      // the batched apply reads the packed symmetric factor as (hi, lo) pairs
-      if (!b->fpair[q]) {
-        b->fpair[q] = (float2*)b->dalloc(sym_packed_pairs(b->n) * sizeof(float2));
-        if (!b->fpair[q]) { set_error("sadmm_batch_solve: factor allocation failed"); return SADMM_ENOMEM; }
-      }
-      SADMM_TRY(launch_pack_sym(F, b->ld, b->n, b->fpair[q], b->st));
-      Ap[q] = (void*)A;
-      Fp[q] = (void*)b->fpair[q];
-      b->hA[q] = A;
-    }
-    if (!b->bpart) {
-      const size_t nt = div_up(b->n, kT);
-      b->bpart_stride = nt * (nt + 1) / 2 * kBtPart;
-      b->bpart = (float2*)b->dalloc((size_t)b->Q * b->bpart_stride * sizeof(float2));
-      if (!b->bpart) { set_error("sadmm_batch_solve: scratch allocation failed"); return SADMM_ENOMEM; }
-    }
-    SADMM_CUDA_TRY(cudaMemcpyAsync(b->dF, Fp.data(), b->Q * sizeof(void*), cudaMemcpyHostToDevice, b->st));
-    SADMM_CUDA_TRY(cudaStreamSynchronize(b->st));
-    if (b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; }
-    // capture one iteration; replay it `iters` times
-    cudaStream_t cap;
-    SADMM_CUDA_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
-    cudaStream_t saved = b->st;
-    b->st = cap;
-    cudaGraph_t g;
-    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
-    const long long n0 = sadmm_launch_count();
-    int rc = e == cudaSuccess ? batch_launch_iteration(*b) : SADMM_ECUDA;
-    b->kernels_per_iter = (int)(sadmm_launch_count() - n0);
-    cudaError_t e2 = cudaStreamEndCapture(cap, &g);
-    b->st = saved;
-    cudaStreamDestroy(cap);
-    if (rc != SADMM_OK) return rc;
-    SADMM_CUDA_TRY(e);
-    SADMM_CUDA_TRY(e2);
-    e = cudaGraphInstantiate(&b->graph, g, 0);
-    cudaGraphDestroy(g);
-    SADMM_CUDA_TRY(e);
-    b->graph_valid = true;
-  }
-  // reset and load measurements
-  const size_t QNS = (size_t)b->Q * b->N * kBS, NS = (size_t)b->N * kBS;
-  SADMM_CUDA_TRY(cudaMemsetAsync(b->X, 0, QNS * 4, b->st));
-  SADMM_CUDA_TRY(cudaMemsetAsync(b->dX, 0, QNS * 4, b->st));
-  SADMM_CUDA_TRY(cudaMemsetAsync(b->xbar, 0, NS * 4, b->st));
-  SADMM_CUDA_TRY(cudaMemsetAsync(b->zbar, 0, NS * 4, b->st));
-  SADMM_CUDA_TRY(cudaMemsetAsync(b->sd, 0, NS * 4, b->st));
-  SADMM_CUDA_TRY(cudaMemcpyAsync(b->ybuf, y, (size_t)kBS * b->Q * b->KM * sizeof(float2), cudaMemcpyDefault, b->st));
-  bload_y_kernel<<<dim3(div_up((long long)b->KM * kBS, 256), b->Q), 256, 0, b->st>>>(b->ybuf, b->dY, b->Q, b->KM);
-  SADMM_LAUNCH_CHECK();
+  SADMM_TRY(batch_setup(*b));
+  if (!b->graph_valid) SADMM_TRY(batch_capture(*b));
+  SADMM_TRY(batch_reset(*b, y, b->st));
   for (int it = 0; it < iters; ++it) {
     SADMM_CUDA_TRY(cudaGraphLaunch(b->graph, b->st));
     for (int kk = 0; kk < b->kernels_per_iter; ++kk) count_launch();
   }
-  if (x_out) {
-    bscale_kernel<<<div_up(NS, 256), 256, 0, b->st>>>(b->zbar, (float)b->Q, b->xout, b->N);
-    SADMM_LAUNCH_CHECK();
-    SADMM_CUDA_TRY(cudaMemcpyAsync(x_out, b->xout, NS * 4, cudaMemcpyDefault, b->st));
-  }
-  IterScalars h[kBS];
-  int herr = 0;
-  SADMM_CUDA_TRY(cudaMemcpyAsync(h, b->scal, sizeof h, cudaMemcpyDeviceToHost, b->st));
-  SADMM_CUDA_TRY(cudaMemcpyAsync(&herr, b->berr, sizeof(int), cudaMemcpyDeviceToHost, b->st));
+  SADMM_TRY(batch_collect(*b, x_out, b->st));
   SADMM_CUDA_TRY(cudaStreamSynchronize(b->st));
-  b->k = iters;
+  const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  return batch_finish(*b, iters, st, ms);
+}
+
+int sadmm_batch_tune(sadmm_batch_t b, int reps, sadmm_batch_tuning* out) {
+  using namespace sadmm;
+  if (!b || reps < 1) { set_error("sadmm_batch_tune: bad arguments"); return SADMM_EINVAL; }
+  SADMM_TRY(batch_setup(*b));
+  // defined inputs for the timed launches (the next solve resets the state)
+  const size_t QNS = (size_t)b->Q * b->N * kBS, NS = (size_t)b->N * kBS, KS = (size_t)b->KM * kBS;
+  for (float* p : {b->X, b->dX}) SADMM_CUDA_TRY(cudaMemsetAsync(p, 0, QNS * 4, b->st));
+  for (float* p : {b->xbar, b->zbar, b->sd}) SADMM_CUDA_TRY(cudaMemsetAsync(p, 0, NS * 4, b->st));
+  for (int q = 0; q < b->Q; ++q) {
+    SADMM_CUDA_TRY(cudaMemsetAsync(b->hY[q], 0, KS * sizeof(float2), b->st));
+    SADMM_CUDA_TRY(cudaMemsetAsync((void*)b->hR[q], 0, KS * sizeof(float2), b->st));
+    SADMM_CUDA_TRY(cudaMemsetAsync((void*)b->hU[q], 0, 2 * KS * sizeof(float), b->st));
+  }
+  const BatchDev bv = b->view();
+  cudaEvent_t e0, e1;
+  SADMM_CUDA_TRY(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); set_error("sadmm_batch_tune: event"); return SADMM_ECUDA; }
+  sadmm_batch_tuning t;
+  memset(&t, 0, sizeof t);
+  int rc = SADMM_OK;
+  auto time_it = [&](auto&& launch, double* ms) -> int {
+    int r = launch();                                  // untimed first launch
+    if (r != SADMM_OK) return r;
+    if (cudaEventRecord(e0, b->st) != cudaSuccess) return SADMM_ECUDA;
+    for (int i = 0; i < reps && r == SADMM_OK; ++i) r = launch();
+    if (r != SADMM_OK) return r;
+    if (cudaEventRecord(e1, b->st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) return SADMM_ECUDA;
+    float f = 0.f;
+    if (cudaEventElapsedTime(&f, e0, e1) != cudaSuccess) return SADMM_ECUDA;
+    *ms = (double)f / reps;
+    return SADMM_OK;
+  };
+  const std::vector<int> fc = split_candidates(b->chunks0, b->chunks_cap);
+  const std::vector<int> ac = split_candidates(b->asplits0, b->asplits_cap);
+  const float2* const* adj_in = b->woodbury ? b->hU.data() : b->hR.data();
+  int best_f = b->chunks0, best_a = b->asplits0;
+  double tf = 1e300, ta = 1e300;
+  for (size_t i = 0; i < fc.size() && rc == SADMM_OK; ++i) {
+    const int c = fc[i];
+    rc = time_it([&] { return launch_forward_products(*b, c, bv); }, &t.fwd_ms[i]);
+    t.fwd_splits[i] = c;
+    t.n_fwd = (int)i + 1;
+    if (rc == SADMM_OK && t.fwd_ms[i] < tf) { tf = t.fwd_ms[i]; best_f = c; }
+  }
+  for (size_t i = 0; i < ac.size() && rc == SADMM_OK; ++i) {
+    const int a = ac[i];
+    rc = time_it([&] { return launch_adjoint_products(*b, a, adj_in, 1, bv); }, &t.adj_ms[i]);
+    t.adj_splits[i] = a;
+    t.n_adj = (int)i + 1;
+    if (rc == SADMM_OK && t.adj_ms[i] < ta) { ta = t.adj_ms[i]; best_a = a; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != SADMM_OK) return rc;
+  int herr = 0;
+  SADMM_CUDA_TRY(cudaMemcpy(&herr, b->berr, sizeof(int), cudaMemcpyDeviceToHost));
   if (herr) {
     SADMM_CUDA_TRY(cudaMemset(b->berr, 0, sizeof(int)));
-    set_error("batched factor apply: a tile copy did not complete within the wait limit");
+    set_error("sadmm_batch_tune: a tensor-core pipeline wait did not complete within its limit");
     return SADMM_ETIMEOUT;
   }
-  for (int s = 0; s < kBS; ++s)
-    if (iters > 0 && h[s].nonfinite) { set_error("non-finite value in scene %d", s); return SADMM_ENONFINITE; }
-  if (st) {
-    memset(st, 0, sizeof *st);
-    st->iters = iters;
-    st->active_total = b->Q * b->N * kBS;
-    st->r_pri = h[0].r_pri; st->eps_pri = h[0].eps_pri; st->d = h[0].d; st->eps_dual = h[0].eps_dual;
-    st->relchange = h[0].relchange;
-    st->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-    st->bytes_iter = (double)iters * ((double)b->Q * b->KM * b->N * 16.0 + (double)b->Q * sym_packed_pairs(b->n) * 8.0);
-  }
+  b->chunks = best_f;
+  b->asplits = best_a;
+  t.fwd_choice = best_f;
+  t.adj_choice = best_a;
+  t.fwd_default = b->chunks0;
+  t.adj_default = b->asplits0;
+  b->graph_valid = false;
+  ++b->epoch;
+  if (out) *out = t;
   return SADMM_OK;
 }
 
@@ -782,6 +931,133 @@ void sadmm_batch_destroy(sadmm_batch_t b) {
   for (void* p : b->owned) cudaFree(p);
   sadmm_destroy(b->single);
   delete b;
+}
+
+// ------------------------------------------------------------ batch groups
+
+static void group_release(sadmm_batch_group_t g) {
+  if (g->graph) cudaGraphExecDestroy(g->graph);
+  for (cudaStream_t s : g->side) cudaStreamDestroy(s);
+  for (cudaEvent_t e : g->ev) cudaEventDestroy(e);
+  delete g;
+}
+
+int sadmm_batch_group_create(const sadmm_batch_t* batches, int n, sadmm_batch_group_t* out) {
+  using namespace sadmm;
+  if (!out || !batches || n < 1 || n > 64) { set_error("sadmm_batch_group_create: 1..64 batches required"); return SADMM_EINVAL; }
+  *out = nullptr;
+  for (int i = 0; i < n; ++i) {
+    if (!batches[i]) { set_error("sadmm_batch_group_create: batch %d is NULL", i); return SADMM_EINVAL; }
+    for (int j = 0; j < i; ++j)
+      if (batches[j] == batches[i]) { set_error("sadmm_batch_group_create: batch %d repeated", i); return SADMM_EINVAL; }
+  }
+  sadmm_batch_group_t g = new (std::nothrow) sadmm_batch_group_ctx();
+  if (!g) return SADMM_ENOMEM;
+  for (int i = 0; i < n; ++i) g->b.push_back(batches[i]);
+  g->epochs.assign(n, ~0u);
+  for (int i = 0; i < n; ++i) {
+    cudaStream_t s;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+      group_release(g);
+      set_error("sadmm_batch_group_create: stream creation failed");
+      return SADMM_ECUDA;
+    }
+    g->side.push_back(s);
+  }
+  for (int i = 0; i <= n; ++i) {
+    cudaEvent_t e;
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+      group_release(g);
+      set_error("sadmm_batch_group_create: event creation failed");
+      return SADMM_ECUDA;
+    }
+    g->ev.push_back(e);
+  }
+  *out = g;
+  return SADMM_OK;
+}
+
+int sadmm_batch_group_set_stream(sadmm_batch_group_t g, void* stream) {
+  using namespace sadmm;
+  if (!g) return SADMM_EINVAL;
+  SADMM_CUDA_TRY(cudaStreamSynchronize(g->st));
+  g->st = (cudaStream_t)stream;
+  return SADMM_OK;
+}
+
+// One iteration of every batch, each on its own branch of one graph.
+static int group_capture(sadmm_batch_group_t g) {
+  using namespace sadmm;
+  if (g->graph) { cudaGraphExecDestroy(g->graph); g->graph = nullptr; }
+  cudaStream_t cap;
+  SADMM_CUDA_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+  int rc = e == cudaSuccess ? SADMM_OK : SADMM_ECUDA;
+  const long long n0 = sadmm_launch_count();
+  if (rc == SADMM_OK && cudaEventRecord(g->ev[0], cap) != cudaSuccess) rc = SADMM_ECUDA;
+  for (size_t i = 0; i < g->b.size() && rc == SADMM_OK; ++i) {
+    BatchCtx& b = *g->b[i];
+    if (cudaStreamWaitEvent(g->side[i], g->ev[0], 0) != cudaSuccess) { rc = SADMM_ECUDA; break; }
+    cudaStream_t saved = b.st;
+    b.st = g->side[i];
+    rc = batch_launch_iteration(b);
+    b.st = saved;
+    if (rc == SADMM_OK && (cudaEventRecord(g->ev[i + 1], g->side[i]) != cudaSuccess ||
+                           cudaStreamWaitEvent(cap, g->ev[i + 1], 0) != cudaSuccess))
+      rc = SADMM_ECUDA;
+  }
+  g->kernels_per_iter = (int)(sadmm_launch_count() - n0);
+  cudaError_t e2 = e == cudaSuccess ? cudaStreamEndCapture(cap, &graph) : cudaSuccess;
+  cudaStreamDestroy(cap);
+  if (rc != SADMM_OK || e2 != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    if (rc == SADMM_OK) set_error("batch group: graph capture failed (%s)", cudaGetErrorString(e2));
+    return rc != SADMM_OK ? rc : SADMM_ECUDA;
+  }
+  e = cudaGraphInstantiate(&g->graph, graph, 0);
+  cudaGraphDestroy(graph);
+  SADMM_CUDA_TRY(e);
+  for (size_t i = 0; i < g->b.size(); ++i) g->epochs[i] = g->b[i]->epoch;
+  return SADMM_OK;
+}
+
+int sadmm_batch_group_solve(sadmm_batch_group_t g, const float* const* y, float* const* x_out, int iters,
+                            sadmm_stats* st) {
+  using namespace sadmm;
+  if (!g || !y || iters < 0) { set_error("sadmm_batch_group_solve: bad arguments"); return SADMM_EINVAL; }
+  const int n = (int)g->b.size();
+  for (int i = 0; i < n; ++i)
+    if (!y[i]) { set_error("sadmm_batch_group_solve: y[%d] is NULL", i); return SADMM_EINVAL; }
+  const auto t0 = std::chrono::steady_clock::now();
+  bool stale = !g->graph;
+  for (int i = 0; i < n; ++i) {
+    BatchCtx& b = *g->b[i];
+    SADMM_CUDA_TRY(cudaStreamSynchronize(b.st));
+    SADMM_TRY(batch_setup(b));
+    if (g->epochs[i] != b.epoch) stale = true;
+  }
+  if (stale) SADMM_TRY(group_capture(g));
+  for (int i = 0; i < n; ++i) SADMM_TRY(batch_reset(*g->b[i], y[i], g->st));
+  for (int it = 0; it < iters; ++it) {
+    SADMM_CUDA_TRY(cudaGraphLaunch(g->graph, g->st));
+    for (int kk = 0; kk < g->kernels_per_iter; ++kk) count_launch();
+  }
+  for (int i = 0; i < n; ++i) SADMM_TRY(batch_collect(*g->b[i], x_out ? x_out[i] : nullptr, g->st));
+  SADMM_CUDA_TRY(cudaStreamSynchronize(g->st));
+  const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  int rc = SADMM_OK;
+  for (int i = 0; i < n; ++i) {
+    const int r = batch_finish(*g->b[i], iters, st ? &st[i] : nullptr, ms);
+    if (rc == SADMM_OK) rc = r;
+  }
+  return rc;
+}
+
+void sadmm_batch_group_destroy(sadmm_batch_group_t g) {
+  if (!g) return;
+  cudaStreamSynchronize(g->st);
+  group_release(g);
 }
 
 }  // extern "C"

@@ -115,6 +115,9 @@ int tc_adjoint_splits(int Q, int N, int KM);
 // real rows 2m, 2m+1) = sum over the split's pixels p of B_q[r][p] V[p][s],
 // V = x - x_bar + z_bar - s of scene s (16 scenes); Aq: HOST array of Q device pointers.
 int tc_forward_splits(int Q, int N, int KM);
+// Largest useful split counts (at least four 32-row / 32-pixel slabs per split).
+int tc_adjoint_max_splits(int KM);
+int tc_forward_max_splits(int N);
 int launch_tc_forward(const float2* const* Aq, const float* X, const float* xbar, const float* zbar, const float* sd,
                       float2* partial, int Q, int N, int KM, int splits, int* err, cudaStream_t st);
 int launch_tc_adjoint(const float2* const* Aq, const float2* const* Wq, float* gpart, int Q, int N, int KM, int splits,

@@ -9,6 +9,7 @@
 // order (deterministic).  The adjoint g[p] = Re(a_{idx[p]}^H w) gives one warp
 // per column with w staged in shared memory and a shuffle reduction.
 #include "common.cuh"
+#include "symtile.cuh"
 
 #include <algorithm>
 #include <mutex>
@@ -16,6 +17,11 @@
 namespace sadmm {
 
 namespace {
+
+using symtile::DF;
+using symtile::df_add;
+using symtile::df_add1;
+using symtile::df_norm;
 
 constexpr int kFwdThreads = 128;          // one float4 (2 complex rows) per thread
 constexpr int kFwdRows = 2 * kFwdThreads; // complex rows per CTA slice
@@ -52,7 +58,11 @@ forward_partial_kernel(const __grid_constant__ SetBlock<ColumnSet> sets, int KM,
   const bool active_row = row2 * 2 < KM;
   __shared__ float s_v[kFwdStage];
   __shared__ int s_off[kFwdStage];
-  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  // Eight products per component are summed in FP32 and each such partial
+  // goes into a double-float accumulator: near convergence B v almost cancels
+  // y, and FP32 accumulation over thousands of columns would lose the digits
+  // of the residual that the x-update needs.
+  DF acc[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
   const float4* A4 = reinterpret_cast<const float4*>(cs.A);
   const size_t col4 = (size_t)KM / 2;                        // float4 per column
   for (int b0 = p0; b0 < p1; b0 += kFwdStage) {
@@ -71,27 +81,44 @@ forward_partial_kernel(const __grid_constant__ SetBlock<ColumnSet> sets, int KM,
 #pragma unroll
         for (int u = 0; u < kFwdUnroll; ++u)
           a[u] = ld_stream(A4 + (size_t)s_off[j + u] * col4 + row2);
+        float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
         for (int u = 0; u < kFwdUnroll; ++u) {
           const float v = s_v[j + u];
-          acc.x = fmaf(a[u].x, v, acc.x);
-          acc.y = fmaf(a[u].y, v, acc.y);
-          acc.z = fmaf(a[u].z, v, acc.z);
-          acc.w = fmaf(a[u].w, v, acc.w);
+          t.x = fmaf(a[u].x, v, t.x);
+          t.y = fmaf(a[u].y, v, t.y);
+          t.z = fmaf(a[u].z, v, t.z);
+          t.w = fmaf(a[u].w, v, t.w);
         }
+        df_add1(acc[0], t.x);
+        df_add1(acc[1], t.y);
+        df_add1(acc[2], t.z);
+        df_add1(acc[3], t.w);
       }
+      float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
       for (; j < nb; ++j) {
         const float4 a = ld_stream(A4 + (size_t)s_off[j] * col4 + row2);
         const float v = s_v[j];
-        acc.x = fmaf(a.x, v, acc.x);
-        acc.y = fmaf(a.y, v, acc.y);
-        acc.z = fmaf(a.z, v, acc.z);
-        acc.w = fmaf(a.w, v, acc.w);
+        t.x = fmaf(a.x, v, t.x);
+        t.y = fmaf(a.y, v, t.y);
+        t.z = fmaf(a.z, v, t.z);
+        t.w = fmaf(a.w, v, t.w);
       }
+      df_add1(acc[0], t.x);
+      df_add1(acc[1], t.y);
+      df_add1(acc[2], t.z);
+      df_add1(acc[3], t.w);
     }
   }
-  if (active_row)
-    partial[((size_t)blockIdx.z * chunks + c) * col4 + row2] = acc;
+  if (active_row) {
+    // chunk partial as a pair of float4 planes: high words, then low words
+    float4* out = partial + ((size_t)blockIdx.z * chunks + c) * 2 * col4 + row2;
+    DF n[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) n[k] = df_norm(acc[k]);
+    out[0] = make_float4(n[0].hi, n[1].hi, n[2].hi, n[3].hi);
+    out[col4] = make_float4(n[0].lo, n[1].lo, n[2].lo, n[3].lo);
+  }
 }
 
 // out[r] = base[r] - sum_c partial[c][r], chunks summed in ascending order.
@@ -101,16 +128,39 @@ __global__ void forward_reduce_kernel(const __grid_constant__ SetBlock<ColumnSet
   const int row2 = blockIdx.x * blockDim.x + threadIdx.x;
   if (row2 * 2 >= KM) return;
   const size_t col4 = (size_t)KM / 2;
-  const float4* p = partial + (size_t)blockIdx.y * chunks * col4 + row2;
-  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-  for (int c = 0; c < chunks; ++c) {
-    const float4 t = p[(size_t)c * col4];
-    acc.x += t.x; acc.y += t.y; acc.z += t.z; acc.w += t.w;
+  const float4* p = partial + (size_t)blockIdx.y * chunks * 2 * col4 + row2;
+  DF acc[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+  constexpr int kB = 4;                 // chunk loads issued ahead of their sums
+  for (int c0 = 0; c0 < chunks; c0 += kB) {
+    float4 h[kB], l[kB];
+#pragma unroll
+    for (int u = 0; u < kB; ++u) {
+      h[u] = l[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (c0 + u < chunks) {
+        h[u] = p[(size_t)(c0 + u) * 2 * col4];
+        l[u] = p[(size_t)(c0 + u) * 2 * col4 + col4];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kB; ++u) {
+      df_add(acc[0], DF{h[u].x, l[u].x});
+      df_add(acc[1], DF{h[u].y, l[u].y});
+      df_add(acc[2], DF{h[u].z, l[u].z});
+      df_add(acc[3], DF{h[u].w, l[u].w});
+    }
   }
   float4 b = make_float4(0.f, 0.f, 0.f, 0.f);
   if (cs.base) b = reinterpret_cast<const float4*>(cs.base)[row2];
-  reinterpret_cast<float4*>(cs.out)[row2] =
-      make_float4(b.x - acc.x, b.y - acc.y, b.z - acc.z, b.w - acc.w);
+  // r = b - (sum), formed in double-float and rounded once
+  const float bb[4] = {b.x, b.y, b.z, b.w};
+  float r[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    DF d{-acc[k].hi, -acc[k].lo};
+    df_add1(d, bb[k]);
+    r[k] = d.hi + d.lo;
+  }
+  reinterpret_cast<float4*>(cs.out)[row2] = make_float4(r[0], r[1], r[2], r[3]);
 }
 
 int forward_chunks(int nsets, int KM, int max_cols) {
@@ -144,9 +194,13 @@ adjoint_kernel(const __grid_constant__ SetBlock<AdjointSet> sets, int KM, bool u
     if (p >= as.n) break;
     const int pix = as.idx[p];
     const float4* col = A4 + (size_t)pix * n4;
-    float acc[kAdjUnroll];
+    // Each float4 (two complex entries, four real products) is summed in FP32
+    // and the partial goes into a double-float accumulator: the sum over the
+    // 2KM real rows cancels heavily (|x| is far below sum |b||w|), and plain
+    // FP32 accumulation over thousands of terms loses about three digits.
+    DF acc[kAdjUnroll];
 #pragma unroll
-    for (int u = 0; u < kAdjUnroll; ++u) acc[u] = 0.f;
+    for (int u = 0; u < kAdjUnroll; ++u) acc[u] = DF{0.f, 0.f};
     int i = lane;
     for (; i + 32 * (kAdjUnroll - 1) < n4; i += 32 * kAdjUnroll) {
       float4 a[kAdjUnroll];
@@ -155,25 +209,30 @@ adjoint_kernel(const __grid_constant__ SetBlock<AdjointSet> sets, int KM, bool u
 #pragma unroll
       for (int u = 0; u < kAdjUnroll; ++u) {
         const float4 w = s_w4[i + 32 * u];
-        acc[u] = fmaf(a[u].x, w.x, acc[u]);
-        acc[u] = fmaf(a[u].y, w.y, acc[u]);
-        acc[u] = fmaf(a[u].z, w.z, acc[u]);
-        acc[u] = fmaf(a[u].w, w.w, acc[u]);
+        float t = a[u].x * w.x;
+        t = fmaf(a[u].y, w.y, t);
+        t = fmaf(a[u].z, w.z, t);
+        t = fmaf(a[u].w, w.w, t);
+        df_add1(acc[u], t);
       }
     }
     for (; i < n4; i += 32) {
       const float4 a = ld_stream(col + i);
       const float4 w = s_w4[i];
-      acc[0] = fmaf(a.x, w.x, acc[0]);
-      acc[0] = fmaf(a.y, w.y, acc[0]);
-      acc[0] = fmaf(a.z, w.z, acc[0]);
-      acc[0] = fmaf(a.w, w.w, acc[0]);
+      float t = a.x * w.x;
+      t = fmaf(a.y, w.y, t);
+      t = fmaf(a.z, w.z, t);
+      t = fmaf(a.w, w.w, t);
+      df_add1(acc[0], t);
     }
-    float g = 0.f;
 #pragma unroll
-    for (int u = 0; u < kAdjUnroll; ++u) g += acc[u];
+    for (int u = 1; u < kAdjUnroll; ++u) df_add(acc[0], acc[u]);
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
+    for (int o = 16; o > 0; o >>= 1) {
+      const DF b{__shfl_xor_sync(0xffffffffu, acc[0].hi, o), __shfl_xor_sync(0xffffffffu, acc[0].lo, o)};
+      df_add(acc[0], b);
+    }
+    const float g = acc[0].hi + acc[0].lo;
     if (lane == 0) {
       if (update) {
         // x-update epilogue (Woodbury form): x = v + mu Re(a^H w)
@@ -193,7 +252,7 @@ adjoint_kernel(const __grid_constant__ SetBlock<AdjointSet> sets, int KM, bool u
 }  // namespace
 
 size_t forward_partial_bytes(int nsets, int KM, int max_cols) {
-  return (size_t)nsets * forward_chunks(nsets, KM, max_cols) * KM * sizeof(float2);
+  return (size_t)nsets * forward_chunks(nsets, KM, max_cols) * 2 * KM * sizeof(float2);   // (hi, lo) planes
 }
 
 int launch_forward(const ColumnSet* sets, int nsets, int KM, VMode mode, const SolverView& sv,
@@ -205,7 +264,7 @@ int launch_forward(const ColumnSet* sets, int nsets, int KM, VMode mode, const S
   for (int i = 0; i < nsets; ++i) { blk.v[i] = sets[i]; max_cols = max(max_cols, sets[i].n); }
   const int chunks = forward_chunks(nsets, KM, max(max_cols, 1));
   const int per = max(1, div_up(max_cols, chunks));
-  if ((size_t)nsets * chunks * KM * sizeof(float2) > partial_cap) {
+  if (forward_partial_bytes(nsets, KM, max(max_cols, 1)) > partial_cap) {
     set_error("launch_forward: partial buffer too small");
     return SADMM_EINVAL;
   }
@@ -213,8 +272,8 @@ int launch_forward(const ColumnSet* sets, int nsets, int KM, VMode mode, const S
   forward_partial_kernel<<<grid, kFwdThreads, 0, st>>>(blk, KM, chunks, per, mode, sv,
                                                        reinterpret_cast<float4*>(partial));
   SADMM_LAUNCH_CHECK();
-  dim3 g2(div_up(KM / 2, 256), nsets);
-  forward_reduce_kernel<<<g2, 256, 0, st>>>(blk, KM, chunks, reinterpret_cast<const float4*>(partial));
+  dim3 g2(div_up(KM / 2, 64), nsets);                   // small blocks: one CTA per SM or more
+  forward_reduce_kernel<<<g2, 64, 0, st>>>(blk, KM, chunks, reinterpret_cast<const float4*>(partial));
   SADMM_LAUNCH_CHECK();
   return SADMM_OK;
 }

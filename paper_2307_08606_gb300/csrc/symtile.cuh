@@ -1,5 +1,6 @@
-// Device helpers shared by the symmetric factor applies (spd.cu, batch.cu):
-// double-float accumulation with exact products, bulk asynchronous copies
+// Device helpers shared by the symmetric factor applies (spd.cu, batch.cu) and
+// the adjoint (gemv.cu): double-float accumulation with exact products, bulk
+// asynchronous copies
 // completing on an mbarrier (with bounded waits), and the packed
 // upper-triangular tile numbering.
 #pragma once
@@ -32,6 +33,14 @@ __device__ __forceinline__ void df_add(DF& s, DF b) {
   const float err = (s.hi - (t - bp)) + (b.hi - bp);
   s.hi = t;
   s.lo += err + b.lo;
+}
+
+// s += x (a single FP32 term), error-free up to the low word's own rounding
+__device__ __forceinline__ void df_add1(DF& s, float x) {
+  const float t = s.hi + x;
+  const float bp = t - s.hi;
+  s.lo += (s.hi - (t - bp)) + (x - bp);
+  s.hi = t;
 }
 
 __device__ __forceinline__ DF df_norm(DF s) {

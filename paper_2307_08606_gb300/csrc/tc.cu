@@ -606,10 +606,14 @@ EncodeTiledFn tensor_map_encoder() {
 }
 }  // namespace
 
+int tc_adjoint_max_splits(int KM) { return std::max(1, (2 * KM) / (4 * kTcK)); }
+
+int tc_forward_max_splits(int N) { return std::max(1, div_up(N, 4 * kTcK)); }
+
 int tc_adjoint_splits(int Q, int N, int KM) {
   const int tiles = div_up(N, kTcM) * Q;
   const int want = div_up(152 * 4, tiles);                  // about four items per persistent CTA
-  return std::max(1, std::min(want, (2 * KM) / (4 * kTcK)));
+  return std::max(1, std::min(want, tc_adjoint_max_splits(KM)));
 }
 
 int launch_tc_adjoint(const float2* const* Aq, const float2* const* Wq, float* gpart, int Q, int N, int KM, int splits,
@@ -649,7 +653,7 @@ int launch_tc_adjoint(const float2* const* Aq, const float2* const* Wq, float* g
 int tc_forward_splits(int Q, int N, int KM) {
   const int tiles = div_up(2 * KM, kTcM) * Q;
   const int want = div_up(152 * 4, tiles);
-  return std::max(1, std::min(want, div_up(N, 4 * kTcK)));
+  return std::max(1, std::min(want, tc_forward_max_splits(N)));
 }
 
 int launch_tc_forward(const float2* const* Aq, const float* X, const float* xbar, const float* zbar, const float* sd,

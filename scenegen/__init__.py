@@ -3,9 +3,11 @@ tests and the CUDA-side tests and bench.  No solver arithmetic lives here."""
 from .rng import Stream
 from .radar import (Geometry, Scene, operator, delays, pixel_centres, sensor_positions,
                     point_targets, cluster_targets, measure, lambda_max)
-from .configs import GEOMS, Params, build_scene, resolve_lambda, random_problem
+from .configs import (GEOMS, Params, build_scene, resolve_lambda, random_problem, batch_geometries,
+                      batch_scenes)
 from .cnn_init import cnn_init
 
 __all__ = ["Stream", "Geometry", "Scene", "operator", "delays", "pixel_centres",
            "sensor_positions", "point_targets", "cluster_targets", "measure", "lambda_max",
-           "GEOMS", "Params", "build_scene", "resolve_lambda", "random_problem", "cnn_init"]
+           "GEOMS", "Params", "build_scene", "resolve_lambda", "random_problem", "batch_geometries",
+           "batch_scenes", "cnn_init"]

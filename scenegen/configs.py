@@ -8,6 +8,11 @@
   paper's cell size), same radar and circle as ``small_point``; 40 clusters of
   1..9 pixels, magnitudes U[0.3, 1], p=0.7, 15 dB SNR; relative-change
   tolerance 1e-4, pixel elimination on.
+* mixed-geometry batches (``batch_geometries``, ``batch_scenes``): geometries
+  drawn by seed from the 48 combinations of Q in {2, 4, 6, 8}, M in {4, 8},
+  K in {128, 256}, N in {48^2, 64^2, 96^2} (radar, circle and 5 cm cells as
+  ``paper_scale``), 16 scenes per geometry with 5..60 clusters, visibility
+  p in [0.5, 0.9] and 10..25 dB SNR.
 * ``resolved_tiny``: a well-posed geometry used by the oracle's pins: 8x8
   pixels of 10 cm seen from 0.6 m by sensors with M=16 antennas and BW=4 GHz
   at 60 GHz (K=16, KM=256 > N), so that every sensor resolves the grid on its
@@ -90,3 +95,41 @@ def random_problem(Q, KM, N, seed, snr_db=30.0, k_sparse=3):
         x[q, pix] = amp[q]
     y = measure(A, x, snr_db, seed)
     return Scene(geom=g, A=A, y=y, x_true=x, seed=seed, meta={"name": "random"})
+
+
+BATCH_Q = (2, 4, 6, 8)
+BATCH_M = (4, 8)
+BATCH_K = (128, 256)
+BATCH_NX = (48, 64, 96)
+
+
+def batch_geometries(seed: int, count: int = 32):
+    """`count` distinct geometries drawn by seed (without repetition) from the
+    48 combinations of BATCH_Q x BATCH_M x BATCH_K x BATCH_NX."""
+    from .rng import Stream
+    combos = [(Q, M, K, nx) for Q in BATCH_Q for M in BATCH_M for K in BATCH_K for nx in BATCH_NX]
+    if not 1 <= count <= len(combos):
+        raise ValueError(f"count must be in 1..{len(combos)}")
+    pick = Stream(seed, 301).permutation(len(combos))[:count]
+    return [Geometry(Q=combos[i][0], M=combos[i][1], K=combos[i][2], nx=combos[i][3], cell=0.05, radius=10.0,
+                     fc=77e9, bw=1e9) for i in pick]
+
+
+def batch_scenes(g: Geometry, A, seed: int, S: int = 16):
+    """S scenes sharing the operators A of geometry g: 5..60 clusters of
+    magnitudes U[0.3, 1], visibility p ~ U[0.5, 0.9], SNR ~ U[10, 25] dB, all
+    drawn by seed.  Returns (Y, lams): Y (S, Q, KM) complex64 and the per-scene
+    lambda = 0.05 lambda_max."""
+    from .rng import Stream
+    st = Stream(seed, 302)
+    n_cl = 5 + st.integers(S, 56)
+    p_vis = st.uniform(S, 0.5, 0.9)
+    snr = st.uniform(S, 10.0, 25.0)
+    Y, lams = [], []
+    for s in range(S):
+        sub = 1000 * seed + s
+        x = cluster_targets(g, sub, int(n_cl[s]), amp=(0.3, 1.0), p_vis=float(p_vis[s]))
+        y = measure(A, x, float(snr[s]), sub)
+        Y.append(np.stack(y))
+        lams.append(0.05 * lambda_max(A, y))
+    return np.stack(Y).astype(np.complex64), lams

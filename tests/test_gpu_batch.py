@@ -68,3 +68,87 @@ def test_batch_matches_oracle_and_single_solver(B, name, iters):
         if np.any(ref.xG != 0):
             assert _rel(xg[s], ref.xG) <= 1e-4, s
     bs.close()
+
+
+def _batch(B, g, A, lams):
+    bs = B.BatchSolver(g.Q, g.M, g.K, g.N, 1.0, lams)
+    for q in range(g.Q):
+        bs.set_operator(q, A[q])
+    return bs
+
+
+def _stack_x(bs, g):
+    return np.stack([np.stack([bs.xq(s, q) for q in range(g.Q)]) for s in range(16)])
+
+
+def test_tuner_picks_fastest_candidate_and_keeps_results(B):
+    """sadmm_batch_tune times every candidate split of the two tensor-core
+    products and keeps the fastest; the solve after tuning still matches the
+    oracle (1e-4) and the untuned solve (2e-4: a different split changes only
+    the order of FP32 sums)."""
+    g, A, ys, lams = _scenes("small_point")
+    Y = np.stack([np.stack(y) for y in ys])
+    bs = _batch(B, g, A, lams)
+    iters = 60
+    xg0, _ = bs.solve(Y, iters)
+    X0 = _stack_x(bs, g)
+    t = bs.tune(reps=2)
+    for part, key in (("forward", "forward_splits"), ("adjoint", "adjoint_splits")):
+        times = t[part]
+        assert len(times) >= 2 and all(k >= 1 for k in times)
+        assert all(v > 0 for v in times.values())
+        assert t[key] == min(times, key=times.get)
+    xg1, _ = bs.solve(Y, iters)
+    X1 = _stack_x(bs, g)
+    for s in range(16):
+        assert _rel(X1[s], X0[s]) <= 2e-4, s
+    ref = oracle.sadmm(A, ys[0], 1.0, lams[0], oracle.Criterion(elim=0), iters=iters)
+    assert _rel(X1[0], ref.state.x) <= 1e-4
+    bs.close()
+
+
+def test_group_of_geometries_matches_separate_solves(B):
+    """Three geometries of different Q, KM and N (one with the primal factor,
+    N < 2KM, two with the Woodbury factor) iterate together as one batch
+    group: every scene's iterates equal those of its batch solved alone, bit
+    for bit (same kernels, same splits, fixed summation orders), scene 0 of
+    each geometry matches the oracle (1e-4), a second group solve resets the
+    state, and re-tuning one batch makes the group rebuild its graph."""
+    third = scenegen.Geometry(Q=2, M=4, K=32, nx=16, cell=0.1, radius=5.0, fc=77e9, bw=1e9)
+    specs = []
+    for name in ("small_point", "resolved_tiny", None):
+        if name is None:
+            g = third
+            A = [radar.operator(g, q) for q in range(g.Q)]
+            Y, lams = scenegen.batch_scenes(g, A, seed=7)
+            ys = [list(Y[s]) for s in range(16)]
+        else:
+            g, A, ys, lams = _scenes(name)
+            Y = np.stack([np.stack(y) for y in ys])
+        specs.append((g, A, ys, lams, Y))
+    iters = 40
+    sep = []
+    batches = []
+    for g, A, ys, lams, Y in specs:
+        bs = _batch(B, g, A, lams)
+        xg, _ = bs.solve(Y, iters)
+        sep.append((xg.copy(), _stack_x(bs, g)))
+        batches.append(bs)
+    grp = B.BatchGroup(batches)
+    for rep in range(2):
+        outs, stats = grp.solve([sp[4] for sp in specs], iters)
+        for i, (g, A, ys, lams, Y) in enumerate(specs):
+            assert stats[i]["iters"] == iters
+            assert np.array_equal(outs[i], sep[i][0]), (rep, i)
+            assert np.array_equal(_stack_x(batches[i], g), sep[i][1]), (rep, i)
+    for i, (g, A, ys, lams, Y) in enumerate(specs):
+        ref = oracle.sadmm(A, ys[0], 1.0, lams[0], oracle.Criterion(elim=0), iters=iters)
+        assert _rel(sep[i][1][0], ref.state.x) <= 1e-4, i
+    batches[0].tune(reps=1)
+    xg_alone, _ = batches[0].solve(specs[0][4], iters)
+    outs, _ = grp.solve([sp[4] for sp in specs], iters)
+    assert np.array_equal(outs[0], xg_alone)
+    assert np.array_equal(outs[1], sep[1][0])
+    grp.close()
+    for bs in batches:
+        bs.close()

@@ -376,3 +376,17 @@ def test_pins_catch_planted_mistakes(name):
         fa = oracle.objective(sc.A, sc.y, x, lam)
     caught = (max(k.values()) > 1e-6) or abs(fa - fval) > 1e-8 * abs(fval)
     assert caught, name
+
+
+def test_batch_geometries_draw_distinct_combinations():
+    """The mixed-geometry batched workload draws distinct (Q, M, K, N)
+    combinations from the 48 of its grid, the same ones for the same seed."""
+    gs = scenegen.batch_geometries(3, 32)
+    keys = {(g.Q, g.M, g.K, g.N) for g in gs}
+    assert len(keys) == 32
+    assert all(g.Q in (2, 4, 6, 8) and g.M in (4, 8) and g.K in (128, 256) and g.N in (48 ** 2, 64 ** 2, 96 ** 2)
+               for g in gs)
+    assert [(g.Q, g.M, g.K, g.N) for g in scenegen.batch_geometries(3, 32)] == [(g.Q, g.M, g.K, g.N) for g in gs]
+    assert len({(g.Q, g.M, g.K, g.N) for g in scenegen.batch_geometries(0, 48)}) == 48
+    with pytest.raises(ValueError):
+        scenegen.batch_geometries(0, 49)

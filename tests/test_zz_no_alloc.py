@@ -61,13 +61,14 @@ def test_noalloc_matches_allocating_forward_twice(B, KM, N, nidx):
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch(B):
-    """One column of KM = 2^20 + 2 rows needs 8 MiB + 16 bytes of partial sums,
-    more than the fixed 8 MiB: the host refuses it with EINVAL and a message
+    """One column of KM = 2^19 + 2 rows needs 8 MiB + 32 bytes of partial sums
+    (one chunk of double-float pairs, 16 bytes per complex row), more than the
+    fixed 8 MiB: the host refuses it with EINVAL and a message
     before any device work (the placeholder pointers are never dereferenced)."""
     import ctypes
     lib = B.load()
     p = ctypes.c_void_p(256)
-    rc = lib.sadmm_forward_noalloc(p, (1 << 20) + 2, 1, p, 1, p, None, p, None)
+    rc = lib.sadmm_forward_noalloc(p, (1 << 19) + 2, 1, p, 1, p, None, p, None)
     assert rc == B.EINVAL
     assert b"fixed scratch" in lib.sadmm_last_error()
     rc = lib.sadmm_forward_noalloc(None, 4096, 1, None, 0, None, None, None, None)
