@@ -390,3 +390,26 @@ def test_batch_geometries_draw_distinct_combinations():
     assert len({(g.Q, g.M, g.K, g.N) for g in scenegen.batch_geometries(0, 48)}) == 48
     with pytest.raises(ValueError):
         scenegen.batch_geometries(0, 49)
+
+
+def test_signal_model_operator_pins():
+    """The oracle's signal-model operator (Section II, Eq. 1, entries from the
+    round-trip delays) against the scene generator's complex64 operator, an
+    independent implementation: equal within the FP32 rounding of the
+    generator; unit modulus; a geometric progression in k for every (m, n)
+    with ratio exp(j 2 pi tau df); the k = 0 phase is 2 pi tau f0 (mod 2 pi)."""
+    g = scenegen.Geometry(Q=3, M=4, K=32, nx=12, cell=0.05, radius=10.0, fc=77e9, bw=1e9)
+    for q in (0, 2):
+        tau = radar.delays(g, q)
+        A = oracle.operator_from_delays(tau, g.fc, g.bw / g.K, g.K)
+        A32 = radar.operator(g, q)
+        assert A.shape == A32.shape == (g.N, g.KM)
+        assert np.max(np.abs(A - A32.astype(np.complex128))) <= 2.0 ** -23
+        assert np.allclose(np.abs(A), 1.0, atol=1e-12)
+        Ar = A.reshape(g.N, g.M, g.K)
+        ratio = Ar[:, :, 1:] / Ar[:, :, :-1]
+        want = np.exp(2j * np.pi * tau.T * (g.bw / g.K))
+        assert np.max(np.abs(ratio - want[:, :, None])) <= 1e-9
+        ph0 = np.angle(Ar[:, :, 0])
+        cyc = (tau.T * g.fc) % 1.0
+        assert np.max(np.abs(np.angle(np.exp(1j * (ph0 - 2 * np.pi * cyc))))) <= 1e-7
