@@ -7,8 +7,8 @@ anything here, and nothing here imports the library.
 from .sharing_admm import (Criterion, Eliminator, State, Result, RidgeSolver, sadmm, soft, real_form,
                            real_vec, forward, adjoint_re, objective, kkt, initial_state)
 from .fista import fista
-from .signal_model import operator_from_delays
+from .signal_model import operator_from_delays, backprojection, db_image
 
 __all__ = ["Criterion", "Eliminator", "State", "Result", "RidgeSolver", "sadmm", "soft", "real_form",
            "real_vec", "forward", "adjoint_re", "objective", "kkt", "initial_state", "fista",
-           "operator_from_delays"]
+           "operator_from_delays", "backprojection", "db_image"]
