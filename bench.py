@@ -54,6 +54,8 @@ def parse():
                     help="skip the learned-step cost measurement (elim 2 on the bench scene)")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the 16-scene batched measurement (Q=8, KM=2048, N=96x96)")
+    ap.add_argument("--no-factored", action="store_true",
+                    help="skip the factored-operator measurement (operators from round-trip delays)")
     ap.add_argument("--group-geoms", type=int, default=32,
                     help="geometries in the mixed-geometry batch group (16 scenes each); 0 skips it")
     return ap.parse_args()
@@ -322,6 +324,78 @@ def _tuning_gain(tunings):
     return float(np.mean(gains)) if gains else None
 
 
+def factored_measure(sc, lam, dev, stream, iters=100, reps=3):
+    """The bench workload with every operator set from its round-trip delays
+    (sadmm_set_operator_delays): the per-iteration forward and adjoint read the
+    factored tables C (K/16 per antenna and pixel) and D (16) and form each
+    entry as a product of two factors.  Iterations/s, per-phase times, the
+    FP32 throughput of the two products against the SIMT FMA peak, and the
+    stacked-iterate difference from the stored operator's run after the same
+    number of iterations from zero."""
+    import torch
+    import scenegen
+    from paper_2307_08606_gb300 import binding
+    g = sc.geom
+    s = binding.Solver(g.Q, g.M, g.K, g.N, 1.0, lam, stream=stream.cuda_stream, elim=0)
+    for q in range(g.Q):
+        s.set_operator_delays(q, scenegen.delays(g, q), g.fc, g.bw / g.K)
+    s.prepare()
+    y_dev = [torch.from_numpy(v).to(dev) for v in sc.y]
+    xg = torch.empty(g.N, dtype=torch.float32, device=dev)
+    for _ in range(2):
+        s.solve(y_dev, iters, out=xg)
+    s.set_profiling(True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        s.solve(y_dev, iters, out=xg)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    prof = s.profile()
+    s.set_profiling(False)
+    Xf = s.X()
+    bp_out = torch.empty(g.N, dtype=torch.float32, device=dev)
+
+    def bp_ms():
+        s.backprojection(y_dev, out=bp_out)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(5):
+            s.backprojection(y_dev, out=bp_out)
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t0) * 1e3 / 5
+
+    bp_factored = bp_ms()
+    s.set_products(1)
+    bp_stored = bp_ms()
+    s.solve(y_dev, iters, out=xg)
+    torch.cuda.synchronize()
+    Xs = s.X()
+    s.close()
+    phases = {k: (v[0] / v[1] if v[1] else None) for k, v in prof.items()}
+    flops = 8.0 * g.Q * g.KM * g.N                   # one complex multiply-add per entry and product
+    sm_peak = 152 * 128 * 2 * 2.07e9 / 1e12          # FP32 FMA lanes x 2 flops x max SM clock
+    out = {"workload": "bench scene, operators from round-trip delays (factored tables), plain FP32 SADMM",
+           "iters_per_s": iters * reps / (ms / 1e3), "ms_per_iteration": ms / (iters * reps),
+           "phases_ms_per_launch": phases,
+           "table_bytes_per_product": g.Q * g.M * (g.K // 16 + 16) * g.N * 8.0,
+           "stored_operator_bytes_per_product": g.Q * g.KM * g.N * 8.0,
+           "rel_diff_X_vs_stored": float(np.linalg.norm(Xf - Xs) / max(np.linalg.norm(Xs), 1e-30)),
+           "iterations_compared": iters,
+           "backprojection_ms": {"factored": bp_factored, "stored": bp_stored,
+                                 "what": "composite BP image sum_q |A_q^H y_q| through sadmm_backprojection "
+                                         "(host timer, device result)"}}
+    for k in ("forward", "adjoint_update"):
+        if phases.get(k):
+            ach = flops / (phases[k] / 1e3) / 1e12
+            out[k + "_roofline"] = {"bound": "alu", "achieved": ach, "peak": sm_peak, "unit": "TFLOP/s",
+                                    "frac": ach / sm_peak,
+                                    "peak_source": "152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz"}
+    return out
+
+
 def forms_measure(sc, lam, dev, stream, iters=400):
     """The chosen forms against plain FP32 on the bench scene, from the same
     cold start for the same number of iterations:
@@ -576,7 +650,7 @@ def main():
     per_launch_bytes = {
         "forward": g.Q * g.KM * g.N * bpe,
         "adjoint_update": g.Q * g.KM * g.N * bpe,
-        "spd_woodbury": g.Q * ((2 * g.KM // 64) * (2 * g.KM // 64 + 1) // 2) * 64 * 64 * 4.0,
+        "spd_woodbury": g.Q * ((2 * g.KM // 64) * (2 * g.KM // 64 + 1) // 2) * 64 * 64 * 8.0,   # (hi, lo) pairs
     }
     dom = max((k for k in prof if prof[k][1] > 0), key=lambda k: prof[k][0])
     dom_ms, dom_n = prof[dom]
@@ -608,6 +682,8 @@ def main():
         line["batched"] = batched_measure(args, dev, stream, rank)
     if args.group_geoms > 0:
         line["group"] = group_measure(args, dev, stream, rank)
+    if not args.no_factored and g.K % 16 == 0:
+        line["factored"] = factored_measure(sc, lam, dev, stream)
     if not args.no_learned:
         line["learned"] = learned_measure(sc, lam, dev, stream)
     if not args.no_forms:

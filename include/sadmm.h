@@ -145,6 +145,43 @@ int sadmm_set_stream(sadmm_t ctx, void* stream);
  * device pointer) into the context and invalidates sensor q's factor. */
 int sadmm_set_operator(sadmm_t ctx, int q, const float* A_q);
 
+/* Operator A_q from the signal model of Section II (Eq. 1) instead of its
+ * entries: receiver m, fast-time sample k and pixel n with round-trip delay
+ * tau[m][n] (seconds; M x N doubles, host or device, copied) give
+ * A_q[(m, k), n] = exp(j 2 pi tau[m][n] (f0 + k df)), row m K + k (f0 the chirp
+ * start frequency, df = BW / K the frequency step per sample).  The library
+ * forms A_q itself (phases in FP64, entries rounded to complex64, as
+ * sadmm_set_operator would take them; the factor and the fold use it) and
+ * the factors C[m][a][n] = exp(j 2 pi tau (f0 + 16 a df)) and
+ * D[m][b][n] = exp(j 2 pi tau b df), whose products are the entries
+ * k = 16 a + b.  While every sensor's operator was set this way (and the
+ * criterion's precision is 0), the per-iteration forward and adjoint products
+ * read C and D ((K/16 + 16) M N complex values instead of K M N) and form the
+ * entries on the fly; see sadmm_set_products.  Requires K = 16, 32, 64, 128,
+ * 256 or 512 and M <= 16 (SADMM_EINVAL otherwise); invalidates sensor q's
+ * factor. */
+int sadmm_set_operator_delays(sadmm_t ctx, int q, const double* tau, double f0, double df);
+
+/* Which operator representation the per-iteration products read:
+ * SADMM_PRODUCTS_AUTO (default): the factored tables when every sensor's
+ * operator came from sadmm_set_operator_delays and precision is 0, else the
+ * stored operator; SADMM_PRODUCTS_STORED: always the stored operator;
+ * SADMM_PRODUCTS_FACTORED: the tables (a solve returns SADMM_ENOTREADY if a
+ * sensor has none, SADMM_EINVAL if precision > 0). */
+/* Composite back-projection image out[n] = sum_q |a_{q,n}^H y_q| (N floats,
+ * host or device) from measurements y[0..Q-1] (K*M complex64 each, host or
+ * device): the BP comparison images of Section IV (Fig. 1), read as each
+ * sensor's matched filter taken in magnitude and added over the sensors.  It
+ * uses the operator representation the per-iteration products use (see
+ * sadmm_set_products) and leaves the solver state untouched.  Returns
+ * SADMM_ENOTREADY if an operator is missing. */
+int sadmm_backprojection(sadmm_t ctx, const float* const* y, float* out);
+
+#define SADMM_PRODUCTS_AUTO 0
+#define SADMM_PRODUCTS_STORED 1
+#define SADMM_PRODUCTS_FACTORED 2
+int sadmm_set_products(sadmm_t ctx, int mode);
+
 /* Computes the full-active-set factor of every sensor whose operator changed:
  * (rho I + mu B B^T)^{-1} if N > 2KM, else (rho I + mu B^T B)^{-1}, in FP64
  * (Gram, Cholesky, explicit inverse).  It is kept and reused by later solves.
@@ -342,6 +379,20 @@ int sadmm_forward_noalloc(const float* A, int KM, int N, const int* idx, int nid
  * product).  w: KM complex64 (KM even, <= 16384); g: nidx floats. */
 int sadmm_adjoint(const float* A, int KM, int N, const int* idx, int nidx, const float* w,
                   float* g, void* stream);
+
+/* The factored representation of sadmm_set_operator_delays at kernel level
+ * (device pointers).  sadmm_operator_tables: from tau (M x N doubles) writes
+ * A (N x KM complex64, may be NULL), C (M x K/16 x N complex64) and
+ * D (M x 16 x N complex64; C and D may both be NULL).  K = 16, 32, ..., 512
+ * (a power of two) for C and D. */
+int sadmm_operator_tables(const double* tau, int M, int K, int N, double f0, double df, float* A, float* C,
+                          float* D, void* stream);
+/* r = base - A_J v_J with A given by its factors C, D (as sadmm_forward; M <= 16). */
+int sadmm_forward_factored(const float* C, const float* D, int M, int K, int N, const int* idx, int nidx,
+                           const float* v, const float* base, float* r, void* stream);
+/* g[p] = Re(a_{idx[p]}^H w) with A given by its factors C, D (as sadmm_adjoint). */
+int sadmm_adjoint_factored(const float* C, const float* D, int M, int K, int N, const int* idx, int nidx,
+                           const float* w, float* g, void* stream);
 
 /* Factor of the x-update (Eq. 3, x_q-update) for the listed columns, in FP64:
  * if nidx > 2KM, F = (rho I + mu B_J B_J^T)^{-1} with B_J rows interleaved

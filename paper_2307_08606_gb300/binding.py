@@ -71,6 +71,12 @@ _SIGS = {
                                C.POINTER(Criterion), C.POINTER(_P)]),
     "sadmm_set_stream": (C.c_int, [_P, _P]),
     "sadmm_set_operator": (C.c_int, [_P, C.c_int, _P]),
+    "sadmm_set_operator_delays": (C.c_int, [_P, C.c_int, _P, C.c_double, C.c_double]),
+    "sadmm_set_products": (C.c_int, [_P, C.c_int]),
+    "sadmm_backprojection": (C.c_int, [_P, _P, _P]),
+    "sadmm_operator_tables": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, _P, _P, _P, _P]),
+    "sadmm_forward_factored": (C.c_int, [_P, _P, C.c_int, C.c_int, C.c_int, _P, C.c_int, _P, _P, _P, _P]),
+    "sadmm_adjoint_factored": (C.c_int, [_P, _P, C.c_int, C.c_int, C.c_int, _P, C.c_int, _P, _P, _P]),
     "sadmm_prepare": (C.c_int, [_P]),
     "sadmm_solve": (C.c_int, [_P, C.POINTER(_P), _P, C.c_int, C.c_double, C.POINTER(Stats)]),
     "sadmm_resume": (C.c_int, [_P, _P, C.c_int, C.c_double, C.POINTER(Stats)]),
@@ -239,6 +245,27 @@ class Solver:
         A = _as_c64(A)
         assert tuple(A.shape) == (self.N, self.KM), A.shape
         check(self.lib.sadmm_set_operator(self.h, q, _ptr(A)))
+
+    def set_operator_delays(self, q, tau, f0, df):
+        """Operator of sensor q from its round-trip delays tau (M, N) seconds:
+        A[(m, k), n] = exp(j 2 pi tau[m, n] (f0 + k df)) (sadmm_set_operator_delays)."""
+        if isinstance(tau, np.ndarray):
+            tau = np.ascontiguousarray(tau, dtype=np.float64)
+        assert tuple(tau.shape) == (self.M, self.N)
+        check(self.lib.sadmm_set_operator_delays(self.h, q, _ptr(tau), float(f0), float(df)))
+
+    def backprojection(self, y, out=None):
+        """Composite BP image sum_q |A_q^H y_q| (sadmm_backprojection); y: Q arrays of KM complex64."""
+        ys = [_as_c64(v) for v in y]
+        arr = (C.c_void_p * self.Q)(*[_ptr(v) for v in ys])
+        if out is None:
+            out = np.empty(self.N, dtype=np.float32)
+        check(self.lib.sadmm_backprojection(self.h, arr, _ptr(out)))
+        return out
+
+    def set_products(self, mode):
+        """0 auto (factored tables when every sensor has delays), 1 stored operator, 2 factored."""
+        check(self.lib.sadmm_set_products(self.h, int(mode)))
 
     def prepare(self):
         check(self.lib.sadmm_prepare(self.h))
@@ -528,6 +555,41 @@ def adjoint(A, idx, w, out=None, stream=0):
         out = torch.empty(int(idx.numel()), dtype=torch.float32, device=A.device)
     check(load().sadmm_adjoint(_ptr(A), KM, A.shape[0], _ptr(idx), int(idx.numel()), _ptr(w),
                                _ptr(out), C.c_void_p(stream)))
+    return out
+
+
+def operator_tables(tau, M, K, N, f0, df, with_entries=True, stream=0):
+    """Device tables of the factored operator from delays tau (M, N) float64 on
+    the device: returns (A (N, M K) complex64 or None, C (M, K/16, N), D (M, 16, N))."""
+    import torch
+    dev = tau.device
+    A = torch.empty((N, M * K), dtype=torch.complex64, device=dev) if with_entries else None
+    Ct = torch.empty((M, K // 16, N), dtype=torch.complex64, device=dev)
+    Dt = torch.empty((M, 16, N), dtype=torch.complex64, device=dev)
+    check(load().sadmm_operator_tables(_ptr(tau), M, K, N, float(f0), float(df), _ptr(A), _ptr(Ct), _ptr(Dt),
+                                       C.c_void_p(stream)))
+    return A, Ct, Dt
+
+
+def forward_factored(Ct, Dt, K, idx, v, base=None, out=None, stream=0):
+    """r = base - A_idx v_idx with A given by its factors (sadmm_forward_factored)."""
+    import torch
+    M, N = Ct.shape[0], Ct.shape[2]
+    if out is None:
+        out = torch.empty(M * K, dtype=torch.complex64, device=Ct.device)
+    check(load().sadmm_forward_factored(_ptr(Ct), _ptr(Dt), M, K, N, _ptr(idx), int(idx.numel()), _ptr(v),
+                                        _ptr(base), _ptr(out), C.c_void_p(stream)))
+    return out
+
+
+def adjoint_factored(Ct, Dt, K, idx, w, out=None, stream=0):
+    """g = Re(A_idx^H w) with A given by its factors (sadmm_adjoint_factored)."""
+    import torch
+    M, N = Ct.shape[0], Ct.shape[2]
+    if out is None:
+        out = torch.empty(int(idx.numel()), dtype=torch.float32, device=Ct.device)
+    check(load().sadmm_adjoint_factored(_ptr(Ct), _ptr(Dt), M, K, N, _ptr(idx), int(idx.numel()), _ptr(w),
+                                        _ptr(out), C.c_void_p(stream)))
     return out
 
 

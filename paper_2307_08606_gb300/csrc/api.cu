@@ -66,6 +66,11 @@ struct Sensor {
   int woodbury = 0;          // form in use
   int cnt = 0;               // |J_q| (host mirror)
   bool op_set = false;
+  // factored representation (sadmm_set_operator_delays)
+  double* tau = nullptr;       // M x N round-trip delays
+  float2* C = nullptr;         // M x K/16 x N
+  float2* D = nullptr;         // M x 16 x N
+  bool factored = false;
 };
 
 uint64_t constexpr kStateMagic = 0x31766174734d4453ull;   // "SDMstav1"
@@ -113,6 +118,19 @@ struct Ctx {
   bool corr_due = true;        // precision 3/4: refresh the lo-plane products next iteration
   int last_corr_k = 0;
   int split_kind() const { return (crit.precision == 1 || crit.precision == 3) ? kSplitBF16 : kSplitFP16; }
+  int products = SADMM_PRODUCTS_AUTO;
+  float2* bp_y = nullptr;      // back-projection scratch: Q x [y, -i y]
+  float* bp_g = nullptr;       // Q x [Re, Im] of A^H y
+  float* bp_out = nullptr;     // N
+  bool all_factored() const {
+    for (const Sensor& S : s)
+      if (!S.factored) return false;
+    return true;
+  }
+  // the per-iteration products read the factored tables
+  bool use_factored() const {
+    return products != SADMM_PRODUCTS_STORED && crit.precision == 0 && all_factored();
+  }
   bool periodic() const { return crit.precision >= 3; }
   // profiling: one event pair per (slot, phase); a slot is an iteration not
   // yet collected (one per iteration when the host synchronises each
@@ -318,6 +336,17 @@ int prepare(Ctx& c) {
     }
     if (!c.s[q].full_valid) qs.push_back(q);
   }
+  if (c.products == SADMM_PRODUCTS_FACTORED) {
+    if (c.crit.precision > 0) {
+      set_error("factored products need precision 0 (the split forms read the stored planes)");
+      return SADMM_EINVAL;
+    }
+    for (int q = 0; q < c.Q; ++q)
+      if (!c.s[q].factored) {
+        set_error("factored products requested but sensor %d has no delays (sadmm_set_operator_delays)", q);
+        return SADMM_ENOTREADY;
+      }
+  }
   if (qs.empty()) return SADMM_OK;
   std::vector<int> saved(c.Q);
   for (int q : qs) { saved[q] = c.s[q].cnt; c.s[q].cnt = c.N; }
@@ -428,35 +457,50 @@ int launch_iteration(Ctx& c, IterScalars* out) {
   std::vector<ColumnSet> fw;
   std::vector<SpdSet> spd_w, spd_p;
   std::vector<AdjointSet> adj_w, adj_p;
+  std::vector<FactoredSet> ffw, fadj_w, fadj_p;    // factored representation
+  const bool fac = c.use_factored();
   for (int q = 0; q < c.Q; ++q) {
     Sensor& S = c.s[q];
     if (S.cnt == 0) continue;
     fw.push_back(ColumnSet{S.A, S.J, S.cnt, q, nullptr, S.yp, S.r});
+    ffw.push_back(FactoredSet{S.C, S.D, S.J, S.cnt, q, nullptr, S.yp, S.r, nullptr, nullptr});
     const float2* F = S.fhl[S.cur];
     float2* part = c.spd_part + (size_t)q * c.spd_part_stride;
     if (S.woodbury) {
       spd_w.push_back(SpdSet{F, S.n, reinterpret_cast<const float*>(S.r), reinterpret_cast<float*>(S.w), nullptr, q,
                              part, 0});
       adj_w.push_back(AdjointSet{S.A, S.J, S.cnt, q, S.w, nullptr});
+      fadj_w.push_back(FactoredSet{S.C, S.D, S.J, S.cnt, q, nullptr, nullptr, nullptr, S.w, nullptr});
     } else {
       adj_p.push_back(AdjointSet{S.A, S.J, S.cnt, q, S.r, S.g});
+      fadj_p.push_back(FactoredSet{S.C, S.D, S.J, S.cnt, q, nullptr, nullptr, nullptr, S.r, S.g});
       spd_p.push_back(SpdSet{F, S.n, S.g, nullptr, S.J, q, part, 0});
     }
   }
   c.mark(0, true);
-  SADMM_TRY(launch_forward(fw.data(), (int)fw.size(), c.KM, kVAdmm, sv, c.partial, c.partial_cap, c.st));
+  if (fac)
+    SADMM_TRY(launch_factored_forward(ffw.data(), (int)ffw.size(), c.M, c.K, c.N, kVAdmm, sv, c.partial,
+                                      c.partial_cap, c.st));
+  else
+    SADMM_TRY(launch_forward(fw.data(), (int)fw.size(), c.KM, kVAdmm, sv, c.partial, c.partial_cap, c.st));
   c.mark(0, false);
   if (!spd_w.empty()) {
     c.mark(1, true);
     SADMM_TRY(launch_spd_apply(spd_w.data(), (int)spd_w.size(), false, sv, c.spd_err, c.st));
     c.mark(1, false);
     c.mark(2, true);
-    SADMM_TRY(launch_adjoint(adj_w.data(), (int)adj_w.size(), c.KM, true, sv, c.st));
+    if (fac)
+      SADMM_TRY(launch_factored_adjoint(fadj_w.data(), (int)fadj_w.size(), c.M, c.K, c.N, true, sv, c.st));
+    else
+      SADMM_TRY(launch_adjoint(adj_w.data(), (int)adj_w.size(), c.KM, true, sv, c.st));
     c.mark(2, false);
   }
   if (!spd_p.empty()) {
     c.mark(3, true);
-    SADMM_TRY(launch_adjoint(adj_p.data(), (int)adj_p.size(), c.KM, false, sv, c.st));
+    if (fac)
+      SADMM_TRY(launch_factored_adjoint(fadj_p.data(), (int)fadj_p.size(), c.M, c.K, c.N, false, sv, c.st));
+    else
+      SADMM_TRY(launch_adjoint(adj_p.data(), (int)adj_p.size(), c.KM, false, sv, c.st));
     c.mark(3, false);
     c.mark(4, true);
     SADMM_TRY(launch_spd_apply(spd_p.data(), (int)spd_p.size(), true, sv, c.spd_err, c.st));
@@ -869,6 +913,7 @@ int sadmm_create(int Q, int M, int K, int N, double rho, double lambda, const sa
   ctx->partial_cap = 0;
   for (int ns = 1; ns <= Q; ++ns) {  // any subset of sensors may be launched together
     ctx->partial_cap = std::max(ctx->partial_cap, forward_partial_bytes(ns, (int)KM, N));
+    if (factored_supported(K)) ctx->partial_cap = std::max(ctx->partial_cap, factored_partial_bytes(ns, M, K, N));
     if (c.precision > 0) ctx->partial_cap = std::max(ctx->partial_cap, split_partial_bytes(ns, (int)KM, N));
   }
   ctx->partial = (float2*)A(ctx->partial_cap);
@@ -925,6 +970,7 @@ int sadmm_set_operator(sadmm_t ctx, int q, const float* A_q) {
   SADMM_TRY(sadmm::valid_ctx(ctx));
   if (q < 0 || q >= ctx->Q || !A_q) { set_error("sadmm_set_operator: bad sensor or pointer"); return SADMM_EINVAL; }
   sadmm::Sensor& S = ctx->s[q];
+  S.factored = false;
   SADMM_CUDA_TRY(cudaMemcpyAsync(S.A, A_q, (size_t)ctx->N * ctx->KM * sizeof(float2), cudaMemcpyDefault, ctx->st));
   if (ctx->crit.precision > 0)
     SADMM_TRY(sadmm::launch_split_convert(reinterpret_cast<const float*>(S.A), (size_t)ctx->N * ctx->KM * 2,
@@ -932,6 +978,91 @@ int sadmm_set_operator(sadmm_t ctx, int q, const float* A_q) {
   SADMM_CUDA_TRY(cudaStreamSynchronize(ctx->st));
   S.op_set = true;
   S.full_valid = false;
+  return SADMM_OK;
+}
+
+int sadmm_set_operator_delays(sadmm_t ctx, int q, const double* tau, double f0, double df) {
+  using namespace sadmm;
+  SADMM_TRY(valid_ctx(ctx));
+  if (q < 0 || q >= ctx->Q || !tau || !std::isfinite(f0) || !std::isfinite(df)) {
+    set_error("sadmm_set_operator_delays: bad sensor, pointer or frequency");
+    return SADMM_EINVAL;
+  }
+  if (!factored_supported(ctx->K) || ctx->M > 16) {
+    set_error("sadmm_set_operator_delays: needs K = 16, 32, ..., 512 and M <= 16 (K=%d, M=%d)", ctx->K, ctx->M);
+    return SADMM_EINVAL;
+  }
+  Sensor& S = ctx->s[q];
+  const size_t MN = (size_t)ctx->M * ctx->N;
+  if (!S.tau) {
+    S.tau = (double*)ctx->dalloc(MN * sizeof(double));
+    S.C = (float2*)ctx->dalloc(MN * (ctx->K / kFacB) * sizeof(float2));
+    S.D = (float2*)ctx->dalloc(MN * kFacB * sizeof(float2));
+    if (!S.tau || !S.C || !S.D) { set_error("sadmm_set_operator_delays: device allocation failed"); return SADMM_ENOMEM; }
+  }
+  S.factored = false;
+  SADMM_CUDA_TRY(cudaMemcpyAsync(S.tau, tau, MN * sizeof(double), cudaMemcpyDefault, ctx->st));
+  SADMM_TRY(operator_tables(S.tau, ctx->M, ctx->K, ctx->N, f0, df, S.A, S.C, S.D, ctx->st));
+  if (ctx->crit.precision > 0)
+    SADMM_TRY(launch_split_convert(reinterpret_cast<const float*>(S.A), (size_t)ctx->N * ctx->KM * 2,
+                                   ctx->split_kind(), S.hi, S.lo, ctx->st));
+  SADMM_CUDA_TRY(cudaStreamSynchronize(ctx->st));
+  S.op_set = true;
+  S.full_valid = false;
+  S.factored = true;
+  return SADMM_OK;
+}
+
+int sadmm_backprojection(sadmm_t ctx, const float* const* y, float* out) {
+  using namespace sadmm;
+  SADMM_TRY(valid_ctx(ctx));
+  if (!y || !out) { set_error("sadmm_backprojection: bad arguments"); return SADMM_EINVAL; }
+  for (int q = 0; q < ctx->Q; ++q) {
+    if (!y[q]) { set_error("sadmm_backprojection: y[%d] is NULL", q); return SADMM_EINVAL; }
+    if (!ctx->s[q].op_set) { set_error("operator of sensor %d not set", q); return SADMM_ENOTREADY; }
+  }
+  const bool fac = ctx->use_factored();
+  if (!fac && ctx->KM > 16384) { set_error("sadmm_backprojection: KM > 16384 needs the factored operator"); return SADMM_EINVAL; }
+  const size_t KM = ctx->KM, N = ctx->N;
+  if (!ctx->bp_y) {
+    ctx->bp_y = (float2*)ctx->dalloc((size_t)ctx->Q * 2 * KM * sizeof(float2));
+    ctx->bp_g = (float*)ctx->dalloc((size_t)ctx->Q * 2 * N * sizeof(float));
+    ctx->bp_out = (float*)ctx->dalloc(N * sizeof(float));
+    if (!ctx->bp_y || !ctx->bp_g || !ctx->bp_out) { set_error("sadmm_backprojection: device allocation failed"); return SADMM_ENOMEM; }
+  }
+  std::vector<AdjointSet> as;
+  std::vector<FactoredSet> fs;
+  for (int q = 0; q < ctx->Q; ++q) {
+    float2* yq = ctx->bp_y + (size_t)q * 2 * KM;
+    SADMM_CUDA_TRY(cudaMemcpyAsync(yq, y[q], KM * sizeof(float2), cudaMemcpyDefault, ctx->st));
+    SADMM_TRY(launch_bp_rotate(yq, yq + KM, KM, ctx->st));
+    const Sensor& S = ctx->s[q];
+    for (int part = 0; part < 2; ++part) {
+      const float2* w = yq + part * KM;
+      float* g = ctx->bp_g + ((size_t)q * 2 + part) * N;
+      as.push_back(AdjointSet{S.A, ctx->iota, (int)N, q, w, g});
+      fs.push_back(FactoredSet{S.C, S.D, ctx->iota, (int)N, q, nullptr, nullptr, nullptr, w, g});
+    }
+  }
+  SolverView sv{};
+  for (size_t i0 = 0; i0 < as.size(); i0 += kMaxSets) {
+    const int n = (int)std::min<size_t>(kMaxSets, as.size() - i0);
+    if (fac) SADMM_TRY(launch_factored_adjoint(fs.data() + i0, n, ctx->M, ctx->K, ctx->N, false, sv, ctx->st));
+    else SADMM_TRY(launch_adjoint(as.data() + i0, n, ctx->KM, false, sv, ctx->st));
+  }
+  SADMM_TRY(launch_bp_combine(ctx->bp_g, ctx->Q, ctx->N, ctx->bp_out, ctx->st));
+  SADMM_CUDA_TRY(cudaMemcpyAsync(out, ctx->bp_out, N * sizeof(float), cudaMemcpyDefault, ctx->st));
+  SADMM_CUDA_TRY(cudaStreamSynchronize(ctx->st));
+  return SADMM_OK;
+}
+
+int sadmm_set_products(sadmm_t ctx, int mode) {
+  SADMM_TRY(sadmm::valid_ctx(ctx));
+  if (mode < SADMM_PRODUCTS_AUTO || mode > SADMM_PRODUCTS_FACTORED) {
+    sadmm::set_error("sadmm_set_products: mode %d is not one of 0, 1, 2", mode);
+    return SADMM_EINVAL;
+  }
+  ctx->products = mode;
   return SADMM_OK;
 }
 

@@ -95,6 +95,44 @@ struct ColumnSet {          // one sensor's column list for a batched launch
 int launch_forward(const ColumnSet* sets, int nsets, int KM, VMode mode, const SolverView& sv,
                    float2* partial, size_t partial_cap, cudaStream_t st);
 size_t forward_partial_bytes(int nsets, int KM, int max_cols);
+// out = base - sum over chunks of the double-float chunk partials
+// partial[set][chunk][plane][KM] (plane 0 high words, plane 1 low words).
+int launch_forward_reduce(const ColumnSet* sets, int nsets, int KM, int chunks, const float2* partial,
+                          cudaStream_t st);
+
+// The per-column scalar v of the forward product, by mode.
+__device__ __forceinline__ float v_of(VMode mode, const SolverView& sv, int q, int pix, const float* vexp) {
+  if (mode == kVExplicit) return vexp[pix];
+  const float xq = sv.x[(size_t)q * sv.N + pix];
+  if (mode == kVX) return xq;
+  if (mode == kVNegX) return -xq;
+  return xq - sv.xbar[pix] + sv.zbar[pix] - sv.s[pix];
+}
+
+// Factored operator (factored.cu): A[(m, k), n] = C[m][a][n] D[m][b][n] with
+// k = 16 a + b, C = exp(j 2 pi tau (f0 + 16 a df)), D = exp(j 2 pi tau b df).
+constexpr int kFacB = 16;
+struct FactoredSet {
+  const float2* C;          // M x K/16 x N (pixel fastest)
+  const float2* D;          // M x 16 x N
+  const int* idx;           // column (pixel) indices
+  int n;
+  int q;
+  const float* vexp;        // forward: explicit v (kVExplicit)
+  const float2* base;       // forward: base vector (KM complex) or null
+  float2* out;              // forward: KM complex output
+  const float2* w;          // adjoint: KM complex input
+  float* g;                 // adjoint: g[p] output (mode g)
+};
+bool factored_supported(int K);   // K = 16, 32, 64, 128, 256 or 512
+int operator_tables(const double* tau, int M, int K, int N, double f0, double df, float2* A, float2* C, float2* D,
+                    cudaStream_t st);
+int factored_chunks(int nsets, int M, int K, int max_cols);
+size_t factored_partial_bytes(int nsets, int M, int K, int max_cols);
+int launch_factored_forward(const FactoredSet* sets, int nsets, int M, int K, int N, VMode mode, const SolverView& sv,
+                            float2* partial, size_t partial_cap, cudaStream_t st);
+int launch_factored_adjoint(const FactoredSet* sets, int nsets, int M, int K, int N, bool update, const SolverView& sv,
+                            cudaStream_t st);
 
 struct AdjointSet {
   const float2* A;
@@ -148,6 +186,10 @@ struct SpdSet {
 int launch_spd_apply(const SpdSet* sets, int nsets, bool update, const SolverView& sv, int* err,
                      cudaStream_t st);
 
+// Back-projection helpers (elementwise.cu): out = -i y; out = sum_q |g_re + i g_im|
+// with g laid out per sensor as [re N][im N].
+int launch_bp_rotate(const float2* y, float2* out, size_t n, cudaStream_t st);
+int launch_bp_combine(const float* g, int Q, int N, float* out, cudaStream_t st);
 int launch_residuals(const SolverView& sv, const sadmm_criterion& c, double* partials,
                      unsigned int* ticket, IterScalars* out, int k_after, cudaStream_t st);
 int residual_blocks(int N);

@@ -260,6 +260,41 @@ int launch_ssc(const SolverView& sv, int* const* J, int* const* E, int* counts, 
   return SADMM_OK;
 }
 
+// ------------------------------------------------------- back-projection
+// out = -i y (KM complex per sensor, in place after the copy of y).
+__global__ void bp_rotate_kernel(const float2* __restrict__ y, float2* __restrict__ out, size_t n) {
+  const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (i < n) {
+    const float2 v = y[i];
+    out[i] = make_float2(v.y, -v.x);
+  }
+}
+
+// out[n] = sum_q |g_q,re[n] + i g_q,im[n]|, sensors in order.
+__global__ void bp_combine_kernel(const float* __restrict__ g, int Q, int N, float* __restrict__ out) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  float acc = 0.f;
+  for (int q = 0; q < Q; ++q) {
+    const float re = g[(size_t)q * 2 * N + n], im = g[(size_t)q * 2 * N + N + n];
+    acc += sqrtf(fmaf(re, re, im * im));
+  }
+  out[n] = acc;
+}
+
+int launch_bp_rotate(const float2* y, float2* out, size_t n, cudaStream_t st) {
+  if (n == 0) return SADMM_OK;
+  bp_rotate_kernel<<<div_up((long long)n, 256), 256, 0, st>>>(y, out, n);
+  SADMM_LAUNCH_CHECK();
+  return SADMM_OK;
+}
+
+int launch_bp_combine(const float* g, int Q, int N, float* out, cudaStream_t st) {
+  bp_combine_kernel<<<div_up(N, 256), 256, 0, st>>>(g, Q, N, out);
+  SADMM_LAUNCH_CHECK();
+  return SADMM_OK;
+}
+
 int launch_recompute_xbar(const SolverView& sv, cudaStream_t st) {
   xbar_kernel<<<div_up(sv.N, 256), 256, 0, st>>>(sv);
   SADMM_LAUNCH_CHECK();

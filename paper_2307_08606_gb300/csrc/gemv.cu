@@ -37,15 +37,6 @@ __device__ __forceinline__ float4 ld_stream(const float4* p) {
   return v;
 }
 
-__device__ __forceinline__ float v_of(VMode mode, const SolverView& sv, int q, int pix,
-                                      const float* vexp) {
-  if (mode == kVExplicit) return vexp[pix];
-  float xq = sv.x[(size_t)q * sv.N + pix];
-  if (mode == kVX) return xq;
-  if (mode == kVNegX) return -xq;
-  return xq - sv.xbar[pix] + sv.zbar[pix] - sv.s[pix];
-}
-
 __global__ void __launch_bounds__(kFwdThreads)
 forward_partial_kernel(const __grid_constant__ SetBlock<ColumnSet> sets, int KM, int chunks,
                        int cols_per_chunk, VMode mode, const __grid_constant__ SolverView sv,
@@ -272,6 +263,15 @@ int launch_forward(const ColumnSet* sets, int nsets, int KM, VMode mode, const S
   forward_partial_kernel<<<grid, kFwdThreads, 0, st>>>(blk, KM, chunks, per, mode, sv,
                                                        reinterpret_cast<float4*>(partial));
   SADMM_LAUNCH_CHECK();
+  return launch_forward_reduce(sets, nsets, KM, chunks, partial, st);
+}
+
+int launch_forward_reduce(const ColumnSet* sets, int nsets, int KM, int chunks, const float2* partial,
+                          cudaStream_t st) {
+  if (nsets <= 0) return SADMM_OK;
+  if (nsets > kMaxSets) { set_error("launch_forward_reduce: %d sets > %d", nsets, kMaxSets); return SADMM_EINVAL; }
+  SetBlock<ColumnSet> blk;
+  for (int i = 0; i < nsets; ++i) blk.v[i] = sets[i];
   dim3 g2(div_up(KM / 2, 64), nsets);                   // small blocks: one CTA per SM or more
   forward_reduce_kernel<<<g2, 64, 0, st>>>(blk, KM, chunks, reinterpret_cast<const float4*>(partial));
   SADMM_LAUNCH_CHECK();

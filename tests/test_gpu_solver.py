@@ -357,28 +357,41 @@ def test_full_size_first_iteration_matches_oracle(B, paper_scene):
     s.close()
 
 
-def test_full_size_iterations_match_oracle(B, paper_scene):
+@pytest.fixture(scope="module")
+def paper_ref(paper_scene):
+    sc, lam = paper_scene
+    iters = 5
+    return oracle.sadmm(sc.A, sc.y, 1.0, lam, oracle.Criterion(elim=0), iters=iters,
+                        snapshots=range(1, iters + 1))
+
+
+@pytest.mark.parametrize("representation", ["stored", "factored"])
+def test_full_size_iterations_match_oracle(B, paper_scene, paper_ref, representation):
     """The benchmark's workload at its full size (Q=8, KM=2048, N=128x128,
     rho=1, lambda=0.05 lambda_max, no elimination): all eight sensors over
     five iterations against the FP64 oracle at equal k, X and x_G within
     1e-4 relative after every iteration (the solver is resumed one iteration
-    at a time and compared with the oracle's snapshots)."""
+    at a time and compared with the oracle's snapshots).  Both operator
+    representations: the stored entries, and the factored tables built from
+    the round-trip delays (whose products form each entry from two factors)."""
     sc, lam = paper_scene
     g = sc.geom
     iters = 5
-    ref = oracle.sadmm(sc.A, sc.y, 1.0, lam, oracle.Criterion(elim=0), iters=iters,
-                       snapshots=range(1, iters + 1))
+    ref = paper_ref
     dev = torch.device("cuda:0")
     s = B.Solver(g.Q, g.M, g.K, g.N, 1.0, lam, elim=0)
     for q in range(g.Q):
-        s.set_operator(q, torch.from_numpy(sc.A[q]).to(dev))
+        if representation == "stored":
+            s.set_operator(q, torch.from_numpy(sc.A[q]).to(dev))
+        else:
+            s.set_operator_delays(q, scenegen.delays(g, q), g.fc, g.bw / g.K)
     xg, _ = s.solve([torch.from_numpy(v).to(dev) for v in sc.y], 1)
     for k in range(1, iters + 1):
         if k > 1:
             xg, _ = s.resume(1)
         want = ref.snapshots[k]
         err = _rel(s.X(), want.x)
-        print(f"k={k}: relative error of X {err:.2e}")
+        print(f"{representation} k={k}: relative error of X {err:.2e}")
         assert err <= TOL, k
     if np.any(ref.xG != 0):
         assert _rel(np.asarray(xg, dtype=np.float64), ref.xG) <= TOL
