@@ -112,34 +112,55 @@ forward_partial_kernel(const __grid_constant__ SetBlock<ColumnSet> sets, int KM,
   }
 }
 
-// out[r] = base[r] - sum_c partial[c][r], chunks summed in ascending order.
-__global__ void forward_reduce_kernel(const __grid_constant__ SetBlock<ColumnSet> sets, int KM,
-                                      int chunks, const float4* __restrict__ partial) {
+// out[r] = base[r] - sum_c partial[c][r].  Four threads per float4 of rows:
+// thread part p adds chunks p, p + 4, p + 8, ... in double-float, and the
+// four sums are added in the order 0, 1, 2, 3.
+constexpr int kRedParts = 4;
+constexpr int kRedRows = 64;                 // float4 rows per CTA
+
+__global__ void __launch_bounds__(kRedRows * kRedParts)
+forward_reduce_kernel(const __grid_constant__ SetBlock<ColumnSet> sets, int KM, int chunks,
+                      const float4* __restrict__ partial) {
   const ColumnSet& cs = sets.v[blockIdx.y];
-  const int row2 = blockIdx.x * blockDim.x + threadIdx.x;
-  if (row2 * 2 >= KM) return;
+  const int part = threadIdx.x % kRedParts;
+  const int row2 = blockIdx.x * kRedRows + threadIdx.x / kRedParts;
+  const bool live = row2 * 2 < KM;
   const size_t col4 = (size_t)KM / 2;
   const float4* p = partial + (size_t)blockIdx.y * chunks * 2 * col4 + row2;
   DF acc[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-  constexpr int kB = 4;                 // chunk loads issued ahead of their sums
-  for (int c0 = 0; c0 < chunks; c0 += kB) {
-    float4 h[kB], l[kB];
+  constexpr int kB = 3;                 // chunk loads issued ahead of their sums
+  if (live) {
+    for (int c0 = part; c0 < chunks; c0 += kB * kRedParts) {
+      float4 h[kB], l[kB];
 #pragma unroll
-    for (int u = 0; u < kB; ++u) {
-      h[u] = l[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (c0 + u < chunks) {
-        h[u] = p[(size_t)(c0 + u) * 2 * col4];
-        l[u] = p[(size_t)(c0 + u) * 2 * col4 + col4];
+      for (int u = 0; u < kB; ++u) {
+        const int c = c0 + u * kRedParts;
+        h[u] = l[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (c < chunks) {
+          h[u] = p[(size_t)c * 2 * col4];
+          l[u] = p[(size_t)c * 2 * col4 + col4];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kB; ++u) {
+        df_add(acc[0], DF{h[u].x, l[u].x});
+        df_add(acc[1], DF{h[u].y, l[u].y});
+        df_add(acc[2], DF{h[u].z, l[u].z});
+        df_add(acc[3], DF{h[u].w, l[u].w});
       }
     }
+  }
+  // parts 1, 2, 3 of this row join part 0, in order
+  DF tot[4] = {acc[0], acc[1], acc[2], acc[3]};
 #pragma unroll
-    for (int u = 0; u < kB; ++u) {
-      df_add(acc[0], DF{h[u].x, l[u].x});
-      df_add(acc[1], DF{h[u].y, l[u].y});
-      df_add(acc[2], DF{h[u].z, l[u].z});
-      df_add(acc[3], DF{h[u].w, l[u].w});
+  for (int o = 1; o < kRedParts; ++o) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const DF x{__shfl_down_sync(0xffffffffu, acc[k].hi, o), __shfl_down_sync(0xffffffffu, acc[k].lo, o)};
+      if (part == 0) df_add(tot[k], x);
     }
   }
+  if (!live || part != 0) return;
   float4 b = make_float4(0.f, 0.f, 0.f, 0.f);
   if (cs.base) b = reinterpret_cast<const float4*>(cs.base)[row2];
   // r = b - (sum), formed in double-float and rounded once
@@ -147,7 +168,7 @@ __global__ void forward_reduce_kernel(const __grid_constant__ SetBlock<ColumnSet
   float r[4];
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
-    DF d{-acc[k].hi, -acc[k].lo};
+    DF d{-tot[k].hi, -tot[k].lo};
     df_add1(d, bb[k]);
     r[k] = d.hi + d.lo;
   }
@@ -272,8 +293,9 @@ int launch_forward_reduce(const ColumnSet* sets, int nsets, int KM, int chunks, 
   if (nsets > kMaxSets) { set_error("launch_forward_reduce: %d sets > %d", nsets, kMaxSets); return SADMM_EINVAL; }
   SetBlock<ColumnSet> blk;
   for (int i = 0; i < nsets; ++i) blk.v[i] = sets[i];
-  dim3 g2(div_up(KM / 2, 64), nsets);                   // small blocks: one CTA per SM or more
-  forward_reduce_kernel<<<g2, 64, 0, st>>>(blk, KM, chunks, reinterpret_cast<const float4*>(partial));
+  dim3 g2(div_up(KM / 2, kRedRows), nsets);
+  forward_reduce_kernel<<<g2, kRedRows * kRedParts, 0, st>>>(blk, KM, chunks,
+                                                            reinterpret_cast<const float4*>(partial));
   SADMM_LAUNCH_CHECK();
   return SADMM_OK;
 }

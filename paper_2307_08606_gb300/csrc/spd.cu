@@ -16,9 +16,11 @@
 // block row J.  Persistent CTAs (six per SM, so that one CTA's copy overlaps
 // the others' arithmetic) pull tiles with one bulk asynchronous copy each
 // (cp.async.bulk into shared memory, completion on an mbarrier), then 64
-// threads form the row sums and 64 the column sums of the
-// tile, reading it along diagonals so that shared-memory accesses do not
-// conflict.  Per-tile partial sums (pairs) go to a scratch buffer; a second
+// threads form the row sums and 64 the column sums of the tile: the row
+// threads read column pairs as one 16-byte load along skewed diagonals, the
+// column threads walk the rows in order (their loads hit distinct banks by
+// column and their u values are broadcasts), so that shared-memory accesses
+// do not conflict.  Per-tile partial sums (pairs) go to a scratch buffer; a second
 // kernel adds them in a fixed order and applies the epilogue.
 #include "common.cuh"
 #include "symtile.cuh"
@@ -43,7 +45,7 @@ spd_tile_kernel(const __grid_constant__ SetBlock<SpdSet> sets, int nsets, int it
   extern __shared__ __align__(128) unsigned char smem_raw[];
   float2* tile = reinterpret_cast<float2*>(smem_raw);           // 64 x 64 pairs
   __shared__ __align__(8) uint64_t bar;
-  __shared__ float s_u[2][kT];                                  // u_I, u_J
+  __shared__ __align__(16) float s_u[2][kT];                    // u_I, u_J
   const int tid = threadIdx.x;
   const int lt = tid;                                            // < 64: row lt, else column lt - 64
   if ((int)blockIdx.x >= items) return;
@@ -79,24 +81,36 @@ spd_tile_kernel(const __grid_constant__ SetBlock<SpdSet> sets, int nsets, int it
     }
     DF acc0{0.f, 0.f}, acc1{0.f, 0.f};
     if (lt < kT) {
-      // row r of F_IJ times u_J, read along the diagonal (r, (r + c) mod 64)
+      // row r of F_IJ times u_J, two columns per 16-byte load: pairs
+      // (b, b + 1) with b = (2r + c) mod 64, so that the eight threads of a
+      // quarter-warp hit eight different bank groups
       const float* uJ = s_u[1];
+      const float4* row = reinterpret_cast<const float4*>(tile + r * kT);
 #pragma unroll 8
-      for (int c = 0; c < kT; c += 2) {
-        const int c0 = (r + c) & (kT - 1), c1 = (r + c + 1) & (kT - 1);
-        const float2 f0 = tile[r * kT + c0], f1 = tile[r * kT + c1];
-        df_acc(acc0, f0.x, f0.y, uJ[c0]);
-        df_acc(acc1, f1.x, f1.y, uJ[c1]);
+      for (int c = 0; c < kT; c += 4) {
+        const int b0 = (2 * r + c) & (kT - 2), b1 = (2 * r + c + 2) & (kT - 2);
+        const float4 f0 = row[b0 >> 1], f1 = row[b1 >> 1];
+        const float2 u0 = *reinterpret_cast<const float2*>(uJ + b0);
+        const float2 u1 = *reinterpret_cast<const float2*>(uJ + b1);
+        df_acc(acc0, f0.x, f0.y, u0.x);
+        df_acc(acc0, f0.z, f0.w, u0.y);
+        df_acc(acc1, f1.x, f1.y, u1.x);
+        df_acc(acc1, f1.z, f1.w, u1.y);
       }
     } else if (I != J) {
-      // column r of F_IJ times u_I (the transposed contribution to block row J)
+      // column r of F_IJ times u_I (the transposed contribution to block row
+      // J): every thread reads row i of the tile at its own column, so the
+      // loads are conflict-free and u_I[i] is a broadcast
       const float* uI = s_u[0];
-#pragma unroll 8
-      for (int c = 0; c < kT; c += 2) {
-        const int r0 = (r + c) & (kT - 1), r1 = (r + c + 1) & (kT - 1);
-        const float2 f0 = tile[r0 * kT + r], f1 = tile[r1 * kT + r];
-        df_acc(acc0, f0.x, f0.y, uI[r0]);
-        df_acc(acc1, f1.x, f1.y, uI[r1]);
+#pragma unroll 4
+      for (int i = 0; i < kT; i += 4) {
+        const float4 u4 = *reinterpret_cast<const float4*>(uI + i);
+        const float2 f0 = tile[i * kT + r], f1 = tile[(i + 1) * kT + r];
+        const float2 f2 = tile[(i + 2) * kT + r], f3 = tile[(i + 3) * kT + r];
+        df_acc(acc0, f0.x, f0.y, u4.x);
+        df_acc(acc1, f1.x, f1.y, u4.y);
+        df_acc(acc0, f2.x, f2.y, u4.z);
+        df_acc(acc1, f3.x, f3.y, u4.w);
       }
     }
     df_add(acc0, acc1);

@@ -437,3 +437,29 @@ def test_backprojection_pins():
     assert np.allclose(oracle.backprojection(A, yr), two, rtol=1e-12)
     d = oracle.db_image(bp)
     assert d[n0] == 0.0 and d.min() >= -30.0
+
+
+def test_golden_limit_is_optimal():
+    """The stored limit x_G* (tests/golden/resolved_32_limit.json, written by
+    tests/golden/make_limits.py from the oracle) certified from x_G* alone,
+    independently of the iteration that produced it: on this well-posed
+    workload every B_q^T B_q is invertible, so the stationarity conditions of
+    Eq. 2 give x_q = H_q (mu B_q^T y_q - nu) with H_q = (mu B_q^T B_q)^{-1}, and
+    sum_q x_q = x_G* fixes nu = (sum_q H_q)^{-1} (sum_q H_q mu B_q^T y_q - x_G*);
+    x_G* is optimal iff that nu is a subgradient of lambda ||.||_1 at x_G*."""
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", "resolved_32_limit.json")) as f:
+        d = json.load(f)
+    sc = scenegen.build_scene(d["scene"], seed=d["seed"])
+    lam, mu = d["lam"], d["mu"]
+    assert lam == pytest.approx(d["lam_frac"] * scenegen.lambda_max(sc.A, sc.y), rel=1e-12)
+    xg = np.array(d["xG"])
+    B = [oracle.real_form(a) for a in sc.A]
+    Hs = [np.linalg.inv(mu * (Bq.T @ Bq)) for Bq in B]
+    rhs = sum(H @ (mu * (Bq.T @ oracle.real_vec(yq))) for H, Bq, yq in zip(Hs, B, sc.y)) - xg
+    nu = np.linalg.solve(sum(Hs), rhs)
+    supp = xg != 0
+    assert supp.any() and not supp.all()
+    assert np.max(np.abs(nu)) <= lam * (1 + 1e-6)
+    assert np.max(np.abs(nu[supp] - lam * np.sign(xg[supp]))) <= 1e-6 * lam
