@@ -54,6 +54,8 @@ def parse():
                     help="skip the learned-step cost measurement (elim 2 on the bench scene)")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the 16-scene batched measurement (Q=8, KM=2048, N=96x96)")
+    ap.add_argument("--no-accuracy", action="store_true",
+                    help="skip the time-to-accuracy measurement on the well-posed 32x32 workload")
     ap.add_argument("--no-factored", action="store_true",
                     help="skip the factored-operator measurement (operators from round-trip delays)")
     ap.add_argument("--group-geoms", type=int, default=32,
@@ -396,6 +398,127 @@ def factored_measure(sc, lam, dev, stream, iters=100, reps=3):
     return out
 
 
+def accuracy_measure(dev, stream):
+    """Time to accuracy on the well-posed 32x32 workload (resolved_32, seed 20,
+    rho = 100, lambda = 0.05 lambda_max): for each form, the fewest
+    iterations from zero whose x_G is within 1e-3 (relative) of the FP64
+    oracle's limit stored in tests/golden/resolved_32_limit.json, and the
+    device time of a solve of that many iterations (the factor, computed once
+    per operator, is reported beside it)."""
+    import torch
+    import scenegen
+    from scenegen import radar
+    from paper_2307_08606_gb300 import binding
+    with open(os.path.join(ROOT, "tests", "golden", "resolved_32_limit.json")) as f:
+        gold = json.load(f)
+    sc = scenegen.build_scene(gold["scene"], seed=gold["seed"])
+    g = sc.geom
+    rho, lam = gold["rho"], gold["lam"]
+    xstar = np.array(gold["xG"])
+    y_dev = [torch.from_numpy(v).to(dev) for v in sc.y]
+    forms = {
+        "plain_fp32": dict(kw=dict(elim=0), delays=False),
+        "factored": dict(kw=dict(elim=0), delays=True),
+        "bf16_hi_corr4": dict(kw=dict(elim=0, precision=3, correct_every=4), delays=False),
+        "asadmm_fp32": dict(kw=dict(elim=1), delays=False),
+    }
+    out = {"workload": "resolved_32 seed 20 (Q=4, M=32, K=32, N=32x32; rho=100, lambda=0.05 lambda_max)",
+           "reference": "FP64 oracle limit (tests/golden/resolved_32_limit.json, KKT residuals <= 5e-14)",
+           "target_rel_error": 1e-3}
+    for name, spec in forms.items():
+        s = binding.Solver(g.Q, g.M, g.K, g.N, rho, lam, stream=stream.cuda_stream, **spec["kw"])
+        for q in range(g.Q):
+            if spec["delays"]:
+                s.set_operator_delays(q, scenegen.delays(g, q), g.fc, g.bw / g.K)
+            else:
+                s.set_operator(q, torch.from_numpy(sc.A[q]).to(dev))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s.prepare()
+        torch.cuda.synchronize()
+        factor_ms = (time.perf_counter() - t0) * 1e3
+
+        def err(k):
+            xg, _ = s.solve(y_dev, k)
+            return float(np.linalg.norm(xg - xstar) / np.linalg.norm(xstar))
+
+        k, e = 8, err(8)
+        while e > 1e-3 and k < 8192:
+            k *= 2
+            e = err(k)
+        lo, hi = k // 2, k
+        if e <= 1e-3:
+            while hi - lo > 1:
+                mid = (lo + hi) // 2
+                if err(mid) <= 1e-3:
+                    hi = mid
+                else:
+                    lo = mid
+            k = hi
+            e = err(k)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(3):
+                s.solve(y_dev, k)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / 3
+            out[name] = {"iterations": k, "ms": ms, "rel_error": e, "factor_ms": factor_ms}
+        else:
+            out[name] = {"iterations": None, "rel_error_at_8192": e, "factor_ms": factor_ms}
+        s.close()
+    # the batched form: this scene and 15 more of the same geometry (other
+    # seeds) iterate together; iterations until this scene is within 1e-3
+    Ys, lams = [np.stack(sc.y)], [lam]
+    for sd in range(21, 36):
+        o = scenegen.build_scene(gold["scene"], seed=sd)
+        Ys.append(np.stack(o.y))
+        lams.append(gold["lam_frac"] * scenegen.lambda_max(o.A, o.y))
+    Yt = torch.from_numpy(np.stack(Ys)).to(dev)
+    bs = binding.BatchSolver(g.Q, g.M, g.K, g.N, rho, lams, stream=stream.cuda_stream)
+    for q in range(g.Q):
+        bs.set_operator(q, torch.from_numpy(sc.A[q]).to(dev))
+
+    def berr(k):
+        xg, _ = bs.solve(Yt, k)
+        return float(np.linalg.norm(xg[0] - xstar) / np.linalg.norm(xstar))
+
+    k, e = 8, berr(8)
+    while e > 1e-3 and k < 8192:
+        k *= 2
+        e = berr(k)
+    if e <= 1e-3:
+        lo, hi = k // 2, k
+        while hi - lo > 1:
+            mid = (lo + hi) // 2
+            if berr(mid) <= 1e-3:
+                hi = mid
+            else:
+                lo = mid
+        k = hi
+        e = berr(k)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(3):
+            bs.solve(Yt, k)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 3
+        out["batched_16"] = {"iterations": k, "ms": ms, "ms_per_scene": ms / 16, "rel_error": e,
+                             "scenes": "this scene and seeds 21-35 of the same geometry"}
+    else:
+        out["batched_16"] = {"iterations": None, "rel_error_at_8192": e}
+    bs.close()
+    base = out["plain_fp32"].get("ms")
+    for name in list(forms) + ["batched_16"]:
+        t = out[name].get("ms_per_scene", out[name].get("ms"))
+        if base and t:
+            out[name]["speedup_vs_plain_fp32"] = base / t
+    return out
+
+
 def forms_measure(sc, lam, dev, stream, iters=400):
     """The chosen forms against plain FP32 on the bench scene, from the same
     cold start for the same number of iterations:
@@ -684,6 +807,8 @@ def main():
         line["group"] = group_measure(args, dev, stream, rank)
     if not args.no_factored and g.K % 16 == 0:
         line["factored"] = factored_measure(sc, lam, dev, stream)
+    if not args.no_accuracy:
+        line["time_to_accuracy"] = accuracy_measure(dev, stream)
     if not args.no_learned:
         line["learned"] = learned_measure(sc, lam, dev, stream)
     if not args.no_forms:

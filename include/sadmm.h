@@ -158,8 +158,7 @@ int sadmm_set_operator(sadmm_t ctx, int q, const float* A_q);
  * criterion's precision is 0), the per-iteration forward and adjoint products
  * read C and D ((K/16 + 16) M N complex values instead of K M N) and form the
  * entries on the fly; see sadmm_set_products.  Requires K = 16, 32, 64, 128,
- * 256 or 512 and M <= 16 (SADMM_EINVAL otherwise); invalidates sensor q's
- * factor. */
+ * 256 or 512 (SADMM_EINVAL otherwise); invalidates sensor q's factor. */
 int sadmm_set_operator_delays(sadmm_t ctx, int q, const double* tau, double f0, double df);
 
 /* Which operator representation the per-iteration products read:
@@ -387,10 +386,11 @@ int sadmm_adjoint(const float* A, int KM, int N, const int* idx, int nidx, const
  * (a power of two) for C and D. */
 int sadmm_operator_tables(const double* tau, int M, int K, int N, double f0, double df, float* A, float* C,
                           float* D, void* stream);
-/* r = base - A_J v_J with A given by its factors C, D (as sadmm_forward; M <= 16). */
+/* r = base - A_J v_J with A given by its factors C, D (as sadmm_forward). */
 int sadmm_forward_factored(const float* C, const float* D, int M, int K, int N, const int* idx, int nidx,
                            const float* v, const float* base, float* r, void* stream);
-/* g[p] = Re(a_{idx[p]}^H w) with A given by its factors C, D (as sadmm_adjoint). */
+/* g[p] = Re(a_{idx[p]}^H w) with A given by its factors C, D (as sadmm_adjoint;
+ * M K <= 16384). */
 int sadmm_adjoint_factored(const float* C, const float* D, int M, int K, int N, const int* idx, int nidx,
                            const float* w, float* g, void* stream);
 

@@ -988,8 +988,8 @@ int sadmm_set_operator_delays(sadmm_t ctx, int q, const double* tau, double f0, 
     set_error("sadmm_set_operator_delays: bad sensor, pointer or frequency");
     return SADMM_EINVAL;
   }
-  if (!factored_supported(ctx->K) || ctx->M > 16) {
-    set_error("sadmm_set_operator_delays: needs K = 16, 32, ..., 512 and M <= 16 (K=%d, M=%d)", ctx->K, ctx->M);
+  if (!factored_supported(ctx->K)) {
+    set_error("sadmm_set_operator_delays: needs K = 16, 32, 64, 128, 256 or 512 (K=%d)", ctx->K);
     return SADMM_EINVAL;
   }
   Sensor& S = ctx->s[q];

@@ -242,7 +242,7 @@ factored_forward_kernel(const __grid_constant__ SetBlock<FactoredSet> sets, int 
 // ---------------------------------------------------------------- adjoint
 // grid (pixel groups of 128, sets); 4 warps, one lane per pixel; every lane
 // runs all M antennas in order.
-constexpr int kMaxM = 16;
+constexpr int kMaxKM = 16384;                // w (M K complex) staged in shared memory
 constexpr int kAdjPix = 128;
 
 template <int K1>
@@ -323,7 +323,7 @@ int launch_adjoint_k1(const SetBlock<FactoredSet>& blk, int nsets, int M, int N,
   static bool configured = false;
   if (!configured) {
     SADMM_CUDA_TRY(cudaFuncSetAttribute(factored_adjoint_kernel<K1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        kMaxM * K1 * kFacB * (int)sizeof(float2)));
+                                        kMaxKM * (int)sizeof(float2)));
     configured = true;
   }
   factored_adjoint_kernel<K1><<<dim3(div_up(max_cols, kAdjPix), nsets), kAdjPix, smem, st>>>(blk, M, N, update, sv);
@@ -426,8 +426,8 @@ int launch_factored_forward(const FactoredSet* sets, int nsets, int M, int K, in
 int launch_factored_adjoint(const FactoredSet* sets, int nsets, int M, int K, int N, bool update, const SolverView& sv,
                             cudaStream_t st) {
   if (nsets <= 0) return SADMM_OK;
-  if (nsets > kMaxSets || !factored_supported(K) || M < 1 || M > kMaxM) {
-    set_error("launch_factored_adjoint: bad sizes (M up to %d, K = 16, 32, ..., 512)", kMaxM);
+  if (nsets > kMaxSets || !factored_supported(K) || M < 1 || M * K > kMaxKM) {
+    set_error("launch_factored_adjoint: bad sizes (M K up to %d, K = 16, 32, ..., 512)", kMaxKM);
     return SADMM_EINVAL;
   }
   SetBlock<FactoredSet> blk;
@@ -487,7 +487,7 @@ int sadmm_forward_factored(const float* C, const float* D, int M, int K, int N, 
 int sadmm_adjoint_factored(const float* C, const float* D, int M, int K, int N, const int* idx, int nidx,
                            const float* w, float* g, void* stream) {
   using namespace sadmm;
-  if (!C || !D || !w || M <= 0 || M > 16 || !factored_supported(K) || N <= 0 || nidx < 0 ||
+  if (!C || !D || !w || M <= 0 || !factored_supported(K) || M * K > 16384 || N <= 0 || nidx < 0 ||
       (nidx > 0 && (!idx || !g))) {
     set_error("sadmm_adjoint_factored: bad arguments");
     return SADMM_EINVAL;

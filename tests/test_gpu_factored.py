@@ -80,7 +80,7 @@ def test_tables_match_signal_model(B, M, K, nx):
 
 
 @pytest.mark.parametrize("M,K,nx,nidx", [(4, 64, 32, 700), (8, 256, 64, 3000), (2, 16, 24, 577),
-                                         (3, 512, 16, 256), (4, 64, 32, 0)])
+                                         (3, 512, 16, 256), (4, 64, 32, 0), (32, 32, 16, 200)])
 def test_factored_forward_matches_oracle(B, M, K, nx, nidx):
     g = _geom(M, K, nx)
     dev = torch.device("cuda:0")
@@ -105,7 +105,7 @@ def test_factored_forward_matches_oracle(B, M, K, nx, nidx):
 
 
 @pytest.mark.parametrize("M,K,nx,nidx", [(4, 64, 32, 700), (8, 256, 64, 4096), (16, 16, 12, 100),
-                                         (2, 512, 16, 33)])
+                                         (2, 512, 16, 33), (32, 32, 16, 200)])
 def test_factored_adjoint_matches_oracle(B, M, K, nx, nidx):
     g = _geom(M, K, nx)
     dev = torch.device("cuda:0")
