@@ -21,9 +21,11 @@
 //            product's reduction.
 //   adjoint  g_n = sum_m sum_a Re(conj(C[m][a][n]) t_a),
 //            t_a = sum_b conj(D[m][b][n]) w[m][16a+b]:
-//            one lane per pixel, antennas in order with the next antenna's D
-//            row loaded ahead; the 16-term sums t_a are FP32 and the (m, a)
-//            terms go into a double-float accumulator.
+//            one lane per pixel, antennas in order; 64 registers a thread,
+//            so that every pixel of a paper-scale launch is resident at once
+//            and other warps cover each warp's table loads; the 16-term sums
+//            t_a are FP32 and the (m, a) terms go into a double-float
+//            accumulator.
 // The tables are pixel-fastest ([m][a][n], [m][b][n]), so a warp's loads
 // for consecutive pixels are contiguous.
 #include "common.cuh"
@@ -84,28 +86,30 @@ __global__ void op_factors_kernel(const double* __restrict__ tau, int M, int K, 
 }
 
 // ---------------------------------------------------------------- forward
-// grid (chunks, M, sets); NT = max(32, 8 K1) threads, K1 = K/16: thread
-// (a, bp) = (t / 8, t % 8) forms rows 16 a + 2 bp and 16 a + 2 bp + 1 of
-// antenna m.  K1 is a template parameter so that index arithmetic is shifts
-// and the loops unroll.
+// grid (chunks, M, sets); K1 = K/16 is a template parameter so that index
+// arithmetic is shifts and the loops unroll.  Thread (h, bp) = (t / 8, t % 8)
+// forms rows 16 a + 2 bp and 16 a + 2 bp + 1 of antenna m for AB values of
+// a (a = h and, when AB = 2, a = h + K1/2): each 16-byte shared-memory load
+// of a table pair then feeds 8 AB multiply-adds.
 template <int K1>
 struct FwdCfg {
-  static constexpr int NT = K1 * 8 > 32 ? K1 * 8 : 32;
-  static constexpr int P = K1 >= 8 ? 64 : 32;                    // pixels per stage
+  static constexpr int AB = K1 >= 2 ? 2 : 1;                     // values of a per thread
+  static constexpr int NT = K1 * 8 / AB > 32 ? K1 * 8 / AB : 32;
+  static constexpr int P = 32;                                    // pixels per stage
   static constexpr int CE = (K1 * P + NT - 1) / NT;              // C elements a thread stages
   static constexpr int DE = (kFacB * P + NT - 1) / NT;           // D elements a thread stages
 };
 
 template <int K1>
-__global__ void __launch_bounds__(FwdCfg<K1>::NT, 768 / FwdCfg<K1>::NT)
+__global__ void __launch_bounds__(FwdCfg<K1>::NT, 640 / FwdCfg<K1>::NT)
 factored_forward_kernel(const __grid_constant__ SetBlock<FactoredSet> sets, int M, int N, int chunks, int per,
                         VMode mode, const __grid_constant__ SolverView sv, float2* __restrict__ partial) {
   using Cf = FwdCfg<K1>;
-  constexpr int NT = Cf::NT, P = Cf::P, CE = Cf::CE, DE = Cf::DE, K = K1 * kFacB;
+  constexpr int NT = Cf::NT, P = Cf::P, CE = Cf::CE, DE = Cf::DE, AB = Cf::AB, K = K1 * kFacB;
   const FactoredSet& fs = sets.v[blockIdx.z];
   const int m = blockIdx.y, c = blockIdx.x;
-  const int t = threadIdx.x, a = t >> 3, bp = t & 7;
-  const bool owner = t < K1 * 8;
+  const int t = threadIdx.x, h = t >> 3, bp = t & 7;
+  const bool owner = t < K1 * 8 / AB;
   const int p0 = c * per, p1 = min(fs.n, p0 + per);
   const int nst = p1 > p0 ? (p1 - p0 + P - 1) / P : 0;
   // v_n C[m][a][n] by rows of a (pixel pairs read as one 16-byte load), and
@@ -149,7 +153,11 @@ factored_forward_kernel(const __grid_constant__ SetBlock<FactoredSet> sets, int 
       if (e < kFacB * P) s_d[buf][p][bb] = rd[j];
     }
   };
-  DF acc[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};   // (re, im) of rows 2bp, 2bp + 1
+  DF acc[AB][4];                                                  // (re, im) of rows 2bp, 2bp + 1, per a
+#pragma unroll
+  for (int j = 0; j < AB; ++j)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) acc[j][i] = DF{0.f, 0.f};
   if (nst > 0) {
     // prologue: stage 0 into buffer 0, stage 1's pixels into s_pix[1]
     for (int i = t; i < P; i += NT) {
@@ -180,44 +188,50 @@ factored_forward_kernel(const __grid_constant__ SetBlock<FactoredSet> sets, int 
       nv = v_of(mode, sv, fs.q, npix, fs.vexp);
     }
     if (owner) {
-      float t0r = 0.f, t0i = 0.f, t1r = 0.f, t1i = 0.f;
-      float u0r = 0.f, u0i = 0.f, u1r = 0.f, u1i = 0.f;          // second chain: odd pixels
-      const float2* su = &s_u[b][a][0];
+      // per value of a: rows (2bp, 2bp + 1) x pixels (even, odd) -> 8 sums
+      float tt[AB][8];
+#pragma unroll
+      for (int j = 0; j < AB; ++j)
+#pragma unroll
+        for (int i = 0; i < 8; ++i) tt[j][i] = 0.f;
       int p = 0;
 #pragma unroll 2
       for (; p + 1 < np; p += 2) {
-        const float4 uw = *reinterpret_cast<const float4*>(su + p);            // pixels p, p + 1
         const float4 dx = *reinterpret_cast<const float4*>(&s_d[b][p][2 * bp]);     // D_{2bp}, D_{2bp+1} at p
         const float4 dy = *reinterpret_cast<const float4*>(&s_d[b][p + 1][2 * bp]); // ... at p + 1
-        const float2 u = make_float2(uw.x, uw.y), w = make_float2(uw.z, uw.w);
-        const float2 x0 = make_float2(dx.x, dx.y), x1 = make_float2(dx.z, dx.w);
-        const float2 y0 = make_float2(dy.x, dy.y), y1 = make_float2(dy.z, dy.w);
-        t0r = fmaf(u.x, x0.x, t0r); t0r = fmaf(-u.y, x0.y, t0r);
-        t0i = fmaf(u.x, x0.y, t0i); t0i = fmaf(u.y, x0.x, t0i);
-        t1r = fmaf(u.x, x1.x, t1r); t1r = fmaf(-u.y, x1.y, t1r);
-        t1i = fmaf(u.x, x1.y, t1i); t1i = fmaf(u.y, x1.x, t1i);
-        u0r = fmaf(w.x, y0.x, u0r); u0r = fmaf(-w.y, y0.y, u0r);
-        u0i = fmaf(w.x, y0.y, u0i); u0i = fmaf(w.y, y0.x, u0i);
-        u1r = fmaf(w.x, y1.x, u1r); u1r = fmaf(-w.y, y1.y, u1r);
-        u1i = fmaf(w.x, y1.y, u1i); u1i = fmaf(w.y, y1.x, u1i);
+#pragma unroll
+        for (int j = 0; j < AB; ++j) {
+          const float4 uw = *reinterpret_cast<const float4*>(&s_u[b][h + j * (K1 / 2)][p]);  // pixels p, p + 1
+          float* q = tt[j];
+          q[0] = fmaf(uw.x, dx.x, q[0]); q[0] = fmaf(-uw.y, dx.y, q[0]);
+          q[1] = fmaf(uw.x, dx.y, q[1]); q[1] = fmaf(uw.y, dx.x, q[1]);
+          q[2] = fmaf(uw.x, dx.z, q[2]); q[2] = fmaf(-uw.y, dx.w, q[2]);
+          q[3] = fmaf(uw.x, dx.w, q[3]); q[3] = fmaf(uw.y, dx.z, q[3]);
+          q[4] = fmaf(uw.z, dy.x, q[4]); q[4] = fmaf(-uw.w, dy.y, q[4]);
+          q[5] = fmaf(uw.z, dy.y, q[5]); q[5] = fmaf(uw.w, dy.x, q[5]);
+          q[6] = fmaf(uw.z, dy.z, q[6]); q[6] = fmaf(-uw.w, dy.w, q[6]);
+          q[7] = fmaf(uw.z, dy.w, q[7]); q[7] = fmaf(uw.w, dy.z, q[7]);
+        }
       }
       if (p < np) {
-        const float2 u = su[p];
         const float4 dx = *reinterpret_cast<const float4*>(&s_d[b][p][2 * bp]);
-        const float2 x0 = make_float2(dx.x, dx.y), x1 = make_float2(dx.z, dx.w);
-        t0r = fmaf(u.x, x0.x, t0r); t0r = fmaf(-u.y, x0.y, t0r);
-        t0i = fmaf(u.x, x0.y, t0i); t0i = fmaf(u.y, x0.x, t0i);
-        t1r = fmaf(u.x, x1.x, t1r); t1r = fmaf(-u.y, x1.y, t1r);
-        t1i = fmaf(u.x, x1.y, t1i); t1i = fmaf(u.y, x1.x, t1i);
+#pragma unroll
+        for (int j = 0; j < AB; ++j) {
+          const float2 u = s_u[b][h + j * (K1 / 2)][p];
+          float* q = tt[j];
+          q[0] = fmaf(u.x, dx.x, q[0]); q[0] = fmaf(-u.y, dx.y, q[0]);
+          q[1] = fmaf(u.x, dx.y, q[1]); q[1] = fmaf(u.y, dx.x, q[1]);
+          q[2] = fmaf(u.x, dx.z, q[2]); q[2] = fmaf(-u.y, dx.w, q[2]);
+          q[3] = fmaf(u.x, dx.w, q[3]); q[3] = fmaf(u.y, dx.z, q[3]);
+        }
       }
-      df_add1(acc[0], t0r);
-      df_add1(acc[1], t0i);
-      df_add1(acc[2], t1r);
-      df_add1(acc[3], t1i);
-      df_add1(acc[0], u0r);
-      df_add1(acc[1], u0i);
-      df_add1(acc[2], u1r);
-      df_add1(acc[3], u1i);
+#pragma unroll
+      for (int j = 0; j < AB; ++j)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          df_add1(acc[j][i], tt[j][i]);
+          df_add1(acc[j][i], tt[j][i + 4]);
+        }
     }
     // buffer b ^ 1 was last read in stage s - 1 (before the previous
     // barrier); s_pix[b] / s_v[b] (stage s) are no longer needed
@@ -230,23 +244,26 @@ factored_forward_kernel(const __grid_constant__ SetBlock<FactoredSet> sets, int 
   }
   if (!owner) return;
   const int KM = M * K;
-  const int r = m * K + a * kFacB + 2 * bp;                      // even: two complex rows = one float4
-  DF o[4];
-#pragma unroll
-  for (int i = 0; i < 4; ++i) o[i] = df_norm(acc[i]);
   float2* pp = partial + ((size_t)blockIdx.z * chunks + c) * 2 * KM;
-  reinterpret_cast<float4*>(pp + r)[0] = make_float4(o[0].hi, o[1].hi, o[2].hi, o[3].hi);
-  reinterpret_cast<float4*>(pp + KM + r)[0] = make_float4(o[0].lo, o[1].lo, o[2].lo, o[3].lo);
+#pragma unroll
+  for (int j = 0; j < AB; ++j) {
+    const int r = m * K + (h + j * (K1 / 2)) * kFacB + 2 * bp;   // even: two complex rows = one float4
+    DF o[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) o[i] = df_norm(acc[j][i]);
+    reinterpret_cast<float4*>(pp + r)[0] = make_float4(o[0].hi, o[1].hi, o[2].hi, o[3].hi);
+    reinterpret_cast<float4*>(pp + KM + r)[0] = make_float4(o[0].lo, o[1].lo, o[2].lo, o[3].lo);
+  }
 }
 
 // ---------------------------------------------------------------- adjoint
 // grid (pixel groups of 128, sets); 4 warps, one lane per pixel; every lane
-// runs all M antennas in order.
+// runs all M antennas in order (eight CTAs per SM: 64 registers a thread).
 constexpr int kMaxKM = 16384;                // w (M K complex) staged in shared memory
 constexpr int kAdjPix = 128;
 
 template <int K1>
-__global__ void __launch_bounds__(kAdjPix)
+__global__ void __launch_bounds__(kAdjPix, 8)
 factored_adjoint_kernel(const __grid_constant__ SetBlock<FactoredSet> sets, int M, int N, bool update,
                         const __grid_constant__ SolverView sv) {
   constexpr int K = K1 * kFacB;
@@ -263,15 +280,10 @@ factored_adjoint_kernel(const __grid_constant__ SetBlock<FactoredSet> sets, int 
   if (p >= fs.n) return;
   const int pix = fs.idx[p];
   DF g{0.f, 0.f};
-  float2 d[kFacB];
-#pragma unroll
-  for (int b = 0; b < kFacB; ++b) d[b] = fs.D[(size_t)b * N + pix];
   for (int m = 0; m < M; ++m) {
-    float2 dn[kFacB];                                             // the next antenna's D, loaded ahead
-    const bool more = m + 1 < M;
+    float2 d[kFacB];
 #pragma unroll
-    for (int b = 0; b < kFacB; ++b)
-      dn[b] = more ? fs.D[((size_t)(m + 1) * kFacB + b) * N + pix] : make_float2(0.f, 0.f);
+    for (int b = 0; b < kFacB; ++b) d[b] = fs.D[((size_t)m * kFacB + b) * N + pix];
     const float2* Cp = fs.C + (size_t)m * K1 * N + pix;
     const float4* wm = s_w4 + (size_t)m * K / 2;
 #pragma unroll 4
@@ -290,8 +302,6 @@ factored_adjoint_kernel(const __grid_constant__ SetBlock<FactoredSet> sets, int 
       }
       df_add1(g, fmaf(cv.x, tr0 + tr1, cv.y * (ti0 + ti1)));     // Re(conj(C_a) t_a)
     }
-#pragma unroll
-    for (int b = 0; b < kFacB; ++b) d[b] = dn[b];
   }
   const float gv = g.hi + g.lo;
   if (update) {
