@@ -432,6 +432,8 @@ def accuracy_measure(dev, stream):
                 s.set_operator_delays(q, scenegen.delays(g, q), g.fc, g.bw / g.K)
             else:
                 s.set_operator(q, torch.from_numpy(sc.A[q]).to(dev))
+        if spec["delays"]:
+            s.set_products(2)   # N < 2KM here (primal form): automatic selection keeps the stored operator
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         s.prepare()

@@ -46,6 +46,7 @@ struct Sensor {
   float2* r = nullptr;       // KM, residual y' - A_J v_J
   float2* w = nullptr;       // KM, W r (Woodbury form)
   float* g = nullptr;        // N, Re(A_J^H r) in list order (primal form)
+  float* g_lo = nullptr;     // N, its low words (plain FP32 path: g exact to double-float)
   int* J = nullptr;          // N, active list
   int* E = nullptr;          // N, pixels removed in the last SSC pass
   int* F = nullptr;          // N, frozen pixels at the last learned step (elim = 2)
@@ -128,8 +129,16 @@ struct Ctx {
     return true;
   }
   // the per-iteration products read the factored tables
+  // (automatically only while every sensor is in the Woodbury form: the
+  // primal form's H g amplifies the factored entries' rounding by the
+  // condition number of rho I + mu B^T B, which the stored path avoids with
+  // an exact g)
   bool use_factored() const {
-    return products != SADMM_PRODUCTS_STORED && crit.precision == 0 && all_factored();
+    if (products == SADMM_PRODUCTS_STORED || crit.precision != 0 || !all_factored()) return false;
+    if (products == SADMM_PRODUCTS_AUTO)
+      for (const Sensor& S : s)
+        if (S.cnt > 0 && !S.woodbury) return false;
+    return true;
   }
   bool periodic() const { return crit.precision >= 3; }
   // profiling: one event pair per (slot, phase); a slot is an iteration not
@@ -472,9 +481,11 @@ int launch_iteration(Ctx& c, IterScalars* out) {
       adj_w.push_back(AdjointSet{S.A, S.J, S.cnt, q, S.w, nullptr});
       fadj_w.push_back(FactoredSet{S.C, S.D, S.J, S.cnt, q, nullptr, nullptr, nullptr, S.w, nullptr});
     } else {
-      adj_p.push_back(AdjointSet{S.A, S.J, S.cnt, q, S.r, S.g});
+      adj_p.push_back(AdjointSet{S.A, S.J, S.cnt, q, S.r, S.g, S.g_lo});
       fadj_p.push_back(FactoredSet{S.C, S.D, S.J, S.cnt, q, nullptr, nullptr, nullptr, S.r, S.g});
-      spd_p.push_back(SpdSet{F, S.n, S.g, nullptr, S.J, q, part, 0});
+      // primal form: g enters H g as an exact pair (the factored entries
+      // carry their own rounding, so that path passes g alone)
+      spd_p.push_back(SpdSet{F, S.n, S.g, nullptr, S.J, q, part, 0, nullptr, 0, fac ? nullptr : S.g_lo});
     }
   }
   c.mark(0, true);
@@ -887,6 +898,7 @@ int sadmm_create(int Q, int M, int K, int N, double rho, double lambda, const sa
     S.r = (float2*)A(KM * sizeof(float2));
     S.w = (float2*)A(KM * sizeof(float2));
     S.g = (float*)A((size_t)N * sizeof(float));
+    S.g_lo = (float*)A((size_t)N * sizeof(float));
     S.J = (int*)A((size_t)N * sizeof(int));
     S.E = (int*)A((size_t)N * sizeof(int));
     S.F = (int*)A((size_t)N * sizeof(int));
@@ -1022,7 +1034,6 @@ int sadmm_backprojection(sadmm_t ctx, const float* const* y, float* out) {
     if (!ctx->s[q].op_set) { set_error("operator of sensor %d not set", q); return SADMM_ENOTREADY; }
   }
   const bool fac = ctx->use_factored();
-  if (!fac && ctx->KM > 16384) { set_error("sadmm_backprojection: KM > 16384 needs the factored operator"); return SADMM_EINVAL; }
   const size_t KM = ctx->KM, N = ctx->N;
   if (!ctx->bp_y) {
     ctx->bp_y = (float2*)ctx->dalloc((size_t)ctx->Q * 2 * KM * sizeof(float2));

@@ -141,6 +141,8 @@ struct AdjointSet {
   int q;
   const float2* w;   // KM complex
   float* g;          // output g[p] (mode g) or unused (mode update)
+  float* g_lo;       // mode g, optional: g from exact products summed in double-float, written as
+                     // the pair (g, g_lo) (the primal x-update amplifies any error in g, see api.cu)
 };
 int launch_adjoint(const AdjointSet* sets, int nsets, int KM, bool update, const SolverView& sv,
                    cudaStream_t st);
@@ -180,6 +182,7 @@ struct SpdSet {
   int tile0;         // set by launch_spd_apply
   double* outd;      // optional: out written as hi + lo in FP64, element i at outd[i * ldd]
   int ldd;
+  const float* u_lo; // optional: low words of u (the input is the pair u + u_lo)
 };
 // out = F u for every set (or, with update, the primal x-update epilogue).
 // *err is set to 1 if a tile copy did not complete within the wait limit.

@@ -15,10 +15,10 @@
 //            per pixel a (K/16) x 16 outer product, accumulated per CTA over
 //            a chunk of pixels staged through shared memory (two buffers:
 //            the next stage's tables and the stage after's pixel indices and
-//            v are loaded while the current stage is summed); FP32 sums over
-//            at most 32 pixels (two chains per stage) go into double-float
-//            accumulators, and the chunk partials are added by the forward
-//            product's reduction.
+//            v are loaded while the current stage is summed); the FP32 sums
+//            over the 16 even and the 16 odd pixels of each 32-pixel stage go
+//            into double-float accumulators, and the chunk partials are added
+//            by the forward product's reduction.
 //   adjoint  g_n = sum_m sum_a Re(conj(C[m][a][n]) t_a),
 //            t_a = sum_b conj(D[m][b][n]) w[m][16a+b]:
 //            one lane per pixel, antennas in order; 64 registers a thread,

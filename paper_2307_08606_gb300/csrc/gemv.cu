@@ -21,6 +21,7 @@ namespace {
 using symtile::DF;
 using symtile::df_add;
 using symtile::df_add1;
+using symtile::df_mul_acc;
 using symtile::df_norm;
 
 constexpr int kFwdThreads = 128;          // one float4 (2 complex rows) per thread
@@ -187,6 +188,13 @@ constexpr int kAdjWarps = 8;
 constexpr int kAdjColsPerWarp = 8;
 constexpr int kAdjUnroll = 4;
 
+// EXACT (mode g only): every product is formed exactly and added with an
+// error-free two-sum, and g leaves as the pair (g, g_lo).  The primal
+// x-update x = v + mu H g weights g by H = (rho I + mu B^T B)^{-1}, whose
+// condition number is that of rho I + mu B^T B: where B^T B is (nearly)
+// singular, any error in g outside the range of B^T is amplified by up to that
+// factor, so g must be exact to double-float accuracy there.
+template <bool EXACT>
 __global__ void __launch_bounds__(kAdjWarps * 32)
 adjoint_kernel(const __grid_constant__ SetBlock<AdjointSet> sets, int KM, bool update,
                const __grid_constant__ SolverView sv) {
@@ -221,21 +229,35 @@ adjoint_kernel(const __grid_constant__ SetBlock<AdjointSet> sets, int KM, bool u
 #pragma unroll
       for (int u = 0; u < kAdjUnroll; ++u) {
         const float4 w = s_w4[i + 32 * u];
-        float t = a[u].x * w.x;
-        t = fmaf(a[u].y, w.y, t);
-        t = fmaf(a[u].z, w.z, t);
-        t = fmaf(a[u].w, w.w, t);
-        df_add1(acc[u], t);
+        if (EXACT) {
+          df_mul_acc(acc[u], a[u].x, w.x);
+          df_mul_acc(acc[u], a[u].y, w.y);
+          df_mul_acc(acc[u], a[u].z, w.z);
+          df_mul_acc(acc[u], a[u].w, w.w);
+        } else {
+          float t = a[u].x * w.x;
+          t = fmaf(a[u].y, w.y, t);
+          t = fmaf(a[u].z, w.z, t);
+          t = fmaf(a[u].w, w.w, t);
+          df_add1(acc[u], t);
+        }
       }
     }
     for (; i < n4; i += 32) {
       const float4 a = ld_stream(col + i);
       const float4 w = s_w4[i];
-      float t = a.x * w.x;
-      t = fmaf(a.y, w.y, t);
-      t = fmaf(a.z, w.z, t);
-      t = fmaf(a.w, w.w, t);
-      df_add1(acc[0], t);
+      if (EXACT) {
+        df_mul_acc(acc[0], a.x, w.x);
+        df_mul_acc(acc[0], a.y, w.y);
+        df_mul_acc(acc[0], a.z, w.z);
+        df_mul_acc(acc[0], a.w, w.w);
+      } else {
+        float t = a.x * w.x;
+        t = fmaf(a.y, w.y, t);
+        t = fmaf(a.z, w.z, t);
+        t = fmaf(a.w, w.w, t);
+        df_add1(acc[0], t);
+      }
     }
 #pragma unroll
     for (int u = 1; u < kAdjUnroll; ++u) df_add(acc[0], acc[u]);
@@ -254,6 +276,10 @@ adjoint_kernel(const __grid_constant__ SetBlock<AdjointSet> sets, int KM, bool u
         const float xn = fmaf(sv.mu, g, v);
         sv.ring[((size_t)sv.slot * sv.Q + as.q) * sv.N + pix] = xn - xo;
         sv.x[xi] = xn;
+      } else if (EXACT) {
+        const DF o = df_norm(acc[0]);
+        as.g[p] = o.hi;
+        as.g_lo[p] = o.lo;
       } else {
         as.g[p] = g;
       }
@@ -308,15 +334,24 @@ int launch_adjoint(const AdjointSet* sets, int nsets, int KM, bool update, const
   int max_cols = 0;
   for (int i = 0; i < nsets; ++i) { blk.v[i] = sets[i]; max_cols = max(max_cols, sets[i].n); }
   if (max_cols == 0) return SADMM_OK;
+  const bool exact = !update && sets[0].g_lo != nullptr;
+  for (int i = 1; i < nsets; ++i)
+    if ((sets[i].g_lo != nullptr) != (sets[0].g_lo != nullptr)) {
+      set_error("launch_adjoint: sets mix exact and plain outputs");
+      return SADMM_EINVAL;
+    }
   const size_t smem = (size_t)KM * sizeof(float2);
   static bool configured = false;
   if (!configured) {
-    SADMM_CUDA_TRY(cudaFuncSetAttribute(adjoint_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    SADMM_CUDA_TRY(cudaFuncSetAttribute(adjoint_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        200 * 1024));
+    SADMM_CUDA_TRY(cudaFuncSetAttribute(adjoint_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         200 * 1024));
     configured = true;
   }
   dim3 grid(div_up(max_cols, kAdjWarps * kAdjColsPerWarp), nsets);
-  adjoint_kernel<<<grid, kAdjWarps * 32, smem, st>>>(blk, KM, update, sv);
+  if (exact) adjoint_kernel<true><<<grid, kAdjWarps * 32, smem, st>>>(blk, KM, update, sv);
+  else adjoint_kernel<false><<<grid, kAdjWarps * 32, smem, st>>>(blk, KM, update, sv);
   SADMM_LAUNCH_CHECK();
   return SADMM_OK;
 }

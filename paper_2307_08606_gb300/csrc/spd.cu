@@ -40,12 +40,15 @@ __device__ __forceinline__ int item_set(const SetBlock<SpdSet>& sets, int nsets,
   return s;
 }
 
+// ULO: the input is the pair u + u_lo (every set of the launch has u_lo).
+template <bool ULO>
 __global__ void __launch_bounds__(kSpdThreads)
 spd_tile_kernel(const __grid_constant__ SetBlock<SpdSet> sets, int nsets, int items, int* __restrict__ err) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   float2* tile = reinterpret_cast<float2*>(smem_raw);           // 64 x 64 pairs
   __shared__ __align__(8) uint64_t bar;
   __shared__ __align__(16) float s_u[2][kT];                    // u_I, u_J
+  __shared__ __align__(16) float s_ul[ULO ? 2 : 1][ULO ? kT : 4];  // their low words (ULO)
   const int tid = threadIdx.x;
   const int lt = tid;                                            // < 64: row lt, else column lt - 64
   if ((int)blockIdx.x >= items) return;
@@ -71,6 +74,7 @@ spd_tile_kernel(const __grid_constant__ SetBlock<SpdSet> sets, int nsets, int it
       const int blk = lt < kT ? I : J;
       const int i = blk * kT + r;
       s_u[lt >> 6][r] = i < ss.n ? ss.u[i] : 0.f;
+      if (ULO) s_ul[lt >> 6][r] = i < ss.n ? ss.u_lo[i] : 0.f;
     }
     __syncthreads();                                   // s_u written
     const bool ok = mbar_wait(&bar, phase);
@@ -92,10 +96,19 @@ spd_tile_kernel(const __grid_constant__ SetBlock<SpdSet> sets, int nsets, int it
         const float4 f0 = row[b0 >> 1], f1 = row[b1 >> 1];
         const float2 u0 = *reinterpret_cast<const float2*>(uJ + b0);
         const float2 u1 = *reinterpret_cast<const float2*>(uJ + b1);
-        df_acc(acc0, f0.x, f0.y, u0.x);
-        df_acc(acc0, f0.z, f0.w, u0.y);
-        df_acc(acc1, f1.x, f1.y, u1.x);
-        df_acc(acc1, f1.z, f1.w, u1.y);
+        if (ULO) {
+          const float2 l0 = *reinterpret_cast<const float2*>(&s_ul[1][b0]);
+          const float2 l1 = *reinterpret_cast<const float2*>(&s_ul[1][b1]);
+          df_acc2(acc0, f0.x, f0.y, u0.x, l0.x);
+          df_acc2(acc0, f0.z, f0.w, u0.y, l0.y);
+          df_acc2(acc1, f1.x, f1.y, u1.x, l1.x);
+          df_acc2(acc1, f1.z, f1.w, u1.y, l1.y);
+        } else {
+          df_acc(acc0, f0.x, f0.y, u0.x);
+          df_acc(acc0, f0.z, f0.w, u0.y);
+          df_acc(acc1, f1.x, f1.y, u1.x);
+          df_acc(acc1, f1.z, f1.w, u1.y);
+        }
       }
     } else if (I != J) {
       // column r of F_IJ times u_I (the transposed contribution to block row
@@ -107,10 +120,18 @@ spd_tile_kernel(const __grid_constant__ SetBlock<SpdSet> sets, int nsets, int it
         const float4 u4 = *reinterpret_cast<const float4*>(uI + i);
         const float2 f0 = tile[i * kT + r], f1 = tile[(i + 1) * kT + r];
         const float2 f2 = tile[(i + 2) * kT + r], f3 = tile[(i + 3) * kT + r];
-        df_acc(acc0, f0.x, f0.y, u4.x);
-        df_acc(acc1, f1.x, f1.y, u4.y);
-        df_acc(acc0, f2.x, f2.y, u4.z);
-        df_acc(acc1, f3.x, f3.y, u4.w);
+        if (ULO) {
+          const float4 l4 = *reinterpret_cast<const float4*>(&s_ul[0][i]);
+          df_acc2(acc0, f0.x, f0.y, u4.x, l4.x);
+          df_acc2(acc1, f1.x, f1.y, u4.y, l4.y);
+          df_acc2(acc0, f2.x, f2.y, u4.z, l4.z);
+          df_acc2(acc1, f3.x, f3.y, u4.w, l4.w);
+        } else {
+          df_acc(acc0, f0.x, f0.y, u4.x);
+          df_acc(acc1, f1.x, f1.y, u4.y);
+          df_acc(acc0, f2.x, f2.y, u4.z);
+          df_acc(acc1, f3.x, f3.y, u4.w);
+        }
       }
     }
     df_add(acc0, acc1);
@@ -211,14 +232,19 @@ int launch_spd_apply(const SpdSet* sets, int nsets, bool update, const SolverVie
     nt_max = max(nt_max, nt);
   }
   if (items == 0) return SADMM_OK;
+  const bool ulo = sets[0].u_lo != nullptr;
+  for (int i = 1; i < nsets; ++i)
+    if ((sets[i].u_lo != nullptr) != ulo) { set_error("launch_spd_apply: sets mix pair and plain inputs"); return SADMM_EINVAL; }
   const int smem = kTileBytes;
   static bool configured = false;
   if (!configured) {
-    SADMM_CUDA_TRY(cudaFuncSetAttribute(spd_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    SADMM_CUDA_TRY(cudaFuncSetAttribute(spd_tile_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    SADMM_CUDA_TRY(cudaFuncSetAttribute(spd_tile_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     configured = true;
   }
   const int grid = min(items, 152 * 6);           // six 32 KB tiles in flight per SM
-  spd_tile_kernel<<<grid, kSpdThreads, smem, st>>>(blk, nsets, items, err);
+  if (ulo) spd_tile_kernel<true><<<grid, kSpdThreads, smem, st>>>(blk, nsets, items, err);
+  else spd_tile_kernel<false><<<grid, kSpdThreads, smem, st>>>(blk, nsets, items, err);
   SADMM_LAUNCH_CHECK();
   spd_reduce_kernel<<<dim3(nt_max, nsets), kT, 0, st>>>(blk, update, sv);
   SADMM_LAUNCH_CHECK();

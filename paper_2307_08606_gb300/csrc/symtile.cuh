@@ -27,6 +27,31 @@ __device__ __forceinline__ void df_acc(DF& s, float w_hi, float w_lo, float u) {
   s.lo += err + e;
 }
 
+// s += (w_hi + w_lo)(u + u_lo) to double-float accuracy (the products of the
+// two low words are below the error)
+__device__ __forceinline__ void df_acc2(DF& s, float w_hi, float w_lo, float u, float u_lo) {
+  const float p = w_hi * u;
+  float e = fmaf(w_hi, u, -p);
+  e = fmaf(w_lo, u, e);
+  e = fmaf(w_hi, u_lo, e);
+  const float t = s.hi + p;
+  const float bp = t - s.hi;
+  const float err = (s.hi - (t - bp)) + (p - bp);
+  s.hi = t;
+  s.lo += err + e;
+}
+
+// s += a b with the product formed exactly (p + e = a b)
+__device__ __forceinline__ void df_mul_acc(DF& s, float a, float b) {
+  const float p = a * b;
+  const float e = fmaf(a, b, -p);
+  const float t = s.hi + p;
+  const float bp = t - s.hi;
+  const float err = (s.hi - (t - bp)) + (p - bp);
+  s.hi = t;
+  s.lo += err + e;
+}
+
 __device__ __forceinline__ void df_add(DF& s, DF b) {
   const float t = s.hi + b.hi;
   const float bp = t - s.hi;

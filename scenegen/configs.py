@@ -13,6 +13,9 @@
   K in {128, 256}, N in {48^2, 64^2, 96^2} (radar, circle and 5 cm cells as
   ``paper_scale``), 16 scenes per geometry with 5..60 clusters, visibility
   p in [0.5, 0.9] and 10..25 dB SNR.
+* ``precision_twin``: the sensors of the 256x256 precision workload (Q=8,
+  M=16, K=512, KM=8192) over a 64x64 crop of 5 cm cells, 8 clusters, p=0.7,
+  20 dB: the size the FP64 oracle checks that workload's forms at.
 * ``resolved_tiny``: a well-posed geometry used by the oracle's pins: 8x8
   pixels of 10 cm seen from 0.6 m by sensors with M=16 antennas and BW=4 GHz
   at 60 GHz (K=16, KM=256 > N), so that every sensor resolves the grid on its
@@ -45,6 +48,9 @@ GEOMS = {
     # 32x32 grid that every sensor resolves on its own (2KM = 2N, condition ~300):
     # Eq. 2 is well posed, so the iterates converge to a nonzero image
     "resolved_32": Geometry(Q=4, M=32, K=32, nx=32, cell=0.08, radius=2.0, fc=60e9, bw=4e9),
+    # the precision-form sensors (Q=8, M=16, K=512: KM=8192) over a 64x64 crop
+    # of 5 cm cells, the oracle-sized twin of the 256x256 precision workload
+    "precision_twin": Geometry(Q=8, M=16, K=512, nx=64, cell=0.05, radius=10.0, fc=77e9, bw=1e9),
 }
 
 
@@ -55,6 +61,10 @@ def build_scene(name: str, seed: int = 0, geom: Geometry = None, snr_db="default
     if name == "paper_scale":
         x = cluster_targets(g, seed, n_targets or 40, amp=(0.3, 1.0), p_vis=0.7)
         snr = 15.0
+    elif name == "precision_twin":
+        # 120 targets on 256^2 pixels keep their density on the 64^2 crop
+        x = cluster_targets(g, seed, n_targets or 8, amp=(0.3, 1.0), p_vis=0.7)
+        snr = 20.0
     elif name == "resolved_32":
         x = cluster_targets(g, seed, n_targets or 10, amp=(0.3, 1.0), p_vis=0.7)
         snr = 25.0

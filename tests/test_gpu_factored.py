@@ -8,7 +8,7 @@ Bars, from the arithmetic (u = 2^-24):
   component; the factors C and D likewise, and the factored entry C D within
   3u of A64;
 * forward r = base - A_J v: each term within 3u (factored entry) + u (v C),
-  FP32 sums over stages of 32 pixels (<= 32u of the stage's sum of |terms|),
+  FP32 sums over at most 32 pixels of a stage (<= 32u of their sum of |terms|),
   double-float across stages and chunks, one final rounding:
   |r - r64| <= 40u sum|A||v| + 2u (|base| + |r64|);
 * adjoint g = Re(A_J^H w): 16-term FP32 sums t_a (<= 16u), the C product and
@@ -170,15 +170,17 @@ def test_solver_on_factored_operator_matches_oracle(B):
 
 
 def test_solver_on_factored_operator_with_elimination(B):
-    """resolved_tiny (Q=3, M=16, K=16: one C factor per antenna, sixteen warps
-    in the adjoint) with Algorithm 1 on: iterate within 1e-4 of the oracle and
-    the same active sets while the decision margins allow."""
+    """resolved_tiny (Q=3, M=16, K=16: one C factor per antenna; N < 2KM, so
+    the primal x-update, where factored products run only when asked for) with
+    Algorithm 1 on: iterate within 1e-4 of the oracle and the same active sets
+    while the decision margins allow (this geometry is well conditioned)."""
     sc = scenegen.build_scene("resolved_tiny", seed=2, snr_db=30.0)
     lam = 0.05 * scenegen.lambda_max(sc.A, sc.y)
     crit = oracle.Criterion(elim=1, Kp=4)
     iters = 150
     ref = oracle.sadmm(sc.A, sc.y, 1.0, lam, crit, iters=iters)
     s = _delay_solver(B, sc, 1.0, lam, elim=1, Kp=4)
+    s.set_products(2)           # the primal form: automatic selection would take the stored operator
     s.solve(sc.y, iters)
     assert _rel(s.X(), ref.state.x) <= 1e-4
     ok = all(h["gate_margin"] >= 1e-3 and (not h["gate"] or h["zeta_margin"] >= 0.1 * crit.eps_p)
