@@ -62,8 +62,16 @@ residual_kernel(const __grid_constant__ SolverView sv, double* __restrict__ part
     // per-pixel terms in FP32 (a handful per thread; GB300's FP64 pipe is
     // narrow), cross-thread sums in FP64
     const size_t N = sv.N;
+    constexpr int kQB = 8;               // sensors whose loads are issued together
     float sx = 0.f;
-    for (int q = 0; q < sv.Q; ++q) sx += sv.x[q * N + i];
+    for (int q0 = 0; q0 < sv.Q; q0 += kQB) {
+      float v[kQB];
+#pragma unroll
+      for (int u = 0; u < kQB; ++u) v[u] = q0 + u < sv.Q ? sv.x[(q0 + u) * N + i] : 0.f;
+#pragma unroll
+      for (int u = 0; u < kQB; ++u)
+        if (q0 + u < sv.Q) sx += v[u];
+    }
     const float xb = sx / (float)sv.Q;
     const float xb_old = sv.xbar[i], zb_old = sv.zbar[i], s_old = sv.s[i];
     const float zb = soft_threshold(xb + s_old, sv.lam_over_rho);
@@ -73,15 +81,25 @@ residual_kernel(const __grid_constant__ SolverView sv, double* __restrict__ part
     const float e = xb - zb;
     float a1 = 0.f, a2 = 0.f, a3 = 0.f, a5 = 0.f;
     const float* ring = sv.ring + (size_t)sv.slot * sv.Q * N;
-    for (int q = 0; q < sv.Q; ++q) {
-      const float xq = sv.x[q * N + i];
-      const float dx = ring[q * N + i];
-      const float zq = (xq - xb) + zb;
-      const float dz = (dx - dxb) + dzb;
-      a1 = fmaf(xq, xq, a1);
-      a2 = fmaf(zq, zq, a2);
-      a3 = fmaf(dz, dz, a3);
-      a5 = fmaf(dx, dx, a5);
+    for (int q0 = 0; q0 < sv.Q; q0 += kQB) {
+      float xv[kQB], dv[kQB];
+#pragma unroll
+      for (int u = 0; u < kQB; ++u) {
+        const bool ok = q0 + u < sv.Q;
+        xv[u] = ok ? sv.x[(q0 + u) * N + i] : 0.f;
+        dv[u] = ok ? ring[(q0 + u) * N + i] : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < kQB; ++u) {
+        if (q0 + u >= sv.Q) break;
+        const float xq = xv[u], dx = dv[u];
+        const float zq = (xq - xb) + zb;
+        const float dz = (dx - dxb) + dzb;
+        a1 = fmaf(xq, xq, a1);
+        a2 = fmaf(zq, zq, a2);
+        a3 = fmaf(dz, dz, a3);
+        a5 = fmaf(dx, dx, a5);
+      }
     }
     acc[0] = (double)e * e;
     acc[1] = a1;
