@@ -47,6 +47,7 @@ struct Sensor {
   float2* w = nullptr;       // KM, W r (Woodbury form)
   float* g = nullptr;        // N, Re(A_J^H r) in list order (primal form)
   float* g_lo = nullptr;     // N, its low words (plain FP32 path: g exact to double-float)
+  int* pos = nullptr;        // N, primal-form downdate scratch (elim > 0)
   int* J = nullptr;          // N, active list
   int* E = nullptr;          // N, pixels removed in the last SSC pass
   int* F = nullptr;          // N, frozen pixels at the last learned step (elim = 2)
@@ -583,6 +584,49 @@ int launch_split_products_adj(Ctx& c, const SolverView& sv, bool corr) {
   return launch_split_adjoint(gout.data(), (int)gout.size(), c.KM, kind, planes, false, sv, c.st);
 }
 
+// Primal-form factors whose sets lost e <= kDowndateMax pixels and stay in
+// the primal form: H over J_new is the Schur complement of H_EE in H
+// (run_primal_downdate, FP64), written to the buffer that is neither the
+// cached full-set factor nor the current one, then packed into pairs.
+// Sensors whose small block H_EE is not numerically positive definite are
+// returned in `failed` (they are refactored).
+int primal_downdate(Ctx& c, const std::vector<int>& qs, std::vector<int>* failed) {
+  if (qs.empty()) return SADMM_OK;
+  std::vector<PrimalDdJob> jobs;
+  std::vector<int> dst;
+  for (int q : qs) {
+    Sensor& S = c.s[q];
+    const int d = (S.cur == S.full) ? (S.full + 1) % 3 : 3 - S.full - S.cur;
+    PrimalDdJob j{};
+    j.H = S.fb[S.cur];
+    j.ldh = round_up(S.n, kTile);
+    j.Hn = S.fb[d];
+    j.ldn = round_up(S.cnt, kTile);
+    j.J = S.J;
+    j.E = S.E;
+    j.n_new = S.cnt;
+    j.e = c.h_counts[c.Q + q];
+    j.pos = S.pos;
+    j.V = S.dinv;
+    j.slot = q;
+    jobs.push_back(j);
+    dst.push_back(d);
+  }
+  SADMM_CUDA_TRY(cudaMemsetAsync(c.dstatus, 0, sizeof(int) * c.Q, c.st));
+  SADMM_TRY(run_primal_downdate(jobs.data(), (int)jobs.size(), c.dstatus, c.st));
+  SADMM_CUDA_TRY(cudaMemcpyAsync(c.h_status, c.dstatus, sizeof(int) * c.Q, cudaMemcpyDeviceToHost, c.st));
+  SADMM_CUDA_TRY(cudaStreamSynchronize(c.st));
+  for (size_t i = 0; i < qs.size(); ++i) {
+    Sensor& S = c.s[qs[i]];
+    if (c.h_status[qs[i]]) { failed->push_back(qs[i]); continue; }
+    S.cur = dst[i];
+    S.n = S.cnt;
+    S.cum_dd += jobs[i].e;
+    SADMM_TRY(launch_pack_sym(S.fb[S.cur], jobs[i].ldn, S.n, S.fhl[S.cur], c.st));
+  }
+  return SADMM_OK;
+}
+
 // Columns a Woodbury factor may gain or lose by rank updates before it is
 // rebuilt from scratch.  Each pass applies the Woodbury identity exactly in
 // FP64, so rounding grows with the number of passes only; 2n columns (n = 2KM)
@@ -603,17 +647,22 @@ int apply_changes(Ctx& c, const std::vector<int>& changed) {
   } else {
     SADMM_TRY(launch_recompute_xbar(sv, c.st));
   }
-  // A Woodbury-form factor that stays in Woodbury form is downdated by the
-  // removed columns; a form change, a primal-form factor, or too many
-  // accumulated downdates (rounding) refactor from scratch.
-  std::vector<int> dd, full;
+  // A factor that keeps its form is downdated by the removed columns (a
+  // rank-|E| Woodbury update, or the Schur complement of a primal-form
+  // factor); a form change, more columns than one primal pass takes, or too
+  // many accumulated downdates (rounding) refactor from scratch.
+  std::vector<int> dd, pdd, full;
   for (int q : changed) {
     const Sensor& S = c.s[q];
     const int e = c.h_counts[c.Q + q];
     if (S.woodbury && S.cnt > 2 * c.KM && S.cum_dd + e <= refactor_after(c)) dd.push_back(q);
+    else if (!S.woodbury && S.pos && S.cnt > 0 && e <= kDowndateMax && S.n == S.cnt + e &&
+             S.cum_dd + e <= refactor_after(c))
+      pdd.push_back(q);
     else full.push_back(q);
   }
   SADMM_TRY(downdate(c, dd, &full));
+  SADMM_TRY(primal_downdate(c, pdd, &full));
   c.corr_due = true;        // y' and the active sets changed: refresh the lo-plane products
   return refresh(c, full, false);
 }
@@ -899,6 +948,7 @@ int sadmm_create(int Q, int M, int K, int N, double rho, double lambda, const sa
     S.w = (float2*)A(KM * sizeof(float2));
     S.g = (float*)A((size_t)N * sizeof(float));
     S.g_lo = (float*)A((size_t)N * sizeof(float));
+    if (c.elim > 0) S.pos = (int*)A((size_t)N * sizeof(int));
     S.J = (int*)A((size_t)N * sizeof(int));
     S.E = (int*)A((size_t)N * sizeof(int));
     S.F = (int*)A((size_t)N * sizeof(int));

@@ -305,6 +305,22 @@ struct DdScratch {
   void** dptrs;      // 2 x jobs device pointers
   float2* part;      // jobs x multi_apply_part_pairs(n); also 64 x sym_part_pairs(n) for single-column applies
 };
+// Downdate of a primal-form factor H = (rho I + mu B_J^T B_J)^{-1} over the
+// ordered list J_old when the pixels E leave it (factor.cu): the new factor
+// over J_new = J_old \ E is the Schur complement H_RR - H_RE H_EE^{-1} H_ER.
+struct PrimalDdJob {
+  const double* H;    // old factor, n_old x n_old, leading dimension ldh
+  int ldh;
+  double* Hn;         // new factor, n_new x n_new (identity-padded to ldn), leading dimension ldn
+  int ldn;
+  const int* J;       // new ordered list (n_new pixels, ascending)
+  const int* E;       // removed pixels (e <= kDowndateMax, ascending)
+  int n_new, e;
+  int* pos;           // n_new + e scratch: old positions of the kept rows, then of the removed ones
+  double* V;          // n_new x kDowndateMax scratch, then kDowndateMax^2 for L^{-1} of H_EE
+  int slot;           // status slot
+};
+int run_primal_downdate(const PrimalDdJob* jobs, int njobs, int* d_status, cudaStream_t st);
 int run_downdate_pairs(const DowndateJob* jobs, int njobs, int KM, double mu, const DdScratch& scr, int* d_status,
                        int* err, cudaStream_t st);
 size_t downdate_scratch_doubles(int n);

@@ -706,6 +706,159 @@ int run_downdate_pairs(const DowndateJob* jobs, int njobs, int KM, double mu, co
   return SADMM_OK;
 }
 
+// ------------------------------------------------------- primal downdate
+// Removing the pixels E from the ordered list J_old leaves the principal
+// submatrix M_RR of M = rho I + mu B_J^T B_J, and (M_RR)^{-1} is the Schur
+// complement of H_EE in H = M^{-1}:  H_RR - H_RE H_EE^{-1} H_ER.  With
+// H_EE = L L^T and V = H_RE L^{-T} that is H_RR - V V^T, O(n^2 e) in FP64
+// instead of the Gram, Cholesky and inverse of a refactorisation.
+namespace {
+
+using PddBlock = SetBlock<PrimalDdJob>;
+
+// old positions: kept row p sits at p + #{E < J[p]}, removed row k at
+// k + #{J < E[k]} (both lists ascending and disjoint)
+__global__ void pdd_pos_kernel(const __grid_constant__ PddBlock jobs) {
+  const PrimalDdJob& jb = jobs.v[blockIdx.y];
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= jb.n_new + jb.e) return;
+  const bool kept = t < jb.n_new;
+  const int x = kept ? jb.J[t] : jb.E[t - jb.n_new];
+  const int* other = kept ? jb.E : jb.J;
+  int lo = 0, hi = kept ? jb.e : jb.n_new;            // count of other[] < x
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (other[mid] < x) lo = mid + 1;
+    else hi = mid;
+  }
+  jb.pos[t] = (kept ? t : t - jb.n_new) + lo;
+}
+
+// V[i][k] = H[pos_i][pos_{n+k}] (zero past e)
+__global__ void pdd_gather_kernel(const __grid_constant__ PddBlock jobs) {
+  const PrimalDdJob& jb = jobs.v[blockIdx.y];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= jb.n_new) return;
+  const double* row = jb.H + (size_t)jb.pos[i] * jb.ldh;
+#pragma unroll 4
+  for (int k = 0; k < DM; ++k) jb.V[(size_t)i * DM + k] = k < jb.e ? row[jb.pos[jb.n_new + k]] : 0.0;
+}
+
+// L^{-1} of H_EE = L L^T (identity past e), into V + n_new * DM
+__global__ void __launch_bounds__(DM * DM)
+pdd_chol_kernel(const __grid_constant__ PddBlock jobs, int* status) {
+  const PrimalDdJob& jb = jobs.v[blockIdx.x];
+  __shared__ double L[DM][DM + 1], Li[DM][DM + 1];
+  const int a = threadIdx.x / DM, b = threadIdx.x % DM;
+  L[a][b] = (a < jb.e && b < jb.e) ? jb.H[(size_t)jb.pos[jb.n_new + a] * jb.ldh + jb.pos[jb.n_new + b]]
+                                   : (a == b ? 1.0 : 0.0);
+  __syncthreads();
+  for (int j = 0; j < DM; ++j) {
+    double d = L[j][j];
+    __syncthreads();
+    if (!(d > 0.0) || !isfinite(d)) {
+      if (threadIdx.x == 0) status[jb.slot] = 1;
+      d = 1.0;
+    }
+    d = sqrt(d);
+    if (b == j && a >= j) L[a][j] = (a == j) ? d : L[a][j] / d;
+    __syncthreads();
+    if (b > j && a >= b) L[a][b] = fma(-L[a][j], L[b][j], L[a][b]);
+    __syncthreads();
+  }
+  for (int i = 0; i < DM; ++i) {
+    if (threadIdx.x < DM) {
+      const int c = threadIdx.x;
+      double v = 0.0;
+      if (c <= i) {
+        double s = (c == i) ? 1.0 : 0.0;
+        for (int k = c; k < i; ++k) s = fma(-L[i][k], Li[k][c], s);
+        v = s / L[i][i];
+      }
+      Li[i][c] = v;
+    }
+    __syncthreads();
+  }
+  jb.V[(size_t)jb.n_new * DM + a * DM + b] = Li[a][b];
+}
+
+// V = H_RE L^{-T}, row by row in place
+__global__ void pdd_t_kernel(const __grid_constant__ PddBlock jobs) {
+  const PrimalDdJob& jb = jobs.v[blockIdx.y];
+  __shared__ double Li[DM][DM];
+  for (int t = threadIdx.x; t < DM * DM; t += blockDim.x) Li[t / DM][t % DM] = jb.V[(size_t)jb.n_new * DM + t];
+  __syncthreads();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= jb.n_new) return;
+  double p[DM];
+#pragma unroll
+  for (int c = 0; c < DM; ++c) p[c] = jb.V[(size_t)i * DM + c];
+#pragma unroll
+  for (int c = 0; c < DM; ++c) {
+    double t = 0.0;
+#pragma unroll
+    for (int k = 0; k <= c; ++k) t = fma(p[k], Li[c][k], t);
+    jb.V[(size_t)i * DM + c] = t;
+  }
+}
+
+// Hn[i][j] = H[pos_i][pos_j] - sum_k V[i][k] V[j][k] for i, j < n_new; the
+// identity on the padding up to ldn.  16 x 16 threads per 16 x 16 block,
+// the two blocks of V rows staged in shared memory.
+__global__ void __launch_bounds__(256)
+pdd_update_kernel(const __grid_constant__ PddBlock jobs) {
+  const PrimalDdJob& jb = jobs.v[blockIdx.z];
+  __shared__ double Vi[16][DM + 1], Vj[16][DM + 1];
+  const int i0 = blockIdx.y * 16, j0 = blockIdx.x * 16;
+  if (i0 >= jb.ldn || j0 >= jb.ldn) return;
+  const int ty = threadIdx.x / 16, tx = threadIdx.x % 16;
+  for (int t = threadIdx.x; t < 16 * DM; t += 256) {
+    const int r = t / DM, k = t % DM;
+    Vi[r][k] = (i0 + r < jb.n_new) ? jb.V[(size_t)(i0 + r) * DM + k] : 0.0;
+    Vj[r][k] = (j0 + r < jb.n_new) ? jb.V[(size_t)(j0 + r) * DM + k] : 0.0;
+  }
+  __syncthreads();
+  const int i = i0 + ty, j = j0 + tx;
+  double h;
+  if (i < jb.n_new && j < jb.n_new) {
+    h = jb.H[(size_t)jb.pos[i] * jb.ldh + jb.pos[j]];
+    for (int k = 0; k < jb.e; ++k) h = fma(-Vi[ty][k], Vj[tx][k], h);
+  } else {
+    h = (i == j) ? 1.0 : 0.0;
+  }
+  jb.Hn[(size_t)i * jb.ldn + j] = h;
+}
+
+}  // namespace
+
+int run_primal_downdate(const PrimalDdJob* jobs, int njobs, int* d_status, cudaStream_t st) {
+  if (njobs <= 0) return SADMM_OK;
+  if (njobs > kMaxSets) { set_error("run_primal_downdate: too many jobs"); return SADMM_EINVAL; }
+  PddBlock blk;
+  int nmax = 1, ldmax = 1;
+  for (int i = 0; i < njobs; ++i) {
+    const PrimalDdJob& j = jobs[i];
+    if (j.e < 1 || j.e > DM || j.n_new < 1 || j.ldn < j.n_new || j.ldn % T != 0) {
+      set_error("run_primal_downdate: bad sizes");
+      return SADMM_EINVAL;
+    }
+    blk.v[i] = j;
+    nmax = max(nmax, j.n_new + j.e);
+    ldmax = max(ldmax, j.ldn);
+  }
+  pdd_pos_kernel<<<dim3(div_up(nmax, 256), njobs), 256, 0, st>>>(blk);
+  SADMM_LAUNCH_CHECK();
+  pdd_gather_kernel<<<dim3(div_up(nmax, 128), njobs), 128, 0, st>>>(blk);
+  SADMM_LAUNCH_CHECK();
+  pdd_chol_kernel<<<njobs, DM * DM, 0, st>>>(blk, d_status);
+  SADMM_LAUNCH_CHECK();
+  pdd_t_kernel<<<dim3(div_up(nmax, 128), njobs), 128, 0, st>>>(blk);
+  SADMM_LAUNCH_CHECK();
+  pdd_update_kernel<<<dim3(ldmax / 16, ldmax / 16, njobs), 256, 0, st>>>(blk);
+  SADMM_LAUNCH_CHECK();
+  return SADMM_OK;
+}
+
 int run_factor(const FactorJob* jobs, int njobs, int KM, double mu, double rho, int* d_status,
                cudaStream_t st) {
   if (njobs <= 0) return SADMM_OK;
