@@ -463,3 +463,20 @@ def test_golden_limit_is_optimal():
     assert supp.any() and not supp.all()
     assert np.max(np.abs(nu)) <= lam * (1 + 1e-6)
     assert np.max(np.abs(nu[supp] - lam * np.sign(xg[supp]))) <= 1e-6 * lam
+
+
+def test_batch_scenes_follow_their_recipe():
+    """The mixed-geometry batch scenes: 16 scenes per geometry drawn by seed
+    (the same draws for the same seed), complex64 measurements of shape
+    (S, Q, KM), and per-scene lambda = 0.05 lambda_max of that scene."""
+    g = scenegen.Geometry(Q=2, M=4, K=16, nx=8, cell=0.05, radius=10.0, fc=77e9, bw=1e9)
+    A = [radar.operator(g, q) for q in range(g.Q)]
+    Y, lams = scenegen.batch_scenes(g, A, seed=4)
+    Y2, lams2 = scenegen.batch_scenes(g, A, seed=4)
+    assert Y.shape == (16, g.Q, g.KM) and Y.dtype == np.complex64
+    assert np.array_equal(Y, Y2) and lams == lams2
+    for s in (0, 7, 15):
+        ys = [Y[s, q] for q in range(g.Q)]
+        assert lams[s] == pytest.approx(0.05 * scenegen.lambda_max(A, ys), rel=1e-6)
+    Y3, _ = scenegen.batch_scenes(g, A, seed=5)
+    assert not np.array_equal(Y, Y3)
