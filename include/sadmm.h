@@ -298,6 +298,9 @@ typedef struct {
   int fwd_choice, adj_choice;    /* the splits kept */
   int fwd_default, adj_default;  /* the splits a batch starts with (always among the candidates) */
 } sadmm_batch_tuning;
+/* Returns SADMM_EINVAL for a NULL batch or reps < 1, SADMM_ENOTREADY if an
+ * operator is missing, SADMM_ETIMEOUT if a tensor-core pipeline wait ran out
+ * during the timed launches. */
 int sadmm_batch_tune(sadmm_batch_t b, int reps, sadmm_batch_tuning* out);
 
 /* A group of batches with different geometries (Q, M, K, N may all differ),
@@ -380,17 +383,25 @@ int sadmm_adjoint(const float* A, int KM, int N, const int* idx, int nidx, const
                   float* g, void* stream);
 
 /* The factored representation of sadmm_set_operator_delays at kernel level
- * (device pointers).  sadmm_operator_tables: from tau (M x N doubles) writes
- * A (N x KM complex64, may be NULL), C (M x K/16 x N complex64) and
- * D (M x 16 x N complex64; C and D may both be NULL).  K = 16, 32, ..., 512
- * (a power of two) for C and D. */
+ * (Section II, Eq. 1; all pointers are device pointers owned by the caller,
+ * work is queued on `stream` and the call returns without synchronising).
+ * sadmm_operator_tables: from tau (M x N doubles, row m holds the delays of
+ * receiver m) writes A (N x KM complex64, pixel-major as sadmm_set_operator
+ * takes it; may be NULL), C (M x K/16 x N complex64: C[m][a][n] =
+ * exp(j 2 pi tau (f0 + 16 a df))) and D (M x 16 x N complex64: D[m][b][n] =
+ * exp(j 2 pi tau b df)); C and D may both be NULL.  Phases are formed in
+ * FP64 and rounded once.  K = 16, 32, ..., 512 (a power of two) for C and D;
+ * SADMM_EINVAL for bad sizes, a NULL tau, or non-finite f0 / df. */
 int sadmm_operator_tables(const double* tau, int M, int K, int N, double f0, double df, float* A, float* C,
                           float* D, void* stream);
-/* r = base - A_J v_J with A given by its factors C, D (as sadmm_forward). */
+/* r = base - A_J v_J with A given by its factors C, D (the layouts above; the
+ * other arguments as for sadmm_forward).  Partial sums use stream-ordered
+ * scratch that the call allocates and frees. */
 int sadmm_forward_factored(const float* C, const float* D, int M, int K, int N, const int* idx, int nidx,
                            const float* v, const float* base, float* r, void* stream);
-/* g[p] = Re(a_{idx[p]}^H w) with A given by its factors C, D (as sadmm_adjoint;
- * M K <= 16384). */
+/* g[p] = Re(a_{idx[p]}^H w) with A given by its factors C, D (the layouts
+ * above; the other arguments as for sadmm_adjoint; M K <= 16384, since w is
+ * staged in shared memory). */
 int sadmm_adjoint_factored(const float* C, const float* D, int M, int K, int N, const int* idx, int nidx,
                            const float* w, float* g, void* stream);
 
