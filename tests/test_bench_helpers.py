@@ -1,0 +1,42 @@
+"""Host-side measurement helpers of bench.py (no GPU): the DRAM traffic taken
+from the committed ncu summary only while the kernel's source files are the
+ones it was captured on, and the tuner-gain summary."""
+import json
+import os
+
+import pytest
+
+import bench
+
+
+def test_traffic_is_reported_only_for_the_captured_sources(tmp_path, monkeypatch):
+    root = tmp_path
+    csrc = root / "paper_2307_08606_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    (root / "profiles").mkdir()
+    (csrc / "k.cu").write_text("kernel v1")
+    monkeypatch.setattr(bench, "ROOT", str(root))
+    sha = bench.source_sha(["k.cu"])
+    entry = {"kernel": "k", "files": ["k.cu"], "source_sha": sha, "dram_bytes_per_launch": 1234}
+    (root / "profiles" / "traffic.json").write_text(json.dumps({"kernels": {"fwd": entry}}))
+    assert bench.traffic_for("fwd") == 1234.0
+    assert bench.traffic_for("other") is None
+    (csrc / "k.cu").write_text("kernel v2")          # the kernel changed since the capture
+    assert bench.traffic_for("fwd") is None
+
+
+def test_committed_traffic_summary_names_existing_sources():
+    with open(os.path.join(bench.ROOT, "profiles", "traffic.json")) as f:
+        t = json.load(f)
+    for name, e in t["kernels"].items():
+        assert e["dram_bytes_per_launch"] > 0, name
+        for fn in e["files"]:
+            assert os.path.exists(os.path.join(bench.ROOT, "paper_2307_08606_gb300", "csrc", fn)), fn
+
+
+def test_tuning_gain_is_relative_to_the_default_splits():
+    t = [{"forward": {2: 1.0, 4: 0.8}, "adjoint": {1: 2.0, 2: 1.5},
+          "forward_default": 2, "adjoint_default": 1, "forward_splits": 4, "adjoint_splits": 2}]
+    assert bench._tuning_gain(t) == pytest.approx((3.0 - 2.3) / 3.0)
+    t[0]["forward_splits"], t[0]["adjoint_splits"] = 2, 1
+    assert bench._tuning_gain(t) == 0.0
