@@ -480,3 +480,57 @@ def test_batch_scenes_follow_their_recipe():
         assert lams[s] == pytest.approx(0.05 * scenegen.lambda_max(A, ys), rel=1e-6)
     Y3, _ = scenegen.batch_scenes(g, A, seed=5)
     assert not np.array_equal(Y, Y3)
+
+
+# planted mistakes in the signal-model oracle: every one must fail its pins
+SM_MUTANTS = {
+    "row_index_swapped": ("A[:, m * K + k] =", "A[:, k * M + m] ="),
+    "phase_sign": ("np.exp(2j * np.pi * tau[m] * (f0 + k * df))", "np.exp(-2j * np.pi * tau[m] * (f0 + k * df))"),
+    "start_frequency_dropped": ("tau[m] * (f0 + k * df)", "tau[m] * (k * df)"),
+    "bp_coherent_sum": ("out += np.abs(np.asarray(Aq).astype(np.complex128).conj() @ np.asarray(yq).astype(np.complex128))",
+                        "out = out + (np.asarray(Aq).astype(np.complex128).conj() @ np.asarray(yq).astype(np.complex128)).real"),
+}
+
+
+def _sm_module(name=None):
+    import oracle.signal_model as osm
+    src = inspect.getsource(osm)
+    if name is not None:
+        old, new = SM_MUTANTS[name]
+        assert src.count(old) == 1, name
+        src = src.replace(old, new)
+    mod = types.ModuleType("oracle_sm_" + (name or "original"))
+    exec(compile(src, osm.__file__, "exec"), mod.__dict__)
+    return mod
+
+
+def _sm_pins_hold(m):
+    g = scenegen.Geometry(Q=2, M=3, K=16, nx=8, cell=0.05, radius=10.0, fc=77e9, bw=1e9)
+    ok = True
+    A = []
+    for q in range(g.Q):
+        tau = radar.delays(g, q)
+        Aq = m.operator_from_delays(tau, g.fc, g.bw / g.K, g.K)
+        A.append(Aq)
+        ok &= Aq.shape == (g.N, g.KM)
+        ok &= bool(np.max(np.abs(Aq - radar.operator(g, q).astype(np.complex128))) <= 2.0 ** -23)
+    n0, xq = 21, np.array([0.4, 0.7])
+    y = [xq[q] * A[q][n0] for q in range(g.Q)]
+    bp = m.backprojection(A, y)
+    ok &= bool(abs(bp[n0] - g.KM * xq.sum()) <= 1e-9 * g.KM)
+    ok &= int(np.argmax(bp)) == n0
+    st = scenegen.Stream(6, 1)
+    yr = [st.normal(g.KM) + 1j * st.normal(g.KM) for _ in range(g.Q)]
+    two = sum(np.hypot(oracle.adjoint_re(A[q], yr[q]), oracle.adjoint_re(A[q], -1j * yr[q])) for q in range(g.Q))
+    ok &= bool(np.allclose(m.backprojection(A, yr), two, rtol=1e-12))
+    return bool(ok)
+
+
+def test_signal_model_pins_hold_for_the_oracle():
+    assert _sm_pins_hold(_sm_module())
+
+
+@pytest.mark.parametrize("name", sorted(SM_MUTANTS))
+def test_signal_model_pins_catch_planted_mistakes(name):
+    with np.errstate(all="ignore"):
+        assert not _sm_pins_hold(_sm_module(name)), name
