@@ -692,9 +692,28 @@ def run_reference(args, rank, world):
     return 0
 
 
+def relaunch_under_torchrun(args):
+    """`--gpus N` (N > 1) started without a launcher: start the N ranks
+    ourselves (one process per GPU, torch.distributed.run on this node,
+    rendezvous on 127.0.0.1) and return their exit status."""
+    import socket
+    with socket.socket() as so:
+        so.bind(("127.0.0.1", 0))
+        port = so.getsockname()[1]
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={args.gpus}",
+           "--master-addr", "127.0.0.1", "--master-port", str(port), os.path.abspath(__file__)] + sys.argv[1:]
+    return subprocess.call(cmd)
+
+
 def main():
     args = parse()
     rank, local_rank, world = dist_env()
+    if args.gpus < 1:
+        raise SystemExit("--gpus must be >= 1")
+    if "WORLD_SIZE" not in os.environ and args.gpus > 1:
+        return relaunch_under_torchrun(args)
+    if world != args.gpus:
+        raise SystemExit(f"--gpus {args.gpus} but the launcher started {world} ranks (WORLD_SIZE)")
     if args.impl == "reference":
         return run_reference(args, rank, world)
 

@@ -367,9 +367,10 @@ int sadmm_forward(const float* A, int KM, int N, const int* idx, int nidx, const
  * It allocates nothing: the partial sums go to one fixed 8 MiB device array
  * that every GPU loading this library holds until the process exits.  Sizes
  * whose partial sums (chunks x KM x 16 bytes: double-float pairs) exceed
- * 8 MiB are rejected with SADMM_EINVAL and a message naming the sizes.  The first call on each device
- * looks up the array's device address (with that device current); make that
- * first call before any stream capture begins.  All calls on a device share
+ * 8 MiB are rejected with SADMM_EINVAL and a message naming the sizes.  Every
+ * call looks up the array's device address on the calling device (a lookup
+ * that allocates nothing), so the entry stays valid across a device reset.
+ * All calls on a device share
  * the array and it keeps the last call's contents; every entry a call reads is
  * written earlier in the same call, so nothing needs clearing, but calls whose
  * work overlaps on the GPU (different streams, or different host threads) race
@@ -455,6 +456,16 @@ int sadmm_factor_update(const float* A, int KM, const int* E, int e, double mu, 
  * significant bits).  Allocates the packed copy and partial sums on `stream`
  * and synchronises it.  SADMM_ETIMEOUT if a tile copy did not complete. */
 int sadmm_spd_apply(const double* F, int n, int ldf, const float* u, float* out, void* stream);
+
+/* Failure-handling test hook (the paper has no counterpart).  Sets how many
+ * times the symmetric factor apply (sadmm_spd_apply and the solver's x-update)
+ * polls the barrier of each tile copy before it gives up and reports
+ * SADMM_ETIMEOUT; polls < 0 restores the default (2^26).  A CTA that gives up
+ * still waits, with the default limit, for the copy in flight into its shared
+ * memory before it exits, so a short limit ends the apply early without
+ * leaving work on the GPU.  It applies to the current device and to every
+ * later launch until changed.  SADMM_ECUDA if the device value cannot be set. */
+int sadmm_set_wait_limit(long long polls);
 
 /* G = Re(A^H W) for one sensor and 16 right-hand sides on the tensor cores:
  * the adjoint product of the batched form (Eq. 3, x_q-update for 16 scenes),

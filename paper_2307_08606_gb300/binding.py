@@ -99,6 +99,7 @@ _SIGS = {
     "sadmm_factor": (C.c_int, [_P, C.c_int, C.c_int, _P, C.c_int, C.c_double, C.c_double, _P,
                                C.c_int, C.POINTER(C.c_int), _P]),
     "sadmm_spd_apply": (C.c_int, [_P, C.c_int, C.c_int, _P, _P, _P]),
+    "sadmm_set_wait_limit": (C.c_int, [C.c_longlong]),
     "sadmm_factor_downdate": (C.c_int, [_P, C.c_int, _P, C.c_int, C.c_double, _P, _P]),
     "sadmm_factor_update": (C.c_int, [_P, C.c_int, _P, C.c_int, C.c_double, C.c_int, _P, _P]),
     "sadmm_adjoint16_tc": (C.c_int, [_P, C.c_int, C.c_int, _P, _P, _P]),
@@ -668,3 +669,9 @@ def spd_apply(F, n, u, out=None, stream=0):
         out = torch.empty(n, dtype=torch.float32, device=F.device)
     check(load().sadmm_spd_apply(_ptr(F), n, F.shape[1], _ptr(u), _ptr(out), C.c_void_p(stream)))
     return out
+
+
+def set_wait_limit(polls):
+    """Polls of the factor apply's tile-copy wait before it reports
+    SADMM_ETIMEOUT (failure-handling tests); polls < 0 restores the default."""
+    check(load().sadmm_set_wait_limit(int(polls)))

@@ -728,6 +728,20 @@ sadmm_iter_record make_record(const Ctx& c, const IterScalars& r, int changed, i
   return rec;
 }
 
+// Reads and clears the factor apply's timeout flag; SADMM_ETIMEOUT if it was
+// set.  A timed-out apply leaves its outputs unwritten, so this status takes
+// precedence over a non-finite iterate that it may have caused.
+int take_timeout(Ctx& c) {
+  int spd_err = 0;
+  SADMM_CUDA_TRY(cudaMemcpyAsync(&spd_err, c.spd_err, sizeof(int), cudaMemcpyDeviceToHost, c.st));
+  SADMM_CUDA_TRY(cudaStreamSynchronize(c.st));
+  if (!spd_err) return SADMM_OK;
+  SADMM_CUDA_TRY(cudaMemsetAsync(c.spd_err, 0, sizeof(int), c.st));
+  SADMM_CUDA_TRY(cudaStreamSynchronize(c.st));
+  set_error("factor apply: a tile copy did not complete within the wait limit");
+  return SADMM_ETIMEOUT;
+}
+
 int run(Ctx& c, float* x_out, int iters, double tol, sadmm_stats* st) {
   const double t0 = now_ms();
   double t_ref = 0.0, bytes = 0.0;
@@ -757,6 +771,7 @@ int run(Ctx& c, float* x_out, int iters, double tol, sadmm_stats* st) {
     done = iters;
     for (int it = 0; it < iters; ++it) {
       if (h[it].nonfinite) {
+        SADMM_TRY(take_timeout(c));
         set_error("non-finite value in iteration %d", h[it].k);
         return SADMM_ENONFINITE;
       }
@@ -774,6 +789,7 @@ int run(Ctx& c, float* x_out, int iters, double tol, sadmm_stats* st) {
       done += 1;
       const IterScalars& r = *c.h_scal;
       if (r.nonfinite) {
+        SADMM_TRY(take_timeout(c));
         set_error("non-finite value in iteration %d", c.k);
         return SADMM_ENONFINITE;
       }
@@ -817,14 +833,7 @@ int run(Ctx& c, float* x_out, int iters, double tol, sadmm_stats* st) {
     SADMM_TRY(launch_scale(c.zbar, (float)c.Q, c.xg, c.N, c.st));
     SADMM_CUDA_TRY(cudaMemcpyAsync(x_out, c.xg, c.N * sizeof(float), cudaMemcpyDefault, c.st));
   }
-  int spd_err = 0;
-  SADMM_CUDA_TRY(cudaMemcpyAsync(&spd_err, c.spd_err, sizeof(int), cudaMemcpyDeviceToHost, c.st));
-  SADMM_CUDA_TRY(cudaStreamSynchronize(c.st));
-  if (spd_err) {
-    SADMM_CUDA_TRY(cudaMemsetAsync(c.spd_err, 0, sizeof(int), c.st));
-    set_error("factor apply: a tile copy did not complete within the wait limit");
-    return SADMM_ETIMEOUT;
-  }
+  SADMM_TRY(take_timeout(c));
   if (st) {
     memset(st, 0, sizeof *st);
     st->iters = done;
@@ -1520,6 +1529,8 @@ int sadmm_adjoint_split(const void* hi, const void* lo, int kind, int planes, in
   SolverView sv{};
   return launch_split_adjoint(&as, 1, KM, kind, planes, false, sv, (cudaStream_t)stream);
 }
+
+int sadmm_set_wait_limit(long long polls) { return sadmm::set_spd_wait_limit(polls); }
 
 int sadmm_spd_apply(const double* F, int n, int ldf, const float* u, float* out, void* stream) {
   using namespace sadmm;

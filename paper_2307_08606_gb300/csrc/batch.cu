@@ -162,11 +162,16 @@ bspd_tile_kernel(const float2* const* __restrict__ Pq, const float* const* __res
     }
     __syncthreads();                                        // su written
     const bool ok = mbar_wait(&bar, phase);
-    phase ^= 1u;
     if (!__syncthreads_and(ok)) {
-      if (tid == 0) atomicExch(err, 1);
+      // the timed-out copy writes this CTA's shared memory: let it land
+      // (bounded) before the CTA exits
+      if (tid == 0) {
+        mbar_wait(&bar, phase);
+        atomicExch(err, 1);
+      }
       return;
     }
+    phase ^= 1u;
     const float* uI = su;
     const float* uJ = uI + kT * kBS;
     DF acc[4][4];

@@ -188,6 +188,8 @@ struct SpdSet {
 // *err is set to 1 if a tile copy did not complete within the wait limit.
 int launch_spd_apply(const SpdSet* sets, int nsets, bool update, const SolverView& sv, int* err,
                      cudaStream_t st);
+// Polls of the factor apply's tile-copy wait before it gives up (< 0: the default).
+int set_spd_wait_limit(long long polls);
 
 // Back-projection helpers (elementwise.cu): out = -i y; out = sum_q |g_re + i g_im|
 // with g laid out per sensor as [re N][im N].

@@ -12,7 +12,6 @@
 #include "symtile.cuh"
 
 #include <algorithm>
-#include <mutex>
 
 namespace sadmm {
 
@@ -373,30 +372,17 @@ namespace sadmm {
 namespace {
 
 constexpr size_t kNoAllocScratchBytes = size_t(8) << 20;   // 8 MiB per GPU
-constexpr int kMaxDevices = 64;
-
 __device__ __align__(256) float4 g_noalloc_partial[kNoAllocScratchBytes / sizeof(float4)];
-
-std::mutex g_noalloc_mu;
-void* g_noalloc_ptr[kMaxDevices] = {};
 
 // Device address of the scratch array on the current device.  Host code must
 // not use the array's name as a pointer: it only stands for the symbol.  The
-// address is looked up once per device, with that device current.
+// address is looked up on every call, with the calling device current, so a
+// device reset or a new primary context never leaves a stale address behind;
+// the lookup allocates nothing.
 int noalloc_scratch(void** out) {
-  int dev = 0;
-  SADMM_CUDA_TRY(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= kMaxDevices) {
-    set_error("sadmm_forward_noalloc: device ordinal %d out of range", dev);
-    return SADMM_EINVAL;
-  }
-  std::lock_guard<std::mutex> lock(g_noalloc_mu);
-  if (!g_noalloc_ptr[dev]) {
-    void* p = nullptr;
-    SADMM_CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_partial));
-    g_noalloc_ptr[dev] = p;
-  }
-  *out = g_noalloc_ptr[dev];
+  void* p = nullptr;
+  SADMM_CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_partial));
+  *out = p;
   return SADMM_OK;
 }
 

@@ -30,6 +30,11 @@ namespace {
 
 using namespace symtile;
 constexpr int kTileBytes = kT * kT * (int)sizeof(float2);
+
+// Polls of the tile-copy wait before the apply gives up (sadmm_set_wait_limit
+// lowers it so that tests can make the wait run out; the drain wait that
+// follows a timeout always uses the full limit).
+__device__ long long g_spd_wait_limit = kWaitLimit;
 constexpr int kSpdThreads = 2 * kT;           // 64 row threads + 64 column threads
 
 // item -> (set, tile): items are numbered set after set
@@ -77,12 +82,18 @@ spd_tile_kernel(const __grid_constant__ SetBlock<SpdSet> sets, int nsets, int it
       if (ULO) s_ul[lt >> 6][r] = i < ss.n ? ss.u_lo[i] : 0.f;
     }
     __syncthreads();                                   // s_u written
-    const bool ok = mbar_wait(&bar, phase);
-    phase ^= 1u;
+    const bool ok = mbar_wait(&bar, phase, g_spd_wait_limit);
     if (!__syncthreads_and(ok)) {
-      if (tid == 0) atomicExch(err, 1);              // the one copy in flight is the one that timed out
+      // give up on this apply, but only after the one copy in flight (the one
+      // that timed out) has landed: it writes this CTA's shared memory, which
+      // must stay allocated until then (bounded by the full limit)
+      if (tid == 0) {
+        mbar_wait(&bar, phase);
+        atomicExch(err, 1);
+      }
       return;
     }
+    phase ^= 1u;
     DF acc0{0.f, 0.f}, acc1{0.f, 0.f};
     if (lt < kT) {
       // row r of F_IJ times u_J, two columns per 16-byte load: pairs
@@ -200,6 +211,12 @@ __global__ void pack_sym_kernel(const double* __restrict__ F, int ld, int n, flo
 }
 
 }  // namespace
+
+int set_spd_wait_limit(long long polls) {
+  const long long v = polls < 0 ? kWaitLimit : polls;
+  SADMM_CUDA_TRY(cudaMemcpyToSymbol(g_spd_wait_limit, &v, sizeof(v)));
+  return SADMM_OK;
+}
 
 size_t sym_packed_pairs(int n) {
   const size_t nt = ntiles_side(n);

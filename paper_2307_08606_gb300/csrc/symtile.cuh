@@ -90,9 +90,9 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned b
       : "memory");
 }
 
-// Waits for phase `parity` of the barrier; false after kWaitLimit polls.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
-  for (long long it = 0; it < kWaitLimit; ++it) {
+// Waits for phase `parity` of the barrier; false after `limit` polls.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, long long limit = kWaitLimit) {
+  for (long long it = 0; it < limit; ++it) {
     unsigned ok;
     asm volatile(
         "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"

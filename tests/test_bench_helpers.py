@@ -40,3 +40,21 @@ def test_tuning_gain_is_relative_to_the_default_splits():
     assert bench._tuning_gain(t) == pytest.approx((3.0 - 2.3) / 3.0)
     t[0]["forward_splits"], t[0]["adjoint_splits"] = 2, 1
     assert bench._tuning_gain(t) == 0.0
+
+
+def test_gpus_flag_starts_that_many_ranks(monkeypatch):
+    """`--gpus N` without a launcher re-runs the bench under
+    torch.distributed.run with N processes on 127.0.0.1; a launcher that
+    started a different number of ranks than --gpus is refused."""
+    calls = []
+    monkeypatch.setattr(bench.subprocess, "call", lambda cmd: calls.append(cmd) or 0)
+    monkeypatch.delenv("WORLD_SIZE", raising=False)
+    monkeypatch.setattr(bench.sys, "argv", ["bench.py", "--gpus", "4", "--steps", "2"])
+    assert bench.main() == 0
+    cmd = calls[0]
+    assert cmd[1:3] == ["-m", "torch.distributed.run"]
+    assert "--nproc-per-node=4" in cmd and "127.0.0.1" in cmd
+    assert cmd[-4:] == ["--gpus", "4", "--steps", "2"] and cmd[-5].endswith("bench.py")
+    monkeypatch.setenv("WORLD_SIZE", "2")
+    with pytest.raises(SystemExit, match="--gpus 4 but the launcher started 2 ranks"):
+        bench.main()

@@ -155,6 +155,56 @@ def test_spd_apply_matches_fp64(B, n, ld):
     assert np.all(np.abs(out - ref) <= U32 * np.abs(ref) + (2 * n + 8) * 2.0 ** -47 * mag)
 
 
+def test_bounded_wait_runs_out_and_the_next_call_succeeds(B):
+    """The factor apply's tile-copy wait is bounded: with its limit set to
+    zero polls every wait gives up at once, the CTA waits (with the full
+    limit) for its copy in flight and the call reports SADMM_ETIMEOUT, with
+    the context still usable; with the limit restored the same call succeeds
+    and is correct.  Also through the solver: a solve under the zero limit
+    reports SADMM_ETIMEOUT, and the next solve matches a clean run."""
+    n, ld = 300, 320
+    s = scenegen.Stream(19, n)
+    M = s.normal(n * n).reshape(n, n)
+    F = np.zeros((ld, ld))
+    F[:n, :n] = M + M.T
+    u = s.normal(n).astype(np.float32)
+    dev = torch.device("cuda:0")
+    Ft, ut = torch.from_numpy(F).to(dev), torch.from_numpy(u).to(dev)
+    try:
+        B.set_wait_limit(0)
+        with pytest.raises(B.SadmmError) as ei:
+            B.spd_apply(Ft, n, ut)
+        assert ei.value.status == B.ETIMEOUT
+    finally:
+        B.set_wait_limit(-1)
+    out = B.spd_apply(Ft, n, ut).cpu().numpy().astype(np.float64)
+    ref = F[:n, :n] @ u.astype(np.float64)
+    mag = np.abs(F[:n, :n]) @ np.abs(u.astype(np.float64))
+    assert np.all(np.abs(out - ref) <= U32 * np.abs(ref) + (2 * n + 8) * 2.0 ** -47 * mag)
+
+    sc = scenegen.build_scene("small_point", seed=3)
+    lam = 0.05 * scenegen.lambda_max(sc.A, sc.y)
+    g = sc.geom
+    sol = B.Solver(g.Q, g.M, g.K, g.N, 1.0, lam, elim=0)
+    try:
+        for q in range(g.Q):
+            sol.set_operator(q, sc.A[q])
+        sol.prepare()
+        xg_ref, _ = sol.solve(sc.y, 10)
+        X_ref = sol.X()
+        try:
+            B.set_wait_limit(0)
+            with pytest.raises(B.SadmmError) as ei:
+                sol.solve(sc.y, 10)
+            assert ei.value.status == B.ETIMEOUT
+        finally:
+            B.set_wait_limit(-1)
+        sol.solve(sc.y, 10)
+        assert np.array_equal(sol.X(), X_ref)
+    finally:
+        sol.close()
+
+
 @pytest.mark.parametrize("KM,N,e", [(32, 300, 1), (32, 300, 7), (128, 700, 40), (256, 1024, 3)])
 def test_factor_downdate_matches_fresh_inverse(B, KM, N, e):
     """Rank-e downdate of the Woodbury factor equals the FP64 inverse of the
