@@ -415,6 +415,24 @@ int sadmm_adjoint_factored(const float* C, const float* D, int M, int K, int N, 
 int sadmm_factor(const float* A, int KM, int N, const int* idx, int nidx, double mu,
                  double rho, double* F, int ldf, int* form, void* stream);
 
+/* The first step of sadmm_factor alone: F = mu G + rho I, the matrix of the
+ * x-update system (Eq. 3, x_q-update), with G = B_J^T B_J (primal form, n =
+ * nidx, when nidx <= 2KM) or G = B_J B_J^T (Woodbury form, n = 2KM), rows
+ * interleaved (re, im) as in sadmm_factor; F row-major FP64 with leading
+ * dimension ldf = roundup(n, 64), both triangles written, padding set to the
+ * identity.  method 0 (what the solver's factor uses): tensor cores on exact
+ * BF16 digit slices of the operator (each Gram row scaled by a power of two,
+ * four 8-bit digits per entry, the ten digit products of orders 2..5, exact
+ * integer chunk sums drained to double-float totals): within about 2^-36 of
+ * each entry's row and column scale 2^(e_i + e_j), e_i the least exponent
+ * with max |row i| <= 2^e_i; transient scratch of 4 x 2 bytes per padded
+ * operand entry from the stream-ordered pool.  method 1: FP64 SIMT (KM a
+ * multiple of 8).  Synchronises `stream`.  SADMM_EINVAL for bad sizes,
+ * SADMM_ENOMEM without scratch, SADMM_ETIMEOUT if a bounded device wait
+ * gave up.  form (host pointer, may be NULL) receives 1 for the Woodbury form. */
+int sadmm_gram(const float* A, int KM, int N, const int* idx, int nidx, double mu, double rho, int method,
+               double* F, int ldf, int* form, void* stream);
+
 /* Split-precision operator planes: for each of the 2 n_complex floats a of A,
  * hi = round(a) and lo = round(a - hi) in BF16 (kind 1) or FP16 (kind 2),
  * round-to-nearest; hi + lo is exact in FP32.  hi and lo: device arrays of

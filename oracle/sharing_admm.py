@@ -319,6 +319,75 @@ def sadmm(A, y, rho, lam, crit: Criterion, iters, tol=0.0, state: State = None, 
     return res
 
 
+def sadmm_primal_inverse(A, y, rho, lam, mu=1.0, iters=1000, tol=0.0, record=None):
+    """Plain SADMM (Eq. 3 with every selector the identity: no elimination)
+    for problems whose sensors each resolve the grid (N <= 2KM, so the x-update
+    is taken in its primal form), held in the memory of Q explicit inverses.
+
+    Per sensor, one after another, in FP64 from the complex operator
+    (pixel-major, N x KM):
+        G_q = B_q^T B_q = Re(A_q^H A_q)  (two symmetric rank-KM products of the
+                                          real and imaginary parts),
+        H_q = (rho I + mu G_q)^{-1}       (Cholesky factor, then its inverse),
+        c_q = mu B_q^T [Re y_q; Im y_q] = mu Re(A_q^H y_q).
+    Each iteration is steps 1-5 of the plain iteration (see sadmm): the
+    x-update x_q = H_q (c_q + rho (x_q - x_bar + z_bar - s)) for every q, then
+    x_bar = mean_q x_q, z_bar = soft(x_bar + s, lam / rho), s += x_bar - z_bar,
+    and the relative change of the stacked iterate.  The same iterates as
+    sadmm(..., Criterion(elim=0)) up to rounding (an explicit inverse instead
+    of two triangular solves).  Stops after `iters` iterations or when the
+    relative change is <= tol.  record(k, x_G) is called after every
+    iteration when given.  Returns a Result whose state holds X, x_bar, z_bar,
+    s (J = all pixels, y' = y, the ring unused)."""
+    from scipy.linalg import blas, lapack
+    Q = len(A)
+    N, KM = np.asarray(A[0]).shape
+    if N > 2 * KM:
+        raise ValueError("sadmm_primal_inverse needs N <= 2KM (the primal form)")
+    H, c = [], []
+    for q in range(Q):
+        Ar = np.asarray(A[q]).real.astype(np.float64)
+        Ai = np.asarray(A[q]).imag.astype(np.float64)
+        # Ar, Ai are C-ordered N x KM: their transposes are Fortran-ordered KM x N
+        G = blas.dsyrk(mu, Ar.T, trans=1, lower=0)
+        G = blas.dsyrk(mu, Ai.T, beta=1.0, c=G, trans=1, lower=0, overwrite_c=1)
+        yq = np.asarray(y[q]).astype(np.complex128)
+        c.append(mu * (Ar @ yq.real + Ai @ yq.imag))
+        del Ar, Ai
+        G[np.diag_indices(N)] += rho
+        L, info = lapack.dpotrf(G, lower=0, overwrite_a=1)
+        if info != 0:
+            raise np.linalg.LinAlgError(f"sensor {q}: rho I + mu G is not positive definite ({info})")
+        Hq, info = lapack.dpotri(L, lower=0, overwrite_c=1)
+        if info != 0:
+            raise np.linalg.LinAlgError(f"sensor {q}: inverse failed ({info})")
+        Hq = np.triu(Hq)                     # the upper triangle holds the inverse
+        Hq += np.triu(Hq, 1).T
+        H.append(np.ascontiguousarray(Hq))
+        del L, G
+    st = initial_state(A, y, 1)
+    res = Result(st)
+    for it in range(iters):
+        x_old = st.x.copy()
+        for q in range(Q):
+            v = st.x[q] - st.xbar + st.zbar - st.s
+            st.x[q] = H[q] @ (c[q] + rho * v)
+        xbar_new = st.x.mean(axis=0)
+        zbar_new = soft(xbar_new + st.s, lam / rho)
+        st.s = st.s + xbar_new - zbar_new
+        st.xbar, st.zbar = xbar_new, zbar_new
+        st.k += 1
+        nx = np.linalg.norm(st.x)
+        relchange = np.linalg.norm(st.x - x_old) / nx if nx > 0 else np.inf
+        res.history.append(dict(k=st.k, relchange=relchange))
+        if record is not None:
+            record(st.k, Q * st.zbar)
+        if tol > 0 and relchange <= tol:
+            res.stop_reason = "tol"
+            break
+    return res
+
+
 def objective(A, y, X, lam, mu=1.0, B=None):
     """Eq. 2 objective with the selectors equal to the identity."""
     B = B if B is not None else [real_form(a) for a in A]

@@ -100,6 +100,8 @@ _SIGS = {
                                C.c_int, C.POINTER(C.c_int), _P]),
     "sadmm_spd_apply": (C.c_int, [_P, C.c_int, C.c_int, _P, _P, _P]),
     "sadmm_set_wait_limit": (C.c_int, [C.c_longlong]),
+    "sadmm_gram": (C.c_int, [_P, C.c_int, C.c_int, _P, C.c_int, C.c_double, C.c_double, C.c_int, _P, C.c_int, _P,
+                             _P]),
     "sadmm_factor_downdate": (C.c_int, [_P, C.c_int, _P, C.c_int, C.c_double, _P, _P]),
     "sadmm_factor_update": (C.c_int, [_P, C.c_int, _P, C.c_int, C.c_double, C.c_int, _P, _P]),
     "sadmm_adjoint16_tc": (C.c_int, [_P, C.c_int, C.c_int, _P, _P, _P]),
@@ -675,3 +677,19 @@ def set_wait_limit(polls):
     """Polls of the factor apply's tile-copy wait before it reports
     SADMM_ETIMEOUT (failure-handling tests); polls < 0 restores the default."""
     check(load().sadmm_set_wait_limit(int(polls)))
+
+
+def gram(A, idx, mu, rho, method=0, stream=0):
+    """(F, form, n): F = mu G + rho I of the x-update system for the active
+    columns idx of the pixel-major complex64 operator A (device tensors); the
+    tensor-core digit method (0) or FP64 SIMT (1)."""
+    import torch
+    N, KM = A.shape
+    nidx = int(idx.numel())
+    n = 2 * KM if nidx > 2 * KM else nidx
+    npad = (n + 63) // 64 * 64
+    F = torch.empty((npad, npad), dtype=torch.float64, device=A.device)
+    form = C.c_int(0)
+    check(load().sadmm_gram(_ptr(A), KM, N, _ptr(idx), nidx, float(mu), float(rho), int(method), _ptr(F), npad,
+                            C.byref(form), C.c_void_p(stream)))
+    return F, form.value, n

@@ -269,11 +269,15 @@ int refresh(Ctx& c, const std::vector<int>& qs, bool full_set) {
   SADMM_CUDA_TRY(cudaMemsetAsync(c.dstatus, 0, sizeof(int) * c.Q, c.st));
   for (size_t b = 0; b < jobs.size(); b += kMaxSets) {
     const int nj = (int)std::min<size_t>(kMaxSets, jobs.size() - b);
-    SADMM_TRY(run_factor(jobs.data() + b, nj, c.KM, c.crit.mu, c.rho, c.dstatus, c.st));
+    SADMM_TRY(run_factor(jobs.data() + b, nj, c.KM, c.crit.mu, c.rho, c.dstatus + b, c.st));
   }
   SADMM_CUDA_TRY(cudaMemcpyAsync(c.h_status, c.dstatus, sizeof(int) * c.Q, cudaMemcpyDeviceToHost, c.st));
   SADMM_CUDA_TRY(cudaStreamSynchronize(c.st));
   for (size_t i = 0; i < jobs.size(); ++i) {
+    if (c.h_status[i] == 2) {
+      set_error("factor of sensor %d: a bounded wait of the tensor-core Gram timed out", owner[i]);
+      return SADMM_ETIMEOUT;
+    }
     if (c.h_status[i]) {
       set_error("factor of sensor %d is not positive definite (non-finite operator?)", owner[i]);
       return SADMM_ENONFINITE;
@@ -1439,7 +1443,39 @@ int sadmm_factor(const float* A, int KM, int N, const int* idx, int nidx, double
   cudaFreeAsync(dinv, st);
   cudaFreeAsync(status, st);
   if (rc != SADMM_OK) return rc;
+  if (hs == 2) { set_error("sadmm_factor: a bounded wait of the tensor-core Gram timed out"); return SADMM_ETIMEOUT; }
   if (hs) { set_error("sadmm_factor: matrix not positive definite"); return SADMM_ENONFINITE; }
+  if (form) *form = wb;
+  return SADMM_OK;
+}
+
+int sadmm_gram(const float* A, int KM, int N, const int* idx, int nidx, double mu, double rho, int method,
+               double* F, int ldf, int* form, void* stream) {
+  using namespace sadmm;
+  if (!A || !idx || !F || KM <= 0 || KM % 2 != 0 || N <= 0 || nidx <= 0 || nidx > N || !(rho >= 0.0) ||
+      !(mu > 0.0) || (method != 0 && method != 1) || (method == 1 && KM % 8 != 0)) {
+    set_error("sadmm_gram: bad arguments");
+    return SADMM_EINVAL;
+  }
+  const int wb = nidx > 2 * KM ? 1 : 0;
+  const int n = wb ? 2 * KM : nidx;
+  const int npad = round_up(n, kTile);
+  if (ldf != npad) { set_error("sadmm_gram: ldf must equal roundup(n, 64) = %d", npad); return SADMM_EINVAL; }
+  cudaStream_t st = (cudaStream_t)stream;
+  void* status = nullptr;
+  SADMM_CUDA_TRY(cudaMallocAsync(&status, sizeof(int), st));
+  int rc = cudaMemsetAsync(status, 0, sizeof(int), st) == cudaSuccess ? SADMM_OK : SADMM_ECUDA;
+  FactorJob j{(const float2*)A, idx, nidx, n, npad, wb, F, nullptr, nullptr};
+  if (rc == SADMM_OK) rc = run_gram(j, KM, mu, rho, (int*)status, st, method);
+  int hs = 0;
+  if (rc == SADMM_OK) {
+    SADMM_CUDA_TRY(cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    SADMM_CUDA_TRY(cudaStreamSynchronize(st));
+  }
+  cudaError_t fe = cudaFreeAsync(status, st);
+  if (rc != SADMM_OK) return rc;
+  SADMM_CUDA_TRY(fe);
+  if (hs) { set_error("sadmm_gram: a bounded wait of the tensor-core Gram timed out"); return SADMM_ETIMEOUT; }
   if (form) *form = wb;
   return SADMM_OK;
 }

@@ -261,8 +261,19 @@ struct FactorJob {
   double* tmp;       // npad x npad scratch (inverse of the Cholesky factor)
   double* dinv;      // (npad / kTile) x kTile x kTile inverses of the diagonal blocks
 };
+// gram: 0 = tensor-core Gram from exact BF16 digit slices (gram_tc.cu; takes
+// transient scratch from the stream-ordered pool), 1 = SIMT FP64 Gram.
+// d_status[i] is set to 1 if job i's matrix is not positive definite, 2 if a
+// bounded wait of its Gram timed out.
 int run_factor(const FactorJob* jobs, int njobs, int KM, double mu, double rho, int* d_status,
-               cudaStream_t st);
+               cudaStream_t st, int gram = 0);
+// The Gram step alone: job.out = mu G + rho I (identity padding), same methods.
+int run_gram(const FactorJob& job, int KM, double mu, double rho, int* d_status, cudaStream_t st, int gram);
+size_t gram_tc_scratch_bytes(const FactorJob& j, int KM);
+// job.out (npad x npad, leading dimension npad) = mu G + rho I with identity
+// padding, G the Gram of the job's form; *err = 2 on a timed-out wait.
+int launch_gram_tc(const FactorJob& j, int KM, double mu, double rho, void* scratch, size_t scratch_bytes, int* err,
+                   cudaStream_t st);
 
 // Rank-e downdate of a Woodbury-form factor after removing e <= kDowndateMax
 // columns E from the active set (Eq. 3's system without those pixels):

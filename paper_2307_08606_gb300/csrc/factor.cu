@@ -859,8 +859,35 @@ int run_primal_downdate(const PrimalDdJob* jobs, int njobs, int* d_status, cudaS
   return SADMM_OK;
 }
 
+int run_gram(const FactorJob& job, int KM, double mu, double rho, int* d_status, cudaStream_t st, int gram) {
+  if (job.npad % T != 0 || job.n > job.npad) {
+    set_error("run_gram: bad padding");
+    return SADMM_EINVAL;
+  }
+  if (gram == 0) {
+    const size_t bytes = gram_tc_scratch_bytes(job, KM);
+    void* scratch = nullptr;
+    if (cudaMallocAsync(&scratch, bytes, st) != cudaSuccess) {
+      cudaGetLastError();
+      set_error("run_gram: %zu bytes of Gram scratch unavailable", bytes);
+      return SADMM_ENOMEM;
+    }
+    const int rc = launch_gram_tc(job, KM, mu, rho, scratch, bytes, d_status, st);
+    cudaError_t fe = cudaFreeAsync(scratch, st);
+    if (rc != SADMM_OK) return rc;
+    SADMM_CUDA_TRY(fe);
+    return SADMM_OK;
+  }
+  JobBlock blk;
+  blk.v[0] = job;
+  const int Tn = job.npad / T;
+  gram_kernel<<<dim3(Tn * (Tn + 1) / 2, 1, 1), kThreads, 0, st>>>(blk, KM, mu, rho);
+  SADMM_LAUNCH_CHECK();
+  return SADMM_OK;
+}
+
 int run_factor(const FactorJob* jobs, int njobs, int KM, double mu, double rho, int* d_status,
-               cudaStream_t st) {
+               cudaStream_t st, int gram) {
   if (njobs <= 0) return SADMM_OK;
   if (njobs > kMaxSets) { set_error("run_factor: too many jobs"); return SADMM_EINVAL; }
   JobBlock blk;
@@ -882,8 +909,27 @@ int run_factor(const FactorJob* jobs, int njobs, int KM, double mu, double rho, 
     configured = true;
   }
   const int ntri = Tmax * (Tmax + 1) / 2;
-  gram_kernel<<<dim3(ntri, 1, njobs), kThreads, 0, st>>>(blk, KM, mu, rho);
-  SADMM_LAUNCH_CHECK();
+  if (gram == 0) {
+    // tensor-core Gram, one job after another (each fills the GPU), in one
+    // transient digit buffer sized for the largest job
+    size_t bytes = 0;
+    for (int i = 0; i < njobs; ++i) bytes = std::max(bytes, gram_tc_scratch_bytes(jobs[i], KM));
+    void* scratch = nullptr;
+    if (cudaMallocAsync(&scratch, bytes, st) != cudaSuccess) {
+      cudaGetLastError();
+      set_error("run_factor: %zu bytes of Gram scratch unavailable", bytes);
+      return SADMM_ENOMEM;
+    }
+    int rc = SADMM_OK;
+    for (int i = 0; i < njobs && rc == SADMM_OK; ++i)
+      rc = launch_gram_tc(jobs[i], KM, mu, rho, scratch, bytes, d_status + i, st);
+    cudaError_t fe = cudaFreeAsync(scratch, st);
+    if (rc != SADMM_OK) return rc;
+    SADMM_CUDA_TRY(fe);
+  } else {
+    gram_kernel<<<dim3(ntri, 1, njobs), kThreads, 0, st>>>(blk, KM, mu, rho);
+    SADMM_LAUNCH_CHECK();
+  }
   for (int kb = 0; kb < Tmax; ++kb) {
     potrf_diag_kernel<<<njobs, kThreads, potrf_smem, st>>>(blk, kb, d_status);
     SADMM_LAUNCH_CHECK();

@@ -26,7 +26,8 @@
 // flight, frees its tensor memory and exits.
 #include "common.cuh"
 
-#include <cuda.h>
+#include "tmap.cuh"
+
 #include <cstring>
 
 namespace sadmm {
@@ -584,11 +585,6 @@ tc_forward_kernel(const __grid_constant__ TmapSet tmaps, const __grid_constant__
 
 }  // namespace
 
-namespace {
-typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
 // The tensor-map encoder comes from the driver through the runtime, so the
 // library needs no link-time dependency on libcuda.
 EncodeTiledFn tensor_map_encoder() {
@@ -604,7 +600,6 @@ EncodeTiledFn tensor_map_encoder() {
   }
   return fn;
 }
-}  // namespace
 
 int tc_adjoint_max_splits(int KM) { return std::max(1, (2 * KM) / (4 * kTcK)); }
 

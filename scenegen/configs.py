@@ -16,6 +16,13 @@
 * ``precision_twin``: the sensors of the 256x256 precision workload (Q=8,
   M=16, K=512, KM=8192) over a 64x64 crop of 5 cm cells, 8 clusters, p=0.7,
   20 dB: the size the FP64 oracle checks that workload's forms at.
+* ``resolved_128``: the paper-scale problem size (Q=8 sensors, N=128x128
+  pixels) on a geometry where every sensor resolves the grid on its own, so
+  that Eq. 2 has a unique, nonzero minimiser: 8 cm cells (a 10.24 m scene)
+  seen from an 8 m circle by sensors with M=256 receivers at 60 GHz, BW=4 GHz,
+  K=64 (KM=16384: 2KM = 2N, Gram condition ~8.5e4, as resolved_32's); the
+  scene law of ``paper_scale`` (40 clusters of 1..9 pixels, magnitudes
+  U[0.3, 1], p=0.7, 15 dB SNR).
 * ``resolved_tiny``: a well-posed geometry used by the oracle's pins: 8x8
   pixels of 10 cm seen from 0.6 m by sensors with M=16 antennas and BW=4 GHz
   at 60 GHz (K=16, KM=256 > N), so that every sensor resolves the grid on its
@@ -48,6 +55,9 @@ GEOMS = {
     # 32x32 grid that every sensor resolves on its own (2KM = 2N, condition ~300):
     # Eq. 2 is well posed, so the iterates converge to a nonzero image
     "resolved_32": Geometry(Q=4, M=32, K=32, nx=32, cell=0.08, radius=2.0, fc=60e9, bw=4e9),
+    # Q=8, N=128x128 with every sensor resolving the grid (2KM = 2N, Gram
+    # condition ~8.5e4): the paper-scale size of a well-posed Eq. 2
+    "resolved_128": Geometry(Q=8, M=256, K=64, nx=128, cell=0.08, radius=8.0, fc=60e9, bw=4e9),
     # the precision-form sensors (Q=8, M=16, K=512: KM=8192) over a 64x64 crop
     # of 5 cm cells, the oracle-sized twin of the 256x256 precision workload
     "precision_twin": Geometry(Q=8, M=16, K=512, nx=64, cell=0.05, radius=10.0, fc=77e9, bw=1e9),
@@ -58,7 +68,7 @@ def build_scene(name: str, seed: int = 0, geom: Geometry = None, snr_db="default
                 n_targets=None) -> Scene:
     g = geom or GEOMS[name]
     A = [operator(g, q) for q in range(g.Q)]
-    if name == "paper_scale":
+    if name in ("paper_scale", "resolved_128"):
         x = cluster_targets(g, seed, n_targets or 40, amp=(0.3, 1.0), p_vis=0.7)
         snr = 15.0
     elif name == "precision_twin":

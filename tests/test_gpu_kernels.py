@@ -133,8 +133,102 @@ def test_factor_matches_fp64_inverse(B, KM, N, nidx, mu, rho):
     Fn = F[:n, :n]
     assert np.array_equal(Fn, Fn.T)
     cond = np.linalg.cond(G)
-    assert np.max(np.abs(Fn - ref)) <= 1e-14 * cond * np.max(np.abs(ref)) * n
-    assert np.max(np.abs(Fn @ G - np.eye(n))) <= 1e-13 * cond * n
+    # the factor inverts the tensor-core Gram G + E (|E_ij| within _gram_bound)
+    tol = _inverse_tol(ref, G, Bm, form, mu)
+    assert np.max(np.abs(Fn - ref)) <= tol
+    assert np.max(np.abs(Fn @ G - np.eye(n))) <= 1e-13 * cond * n + np.linalg.norm(G, 2) * tol * n
+
+
+def _inverse_tol(ref, G, Bm_gram, form, mu):
+    """Bound of |F - G^{-1}| for a factor computed from the tensor-core Gram
+    of the columns Bm_gram (error E entrywise within _gram_bound; a downdate
+    or update carries E along) and then inverted in FP64:
+    ||G^{-1}||^2 ||E|| / (1 - ||G^{-1}|| ||E||) + 1e-14 cond(G) max|G^{-1}| n."""
+    n = G.shape[0]
+    Enorm = np.linalg.norm(_gram_bound(Bm_gram, form, mu))
+    r2 = np.linalg.norm(ref, 2)
+    assert r2 * Enorm < 0.5
+    return 1e-14 * np.linalg.cond(G) * np.max(np.abs(ref)) * n + r2 ** 2 * Enorm / (1 - r2 * Enorm)
+
+
+def _row_exponents(R):
+    """Least e with max |row| <= 2^e, per row of R (0 for a zero row)."""
+    m = np.max(np.abs(R), axis=1)
+    e = np.zeros(len(m), dtype=np.int64)
+    nz = m > 0
+    e[nz] = np.frexp(m[nz])[1]
+    return e
+
+
+def _gram_bound(Bm, form, mu):
+    """Entrywise bound of the tensor-core Gram's error against the exact Gram
+    (the arithmetic of the digit method): each Gram row is scaled by 2^-e to
+    [-1, 1] and cut into four 8-bit digits (the rest, at most 2^-32, is
+    dropped); of the digit products, the orders 6..8 (3 + 2 + 1 pairs of
+    weight 2^-32, 2^-40, 2^-48 against the leading 2^-14 scale x 2^14) are
+    dropped: at most 5 x 2^-32 per term; the double-float totals add 2^-46 of
+    the sum of magnitudes.  Returns mu 2^(e_i + e_j) (K 2^-29.6 + 2^-46 K)."""
+    R = Bm.T if form == 0 else Bm            # Gram rows (primal: pixels; Woodbury: real rows)
+    e = _row_exponents(R)
+    K = R.shape[1]
+    return mu * np.ldexp(1.0, (e[:, None] + e[None, :]).astype(np.int64)) * K * (5 * 2.0 ** -32 + 2.0 ** -46)
+
+
+GRAM_CASES = [
+    # KM, N, nidx: primal when nidx <= 2 KM (rows = pixels, k = 2KM real rows),
+    # Woodbury otherwise (rows = 2KM real rows, k = pixels)
+    (256, 300, 300),      # primal: 300 rows -> 3 row blocks (ragged), 2 chunks of k
+    (2048, 700, 129),     # primal: 16 chunks of k, one row past a block
+    (64, 300, 300),       # Woodbury: 128 rows, 300 pixels -> 2 chunks (ragged)
+    (32, 2000, 1500),     # Woodbury: 64 rows (one partial block), 6 chunks
+    (96, 1000, 999),      # Woodbury: 192 rows (ragged second block)
+]
+
+
+@pytest.mark.parametrize("KM,N,nidx", GRAM_CASES)
+def test_tensor_core_gram_is_exact_on_16_bit_entries(B, KM, N, nidx):
+    """Operator entries that are multiples of 2^-15 in (-1, 1) have only two
+    nonzero digits, so no digit product is dropped and every chunk sum is an
+    exact integer: the tensor-core Gram (method 0) must equal the FP64 Gram
+    bit for bit, padding (identity) included, for any active subset."""
+    s = scenegen.Stream(41, KM + nidx)
+    re = s.integers(N * KM, 65535).reshape(N, KM) - 32767
+    im = s.integers(N * KM, 65535).reshape(N, KM) - 32767
+    A = ((re + 1j * im) / 32768.0).astype(np.complex64)
+    idx = np.sort(s.permutation(N)[:nidx]).astype(np.int32)
+    dev = torch.device("cuda:0")
+    mu, rho = 1.0, 0.5
+    F, form, n = B.gram(torch.from_numpy(A).to(dev), torch.from_numpy(idx).to(dev), mu, rho, method=0)
+    F = F.cpu().numpy()
+    Bm = _interleaved_real_form(A, idx)
+    G = Bm @ Bm.T if form == 1 else Bm.T @ Bm
+    assert form == (1 if nidx > 2 * KM else 0) and n == G.shape[0]
+    npad = F.shape[0]
+    ref = np.eye(npad)
+    ref[:n, :n] = mu * G + rho * np.eye(n)
+    assert np.array_equal(F, ref)
+
+
+@pytest.mark.parametrize("KM,N,nidx", GRAM_CASES + [(256, 1024, 1024)])
+def test_tensor_core_gram_matches_fp64(B, KM, N, nidx):
+    """General FP32 operators (Gaussian and, in the last case, the radar
+    signal model): the tensor-core Gram is within the entrywise bound of its
+    arithmetic (_gram_bound) of the exact FP64 Gram, and so is the SIMT FP64
+    method (method 1) to 2^-40 relative."""
+    A = _operator(KM, N, seed=3 * KM + nidx, radar=(N == 1024))
+    idx = np.sort(scenegen.Stream(43, nidx).permutation(N)[:nidx]).astype(np.int32)
+    dev = torch.device("cuda:0")
+    mu, rho = 1.3, 0.7
+    At, it = torch.from_numpy(A).to(dev), torch.from_numpy(idx).to(dev)
+    F0, form, n = B.gram(At, it, mu, rho, method=0)
+    F0 = F0.cpu().numpy()[:n, :n]
+    Bm = _interleaved_real_form(A, idx)
+    G = mu * (Bm @ Bm.T if form == 1 else Bm.T @ Bm) + rho * np.eye(n)
+    assert np.all(np.abs(F0 - G) <= _gram_bound(Bm, form, mu))
+    assert np.array_equal(F0, F0.T)
+    if KM % 8 == 0:
+        F1 = B.gram(At, it, mu, rho, method=1)[0].cpu().numpy()[:n, :n]
+        assert np.max(np.abs(F1 - G)) <= 2.0 ** -40 * np.max(np.abs(G))
 
 
 @pytest.mark.parametrize("n,ld", [(1, 2), (37, 64), (101, 102), (4096, 4096)])
@@ -225,8 +319,7 @@ def test_factor_downdate_matches_fresh_inverse(B, KM, N, e):
     Bm = _interleaved_real_form(A, keep)
     G = rho * np.eye(n) + mu * Bm @ Bm.T
     ref = np.linalg.inv(G)
-    cond = np.linalg.cond(G)
-    assert np.max(np.abs(Wd - ref)) <= 1e-14 * cond * n * np.max(np.abs(ref))
+    assert np.max(np.abs(Wd - ref)) <= _inverse_tol(ref, G, _interleaved_real_form(A, J), 1, mu)
     assert np.array_equal(Wd, Wd.T)
 
 
@@ -249,8 +342,7 @@ def test_factor_rank_update_adds_columns(B, KM, N, e):
     Bm = _interleaved_real_form(A, np.arange(N))
     G = rho * np.eye(n) + mu * Bm @ Bm.T
     ref = np.linalg.inv(G)
-    cond = np.linalg.cond(G)
-    assert np.max(np.abs(Wu - ref)) <= 1e-14 * cond * n * np.max(np.abs(ref))
+    assert np.max(np.abs(Wu - ref)) <= _inverse_tol(ref, G, _interleaved_real_form(A, J), 1, mu)
     assert np.array_equal(Wu, Wu.T)
 
 
