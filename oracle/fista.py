@@ -67,3 +67,39 @@ def fista(A, y, lam, mu=1.0, iters=20000, tol=1e-15, X0=None):
         if step <= tol * max(1.0, np.linalg.norm(X)):
             break
     return X, total(X)
+
+
+def fista_consensus(A, y, lam, mu=1.0, iters=20000, tol=1e-15):
+    """FISTA (with the same restart) on the consensus objective, a LASSO in the
+    common image z with the sensors' operators stacked:
+        F(z) = sum_q mu/2 ||y_q - A_q z||^2,  G(z) = lambda ||z||_1,
+    L = mu ||[B_1; ..; B_Q]||_2^2 (B_q the real form of A_q).
+    Returns (z, F(z) + G(z))."""
+    Ac = [np.asarray(a).astype(np.complex128).T for a in A]
+    yc = [np.asarray(v).astype(np.complex128) for v in y]
+    N = Ac[0].shape[1]
+    stack = np.concatenate([np.concatenate([M.real, M.imag], axis=0) for M in Ac], axis=0)
+    t_step = 1.0 / (mu * np.linalg.norm(stack, 2) ** 2)
+
+    def total(z):
+        return sum(0.5 * mu * np.sum(np.abs(v - M @ z) ** 2) for M, v in zip(Ac, yc)) + lam * np.sum(np.abs(z))
+
+    def grad(z):
+        return sum(mu * (M.conj().T @ (M @ z - v)).real for M, v in zip(Ac, yc))
+
+    z = np.zeros(N)
+    w, t = z.copy(), 1.0
+    f_prev = total(z)
+    for _ in range(iters):
+        zn = _shrink(w - t_step * grad(w), t_step * lam)
+        f_new = total(zn)
+        if f_new > f_prev:
+            w, t = z.copy(), 1.0
+            continue
+        tn = 0.5 * (1.0 + np.sqrt(1.0 + 4.0 * t * t))
+        w = zn + ((t - 1.0) / tn) * (zn - z)
+        step = np.linalg.norm(zn - z)
+        z, t, f_prev = zn, tn, f_new
+        if step <= tol * max(1.0, np.linalg.norm(z)):
+            break
+    return z, total(z)

@@ -48,6 +48,22 @@ sharing form; Algorithm 1's window is the last Kp differences including the newe
 one and its gate uses the newest residual; ties zeta = eps_p are kept; the active
 set only shrinks; all iterates start at zero; the factor is refreshed whenever an
 active set changes.
+
+Consensus formulation (Criterion.consensus; CADMM / ACADMM, the sibling
+variant Section I attributes to the authors' earlier work and does not
+reproduce; read here as Boyd et al. 2011, Sec. 7.1, global consensus): every
+sensor images one common reflectivity z,
+    min_{x_1..x_Q, z}  sum_q mu/2 ||y_q - A_q x_q||^2 + lambda ||z||_1,  x_q = z,
+with scaled duals u_q (one per sensor and pixel).  One iteration:
+  1. x-update on J_q with v = z - u_q (the same system as the sharing form);
+  2. x_bar = mean_q x_q;
+  3. z' = soft(x_bar + u_bar, lambda / (Q rho)),  u_bar = mean_q u_q;
+  4. u_q' = u_q + x_q - z';
+  5. r_pri = ||X - z'||_F, eps_pri = sqrt(QN) eps_abs + eps_rel max(||X||_F, sqrt(Q) ||z'||),
+     d = rho sqrt(Q) ||z' - z||, eps_dual = sqrt(QN) eps_abs + eps_rel rho ||U'||_F;
+  6. Algorithm 1 per sensor on |x_q^{k+1} - x_q^k|, frozen pixels folded into y'_q.
+The image is z (Result.xG).  zbar holds z; xbar and s are kept for the shared
+code path only.  The learned step is defined for the sharing form only.
 """
 from dataclasses import dataclass, field
 import numpy as np
@@ -71,6 +87,7 @@ class Criterion:
     learn_theta: float = 0.5   # elim 2: drop pixel i when the network's p_i > learn_theta
     readmit: float = 10.0  # elim 2: re-admit when the coordinate step exceeds readmit * eps_p
     ssc_every: int = 1     # Algorithm 1's pass after iteration k only when ssc_every divides k
+    consensus: bool = False  # consensus formulation (CADMM / ACADMM, see below) instead of sharing
 
 
 def soft(v, t):
@@ -135,17 +152,19 @@ class State:
     ring: np.ndarray            # (Kp, Q, N) |x^{t+1} - x^t| for the last Kp iterations
     J: list                     # Q sorted int arrays
     yprime: list                # Q arrays (2KM,) real form of y'_q
+    u: np.ndarray = None        # (Q, N) scaled duals of the consensus formulation (zbar then holds z)
 
     def copy(self):
         return State(self.k, self.x.copy(), self.xbar.copy(), self.zbar.copy(), self.s.copy(),
-                     self.ring.copy(), [j.copy() for j in self.J], [v.copy() for v in self.yprime])
+                     self.ring.copy(), [j.copy() for j in self.J], [v.copy() for v in self.yprime],
+                     None if self.u is None else self.u.copy())
 
 
-def initial_state(A, y, Kp):
+def initial_state(A, y, Kp, consensus=False):
     Q, N = len(A), A[0].shape[0]
     return State(0, np.zeros((Q, N)), np.zeros(N), np.zeros(N), np.zeros(N),
                  np.zeros((Kp, Q, N)), [np.arange(N) for _ in range(Q)],
-                 [real_vec(v) for v in y])
+                 [real_vec(v) for v in y], np.zeros((Q, N)) if consensus else None)
 
 
 @dataclass
@@ -154,10 +173,12 @@ class Result:
     history: list = field(default_factory=list)
     stop_reason: str = "iters"
     snapshots: dict = field(default_factory=dict)   # k -> State copy (requested k only)
+    consensus: bool = False
 
     @property
     def xG(self):
-        return len(self.state.x) * self.state.zbar
+        """The image: x_G = Q z_bar (sharing), or the consensus variable z."""
+        return self.state.zbar.copy() if self.consensus else len(self.state.x) * self.state.zbar
 
 
 @dataclass
@@ -195,7 +216,10 @@ def sadmm(A, y, rho, lam, crit: Criterion, iters, tol=0.0, state: State = None, 
     mu = crit.mu
     B = B if B is not None else [real_form(a) for a in A]
     N = B[0].shape[1]
-    st = (state.copy() if state is not None else initial_state(A, y, crit.Kp))
+    cons = crit.consensus
+    if cons and crit.elim == 2:
+        raise ValueError("the learned step is defined for the sharing formulation only")
+    st = (state.copy() if state is not None else initial_state(A, y, crit.Kp, consensus=cons))
     solvers, cvec = [None] * Q, [None] * Q
 
     def refresh(q):
@@ -210,29 +234,41 @@ def sadmm(A, y, rho, lam, crit: Criterion, iters, tol=0.0, state: State = None, 
     if crit.elim == 2 and eliminator is not None:
         assert eliminator.H * eliminator.W == N and crit.eps_p > 0
         pr = _learned.round_bf16(eliminator.params)
-    res = Result(st)
+    res = Result(st, consensus=cons)
     Zold = st.x - st.xbar[None, :] + st.zbar[None, :]
     for it in range(iters):
         x_old = st.x.copy()
         # 1. x-update per sensor on its active set
         for q in range(Q):
             J = st.J[q]
-            v = st.x[q, J] - st.xbar[J] + st.zbar[J] - st.s[J]
+            if cons:
+                v = st.zbar[J] - st.u[q, J]
+            else:
+                v = st.x[q, J] - st.xbar[J] + st.zbar[J] - st.s[J]
             st.x[q, J] = solvers[q].solve(cvec[q] + rho * v)
         # 2-4. average, prox, dual
         xbar_new = st.x.mean(axis=0)
-        zbar_new = soft(xbar_new + st.s, lam / rho)
-        s_new = st.s + xbar_new - zbar_new
-        # 5. residuals
-        Z = st.x - xbar_new[None, :] + zbar_new[None, :]
-        r_pri = np.sqrt(Q) * np.linalg.norm(xbar_new - zbar_new)
-        eps_pri = np.sqrt(Q * N) * crit.eps_abs + crit.eps_rel * max(np.linalg.norm(st.x),
-                                                                    np.linalg.norm(Z))
-        d = rho * np.linalg.norm(Z - Zold)
-        eps_dual = np.sqrt(Q * N) * crit.eps_abs + crit.eps_rel * rho * np.sqrt(Q) * np.linalg.norm(s_new)
         nx = np.linalg.norm(st.x)
         relchange = np.linalg.norm(st.x - x_old) / nx if nx > 0 else np.inf
-        st.xbar, st.zbar, st.s = xbar_new, zbar_new, s_new
+        if cons:
+            z_new = soft(xbar_new + st.u.mean(axis=0), lam / (Q * rho))
+            u_new = st.u + st.x - z_new[None, :]
+            # 5. residuals of the consensus form (Boyd Sec. 7.1)
+            r_pri = np.linalg.norm(st.x - z_new[None, :])
+            eps_pri = np.sqrt(Q * N) * crit.eps_abs + crit.eps_rel * max(nx, np.sqrt(Q) * np.linalg.norm(z_new))
+            d = rho * np.sqrt(Q) * np.linalg.norm(z_new - st.zbar)
+            eps_dual = np.sqrt(Q * N) * crit.eps_abs + crit.eps_rel * rho * np.linalg.norm(u_new)
+            st.xbar, st.zbar, st.u = xbar_new, z_new, u_new
+        else:
+            zbar_new = soft(xbar_new + st.s, lam / rho)
+            s_new = st.s + xbar_new - zbar_new
+            # 5. residuals
+            Z = st.x - xbar_new[None, :] + zbar_new[None, :]
+            r_pri = np.sqrt(Q) * np.linalg.norm(xbar_new - zbar_new)
+            eps_pri = np.sqrt(Q * N) * crit.eps_abs + crit.eps_rel * max(nx, np.linalg.norm(Z))
+            d = rho * np.linalg.norm(Z - Zold)
+            eps_dual = np.sqrt(Q * N) * crit.eps_abs + crit.eps_rel * rho * np.sqrt(Q) * np.linalg.norm(s_new)
+            st.xbar, st.zbar, st.s = xbar_new, zbar_new, s_new
         # 6. SSC
         slot = st.k % crit.Kp
         st.ring[slot] = np.abs(st.x - x_old)
@@ -386,6 +422,23 @@ def sadmm_primal_inverse(A, y, rho, lam, mu=1.0, iters=1000, tol=0.0, record=Non
             res.stop_reason = "tol"
             break
     return res
+
+
+def kkt_consensus(A, y, X, U, z, rho, lam, mu=1.0, B=None):
+    """Optimality conditions of the consensus problem for (X, z, nu_q = rho u_q):
+      stationarity  mu B_q^T (B_q x_q - y_q) + nu_q = 0 for every q,
+      subgradient   sum_q nu_q in lambda d||z||_1,
+      feasibility   x_q = z for every q.
+    Residuals normalised by lambda (and by max(1, ||z||_inf) for feasibility)."""
+    B = B if B is not None else [real_form(a) for a in A]
+    nu = rho * np.asarray(U)
+    stat = max(np.max(np.abs(mu * (B[q].T @ (B[q] @ X[q] - real_vec(y[q]))) + nu[q])) for q in range(len(A)))
+    tot = nu.sum(axis=0)
+    sub = max(0.0, float(np.max(np.abs(tot))) - lam)
+    supp = np.abs(z) > 0
+    sgn = float(np.max(np.abs(tot[supp] - lam * np.sign(z[supp])))) if supp.any() else 0.0
+    feas = float(np.max(np.abs(np.asarray(X) - z[None, :]))) / max(1.0, float(np.max(np.abs(z))))
+    return dict(stationarity=stat / lam, subgradient=max(sub, sgn) / lam, feasibility=feas)
 
 
 def objective(A, y, X, lam, mu=1.0, B=None):

@@ -64,10 +64,21 @@ GEOMS = {
 }
 
 
+def operators(g: Geometry):
+    """The Q sensors' operators, built on host threads (the per-entry phase
+    arithmetic releases the interpreter lock)."""
+    if g.Q == 1 or g.N * g.KM < (1 << 22):
+        return [operator(g, q) for q in range(g.Q)]
+    import os
+    from concurrent.futures import ThreadPoolExecutor
+    with ThreadPoolExecutor(max_workers=min(g.Q, os.cpu_count() or 1)) as pool:
+        return list(pool.map(lambda q: operator(g, q), range(g.Q)))
+
+
 def build_scene(name: str, seed: int = 0, geom: Geometry = None, snr_db="default",
                 n_targets=None) -> Scene:
     g = geom or GEOMS[name]
-    A = [operator(g, q) for q in range(g.Q)]
+    A = operators(g)
     if name in ("paper_scale", "resolved_128"):
         x = cluster_targets(g, seed, n_targets or 40, amp=(0.3, 1.0), p_vis=0.7)
         snr = 15.0

@@ -1,40 +1,97 @@
-"""Writes resolved_32_limit.json: the FP64 oracle's limit x_G* of plain SADMM
-on the well-posed 32x32 workload (scene resolved_32, seed 20, rho = 100,
-lambda = 0.05 lambda_max, mu = 1), the reference of the time-to-accuracy
-measurement (relative error ||x_G^k - x_G*|| / ||x_G*|| <= 1e-3).
+"""Writes the FP64 oracle's limits x_G* of plain SADMM on the well-posed
+workloads, the references of the time-to-accuracy measurements (relative
+error ||x_G^k - x_G*|| / ||x_G*|| <= 1e-3):
 
-Calls only the oracle and the scene generator.  The stored limit is checked
+* resolved_32_limit.json: scene resolved_32 (Q=4, N=32x32), seed 20,
+  rho = 100, lambda = 0.05 lambda_max, mu = 1; 1000 iterations of
+  oracle.sadmm.
+* resolved_128_limit.npz (+ .json with the parameters and KKT residuals):
+  scene resolved_128 (Q=8, M=256, K=64, N=128x128), seed 0, lambda = 0.05
+  lambda_max, mu = 1; oracle.sadmm_primal_inverse (the same iteration through
+  explicit inverses) until the relative change of the stacked iterate is
+  below 1e-13.  The .npz holds x_G*, the per-sensor limits X* and the scaled
+  dual s* (so that the KKT conditions of Eq. 2 can be checked without
+  iterating) and the measurements y (complex64) that the benchmark reuses.
+
+Calls only the oracle and the scene generator.  The stored limits are checked
 independently of the iteration by tests/test_oracle_pins.py
-(test_golden_limit_is_optimal: the dual implied by x_G* satisfies the
-subgradient condition of Eq. 2).  Run: python tests/golden/make_limits.py"""
+(test_golden_limit_is_optimal, test_golden_limit_128_is_optimal).
+Run: python tests/golden/make_limits.py [resolved_32|resolved_128]"""
 import json
 import os
 import sys
+import time
 
 import numpy as np
 
-ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(os.path.dirname(HERE))
 sys.path.insert(0, ROOT)
 
 import oracle      # noqa: E402
 import scenegen    # noqa: E402
 
-SCENE, SEED, RHO, LAM_FRAC, ITERS = "resolved_32", 20, 100.0, 0.05, 1000
+R32 = dict(scene="resolved_32", seed=20, rho=100.0, lam_frac=0.05, iters=1000)
+R128 = dict(scene="resolved_128", seed=0, rho=1000.0, lam_frac=0.05, iters=3000, tol=1e-13)
 
 
-def main():
-    sc = scenegen.build_scene(SCENE, seed=SEED)
-    lam = LAM_FRAC * scenegen.lambda_max(sc.A, sc.y)
+def resolved_32():
+    p = R32
+    sc = scenegen.build_scene(p["scene"], seed=p["seed"])
+    lam = p["lam_frac"] * scenegen.lambda_max(sc.A, sc.y)
     B = [oracle.real_form(a) for a in sc.A]
-    r = oracle.sadmm(sc.A, sc.y, RHO, lam, oracle.Criterion(elim=0), iters=ITERS, B=B)
-    k = oracle.kkt(sc.A, sc.y, r.state.x, r.state.s, RHO, lam, xG=r.xG, B=B)
-    out = {"scene": SCENE, "seed": SEED, "rho": RHO, "lam_frac": LAM_FRAC, "lam": lam, "mu": 1.0,
-           "iterations": ITERS, "kkt": {k_: float(v) for k_, v in k.items()},
+    r = oracle.sadmm(sc.A, sc.y, p["rho"], lam, oracle.Criterion(elim=0), iters=p["iters"], B=B)
+    k = oracle.kkt(sc.A, sc.y, r.state.x, r.state.s, p["rho"], lam, xG=r.xG, B=B)
+    out = {"scene": p["scene"], "seed": p["seed"], "rho": p["rho"], "lam_frac": p["lam_frac"], "lam": lam,
+           "mu": 1.0, "iterations": p["iters"], "kkt": {k_: float(v) for k_, v in k.items()},
            "xG": [float(v) for v in r.xG]}
-    with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "resolved_32_limit.json"), "w") as f:
+    with open(os.path.join(HERE, "resolved_32_limit.json"), "w") as f:
         json.dump(out, f, indent=0)
     print(k, float(np.linalg.norm(r.xG)))
 
 
+def kkt_per_sensor(A, y, X, s, rho, lam, xG, mu=1.0):
+    """oracle.kkt's residuals, one sensor's FP64 operator at a time."""
+    nu = rho * s
+    stat = 0.0
+    for q in range(len(A)):
+        r = oracle.forward(A[q], X[q]) - np.asarray(y[q]).astype(np.complex128)
+        stat = max(stat, float(np.max(np.abs(mu * oracle.adjoint_re(A[q], r) + nu))))
+    sub = max(0.0, float(np.max(np.abs(nu))) - lam)
+    supp = np.abs(xG) > 0
+    sgn = float(np.max(np.abs(nu[supp] - lam * np.sign(xG[supp])))) if supp.any() else 0.0
+    feas = float(np.max(np.abs(xG - X.sum(axis=0)))) / max(1.0, float(np.max(np.abs(xG))))
+    return dict(stationarity=stat / lam, subgradient=max(sub, sgn) / lam, feasibility=feas)
+
+
+def resolved_128():
+    p = R128
+    t0 = time.time()
+    sc = scenegen.build_scene(p["scene"], seed=p["seed"])
+    lam = p["lam_frac"] * scenegen.lambda_max(sc.A, sc.y)
+    print(f"scene {time.time() - t0:.0f} s, lambda {lam:.6g}", flush=True)
+    log = []
+
+    def record(k, xg):
+        if k % 50 == 0:
+            log.append((k, float(np.linalg.norm(xg))))
+            print(f"k {k} |x_G| {log[-1][1]:.12g} ({time.time() - t0:.0f} s)", flush=True)
+
+    r = oracle.sadmm_primal_inverse(sc.A, sc.y, p["rho"], lam, iters=p["iters"], tol=p["tol"], record=record)
+    xg = r.xG
+    k = kkt_per_sensor(sc.A, sc.y, r.state.x, r.state.s, p["rho"], lam, xg)
+    print(k, r.state.k, float(np.linalg.norm(xg)), int(np.count_nonzero(xg)), flush=True)
+    np.savez_compressed(os.path.join(HERE, "resolved_128_limit.npz"), xG=xg, X=r.state.x, s=r.state.s,
+                        y=np.stack(sc.y).astype(np.complex64))
+    meta = {"scene": p["scene"], "seed": p["seed"], "rho": p["rho"], "lam_frac": p["lam_frac"], "lam": lam,
+            "mu": 1.0, "iterations": r.state.k, "final_relchange": r.history[-1]["relchange"],
+            "kkt": {k_: float(v) for k_, v in k.items()}, "support": int(np.count_nonzero(xg)),
+            "norm_xG": float(np.linalg.norm(xg))}
+    with open(os.path.join(HERE, "resolved_128_limit.json"), "w") as f:
+        json.dump(meta, f, indent=1)
+
+
 if __name__ == "__main__":
-    main()
+    which = sys.argv[1:] or ["resolved_32"]
+    for w in which:
+        {"resolved_32": resolved_32, "resolved_128": resolved_128}[w]()

@@ -534,3 +534,178 @@ def test_signal_model_pins_hold_for_the_oracle():
 def test_signal_model_pins_catch_planted_mistakes(name):
     with np.errstate(all="ignore"):
         assert not _sm_pins_hold(_sm_module(name)), name
+
+
+@pytest.mark.parametrize("kind", [1, 2])
+def test_pair_operator_is_two_nearest_roundings(kind):
+    """oracle.precision: hi = RN(a) and lo = RN(a - hi) per real component,
+    checked against torch's round-to-nearest-even conversions (independent
+    code), the bounds |a - hi| <= u |a| and |a - P| <= u^2 |a| (BF16 u = 2^-8,
+    FP16 u = 2^-11, plus FP16's subnormal half-spacing 2^-25), and exactness
+    of P = hi + lo in complex64."""
+    torch = pytest.importorskip("torch")
+    g = scenegen.Geometry(Q=1, M=4, K=32, nx=8, cell=0.05, radius=10.0, fc=77e9, bw=1e9)
+    A = radar.operator(g, 0)
+    A[0, :4] = [1.0 + 0j, 2.0 ** -20 + 0.5j, -3.0e-9 + 0j, 1.0 + 2.0 ** -9 * 1j]   # edge values
+    h, l = oracle.precision.split_planes(A, kind)
+    dt = torch.bfloat16 if kind == 1 else torch.float16
+    for part, hp, lp in ((A.real, h.real, l.real), (A.imag, h.imag, l.imag)):
+        t = torch.from_numpy(np.ascontiguousarray(part, dtype=np.float32))
+        th = t.to(dt)
+        assert np.array_equal(hp, th.to(torch.float64).numpy())
+        tl = (t - th.to(torch.float32)).to(dt)
+        assert np.array_equal(lp, tl.to(torch.float64).numpy())
+    u = 2.0 ** -8 if kind == 1 else 2.0 ** -11
+    sub = 0.0 if kind == 1 else 2.0 ** -25
+    P = oracle.precision.pair_operator(A, kind).astype(np.complex128)
+    a = A.astype(np.complex128)
+    for f in (np.real, np.imag):
+        assert np.all(np.abs(f(a) - f(h)) <= u * np.abs(f(a)) + sub)
+        assert np.all(np.abs(f(a) - f(P)) <= u * u * np.abs(f(a)) + sub)
+    assert np.array_equal(P, h + l)
+
+
+def _kkt_stationarity_chunked(Aq, yq, xq, nu, mu, chunk=2048):
+    """max_i |mu Re(a_i^H (A_q x_q - y_q)) + nu_i| with the FP64 products of
+    oracle.forward / oracle.adjoint_re taken over pixel chunks (the operator is
+    never held in complex128 as a whole)."""
+    N = Aq.shape[0]
+    r = -np.asarray(yq).astype(np.complex128)
+    for n0 in range(0, N, chunk):
+        r += oracle.forward(Aq[n0:n0 + chunk], xq[n0:n0 + chunk])
+    g = np.concatenate([oracle.adjoint_re(Aq[n0:n0 + chunk], r) for n0 in range(0, N, chunk)])
+    return float(np.max(np.abs(mu * g + nu)))
+
+
+def test_golden_limit_128_is_optimal():
+    """The stored limit of the well-posed paper-size workload
+    (tests/golden/resolved_128_limit.npz, written by tests/golden/make_limits.py
+    from the oracle) certified by the KKT conditions of Eq. 2 alone: for the
+    stored per-sensor images X* and dual nu = rho s*, stationarity
+    mu Re(A_q^H (A_q x_q - y_q)) + nu = 0 for every sensor, nu a subgradient of
+    lambda ||.||_1 at x_G* (|nu| <= lambda, nu = lambda sign(x_G*) on its
+    support) and x_G* = sum_q x_q.  The scene and lambda are regenerated from
+    the scene generator and must match the stored measurements."""
+    import json
+    import os
+    from concurrent.futures import ThreadPoolExecutor
+    here = os.path.join(os.path.dirname(__file__), "golden")
+    with open(os.path.join(here, "resolved_128_limit.json")) as f:
+        meta = json.load(f)
+    d = np.load(os.path.join(here, "resolved_128_limit.npz"))
+    sc = scenegen.build_scene(meta["scene"], seed=meta["seed"])
+    assert np.array_equal(np.stack(sc.y).astype(np.complex64), d["y"])
+    lam, mu, rho = meta["lam"], meta["mu"], meta["rho"]
+    assert lam == pytest.approx(meta["lam_frac"] * scenegen.lambda_max(sc.A, sc.y), rel=1e-12)
+    X, s, xg = d["X"], d["s"], d["xG"]
+    nu = rho * s
+    with ThreadPoolExecutor(max_workers=4) as pool:
+        stat = list(pool.map(lambda q: _kkt_stationarity_chunked(sc.A[q], sc.y[q], X[q], nu, mu),
+                             range(sc.geom.Q)))
+    supp = xg != 0
+    assert 0 < supp.sum() < len(xg)
+    assert max(stat) <= 1e-6 * lam
+    assert np.max(np.abs(nu)) <= lam * (1 + 1e-6)
+    assert np.max(np.abs(nu[supp] - lam * np.sign(xg[supp]))) <= 1e-6 * lam
+    assert np.max(np.abs(xg - X.sum(axis=0))) <= 1e-6 * max(1.0, np.max(np.abs(xg)))
+
+
+# ------------------------------------------------- consensus form (ACADMM)
+@pytest.mark.parametrize("seed,rho", [(31, 2.0), (32, 0.5)])
+def test_consensus_limit_satisfies_kkt_and_matches_fista(seed, rho):
+    """Consensus ADMM (Criterion.consensus, Boyd Sec. 7.1 read for the CADMM
+    form of Section I), elimination off: at the limit the KKT conditions of
+    min sum_q mu/2 ||y_q - A_q z||^2 + lambda ||z||_1 hold to 1e-8 and z
+    agrees with an independent FISTA on the stacked LASSO (objective to 1e-10,
+    iterate to 1e-6)."""
+    sc = scenegen.random_problem(3, 24, 20, seed=seed)
+    lam = 0.2 * scenegen.lambda_max(sc.A, sc.y)
+    r = oracle.sadmm(sc.A, sc.y, rho, lam, oracle.Criterion(elim=0, consensus=True), iters=20000, tol=1e-15)
+    k = oracle.kkt_consensus(sc.A, sc.y, r.state.x, r.state.u, r.xG, rho, lam)
+    assert max(k.values()) <= 1e-8, k
+    z, fz = oracle.fista_consensus(sc.A, sc.y, lam, iters=30000, tol=1e-14)
+    Bs = [oracle.real_form(a) for a in sc.A]
+    fa = sum(0.5 * np.sum((oracle.real_vec(v) - Bq @ r.xG) ** 2) for Bq, v in zip(Bs, sc.y)) + lam * np.sum(
+        np.abs(r.xG))
+    assert abs(fa - fz) <= 1e-10 * abs(fz)
+    assert np.linalg.norm(r.xG - z) <= 1e-6 * np.linalg.norm(z)
+    assert np.count_nonzero(r.xG) < len(r.xG)
+
+
+def test_consensus_limit_matches_a_library_lasso():
+    """The consensus problem is a LASSO in z with the real forms stacked:
+    scikit-learn's coordinate-descent Lasso (its objective
+    1/(2n) ||b - B z||^2 + alpha ||z||_1 with alpha = lambda / (mu n)) gives
+    the same minimiser."""
+    lm = pytest.importorskip("sklearn.linear_model")
+    sc = scenegen.random_problem(2, 24, 16, seed=33)
+    lam = 0.2 * scenegen.lambda_max(sc.A, sc.y)
+    r = oracle.sadmm(sc.A, sc.y, 1.0, lam, oracle.Criterion(elim=0, consensus=True), iters=20000, tol=1e-15)
+    Bst = np.concatenate([oracle.real_form(a) for a in sc.A], axis=0)
+    b = np.concatenate([oracle.real_vec(v) for v in sc.y])
+    n = Bst.shape[0]
+    las = lm.Lasso(alpha=lam / n, fit_intercept=False, tol=1e-14, max_iter=1000000).fit(Bst, b)
+    assert np.linalg.norm(r.xG - las.coef_) <= 1e-6 * np.linalg.norm(las.coef_)
+
+
+def test_consensus_elimination_invariants():
+    """ACADMM (consensus with Algorithm 1): eps_p = 0 reproduces plain CADMM
+    bit for bit; with the paper's eps_p the active sets only shrink, frozen
+    entries keep their value, and the result stays near the plain limit."""
+    sc = scenegen.build_scene("resolved_tiny", seed=1)
+    lam = 0.05 * scenegen.lambda_max(sc.A, sc.y)
+    plain = oracle.sadmm(sc.A, sc.y, 2.0, lam, oracle.Criterion(elim=0, consensus=True), iters=300)
+    zero = oracle.sadmm(sc.A, sc.y, 2.0, lam, oracle.Criterion(elim=1, eps_p=0.0, consensus=True), iters=300)
+    assert np.array_equal(plain.state.x, zero.state.x) and np.array_equal(plain.xG, zero.xG)
+    r = oracle.sadmm(sc.A, sc.y, 2.0, lam, oracle.Criterion(elim=1, consensus=True), iters=600,
+                     snapshots=set(range(1, 601)))
+    prev = [set(range(sc.geom.N))] * sc.geom.Q
+    for k in range(1, 601):
+        st = r.snapshots[k]
+        for q in range(sc.geom.Q):
+            cur = set(st.J[q].tolist())
+            assert cur <= prev[q]
+            frozen = np.setdiff1d(np.arange(sc.geom.N), st.J[q])
+            if k > 1 and len(frozen):
+                before = r.snapshots[k - 1]
+                was = np.setdiff1d(np.arange(sc.geom.N), before.J[q])
+                assert np.array_equal(st.x[q, was], before.x[q, was])
+        prev = [set(j.tolist()) for j in st.J]
+    assert sum(len(j) for j in r.state.J) < sc.geom.Q * sc.geom.N
+    lim = oracle.sadmm(sc.A, sc.y, 2.0, lam, oracle.Criterion(elim=0, consensus=True), iters=4000)
+    assert np.linalg.norm(r.xG - lim.xG) <= 1e-2 * np.linalg.norm(lim.xG)
+
+
+CONSENSUS_MUTANTS = {
+    "threshold_without_Q": ("soft(xbar_new + st.u.mean(axis=0), lam / (Q * rho))",
+                            "soft(xbar_new + st.u.mean(axis=0), lam / rho)"),
+    "dual_sign": ("u_new = st.u + st.x - z_new[None, :]", "u_new = st.u - st.x + z_new[None, :]"),
+    "v_without_dual": ("v = st.zbar[J] - st.u[q, J]", "v = st.zbar[J]"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(CONSENSUS_MUTANTS))
+def test_consensus_pins_catch_planted_mistakes(name):
+    old, new = CONSENSUS_MUTANTS[name]
+    src = inspect.getsource(osadmm)
+    assert src.count(old) == 1, name
+    mod = types.ModuleType("oracle_cmutant_" + name)
+    mod.__package__ = "oracle"
+    sys.modules[mod.__name__] = mod
+    try:
+        exec(compile(src.replace(old, new), osadmm.__file__, "exec"), mod.__dict__)
+    finally:
+        sys.modules.pop(mod.__name__, None)
+    sc = scenegen.random_problem(3, 24, 20, seed=31)
+    lam = 0.2 * scenegen.lambda_max(sc.A, sc.y)
+    with np.errstate(all="ignore"):
+        try:
+            r = mod.sadmm(sc.A, sc.y, 2.0, lam, mod.Criterion(elim=0, consensus=True), iters=5000, tol=1e-15)
+        except Exception:
+            return
+        if not np.all(np.isfinite(r.state.x)):
+            return
+        k = oracle.kkt_consensus(sc.A, sc.y, r.state.x, r.state.u, r.xG, 2.0, lam)
+        z, _ = oracle.fista_consensus(sc.A, sc.y, lam, iters=30000, tol=1e-14)
+    caught = max(k.values()) > 1e-6 or np.linalg.norm(r.xG - z) > 1e-4 * np.linalg.norm(z)
+    assert caught, name
