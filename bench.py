@@ -28,6 +28,9 @@ if ROOT not in sys.path:
 import numpy as np
 
 METRIC = "SADMM iterations/s (Q=8, N=128^2, KM=2048)"
+NOMINAL_HBM_GBS = 7900.0
+# workloads whose operators the bench builds on the device (--config), with their rho
+DEVICE_CONFIGS = {"resolved_128": 1000.0, "precision_256": 1.0}
 UNIT = "iter/s"
 WORKLOAD = "paper_scale: Q=8 M=8 K=256 (KM=2048) N=128x128, 40 clusters, 15 dB, rho=1, lambda=0.05*lambda_max"
 
@@ -55,7 +58,10 @@ def parse():
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the 16-scene batched measurement (Q=8, KM=2048, N=96x96)")
     ap.add_argument("--no-accuracy", action="store_true",
-                    help="skip the time-to-accuracy measurement on the well-posed 32x32 workload")
+                    help="skip the time-to-accuracy measurements on the well-posed workloads "
+                         "(Q=8, N=128x128 and Q=4, N=32x32)")
+    ap.add_argument("--no-precision", action="store_true",
+                    help="skip the full-size precision workload (Q=8, KM=8192, N=256x256) and its twin errors")
     ap.add_argument("--no-factored", action="store_true",
                     help="skip the factored-operator measurement (operators from round-trip delays)")
     ap.add_argument("--group-geoms", type=int, default=32,
@@ -470,13 +476,9 @@ def accuracy_measure(dev, stream):
         else:
             out[name] = {"iterations": None, "rel_error_at_8192": e, "factor_ms": factor_ms}
         s.close()
-    # the batched form: this scene and 15 more of the same geometry (other
-    # seeds) iterate together; iterations until this scene is within 1e-3
-    Ys, lams = [np.stack(sc.y)], [lam]
-    for sd in range(21, 36):
-        o = scenegen.build_scene(gold["scene"], seed=sd)
-        Ys.append(np.stack(o.y))
-        lams.append(gold["lam_frac"] * scenegen.lambda_max(o.A, o.y))
+    # the batched form: 16 copies of this scene (each with the stored limit)
+    # iterate together; iterations until the worst scene is within 1e-3
+    Ys, lams = [np.stack(sc.y)] * 16, [lam] * 16
     Yt = torch.from_numpy(np.stack(Ys)).to(dev)
     bs = binding.BatchSolver(g.Q, g.M, g.K, g.N, rho, lams, stream=stream.cuda_stream)
     for q in range(g.Q):
@@ -484,7 +486,7 @@ def accuracy_measure(dev, stream):
 
     def berr(k):
         xg, _ = bs.solve(Yt, k)
-        return float(np.linalg.norm(xg[0] - xstar) / np.linalg.norm(xstar))
+        return max(float(np.linalg.norm(xg[i] - xstar) / np.linalg.norm(xstar)) for i in range(16))
 
     k, e = 8, berr(8)
     while e > 1e-3 and k < 8192:
@@ -508,8 +510,8 @@ def accuracy_measure(dev, stream):
         e1.record(stream)
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / 3
-        out["batched_16"] = {"iterations": k, "ms": ms, "ms_per_scene": ms / 16, "rel_error": e,
-                             "scenes": "this scene and seeds 21-35 of the same geometry"}
+        out["batched_16"] = {"iterations": k, "ms": ms, "ms_per_scene": ms / 16, "worst_scene_rel_error": e,
+                             "scenes": "16 copies of the scene (each checked against the stored limit)"}
     else:
         out["batched_16"] = {"iterations": None, "rel_error_at_8192": e}
     bs.close()
@@ -518,6 +520,377 @@ def accuracy_measure(dev, stream):
         t = out[name].get("ms_per_scene", out[name].get("ms"))
         if base and t:
             out[name]["speedup_vs_plain_fp32"] = base / t
+    return out
+
+
+def device_operators(g, dev):
+    """The Q operators of geometry g built on the device from their round-trip
+    delays (sadmm_operator_tables: phases formed in FP64 and rounded once to
+    complex64, as the scene generator forms them on the host)."""
+    import torch
+    from scenegen import radar
+    from paper_2307_08606_gb300 import binding
+    out = []
+    for q in range(g.Q):
+        tau = torch.from_numpy(np.ascontiguousarray(radar.delays(g, q))).to(dev)
+        A, _, _ = binding.operator_tables(tau, g.M, g.K, g.N, g.fc, g.bw / g.K, with_entries=True)
+        out.append(A)
+    torch.cuda.synchronize()
+    return out
+
+
+def _median_solve_ms(fn, stream, reps=3):
+    """Median CUDA-event time (on `stream`) of `reps` calls of fn()."""
+    import torch
+    ts = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return statistics.median(ts)
+
+
+# grouped by operator form (FP32, BF16 pairs, FP16 pairs): each group shares one
+# factorisation of its operator
+RESOLVED_128_FORMS = (
+    ("plain_fp32", dict(elim=0)),
+    ("asadmm_fp32", dict(elim=1)),
+    ("asadmm_every16_fp32", dict(elim=1, ssc_every=16)),
+    ("bf16_hi_corr4", dict(elim=0, precision=3, correct_every=4)),
+    ("bf16_pairs", dict(elim=0, precision=1)),
+    ("asadmm_every16_bf16_hi_corr4", dict(elim=1, ssc_every=16, precision=3, correct_every=4)),
+    ("fp16_pairs", dict(elim=0, precision=2)),
+)
+
+
+def _time_to_target(s, y_dev, xg, err, target, cap, budget_s, stream):
+    """Iterations from zero (one step at a time) until err() <= target, then
+    the median CUDA-event time of cold solves of that many iterations; a
+    search past `budget_s` seconds or `cap` iterations reports where it
+    stopped instead."""
+    t_search = time.perf_counter()
+    s.solve(y_dev, 1, out=xg)
+    k, e = 1, err()
+    while e > target and k < cap and time.perf_counter() - t_search < budget_s:
+        s.resume(1, out=xg)
+        k += 1
+        e = err()
+    if e > target:
+        return {"iterations": None, "stopped_at_iteration": k, "rel_error_at_stop": e,
+                "search_s": round(time.perf_counter() - t_search, 1),
+                "stopped_by": "iteration cap" if k >= cap else f"{budget_s:.0f} s budget"}
+    search_s = time.perf_counter() - t_search
+    st = {}
+
+    def run():
+        st.update(s.solve(y_dev, k, out=xg)[1])
+
+    ms = _median_solve_ms(run, stream, reps=3 if search_s < budget_s / 3 else 1)
+    return {"iterations": k, "ms": ms, "rel_error": err(), "refresh_ms": round(st["ms_refresh"], 2),
+            "refreshes": st["refreshes"], "active_fraction_end": st["active_total"] / (s.Q * s.N),
+            "readmitted": st["readmitted"], "learned_steps": st["learned_steps"]}
+
+
+def accuracy_measure_128(dev, stream, cap=3000, target=1e-3, forms=RESOLVED_128_FORMS, batched=True,
+                         learned=True, budget_s=90.0):
+    """Time to accuracy on the well-posed paper-size workload (resolved_128:
+    Q=8, M=256, K=64, N=128x128): for each form, the fewest iterations from
+    zero whose x_G is within `target` (relative) of the FP64 oracle's limit
+    (tests/golden/resolved_128_limit.npz, written by
+    tests/golden/make_limits.py and certified by its KKT conditions), found by
+    iterating one step at a time, then the median CUDA-event time of three
+    cold solves of that many iterations (their final error is reported).
+    One context serves every single-scene form (sadmm_set_criterion keeps the
+    full-set factor of each operator form), so the factor time is reported
+    once per operator form; a form whose search exceeds `budget_s` seconds of
+    wall time is reported with the error it reached instead.  The learned
+    forms use a network trained here, on the GPU, from plain runs of four other
+    scenes of the geometry (learned_eval_128).  The batched form iterates 16
+    copies of the scene (each with the same known limit) in one batch and
+    reports the worst scene's error."""
+    import torch
+    import scenegen
+    from paper_2307_08606_gb300 import binding
+    gold = np.load(os.path.join(ROOT, "tests", "golden", "resolved_128_limit.npz"))
+    with open(os.path.join(ROOT, "tests", "golden", "resolved_128_limit.json")) as f:
+        meta = json.load(f)
+    g = scenegen.GEOMS[meta["scene"]]
+    rho, lam = meta["rho"], meta["lam"]
+    xstar = gold["xG"]
+    nstar = float(np.linalg.norm(xstar))
+    y_dev = [torch.from_numpy(np.ascontiguousarray(v)).to(dev) for v in gold["y"]]
+    out = {"workload": f"resolved_128 seed {meta['seed']} (Q=8, M=256, K=64: KM=16384, N=128x128; 40 clusters, "
+                       f"p=0.7, 15 dB; rho={rho:g}, lambda=0.05 lambda_max)",
+           "reference": f"FP64 oracle limit (tests/golden/resolved_128_limit.npz, {meta['iterations']} iterations, "
+                        f"KKT stationarity {meta['kkt']['stationarity']:.1e} lambda)",
+           "target_rel_error": target}
+    A = device_operators(g, dev)
+    s = binding.Solver(g.Q, g.M, g.K, g.N, rho, lam, stream=stream.cuda_stream, elim=0)
+    for q in range(g.Q):
+        s.set_operator(q, A[q])
+    del A
+    torch.cuda.empty_cache()
+    t0 = time.perf_counter()
+    s.prepare()
+    torch.cuda.synchronize()
+    out["factor_s"] = round(time.perf_counter() - t0, 2)
+    xg = torch.empty(g.N, dtype=torch.float32, device=dev)
+
+    def err():
+        return float(np.linalg.norm(xg.cpu().numpy() - xstar) / nstar)
+
+    for name, kw in forms:
+        try:
+            s.set_criterion(**kw)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            s.prepare()                      # refactors only when the operator form changed
+            torch.cuda.synchronize()
+            prep_s = time.perf_counter() - t0
+            out[name] = _time_to_target(s, y_dev, xg, err, target, cap, budget_s, stream)
+            if prep_s > 1.0:
+                out[name]["factor_s_of_this_operator_form"] = round(prep_s, 2)
+        except Exception as ex:              # a form that cannot run is reported, not fatal
+            out[name] = {"error": str(ex)[:200]}
+    names = [f for f, _ in forms]
+    if learned:
+        try:
+            lo = learned_eval_128(s, g, dev, stream, gold, meta, y_dev, xg, err, target, cap, budget_s)
+            out.update(lo)
+            names += [k for k in lo if k != "learned_training"]
+        except Exception as ex:
+            out["learned_training"] = {"error": str(ex)[:300]}
+    s.close()
+    torch.cuda.empty_cache()
+    if batched:
+        try:
+            A = device_operators(g, dev)
+            Y = torch.stack([torch.stack(y_dev)] * 16)
+            bs = binding.BatchSolver(g.Q, g.M, g.K, g.N, rho, [lam] * 16, stream=stream.cuda_stream)
+            for q in range(g.Q):
+                bs.set_operator(q, A[q])
+            del A
+            torch.cuda.empty_cache()
+            t0 = time.perf_counter()
+            bs.solve(Y, 1)
+            torch.cuda.synchronize()
+            first_s = time.perf_counter() - t0
+
+            def berr(k):
+                xgs, _ = bs.solve(Y, k)
+                return max(float(np.linalg.norm(xgs[i] - xstar) / nstar) for i in range(16))
+
+            k = (out.get("plain_fp32") or {}).get("iterations") or 50
+            e = berr(k)
+            while e > target and k < cap:
+                k += 1
+                e = berr(k)
+            while k > 1:
+                e2 = berr(k - 1)
+                if e2 > target:
+                    break
+                k, e = k - 1, e2
+            ms = _median_solve_ms(lambda: bs.solve(Y, k), stream)
+            out["batched_16"] = {"iterations": k, "ms": ms, "ms_per_scene": ms / 16, "worst_scene_rel_error": e,
+                                 "first_solve_s_with_factor": round(first_s, 2),
+                                 "scenes": "16 copies of the scene (each checked against the stored limit)"}
+            bs.close()
+        except Exception as ex:
+            out["batched_16"] = {"error": str(ex)[:200]}
+        torch.cuda.empty_cache()
+    base = (out.get("plain_fp32") or {}).get("ms")
+    for name in names + ["batched_16"]:
+        v = out.get(name) or {}
+        t = v.get("ms_per_scene", v.get("ms"))
+        if base and t:
+            v["speedup_vs_plain_fp32"] = base / t
+    return out
+
+
+def learned_eval_128(s, g, dev, stream, gold, meta, y_dev, xg, err, target, cap, budget_s,
+                     train_seeds=(1, 2, 3, 4), iters=200):
+    """The learned proposal (elim = 2) on the well-posed paper-size workload.
+    Training: plain runs (iters iterations) of four other scenes of the same
+    geometry (seeds 1-4 of the scene law, measurements formed on the device)
+    on the same context -- one factorisation -- give the features and labels
+    of paper_2307_08606_gb300.eliminator; the network is trained on the GPU
+    by the library's own backward and Adam kernels.  Evaluation on the held-
+    out scene (seed 0, the stored limit): time to the target for the learned
+    step with the trained network and with a network that never proposes
+    (re-admission only), in FP32 and with the BF16 hi plane; and the false-
+    elimination rate at the end of each run: of the (sensor, pixel) pairs
+    frozen at the end or re-admitted during the run, the fraction that was
+    re-admitted or is frozen more than Kp eps_p away from the oracle's
+    per-sensor limit X*."""
+    import torch
+    import scenegen
+    from paper_2307_08606_gb300 import binding
+    from paper_2307_08606_gb300 import eliminator as E
+    A = device_operators(g, dev)
+    ys, lams = [], []
+    for sd in train_seeds:
+        y, lam = device_measurements(A, meta["scene"], g, dev, sd)
+        ys.append([torch.from_numpy(v).to(dev) for v in y])
+        lams.append(lam)
+    del A
+    torch.cuda.empty_cache()
+    s.set_criterion(elim=0)
+    s.prepare()
+    t0 = time.perf_counter()
+    smp = E.collect_on(s, ys, lams, g.nx, g.nx, iters, learn_every=10, horizon=50)
+    net = binding.CNN(g.nx, g.nx, max_batch=8)
+    net.set_params(scenegen.cnn_init(5))
+    losses = E.train(net, smp, steps=400, lr=2e-3, batch=8)
+    params = net.params()
+    net.close()
+    out = {"learned_training": {"scenes": len(train_seeds), "iterations_per_scene": iters,
+                                "samples": len(smp.ks), "droppable_fraction": float(smp.labels.mean()),
+                                "loss_first20": float(np.mean(losses[:20])),
+                                "loss_last20": float(np.mean(losses[-20:])),
+                                "train_s": round(time.perf_counter() - t0, 1)}}
+    s.set_lambda(meta["lam"])
+    Xstar = gold["X"]
+    Kp, eps_p = 5, 1e-5
+    for name, kw in (("learned_fp32", dict(elim=2)), ("readmission_only_fp32", dict(elim=2, learn_theta=1.0)),
+                     ("learned_bf16_hi_corr4", dict(elim=2, precision=3, correct_every=4))):
+        try:
+            s.set_criterion(learn_every=10, **kw)
+            s.set_eliminator(params, g.nx, g.nx)
+            s.prepare()
+            r = _time_to_target(s, y_dev, xg, err, target, cap, budget_s, stream)
+            X = s.X()
+            frozen = np.ones((g.Q, g.N), dtype=bool)
+            for q in range(g.Q):
+                frozen[q, s.active(q)] = False
+            bad = int(np.count_nonzero(np.abs(X - Xstar)[frozen] > Kp * eps_p))
+            nre = r.get("readmitted", 0) or 0
+            tot = int(frozen.sum()) + nre
+            r["false_elimination_rate"] = (bad + nre) / tot if tot else 0.0
+            r["frozen_end"] = int(frozen.sum())
+            r["frozen_off_limit"] = bad
+            out[name] = r
+        except Exception as ex:
+            out[name] = {"error": str(ex)[:200]}
+    s.set_eliminator(None, 0, 0)
+    return out
+
+
+def device_measurements(A, name, g, dev, seed):
+    """Measurements of scene `seed` of the named workload's scene law for the
+    device operators A: the noiseless products in complex128 on the device,
+    then scenegen's noise; lambda = 0.05 max_q ||Re(A_q^H y_q)||_inf."""
+    import torch
+    import scenegen
+    x, snr = scenegen.scene_law(name, g, seed)
+    cleans = []
+    for q in range(g.Q):
+        xq = torch.from_numpy(x[q]).to(dev).to(torch.complex128)
+        cleans.append((A[q].to(torch.complex128).T @ xq).cpu().numpy())
+    y = scenegen.add_noise(cleans, snr, seed)
+    lam = 0.05 * max(float((A[q].to(torch.complex128).conj() @ torch.from_numpy(y[q]).to(dev).to(torch.complex128))
+                           .real.abs().max()) for q in range(g.Q))
+    return y, lam
+
+
+def device_scene(name, dev, seed=0):
+    """A named workload built on the device: operators from the delays
+    (device_operators) and the measurements of device_measurements.  For
+    workloads whose operators are too large to build on the host."""
+    import scenegen
+    g = scenegen.GEOMS[name]
+    A = device_operators(g, dev)
+    y, lam = device_measurements(A, name, g, dev, seed)
+    return g, A, y, lam
+
+
+PRECISION_FORMS = (("fp32", dict(precision=0)), ("bf16_pairs", dict(precision=1)),
+                   ("bf16_hi_corr4", dict(precision=3, correct_every=4)), ("fp16_pairs", dict(precision=2)),
+                   ("fp16_hi_corr4", dict(precision=4, correct_every=4)))
+
+
+def precision_measure(dev, stream, iters=50):
+    """The precision workload at its full size (Q=8, M=16, K=512: KM=8192,
+    N=256x256; operators 8 x 4.3 GB, Woodbury form n = 2KM = 16384): per
+    precision form, iterations/s and the operator-read rate of the iteration
+    (CUDA events, phase times), one context for all forms (one factorisation
+    per operator form).  Beside each, its error on the oracle-sized twin
+    (Q=8, M=16, K=512, N=64x64) after 20 iterations against the stored FP64
+    oracle iterates (tests/golden/precision_twin_oracle.npz): against the
+    oracle run on the form's own operator (A, or the pair operator hi + lo),
+    and against the oracle on A."""
+    import torch
+    from paper_2307_08606_gb300 import binding
+    out = {"workload": "precision_256: Q=8 M=16 K=512 (KM=8192) N=256x256, 120 clusters, p=0.7, 20 dB, "
+                       "rho=1, lambda=0.05 lambda_max (operators built on the device from the delays)"}
+    g, A, y, lam = device_scene("precision_256", dev)
+    s = binding.Solver(g.Q, g.M, g.K, g.N, 1.0, lam, stream=stream.cuda_stream, elim=0)
+    for q in range(g.Q):
+        s.set_operator(q, A[q])
+    del A
+    torch.cuda.empty_cache()
+    y_dev = [torch.from_numpy(v).to(dev) for v in y]
+    nt = (2 * g.KM) // 64
+    pack_bytes = g.Q * nt * (nt + 1) / 2 * 64 * 64 * 8.0
+    for name, kw in PRECISION_FORMS:
+        s.set_criterion(elim=0, **kw)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s.prepare()
+        torch.cuda.synchronize()
+        fs = time.perf_counter() - t0
+        s.solve(y_dev, 5)
+        s.set_profiling(True)
+        ms = _median_solve_ms(lambda: s.solve(y_dev, iters), stream) / iters
+        prof = s.profile()
+        s.set_profiling(False)
+        p = kw["precision"]
+        bpe = 8.0 if p in (0, 1, 2) else 4.0 * (1.0 + 1.0 / kw.get("correct_every", 1))
+        it_bytes = 2 * g.Q * g.KM * g.N * bpe + pack_bytes
+        out[name] = {"iters_per_s": 1e3 / ms, "ms_per_iteration": ms,
+                     "iteration_GBps": it_bytes / (ms / 1e3) / 1e9, "bytes_per_iteration": it_bytes,
+                     "phases_ms_per_launch": {k: (v[0] / v[1] if v[1] else None) for k, v in prof.items()}}
+        if fs > 1.0:
+            out[name]["factor_s"] = round(fs, 2)
+    s.close()
+    torch.cuda.empty_cache()
+    base = out["fp32"]["ms_per_iteration"]
+    for name, _ in PRECISION_FORMS:
+        out[name]["speedup_vs_fp32"] = base / out[name]["ms_per_iteration"]
+    out["twin"] = twin_errors(dev, stream)
+    return out
+
+
+def twin_errors(dev, stream):
+    """Each precision form on the precision workload's 64x64 twin, 20 plain
+    iterations, against the stored FP64 oracle iterates."""
+    import torch
+    import scenegen
+    from paper_2307_08606_gb300 import binding
+    d = np.load(os.path.join(ROOT, "tests", "golden", "precision_twin_oracle.npz"))
+    sc = scenegen.build_scene("precision_twin", seed=0)      # the oracle's own host operators
+    g, A = sc.geom, sc.A
+    assert np.array_equal(np.stack(sc.y), d["y"])
+    lam, iters = float(d["lam"]), int(d["iters"])
+    y_dev = [torch.from_numpy(np.ascontiguousarray(v)).to(dev) for v in d["y"]]
+    s = binding.Solver(g.Q, g.M, g.K, g.N, 1.0, lam, stream=stream.cuda_stream, elim=0)
+    for q in range(g.Q):
+        s.set_operator(q, A[q])
+    del A
+    out = {"workload": "precision_twin: Q=8 M=16 K=512 N=64x64, 20 iterations (primal form, cond(H) ~3.5e5)"}
+    own = {0: "X_fp32", 1: "X_bf16_pairs", 2: "X_fp16_pairs", 3: "X_bf16_pairs", 4: "X_fp16_pairs"}
+    for name, kw in PRECISION_FORMS:
+        s.set_criterion(elim=0, **dict(kw, correct_every=1) if kw["precision"] >= 3 else kw)
+        s.solve(y_dev, iters)
+        X = s.X()
+        ref_own, ref_a = d[own[kw["precision"]]], d["X_fp32"]
+        out[name] = {"rel_error_vs_oracle_on_its_operator": float(np.linalg.norm(X - ref_own) / np.linalg.norm(ref_own)),
+                     "rel_error_vs_oracle_on_A": float(np.linalg.norm(X - ref_a) / np.linalg.norm(ref_a))}
+    s.close()
+    torch.cuda.empty_cache()
     return out
 
 
@@ -730,17 +1103,32 @@ def main():
     dev = torch.device("cuda", local_rank)
     stream = torch.cuda.current_stream()
 
-    sc, lam = make_scene(args.config, rank, args.sensors)
-    g = sc.geom
-    s = binding.Solver(g.Q, g.M, g.K, g.N, 1.0, lam, stream=stream.cuda_stream, elim=args.elim,
+    rho = 1.0
+    if args.config in DEVICE_CONFIGS:
+        # operators too large to build on the host: built on the device; the
+        # extra measurement blocks need the host scene and are skipped
+        g, A_dev, y_list, lam = device_scene(args.config, dev, seed=rank)
+        rho = DEVICE_CONFIGS[args.config]
+        sc = None
+        args.no_batched = args.no_factored = args.no_accuracy = args.no_learned = args.no_forms = True
+        args.no_precision = args.no_cpu_baseline = True
+        args.group_geoms = 0
+    else:
+        sc, lam = make_scene(args.config, rank, args.sensors)
+        g = sc.geom
+        A_dev = [torch.from_numpy(a).to(dev) for a in sc.A]
+        y_list = sc.y
+    s = binding.Solver(g.Q, g.M, g.K, g.N, rho, lam, stream=stream.cuda_stream, elim=args.elim,
                        precision=args.precision, correct_every=args.correct_every)
     for q in range(g.Q):
-        s.set_operator(q, torch.from_numpy(sc.A[q]).to(dev))
+        s.set_operator(q, A_dev[q])
+    del A_dev
+    torch.cuda.empty_cache()
     t0 = time.perf_counter()
     s.prepare()
     torch.cuda.synchronize()
     factor_s = time.perf_counter() - t0
-    y_dev = [torch.from_numpy(v).to(dev) for v in sc.y]
+    y_dev = [torch.from_numpy(v).to(dev) for v in y_list]
     xg = torch.empty(g.N, dtype=torch.float32, device=dev)
 
     def barrier():
@@ -773,7 +1161,7 @@ def main():
     # end to end through the C ABI with pinned host buffers
     e2e = None
     if not args.no_e2e:
-        y_host = [torch.from_numpy(v).pin_memory() for v in sc.y]
+        y_host = [torch.from_numpy(v).pin_memory() for v in y_list]
         x_host = torch.empty(g.N, dtype=torch.float32).pin_memory()
         barrier()
         t0 = time.perf_counter()
@@ -791,17 +1179,23 @@ def main():
     hbm, src = peaks()
     # operator bytes per entry: complex64 or hi+lo pairs 8; hi plane 4 (+4 on refresh iterations)
     bpe = 8.0 if args.precision in (0, 1, 2) else 4.0 * (1.0 + 1.0 / args.correct_every)
+    nt = -(-min(g.N, 2 * g.KM) // 64)
+    packed = g.Q * nt * (nt + 1) // 2 * 64 * 64 * 8.0                 # (hi, lo) pairs of the packed factor
     per_launch_bytes = {
         "forward": g.Q * g.KM * g.N * bpe,
         "adjoint_update": g.Q * g.KM * g.N * bpe,
-        "spd_woodbury": g.Q * ((2 * g.KM // 64) * (2 * g.KM // 64 + 1) // 2) * 64 * 64 * 8.0,   # (hi, lo) pairs
+        "adjoint_primal": g.Q * g.KM * g.N * bpe,
+        "spd_woodbury": packed,
+        "spd_update": packed,
     }
     dom = max((k for k in prof if prof[k][1] > 0), key=lambda k: prof[k][0])
     dom_ms, dom_n = prof[dom]
     ach = per_launch_bytes.get(dom, 0.0) / (dom_ms / dom_n / 1e3) / 1e9 if dom_n else None
     roof = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": hbm, "unit": "GB/s",
             "frac": (ach / hbm) if ach else None, "traffic": traffic_for(dom),
-            "peak_source": src,
+            "peak_source": f"{src}: copy bandwidth (read + write), MEASURED_PEAKS.json hbm_gbs",
+            "nominal_peak": NOMINAL_HBM_GBS, "frac_of_nominal": (ach / NOMINAL_HBM_GBS) if ach else None,
+            "nominal_source": "GB300 HBM3e nominal 7.9 TB/s; a read-only stream can exceed the copy peak",
             "phases_ms_per_launch": {k: (v[0] / v[1] if v[1] else None) for k, v in prof.items()},
             "algorithmic_bytes_per_launch": per_launch_bytes.get(dom)}
 
@@ -811,11 +1205,13 @@ def main():
         "scaling": "weak", "vs_baseline": None,
         "dtype": {0: "f32", 1: "bf16x2/f32", 2: "f16x2/f32", 3: "bf16/f32", 4: "f16/f32"}[args.precision],
         "data": "synthetic",
-        "config": {"workload": WORKLOAD if not args.sensors else WORKLOAD + f", first {g.Q} sensors",
+        "config": {"workload": (WORKLOAD if args.config == "paper_scale" else
+                                f"{args.config}: Q={g.Q} M={g.M} K={g.K} (KM={g.KM}) N={g.nx}x{g.nx}")
+                   + (f", first {g.Q} sensors" if args.sensors else ""),
                    "iters_per_step": args.iters, "elim": args.elim, "precision": args.precision,
                    "correct_every": args.correct_every if args.precision >= 3 else None,
                    "parallelism": f"replicas x{world}",
-                   "l2": "inputs larger than L2 (operators 2.1 GB per replica)",
+                   "l2": f"inputs larger than L2 (operators {g.Q * g.KM * g.N * 8 / 1e9:.1f} GB per replica)",
                    "factor_s": round(factor_s, 3), "refresh_ms_total": round(refresh_ms, 3)},
         "roofline": roof,
         "e2e": e2e,
@@ -829,7 +1225,14 @@ def main():
     if not args.no_factored and g.K % 16 == 0:
         line["factored"] = factored_measure(sc, lam, dev, stream)
     if not args.no_accuracy:
-        line["time_to_accuracy"] = accuracy_measure(dev, stream)
+        if os.path.exists(os.path.join(ROOT, "tests", "golden", "resolved_128_limit.npz")):
+            line["time_to_accuracy"] = accuracy_measure_128(dev, stream)
+        line["time_to_accuracy_32"] = accuracy_measure(dev, stream)
+    if not args.no_precision:
+        try:
+            line["precision"] = precision_measure(dev, stream)
+        except Exception as ex:              # reported, never fatal to the headline line
+            line["precision"] = {"error": str(ex)[:300]}
     if not args.no_learned:
         line["learned"] = learned_measure(sc, lam, dev, stream)
     if not args.no_forms:

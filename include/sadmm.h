@@ -67,8 +67,13 @@ typedef struct {
   int    precision;   /* operator used by the per-iteration products:
                          0 = complex64 (FP32), 1 = BF16 hi/lo pairs, 2 = FP16 hi/lo pairs,
                          3 = BF16 hi plane with the lo-plane products refreshed every
-                         correct_every iterations, 4 = the same with FP16 planes.  The
-                         factor, its refreshes and the fold always use the FP32 operator. */
+                         correct_every iterations, 4 = the same with FP16 planes.  With
+                         planes, the method is solved for the pair operator hi + lo (exact
+                         in FP32, within 2^-16 (BF16) or 2^-22 (FP16) of each entry): the
+                         factor, its updates and the fold use it too, and the primal-form
+                         adjoint passes g to the factor apply as an exact pair.  Changing
+                         the operator form (sadmm_set_criterion) refactors on the next
+                         solve. */
   int    correct_every; /* precision 3/4: lo-plane refresh period (>= 1)                    */
   /* elim = 2 (an extension; the paper has no counterpart).  Every learn_every
      iterations (once k >= max(Kp, 4)), before Algorithm 1's pass:
@@ -89,6 +94,16 @@ typedef struct {
      Algorithm 1's pass runs after iteration k only when k is a multiple of
      ssc_every (default 1), so that each factor update takes a batch of columns. */
   int    ssc_every;
+  /* Formulation (an option; the paper's method is the sharing form of Eq. 2-3):
+     0 = sharing ADMM (SADMM / ASADMM; output x_G = sum_q x_q);
+     1 = consensus ADMM (CADMM / ACADMM, the sibling formulation of Section I,
+     read as global consensus, Boyd et al. 2011 Sec. 7.1): every sensor images
+     one common z, min sum_q mu/2 ||y_q - A_q x_q||^2 + lambda ||z||_1 with
+     x_q = z, scaled duals u_q per sensor; x-update with v = z - u_q (the same
+     system), z = soft(mean_q (x_q + u_q), lambda / (Q rho)), u_q += x_q - z,
+     residuals of Boyd Sec. 7.1, Algorithm 1 per sensor as in the sharing form;
+     output z.  elim = 2 needs the sharing form. */
+  int    consensus;
 } sadmm_criterion;
 
 /* Per-solve summary. */
@@ -131,11 +146,32 @@ int sadmm_set_allocator(sadmm_alloc_fn alloc, sadmm_free_fn release, void* user)
 /* Creates a solver for Q sensors, M receivers, K fast-time samples and N pixels
  * on the current CUDA device (Eq. 1 sizes, Eq. 2 weights rho = beta, lambda).
  * Requirements: 1 <= Q <= 64, K*M a multiple of 32 and <= 16384, 1 <= N, rho > 0,
- * lambda >= 0, crit->mu > 0, 1 <= crit->Kp <= 64.  Allocates all device state
- * (about (8 K M N + 16 min(N, 2KM)^2) Q bytes plus O((Kp + 4) Q N)).
+ * lambda >= 0, crit->mu > 0, 1 <= crit->Kp <= 64.  Allocates the device
+ * state: about (8 K M N + 20 n^2) Q bytes with n = min(N, 2KM) (the operator,
+ * the FP64 full-set factor with its scratch, its packed pair copy), 16 n^2 Q
+ * more for the factors of shrunken sets when elim > 0 (allocated on first
+ * need otherwise), 8 K M N Q more for split-precision planes, plus
+ * O((Kp + 4) Q N).
  * crit may be NULL (defaults).  On failure *out is NULL. */
 int sadmm_create(int Q, int M, int K, int N, double rho, double lambda,
                  const sadmm_criterion* crit, sadmm_t* out);
+
+/* Replaces the method knobs of an existing context between solves (same
+ * validity rules as sadmm_create), keeping its operators and its full-set
+ * factors (refactored on the next solve only if mu or the operator form --
+ * FP32 or BF16 / FP16 pairs -- changed), so that one
+ * factorisation serves several forms of the method (plain, elimination,
+ * split precision, learned).  Buffers the new knobs need are allocated on
+ * first use; switching between BF16 and FP16 planes reconverts them.  The next
+ * sadmm_solve starts from zero as usual (sadmm_resume after a change is not
+ * supported).  SADMM_EINVAL for an invalid criterion, SADMM_ENOMEM if a
+ * buffer cannot be allocated (the context keeps its previous criterion). */
+int sadmm_set_criterion(sadmm_t ctx, const sadmm_criterion* crit);
+
+/* Replaces lambda (Eq. 2) for the next solves; the factors do not depend on
+ * it, so several scenes of one geometry (different measurements and lambda)
+ * share one factorisation.  SADMM_EINVAL unless lambda is finite and >= 0. */
+int sadmm_set_lambda(sadmm_t ctx, double lambda);
 
 /* Uses `stream` (a cudaStream_t, may be NULL for the legacy default stream)
  * for all later work of this context. */
@@ -211,7 +247,8 @@ int sadmm_get_active(sadmm_t ctx, int q, int* idx, int* count);
 int sadmm_history(sadmm_t ctx, sadmm_iter_record* out, int cap);
 
 /* Checkpoint: serialises (k, x, x_bar, z_bar, s, the Kp-deep update ring, the
- * active sets and y') into host memory.  With buf == NULL only *bytes is set. */
+ * active sets and y', and in the consensus form the duals u) into host memory.
+ * With buf == NULL only *bytes is set. */
 int sadmm_get_state(sadmm_t ctx, void* buf, size_t* bytes);
 
 /* Restores a checkpoint made by sadmm_get_state (same sizes and Kp).  Factors
@@ -269,7 +306,7 @@ const char* sadmm_last_error(void);
 typedef struct sadmm_batch_ctx* sadmm_batch_t;
 
 /* S must be 16; lambda: S per-scene l1 weights; criterion as for
- * sadmm_create (elim and precision are ignored). */
+ * sadmm_create (elim and precision are ignored; consensus must be 0: SADMM_EINVAL). */
 int sadmm_batch_create(int Q, int M, int K, int N, int S, double rho, const double* lambda,
                        const sadmm_criterion* crit, sadmm_batch_t* out);
 int sadmm_batch_set_stream(sadmm_batch_t b, void* stream);

@@ -408,10 +408,10 @@ def sadmm_primal_inverse(A, y, rho, lam, mu=1.0, iters=1000, tol=0.0, record=Non
         for q in range(Q):
             v = st.x[q] - st.xbar + st.zbar - st.s
             st.x[q] = H[q] @ (c[q] + rho * v)
-        xbar_new = st.x.mean(axis=0)
-        zbar_new = soft(xbar_new + st.s, lam / rho)
-        st.s = st.s + xbar_new - zbar_new
-        st.xbar, st.zbar = xbar_new, zbar_new
+        xb = np.mean(st.x, axis=0)
+        zb = soft(xb + st.s, lam / rho)
+        st.s = st.s + xb - zb
+        st.xbar, st.zbar = xb, zb
         st.k += 1
         nx = np.linalg.norm(st.x)
         relchange = np.linalg.norm(st.x - x_old) / nx if nx > 0 else np.inf

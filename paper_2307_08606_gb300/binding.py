@@ -26,7 +26,7 @@ class Criterion(C.Structure):
                 ("eps_abs", C.c_double), ("eps_rel", C.c_double), ("elim", C.c_int),
                 ("freeze_mode", C.c_int), ("stop", C.c_int), ("precision", C.c_int),
                 ("correct_every", C.c_int), ("learn_every", C.c_int), ("learn_theta", C.c_double),
-                ("readmit", C.c_double), ("ssc_every", C.c_int)]
+                ("readmit", C.c_double), ("ssc_every", C.c_int), ("consensus", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -100,6 +100,8 @@ _SIGS = {
                                C.c_int, C.POINTER(C.c_int), _P]),
     "sadmm_spd_apply": (C.c_int, [_P, C.c_int, C.c_int, _P, _P, _P]),
     "sadmm_set_wait_limit": (C.c_int, [C.c_longlong]),
+    "sadmm_set_criterion": (C.c_int, [_P, _P]),
+    "sadmm_set_lambda": (C.c_int, [_P, C.c_double]),
     "sadmm_gram": (C.c_int, [_P, C.c_int, C.c_int, _P, C.c_int, C.c_double, C.c_double, C.c_int, _P, C.c_int, _P,
                              _P]),
     "sadmm_factor_downdate": (C.c_int, [_P, C.c_int, _P, C.c_int, C.c_double, _P, _P]),
@@ -242,6 +244,17 @@ class Solver:
 
     def set_stream(self, stream):
         check(self.lib.sadmm_set_stream(self.h, C.c_void_p(stream)))
+
+    def set_criterion(self, **criterion):
+        """New method knobs (defaults for those not given) for the next solves,
+        keeping the operators and factors (sadmm_set_criterion)."""
+        crit = default_criterion(**criterion)
+        check(self.lib.sadmm_set_criterion(self.h, C.byref(crit)))
+        self.crit = crit
+
+    def set_lambda(self, lam):
+        """lambda of Eq. 2 for the next solves (the factors are kept)."""
+        check(self.lib.sadmm_set_lambda(self.h, float(lam)))
 
     def set_operator(self, q, A):
         """A: (N, KM) complex64 pixel-major, numpy (host) or torch (host/cuda)."""
@@ -493,8 +506,9 @@ class CNN:
 
 
 # ------------------------------------------------------ state blob conversion
-def pack_state(Q, N, KM, Kp, k, x, xbar, zbar, s, ring, J, yprime):
-    """Build a state blob (layout of sadmm_get_state) from host arrays."""
+def pack_state(Q, N, KM, Kp, k, x, xbar, zbar, s, ring, J, yprime, u=None):
+    """Build a state blob (layout of sadmm_get_state) from host arrays; u: the
+    consensus form's duals (Q, N), appended last."""
     hdr = np.array([0x31766174734d4453], dtype=np.uint64).tobytes() + np.array(
         [Q, N, KM, Kp, k, 0], dtype=np.int32).tobytes()
     cnt = np.array([len(j) for j in J], dtype=np.int32)
@@ -505,6 +519,8 @@ def pack_state(Q, N, KM, Kp, k, x, xbar, zbar, s, ring, J, yprime):
              np.asarray(zbar, np.float32).tobytes(), np.asarray(s, np.float32).tobytes(),
              np.asarray(ring, np.float32).tobytes(), cnt.tobytes(), Jpad.tobytes(),
              np.asarray(yprime, np.complex64).tobytes()]
+    if u is not None:
+        parts.append(np.asarray(u, np.float32).tobytes())
     return np.frombuffer(b"".join(parts), dtype=np.uint8).copy()
 
 

@@ -52,6 +52,7 @@ struct Sensor {
   int* E = nullptr;          // N, pixels removed in the last SSC pass
   int* F = nullptr;          // N, frozen pixels at the last learned step (elim = 2)
   int* R = nullptr;          // N, pixels re-admitted at the last learned step (elim = 2)
+  int* Jm = nullptr;         // N, intermediate lists of a multi-pass primal downdate
   double* fb[3] = {nullptr, nullptr, nullptr};   // FP64 factor buffers
   float2* fhl[3] = {nullptr, nullptr, nullptr};  // their packed symmetric (hi, lo) pair copies, used every iteration
   double* dinv = nullptr;      // diagonal-block inverses; also the downdate's n x 32 scratch
@@ -59,6 +60,8 @@ struct Sensor {
   int cum_dd = 0;              // columns downdated since the last full factorisation
   uint16_t* hi = nullptr;      // split-precision planes (precision > 0)
   uint16_t* lo = nullptr;
+  float2* P = nullptr;         // the pair operator hi + lo (exact in FP32): what the split
+                               // products see, so the factor, fold and updates use it too
   float2* base_corr = nullptr; // y' - A_lo,J v at the last lo refresh (precision 3/4)
   float* gcorr = nullptr;      // Re(a_lo^H w) per pixel at the last lo refresh
   int full = 0;              // buffer holding the full-set factor
@@ -88,6 +91,7 @@ struct Ctx {
   std::vector<void*> owned;
   std::vector<Sensor> s;
   float *x = nullptr, *xbar = nullptr, *zbar = nullptr, *sd = nullptr, *ring = nullptr;
+  float* u = nullptr;          // consensus form: Q x N scaled duals
   float* xg = nullptr;
   int* iota = nullptr;
   float2* partial = nullptr;
@@ -120,6 +124,11 @@ struct Ctx {
   bool corr_due = true;        // precision 3/4: refresh the lo-plane products next iteration
   int last_corr_k = 0;
   int split_kind() const { return (crit.precision == 1 || crit.precision == 3) ? kSplitBF16 : kSplitFP16; }
+  // the operator the iteration solves with: the stored one, or its pair form
+  const float2* op(int q) const { return crit.precision > 0 && s[q].P ? s[q].P : s[q].A; }
+  int op_kind() const { return crit.precision > 0 ? split_kind() : 0; }
+  int factor_kind = -1;        // op_kind() of the operator the full-set factors were formed from
+  int ring_kp = 0;             // update-ring capacity (Kp slots)
   int products = SADMM_PRODUCTS_AUTO;
   float2* bp_y = nullptr;      // back-projection scratch: Q x [y, -i y]
   float* bp_g = nullptr;       // Q x [Re, Im] of A^H y
@@ -220,7 +229,9 @@ struct Ctx {
   SolverView view() const {
     SolverView v;
     v.Q = Q; v.N = N; v.KM = KM; v.Kp = crit.Kp;
-    v.mu = (float)crit.mu; v.rho = (float)rho; v.lam_over_rho = (float)(lam / rho);
+    v.mu = (float)crit.mu; v.rho = (float)rho;
+    v.lam_over_rho = (float)(crit.consensus ? lam / (Q * rho) : lam / rho);
+    v.u = crit.consensus ? u : nullptr;
     v.x = x; v.xbar = xbar; v.zbar = zbar; v.s = sd; v.ring = ring;
     v.slot = k % crit.Kp;
     return v;
@@ -245,8 +256,30 @@ int factor_dims(const Ctx& c, int cnt, int* n, int* woodbury) {
   return SADMM_OK;
 }
 
+// Buffers for factors of shrunken active sets (elimination, re-admission,
+// restored states): the third FP64 buffer and two more packed pair copies, so
+// that the full-set factor (buffer 0 and its pairs) survives.  Contexts that
+// never shrink a set (plain SADMM) do without them.
+int ensure_set_buffers(Ctx& c) {
+  const size_t fbytes = (size_t)c.npad_max * c.npad_max * sizeof(double);
+  const size_t pbytes = sym_packed_pairs(c.npad_max) * sizeof(float2);
+  for (Sensor& S : c.s) {
+    if (!S.fb[2]) S.fb[2] = (double*)c.dalloc(fbytes);
+    for (int b = 1; b < 3; ++b)
+      if (!S.fhl[b]) S.fhl[b] = (float2*)c.dalloc(pbytes);
+    if (!S.Jm) S.Jm = (int*)c.dalloc((size_t)c.N * sizeof(int));
+    if (!S.fb[2] || !S.fhl[1] || !S.fhl[2] || !S.Jm) {
+      cudaGetLastError();
+      set_error("factor buffers for shrunken active sets: device allocation failed");
+      return SADMM_ENOMEM;
+    }
+  }
+  return SADMM_OK;
+}
+
 // Factor refresh for the listed sensors at their current active sets.
 int refresh(Ctx& c, const std::vector<int>& qs, bool full_set) {
+  if (!full_set) SADMM_TRY(ensure_set_buffers(c));
   std::vector<FactorJob> jobs;
   std::vector<int> owner, outbuf;
   for (int q : qs) {
@@ -258,7 +291,7 @@ int refresh(Ctx& c, const std::vector<int>& qs, bool full_set) {
     if (full_set) { o = 0; t = 1; }
     else { o = (S.full + 1) % 3; t = (S.full + 2) % 3; }
     FactorJob j;
-    j.A = S.A; j.idx = full_set ? c.iota : S.J; j.ncols = S.cnt; j.n = n;
+    j.A = c.op(q); j.idx = full_set ? c.iota : S.J; j.ncols = S.cnt; j.n = n;
     j.npad = round_up(n, kTile); j.woodbury = wb; j.out = S.fb[o]; j.tmp = S.fb[t];
     j.dinv = S.dinv;
     jobs.push_back(j);
@@ -303,6 +336,7 @@ int refresh(Ctx& c, const std::vector<int>& qs, bool full_set) {
 // definite) are returned in `failed`.
 int downdate(Ctx& c, const std::vector<int>& qs, std::vector<int>* failed, bool add = false) {
   if (qs.empty()) return SADMM_OK;
+  SADMM_TRY(ensure_set_buffers(c));
   std::vector<int> dst(c.Q), etot(c.Q);
   int max_e = 0;
   for (int q : qs) {
@@ -320,7 +354,7 @@ int downdate(Ctx& c, const std::vector<int>& qs, std::vector<int>* failed, bool 
       Sensor& S = c.s[q];
       if (etot[q] <= off) continue;
       DowndateJob j{};
-      j.A = S.A; j.E = (add ? S.R : S.E) + off; j.e = std::min(kDowndateMax, etot[q] - off); j.n = n;
+      j.A = c.op(q); j.E = (add ? S.R : S.E) + off; j.e = std::min(kDowndateMax, etot[q] - off); j.n = n;
       j.Fsrc = (off == 0) ? S.fhl[S.cur] : S.fhl[dst[q]];
       j.Fdst = S.fhl[dst[q]];
       j.P = S.dinv; j.Spart = S.dd; j.S = S.dd + nblk * kDowndateMax * kDowndateMax;
@@ -343,6 +377,8 @@ int downdate(Ctx& c, const std::vector<int>& qs, std::vector<int>* failed, bool 
 
 int prepare(Ctx& c) {
   std::vector<int> qs;
+  if (c.factor_kind != c.op_kind())        // the factors belong to another operator form
+    for (Sensor& S : c.s) S.full_valid = false;
   for (int q = 0; q < c.Q; ++q) {
     if (!c.s[q].op_set) {
       set_error("operator of sensor %d not set", q);
@@ -366,6 +402,7 @@ int prepare(Ctx& c) {
   for (int q : qs) { saved[q] = c.s[q].cnt; c.s[q].cnt = c.N; }
   int rc = refresh(c, qs, true);
   for (int q : qs) c.s[q].cnt = saved[q];
+  if (rc == SADMM_OK) c.factor_kind = c.op_kind();
   return rc;
 }
 
@@ -377,6 +414,7 @@ int reset_state(Ctx& c) {
   SADMM_CUDA_TRY(cudaMemsetAsync(c.zbar, 0, c.N * sizeof(float), c.st));
   SADMM_CUDA_TRY(cudaMemsetAsync(c.sd, 0, c.N * sizeof(float), c.st));
   SADMM_CUDA_TRY(cudaMemsetAsync(c.ring, 0, (size_t)c.crit.Kp * QN * sizeof(float), c.st));
+  if (c.u) SADMM_CUDA_TRY(cudaMemsetAsync(c.u, 0, QN * sizeof(float), c.st));
   std::vector<int> cnts(2 * c.Q, 0);
   for (int q = 0; q < c.Q; ++q) {
     Sensor& S = c.s[q];
@@ -415,9 +453,9 @@ int launch_elimination(Ctx& c, const SolverView& sv, IterScalars* out) {
     std::vector<ReadmitSet> rs;
     for (int q = 0; q < c.Q; ++q) {
       Sensor& S = c.s[q];
-      if (S.cnt > 0) fw.push_back(ColumnSet{S.A, S.J, S.cnt, q, nullptr, S.yp, S.r});
+      if (S.cnt > 0) fw.push_back(ColumnSet{c.op(q), S.J, S.cnt, q, nullptr, S.yp, S.r});
       else SADMM_CUDA_TRY(cudaMemcpyAsync(S.r, S.yp, c.KM * sizeof(float2), cudaMemcpyDeviceToDevice, c.st));
-      if (S.cnt < c.N) rs.push_back(ReadmitSet{S.A, S.F, c.N - S.cnt, q, S.r});
+      if (S.cnt < c.N) rs.push_back(ReadmitSet{c.op(q), S.F, c.N - S.cnt, q, S.r});
     }
     if (!fw.empty())
       SADMM_TRY(launch_forward(fw.data(), (int)fw.size(), c.KM, kVX, sv, c.partial, c.partial_cap, c.st));
@@ -449,8 +487,8 @@ int launch_iteration(Ctx& c, IterScalars* out) {
       if (S.woodbury)
         spd_w.push_back(SpdSet{F, S.n, reinterpret_cast<const float*>(S.r), reinterpret_cast<float*>(S.w), nullptr, q,
                                part, 0});
-      else
-        spd_p.push_back(SpdSet{F, S.n, S.g, nullptr, S.J, q, part, 0});
+      else   // g from the split adjoint as an exact pair (g, g_lo)
+        spd_p.push_back(SpdSet{F, S.n, S.g, nullptr, S.J, q, part, 0, nullptr, 0, S.g_lo});
     }
     c.mark(1, true);
     SADMM_TRY(launch_spd_apply(spd_w.data(), (int)spd_w.size(), false, sv, c.spd_err, c.st));
@@ -578,7 +616,7 @@ int launch_split_products_adj(Ctx& c, const SolverView& sv, bool corr) {
       x.gcorr_in = S.gcorr;
     }
     if (S.woodbury) upd.push_back(x);
-    else { x.g = S.g; gout.push_back(x); }
+    else { x.g = S.g; x.g_lo = S.g_lo; gout.push_back(x); }
   }
   const int kind = c.split_kind();
   const int planes = c.periodic() ? 1 : 3;
@@ -588,47 +626,83 @@ int launch_split_products_adj(Ctx& c, const SolverView& sv, bool corr) {
   return launch_split_adjoint(gout.data(), (int)gout.size(), c.KM, kind, planes, false, sv, c.st);
 }
 
-// Primal-form factors whose sets lost e <= kDowndateMax pixels and stay in
-// the primal form: H over J_new is the Schur complement of H_EE in H
-// (run_primal_downdate, FP64), written to the buffer that is neither the
-// cached full-set factor nor the current one, then packed into pairs.
-// Sensors whose small block H_EE is not numerically positive definite are
-// returned in `failed` (they are refactored).
+// Primal-form factors whose sets lost e pixels and stay in the primal form:
+// H over J_new is the Schur complement of H_EE in H (the inverse of a
+// principal submatrix), taken in passes of at most kDowndateMax removed
+// pixels in list order; before each pass but the last, the list the pass
+// leaves (J_new merged with the pixels still to be removed) is formed in
+// S.Jm.  The pair copy is packed once, after the last pass.  Sensors whose
+// small block H_EE is not numerically positive definite are returned in
+// `failed` (they are refactored).
 int primal_downdate(Ctx& c, const std::vector<int>& qs, std::vector<int>* failed) {
   if (qs.empty()) return SADMM_OK;
-  std::vector<PrimalDdJob> jobs;
-  std::vector<int> dst;
+  SADMM_TRY(ensure_set_buffers(c));
+  std::vector<int> etot(c.Q, 0), bad(c.Q, 0);
+  int passes = 0;
   for (int q : qs) {
-    Sensor& S = c.s[q];
-    const int d = (S.cur == S.full) ? (S.full + 1) % 3 : 3 - S.full - S.cur;
-    PrimalDdJob j{};
-    j.H = S.fb[S.cur];
-    j.ldh = round_up(S.n, kTile);
-    j.Hn = S.fb[d];
-    j.ldn = round_up(S.cnt, kTile);
-    j.J = S.J;
-    j.E = S.E;
-    j.n_new = S.cnt;
-    j.e = c.h_counts[c.Q + q];
-    j.pos = S.pos;
-    j.V = S.dinv;
-    j.slot = q;
-    jobs.push_back(j);
-    dst.push_back(d);
+    etot[q] = c.h_counts[c.Q + q];
+    passes = std::max(passes, div_up(etot[q], kDowndateMax));
   }
-  SADMM_CUDA_TRY(cudaMemsetAsync(c.dstatus, 0, sizeof(int) * c.Q, c.st));
-  SADMM_TRY(run_primal_downdate(jobs.data(), (int)jobs.size(), c.dstatus, c.st));
-  SADMM_CUDA_TRY(cudaMemcpyAsync(c.h_status, c.dstatus, sizeof(int) * c.Q, cudaMemcpyDeviceToHost, c.st));
-  SADMM_CUDA_TRY(cudaStreamSynchronize(c.st));
-  for (size_t i = 0; i < qs.size(); ++i) {
-    Sensor& S = c.s[qs[i]];
-    if (c.h_status[qs[i]]) { failed->push_back(qs[i]); continue; }
-    S.cur = dst[i];
-    S.n = S.cnt;
-    S.cum_dd += jobs[i].e;
-    SADMM_TRY(launch_pack_sym(S.fb[S.cur], jobs[i].ldn, S.n, S.fhl[S.cur], c.st));
+  for (int pass = 0; pass < passes; ++pass) {
+    std::vector<PrimalDdJob> jobs;
+    std::vector<int> owner, dst;
+    for (int q : qs) {
+      Sensor& S = c.s[q];
+      const int off = pass * kDowndateMax;
+      if (bad[q] || off >= etot[q]) continue;
+      const int e = std::min(kDowndateMax, etot[q] - off);
+      const int rest = etot[q] - off - e;          // removed by later passes
+      const int* Jp = S.J;
+      if (rest > 0) {
+        SADMM_TRY(launch_merge_lists(S.J, S.cnt, S.E + off + e, rest, S.Jm, c.st));
+        Jp = S.Jm;
+      }
+      const int d = (S.cur == S.full) ? (S.full + 1) % 3 : 3 - S.full - S.cur;
+      PrimalDdJob j{};
+      j.H = S.fb[S.cur];
+      j.ldh = round_up(S.n, kTile);
+      j.Hn = S.fb[d];
+      j.n_new = S.cnt + rest;
+      j.ldn = round_up(j.n_new, kTile);
+      j.J = Jp;
+      j.E = S.E + off;
+      j.e = e;
+      j.pos = S.pos;
+      j.V = S.dinv;
+      j.slot = q;
+      jobs.push_back(j);
+      owner.push_back(q);
+      dst.push_back(d);
+    }
+    if (jobs.empty()) continue;
+    SADMM_CUDA_TRY(cudaMemsetAsync(c.dstatus, 0, sizeof(int) * c.Q, c.st));
+    SADMM_TRY(run_primal_downdate(jobs.data(), (int)jobs.size(), c.dstatus, c.st));
+    SADMM_CUDA_TRY(cudaMemcpyAsync(c.h_status, c.dstatus, sizeof(int) * c.Q, cudaMemcpyDeviceToHost, c.st));
+    SADMM_CUDA_TRY(cudaStreamSynchronize(c.st));
+    for (size_t i = 0; i < jobs.size(); ++i) {
+      const int q = owner[i];
+      Sensor& S = c.s[q];
+      if (c.h_status[q]) { bad[q] = 1; failed->push_back(q); continue; }
+      S.cur = dst[i];
+      S.n = jobs[i].n_new;
+      S.cum_dd += jobs[i].e;
+    }
+  }
+  for (int q : qs) {
+    if (bad[q]) continue;
+    Sensor& S = c.s[q];
+    SADMM_TRY(launch_pack_sym(S.fb[S.cur], round_up(S.n, kTile), S.n, S.fhl[S.cur], c.st));
   }
   return SADMM_OK;
+}
+
+// A Schur-complement pass costs about 2 n^2 kDowndateMax FP64 flops (n the
+// factor's size before it), a refactorisation of the n_new kept pixels about
+// n_new^3 (Cholesky, triangular inverse, product; the Gram runs on the tensor
+// cores): the passes are taken while they are cheaper.
+bool primal_downdate_cheaper(int n_old, int n_new) {
+  const double e = n_old - n_new;
+  return 2.0 * (double)n_old * n_old * e < (double)n_new * n_new * n_new;
 }
 
 // Columns a Woodbury factor may gain or lose by rank updates before it is
@@ -645,7 +719,7 @@ int apply_changes(Ctx& c, const std::vector<int>& changed) {
     std::vector<ColumnSet> fold;
     for (int q : changed) {
       Sensor& S = c.s[q];
-      fold.push_back(ColumnSet{S.A, S.E, c.h_counts[c.Q + q], q, nullptr, S.yp, S.yp});
+      fold.push_back(ColumnSet{c.op(q), S.E, c.h_counts[c.Q + q], q, nullptr, S.yp, S.yp});
     }
     SADMM_TRY(launch_forward(fold.data(), (int)fold.size(), c.KM, kVX, sv, c.partial, c.partial_cap, c.st));
   } else {
@@ -660,7 +734,7 @@ int apply_changes(Ctx& c, const std::vector<int>& changed) {
     const Sensor& S = c.s[q];
     const int e = c.h_counts[c.Q + q];
     if (S.woodbury && S.cnt > 2 * c.KM && S.cum_dd + e <= refactor_after(c)) dd.push_back(q);
-    else if (!S.woodbury && S.pos && S.cnt > 0 && e <= kDowndateMax && S.n == S.cnt + e &&
+    else if (!S.woodbury && S.pos && S.cnt > 0 && S.n == S.cnt + e && primal_downdate_cheaper(S.n, S.cnt) &&
              S.cum_dd + e <= refactor_after(c))
       pdd.push_back(q);
     else full.push_back(q);
@@ -693,7 +767,7 @@ int readmit(Ctx& c, int* total) {
     added.push_back(q);
     S.cnt = c.h_counts[q];
     *total += nr;
-    unfold.push_back(ColumnSet{S.A, S.R, nr, q, nullptr, S.yp, S.yp});
+    unfold.push_back(ColumnSet{c.op(q), S.R, nr, q, nullptr, S.yp, S.yp});
   }
   if (added.empty()) return SADMM_OK;
   if (c.crit.freeze_mode == 0)
@@ -834,7 +908,7 @@ int run(Ctx& c, float* x_out, int iters, double tol, sadmm_stats* st) {
     }
   }
   if (x_out) {
-    SADMM_TRY(launch_scale(c.zbar, (float)c.Q, c.xg, c.N, c.st));
+    SADMM_TRY(launch_scale(c.zbar, c.crit.consensus ? 1.f : (float)c.Q, c.xg, c.N, c.st));
     SADMM_CUDA_TRY(cudaMemcpyAsync(x_out, c.xg, c.N * sizeof(float), cudaMemcpyDefault, c.st));
   }
   SADMM_TRY(take_timeout(c));
@@ -856,6 +930,15 @@ int run(Ctx& c, float* x_out, int iters, double tol, sadmm_stats* st) {
     st->bytes_iter = bytes;
   }
   return SADMM_OK;
+}
+
+bool valid_criterion(const sadmm_criterion& c) {
+  return c.mu > 0.0 && c.Kp >= 1 && c.Kp <= 64 && c.eps_p >= 0.0 && c.elim >= 0 && c.elim <= 2 &&
+         c.freeze_mode >= 0 && c.freeze_mode <= 1 &&
+         !(c.elim == 2 && (c.learn_every < 1 || !(c.eps_p > 0.0) || !(c.learn_theta >= 0.0 && c.learn_theta <= 1.0) ||
+                           !(c.readmit >= 0.0))) &&
+         c.stop >= 0 && c.stop <= 1 && c.precision >= 0 && c.precision <= 4 && c.correct_every >= 1 &&
+         c.ssc_every >= 1 && (c.consensus == 0 || c.consensus == 1) && !(c.consensus && c.elim == 2);
 }
 
 int valid_ctx(sadmm_t c) {
@@ -908,6 +991,7 @@ void sadmm_default_criterion(sadmm_criterion* c) {
   c->learn_theta = 0.5;
   c->readmit = 10.0;
   c->ssc_every = 1;
+  c->consensus = 0;
 }
 
 int sadmm_set_allocator(sadmm_alloc_fn alloc, sadmm_free_fn release, void* user) {
@@ -930,12 +1014,7 @@ int sadmm_create(int Q, int M, int K, int N, double rho, double lambda, const sa
   if (crit) c = *crit; else sadmm_default_criterion(&c);
   const long long KM = (long long)K * M;
   if (Q < 1 || Q > kMaxSets || M < 1 || K < 1 || N < 1 || KM % 32 != 0 || KM > 16384 ||
-      !(rho > 0.0) || !(lambda >= 0.0) || !(c.mu > 0.0) || c.Kp < 1 || c.Kp > 64 ||
-      !(c.eps_p >= 0.0) || c.elim < 0 || c.elim > 2 || c.freeze_mode < 0 || c.freeze_mode > 1 ||
-      (c.elim == 2 && (c.learn_every < 1 || !(c.eps_p > 0.0) || !(c.learn_theta >= 0.0 && c.learn_theta <= 1.0) ||
-                       !(c.readmit >= 0.0))) ||
-      c.stop < 0 || c.stop > 1 || !std::isfinite(rho) || !std::isfinite(lambda) ||
-      c.precision < 0 || c.precision > 4 || c.correct_every < 1 || c.ssc_every < 1) {
+      !(rho > 0.0) || !(lambda >= 0.0) || !valid_criterion(c) || !std::isfinite(rho) || !std::isfinite(lambda)) {
     set_error("sadmm_create: invalid sizes or parameters (Q=%d M=%d K=%d N=%d rho=%g lambda=%g)", Q, M,
               K, N, rho, lambda);
     return SADMM_EINVAL;
@@ -966,13 +1045,14 @@ int sadmm_create(int Q, int M, int K, int N, double rho, double lambda, const sa
     S.E = (int*)A((size_t)N * sizeof(int));
     S.F = (int*)A((size_t)N * sizeof(int));
     S.R = (int*)A((size_t)N * sizeof(int));
-    for (int b = 0; b < 3; ++b) S.fb[b] = (double*)A(fbytes);
-    for (int b = 0; b < 3; ++b) S.fhl[b] = (float2*)A(pbytes);
+    for (int b = 0; b < 2; ++b) S.fb[b] = (double*)A(fbytes);   // full-set factor and its scratch
+    S.fhl[0] = (float2*)A(pbytes);
     S.dinv = (double*)A((size_t)ctx->npad_max * kTile * sizeof(double));
     S.dd = (double*)A(downdate_scratch_doubles(2 * (int)KM) * sizeof(double));
     if (c.precision > 0) {
       S.hi = (uint16_t*)A((size_t)N * KM * 2 * sizeof(uint16_t));
       S.lo = (uint16_t*)A((size_t)N * KM * 2 * sizeof(uint16_t));
+      S.P = (float2*)A((size_t)N * KM * sizeof(float2));
       S.base_corr = (float2*)A(KM * sizeof(float2));
       S.gcorr = (float*)A((size_t)N * sizeof(float));
     }
@@ -984,6 +1064,8 @@ int sadmm_create(int Q, int M, int K, int N, double rho, double lambda, const sa
   ctx->sd = (float*)A(N * sizeof(float));
   ctx->xg = (float*)A(N * sizeof(float));
   ctx->ring = (float*)A((size_t)c.Kp * QN * sizeof(float));
+  ctx->ring_kp = c.Kp;
+  if (c.consensus) ctx->u = (float*)A(QN * sizeof(float));
   ctx->iota = (int*)A(N * sizeof(int));
   ctx->partial_cap = 0;
   for (int ns = 1; ns <= Q; ++ns) {  // any subset of sensors may be launched together
@@ -1010,6 +1092,7 @@ int sadmm_create(int Q, int M, int K, int N, double rho, double lambda, const sa
   ctx->prob = (float*)A((size_t)N * sizeof(float));
   ctx->mask = (uint8_t*)A((size_t)Q * 2 * N);
   ctx->dstatus = (int*)A(Q * sizeof(int));
+  if (ok && c.elim > 0 && ensure_set_buffers(*ctx) != SADMM_OK) ok = false;
   if (ok && (cudaMallocHost(&ctx->h_scal, sizeof(IterScalars)) != cudaSuccess ||
              cudaMallocHost(&ctx->h_counts, 4 * Q * sizeof(int)) != cudaSuccess ||
              cudaMallocHost(&ctx->h_status, Q * sizeof(int)) != cudaSuccess))
@@ -1041,6 +1124,76 @@ int sadmm_set_stream(sadmm_t ctx, void* stream) {
   return SADMM_OK;
 }
 
+int sadmm_set_criterion(sadmm_t ctx, const sadmm_criterion* crit) {
+  using namespace sadmm;
+  SADMM_TRY(valid_ctx(ctx));
+  if (!crit || !valid_criterion(*crit)) { set_error("sadmm_set_criterion: invalid criterion"); return SADMM_EINVAL; }
+  const sadmm_criterion c = *crit;
+  SADMM_CUDA_TRY(cudaStreamSynchronize(ctx->st));
+  const size_t N = ctx->N, KM = ctx->KM, QN = (size_t)ctx->Q * N;
+  bool ok = true;
+  auto A = [&](size_t b) { void* p = ctx->dalloc(b); if (!p) ok = false; return p; };
+  // buffers the new knobs need that the context was created without
+  if (c.Kp > ctx->ring_kp) {
+    ctx->ring = (float*)A((size_t)c.Kp * QN * sizeof(float));
+    ctx->ring_kp = c.Kp;
+  }
+  if (c.consensus && !ctx->u) ctx->u = (float*)A(QN * sizeof(float));
+  const int old_kind = ctx->crit.precision > 0 ? ctx->split_kind() : -1;
+  for (int q = 0; q < ctx->Q && ok; ++q) {
+    Sensor& S = ctx->s[q];
+    if (c.elim > 0 && !S.pos) S.pos = (int*)A(N * sizeof(int));
+    if (c.precision > 0 && !S.hi) {
+      S.hi = (uint16_t*)A(N * KM * 2 * sizeof(uint16_t));
+      S.lo = (uint16_t*)A(N * KM * 2 * sizeof(uint16_t));
+      S.P = (float2*)A(N * KM * sizeof(float2));
+      S.base_corr = (float2*)A(KM * sizeof(float2));
+      S.gcorr = (float*)A(N * sizeof(float));
+    }
+  }
+  if (ok && c.elim > 0 && ctx->npad_max == 2 * (int)KM && !ctx->dd.U) {
+    const int n = 2 * (int)KM;
+    ctx->dd.U = (float*)A((size_t)ctx->Q * n * 16 * sizeof(float));
+    ctx->dd.dptrs = (void**)A((size_t)2 * ctx->Q * sizeof(void*));
+    ctx->dd.part = (float2*)A(std::max((size_t)ctx->Q * multi_apply_part_pairs(n),
+                                       (size_t)kMaxSets * sym_part_pairs(n)) * sizeof(float2));
+  }
+  if (ok && c.precision > 0) {
+    size_t need = 0;
+    for (int ns = 1; ns <= ctx->Q; ++ns) need = std::max(need, split_partial_bytes(ns, (int)KM, (int)N));
+    if (need > ctx->partial_cap) {
+      ctx->partial = (float2*)A(need);
+      ctx->partial_cap = need;
+    }
+  }
+  if (ok && c.elim > 0 && ensure_set_buffers(*ctx) != SADMM_OK) ok = false;
+  if (!ok) {
+    cudaGetLastError();
+    set_error("sadmm_set_criterion: device allocation failed");
+    return SADMM_ENOMEM;
+  }
+  const bool mu_changed = c.mu != ctx->crit.mu;
+  ctx->crit = c;
+  if (c.precision > 0 && ctx->split_kind() != old_kind)
+    for (int q = 0; q < ctx->Q; ++q)
+      if (ctx->s[q].op_set)
+        SADMM_TRY(launch_split_convert(reinterpret_cast<const float*>(ctx->s[q].A), N * KM * 2, ctx->split_kind(),
+                                       ctx->s[q].hi, ctx->s[q].lo, ctx->st, reinterpret_cast<float*>(ctx->s[q].P)));
+  if (mu_changed)
+    for (Sensor& S : ctx->s) S.full_valid = false;
+  ctx->corr_due = true;
+  ctx->last_corr_k = 0;
+  SADMM_CUDA_TRY(cudaStreamSynchronize(ctx->st));
+  return SADMM_OK;
+}
+
+int sadmm_set_lambda(sadmm_t ctx, double lambda) {
+  SADMM_TRY(sadmm::valid_ctx(ctx));
+  if (!(lambda >= 0.0) || !std::isfinite(lambda)) { set_error("sadmm_set_lambda: lambda must be finite and >= 0"); return SADMM_EINVAL; }
+  ctx->lam = lambda;
+  return SADMM_OK;
+}
+
 int sadmm_set_operator(sadmm_t ctx, int q, const float* A_q) {
   SADMM_TRY(sadmm::valid_ctx(ctx));
   if (q < 0 || q >= ctx->Q || !A_q) { set_error("sadmm_set_operator: bad sensor or pointer"); return SADMM_EINVAL; }
@@ -1049,7 +1202,7 @@ int sadmm_set_operator(sadmm_t ctx, int q, const float* A_q) {
   SADMM_CUDA_TRY(cudaMemcpyAsync(S.A, A_q, (size_t)ctx->N * ctx->KM * sizeof(float2), cudaMemcpyDefault, ctx->st));
   if (ctx->crit.precision > 0)
     SADMM_TRY(sadmm::launch_split_convert(reinterpret_cast<const float*>(S.A), (size_t)ctx->N * ctx->KM * 2,
-                                          ctx->split_kind(), S.hi, S.lo, ctx->st));
+                                          ctx->split_kind(), S.hi, S.lo, ctx->st, reinterpret_cast<float*>(S.P)));
   SADMM_CUDA_TRY(cudaStreamSynchronize(ctx->st));
   S.op_set = true;
   S.full_valid = false;
@@ -1080,7 +1233,7 @@ int sadmm_set_operator_delays(sadmm_t ctx, int q, const double* tau, double f0, 
   SADMM_TRY(operator_tables(S.tau, ctx->M, ctx->K, ctx->N, f0, df, S.A, S.C, S.D, ctx->st));
   if (ctx->crit.precision > 0)
     SADMM_TRY(launch_split_convert(reinterpret_cast<const float*>(S.A), (size_t)ctx->N * ctx->KM * 2,
-                                   ctx->split_kind(), S.hi, S.lo, ctx->st));
+                                   ctx->split_kind(), S.hi, S.lo, ctx->st, reinterpret_cast<float*>(S.P)));
   SADMM_CUDA_TRY(cudaStreamSynchronize(ctx->st));
   S.op_set = true;
   S.full_valid = false;
@@ -1199,7 +1352,7 @@ struct StateHeader {
 size_t state_bytes(const Ctx& c) {
   const size_t QN = (size_t)c.Q * c.N;
   return sizeof(StateHeader) + QN * 4 + 3 * (size_t)c.N * 4 + (size_t)c.crit.Kp * QN * 4 + c.Q * 4 +
-         QN * 4 + (size_t)c.Q * c.KM * 8;
+         QN * 4 + (size_t)c.Q * c.KM * 8 + (c.crit.consensus ? QN * 4 : 0);
 }
 }  // namespace
 
@@ -1228,6 +1381,7 @@ int sadmm_get_state(sadmm_t ctx, void* buf, size_t* bytes) {
   for (int q = 0; q < ctx->Q; ++q) { memcpy(p, &ctx->s[q].cnt, 4); p += 4; }
   for (int q = 0; q < ctx->Q; ++q) SADMM_TRY(d2h(ctx->s[q].J, (size_t)ctx->N * 4));
   for (int q = 0; q < ctx->Q; ++q) SADMM_TRY(d2h(ctx->s[q].yp, (size_t)ctx->KM * 8));
+  if (ctx->crit.consensus) SADMM_TRY(d2h(ctx->u, QN * 4));     // consensus duals last
   SADMM_CUDA_TRY(cudaStreamSynchronize(ctx->st));
   return SADMM_OK;
 }
@@ -1279,6 +1433,7 @@ int sadmm_set_state(sadmm_t ctx, const void* buf, size_t bytes) {
   SADMM_TRY(h2d(ctx->zbar, p + QN * 4 + ctx->N * 4, ctx->N * 4));
   SADMM_TRY(h2d(ctx->sd, p + QN * 4 + 2 * (size_t)ctx->N * 4, ctx->N * 4));
   SADMM_TRY(h2d(ctx->ring, ring.data(), ring.size() * 4));
+  if (ctx->crit.consensus) SADMM_TRY(h2d(ctx->u, ypp + (size_t)ctx->Q * ctx->KM * 8, QN * 4));
   std::vector<int> counts(2 * ctx->Q, 0);
   std::vector<int> changed;
   for (int q = 0; q < ctx->Q; ++q) {

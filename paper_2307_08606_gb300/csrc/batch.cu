@@ -744,6 +744,10 @@ int sadmm_batch_create(int Q, int M, int K, int N, int S, double rho, const doub
   *out = nullptr;
   sadmm_criterion c;
   if (crit) c = *crit; else sadmm_default_criterion(&c);
+  if (c.consensus) {
+    set_error("sadmm_batch_create: the batched form runs the sharing formulation (consensus = 0)");
+    return SADMM_EINVAL;
+  }
   c.elim = 0;
   c.precision = 0;
   for (int s = 0; s < S; ++s)

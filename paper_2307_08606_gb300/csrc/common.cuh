@@ -79,7 +79,16 @@ struct SolverView {
   float* s;          // N
   float* ring;       // Kp x Q x N signed updates x^{t+1} - x^t
   int slot;          // ring slot written this iteration
+  float* u;          // consensus form: Q x N scaled duals (zbar holds z); null for the sharing form
 };
+
+// The x-update's v on pixel pix of sensor q (Eq. 3, x_q-update, read as
+// Boyd's sharing step: v = x_q - x_bar + z_bar - s), or, for the consensus
+// form, v = z - u_q.
+__device__ __forceinline__ float v_admm(const SolverView& sv, int q, int pix, float xq) {
+  if (sv.u) return sv.zbar[pix] - sv.u[(size_t)q * sv.N + pix];
+  return xq - sv.xbar[pix] + sv.zbar[pix] - sv.s[pix];
+}
 
 // ---- kernel launchers (implemented in the .cu files) ----
 struct ColumnSet {          // one sensor's column list for a batched launch
@@ -106,7 +115,7 @@ __device__ __forceinline__ float v_of(VMode mode, const SolverView& sv, int q, i
   const float xq = sv.x[(size_t)q * sv.N + pix];
   if (mode == kVX) return xq;
   if (mode == kVNegX) return -xq;
-  return xq - sv.xbar[pix] + sv.zbar[pix] - sv.s[pix];
+  return v_admm(sv, q, pix, xq);
 }
 
 // Factored operator (factored.cu): A[(m, k), n] = C[m][a][n] D[m][b][n] with
@@ -238,6 +247,7 @@ struct SplitSet {
   float2* out2;              // forward: the product itself (may be null)
   const float2* w;           // adjoint input (KM complex)
   float* g;                  // adjoint output in list order (+ gcorr_in when set)
+  float* g_lo;               // with g: the low words of an exact double-float g (split adjoint, no update)
   const float* gcorr_in;     // per-pixel correction added to the adjoint
   float* gcorr_out;          // adjoint: per-pixel store of the product
 };
@@ -245,8 +255,10 @@ int launch_split_forward(const SplitSet* sets, int nsets, int KM, int kind, int 
                          const SolverView& sv, float2* partial, size_t partial_cap, cudaStream_t st);
 int launch_split_adjoint(const SplitSet* sets, int nsets, int KM, int kind, int planes, bool update,
                          const SolverView& sv, cudaStream_t st);
+// hi = RN(a), lo = RN(a - hi) per float; P (may be null) = hi + lo, exact in
+// FP32: the pair operator the split products see.
 int launch_split_convert(const float* A, size_t nfloats, int kind, uint16_t* hi, uint16_t* lo,
-                         cudaStream_t st);
+                         cudaStream_t st, float* P = nullptr);
 size_t split_partial_bytes(int nsets, int KM, int max_cols);
 
 // FP64 factor: F <- (rho I + mu G)^{-1} for the Gram of the listed columns.
@@ -334,6 +346,8 @@ struct PrimalDdJob {
   int slot;           // status slot
 };
 int run_primal_downdate(const PrimalDdJob* jobs, int njobs, int* d_status, cudaStream_t st);
+// out (na + nb) = ascending merge of the ascending, disjoint lists a and b
+int launch_merge_lists(const int* a, int na, const int* b, int nb, int* out, cudaStream_t st);
 int run_downdate_pairs(const DowndateJob* jobs, int njobs, int KM, double mu, const DdScratch& scr, int* d_status,
                        int* err, cudaStream_t st);
 size_t downdate_scratch_doubles(int n);

@@ -58,7 +58,44 @@ residual_kernel(const __grid_constant__ SolverView sv, double* __restrict__ part
   double acc[kNumSums];
 #pragma unroll
   for (int j = 0; j < kNumSums; ++j) acc[j] = 0.0;
-  if (i < sv.N) {
+  if (i < sv.N && sv.u) {
+    // consensus form: z' = soft(x_bar + u_bar, lambda / (Q rho)) (lam_over_rho
+    // holds lambda / (Q rho)), u_q' = u_q + x_q - z'; sums for
+    // r_pri = ||X - z'||, ||X||, sqrt(Q) ||z'||, the dual residual
+    // rho sqrt(Q) ||z' - z||, ||U'||, ||dX||, ||z'||, ||z' - z||
+    const size_t N = sv.N;
+    float sx = 0.f, su = 0.f;
+    for (int q = 0; q < sv.Q; ++q) {
+      sx += sv.x[q * N + i];
+      su += sv.u[q * N + i];
+    }
+    const float xb = sx / (float)sv.Q, ub = su / (float)sv.Q;
+    const float z_old = sv.zbar[i];
+    const float z = soft_threshold(xb + ub, sv.lam_over_rho);
+    const float dz = z - z_old;
+    const float* ring = sv.ring + (size_t)sv.slot * sv.Q * N;
+    float a0 = 0.f, a1 = 0.f, a4 = 0.f, a5 = 0.f;
+    for (int q = 0; q < sv.Q; ++q) {
+      const float xq = sv.x[q * N + i], dx = ring[q * N + i];
+      const float e = xq - z;
+      const float un = sv.u[q * N + i] + e;
+      sv.u[q * N + i] = un;
+      a0 = fmaf(e, e, a0);
+      a1 = fmaf(xq, xq, a1);
+      a4 = fmaf(un, un, a4);
+      a5 = fmaf(dx, dx, a5);
+    }
+    acc[0] = a0;
+    acc[1] = a1;
+    acc[2] = (double)sv.Q * z * z;
+    acc[3] = (double)sv.Q * dz * dz;
+    acc[4] = a4;
+    acc[5] = a5;
+    acc[6] = (double)z * z;
+    acc[7] = (double)dz * dz;
+    sv.xbar[i] = xb;
+    sv.zbar[i] = z;
+  } else if (i < sv.N) {
     // per-pixel terms in FP32 (a handful per thread; GB300's FP64 pipe is
     // narrow), cross-thread sums in FP64
     const size_t N = sv.N;
@@ -135,14 +172,15 @@ residual_kernel(const __grid_constant__ SolverView sv, double* __restrict__ part
   if (threadIdx.x == 0) {
     const double Q = sv.Q, QN = (double)sv.Q * sv.N;
     IterScalars r;
-    r.r_pri = sqrt(Q) * sqrt(tot[0]);
+    const bool cons = sv.u != nullptr;
+    r.r_pri = (cons ? 1.0 : sqrt(Q)) * sqrt(tot[0]);
     const double xn = sqrt(tot[1]), zn = sqrt(tot[2]);
     r.eps_pri = sqrt(QN) * eps_abs + eps_rel * fmax(xn, zn);
     r.d = (double)sv.rho * sqrt(tot[3]);
-    r.eps_dual = sqrt(QN) * eps_abs + eps_rel * (double)sv.rho * sqrt(Q) * sqrt(tot[4]);
+    r.eps_dual = sqrt(QN) * eps_abs + eps_rel * (double)sv.rho * (cons ? 1.0 : sqrt(Q)) * sqrt(tot[4]);
     r.relchange = xn > 0.0 ? sqrt(tot[5]) / xn : INFINITY;
-    r.xg_norm = Q * sqrt(tot[6]);
-    r.dxg_norm = Q * sqrt(tot[7]);
+    r.xg_norm = (cons ? 1.0 : Q) * sqrt(tot[6]);
+    r.dxg_norm = (cons ? 1.0 : Q) * sqrt(tot[7]);
     r.xnorm = xn;
     r.k = k_after;
     r.gate = (elim && k_after >= Kp && k_after % ssc_every == 0 && r.r_pri <= r.eps_pri) ? 1 : 0;

@@ -831,6 +831,33 @@ pdd_update_kernel(const __grid_constant__ PddBlock jobs) {
 
 }  // namespace
 
+namespace {
+// out = the ascending merge of two ascending, disjoint lists: element t of a
+// goes to t + #{b < a[t]}, element t of b to t + #{a < b[t]}
+__global__ void merge_lists_kernel(const int* __restrict__ a, int na, const int* __restrict__ b, int nb,
+                                   int* __restrict__ out) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= na + nb) return;
+  const bool in_a = t < na;
+  const int x = in_a ? a[t] : b[t - na];
+  const int* other = in_a ? b : a;
+  int lo = 0, hi = in_a ? nb : na;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (other[mid] < x) lo = mid + 1;
+    else hi = mid;
+  }
+  out[(in_a ? t : t - na) + lo] = x;
+}
+}  // namespace
+
+int launch_merge_lists(const int* a, int na, const int* b, int nb, int* out, cudaStream_t st) {
+  if (na + nb <= 0) return SADMM_OK;
+  merge_lists_kernel<<<div_up(na + nb, 256), 256, 0, st>>>(a, na, b, nb, out);
+  SADMM_LAUNCH_CHECK();
+  return SADMM_OK;
+}
+
 int run_primal_downdate(const PrimalDdJob* jobs, int njobs, int* d_status, cudaStream_t st) {
   if (njobs <= 0) return SADMM_OK;
   if (njobs > kMaxSets) { set_error("run_primal_downdate: too many jobs"); return SADMM_EINVAL; }

@@ -308,7 +308,7 @@ factored_adjoint_kernel(const __grid_constant__ SetBlock<FactoredSet> sets, int 
     // x-update epilogue (Woodbury form): x = v + mu Re(a^H w)
     const size_t xi = (size_t)fs.q * sv.N + pix;
     const float xo = sv.x[xi];
-    const float v = xo - sv.xbar[pix] + sv.zbar[pix] - sv.s[pix];
+    const float v = v_admm(sv, fs.q, pix, xo);
     const float xn = fmaf(sv.mu, gv, v);
     sv.ring[((size_t)sv.slot * sv.Q + fs.q) * sv.N + pix] = xn - xo;
     sv.x[xi] = xn;

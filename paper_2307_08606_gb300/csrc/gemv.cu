@@ -186,6 +186,7 @@ int forward_chunks(int nsets, int KM, int max_cols) {
 constexpr int kAdjWarps = 8;
 constexpr int kAdjColsPerWarp = 8;
 constexpr int kAdjUnroll = 4;
+constexpr int kAdjWChunk = 2048;      // float4 of w staged at once (4096 complex, 32 KB)
 
 // EXACT (mode g only): every product is formed exactly and added with an
 // error-free two-sum, and g leaves as the pair (g, g_lo).  The primal
@@ -197,86 +198,108 @@ template <bool EXACT>
 __global__ void __launch_bounds__(kAdjWarps * 32)
 adjoint_kernel(const __grid_constant__ SetBlock<AdjointSet> sets, int KM, bool update,
                const __grid_constant__ SolverView sv) {
-  extern __shared__ float4 s_w4[];               // KM/2 float4 = KM complex
+  extern __shared__ float4 s_w4[];               // one chunk of w: up to kAdjWChunk float4
   const AdjointSet& as = sets.v[blockIdx.y];
   const int cols_per_cta = kAdjWarps * kAdjColsPerWarp;
   const int pbeg = blockIdx.x * cols_per_cta;
   if (pbeg >= as.n) return;
   const int n4 = KM / 2;
   const float4* w4 = reinterpret_cast<const float4*>(as.w);
-  for (int t = threadIdx.x; t < n4; t += blockDim.x) s_w4[t] = w4[t];
-  __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const float4* A4 = reinterpret_cast<const float4*>(as.A);
+  // per column of this warp, the double-float sum over the chunks done so far
+  DF colacc[kAdjColsPerWarp];
+  int pixs[kAdjColsPerWarp];
+#pragma unroll
   for (int cw = 0; cw < kAdjColsPerWarp; ++cw) {
+    colacc[cw] = DF{0.f, 0.f};
     const int p = pbeg + warp * kAdjColsPerWarp + cw;
-    if (p >= as.n) break;
-    const int pix = as.idx[p];
-    const float4* col = A4 + (size_t)pix * n4;
-    // Each float4 (two complex entries, four real products) is summed in FP32
-    // and the partial goes into a double-float accumulator: the sum over the
-    // 2KM real rows cancels heavily (|x| is far below sum |b||w|), and plain
-    // FP32 accumulation over thousands of terms loses about three digits.
-    DF acc[kAdjUnroll];
+    pixs[cw] = p < as.n ? as.idx[p] : -1;
+  }
+  // w is staged in chunks so that large KM keeps several CTAs per SM resident
+  for (int c0 = 0; c0 < n4; c0 += kAdjWChunk) {
+    const int cn = min(kAdjWChunk, n4 - c0);
+    __syncthreads();                             // the previous chunk is consumed
+    for (int t = threadIdx.x; t < cn; t += blockDim.x) s_w4[t] = w4[c0 + t];
+    __syncthreads();
+#pragma unroll 1
+    for (int cw = 0; cw < kAdjColsPerWarp; ++cw) {
+      const int pix = pixs[cw];
+      if (pix < 0) break;
+      const float4* col = A4 + (size_t)pix * n4 + c0;
+      // Each float4 (two complex entries, four real products) is summed in FP32
+      // and the partial goes into a double-float accumulator: the sum over the
+      // 2KM real rows cancels heavily (|x| is far below sum |b||w|), and plain
+      // FP32 accumulation over thousands of terms loses about three digits.
+      DF acc[kAdjUnroll];
 #pragma unroll
-    for (int u = 0; u < kAdjUnroll; ++u) acc[u] = DF{0.f, 0.f};
-    int i = lane;
-    for (; i + 32 * (kAdjUnroll - 1) < n4; i += 32 * kAdjUnroll) {
-      float4 a[kAdjUnroll];
+      for (int u = 0; u < kAdjUnroll; ++u) acc[u] = DF{0.f, 0.f};
+      int i = lane;
+      for (; i + 32 * (kAdjUnroll - 1) < cn; i += 32 * kAdjUnroll) {
+        float4 a[kAdjUnroll];
 #pragma unroll
-      for (int u = 0; u < kAdjUnroll; ++u) a[u] = ld_stream(col + i + 32 * u);
+        for (int u = 0; u < kAdjUnroll; ++u) a[u] = ld_stream(col + i + 32 * u);
 #pragma unroll
-      for (int u = 0; u < kAdjUnroll; ++u) {
-        const float4 w = s_w4[i + 32 * u];
-        if (EXACT) {
-          df_mul_acc(acc[u], a[u].x, w.x);
-          df_mul_acc(acc[u], a[u].y, w.y);
-          df_mul_acc(acc[u], a[u].z, w.z);
-          df_mul_acc(acc[u], a[u].w, w.w);
-        } else {
-          float t = a[u].x * w.x;
-          t = fmaf(a[u].y, w.y, t);
-          t = fmaf(a[u].z, w.z, t);
-          t = fmaf(a[u].w, w.w, t);
-          df_add1(acc[u], t);
+        for (int u = 0; u < kAdjUnroll; ++u) {
+          const float4 w = s_w4[i + 32 * u];
+          if (EXACT) {
+            df_mul_acc(acc[u], a[u].x, w.x);
+            df_mul_acc(acc[u], a[u].y, w.y);
+            df_mul_acc(acc[u], a[u].z, w.z);
+            df_mul_acc(acc[u], a[u].w, w.w);
+          } else {
+            float t = a[u].x * w.x;
+            t = fmaf(a[u].y, w.y, t);
+            t = fmaf(a[u].z, w.z, t);
+            t = fmaf(a[u].w, w.w, t);
+            df_add1(acc[u], t);
+          }
         }
       }
-    }
-    for (; i < n4; i += 32) {
-      const float4 a = ld_stream(col + i);
-      const float4 w = s_w4[i];
-      if (EXACT) {
-        df_mul_acc(acc[0], a.x, w.x);
-        df_mul_acc(acc[0], a.y, w.y);
-        df_mul_acc(acc[0], a.z, w.z);
-        df_mul_acc(acc[0], a.w, w.w);
-      } else {
-        float t = a.x * w.x;
-        t = fmaf(a.y, w.y, t);
-        t = fmaf(a.z, w.z, t);
-        t = fmaf(a.w, w.w, t);
-        df_add1(acc[0], t);
+      for (; i < cn; i += 32) {
+        const float4 a = ld_stream(col + i);
+        const float4 w = s_w4[i];
+        if (EXACT) {
+          df_mul_acc(acc[0], a.x, w.x);
+          df_mul_acc(acc[0], a.y, w.y);
+          df_mul_acc(acc[0], a.z, w.z);
+          df_mul_acc(acc[0], a.w, w.w);
+        } else {
+          float t = a.x * w.x;
+          t = fmaf(a.y, w.y, t);
+          t = fmaf(a.z, w.z, t);
+          t = fmaf(a.w, w.w, t);
+          df_add1(acc[0], t);
+        }
       }
-    }
 #pragma unroll
-    for (int u = 1; u < kAdjUnroll; ++u) df_add(acc[0], acc[u]);
+      for (int u = 1; u < kAdjUnroll; ++u) df_add(acc[0], acc[u]);
+      df_add(colacc[cw], acc[0]);
+    }
+  }
+#pragma unroll 1
+  for (int cw = 0; cw < kAdjColsPerWarp; ++cw) {
+    const int pix = pixs[cw];
+    if (pix < 0) break;
+    const int p = pbeg + warp * kAdjColsPerWarp + cw;
+    DF tot = colacc[cw];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-      const DF b{__shfl_xor_sync(0xffffffffu, acc[0].hi, o), __shfl_xor_sync(0xffffffffu, acc[0].lo, o)};
-      df_add(acc[0], b);
+      const DF b{__shfl_xor_sync(0xffffffffu, tot.hi, o), __shfl_xor_sync(0xffffffffu, tot.lo, o)};
+      df_add(tot, b);
     }
-    const float g = acc[0].hi + acc[0].lo;
+    const float g = tot.hi + tot.lo;
     if (lane == 0) {
       if (update) {
         // x-update epilogue (Woodbury form): x = v + mu Re(a^H w)
         const size_t xi = (size_t)as.q * sv.N + pix;
         const float xo = sv.x[xi];
-        const float v = xo - sv.xbar[pix] + sv.zbar[pix] - sv.s[pix];
+        const float v = v_admm(sv, as.q, pix, xo);
         const float xn = fmaf(sv.mu, g, v);
         sv.ring[((size_t)sv.slot * sv.Q + as.q) * sv.N + pix] = xn - xo;
         sv.x[xi] = xn;
       } else if (EXACT) {
-        const DF o = df_norm(acc[0]);
+        const DF o = df_norm(tot);
         as.g[p] = o.hi;
         as.g_lo[p] = o.lo;
       } else {
@@ -339,7 +362,7 @@ int launch_adjoint(const AdjointSet* sets, int nsets, int KM, bool update, const
       set_error("launch_adjoint: sets mix exact and plain outputs");
       return SADMM_EINVAL;
     }
-  const size_t smem = (size_t)KM * sizeof(float2);
+  const size_t smem = (size_t)std::min(KM / 2, kAdjWChunk) * sizeof(float4);
   static bool configured = false;
   if (!configured) {
     SADMM_CUDA_TRY(cudaFuncSetAttribute(adjoint_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,

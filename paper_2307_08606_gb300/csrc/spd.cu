@@ -185,7 +185,7 @@ spd_reduce_kernel(const __grid_constant__ SetBlock<SpdSet> sets, bool update, co
     const int pix = ss.idx[i];
     const size_t xi = (size_t)ss.q * sv.N + pix;
     const float xo = sv.x[xi];
-    const float v = xo - sv.xbar[pix] + sv.zbar[pix] - sv.s[pix];
+    const float v = v_admm(sv, ss.q, pix, xo);
     const float xn = fmaf(sv.mu, g, v);
     sv.ring[((size_t)sv.slot * sv.Q + ss.q) * sv.N + pix] = xn - xo;
     sv.x[xi] = xn;

@@ -53,7 +53,7 @@ __device__ __forceinline__ float v_split(VMode mode, const SolverView& sv, int q
   const float xq = sv.x[(size_t)q * sv.N + pix];
   if (mode == kVX) return xq;
   if (mode == kVNegX) return -xq;
-  return xq - sv.xbar[pix] + sv.zbar[pix] - sv.s[pix];
+  return v_admm(sv, q, pix, xq);
 }
 
 // Partial sums of sum_p (A_hi + A_lo)[:, idx[p]] v[idx[p]] (planes as selected),
@@ -160,63 +160,132 @@ int split_chunks(int nsets, int KM, int max_cols) {
 constexpr int kSaWarps = 8;
 constexpr int kSaColsPerWarp = 8;
 constexpr int kSaUnroll = 4;
+constexpr int kSaChunk = 1024;        // uint4 of a column per staged chunk of w (4096 complex, 32 KB)
 
 // g = Re((A_hi + A_lo)[:, idx[p]]^H w) (planes as selected).  Epilogue:
 // update -> x = v + mu (g + gcorr[pix]) with the ring entry; else g[p] = g and,
 // if gcorr_out is set, gcorr_out[pix] = g (the lo-plane correction store).
-template <int KIND, bool HI, bool LO>
+template <int KIND, bool HI, bool LO, bool EXACT>
 __global__ void __launch_bounds__(kSaWarps * 32)
 split_adjoint_kernel(const __grid_constant__ SetBlock<SplitSet> sets, int KM, bool update,
                      const __grid_constant__ SolverView sv) {
-  extern __shared__ float4 s_w[];                    // KM/2 float4
+  extern __shared__ float4 s_w[];                    // one chunk of w: up to 2 kSaChunk float4
   const SplitSet& as = sets.v[blockIdx.y];
   const int pbeg = blockIdx.x * kSaWarps * kSaColsPerWarp;
   if (pbeg >= as.n) return;
   const float4* w4 = reinterpret_cast<const float4*>(as.w);
-  for (int t = threadIdx.x; t < KM / 2; t += blockDim.x) s_w[t] = w4[t];
-  __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int n4 = KM / 4;
+  const int n4 = KM / 4;                              // uint4 (4 complex) per column and plane
   const uint4* H = reinterpret_cast<const uint4*>(as.hi);
   const uint4* L = reinterpret_cast<const uint4*>(as.lo);
+  // exact mode (g_lo set): each uint4's eight products are formed exactly
+  // (two-product) and summed in double-float, so that g carries no rounding
+  // of the long 2KM-term sum (the primal x-update amplifies it by up to
+  // cond(rho I + mu B^T B))
+  constexpr bool exact = EXACT;           // g_lo set, no update: every set of the launch
+  float cs[kSaColsPerWarp], dh[kSaColsPerWarp], dl[kSaColsPerWarp];
+  int pixs[kSaColsPerWarp];
+#pragma unroll
   for (int cw = 0; cw < kSaColsPerWarp; ++cw) {
+    cs[cw] = 0.f; dh[cw] = 0.f; dl[cw] = 0.f;
     const int p = pbeg + warp * kSaColsPerWarp + cw;
-    if (p >= as.n) break;
-    const int pix = as.idx[p];
-    const size_t base = (size_t)pix * n4;
-    float acc[kSaUnroll];
+    pixs[cw] = p < as.n ? as.idx[p] : -1;
+  }
+  // w is staged in chunks so that large KM keeps several CTAs per SM resident
+  for (int c0 = 0; c0 < n4; c0 += kSaChunk) {
+    const int cn = min(kSaChunk, n4 - c0);
+    __syncthreads();
+    for (int t = threadIdx.x; t < 2 * cn; t += blockDim.x) s_w[t] = w4[2 * c0 + t];
+    __syncthreads();
+#pragma unroll 1
+    for (int cw = 0; cw < kSaColsPerWarp; ++cw) {
+      const int pix = pixs[cw];
+      if (pix < 0) break;
+      const size_t base = (size_t)pix * n4 + c0;
+      float acc[kSaUnroll];
 #pragma unroll
-    for (int u = 0; u < kSaUnroll; ++u) acc[u] = 0.f;
-    for (int i0 = 0; i0 < n4; i0 += 32 * kSaUnroll) {
-      uint4 h[kSaUnroll], l[kSaUnroll];
+      for (int u = 0; u < kSaUnroll; ++u) acc[u] = 0.f;
+      float h_ = dh[cw], l_ = dl[cw];
+      for (int i0 = 0; i0 < cn; i0 += 32 * kSaUnroll) {
+        uint4 h[kSaUnroll], l[kSaUnroll];
 #pragma unroll
-      for (int u = 0; u < kSaUnroll; ++u) {
-        const int i = i0 + lane + 32 * u;
-        if (i < n4) {
-          if (HI) h[u] = ld_stream_u4(H + base + i);
-          if (LO) l[u] = ld_stream_u4(L + base + i);
+        for (int u = 0; u < kSaUnroll; ++u) {
+          const int i = i0 + lane + 32 * u;
+          if (i < cn) {
+            if (HI) h[u] = ld_stream_u4(H + base + i);
+            if (LO) l[u] = ld_stream_u4(L + base + i);
+          }
         }
-      }
 #pragma unroll
-      for (int u = 0; u < kSaUnroll; ++u) {
-        const int i = i0 + lane + 32 * u;
-        if (i < n4) {
-          float a[8], b[8];
-          if (HI) unpack4<KIND>(h[u], a);
-          if (LO) unpack4<KIND>(l[u], b);
-          const float4 wa = s_w[2 * i], wb = s_w[2 * i + 1];
-          const float wv[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
+        for (int u = 0; u < kSaUnroll; ++u) {
+          const int i = i0 + lane + 32 * u;
+          if (i < cn) {
+            float a[8], b[8];
+            if (HI) unpack4<KIND>(h[u], a);
+            if (LO) unpack4<KIND>(l[u], b);
+            const float4 wa = s_w[2 * i], wb = s_w[2 * i + 1];
+            const float wv[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
+            if constexpr (exact) {
 #pragma unroll
-          for (int k = 0; k < 8; ++k) {
-            const float e = HI ? (LO ? a[k] + b[k] : a[k]) : b[k];
-            acc[u] = fmaf(e, wv[k], acc[u]);
+              for (int k = 0; k < 8; ++k) {
+                const float e = HI ? (LO ? a[k] + b[k] : a[k]) : b[k];
+                const float p = e * wv[k];
+                const float pe = fmaf(e, wv[k], -p);     // e w = p + pe exactly
+                const float t = h_ + p;                   // two-sum h_ + p = t + err
+                const float bp = t - h_;
+                l_ += ((h_ - (t - bp)) + (p - bp)) + pe;
+                h_ = t;
+              }
+            } else {
+#pragma unroll
+              for (int k = 0; k < 8; ++k) {
+                const float e = HI ? (LO ? a[k] + b[k] : a[k]) : b[k];
+                acc[u] = fmaf(e, wv[k], acc[u]);
+              }
+            }
           }
         }
       }
-    }
-    float g = 0.f;
+      dh[cw] = h_;
+      dl[cw] = l_;
 #pragma unroll
-    for (int u = 0; u < kSaUnroll; ++u) g += acc[u];
+      for (int u = 0; u < kSaUnroll; ++u) cs[cw] += acc[u];
+    }
+  }
+#pragma unroll 1
+  for (int cw = 0; cw < kSaColsPerWarp; ++cw) {
+    const int pix = pixs[cw];
+    if (pix < 0) break;
+    const int p = pbeg + warp * kSaColsPerWarp + cw;
+    if constexpr (exact) {
+      // lane totals into one double-float (two-sum per step), plus the
+      // correction term, then the pair (g, g_lo)
+      float h_ = dh[cw], l_ = dl[cw];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const float oh = __shfl_xor_sync(0xffffffffu, h_, o);
+        const float ol = __shfl_xor_sync(0xffffffffu, l_, o);
+        const float t = h_ + oh;
+        const float bp = t - h_;
+        l_ += ((h_ - (t - bp)) + (oh - bp)) + ol;
+        h_ = t;
+      }
+      if (lane == 0) {
+        if (as.gcorr_in) {
+          const float c = as.gcorr_in[pix];
+          const float t = h_ + c;
+          const float bp = t - h_;
+          l_ += (h_ - (t - bp)) + (c - bp);
+          h_ = t;
+        }
+        const float hh = h_ + l_;
+        as.g[p] = hh;
+        as.g_lo[p] = l_ - (hh - h_);
+        if (as.gcorr_out) as.gcorr_out[pix] = hh;
+      }
+      continue;
+    }
+    float g = cs[cw];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
     if (lane == 0) {
@@ -224,7 +293,7 @@ split_adjoint_kernel(const __grid_constant__ SetBlock<SplitSet> sets, int KM, bo
         const float gc = as.gcorr_in ? as.gcorr_in[pix] : 0.f;
         const size_t xi = (size_t)as.q * sv.N + pix;
         const float xo = sv.x[xi];
-        const float v = xo - sv.xbar[pix] + sv.zbar[pix] - sv.s[pix];
+        const float v = v_admm(sv, as.q, pix, xo);
         const float xn = fmaf(sv.mu, g + gc, v);
         sv.ring[((size_t)sv.slot * sv.Q + as.q) * sv.N + pix] = xn - xo;
         sv.x[xi] = xn;
@@ -239,20 +308,24 @@ split_adjoint_kernel(const __grid_constant__ SetBlock<SplitSet> sets, int KM, bo
 // -------------------------------------------------------------- conversion
 template <int KIND>
 __global__ void split_convert_kernel(const float* __restrict__ a, uint16_t* __restrict__ hi,
-                                     uint16_t* __restrict__ lo, size_t n) {
+                                     uint16_t* __restrict__ lo, float* __restrict__ P, size_t n) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
     const float x = a[i];
+    float pair;
     if constexpr (KIND == kSplitBF16) {
       const __nv_bfloat16 h = __float2bfloat16_rn(x);
       const __nv_bfloat16 l = __float2bfloat16_rn(x - __bfloat162float(h));
       hi[i] = *reinterpret_cast<const uint16_t*>(&h);
       lo[i] = *reinterpret_cast<const uint16_t*>(&l);
+      pair = __bfloat162float(h) + __bfloat162float(l);
     } else {
       const __half h = __float2half_rn(x);
       const __half l = __float2half_rn(x - __half2float(h));
       hi[i] = *reinterpret_cast<const uint16_t*>(&h);
       lo[i] = *reinterpret_cast<const uint16_t*>(&l);
+      pair = __half2float(h) + __half2float(l);
     }
+    if (P) P[i] = pair;
   }
 }
 
@@ -266,19 +339,29 @@ int launch_split_forward_t(const SetBlock<SplitSet>& blk, int nsets, int KM, int
   return SADMM_OK;
 }
 
-template <int KIND, bool HI, bool LO>
-int launch_split_adjoint_t(const SetBlock<SplitSet>& blk, int nsets, int KM, int max_cols, bool update,
+template <int KIND, bool HI, bool LO, bool EXACT>
+int launch_split_adjoint_e(const SetBlock<SplitSet>& blk, int nsets, int KM, int max_cols, bool update,
                            const SolverView& sv, cudaStream_t st) {
   static bool configured = false;
   if (!configured) {
-    SADMM_CUDA_TRY(cudaFuncSetAttribute(split_adjoint_kernel<KIND, HI, LO>,
+    SADMM_CUDA_TRY(cudaFuncSetAttribute(split_adjoint_kernel<KIND, HI, LO, EXACT>,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     configured = true;
   }
   dim3 grid(div_up(max_cols, kSaWarps * kSaColsPerWarp), nsets);
-  split_adjoint_kernel<KIND, HI, LO><<<grid, kSaWarps * 32, (size_t)KM * sizeof(float2), st>>>(blk, KM, update, sv);
+  const size_t smem = (size_t)std::min(KM / 4, kSaChunk) * 2 * sizeof(float4);
+  split_adjoint_kernel<KIND, HI, LO, EXACT><<<grid, kSaWarps * 32, smem, st>>>(blk, KM, update, sv);
   SADMM_LAUNCH_CHECK();
   return SADMM_OK;
+}
+
+// exact double-float g when the sets ask for (g, g_lo) and no update
+template <int KIND, bool HI, bool LO>
+int launch_split_adjoint_t(const SetBlock<SplitSet>& blk, int nsets, int KM, int max_cols, bool update,
+                           const SolverView& sv, cudaStream_t st) {
+  if (blk.v[0].g_lo != nullptr && !update)
+    return launch_split_adjoint_e<KIND, HI, LO, true>(blk, nsets, KM, max_cols, update, sv, st);
+  return launch_split_adjoint_e<KIND, HI, LO, false>(blk, nsets, KM, max_cols, update, sv, st);
 }
 
 }  // namespace
@@ -344,11 +427,12 @@ int launch_split_adjoint(const SplitSet* sets, int nsets, int KM, int kind, int 
                      : launch_split_adjoint_t<kSplitFP16, false, true>(blk, nsets, KM, max_cols, update, sv, st);
 }
 
-int launch_split_convert(const float* A, size_t nfloats, int kind, uint16_t* hi, uint16_t* lo, cudaStream_t st) {
+int launch_split_convert(const float* A, size_t nfloats, int kind, uint16_t* hi, uint16_t* lo, cudaStream_t st,
+                         float* P) {
   if (nfloats == 0) return SADMM_OK;
   const int grid = (int)std::min<size_t>(div_up((long long)nfloats, 256), 152 * 64);
-  if (kind == kSplitBF16) split_convert_kernel<kSplitBF16><<<grid, 256, 0, st>>>(A, hi, lo, nfloats);
-  else if (kind == kSplitFP16) split_convert_kernel<kSplitFP16><<<grid, 256, 0, st>>>(A, hi, lo, nfloats);
+  if (kind == kSplitBF16) split_convert_kernel<kSplitBF16><<<grid, 256, 0, st>>>(A, hi, lo, P, nfloats);
+  else if (kind == kSplitFP16) split_convert_kernel<kSplitFP16><<<grid, 256, 0, st>>>(A, hi, lo, P, nfloats);
   else { set_error("launch_split_convert: bad kind"); return SADMM_EINVAL; }
   SADMM_LAUNCH_CHECK();
   return SADMM_OK;

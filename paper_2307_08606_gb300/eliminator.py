@@ -73,6 +73,21 @@ def collect(scenes, lam_of, H, W, iters, learn_every=10, horizon=50, rho=1.0, **
     return Samples(np.concatenate(F), np.concatenate(L), K)
 
 
+def collect_on(solver, ys, lams, H, W, iters, learn_every=10, horizon=50):
+    """Samples from plain runs of several scenes of one geometry on one solver
+    (created with elim = 0, operators set): the factorisation is shared, each
+    scene sets its own measurements y and lambda (sadmm_set_lambda)."""
+    F, L, K = [], [], []
+    for y, lam in zip(ys, lams):
+        solver.set_lambda(lam)
+        ks, feats, X = plain_trajectory(solver, y, iters, learn_every)
+        keep, lab = labels(X, ks, solver.crit.Kp, solver.crit.eps_p, horizon)
+        F.append(feats[keep].reshape(len(keep), 6, H, W))
+        L.append(lab.reshape(len(keep), H, W))
+        K += [ks[i] for i in keep]
+    return Samples(np.concatenate(F), np.concatenate(L), K)
+
+
 def train(net, samples, steps, lr=1e-3, batch=8, pos_weight=1.0, seed=0):
     """Adam on the network `net` (binding.CNN, max_batch >= batch) over random
     mini-batches of `samples`; returns the loss of every step."""

@@ -58,6 +58,9 @@ GEOMS = {
     # Q=8, N=128x128 with every sensor resolving the grid (2KM = 2N, Gram
     # condition ~8.5e4): the paper-scale size of a well-posed Eq. 2
     "resolved_128": Geometry(Q=8, M=256, K=64, nx=128, cell=0.08, radius=8.0, fc=60e9, bw=4e9),
+    # the precision workload at its full size (Q=8, M=16, K=512: KM=8192,
+    # N=256x256 of 5 cm; operators 8 x 4.3 GB): built on the device
+    "precision_256": Geometry(Q=8, M=16, K=512, nx=256, cell=0.05, radius=10.0, fc=77e9, bw=1e9),
     # the precision-form sensors (Q=8, M=16, K=512: KM=8192) over a 64x64 crop
     # of 5 cm cells, the oracle-sized twin of the 256x256 precision workload
     "precision_twin": Geometry(Q=8, M=16, K=512, nx=64, cell=0.05, radius=10.0, fc=77e9, bw=1e9),
@@ -75,13 +78,14 @@ def operators(g: Geometry):
         return list(pool.map(lambda q: operator(g, q), range(g.Q)))
 
 
-def build_scene(name: str, seed: int = 0, geom: Geometry = None, snr_db="default",
-                n_targets=None) -> Scene:
-    g = geom or GEOMS[name]
-    A = operators(g)
+def scene_law(name: str, g: Geometry, seed: int = 0, n_targets=None):
+    """(per-sensor reflectivities x (Q, N), SNR in dB) of the named workload."""
     if name in ("paper_scale", "resolved_128"):
         x = cluster_targets(g, seed, n_targets or 40, amp=(0.3, 1.0), p_vis=0.7)
         snr = 15.0
+    elif name == "precision_256":
+        x = cluster_targets(g, seed, n_targets or 120, amp=(0.3, 1.0), p_vis=0.7)
+        snr = 20.0
     elif name == "precision_twin":
         # 120 targets on 256^2 pixels keep their density on the 64^2 crop
         x = cluster_targets(g, seed, n_targets or 8, amp=(0.3, 1.0), p_vis=0.7)
@@ -95,6 +99,14 @@ def build_scene(name: str, seed: int = 0, geom: Geometry = None, snr_db="default
     else:
         x = point_targets(g, seed, n_targets or 8, amp=(0.5, 1.0), p_vis=0.8)
         snr = 20.0
+    return x, snr
+
+
+def build_scene(name: str, seed: int = 0, geom: Geometry = None, snr_db="default",
+                n_targets=None) -> Scene:
+    g = geom or GEOMS[name]
+    A = operators(g)
+    x, snr = scene_law(name, g, seed, n_targets)
     if snr_db != "default":
         snr = snr_db
     y = measure(A, x, snr, seed)

@@ -148,10 +148,16 @@ def cluster_targets(g: Geometry, seed: int, n_clusters: int, amp=(0.3, 1.0), p_v
 def measure(A, x_true, snr_db, seed):
     """y_q = A_q x_q + w_q (Eq. 1); w_q circular Gaussian with
     sigma^2 = ||A_q x_q||^2 / KM * 10^(-SNR/10).  Products in float64."""
+    return add_noise([Aq.astype(np.complex128).T @ x_true[q] for q, Aq in enumerate(A)], snr_db, seed)
+
+
+def add_noise(cleans, snr_db, seed):
+    """The noise of measure() added to given noiseless products A_q x_q
+    (complex128, one per sensor), for operators too large to hold on the host."""
     ns = Stream(seed, _S_NOISE)
     ys = []
-    for q, Aq in enumerate(A):
-        clean = Aq.astype(np.complex128).T @ x_true[q]
+    for clean in cleans:
+        clean = np.asarray(clean, dtype=np.complex128)
         KM = clean.shape[0]
         wr, wi = ns.normal(KM), ns.normal(KM)   # drawn even when silent: fixed stream use
         if snr_db is None:

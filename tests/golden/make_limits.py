@@ -13,10 +13,17 @@ error ||x_G^k - x_G*|| / ||x_G*|| <= 1e-3):
   dual s* (so that the KKT conditions of Eq. 2 can be checked without
   iterating) and the measurements y (complex64) that the benchmark reuses.
 
+* precision_twin_oracle.npz: the precision workload's oracle-sized twin
+  (scene precision_twin, seed 0: Q=8, M=16, K=512, N=64x64; rho = 1,
+  lambda = 0.05 lambda_max), 20 plain SADMM iterations of oracle.sadmm on the
+  complex64 operator A and on its BF16 and FP16 pair operators
+  (oracle.precision): the stacked iterates X that the benchmark compares its
+  split-precision runs with, and the measurements y.
+
 Calls only the oracle and the scene generator.  The stored limits are checked
 independently of the iteration by tests/test_oracle_pins.py
 (test_golden_limit_is_optimal, test_golden_limit_128_is_optimal).
-Run: python tests/golden/make_limits.py [resolved_32|resolved_128]"""
+Run: python tests/golden/make_limits.py [resolved_32|resolved_128|precision_twin]"""
 import json
 import os
 import sys
@@ -91,7 +98,19 @@ def resolved_128():
         json.dump(meta, f, indent=1)
 
 
+def precision_twin(iters=20):
+    sc = scenegen.build_scene("precision_twin", seed=0)
+    lam = 0.05 * scenegen.lambda_max(sc.A, sc.y)
+    out = {"y": np.stack(sc.y).astype(np.complex64), "lam": np.float64(lam), "iters": np.int64(iters)}
+    for name, A in (("X_fp32", sc.A), ("X_bf16_pairs", [oracle.precision.pair_operator(a, 1) for a in sc.A]),
+                    ("X_fp16_pairs", [oracle.precision.pair_operator(a, 2) for a in sc.A])):
+        r = oracle.sadmm(A, sc.y, 1.0, lam, oracle.Criterion(elim=0), iters=iters)
+        out[name] = r.state.x
+        print(name, float(np.linalg.norm(r.state.x)), flush=True)
+    np.savez_compressed(os.path.join(HERE, "precision_twin_oracle.npz"), **out)
+
+
 if __name__ == "__main__":
     which = sys.argv[1:] or ["resolved_32"]
     for w in which:
-        {"resolved_32": resolved_32, "resolved_128": resolved_128}[w]()
+        {"resolved_32": resolved_32, "resolved_128": resolved_128, "precision_twin": precision_twin}[w]()

@@ -209,7 +209,7 @@ def test_tensor_core_gram_is_exact_on_16_bit_entries(B, KM, N, nidx):
     assert np.array_equal(F, ref)
 
 
-@pytest.mark.parametrize("KM,N,nidx", GRAM_CASES + [(256, 1024, 1024)])
+@pytest.mark.parametrize("KM,N,nidx", GRAM_CASES + [(256, 1024, 1024), (4096, 4096, 4096)])
 def test_tensor_core_gram_matches_fp64(B, KM, N, nidx):
     """General FP32 operators (Gaussian and, in the last case, the radar
     signal model): the tensor-core Gram is within the entrywise bound of its

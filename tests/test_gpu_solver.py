@@ -296,6 +296,32 @@ def test_downdated_factor_matches_fresh_factorisation(B):
     assert _rel(c.X(), a.X()) <= 1e-6
 
 
+def test_primal_multipass_downdate_matches_fresh_factorisation(B):
+    """Primal-form factors (resolved_32: N = 1024 <= 2KM) downdated by
+    Algorithm 1 passes that remove more than 32 pixels of a sensor at once
+    (eps_p = 1e-3): the Schur complement is taken in passes of 32 pixels over
+    merged intermediate lists.  From the same state, one iteration with the
+    downdated factors equals one with factors rebuilt from scratch (set_state)
+    to FP32 rounding."""
+    sc = scenegen.build_scene("resolved_32", seed=20)
+    lam = 0.05 * scenegen.lambda_max(sc.A, sc.y)
+    a = _solver(B, sc, 100.0, lam, elim=1, eps_p=1e-3)
+    a.solve(sc.y, 40)
+    h = a.history()
+    drops = [h[i - 1]["active_total"] - h[i]["active_total"] for i in range(1, len(h))]
+    assert max(drops) > 32 * sc.geom.Q
+    assert sum(len(a.active(q)) for q in range(sc.geom.Q)) < sc.geom.Q * sc.geom.N
+    blob = a.get_state()
+    c = _solver(B, sc, 100.0, lam, elim=1, eps_p=1e-3)
+    c.prepare()
+    c.set_state(blob)
+    a.resume(1)
+    c.resume(1)
+    assert _rel(c.X(), a.X()) <= 1e-5
+    a.close()
+    c.close()
+
+
 def test_batched_removal_policy(B):
     """ssc_every = 3: Algorithm 1's pass runs only after iterations 3, 6, ...;
     on the resolved 8x8 scene the GPU run matches the oracle's iterate (1e-4)
@@ -314,6 +340,82 @@ def test_batched_removal_policy(B):
         for q in range(sc.geom.Q):
             assert np.array_equal(s.active(q), ref.state.J[q])
     s.close()
+
+
+@pytest.mark.parametrize("scene,seed,rho", [("small_point", 0, 1.0), ("resolved_tiny", 1, 2.0),
+                                             ("resolved_32", 20, 100.0)])
+def test_consensus_form_matches_oracle(B, scene, seed, rho):
+    """CADMM (criterion consensus = 1) against the oracle's consensus form at
+    equal k: the stacked iterate and z within 1e-4 after 200 iterations, in
+    the Woodbury form (small_point, N > 2KM) and the primal form (resolved_*),
+    and the returned image is z itself."""
+    sc = scenegen.build_scene(scene, seed=seed)
+    lam = 0.05 * scenegen.lambda_max(sc.A, sc.y)
+    ref = oracle.sadmm(sc.A, sc.y, rho, lam, oracle.Criterion(elim=0, consensus=True), iters=200)
+    s = _solver(B, sc, rho, lam, elim=0, consensus=1)
+    z, st = s.solve(sc.y, 200)
+    assert st["iters"] == 200
+    assert _rel(s.X(), ref.state.x) <= TOL
+    assert _rel(z, ref.xG) <= TOL
+    s.close()
+
+
+def test_consensus_elimination_synced(B):
+    """ACADMM (consensus with Algorithm 1) on the resolved 8x8 scene, one
+    iteration at a time from the oracle's state (duals u included in the
+    state blob): X within 1e-4 and the active sets equal except at pixels
+    whose oracle zeta is within 0.1 eps_p of eps_p."""
+    sc = scenegen.build_scene("resolved_tiny", seed=1)
+    lam = 0.05 * scenegen.lambda_max(sc.A, sc.y)
+    eps_p, Kp = 1e-5, 5
+    crit = oracle.Criterion(elim=1, Kp=Kp, eps_p=eps_p, consensus=True)
+    ks = [6, 40, 120, 300]
+    ref = oracle.sadmm(sc.A, sc.y, 2.0, lam, crit, iters=max(ks) + 1, snapshots=set(ks) | {k + 1 for k in ks})
+    assert sum(len(j) for j in ref.state.J) < sc.geom.Q * sc.geom.N
+    s = _solver(B, sc, 2.0, lam, elim=1, Kp=Kp, eps_p=eps_p, consensus=1)
+    s.prepare()
+    g = sc.geom
+    for k in ks:
+        st = ref.snapshots[k]
+        s.set_state(B.pack_state(g.Q, g.N, g.KM, Kp, st.k, st.x, st.xbar, st.zbar, st.s, st.ring, st.J,
+                                 np.stack([v[: g.KM] + 1j * v[g.KM:] for v in st.yprime]), u=st.u))
+        s.resume(1)
+        want = ref.snapshots[k + 1]
+        assert _rel(s.X(), want.x) <= TOL, k
+        zeta = want.ring.mean(axis=0)
+        for q in range(g.Q):
+            diff = set(s.active(q).tolist()) ^ set(want.J[q].tolist())
+            assert all(abs(zeta[q, i] - eps_p) < 0.1 * eps_p for i in diff), (k, q)
+    s.close()
+
+
+def test_criterion_change_keeps_the_factor_and_matches_fresh_contexts(B):
+    """sadmm_set_criterion between solves: one context (one factorisation)
+    run as plain SADMM, then BF16 hi plane with lo refresh, FP16 pairs, and
+    Algorithm 1 elimination gives bit-identical iterates to fresh contexts
+    created with each criterion (the factor does not depend on these knobs),
+    and switching back to the plain form reproduces the first solve."""
+    sc = scenegen.build_scene("small_point", seed=4)
+    lam = 0.05 * scenegen.lambda_max(sc.A, sc.y)
+    one = _solver(B, sc, 1.0, lam, elim=0)
+    one.prepare()
+    one.solve(sc.y, 30)
+    X0 = one.X()
+    for kw in (dict(elim=0, precision=3, correct_every=4), dict(elim=0, precision=2),
+               dict(elim=1, Kp=4), dict(elim=1, precision=1, ssc_every=2)):
+        one.set_criterion(**kw)
+        one.solve(sc.y, 30)
+        fresh = _solver(B, sc, 1.0, lam, **kw)
+        fresh.solve(sc.y, 30)
+        assert np.array_equal(one.X(), fresh.X()), kw
+        if kw["elim"]:
+            for q in range(sc.geom.Q):
+                assert np.array_equal(one.active(q), fresh.active(q))
+        fresh.close()
+    one.set_criterion(elim=0)
+    one.solve(sc.y, 30)
+    assert np.array_equal(one.X(), X0)
+    one.close()
 
 
 @pytest.fixture(scope="module")
