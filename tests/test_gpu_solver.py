@@ -369,7 +369,7 @@ def test_consensus_elimination_synced(B):
     lam = 0.05 * scenegen.lambda_max(sc.A, sc.y)
     eps_p, Kp = 1e-5, 5
     crit = oracle.Criterion(elim=1, Kp=Kp, eps_p=eps_p, consensus=True)
-    ks = [6, 40, 120, 300]
+    ks = [6, 300, 513, 520, 560]          # the first gate pass is iteration 514
     ref = oracle.sadmm(sc.A, sc.y, 2.0, lam, crit, iters=max(ks) + 1, snapshots=set(ks) | {k + 1 for k in ks})
     assert sum(len(j) for j in ref.state.J) < sc.geom.Q * sc.geom.N
     s = _solver(B, sc, 2.0, lam, elim=1, Kp=Kp, eps_p=eps_p, consensus=1)
