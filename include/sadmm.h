@@ -118,6 +118,10 @@ typedef struct {
   double ms_total;     /* host wall time of the solve                                  */
   double ms_refresh;   /* of which: fold + factor refresh after set changes            */
   double bytes_iter;   /* algorithmic bytes read by the iteration kernels, summed      */
+  int    proposed;     /* (sensor, pixel) pairs the learned proposal removed that
+                          Algorithm 1 alone would have kept (elim = 2), since the start  */
+  int    proposed_readmitted; /* of those, re-admitted later: the proposal's false
+                          eliminations caught by the re-admission test                  */
 } sadmm_stats;
 
 /* One record per iteration of the last solve. */

@@ -34,7 +34,8 @@ class Stats(C.Structure):
                 ("active_total", C.c_int), ("learned_steps", C.c_int), ("readmitted", C.c_int),
                 ("r_pri", C.c_double), ("eps_pri", C.c_double),
                 ("d", C.c_double), ("eps_dual", C.c_double), ("relchange", C.c_double),
-                ("ms_total", C.c_double), ("ms_refresh", C.c_double), ("bytes_iter", C.c_double)]
+                ("ms_total", C.c_double), ("ms_refresh", C.c_double), ("bytes_iter", C.c_double),
+                ("proposed", C.c_int), ("proposed_readmitted", C.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -116,6 +116,8 @@ struct Ctx {
   float* feat = nullptr;       // 6 x N features
   float* prob = nullptr;       // N proposal probabilities
   uint8_t* mask = nullptr;     // Q x 2N: active flags, re-admission flags
+  uint8_t* ptag = nullptr;     // Q x N: removed by the learned proposal alone (until re-admitted)
+  int* ptally = nullptr;       // 2Q: proposal removals, re-admissions of those
   bool learned_now = false;    // the iteration last launched ran the learned step
   bool learned_due() const {
     return crit.elim == 2 && cnn != nullptr && (k + 1) % crit.learn_every == 0 && k + 1 >= std::max(crit.Kp, 4);
@@ -143,8 +145,10 @@ struct Ctx {
   // primal form's H g amplifies the factored entries' rounding by the
   // condition number of rho I + mu B^T B, which the stored path avoids with
   // an exact g)
+  // the forward product's right-hand side: the sharing or the consensus x-update
+  VMode vmode() const { return crit.consensus ? kVCons : kVAdmm; }
   bool use_factored() const {
-    if (products == SADMM_PRODUCTS_STORED || crit.precision != 0 || !all_factored()) return false;
+    if (products == SADMM_PRODUCTS_STORED || crit.precision != 0 || crit.consensus || !all_factored()) return false;
     if (products == SADMM_PRODUCTS_AUTO)
       for (const Sensor& S : s)
         if (S.cnt > 0 && !S.woodbury) return false;
@@ -391,6 +395,10 @@ int prepare(Ctx& c) {
       set_error("factored products need precision 0 (the split forms read the stored planes)");
       return SADMM_EINVAL;
     }
+    if (c.crit.consensus) {
+      set_error("factored products run the sharing form (consensus = 0)");
+      return SADMM_EINVAL;
+    }
     for (int q = 0; q < c.Q; ++q)
       if (!c.s[q].factored) {
         set_error("factored products requested but sensor %d has no delays (sadmm_set_operator_delays)", q);
@@ -415,6 +423,8 @@ int reset_state(Ctx& c) {
   SADMM_CUDA_TRY(cudaMemsetAsync(c.sd, 0, c.N * sizeof(float), c.st));
   SADMM_CUDA_TRY(cudaMemsetAsync(c.ring, 0, (size_t)c.crit.Kp * QN * sizeof(float), c.st));
   if (c.u) SADMM_CUDA_TRY(cudaMemsetAsync(c.u, 0, QN * sizeof(float), c.st));
+  SADMM_CUDA_TRY(cudaMemsetAsync(c.ptag, 0, QN, c.st));
+  SADMM_CUDA_TRY(cudaMemsetAsync(c.ptally, 0, 2 * c.Q * sizeof(int), c.st));
   std::vector<int> cnts(2 * c.Q, 0);
   for (int q = 0; q < c.Q; ++q) {
     Sensor& S = c.s[q];
@@ -466,7 +476,7 @@ int launch_elimination(Ctx& c, const SolverView& sv, IterScalars* out) {
     SADMM_TRY(sadmm_cnn_forward(c.cnn, c.feat, 1, c.prob, (void*)c.st));
   }
   SADMM_TRY(launch_ssc(sv, Jp.data(), Ep.data(), c.counts, c.crit.eps_p, c.crit.freeze_mode, out, c.prob,
-                       (float)c.crit.learn_theta, c.learned_now ? 1 : 0, c.st));
+                       (float)c.crit.learn_theta, c.learned_now ? 1 : 0, c.st, c.ptag, c.ptally));
   c.mark(6, false);
   return SADMM_OK;
 }
@@ -533,10 +543,10 @@ int launch_iteration(Ctx& c, IterScalars* out) {
   }
   c.mark(0, true);
   if (fac)
-    SADMM_TRY(launch_factored_forward(ffw.data(), (int)ffw.size(), c.M, c.K, c.N, kVAdmm, sv, c.partial,
+    SADMM_TRY(launch_factored_forward(ffw.data(), (int)ffw.size(), c.M, c.K, c.N, c.vmode(), sv, c.partial,
                                       c.partial_cap, c.st));
   else
-    SADMM_TRY(launch_forward(fw.data(), (int)fw.size(), c.KM, kVAdmm, sv, c.partial, c.partial_cap, c.st));
+    SADMM_TRY(launch_forward(fw.data(), (int)fw.size(), c.KM, c.vmode(), sv, c.partial, c.partial_cap, c.st));
   c.mark(0, false);
   if (!spd_w.empty()) {
     c.mark(1, true);
@@ -592,8 +602,9 @@ int launch_split_products_fwd(Ctx& c, const SolverView& sv, bool corr) {
   }
   const int kind = c.split_kind();
   if (!b.empty())
-    SADMM_TRY(launch_split_forward(b.data(), (int)b.size(), c.KM, kind, 2, kVAdmm, sv, c.partial, c.partial_cap, c.st));
-  return launch_split_forward(a.data(), (int)a.size(), c.KM, kind, c.periodic() ? 1 : 3, kVAdmm, sv,
+    SADMM_TRY(launch_split_forward(b.data(), (int)b.size(), c.KM, kind, 2, c.vmode(), sv, c.partial, c.partial_cap,
+                                   c.st));
+  return launch_split_forward(a.data(), (int)a.size(), c.KM, kind, c.periodic() ? 1 : 3, c.vmode(), sv,
                               c.partial, c.partial_cap, c.st);
 }
 
@@ -755,7 +766,7 @@ int readmit(Ctx& c, int* total) {
   std::vector<int*> Jp(c.Q), Rp(c.Q);
   for (int q = 0; q < c.Q; ++q) { Jp[q] = c.s[q].J; Rp[q] = c.s[q].R; }
   SADMM_TRY(launch_rebuild_lists(sv, Jp.data(), Rp.data(), c.mask, c.counts, c.counts + 3 * c.Q,
-                                 2.0 * c.crit.eps_p, c.st));
+                                 2.0 * c.crit.eps_p, c.st, c.ptag, c.ptally));
   SADMM_CUDA_TRY(cudaMemcpyAsync(c.h_counts, c.counts, 4 * c.Q * sizeof(int), cudaMemcpyDeviceToHost, c.st));
   SADMM_CUDA_TRY(cudaStreamSynchronize(c.st));
   std::vector<int> added;
@@ -928,6 +939,9 @@ int run(Ctx& c, float* x_out, int iters, double tol, sadmm_stats* st) {
     st->ms_total = now_ms() - t0;
     st->ms_refresh = t_ref;
     st->bytes_iter = bytes;
+    std::vector<int> tally(2 * c.Q, 0);
+    SADMM_CUDA_TRY(cudaMemcpy(tally.data(), c.ptally, tally.size() * sizeof(int), cudaMemcpyDeviceToHost));
+    for (int q = 0; q < c.Q; ++q) { st->proposed += tally[q]; st->proposed_readmitted += tally[c.Q + q]; }
   }
   return SADMM_OK;
 }
@@ -1091,6 +1105,8 @@ int sadmm_create(int Q, int M, int K, int N, double rho, double lambda, const sa
   ctx->feat = (float*)A((size_t)6 * N * sizeof(float));
   ctx->prob = (float*)A((size_t)N * sizeof(float));
   ctx->mask = (uint8_t*)A((size_t)Q * 2 * N);
+  ctx->ptag = (uint8_t*)A((size_t)Q * N);
+  ctx->ptally = (int*)A((size_t)2 * Q * sizeof(int));
   ctx->dstatus = (int*)A(Q * sizeof(int));
   if (ok && c.elim > 0 && ensure_set_buffers(*ctx) != SADMM_OK) ok = false;
   if (ok && (cudaMallocHost(&ctx->h_scal, sizeof(IterScalars)) != cudaSuccess ||

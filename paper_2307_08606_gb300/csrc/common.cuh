@@ -55,7 +55,8 @@ enum VMode : int {
   kVAdmm = 0,   // v = x_q - x_bar + z_bar - s   (Eq. 3, x_q-update right-hand side)
   kVX = 1,      // v = x_q                       (fold of frozen pixels into y')
   kVExplicit = 2,// v = caller array indexed by pixel
-  kVNegX = 3     // v = -x_q                      (unfold of re-admitted pixels)
+  kVNegX = 3,    // v = -x_q                      (unfold of re-admitted pixels)
+  kVCons = 4     // v = z - u_q                   (consensus form's x-update right-hand side)
 };
 
 // Device-resident per-iteration scalars written by the residual kernel
@@ -115,7 +116,16 @@ __device__ __forceinline__ float v_of(VMode mode, const SolverView& sv, int q, i
   const float xq = sv.x[(size_t)q * sv.N + pix];
   if (mode == kVX) return xq;
   if (mode == kVNegX) return -xq;
-  return v_admm(sv, q, pix, xq);
+  return xq - sv.xbar[pix] + sv.zbar[pix] - sv.s[pix];
+}
+
+// The per-column scalar with the consensus mode as a compile-time choice: the
+// forward kernels are instantiated apart for it, so that the sharing form's
+// instantiation keeps the code it had without the consensus read.
+template <bool CONS>
+__device__ __forceinline__ float v_col(VMode mode, const SolverView& sv, int q, int pix, const float* vexp) {
+  if constexpr (CONS) return sv.zbar[pix] - sv.u[(size_t)q * sv.N + pix];
+  return v_of(mode, sv, q, pix, vexp);
 }
 
 // Factored operator (factored.cu): A[(m, k), n] = C[m][a][n] D[m][b][n] with
@@ -211,9 +221,13 @@ int residual_blocks(int N);
 // Algorithm 1 on every sensor: reads the gate from `sc`; compacts J[q] in
 // place (order kept), lists removed pixels in E[q], zeroes their ring entries
 // (and x in zero mode).  counts[q] = new |J_q|, counts[Q + q] = |E_q|.
+// tag (Q x N, may be null) / tally (2Q ints): pixels the learned proposal
+// removed that Algorithm 1 alone would have kept are tagged and counted in
+// tally[q]; the rebuild counts tagged pixels that are re-admitted in
+// tally[Q + q] and clears their tags (false eliminations of the proposal).
 int launch_ssc(const SolverView& sv, int* const* J, int* const* E, int* counts, double eps_p,
                int freeze_mode, const IterScalars* sc, const float* prob, float theta, int learned_now,
-               cudaStream_t st);
+               cudaStream_t st, uint8_t* tag = nullptr, int* tally = nullptr);
 // Learned proposal and re-admission (learned.cu)
 int launch_features(const SolverView& sv, int k_done, double eps_p, float* out, cudaStream_t st);
 int launch_frozen_lists(const SolverView& sv, int* const* J, const int* counts, uint8_t* mask, int* const* F,
@@ -228,7 +242,8 @@ struct ReadmitSet {
 int launch_readmit_check(const ReadmitSet* sets, int nsets, int KM, const SolverView& sv, double thr,
                          uint8_t* mask, cudaStream_t st);
 int launch_rebuild_lists(const SolverView& sv, int* const* J, int* const* R, uint8_t* mask, int* counts,
-                         int* rcounts, double ring_fill, cudaStream_t st);
+                         int* rcounts, double ring_fill, cudaStream_t st, uint8_t* tag = nullptr,
+                         int* tally = nullptr);
 int launch_recompute_xbar(const SolverView& sv, cudaStream_t st);
 int launch_scale(const float* in, float a, float* out, int n, cudaStream_t st);
 

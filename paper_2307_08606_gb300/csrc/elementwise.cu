@@ -207,7 +207,8 @@ struct SscSet {
 __global__ void __launch_bounds__(kSscThreads)
 ssc_kernel(const __grid_constant__ SetBlock<SscSet> sets, const __grid_constant__ SolverView sv,
            int* __restrict__ counts, double eps_p, int freeze_mode, const IterScalars* sc,
-           const float* __restrict__ prob, float theta, int learned_now) {
+           const float* __restrict__ prob, float theta, int learned_now, uint8_t* __restrict__ tag,
+           int* __restrict__ tally) {
   const int q = blockIdx.x;
   const int gate = sc->gate;
   if (!gate && !learned_now) {
@@ -234,7 +235,13 @@ ssc_kernel(const __grid_constant__ SetBlock<SscSet> sets, const __grid_constant_
       z /= (double)sv.Kp;
       keep = gate ? (z >= eps_p) : true;
       // learned proposal: drop pixels the network marks as converged
-      if (learned_now && prob[pix] > theta) keep = false;
+      if (learned_now && prob[pix] > theta && keep) {
+        keep = false;
+        if (tag) {                     // removed by the proposal alone
+          tag[(size_t)q * N + pix] = 1;
+          atomicAdd(tally + q, 1);
+        }
+      }
     }
     const bool rem = valid && !keep;
     const unsigned bk = __ballot_sync(0xffffffffu, keep);
@@ -306,12 +313,12 @@ int launch_residuals(const SolverView& sv, const sadmm_criterion& c, double* par
 
 int launch_ssc(const SolverView& sv, int* const* J, int* const* E, int* counts, double eps_p,
                int freeze_mode, const IterScalars* sc, const float* prob, float theta, int learned_now,
-               cudaStream_t st) {
+               cudaStream_t st, uint8_t* tag, int* tally) {
   if (sv.Q > kMaxSets) return SADMM_EINVAL;
   SetBlock<SscSet> blk;
   for (int q = 0; q < sv.Q; ++q) blk.v[q] = SscSet{J[q], E[q]};
   ssc_kernel<<<sv.Q, kSscThreads, 0, st>>>(blk, sv, counts, eps_p, freeze_mode, sc, prob, theta,
-                                           learned_now && prob ? 1 : 0);
+                                           learned_now && prob ? 1 : 0, tally ? tag : nullptr, tally);
   SADMM_LAUNCH_CHECK();
   return SADMM_OK;
 }

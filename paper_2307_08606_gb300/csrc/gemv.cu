@@ -37,6 +37,7 @@ __device__ __forceinline__ float4 ld_stream(const float4* p) {
   return v;
 }
 
+template <bool CONS>
 __global__ void __launch_bounds__(kFwdThreads)
 forward_partial_kernel(const __grid_constant__ SetBlock<ColumnSet> sets, int KM, int chunks,
                        int cols_per_chunk, VMode mode, const __grid_constant__ SolverView sv,
@@ -61,7 +62,7 @@ forward_partial_kernel(const __grid_constant__ SetBlock<ColumnSet> sets, int KM,
     __syncthreads();
     for (int t = threadIdx.x; t < nb; t += kFwdThreads) {
       const int pix = cs.idx[b0 + t];
-      s_v[t] = v_of(mode, sv, cs.q, pix, cs.vexp);
+      s_v[t] = v_col<CONS>(mode, sv, cs.q, pix, cs.vexp);
       s_off[t] = pix;
     }
     __syncthreads();
@@ -194,6 +195,103 @@ constexpr int kAdjWChunk = 2048;      // float4 of w staged at once (4096 comple
 // condition number is that of rho I + mu B^T B: where B^T B is (nearly)
 // singular, any error in g outside the range of B^T is amplified by up to that
 // factor, so g must be exact to double-float accuracy there.
+// Whole-w form (w fits one staged chunk): each warp sums its columns in one
+// pass over the rows.
+template <bool EXACT>
+__global__ void __launch_bounds__(kAdjWarps * 32)
+adjoint_whole_kernel(const __grid_constant__ SetBlock<AdjointSet> sets, int KM, bool update,
+               const __grid_constant__ SolverView sv) {
+  extern __shared__ float4 s_w4[];               // KM/2 float4 = KM complex (KM/2 <= kAdjWChunk)
+  const AdjointSet& as = sets.v[blockIdx.y];
+  const int cols_per_cta = kAdjWarps * kAdjColsPerWarp;
+  const int pbeg = blockIdx.x * cols_per_cta;
+  if (pbeg >= as.n) return;
+  const int n4 = KM / 2;
+  const float4* w4 = reinterpret_cast<const float4*>(as.w);
+  for (int t = threadIdx.x; t < n4; t += blockDim.x) s_w4[t] = w4[t];
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const float4* A4 = reinterpret_cast<const float4*>(as.A);
+  for (int cw = 0; cw < kAdjColsPerWarp; ++cw) {
+    const int p = pbeg + warp * kAdjColsPerWarp + cw;
+    if (p >= as.n) break;
+    const int pix = as.idx[p];
+    const float4* col = A4 + (size_t)pix * n4;
+    // Each float4 (two complex entries, four real products) is summed in FP32
+    // and the partial goes into a double-float accumulator: the sum over the
+    // 2KM real rows cancels heavily (|x| is far below sum |b||w|), and plain
+    // FP32 accumulation over thousands of terms loses about three digits.
+    DF acc[kAdjUnroll];
+#pragma unroll
+    for (int u = 0; u < kAdjUnroll; ++u) acc[u] = DF{0.f, 0.f};
+    int i = lane;
+    for (; i + 32 * (kAdjUnroll - 1) < n4; i += 32 * kAdjUnroll) {
+      float4 a[kAdjUnroll];
+#pragma unroll
+      for (int u = 0; u < kAdjUnroll; ++u) a[u] = ld_stream(col + i + 32 * u);
+#pragma unroll
+      for (int u = 0; u < kAdjUnroll; ++u) {
+        const float4 w = s_w4[i + 32 * u];
+        if (EXACT) {
+          df_mul_acc(acc[u], a[u].x, w.x);
+          df_mul_acc(acc[u], a[u].y, w.y);
+          df_mul_acc(acc[u], a[u].z, w.z);
+          df_mul_acc(acc[u], a[u].w, w.w);
+        } else {
+          float t = a[u].x * w.x;
+          t = fmaf(a[u].y, w.y, t);
+          t = fmaf(a[u].z, w.z, t);
+          t = fmaf(a[u].w, w.w, t);
+          df_add1(acc[u], t);
+        }
+      }
+    }
+    for (; i < n4; i += 32) {
+      const float4 a = ld_stream(col + i);
+      const float4 w = s_w4[i];
+      if (EXACT) {
+        df_mul_acc(acc[0], a.x, w.x);
+        df_mul_acc(acc[0], a.y, w.y);
+        df_mul_acc(acc[0], a.z, w.z);
+        df_mul_acc(acc[0], a.w, w.w);
+      } else {
+        float t = a.x * w.x;
+        t = fmaf(a.y, w.y, t);
+        t = fmaf(a.z, w.z, t);
+        t = fmaf(a.w, w.w, t);
+        df_add1(acc[0], t);
+      }
+    }
+#pragma unroll
+    for (int u = 1; u < kAdjUnroll; ++u) df_add(acc[0], acc[u]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const DF b{__shfl_xor_sync(0xffffffffu, acc[0].hi, o), __shfl_xor_sync(0xffffffffu, acc[0].lo, o)};
+      df_add(acc[0], b);
+    }
+    const float g = acc[0].hi + acc[0].lo;
+    if (lane == 0) {
+      if (update) {
+        // x-update epilogue (Woodbury form): x = v + mu Re(a^H w)
+        const size_t xi = (size_t)as.q * sv.N + pix;
+        const float xo = sv.x[xi];
+        const float v = v_admm(sv, as.q, pix, xo);
+        const float xn = fmaf(sv.mu, g, v);
+        sv.ring[((size_t)sv.slot * sv.Q + as.q) * sv.N + pix] = xn - xo;
+        sv.x[xi] = xn;
+      } else if (EXACT) {
+        const DF o = df_norm(acc[0]);
+        as.g[p] = o.hi;
+        as.g_lo[p] = o.lo;
+      } else {
+        as.g[p] = g;
+      }
+    }
+  }
+}
+
+// Chunked form (large KM): w is staged in chunks; each warp keeps its
+// columns' double-float sums across the chunks.
 template <bool EXACT>
 __global__ void __launch_bounds__(kAdjWarps * 32)
 adjoint_kernel(const __grid_constant__ SetBlock<AdjointSet> sets, int KM, bool update,
@@ -329,8 +427,12 @@ int launch_forward(const ColumnSet* sets, int nsets, int KM, VMode mode, const S
     return SADMM_EINVAL;
   }
   dim3 grid(div_up(KM, kFwdRows), chunks, nsets);
-  forward_partial_kernel<<<grid, kFwdThreads, 0, st>>>(blk, KM, chunks, per, mode, sv,
-                                                       reinterpret_cast<float4*>(partial));
+  if (mode == kVCons)
+    forward_partial_kernel<true><<<grid, kFwdThreads, 0, st>>>(blk, KM, chunks, per, mode, sv,
+                                                               reinterpret_cast<float4*>(partial));
+  else
+    forward_partial_kernel<false><<<grid, kFwdThreads, 0, st>>>(blk, KM, chunks, per, mode, sv,
+                                                                reinterpret_cast<float4*>(partial));
   SADMM_LAUNCH_CHECK();
   return launch_forward_reduce(sets, nsets, KM, chunks, partial, st);
 }
@@ -372,8 +474,13 @@ int launch_adjoint(const AdjointSet* sets, int nsets, int KM, bool update, const
     configured = true;
   }
   dim3 grid(div_up(max_cols, kAdjWarps * kAdjColsPerWarp), nsets);
-  if (exact) adjoint_kernel<true><<<grid, kAdjWarps * 32, smem, st>>>(blk, KM, update, sv);
-  else adjoint_kernel<false><<<grid, kAdjWarps * 32, smem, st>>>(blk, KM, update, sv);
+  if (KM / 2 <= kAdjWChunk) {
+    if (exact) adjoint_whole_kernel<true><<<grid, kAdjWarps * 32, smem, st>>>(blk, KM, update, sv);
+    else adjoint_whole_kernel<false><<<grid, kAdjWarps * 32, smem, st>>>(blk, KM, update, sv);
+  } else {
+    if (exact) adjoint_kernel<true><<<grid, kAdjWarps * 32, smem, st>>>(blk, KM, update, sv);
+    else adjoint_kernel<false><<<grid, kAdjWarps * 32, smem, st>>>(blk, KM, update, sv);
+  }
   SADMM_LAUNCH_CHECK();
   return SADMM_OK;
 }

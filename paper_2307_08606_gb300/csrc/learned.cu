@@ -137,7 +137,7 @@ struct RebuildSet {
 __global__ void __launch_bounds__(1024)
 rebuild_lists_kernel(const __grid_constant__ SetBlock<RebuildSet> sets, const __grid_constant__ SolverView sv,
                      uint8_t* __restrict__ mask, int* __restrict__ counts, int* __restrict__ rcounts,
-                     float fill) {
+                     float fill, uint8_t* __restrict__ tag, int* __restrict__ tally) {
   const int q = blockIdx.x;
   const int N = sv.N;
   uint8_t* act = mask + (size_t)q * 2 * N;
@@ -176,6 +176,10 @@ rebuild_lists_kernel(const __grid_constant__ SetBlock<RebuildSet> sets, const __
     if (r) {
       sets.v[q].R[s_br + s_r[warp] + __popc(br & lt)] = i;
       for (int t = 0; t < sv.Kp; ++t) sv.ring[((size_t)t * sv.Q + q) * N + i] = fill;
+      if (tag && tag[(size_t)q * N + i]) {       // a proposal's removal undone: a false elimination
+        tag[(size_t)q * N + i] = 0;
+        atomicAdd(tally + sv.Q + q, 1);
+      }
     }
     __syncthreads();
     if (threadIdx.x == 0) { s_ba += s_ta; s_br += s_tr; }
@@ -217,10 +221,11 @@ int launch_readmit_check(const ReadmitSet* sets, int nsets, int KM, const Solver
 }
 
 int launch_rebuild_lists(const SolverView& sv, int* const* J, int* const* R, uint8_t* mask, int* counts,
-                         int* rcounts, double ring_fill, cudaStream_t st) {
+                         int* rcounts, double ring_fill, cudaStream_t st, uint8_t* tag, int* tally) {
   SetBlock<RebuildSet> blk;
   for (int q = 0; q < sv.Q; ++q) blk.v[q] = RebuildSet{J[q], R[q]};
-  rebuild_lists_kernel<<<sv.Q, 1024, 0, st>>>(blk, sv, mask, counts, rcounts, (float)ring_fill);
+  rebuild_lists_kernel<<<sv.Q, 1024, 0, st>>>(blk, sv, mask, counts, rcounts, (float)ring_fill,
+                                             tally ? tag : nullptr, tally);
   SADMM_LAUNCH_CHECK();
   return SADMM_OK;
 }

@@ -53,12 +53,12 @@ __device__ __forceinline__ float v_split(VMode mode, const SolverView& sv, int q
   const float xq = sv.x[(size_t)q * sv.N + pix];
   if (mode == kVX) return xq;
   if (mode == kVNegX) return -xq;
-  return v_admm(sv, q, pix, xq);
+  return xq - sv.xbar[pix] + sv.zbar[pix] - sv.s[pix];
 }
 
 // Partial sums of sum_p (A_hi + A_lo)[:, idx[p]] v[idx[p]] (planes as selected),
 // written in the float4 layout of the FP32 forward partials.
-template <int KIND, bool HI, bool LO>
+template <int KIND, bool HI, bool LO, bool CONS>
 __global__ void __launch_bounds__(kSpThreads)
 split_forward_partial_kernel(const __grid_constant__ SetBlock<SplitSet> sets, int KM, int chunks,
                              int cols_per_chunk, VMode mode, const __grid_constant__ SolverView sv,
@@ -82,7 +82,7 @@ split_forward_partial_kernel(const __grid_constant__ SetBlock<SplitSet> sets, in
     __syncthreads();
     for (int t = threadIdx.x; t < nb; t += kSpThreads) {
       const int pix = cs.idx[b0 + t];
-      s_v[t] = v_split(mode, sv, cs.q, pix, cs.vexp);
+      s_v[t] = CONS ? sv.zbar[pix] - sv.u[(size_t)cs.q * sv.N + pix] : v_split(mode, sv, cs.q, pix, cs.vexp);
       s_off[t] = pix;
     }
     __syncthreads();
@@ -165,7 +165,117 @@ constexpr int kSaChunk = 1024;        // uint4 of a column per staged chunk of w
 // g = Re((A_hi + A_lo)[:, idx[p]]^H w) (planes as selected).  Epilogue:
 // update -> x = v + mu (g + gcorr[pix]) with the ring entry; else g[p] = g and,
 // if gcorr_out is set, gcorr_out[pix] = g (the lo-plane correction store).
+// One column's products over the rows [c0, c0 + cn) of w staged in s_w (from
+// row c0): plain mode adds them to cs (FP32 partials per lane); exact mode
+// (two-product per term, double-float sum) to (h_, l_).
 template <int KIND, bool HI, bool LO, bool EXACT>
+__device__ __forceinline__ void split_adj_accumulate(const uint4* __restrict__ H, const uint4* __restrict__ L,
+                                                     size_t base, int cn, int lane, const float4* s_w, float& cs,
+                                                     float& h_, float& l_) {
+  float acc[kSaUnroll];
+#pragma unroll
+  for (int u = 0; u < kSaUnroll; ++u) acc[u] = 0.f;
+  for (int i0 = 0; i0 < cn; i0 += 32 * kSaUnroll) {
+    uint4 h[kSaUnroll], l[kSaUnroll];
+#pragma unroll
+    for (int u = 0; u < kSaUnroll; ++u) {
+      const int i = i0 + lane + 32 * u;
+      if (i < cn) {
+        if (HI) h[u] = ld_stream_u4(H + base + i);
+        if (LO) l[u] = ld_stream_u4(L + base + i);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kSaUnroll; ++u) {
+      const int i = i0 + lane + 32 * u;
+      if (i < cn) {
+        float a[8], b[8];
+        if (HI) unpack4<KIND>(h[u], a);
+        if (LO) unpack4<KIND>(l[u], b);
+        const float4 wa = s_w[2 * i], wb = s_w[2 * i + 1];
+        const float wv[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
+        if constexpr (EXACT) {
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {
+            const float e = HI ? (LO ? a[k] + b[k] : a[k]) : b[k];
+            const float p = e * wv[k];
+            const float pe = fmaf(e, wv[k], -p);     // e w = p + pe exactly
+            const float t = h_ + p;                   // two-sum h_ + p = t + err
+            const float bp = t - h_;
+            l_ += ((h_ - (t - bp)) + (p - bp)) + pe;
+            h_ = t;
+          }
+        } else {
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {
+            const float e = HI ? (LO ? a[k] + b[k] : a[k]) : b[k];
+            acc[u] = fmaf(e, wv[k], acc[u]);
+          }
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < kSaUnroll; ++u) cs += acc[u];
+}
+
+// Warp reduction of a column's sums and the epilogue: exact mode writes the
+// pair (g, g_lo) (+ the correction); else the x-update (update) or g.
+template <bool EXACT>
+__device__ __forceinline__ void split_adj_finish(const SplitSet& as, const SolverView& sv, bool update, int p,
+                                                 int pix, int lane, float g, float h_, float l_) {
+  if constexpr (EXACT) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float oh = __shfl_xor_sync(0xffffffffu, h_, o);
+      const float ol = __shfl_xor_sync(0xffffffffu, l_, o);
+      const float t = h_ + oh;
+      const float bp = t - h_;
+      l_ += ((h_ - (t - bp)) + (oh - bp)) + ol;
+      h_ = t;
+    }
+    if (lane == 0) {
+      if (as.gcorr_in) {
+        const float c = as.gcorr_in[pix];
+        const float t = h_ + c;
+        const float bp = t - h_;
+        l_ += (h_ - (t - bp)) + (c - bp);
+        h_ = t;
+      }
+      const float hh = h_ + l_;
+      as.g[p] = hh;
+      as.g_lo[p] = l_ - (hh - h_);
+      if (as.gcorr_out) as.gcorr_out[pix] = hh;
+    }
+    return;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
+  if (lane == 0) {
+    if (update) {
+      const float gc = as.gcorr_in ? as.gcorr_in[pix] : 0.f;
+      const size_t xi = (size_t)as.q * sv.N + pix;
+      const float xo = sv.x[xi];
+      const float v = v_admm(sv, as.q, pix, xo);
+      const float xn = fmaf(sv.mu, g + gc, v);
+      sv.ring[((size_t)sv.slot * sv.Q + as.q) * sv.N + pix] = xn - xo;
+      sv.x[xi] = xn;
+    } else {
+      if (as.g) as.g[p] = g + (as.gcorr_in ? as.gcorr_in[pix] : 0.f);
+      if (as.gcorr_out) as.gcorr_out[pix] = g;
+    }
+  }
+}
+
+// g = Re((A_hi + A_lo)[:, idx[p]]^H w) (planes as selected).  EXACT: the
+// launch's sets ask for g as an exact pair (g_lo set, no update): each
+// uint4's eight products are formed exactly and summed in double-float, so
+// that g carries no rounding of the long 2KM-term sum (the primal x-update
+// amplifies it by up to cond(rho I + mu B^T B)).  WHOLE: w fits one staged
+// chunk and each column is summed in one pass; otherwise w is staged in
+// chunks and each warp keeps its columns' sums across them, so that large KM
+// keeps several CTAs per SM resident.
+template <int KIND, bool HI, bool LO, bool EXACT, bool WHOLE>
 __global__ void __launch_bounds__(kSaWarps * 32)
 split_adjoint_kernel(const __grid_constant__ SetBlock<SplitSet> sets, int KM, bool update,
                      const __grid_constant__ SolverView sv) {
@@ -178,11 +288,19 @@ split_adjoint_kernel(const __grid_constant__ SetBlock<SplitSet> sets, int KM, bo
   const int n4 = KM / 4;                              // uint4 (4 complex) per column and plane
   const uint4* H = reinterpret_cast<const uint4*>(as.hi);
   const uint4* L = reinterpret_cast<const uint4*>(as.lo);
-  // exact mode (g_lo set): each uint4's eight products are formed exactly
-  // (two-product) and summed in double-float, so that g carries no rounding
-  // of the long 2KM-term sum (the primal x-update amplifies it by up to
-  // cond(rho I + mu B^T B))
-  constexpr bool exact = EXACT;           // g_lo set, no update: every set of the launch
+  if constexpr (WHOLE) {
+    for (int t = threadIdx.x; t < 2 * n4; t += blockDim.x) s_w[t] = w4[t];
+    __syncthreads();
+    for (int cw = 0; cw < kSaColsPerWarp; ++cw) {
+      const int p = pbeg + warp * kSaColsPerWarp + cw;
+      if (p >= as.n) break;
+      const int pix = as.idx[p];
+      float g = 0.f, h_ = 0.f, l_ = 0.f;
+      split_adj_accumulate<KIND, HI, LO, EXACT>(H, L, (size_t)pix * n4, n4, lane, s_w, g, h_, l_);
+      split_adj_finish<EXACT>(as, sv, update, p, pix, lane, g, h_, l_);
+    }
+    return;
+  }
   float cs[kSaColsPerWarp], dh[kSaColsPerWarp], dl[kSaColsPerWarp];
   int pixs[kSaColsPerWarp];
 #pragma unroll
@@ -191,7 +309,6 @@ split_adjoint_kernel(const __grid_constant__ SetBlock<SplitSet> sets, int KM, bo
     const int p = pbeg + warp * kSaColsPerWarp + cw;
     pixs[cw] = p < as.n ? as.idx[p] : -1;
   }
-  // w is staged in chunks so that large KM keeps several CTAs per SM resident
   for (int c0 = 0; c0 < n4; c0 += kSaChunk) {
     const int cn = min(kSaChunk, n4 - c0);
     __syncthreads();
@@ -201,107 +318,16 @@ split_adjoint_kernel(const __grid_constant__ SetBlock<SplitSet> sets, int KM, bo
     for (int cw = 0; cw < kSaColsPerWarp; ++cw) {
       const int pix = pixs[cw];
       if (pix < 0) break;
-      const size_t base = (size_t)pix * n4 + c0;
-      float acc[kSaUnroll];
-#pragma unroll
-      for (int u = 0; u < kSaUnroll; ++u) acc[u] = 0.f;
-      float h_ = dh[cw], l_ = dl[cw];
-      for (int i0 = 0; i0 < cn; i0 += 32 * kSaUnroll) {
-        uint4 h[kSaUnroll], l[kSaUnroll];
-#pragma unroll
-        for (int u = 0; u < kSaUnroll; ++u) {
-          const int i = i0 + lane + 32 * u;
-          if (i < cn) {
-            if (HI) h[u] = ld_stream_u4(H + base + i);
-            if (LO) l[u] = ld_stream_u4(L + base + i);
-          }
-        }
-#pragma unroll
-        for (int u = 0; u < kSaUnroll; ++u) {
-          const int i = i0 + lane + 32 * u;
-          if (i < cn) {
-            float a[8], b[8];
-            if (HI) unpack4<KIND>(h[u], a);
-            if (LO) unpack4<KIND>(l[u], b);
-            const float4 wa = s_w[2 * i], wb = s_w[2 * i + 1];
-            const float wv[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
-            if constexpr (exact) {
-#pragma unroll
-              for (int k = 0; k < 8; ++k) {
-                const float e = HI ? (LO ? a[k] + b[k] : a[k]) : b[k];
-                const float p = e * wv[k];
-                const float pe = fmaf(e, wv[k], -p);     // e w = p + pe exactly
-                const float t = h_ + p;                   // two-sum h_ + p = t + err
-                const float bp = t - h_;
-                l_ += ((h_ - (t - bp)) + (p - bp)) + pe;
-                h_ = t;
-              }
-            } else {
-#pragma unroll
-              for (int k = 0; k < 8; ++k) {
-                const float e = HI ? (LO ? a[k] + b[k] : a[k]) : b[k];
-                acc[u] = fmaf(e, wv[k], acc[u]);
-              }
-            }
-          }
-        }
-      }
-      dh[cw] = h_;
-      dl[cw] = l_;
-#pragma unroll
-      for (int u = 0; u < kSaUnroll; ++u) cs[cw] += acc[u];
+      float g = cs[cw], h_ = dh[cw], l_ = dl[cw];
+      split_adj_accumulate<KIND, HI, LO, EXACT>(H, L, (size_t)pix * n4 + c0, cn, lane, s_w, g, h_, l_);
+      cs[cw] = g; dh[cw] = h_; dl[cw] = l_;
     }
   }
 #pragma unroll 1
   for (int cw = 0; cw < kSaColsPerWarp; ++cw) {
     const int pix = pixs[cw];
     if (pix < 0) break;
-    const int p = pbeg + warp * kSaColsPerWarp + cw;
-    if constexpr (exact) {
-      // lane totals into one double-float (two-sum per step), plus the
-      // correction term, then the pair (g, g_lo)
-      float h_ = dh[cw], l_ = dl[cw];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const float oh = __shfl_xor_sync(0xffffffffu, h_, o);
-        const float ol = __shfl_xor_sync(0xffffffffu, l_, o);
-        const float t = h_ + oh;
-        const float bp = t - h_;
-        l_ += ((h_ - (t - bp)) + (oh - bp)) + ol;
-        h_ = t;
-      }
-      if (lane == 0) {
-        if (as.gcorr_in) {
-          const float c = as.gcorr_in[pix];
-          const float t = h_ + c;
-          const float bp = t - h_;
-          l_ += (h_ - (t - bp)) + (c - bp);
-          h_ = t;
-        }
-        const float hh = h_ + l_;
-        as.g[p] = hh;
-        as.g_lo[p] = l_ - (hh - h_);
-        if (as.gcorr_out) as.gcorr_out[pix] = hh;
-      }
-      continue;
-    }
-    float g = cs[cw];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
-    if (lane == 0) {
-      if (update) {
-        const float gc = as.gcorr_in ? as.gcorr_in[pix] : 0.f;
-        const size_t xi = (size_t)as.q * sv.N + pix;
-        const float xo = sv.x[xi];
-        const float v = v_admm(sv, as.q, pix, xo);
-        const float xn = fmaf(sv.mu, g + gc, v);
-        sv.ring[((size_t)sv.slot * sv.Q + as.q) * sv.N + pix] = xn - xo;
-        sv.x[xi] = xn;
-      } else {
-        if (as.g) as.g[p] = g + (as.gcorr_in ? as.gcorr_in[pix] : 0.f);
-        if (as.gcorr_out) as.gcorr_out[pix] = g;
-      }
-    }
+    split_adj_finish<EXACT>(as, sv, update, pbeg + warp * kSaColsPerWarp + cw, pix, lane, cs[cw], dh[cw], dl[cw]);
   }
 }
 
@@ -333,8 +359,12 @@ template <int KIND, bool HI, bool LO>
 int launch_split_forward_t(const SetBlock<SplitSet>& blk, int nsets, int KM, int chunks, int per, VMode mode,
                            const SolverView& sv, float2* partial, cudaStream_t st) {
   dim3 grid(div_up(KM, kSpRows), chunks, nsets);
-  split_forward_partial_kernel<KIND, HI, LO><<<grid, kSpThreads, 0, st>>>(blk, KM, chunks, per, mode, sv,
-                                                                         reinterpret_cast<float4*>(partial));
+  if (mode == kVCons)
+    split_forward_partial_kernel<KIND, HI, LO, true><<<grid, kSpThreads, 0, st>>>(
+        blk, KM, chunks, per, mode, sv, reinterpret_cast<float4*>(partial));
+  else
+    split_forward_partial_kernel<KIND, HI, LO, false><<<grid, kSpThreads, 0, st>>>(
+        blk, KM, chunks, per, mode, sv, reinterpret_cast<float4*>(partial));
   SADMM_LAUNCH_CHECK();
   return SADMM_OK;
 }
@@ -344,13 +374,16 @@ int launch_split_adjoint_e(const SetBlock<SplitSet>& blk, int nsets, int KM, int
                            const SolverView& sv, cudaStream_t st) {
   static bool configured = false;
   if (!configured) {
-    SADMM_CUDA_TRY(cudaFuncSetAttribute(split_adjoint_kernel<KIND, HI, LO, EXACT>,
+    SADMM_CUDA_TRY(cudaFuncSetAttribute(split_adjoint_kernel<KIND, HI, LO, EXACT, false>,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     configured = true;
   }
   dim3 grid(div_up(max_cols, kSaWarps * kSaColsPerWarp), nsets);
   const size_t smem = (size_t)std::min(KM / 4, kSaChunk) * 2 * sizeof(float4);
-  split_adjoint_kernel<KIND, HI, LO, EXACT><<<grid, kSaWarps * 32, smem, st>>>(blk, KM, update, sv);
+  if (KM / 4 <= kSaChunk)
+    split_adjoint_kernel<KIND, HI, LO, EXACT, true><<<grid, kSaWarps * 32, smem, st>>>(blk, KM, update, sv);
+  else
+    split_adjoint_kernel<KIND, HI, LO, EXACT, false><<<grid, kSaWarps * 32, smem, st>>>(blk, KM, update, sv);
   SADMM_LAUNCH_CHECK();
   return SADMM_OK;
 }

@@ -76,7 +76,8 @@ def test_forward_matches_oracle(B, KM, N, nidx, repeats, radar):
         assert rel <= 1e-5
 
 
-@pytest.mark.parametrize("KM,N,nidx", [(32, 100, 37), (96, 513, 513), (2048, 700, 650), (8192, 70, 69)])
+@pytest.mark.parametrize("KM,N,nidx", [(32, 100, 37), (96, 513, 513), (2048, 700, 650), (8192, 70, 69),
+                                       (16384, 3000, 2999)])
 def test_adjoint_matches_oracle(B, KM, N, nidx):
     A = _operator(KM, N, seed=3 * KM + N)
     s = scenegen.Stream(11, KM)

@@ -241,7 +241,13 @@ def test_trained_proposal_on_held_out_scene(B):
         out[name] = dict(work=round(sum(r["active_total"] for r in h) / full, 4),
                          dev=float(np.linalg.norm(xg - xp) / np.linalg.norm(xp)),
                          readmitted=st["readmitted"], learned_steps=st["learned_steps"],
-                         active=st["active_total"], ms=round(st["ms_total"], 1))
+                         active=st["active_total"], ms=round(st["ms_total"], 1),
+                         proposed=st["proposed"], proposed_readmitted=st["proposed_readmitted"])
+        # the proposal's own removals are counted on the device; only they can
+        # be its false eliminations, and re-admissions include them
+        assert 0 <= st["proposed_readmitted"] <= min(st["proposed"], st["readmitted"])
+        if mode == 1 or theta >= 1.0:
+            assert st["proposed"] == 0
         s.close()
     for k, v in out.items():
         print(f"{k:12s} {v}")
