@@ -474,6 +474,23 @@ int sadmm_factor(const float* A, int KM, int N, const int* idx, int nidx, double
 int sadmm_gram(const float* A, int KM, int N, const int* idx, int nidx, double mu, double rho, int method,
                double* F, int ldf, int* form, void* stream);
 
+/* The batched form's factor apply with 16 right-hand sides (Eq. 3, x_q-update:
+ * U = W R in the Woodbury form, H G in the primal form) on the tensor cores:
+ * out[i][s] = sum_{j < n} F[i][j] U[j][s], i < n, s < 16.  F: device, n x n
+ * FP64, row-major, leading dimension ld >= n (read, not modified); U: device,
+ * n x 16 FP32 [row][s]; out: device, n x 16 FP64 [row][s].  Each row of F
+ * and each column of U is scaled by a power of two (2^-e_i, 2^-f_s: the least
+ * exponents with max_j |F_ij| <= 2^e_i and max_j |U_js| <= 2^f_s) and cut into
+ * four exact 8-bit BF16 digits; the ten digit GEMMs of orders 0..3 run as
+ * tcgen05 MMAs whose 256-term chunk sums are exact integers, drained to
+ * double-float totals.  Error per entry at most about 5 * 2^-32 * n *
+ * 2^(e_i + f_s); integer-valued F and U with |F_ij|, |U_js| <= 128 give the
+ * exact product (up to 2^48).  Allocates and frees its scratch (cudaMalloc,
+ * about 8 bytes per padded entry of F) and synchronises `stream`.
+ * SADMM_EINVAL for bad arguments, SADMM_ETIMEOUT if a bounded device wait
+ * gave up. */
+int sadmm_digit_apply16(const double* F, int ld, int n, const float* U, double* out, void* stream);
+
 /* Split-precision operator planes: for each of the 2 n_complex floats a of A,
  * hi = round(a) and lo = round(a - hi) in BF16 (kind 1) or FP16 (kind 2),
  * round-to-nearest; hi + lo is exact in FP32.  hi and lo: device arrays of

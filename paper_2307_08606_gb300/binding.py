@@ -103,6 +103,7 @@ _SIGS = {
     "sadmm_set_wait_limit": (C.c_int, [C.c_longlong]),
     "sadmm_set_criterion": (C.c_int, [_P, _P]),
     "sadmm_set_lambda": (C.c_int, [_P, C.c_double]),
+    "sadmm_digit_apply16": (C.c_int, [_P, C.c_int, C.c_int, _P, _P, _P]),
     "sadmm_gram": (C.c_int, [_P, C.c_int, C.c_int, _P, C.c_int, C.c_double, C.c_double, C.c_int, _P, C.c_int, _P,
                              _P]),
     "sadmm_factor_downdate": (C.c_int, [_P, C.c_int, _P, C.c_int, C.c_double, _P, _P]),
@@ -710,3 +711,18 @@ def gram(A, idx, mu, rho, method=0, stream=0):
     check(load().sadmm_gram(_ptr(A), KM, N, _ptr(idx), nidx, float(mu), float(rho), int(method), _ptr(F), npad,
                             C.byref(form), C.c_void_p(stream)))
     return F, form.value, n
+
+
+def digit_apply16(F, U, stream=0):
+    """F[:n, :n] @ U (n x 16) on the tensor cores through exact BF16 digit
+    slices (the batched form's factor apply): F float64 (n x ld, row-major),
+    U float32 (n x 16), device tensors; returns the float64 product (n x 16)."""
+    import torch
+    n = int(U.shape[0])
+    if U.shape != (n, 16) or U.dtype != torch.float32 or F.dtype != torch.float64 or F.shape[0] < n:
+        raise ValueError("digit_apply16: F float64 (n x ld), U float32 (n x 16)")
+    F = F.contiguous()
+    U = U.contiguous()
+    out = torch.empty((n, 16), dtype=torch.float64, device=U.device)
+    check(load().sadmm_digit_apply16(_ptr(F), int(F.shape[1]), n, _ptr(U), _ptr(out), C.c_void_p(stream)))
+    return out

@@ -3,7 +3,8 @@
 // from HBM serves S scenes.  The per-iteration products become GEMMs with S
 // right-hand sides (Eq. 3, x_q-update, for all scenes at once):
 //   R_q (KM x S) = Y'_q - A_q V_q          V_q[j][s] = x - x_bar + z_bar - s  (scene s)
-//   U_q (n x S)  = F_q R_q                 (factor, double-float pairs)
+//   U_q (n x S)  = F_q R_q                 (factor; exact BF16 digit GEMMs on the
+//                                           tensor cores, bapply_tc.cu)
 //   X_q[j][s]    = V_q[j][s] + mu Re(a_j^H U_q[:, s])
 // followed by the per-scene prox / dual / residual step (Eq. 3, x_G- and dual
 // updates).  Pixel elimination is not used in this form (every scene keeps
@@ -13,6 +14,7 @@
 // s [pixel][scene], Y'_q, R_q, U_q [row][scene] (complex as float2).
 #include "common.cuh"
 #include "symtile.cuh"
+#include "digits.cuh"
 
 #include <algorithm>
 #include <chrono>
@@ -58,8 +60,8 @@ __global__ void bfwd_reduce_kernel(const float2* __restrict__ partial, const flo
   Rq[q][e] = make_float2(y.x - acc.x, y.y - acc.y);
 }
 
-// ------------------------------------------------------------ factor apply
-// U[i][s] = sum_j F[i][j] u_s[j] for the 16 scenes with F symmetric, packed
+// ------------------------------------------------- packed symmetric apply
+// U[i][s] = sum_j F[i][j] u_s[j] for 16 right-hand sides with F symmetric, packed
 // as upper-triangular 64 x 64 tiles of double-float pairs (as the
 // single-scene apply): exact products, two-sum accumulation, about 48 bits.
 // A tile (I, J) is a pair of small GEMMs, OUT_I += F_IJ U_J and (off the
@@ -68,9 +70,10 @@ __global__ void bfwd_reduce_kernel(const float2* __restrict__ partial, const flo
 // by bulk asynchronous copy (mbarrier, bounded waits); 64 threads hold 4 rows x 4 scenes of F_IJ U_J and 64 threads 4
 // columns x 4 scenes of F_IJ^T U_I, stepping along skewed diagonals so that
 // shared-memory reads do not conflict.  Per-tile partials go to a scratch
-// buffer that bspd_reduce_kernel adds in a fixed order.
-// u (and U in mode 0) use the interleaved real index of a complex [row][scene]
-// array: real row j = 2m + c lives at float (m * 16 + s) * 2 + c.
+// buffer that bspd_reduce_cols_kernel adds in a fixed order.  This serves the
+// multi-column applies of the single-scene factor updates
+// (launch_multi_apply_cols); the batched iteration uses the tensor-core digit
+// apply (bapply_tc.cu).
 using namespace symtile;
 
 constexpr int kBtThreads = 128;
@@ -80,55 +83,28 @@ constexpr int kBtPart = 2 * kT * kBS;          // float2 partials per tile (row 
 __device__ __forceinline__ size_t cidx(int j, int s) { return ((size_t)(j >> 1) * kBS + s) * 2 + (j & 1); }
 
 // The 16 values of u this thread stages for tile (I, J): thread t covers
-// slice t / 64 (u_I, then u_J) and, in mode 1, row t % 64 of it; in mode 0 the
-// complex row (t % 64) / 2 and scenes 8 (t % 2) .. 8 (t % 2) + 7 of both its
-// real rows.
-__device__ __forceinline__ void bt_load_u(const float* __restrict__ u, int n, int mode, int I, int J, int t,
-                                          float (&v)[16]) {
+// slice t / 64 (u_I, then u_J), row t % 64 of it.
+__device__ __forceinline__ void bt_load_u(const float* __restrict__ u, int n, int I, int J, int t, float (&v)[16]) {
   const int blk = (t >> 6) ? J : I;
-  const int l = t & 63;
-  if (mode == 1) {
-    const int j = blk * kT + l;
+  const int j = blk * kT + (t & 63);
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const float4 x = j < n ? reinterpret_cast<const float4*>(u + (size_t)j * kBS)[e] : make_float4(0.f, 0.f, 0.f, 0.f);
-      v[4 * e] = x.x; v[4 * e + 1] = x.y; v[4 * e + 2] = x.z; v[4 * e + 3] = x.w;
-    }
-  } else {
-    const int m = blk * (kT / 2) + (l >> 1), h = l & 1;
-    const bool ok = 2 * m < n;
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const float4 x = ok ? reinterpret_cast<const float4*>(u + ((size_t)m * kBS + 8 * h) * 2)[e]
-                          : make_float4(0.f, 0.f, 0.f, 0.f);
-      // (re, im) of scenes 8h + 2e, 8h + 2e + 1
-      v[2 * e] = x.x; v[8 + 2 * e] = x.y; v[2 * e + 1] = x.z; v[8 + 2 * e + 1] = x.w;
-    }
+  for (int e = 0; e < 4; ++e) {
+    const float4 x = j < n ? reinterpret_cast<const float4*>(u + (size_t)j * kBS)[e] : make_float4(0.f, 0.f, 0.f, 0.f);
+    v[4 * e] = x.x; v[4 * e + 1] = x.y; v[4 * e + 2] = x.z; v[4 * e + 3] = x.w;
   }
 }
 
 // ... and writes them to the staged slices su[2][64][16].
-__device__ __forceinline__ void bt_store_u(float* su, int mode, int t, const float (&v)[16]) {
-  const int slice = t >> 6, l = t & 63;
-  float* base = su + (size_t)slice * kT * kBS;
-  if (mode == 1) {
+__device__ __forceinline__ void bt_store_u(float* su, int t, const float (&v)[16]) {
+  float* base = su + (size_t)(t >> 6) * kT * kBS + (t & 63) * kBS;
 #pragma unroll
-    for (int e = 0; e < 4; ++e)
-      reinterpret_cast<float4*>(base + l * kBS)[e] = make_float4(v[4 * e], v[4 * e + 1], v[4 * e + 2], v[4 * e + 3]);
-  } else {
-    const int r = (l >> 1) * 2, h = l & 1;     // real rows r (re) and r + 1 (im), scenes 8h..8h+7
-#pragma unroll
-    for (int e = 0; e < 2; ++e) {
-      reinterpret_cast<float4*>(base + r * kBS + 8 * h)[e] = make_float4(v[4 * e], v[4 * e + 1], v[4 * e + 2], v[4 * e + 3]);
-      reinterpret_cast<float4*>(base + (r + 1) * kBS + 8 * h)[e] =
-          make_float4(v[8 + 4 * e], v[8 + 4 * e + 1], v[8 + 4 * e + 2], v[8 + 4 * e + 3]);
-    }
-  }
+  for (int e = 0; e < 4; ++e)
+    reinterpret_cast<float4*>(base)[e] = make_float4(v[4 * e], v[4 * e + 1], v[4 * e + 2], v[4 * e + 3]);
 }
 
 __global__ void __launch_bounds__(kBtThreads)
 bspd_tile_kernel(const float2* const* __restrict__ Pq, const float* const* __restrict__ uq, float2* __restrict__ part,
-                 size_t part_stride, int n, int mode, int items, int* __restrict__ err) {
+                 size_t part_stride, int n, int items, int* __restrict__ err) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   float2* tile = reinterpret_cast<float2*>(smem_raw);                        // 64 x 64 pairs
   float* su = reinterpret_cast<float*>(smem_raw + kBtTileBytes);            // (u_I, u_J) x 64 x 16
@@ -157,8 +133,8 @@ bspd_tile_kernel(const float2* const* __restrict__ Pq, const float* const* __res
     }
     {
       float v[16];
-      bt_load_u(uq[q], n, mode, I, J, tid, v);
-      bt_store_u(su, mode, tid, v);
+      bt_load_u(uq[q], n, I, J, tid, v);
+      bt_store_u(su, tid, v);
     }
     __syncthreads();                                        // su written
     const bool ok = mbar_wait(&bar, phase);
@@ -221,44 +197,33 @@ bspd_tile_kernel(const float2* const* __restrict__ Pq, const float* const* __res
   }
 }
 
-// OUT[i][s] = sum_{J >= I} row part of tile (I, J) + sum_{J < I} column part of
-// tile (J, I), in a fixed order, then the epilogue:
+// OUT[i][s] = sum over the k ranges of the digit apply's partial results
+// (double-float, in a fixed order), then the epilogue:
 // mode 0 (Woodbury): U written as complex [row][scene]
 // mode 1 (primal):   x-update X = V + mu U (row i is pixel i: the full active set)
 __global__ void __launch_bounds__(256)
-bspd_reduce_kernel(const float2* __restrict__ part, size_t part_stride, float* const* __restrict__ outq, int n,
-                   int mode, BatchDev b) {
-  const int q = blockIdx.y, I = blockIdx.x;
-  const int nt = ntiles_side(n);
-  const int i = I * kT + (threadIdx.x >> 2), s0 = 4 * (threadIdx.x & 3);
-  DF acc[4] = {DF{0.f, 0.f}, DF{0.f, 0.f}, DF{0.f, 0.f}, DF{0.f, 0.f}};
-  const float2* pq = part + (size_t)q * part_stride;
-  for (int J = 0; J < nt; ++J) {
-    const int a = min(I, J), c = max(I, J);
-    const float2* p = pq + (size_t)tile_index(a, c, nt) * kBtPart + (J >= I ? 0 : kT * kBS) +
-                      (threadIdx.x >> 2) * kBS + s0;
-    const float4 x = reinterpret_cast<const float4*>(p)[0], y = reinterpret_cast<const float4*>(p)[1];
-    df_add(acc[0], DF{x.x, x.y});
-    df_add(acc[1], DF{x.z, x.w});
-    df_add(acc[2], DF{y.x, y.y});
-    df_add(acc[3], DF{y.z, y.w});
-  }
+bapply_reduce_kernel(const float2* __restrict__ part, int ksplit, int rows_pad, float* const* __restrict__ outq,
+                     int n, int mode, BatchDev b) {
+  const int q = blockIdx.y;
+  const int e = blockIdx.x * 256 + threadIdx.x;
+  const int i = e / kBS, s = e % kBS;
   if (i >= n) return;
-#pragma unroll
-  for (int e = 0; e < 4; ++e) {
-    const int s = s0 + e;
-    const float g = acc[e].hi + acc[e].lo;
-    if (mode == 0) {
-      outq[q][cidx(i, s)] = g;
-    } else {
-      const size_t o = ((size_t)q * b.N + i) * kBS + s;
-      const size_t pp = (size_t)i * kBS + s;
-      const float xo = b.X[o];
-      const float v = xo - b.xbar[pp] + b.zbar[pp] - b.sd[pp];
-      const float xn = fmaf(b.mu, g, v);
-      b.dX[o] = xn - xo;
-      b.X[o] = xn;
-    }
+  DF acc{0.f, 0.f};
+  for (int k = 0; k < ksplit; ++k) {
+    const float2 v = part[(((size_t)q * ksplit + k) * rows_pad + i) * kBS + s];
+    df_add(acc, DF{v.x, v.y});
+  }
+  const float g = acc.hi + acc.lo;
+  if (mode == 0) {
+    outq[q][cidx(i, s)] = g;
+  } else {
+    const size_t o = ((size_t)q * b.N + i) * kBS + s;
+    const size_t pp = (size_t)i * kBS + s;
+    const float xo = b.X[o];
+    const float v = xo - b.xbar[pp] + b.zbar[pp] - b.sd[pp];
+    const float xn = fmaf(b.mu, g, v);
+    b.dX[o] = xn - xo;
+    b.X[o] = xn;
   }
 }
 
@@ -458,12 +423,11 @@ struct BatchCtx {
   sadmm_t single = nullptr;        // owns the operators and the FP64 factors
   std::vector<void*> owned;
   float *X = nullptr, *dX = nullptr, *xbar = nullptr, *zbar = nullptr, *sd = nullptr, *lor = nullptr;
-  float2 **dY = nullptr, **dR = nullptr, **dF = nullptr;
-  std::vector<float2*> fpair;      // packed symmetric factor pairs, one per sensor
+  float2 **dY = nullptr, **dR = nullptr;
+  DigitApply dapp;                 // factor digits and the apply's scratch (bapply_tc.cu)
+  bool dapp_bound = false;
   std::vector<const float2*> hA, hR, hU;   // host copies of the per-sensor device pointers
   std::vector<void*> hY, hG;
-  float2* bpart = nullptr;         // per-tile partial sums of the factor apply
-  size_t bpart_stride = 0;
   int* berr = nullptr;             // set if a factor tile copy timed out
   float **dU = nullptr, **dG = nullptr;
   float2* partial = nullptr;
@@ -507,18 +471,10 @@ int single_export(sadmm_t h, int q, const float2** A, const double** F, int* n, 
 
 namespace {
 
-int launch_bspd(BatchCtx& c, const float* const* u, float* const* out, int mode, const BatchDev& bv) {
-  const int nt = div_up(c.n, kT), items = c.Q * nt * (nt + 1) / 2;
-  const int smem = kBtTileBytes + 2 * kT * kBS * (int)sizeof(float);
-  static bool conf = false;
-  if (!conf) {
-    SADMM_CUDA_TRY(cudaFuncSetAttribute(bspd_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    conf = true;
-  }
-  bspd_tile_kernel<<<std::min(items, 152 * 5), kBtThreads, smem, c.st>>>(
-      (const float2* const*)c.dF, u, c.bpart, c.bpart_stride, c.n, mode, items, c.berr);
-  SADMM_LAUNCH_CHECK();
-  bspd_reduce_kernel<<<dim3(nt, c.Q), 256, 0, c.st>>>(c.bpart, c.bpart_stride, out, c.n, mode, bv);
+int launch_bapply(BatchCtx& c, const float* const* u, float* const* out, int mode, const BatchDev& bv) {
+  SADMM_TRY(launch_digit_apply(c.dapp, u, mode == 0 ? 0 : 1, c.berr, c.st));
+  bapply_reduce_kernel<<<dim3(div_up((long long)c.n * kBS, 256), c.Q), 256, 0, c.st>>>(
+      c.dapp.part, c.dapp.ksplit, c.dapp.rows_pad, out, c.n, mode, bv);
   SADMM_LAUNCH_CHECK();
   return SADMM_OK;
 }
@@ -545,11 +501,11 @@ int batch_launch_iteration(BatchCtx& c) {
   const BatchDev bv = c.view();
   SADMM_TRY(launch_forward_products(c, c.chunks, bv));
   if (c.woodbury) {
-    SADMM_TRY(launch_bspd(c, (const float* const*)c.dR, c.dU, 0, bv));
+    SADMM_TRY(launch_bapply(c, (const float* const*)c.dR, c.dU, 0, bv));
     SADMM_TRY(launch_adjoint_products(c, c.asplits, c.hU.data(), 0, bv));
   } else {
     SADMM_TRY(launch_adjoint_products(c, c.asplits, c.hR.data(), 1, bv));
-    SADMM_TRY(launch_bspd(c, (const float* const*)c.dG, nullptr, 1, bv));
+    SADMM_TRY(launch_bapply(c, (const float* const*)c.dG, nullptr, 1, bv));
   }
   const int nblk = div_up(c.N, kBrThreads / kBS);
   bresid_kernel<<<nblk, kBrThreads, 0, c.st>>>(bv, c.rpart);
@@ -560,32 +516,26 @@ int batch_launch_iteration(BatchCtx& c) {
 }
 
 // Factors for the current operators (FP64, from the single-scene context),
-// packed as double-float pairs; the apply's scratch.  Synchronises b.st.
+// cut into the tensor-core apply's digit planes; the apply's scratch.
+// Synchronises b.st.
 int batch_setup(BatchCtx& b) {
   SADMM_TRY(sadmm_prepare(b.single));
   if (b.ready) return SADMM_OK;
-  std::vector<void*> Fp(b.Q);
-  if (b.fpair.empty()) b.fpair.assign(b.Q, nullptr);
   b.hA.assign(b.Q, nullptr);
   for (int q = 0; q < b.Q; ++q) {
     const float2* A = nullptr;
     const double* F = nullptr;
     SADMM_TRY(single_export(b.single, q, &A, &F, &b.n, &b.ld, &b.woodbury));
-    if (!b.fpair[q]) {
-      b.fpair[q] = (float2*)b.dalloc(sym_packed_pairs(b.n) * sizeof(float2));
-      if (!b.fpair[q]) { set_error("batched form: factor allocation failed"); return SADMM_ENOMEM; }
+    if (!b.dapp_bound) {
+      digit_apply_dims(b.dapp, b.Q, b.n);
+      void* mem = b.dalloc(digit_apply_bytes(b.dapp));
+      if (!mem) { set_error("batched form: factor digit allocation failed"); return SADMM_ENOMEM; }
+      SADMM_TRY(digit_apply_bind(b.dapp, mem));
+      b.dapp_bound = true;
     }
-    SADMM_TRY(launch_pack_sym(F, b.ld, b.n, b.fpair[q], b.st));
-    Fp[q] = (void*)b.fpair[q];
+    SADMM_TRY(launch_factor_digits(b.dapp, q, F, b.ld, b.st));
     b.hA[q] = A;
   }
-  if (!b.bpart) {
-    const size_t nt = div_up(b.n, kT);
-    b.bpart_stride = nt * (nt + 1) / 2 * kBtPart;
-    b.bpart = (float2*)b.dalloc((size_t)b.Q * b.bpart_stride * sizeof(float2));
-    if (!b.bpart) { set_error("batched form: scratch allocation failed"); return SADMM_ENOMEM; }
-  }
-  SADMM_CUDA_TRY(cudaMemcpyAsync(b.dF, Fp.data(), b.Q * sizeof(void*), cudaMemcpyHostToDevice, b.st));
   SADMM_CUDA_TRY(cudaStreamSynchronize(b.st));
   b.ready = true;
   return SADMM_OK;
@@ -663,7 +613,7 @@ int batch_finish(BatchCtx& b, int iters, sadmm_stats* st, double ms) {
     st->r_pri = h.r_pri; st->eps_pri = h.eps_pri; st->d = h.d; st->eps_dual = h.eps_dual;
     st->relchange = h.relchange;
     st->ms_total = ms;
-    st->bytes_iter = (double)iters * ((double)b.Q * b.KM * b.N * 16.0 + (double)b.Q * sym_packed_pairs(b.n) * 8.0);
+    st->bytes_iter = (double)iters * ((double)b.Q * b.KM * b.N * 16.0 + (double)b.Q * b.dapp.rows_pad * b.dapp.kpad * 8.0);
   }
   return SADMM_OK;
 }
@@ -711,7 +661,7 @@ int launch_multi_apply_cols(const float2* const* F, const float2* const* A, cons
   const size_t stride = multi_apply_part_pairs(n);
   bspd_tile_kernel<<<std::min(items, 152 * 5), kBtThreads, smem, st>>>(
       reinterpret_cast<const float2* const*>(dptrs), reinterpret_cast<const float* const*>(dptrs + njobs), part, stride,
-      n, 1, items, err);
+      n, items, err);
   SADMM_LAUNCH_CHECK();
   bspd_reduce_cols_kernel<<<dim3(nt, njobs), 256, 0, st>>>(part, stride, blk, n, c0);
   SADMM_LAUNCH_CHECK();
@@ -765,7 +715,7 @@ int sadmm_batch_create(int Q, int M, int K, int N, int S, double rho, const doub
   b->xbar = (float*)A(NS * 4); b->zbar = (float*)A(NS * 4); b->sd = (float*)A(NS * 4);
   b->lor = (float*)A(kBS * 4);
   b->dY = (float2**)A(Q * sizeof(void*));
-  b->dR = (float2**)A(Q * sizeof(void*)); b->dF = (float2**)A(Q * sizeof(void*));
+  b->dR = (float2**)A(Q * sizeof(void*));
   b->dU = (float**)A(Q * sizeof(void*)); b->dG = (float**)A(Q * sizeof(void*));
   b->chunks = b->chunks0 = tc_forward_splits(Q, N, b->KM);
   b->asplits = b->asplits0 = tc_adjoint_splits(Q, N, b->KM);

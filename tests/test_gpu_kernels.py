@@ -365,3 +365,81 @@ def test_tensor_core_adjoint16_matches_fp64(B, KM, N):
     err = np.abs(G - ref)
     print(f"KM={KM} N={N}: max |G - G64| / bound = {np.max(err / bound):.3f}")
     assert np.all(err <= bound)
+
+
+# ------------------------------------------- batched factor apply (digits)
+def _digit_entries(s, rows, cols, ndig):
+    """Values that are exactly ndig balanced 8-bit digits below 2^7: d_0 +
+    2^-8 d_1 + ..., |d_a| <= 127, and one entry of 100 per row (so that the
+    row scale 2^-e_i is 2^-7 and the digits are the ones drawn)."""
+    D = [s.integers(rows * cols, 255).reshape(rows, cols).astype(np.int64) - 127 for _ in range(ndig)]
+    D[0][np.arange(rows), s.integers(rows, cols)] = 100
+    v = sum(D[a].astype(np.float64) * 2.0 ** (-8 * a) for a in range(ndig))
+    return v, D
+
+
+@pytest.mark.parametrize("n", [1, 200, 1000, 4133])
+def test_digit_apply_is_exact_on_integers(B, n):
+    """Integer F and U with |entries| <= 128: every digit but the first is
+    zero and the chunk sums are exact, so the tensor-core apply equals the
+    integer product exactly (ragged n, several 256-chunks and row blocks)."""
+    s = scenegen.Stream(71, n)
+    F = s.integers(n * n, 257).reshape(n, n).astype(np.float64) - 128
+    U = (s.integers(n * 16, 257).reshape(n, 16) - 128).astype(np.float32)
+    U[:, 5] = 0.0                                     # a zero right-hand side
+    F[n // 2, :] = 0.0                                # a zero row
+    dev = torch.device("cuda:0")
+    out = B.digit_apply16(torch.from_numpy(F).to(dev), torch.from_numpy(U).to(dev)).cpu().numpy()
+    ref = F.astype(np.int64) @ U.astype(np.int64)
+    assert np.array_equal(out, ref.astype(np.float64))
+
+
+@pytest.mark.parametrize("n", [300, 2000])
+def test_digit_apply_keeps_orders_zero_to_three(B, n):
+    """F with four exact digits per entry, U with three: the apply forms the
+    digit products of orders 0..3 exactly (orders 4..6 are dropped by
+    design), so its result equals that truncated sum, computed here in exact
+    integer arithmetic, to the double-float totals' rounding: four additions
+    per 256-chunk, each within 2^-48 of the running total, one or two chunks
+    per work item at these sizes (2^-44 of sum |F||U|)."""
+    s = scenegen.Stream(72, n)
+    F, DF = _digit_entries(s, n, n, 4)
+    Ut, DU = _digit_entries(s, 16, n, 3)               # columns of U as rows
+    U = Ut.T.astype(np.float32)
+    assert np.array_equal(U.astype(np.float64), Ut.T)
+    DU = [d.T for d in DU] + [np.zeros((n, 16), np.int64)]
+    dev = torch.device("cuda:0")
+    out = B.digit_apply16(torch.from_numpy(F).to(dev), torch.from_numpy(U).to(dev)).cpu().numpy()
+    # sum_{a+b<=3} 2^(-8(a+b)) D_a E_b, scaled by 2^24 to integers
+    T = sum((DF[a] @ DU[b]) * (1 << (8 * (3 - a - b))) for a in range(4) for b in range(4) if a + b <= 3)
+    ref = T.astype(np.float64) * 2.0 ** -24
+    full = F @ Ut.T
+    mag = np.abs(F) @ np.abs(Ut.T)
+    assert np.all(np.abs(out - ref) <= 2.0 ** -44 * mag)
+    # and the dropped orders are visible: the exact product differs
+    assert np.max(np.abs(full - ref)) > 2.0 ** -40 * np.max(mag)
+
+
+@pytest.mark.parametrize("n", [129, 3000, 16384])
+def test_digit_apply_matches_fp64(B, n):
+    """General FP64 F (rows scaled over six decades) and FP32 U (columns over
+    four, one zero): within the apply's entrywise bound 5 * 2^-32 * n *
+    2^(e_i + f_s) of the FP64 product (the three slicing and truncation
+    terms), at the batched form's full primal size among others."""
+    s = scenegen.Stream(73, n)
+    w = min(n, 512)                                   # a drawn panel, tiled and rescaled per column
+    F = np.tile(s.normal(n * w).reshape(n, w), (1, -(-n // w)))[:, :n]
+    F *= s.uniform(n, 0.5, 1.5)[None, :] * (10.0 ** s.uniform(n, -3, 3))[:, None]
+    U = (s.normal(n * 16).reshape(n, 16) * (10.0 ** s.uniform(16, -2, 2))[None, :]).astype(np.float32)
+    U[:, 11] = 0.0
+    dev = torch.device("cuda:0")
+    out = B.digit_apply16(torch.from_numpy(F).to(dev), torch.from_numpy(U).to(dev)).cpu().numpy()
+    ref = F @ U.astype(np.float64)
+    ei = np.frexp(np.max(np.abs(F), axis=1))[1].astype(np.float64)
+    fs = np.frexp(np.max(np.abs(U.astype(np.float64)), axis=0))[1].astype(np.float64)
+    bound = 5.0 * 2.0 ** -32 * n * np.exp2(ei[:, None] + fs[None, :])
+    assert np.all(np.abs(out - ref) <= bound)
+    assert np.all(out[:, 11] == 0.0)
+    # typical error far inside the bound (random rounding, not a lost order)
+    scale = np.exp2(ei[:, None] + fs[None, :]) * np.sqrt(n)
+    assert np.sqrt(np.mean(((out - ref) / scale) ** 2)) <= 2.0 ** -30
