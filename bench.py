@@ -57,6 +57,9 @@ def parse():
                     help="skip the learned-step cost measurement (elim 2 on the bench scene)")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the 16-scene batched measurement (Q=8, KM=2048, N=96x96)")
+    ap.add_argument("--batched-config", default="paper_96", choices=["paper_96", "resolved_128"],
+                    help="geometry of the batched measurement: Q=8, KM=2048, N=96x96 (default) or the "
+                         "well-posed resolved_128 (Q=8, KM=16384, N=128x128, its stored measurements)")
     ap.add_argument("--no-accuracy", action="store_true",
                     help="skip the time-to-accuracy measurements on the well-posed workloads "
                          "(Q=8, N=128x128 and Q=4, N=32x32)")
@@ -184,6 +187,60 @@ def cpu_baseline_sample(scene, lam, iters=4):
     }
 
 
+def _factor_order(g):
+    """Order of the x-update factor: 2KM (Woodbury) when N > 2KM, else N (primal)."""
+    return 2 * g.KM if g.N > 2 * g.KM else g.N
+
+
+def batched_measure_128(args, dev, stream):
+    """16 scenes of the resolved_128 geometry (Q=8, KM=16384, N=128x128; the
+    stored measurements of tests/golden/resolved_128_limit.npz, one copy per
+    scene), iterated together: scene-iterations per second and the bytes one
+    iteration streams (both operator GEMMs and the factor digits)."""
+    import torch
+    import scenegen
+    from paper_2307_08606_gb300 import binding
+    g = scenegen.GEOMS["resolved_128"]
+    with open(os.path.join(ROOT, "tests", "golden", "resolved_128_limit.json")) as f:
+        meta = json.load(f)
+    d = np.load(os.path.join(ROOT, "tests", "golden", "resolved_128_limit.npz"))
+    A = device_operators(g, dev)
+    bs = binding.BatchSolver(g.Q, g.M, g.K, g.N, meta["rho"], [meta["lam"]] * 16, stream=stream.cuda_stream)
+    for q in range(g.Q):
+        bs.set_operator(q, A[q])
+    del A
+    torch.cuda.empty_cache()
+    Y = torch.stack([torch.from_numpy(np.ascontiguousarray(d["y"])).to(dev)] * 16)
+    t0 = time.perf_counter()
+    bs.solve(Y, 1)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    iters, reps = args.iters if args.iters < 100 else 20, 3
+    bs.solve(Y, iters)
+    torch.cuda.synchronize()
+    n0 = binding.launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        bs.solve(Y, iters)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    launches = binding.launch_count() - n0
+    bs.close()
+    n = _factor_order(g)
+    op_bytes = 2.0 * g.Q * g.KM * g.N * 8.0
+    f_bytes = 8.0 * g.Q * n * n
+    it_ms = ms / (iters * reps)
+    return {"metric": "batched scene-iterations/s", "value": 16 * iters * reps / (ms / 1e3), "unit": "scene-iter/s",
+            "workload": "16 scenes of resolved_128 (Q=8, M=256, K=64: KM=16384, N=128x128, primal factor "
+                        f"n={n}); plain SADMM, {iters} iterations per solve",
+            "ms_per_iteration": it_ms, "operator_bytes_per_iteration": op_bytes,
+            "factor_digit_bytes_per_iteration": f_bytes,
+            "iteration_GBps": (op_bytes + f_bytes) / (it_ms / 1e3) / 1e9,
+            "setup_s_with_factor": round(setup_s, 2), "gpu_launches": int(launches)}
+
+
 def batched_measure(args, dev, stream, rank):
     """16 scenes sharing one geometry (Q=8, M=8, K=256, N=96x96), iterated together;
     scene-iterations per second and the operator-GEMM roofline."""
@@ -191,6 +248,8 @@ def batched_measure(args, dev, stream, rank):
     import scenegen
     from scenegen import radar
     from paper_2307_08606_gb300 import binding
+    if args.batched_config == "resolved_128":
+        return batched_measure_128(args, dev, stream)
     g = scenegen.Geometry(Q=8, M=8, K=256, nx=96, cell=0.05, radius=10.0, fc=77e9, bw=1e9)
     A = [radar.operator(g, q) for q in range(g.Q)]
     At = [torch.from_numpy(a).to(dev) for a in A]
@@ -235,10 +294,15 @@ def batched_measure(args, dev, stream, rank):
     single_its = iters / (time.perf_counter() - t0)
     one.close()
     op_bytes = 2.0 * g.Q * g.KM * g.N * 8.0            # forward + adjoint, read once for 16 scenes
+    n = _factor_order(g)
+    f_bytes = 8.0 * g.Q * n * n                         # the factor's four BF16 digits per entry
+    it_ms = ms / (iters * reps)
     return {"metric": "batched scene-iterations/s", "value": scene_its, "unit": "scene-iter/s",
             "workload": "16 scenes sharing Q=8 M=8 K=256 (KM=2048) N=96x96; plain SADMM, 100 iterations per solve",
-            "ms_per_iteration": ms / (iters * reps), "operator_bytes_per_iteration": op_bytes,
-            "operator_GBps_effective": op_bytes / (ms / (iters * reps) / 1e3) / 1e9,
+            "ms_per_iteration": it_ms, "operator_bytes_per_iteration": op_bytes,
+            "operator_GBps_effective": op_bytes / (it_ms / 1e3) / 1e9,
+            "factor_digit_bytes_per_iteration": f_bytes,
+            "iteration_GBps": (op_bytes + f_bytes) / (it_ms / 1e3) / 1e9,
             "single_scene_iters_per_s_same_geometry": single_its,
             "speedup_vs_single_scene": scene_its / single_its,
             "gpu_launches": int(launches)}
@@ -510,7 +574,8 @@ def accuracy_measure(dev, stream):
         e1.record(stream)
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / 3
-        out["batched_16"] = {"iterations": k, "ms": ms, "ms_per_scene": ms / 16, "worst_scene_rel_error": e,
+        out["batched_16"] = {"iterations": k, "ms": ms, "ms_per_scene": ms / 16, "ms_per_iteration": ms / k,
+                             "worst_scene_rel_error": e,
                              "scenes": "16 copies of the scene (each checked against the stored limit)"}
     else:
         out["batched_16"] = {"iterations": None, "rel_error_at_8192": e}

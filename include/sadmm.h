@@ -554,6 +554,16 @@ int sadmm_set_wait_limit(long long polls);
  * SADMM_ETIMEOUT if a tensor-core wait timed out. */
 int sadmm_adjoint16_tc(const float* A, int KM, int N, const float* W, float* G, void* stream);
 
+/* The batched form's forward product on the tensor cores (Eq. 3, x_q-update:
+ * the B v of r = y' - B v for 16 right-hand sides): R[m][s] = sum_p
+ * A[p][m] V[p][s] (complex A, real V), m < KM, s < 16.  A: device,
+ * pixel-major complex64 (N x KM); V: device, N x 16 FP32 [pixel][s]; R:
+ * device, KM x 16 complex64 [m][s].  3xTF32 products (each within 2^-21 of
+ * the FP32 one) accumulated in FP32 over the N pixels.  2KM must be a
+ * multiple of 16.  Synchronises `stream`; SADMM_EINVAL for bad arguments,
+ * SADMM_ETIMEOUT if a bounded device wait gave up. */
+int sadmm_forward16_tc(const float* A, int KM, int N, const float* V, float* R, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -108,6 +108,7 @@ _SIGS = {
                              _P]),
     "sadmm_factor_downdate": (C.c_int, [_P, C.c_int, _P, C.c_int, C.c_double, _P, _P]),
     "sadmm_factor_update": (C.c_int, [_P, C.c_int, _P, C.c_int, C.c_double, C.c_int, _P, _P]),
+    "sadmm_forward16_tc": (C.c_int, [_P, C.c_int, C.c_int, _P, _P, _P]),
     "sadmm_adjoint16_tc": (C.c_int, [_P, C.c_int, C.c_int, _P, _P, _P]),
     "sadmm_batch_create": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double,
                                      C.POINTER(C.c_double), C.POINTER(Criterion), C.POINTER(_P)]),
@@ -726,3 +727,16 @@ def digit_apply16(F, U, stream=0):
     out = torch.empty((n, 16), dtype=torch.float64, device=U.device)
     check(load().sadmm_digit_apply16(_ptr(F), int(F.shape[1]), n, _ptr(U), _ptr(out), C.c_void_p(stream)))
     return out
+
+
+def forward16_tc(A, V, stream=0):
+    """R = A^T V (KM x 16 complex64) for the pixel-major complex64 operator A
+    (N x KM) and 16 real right-hand sides V (N x 16 float32), device tensors:
+    the batched forward product on the tensor cores (3xTF32)."""
+    import torch
+    N, KM = A.shape
+    if V.shape != (N, 16) or V.dtype != torch.float32 or A.dtype != torch.complex64:
+        raise ValueError("forward16_tc: A complex64 (N x KM), V float32 (N x 16)")
+    R = torch.empty((KM, 16), dtype=torch.complex64, device=A.device)
+    check(load().sadmm_forward16_tc(_ptr(A.contiguous()), KM, N, _ptr(V.contiguous()), _ptr(R), C.c_void_p(stream)))
+    return R

@@ -6,21 +6,28 @@
 // [row][scene], real row r = 2m + c at float (m * 16 + s) * 2 + c).
 //
 // Precision: three TF32 products per term (3xTF32).  Each operand is split
-// x = hi + lo with hi = tf32(x) (round to nearest) and lo = x - hi (exact in
-// FP32; the MMA keeps its top 11 bits); hi*hi, hi*lo and lo*hi accumulate in
-// FP32 in three tensor-memory accumulators, added as hi*hi + (hi*lo + lo*hi)
-// at the end: each product is within 2^-21 of the FP32 one, the dropped lo*lo
-// term is below 2^-22, and the sums over K round as FP32 accumulations do.
+// x = hi + lo, lo = x - hi exact in FP32 (the MMA keeps its top 11 bits): the
+// right-hand sides with hi = tf32(x) rounded to nearest, the operator tile
+// with hi = x itself (the MMA reads the top 19 bits of an FP32 value, its
+// truncation to TF32) and lo = x - trunc(x).  hi*hi, hi*lo and lo*hi
+// accumulate in FP32 in tensor memory, added as hi*hi + (hi*lo + lo*hi) at the
+// end: each product is within 2^-21 of the FP32 one, the dropped lo*lo term is
+// below 2^-21, and the sums over K round as FP32 accumulations do.
 //
 // Tile: M = 128 pixels (TMEM lanes), N = 16 scenes (TMEM columns), K slabs of
 // 32 real rows.  A slab of A arrives by TMA (tensor map over the pixel-major
 // operand, 128-byte swizzle: exactly the SW128 K-major operand layout of the
-// MMA); W's slab (2 KB) by a bulk copy.  The tile is split in place into its
-// TF32 hi part plus a lo tile of the same layout; W goes to hi/lo tiles in the
-// no-swizzle K-major layout (core matrices of 8 rows x 16 bytes, K-adjacent
-// cores LBO bytes apart, N-adjacent cores SBO bytes apart).  One thread issues
-// 4 k-steps x 3 products of tcgen05.mma kind::tf32 (M128 N16 K8) per slab; the
-// accumulator is read back with tcgen05.ld (32 lanes x 16 columns per warp).
+// MMA); W's slab (2 KB) by a bulk copy.  The landed tile is the hi operand
+// and a lo tile of the same layout is formed beside it; W goes to one 32-row
+// B tile (hi rows 0-15, lo rows 16-31) in the no-swizzle K-major layout (core
+// matrices of 8 rows x 16 bytes, K-adjacent cores LBO bytes apart, N-adjacent
+// cores SBO bytes apart).  One thread issues, per k-step of 8, an N = 32 MMA
+// (A hi against the whole B tile: hi*hi and hi*lo from one read of A) and an
+// N = 16 MMA (A lo against the hi rows), tcgen05.mma kind::tf32 (M128 K8);
+// the accumulators are read back with tcgen05.ld (32 lanes x 16 columns per
+// warp).  A variant with separate rings for the landed tiles and the
+// converted operands (more slabs in flight, one more hand-off per slab) ran
+// slower on GB300 (adjoint 4.3 ms against 3.2 ms at Q=8, KM=16384, N=128^2).
 // The pipeline structure is described at tc_adjoint_kernel.  Every wait is
 // bounded; on a timeout the CTA flags *err, waits (bounded) for its copies in
 // flight, frees its tensor memory and exits.
@@ -36,17 +43,27 @@ namespace {
 constexpr int kTcM = 128;              // pixels per CTA
 constexpr int kTcN = 16;               // scenes
 constexpr int kTcK = 32;               // real rows per slab
-constexpr int kTmemCols = 128;         // 2 accumulator sets x 3 products x kTcN columns, power of two
-constexpr int kAccSet = 3 * kTcN;      // one accumulator per product (hi*hi, hi*lo, lo*hi)
+constexpr int kTmemCols = 128;         // 2 accumulator sets, power of two
+// one set: hi x [hi; lo] (an N = 32 accumulator: hi*hi in columns 0-15, hi*lo
+// in 16-31) and lo x hi (columns 32-47); sets 64 columns apart
+constexpr int kAccSet = 64;
 constexpr long long kTcWaitLimit = 1ll << 26;
 
 // operand tile bytes per plane and buffer
 constexpr int kABytes = kTcM * kTcK * 4;          // 16 KB
-constexpr int kBBytes = kTcN * kTcK * 4;          // 2 KB
+constexpr int kBBytes = kTcN * kTcK * 4;          // 2 KB: one 16-row plane
+// The B operand tile holds 32 rows: the TF32 hi parts of the 16 right-hand
+// sides (rows 0-15), then their lo parts (rows 16-31), so that one N = 32 MMA
+// forms hi*hi and hi*lo from a single read of the A tile.
 // canonical K-major layout strides (bytes)
 constexpr int kCore = 128;                         // 8 rows x 16 bytes
-constexpr int kB_SBO = kCore;                      // next 8 scenes
-constexpr int kB_LBO = (kTcN / 8) * kCore;         // next 4 k-elements (256)
+constexpr int kB_SBO = kCore;                      // next 8 rows
+constexpr int kB_LBO = (2 * kTcN / 8) * kCore;     // next 4 k-elements (512)
+
+// byte offset of (row n, k) in the B tile
+__host__ __device__ constexpr int b_off(int n, int k) {
+  return (k >> 2) * kB_LBO + (n >> 3) * kB_SBO + (n & 7) * 16 + (k & 3) * 4;
+}
 
 __device__ __forceinline__ unsigned su32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 
@@ -59,16 +76,24 @@ __device__ __forceinline__ uint64_t smem_desc(unsigned addr, int lbo, int sbo) {
   return d;                            // base offset 0, no swizzle
 }
 
-// kind::tf32, D = F32, A = B = TF32, both K-major, N = 16, M = 128
-constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kTcN >> 3) << 17) |
-                            ((uint32_t)(kTcM >> 4) << 24);
+// kind::tf32, D = F32, A = B = TF32, both K-major, M = 128, N = 16 or 32
+constexpr uint32_t idesc_tf32(int n) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kTcM >> 4) << 24);
+}
+constexpr uint32_t kIdesc16 = idesc_tf32(kTcN), kIdesc32 = idesc_tf32(2 * kTcN);
 
-__device__ __forceinline__ void mma_tf32(unsigned tmem, uint64_t a, uint64_t b, unsigned acc) {
+__device__ __forceinline__ void mma_tf32(unsigned tmem, uint64_t a, uint64_t b, uint32_t idesc, unsigned acc) {
   asm volatile(
       "{ .reg .pred p; setp.ne.b32 p, %4, 0;\n"
       "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p; }" ::"r"(tmem),
-      "l"(a), "l"(b), "r"(kIdesc), "r"(acc)
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
       : "memory");
+}
+
+// hi*[hi; lo] and lo*hi for one k-step of 8: two MMAs into one accumulator set
+__device__ __forceinline__ void mma_3xtf32(unsigned d, uint64_t a_hi, uint64_t a_lo, uint64_t b, unsigned acc) {
+  mma_tf32(d, a_hi, b, kIdesc32, acc);
+  mma_tf32(d + 2 * kTcN, a_lo, b, kIdesc16, acc);     // the first 16 rows of the B tile: hi
 }
 
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
@@ -119,6 +144,9 @@ __device__ __forceinline__ float tf32_rn(float x) {
   return __uint_as_float(r);
 }
 
+// x with its low 13 mantissa bits cleared (truncation to TF32)
+__device__ __forceinline__ float tf32_tz(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
+
 struct TmapSet {
   CUtensorMap m[kMaxSets];     // A_q as a 2-D FP32 tensor: x = real row (2KM), y = pixel (N)
 };
@@ -140,18 +168,18 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
 // tile, row split), kS shared-memory stages deep:
 //   warp 0      producer: per slab one TMA tile load of A (128 pixels x 32
 //               real rows, 128-byte swizzle) and one bulk copy of the W slab;
-//   warp 1      MMA issuer: 4 k-steps x 3 tcgen05.mma per slab into one of two
+//   warp 1      MMA issuer: 4 k-steps x 2 tcgen05.mma per slab into one of two
 //               TMEM accumulators (alternating per item), commits free the
 //               stage and, at the end of an item, publish the accumulator;
-//   warps 2-5   converters: split the landed A tile in place into its TF32 hi
-//               part plus a lo tile (same swizzled layout) and W into hi/lo
-//               operand tiles; after an item, read its accumulator (each warp
+//   warps 2-5   converters: form the lo tile of the landed A tile (same
+//               swizzled layout; the tile itself is the hi operand) and the B
+//               tile from W; after an item, read its accumulator (each warp
 //               its 32-lane quarter of TMEM) and store the 128 x 16 result.
 // Barriers: full (TMA landed), conv (operands ready), empty (stage free),
 // accfull / accempty (accumulator handoff).  All waits are bounded.
 constexpr int kS = 5;
 constexpr int kPipeThreads = 192;
-constexpr int kStageBytes = 2 * kABytes + 3 * kBBytes;        // A hi, A lo, B hi, B lo, W raw
+constexpr int kStageBytes = 2 * kABytes + 3 * kBBytes;        // A (raw = hi), A lo, B (hi; lo), W raw
 constexpr int kPipeSmem = kS * kStageBytes + 1024;            // + alignment slack
 
 // SW128 K-major descriptor: 8-row atoms of 128-byte rows, atoms 1024 bytes apart
@@ -258,16 +286,12 @@ tc_adjoint_kernel(const __grid_constant__ TmapSet tmaps, const __grid_constant__
           if (!ok) break;
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           const unsigned st = su32(smem + s * kStageBytes);
-          const unsigned a_hi = st, a_lo = st + kABytes, b_hi = st + 2 * kABytes, b_lo = b_hi + kBBytes;
+          const unsigned a_hi = st, a_lo = st + kABytes, b = st + 2 * kABytes;
 #pragma unroll
           for (int ks = 0; ks < kTcK / 8; ++ks) {
             const unsigned acc0 = (sl > 0 || ks > 0) ? 1u : 0u;
-            const uint64_t dah = sw128_desc(a_hi + ks * 32), dal = sw128_desc(a_lo + ks * 32);
-            const uint64_t dbh = smem_desc(b_hi + ks * 2 * kB_LBO, kB_LBO, kB_SBO);
-            const uint64_t dbl = smem_desc(b_lo + ks * 2 * kB_LBO, kB_LBO, kB_SBO);
-            mma_tf32(d, dah, dbh, acc0);
-            mma_tf32(d + kTcN, dah, dbl, acc0);
-            mma_tf32(d + 2 * kTcN, dal, dbh, acc0);
+            mma_3xtf32(d, sw128_desc(a_hi + ks * 32), sw128_desc(a_lo + ks * 32),
+                       smem_desc(b + ks * 2 * kB_LBO, kB_LBO, kB_SBO), acc0);
           }
           mma_commit(&empty[s]);
         }
@@ -298,28 +322,27 @@ tc_adjoint_kernel(const __grid_constant__ TmapSet tmaps, const __grid_constant__
         ok = bar_wait(&full[s], (t / kS) & 1);
         if (!ok) break;
         unsigned char* st = smem + s * kStageBytes;
-        float4* ahi = reinterpret_cast<float4*>(st);
+        // the landed tile stays in place as the hi operand (the MMA reads the
+        // top 19 bits of each FP32 value: its truncation to TF32); the lo tile
+        // is the exact remainder
+        const float4* ahi = reinterpret_cast<const float4*>(st);
         float4* alo = reinterpret_cast<float4*>(st + kABytes);
 #pragma unroll
-        for (int c = 0; c < kABytes / 16 / 128; ++c) {
-          const int e = ct + 128 * c;
+        for (int w = 0; w < kABytes / 16 / 128; ++w) {
+          const int e = ct + 128 * w;
           const float4 x = ahi[e];
-          const float4 h = make_float4(tf32_rn(x.x), tf32_rn(x.y), tf32_rn(x.z), tf32_rn(x.w));
-          ahi[e] = h;
-          alo[e] = make_float4(x.x - h.x, x.y - h.y, x.z - h.z, x.w - h.w);
+          alo[e] = make_float4(x.x - tf32_tz(x.x), x.y - tf32_tz(x.y), x.z - tf32_tz(x.z), x.w - tf32_tz(x.w));
         }
-        float* bhi = reinterpret_cast<float*>(st + 2 * kABytes);
-        float* blo = bhi + kBBytes / 4;
+        float* bt = reinterpret_cast<float*>(st + 2 * kABytes);
         const float4 rw = reinterpret_cast<const float4*>(st + 2 * kABytes + 2 * kBBytes)[ct];
         const int wm = ct >> 3, ws = 2 * (ct & 7);
         const float v[4] = {rw.x, rw.y, rw.z, rw.w};       // (ws re, ws im, ws+1 re, ws+1 im)
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           const int sc = ws + (u >> 1), k = 2 * wm + (u & 1);
-          const int off = ((k >> 2) * kB_LBO + (sc >> 3) * kB_SBO + (sc & 7) * 16 + (k & 3) * 4) / 4;
           const float h = tf32_rn(v[u]);
-          bhi[off] = h;
-          blo[off] = v[u] - h;
+          bt[b_off(sc, k) / 4] = h;
+          bt[b_off(kTcN + sc, k) / 4] = v[u] - h;
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_arrive(&conv[s]);
@@ -359,16 +382,17 @@ tc_adjoint_kernel(const __grid_constant__ TmapSet tmaps, const __grid_constant__
 // persistent CTAs.  The operator tile arrives by TMA as [32 pixels][128 rows]
 // (rows contiguous, no swizzle) and the four 2 KB slabs of x, x_bar, z_bar, s
 // by bulk copies; converter warps transpose the tile into the SW128 K-major
-// layout while splitting it into TF32 hi and lo tiles (row m, pixel quad kq
+// layout as the hi tile (the values themselves, truncated to TF32 by the MMA)
+// and the lo tile of exact remainders (row m, pixel quad kq
 // lands in 16-byte chunk kq ^ (m mod 8) of its 128-byte row: conflict-free),
-// form V and split it into the no-swizzle B tiles.  The MMA issuer and the
+// form V and split it into the 32-row B tile.  The MMA issuer and the
 // epilogue are as in tc_adjoint_kernel; the epilogue writes partial sums in
 // the layout of the SIMT forward (partial[q][split][complex row][scene] as
 // float2), which bfwd_reduce_kernel turns into r = y' - sum.
 constexpr int kFwdS = 3;
 constexpr int kFwdRaw = kTcM * kTcK * 4;                       // [32 pixels][128 rows] floats, 16 KB
 constexpr int kVBytes = kTcK * kTcN * 4;                        // one [32 pixels][16 scenes] slab, 2 KB
-constexpr int kFwdStage = kFwdRaw + 2 * kABytes + 2 * kBBytes + 4 * kVBytes;   // 60 KB
+constexpr int kFwdStage = kFwdRaw + 2 * kABytes + 2 * kBBytes + 4 * kVBytes;   // 60 KB: raw, A hi, A lo, B, V
 constexpr int kFwdSmem = kFwdS * kFwdStage + 1024;
 
 struct VSet {
@@ -424,8 +448,7 @@ tc_forward_kernel(const __grid_constant__ TmapSet tmaps, const __grid_constant__
   bool ok = true;
   // stage layout: raw A | A hi | A lo | B hi | B lo | x | x_bar | z_bar | s
   auto stage = [&](int s) { return smem + s * kFwdStage; };
-  constexpr int oAhi = kFwdRaw, oAlo = kFwdRaw + kABytes, oBhi = kFwdRaw + 2 * kABytes, oBlo = oBhi + kBBytes,
-                oV = oBlo + kBBytes;
+  constexpr int oAhi = kFwdRaw, oAlo = kFwdRaw + kABytes, oB = kFwdRaw + 2 * kABytes, oV = oB + 2 * kBBytes;
 
   if (warp == 0) {
     if (lane == 0) {
@@ -478,16 +501,12 @@ tc_forward_kernel(const __grid_constant__ TmapSet tmaps, const __grid_constant__
           if (!ok) break;
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           const unsigned st = su32(stage(s));
-          const unsigned a_hi = st + oAhi, a_lo = st + oAlo, b_hi = st + oBhi, b_lo = st + oBlo;
+          const unsigned a_hi = st + oAhi, a_lo = st + oAlo, b = st + oB;
 #pragma unroll
           for (int ks = 0; ks < kTcK / 8; ++ks) {
             const unsigned acc0 = (sl > 0 || ks > 0) ? 1u : 0u;
-            const uint64_t dah = sw128_desc(a_hi + ks * 32), dal = sw128_desc(a_lo + ks * 32);
-            const uint64_t dbh = smem_desc(b_hi + ks * 2 * kB_LBO, kB_LBO, kB_SBO);
-            const uint64_t dbl = smem_desc(b_lo + ks * 2 * kB_LBO, kB_LBO, kB_SBO);
-            mma_tf32(d, dah, dbh, acc0);
-            mma_tf32(d + kTcN, dah, dbl, acc0);
-            mma_tf32(d + 2 * kTcN, dal, dbh, acc0);
+            mma_3xtf32(d, sw128_desc(a_hi + ks * 32), sw128_desc(a_lo + ks * 32),
+                       smem_desc(b + ks * 2 * kB_LBO, kB_LBO, kB_SBO), acc0);
           }
           mma_commit(&empty[s]);
         }
@@ -523,8 +542,10 @@ tc_forward_kernel(const __grid_constant__ TmapSet tmaps, const __grid_constant__
           float x[4];
 #pragma unroll
           for (int j = 0; j < 4; ++j) x[j] = raw[(4 * kq + j) * kTcM + m];   // zero-filled beyond N by TMA
-          const float4 h = make_float4(tf32_rn(x[0]), tf32_rn(x[1]), tf32_rn(x[2]), tf32_rn(x[3]));
-          const float4 l = make_float4(x[0] - h.x, x[1] - h.y, x[2] - h.z, x[3] - h.w);
+          // hi = x itself (the MMA truncates it to TF32), lo = the exact remainder
+          const float4 h = make_float4(x[0], x[1], x[2], x[3]);
+          const float4 l = make_float4(x[0] - tf32_tz(x[0]), x[1] - tf32_tz(x[1]), x[2] - tf32_tz(x[2]),
+                                       x[3] - tf32_tz(x[3]));
           const int off = (m >> 3) * 1024 + (m & 7) * 128 + ((kq ^ (m & 7)) << 4);
           *reinterpret_cast<float4*>(st + oAhi + off) = h;
           *reinterpret_cast<float4*>(st + oAlo + off) = l;
@@ -543,15 +564,13 @@ tc_forward_kernel(const __grid_constant__ TmapSet tmaps, const __grid_constant__
             v[2] = xx.z - xb.z + zb.z - sdv.z;
             v[3] = xx.w - xb.w + zb.w - sdv.w;
           }
-          float* bhi = reinterpret_cast<float*>(st + oBhi);
-          float* blo = reinterpret_cast<float*>(st + oBlo);
+          float* bt = reinterpret_cast<float*>(st + oB);
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
             const int n = n0 + u;
-            const int off = ((k >> 2) * kB_LBO + (n >> 3) * kB_SBO + (n & 7) * 16 + (k & 3) * 4) / 4;
             const float h = tf32_rn(v[u]);
-            bhi[off] = h;
-            blo[off] = v[u] - h;
+            bt[b_off(n, k) / 4] = h;
+            bt[b_off(kTcN + n, k) / 4] = v[u] - h;
           }
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -707,5 +726,33 @@ extern "C" int sadmm_adjoint16_tc(const float* A, int KM, int N, const float* W,
   cudaFreeAsync(err, st);
   if (rc != SADMM_OK) return rc;
   if (herr) { set_error("sadmm_adjoint16_tc: a tensor-core pipeline wait timed out"); return SADMM_ETIMEOUT; }
+  return SADMM_OK;
+}
+
+extern "C" int sadmm_forward16_tc(const float* A, int KM, int N, const float* V, float* R, void* stream) {
+  using namespace sadmm;
+  if (!A || !V || !R || KM <= 0 || (2 * KM) % 16 != 0 || N <= 0) {
+    set_error("sadmm_forward16_tc: bad arguments");
+    return SADMM_EINVAL;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  // V = x - x_bar + z_bar - s with x = V and the other three zero
+  const size_t vbytes = (size_t)N * kTcN * sizeof(float);
+  char* buf = nullptr;
+  SADMM_CUDA_TRY(cudaMallocAsync((void**)&buf, vbytes + 16, st));
+  int* err = reinterpret_cast<int*>(buf + vbytes);
+  const float* zero = reinterpret_cast<const float*>(buf);
+  int rc = (cudaMemsetAsync(buf, 0, vbytes + 16, st) == cudaSuccess) ? SADMM_OK : SADMM_ECUDA;
+  const float2* a = reinterpret_cast<const float2*>(A);
+  if (rc == SADMM_OK)
+    rc = launch_tc_forward(&a, V, zero, zero, zero, reinterpret_cast<float2*>(R), 1, N, KM, 1, err, st);
+  int herr = 0;
+  if (rc == SADMM_OK) {
+    SADMM_CUDA_TRY(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    SADMM_CUDA_TRY(cudaStreamSynchronize(st));
+  }
+  cudaFreeAsync(buf, st);
+  if (rc != SADMM_OK) return rc;
+  if (herr) { set_error("sadmm_forward16_tc: a tensor-core pipeline wait timed out"); return SADMM_ETIMEOUT; }
   return SADMM_OK;
 }

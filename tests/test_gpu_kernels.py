@@ -347,7 +347,7 @@ def test_factor_rank_update_adds_columns(B, KM, N, e):
     assert np.array_equal(Wu, Wu.T)
 
 
-@pytest.mark.parametrize("KM,N", [(16, 128), (32, 200), (256, 1024), (2048, 300)])
+@pytest.mark.parametrize("KM,N", [(16, 128), (32, 200), (256, 1024), (2048, 300), (4096, 8192)])
 def test_tensor_core_adjoint16_matches_fp64(B, KM, N):
     """Batched adjoint on tcgen05 (3xTF32 split, FP32 accumulation) against the
     FP64 product: each of the 2KM terms is within 2^-21 of its exact value and
@@ -365,6 +365,30 @@ def test_tensor_core_adjoint16_matches_fp64(B, KM, N):
     err = np.abs(G - ref)
     print(f"KM={KM} N={N}: max |G - G64| / bound = {np.max(err / bound):.3f}")
     assert np.all(err <= bound)
+
+
+@pytest.mark.parametrize("KM,N", [(8, 100), (72, 200), (256, 1024), (2048, 9216), (4096, 8192)])
+def test_tensor_core_forward16_matches_fp64(B, KM, N):
+    """Batched forward on tcgen05 (transposing 3xTF32 split, FP32
+    accumulation over the N pixels) against the FP64 product A^T V: each term
+    within 2^-21 of its exact value and at most N FP32 roundings (or
+    truncations, 2^-23) of the running magnitude, so |R - R64| <= (N 2^-23 +
+    2^-20) sum |a||v| per real and imaginary part (ragged N and 2KM/128)."""
+    A = _operator(KM, N, seed=7 * KM + N, radar=(KM == 256))
+    s = scenegen.Stream(37, N)
+    V = s.normal(N * 16).reshape(N, 16).astype(np.float32)
+    V[:, 3] = 0.0
+    dev = torch.device("cuda:0")
+    R = B.forward16_tc(torch.from_numpy(A).to(dev), torch.from_numpy(V).to(dev)).cpu().numpy().astype(np.complex128)
+    A64, V64 = A.astype(np.complex128), V.astype(np.float64)
+    ref = A64.T @ V64
+    for part in (np.real, np.imag):
+        mag = np.abs(part(A64)).T @ np.abs(V64)
+        bound = (N * 2.0 ** -23 + 2.0 ** -20) * mag
+        err = np.abs(part(R) - part(ref))
+        print(f"KM={KM} N={N}: max |R - R64| / bound = {np.max(err / np.maximum(bound, 1e-300)):.3f}")
+        assert np.all(err <= bound)
+    assert np.all(R[:, 3] == 0)
 
 
 # ------------------------------------------- batched factor apply (digits)
