@@ -108,11 +108,20 @@ __host__ __device__ __forceinline__ int ntiles_side(int n) { return (n + kT - 1)
 
 __host__ __device__ __forceinline__ int tile_index(int I, int J, int nt) { return I * nt - I * (I - 1) / 2 + (J - I); }
 
-// tile number t of an nt x nt upper triangle -> (I, J)
+// tile number t of an nt x nt upper triangle -> (I, J).  Row block I starts
+// at tile I nt - I (I - 1) / 2; I is the largest with that start <= t, the
+// smaller root of I^2 - (2 nt + 1) I + 2 t = 0 rounded down (an FP32 estimate,
+// then corrected exactly in integers).
+__device__ __forceinline__ int tile_row_start(int I, int nt) { return I * nt - I * (I - 1) / 2; }
+
 __device__ __forceinline__ void tile_ij(int t, int nt, int& I, int& J) {
-  I = 0;
-  while (t >= nt - I) { t -= nt - I; ++I; }
-  J = I + t;
+  const float b = 2.f * (float)nt + 1.f;
+  int i = (int)((b - sqrtf(fmaxf(b * b - 8.f * (float)t, 0.f))) * 0.5f);
+  i = max(0, min(i, nt - 1));
+  while (i > 0 && tile_row_start(i, nt) > t) --i;
+  while (i + 1 < nt && tile_row_start(i + 1, nt) <= t) ++i;
+  I = i;
+  J = i + (t - tile_row_start(i, nt));
 }
 
 

@@ -334,15 +334,19 @@ tc_adjoint_kernel(const __grid_constant__ TmapSet tmaps, const __grid_constant__
           alo[e] = make_float4(x.x - tf32_tz(x.x), x.y - tf32_tz(x.y), x.z - tf32_tz(x.z), x.w - tf32_tz(x.w));
         }
         float* bt = reinterpret_cast<float*>(st + 2 * kABytes);
-        const float4 rw = reinterpret_cast<const float4*>(st + 2 * kABytes + 2 * kBBytes)[ct];
-        const int wm = ct >> 3, ws = 2 * (ct & 7);
-        const float v[4] = {rw.x, rw.y, rw.z, rw.w};       // (ws re, ws im, ws+1 re, ws+1 im)
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int sc = ws + (u >> 1), k = 2 * wm + (u & 1);
-          const float h = tf32_rn(v[u]);
-          bt[b_off(sc, k) / 4] = h;
-          bt[b_off(kTcN + sc, k) / 4] = v[u] - h;
+        {
+          // scene n = ct % 16, real rows 4j .. 4j + 3 (complex rows 2j, 2j + 1)
+          // with j = ct / 16: one 16-byte chunk of the hi rows and one of the
+          // lo rows per thread (a quarter-warp covers eight scenes: the eight
+          // chunk positions of a 128-byte line, no bank conflict)
+          const float* wr = reinterpret_cast<const float*>(st + 2 * kABytes + 2 * kBBytes);
+          const int n = ct & 15, j = ct >> 4;
+          const float2 w0 = *reinterpret_cast<const float2*>(wr + ((2 * j) * kTcN + n) * 2);
+          const float2 w1 = *reinterpret_cast<const float2*>(wr + ((2 * j + 1) * kTcN + n) * 2);
+          const float4 h = make_float4(tf32_rn(w0.x), tf32_rn(w0.y), tf32_rn(w1.x), tf32_rn(w1.y));
+          *reinterpret_cast<float4*>(bt + b_off(n, 4 * j) / 4) = h;
+          *reinterpret_cast<float4*>(bt + b_off(kTcN + n, 4 * j) / 4) =
+              make_float4(w0.x - h.x, w0.y - h.y, w1.x - h.z, w1.y - h.w);
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_arrive(&conv[s]);
@@ -550,28 +554,24 @@ tc_forward_kernel(const __grid_constant__ TmapSet tmaps, const __grid_constant__
           *reinterpret_cast<float4*>(st + oAhi + off) = h;
           *reinterpret_cast<float4*>(st + oAlo + off) = l;
         }
-        // B: V[k][n] for pixel k = ct / 4, scenes 4 (ct % 4) .. +3
+        // B: V[k][n] for scene n = ct % 16 and pixels k = 4j .. 4j + 3, j = ct / 16:
+        // one 16-byte chunk of the hi rows and one of the lo rows per thread
+        // (a quarter-warp covers eight scenes: no bank conflict)
         {
-          const int k = ct >> 2, n0 = 4 * (ct & 3);
-          float v[4] = {0.f, 0.f, 0.f, 0.f};
-          if (k < nv) {
-            const float4 xx = *reinterpret_cast<const float4*>(st + oV + (k * kTcN + n0) * 4);
-            const float4 xb = *reinterpret_cast<const float4*>(st + oV + kVBytes + (k * kTcN + n0) * 4);
-            const float4 zb = *reinterpret_cast<const float4*>(st + oV + 2 * kVBytes + (k * kTcN + n0) * 4);
-            const float4 sdv = *reinterpret_cast<const float4*>(st + oV + 3 * kVBytes + (k * kTcN + n0) * 4);
-            v[0] = xx.x - xb.x + zb.x - sdv.x;
-            v[1] = xx.y - xb.y + zb.y - sdv.y;
-            v[2] = xx.z - xb.z + zb.z - sdv.z;
-            v[3] = xx.w - xb.w + zb.w - sdv.w;
-          }
-          float* bt = reinterpret_cast<float*>(st + oB);
+          const int n = ct & 15, j = ct >> 4;
+          const float* xv = reinterpret_cast<const float*>(st + oV);
+          float v[4];
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
-            const int n = n0 + u;
-            const float h = tf32_rn(v[u]);
-            bt[b_off(n, k) / 4] = h;
-            bt[b_off(kTcN + n, k) / 4] = v[u] - h;
+            const int k = 4 * j + u;
+            const int e = k * kTcN + n;
+            v[u] = k < nv ? xv[e] - xv[e + kVBytes / 4] + xv[e + 2 * kVBytes / 4] - xv[e + 3 * kVBytes / 4] : 0.f;
           }
+          float* bt = reinterpret_cast<float*>(st + oB);
+          const float4 h = make_float4(tf32_rn(v[0]), tf32_rn(v[1]), tf32_rn(v[2]), tf32_rn(v[3]));
+          *reinterpret_cast<float4*>(bt + b_off(n, 4 * j) / 4) = h;
+          *reinterpret_cast<float4*>(bt + b_off(kTcN + n, 4 * j) / 4) =
+              make_float4(v[0] - h.x, v[1] - h.y, v[2] - h.z, v[3] - h.w);
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_arrive(&conv[s]);
