@@ -185,7 +185,11 @@ int forward_chunks(int nsets, int KM, int max_cols) {
 
 // ------------------------------------------------------------------ adjoint
 constexpr int kAdjWarps = 8;
-constexpr int kAdjColsPerWarp = 8;
+// columns per warp: 8 in the whole-w form; 8, 4 or 2 in the chunked form,
+// chosen per launch so that the last wave of CTAs is as full as possible
+// (pick_adjoint_cols: at KM = 16384, N = 128^2, Q = 8, 2048 CTAs of 64 columns
+// filled 2.25 waves of 912 resident CTAs; 8192 CTAs of 16 fill 8.98, and the
+// adjoint went from 3.03 to 2.61 ms)
 constexpr int kAdjUnroll = 4;
 constexpr int kAdjWChunk = 2048;      // float4 of w staged at once (4096 complex, 32 KB)
 
@@ -197,13 +201,13 @@ constexpr int kAdjWChunk = 2048;      // float4 of w staged at once (4096 comple
 // factor, so g must be exact to double-float accuracy there.
 // Whole-w form (w fits one staged chunk): each warp sums its columns in one
 // pass over the rows.
-template <bool EXACT>
+template <bool EXACT, int COLS>
 __global__ void __launch_bounds__(kAdjWarps * 32)
 adjoint_whole_kernel(const __grid_constant__ SetBlock<AdjointSet> sets, int KM, bool update,
                const __grid_constant__ SolverView sv) {
   extern __shared__ float4 s_w4[];               // KM/2 float4 = KM complex (KM/2 <= kAdjWChunk)
   const AdjointSet& as = sets.v[blockIdx.y];
-  const int cols_per_cta = kAdjWarps * kAdjColsPerWarp;
+  const int cols_per_cta = kAdjWarps * COLS;
   const int pbeg = blockIdx.x * cols_per_cta;
   if (pbeg >= as.n) return;
   const int n4 = KM / 2;
@@ -212,8 +216,8 @@ adjoint_whole_kernel(const __grid_constant__ SetBlock<AdjointSet> sets, int KM, 
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const float4* A4 = reinterpret_cast<const float4*>(as.A);
-  for (int cw = 0; cw < kAdjColsPerWarp; ++cw) {
-    const int p = pbeg + warp * kAdjColsPerWarp + cw;
+  for (int cw = 0; cw < COLS; ++cw) {
+    const int p = pbeg + warp * COLS + cw;
     if (p >= as.n) break;
     const int pix = as.idx[p];
     const float4* col = A4 + (size_t)pix * n4;
@@ -292,13 +296,13 @@ adjoint_whole_kernel(const __grid_constant__ SetBlock<AdjointSet> sets, int KM, 
 
 // Chunked form (large KM): w is staged in chunks; each warp keeps its
 // columns' double-float sums across the chunks.
-template <bool EXACT>
+template <bool EXACT, int COLS>
 __global__ void __launch_bounds__(kAdjWarps * 32)
 adjoint_kernel(const __grid_constant__ SetBlock<AdjointSet> sets, int KM, bool update,
                const __grid_constant__ SolverView sv) {
   extern __shared__ float4 s_w4[];               // one chunk of w: up to kAdjWChunk float4
   const AdjointSet& as = sets.v[blockIdx.y];
-  const int cols_per_cta = kAdjWarps * kAdjColsPerWarp;
+  const int cols_per_cta = kAdjWarps * COLS;
   const int pbeg = blockIdx.x * cols_per_cta;
   if (pbeg >= as.n) return;
   const int n4 = KM / 2;
@@ -306,12 +310,12 @@ adjoint_kernel(const __grid_constant__ SetBlock<AdjointSet> sets, int KM, bool u
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const float4* A4 = reinterpret_cast<const float4*>(as.A);
   // per column of this warp, the double-float sum over the chunks done so far
-  DF colacc[kAdjColsPerWarp];
-  int pixs[kAdjColsPerWarp];
+  DF colacc[COLS];
+  int pixs[COLS];
 #pragma unroll
-  for (int cw = 0; cw < kAdjColsPerWarp; ++cw) {
+  for (int cw = 0; cw < COLS; ++cw) {
     colacc[cw] = DF{0.f, 0.f};
-    const int p = pbeg + warp * kAdjColsPerWarp + cw;
+    const int p = pbeg + warp * COLS + cw;
     pixs[cw] = p < as.n ? as.idx[p] : -1;
   }
   // w is staged in chunks so that large KM keeps several CTAs per SM resident
@@ -321,7 +325,7 @@ adjoint_kernel(const __grid_constant__ SetBlock<AdjointSet> sets, int KM, bool u
     for (int t = threadIdx.x; t < cn; t += blockDim.x) s_w4[t] = w4[c0 + t];
     __syncthreads();
 #pragma unroll 1
-    for (int cw = 0; cw < kAdjColsPerWarp; ++cw) {
+    for (int cw = 0; cw < COLS; ++cw) {
       const int pix = pixs[cw];
       if (pix < 0) break;
       const float4* col = A4 + (size_t)pix * n4 + c0;
@@ -376,10 +380,10 @@ adjoint_kernel(const __grid_constant__ SetBlock<AdjointSet> sets, int KM, bool u
     }
   }
 #pragma unroll 1
-  for (int cw = 0; cw < kAdjColsPerWarp; ++cw) {
+  for (int cw = 0; cw < COLS; ++cw) {
     const int pix = pixs[cw];
     if (pix < 0) break;
-    const int p = pbeg + warp * kAdjColsPerWarp + cw;
+    const int p = pbeg + warp * COLS + cw;
     DF tot = colacc[cw];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -450,6 +454,54 @@ int launch_forward_reduce(const ColumnSet* sets, int nsets, int KM, int chunks, 
   return SADMM_OK;
 }
 
+template <int C>
+int configure_adjoint() {
+  SADMM_CUDA_TRY(cudaFuncSetAttribute(adjoint_kernel<false, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      200 * 1024));
+  SADMM_CUDA_TRY(cudaFuncSetAttribute(adjoint_kernel<true, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      200 * 1024));
+  return SADMM_OK;
+}
+
+template <int C>
+int adjoint_resident(bool whole, bool exact, size_t smem) {
+  int r = 0;
+  const void* f = whole ? (exact ? (const void*)adjoint_whole_kernel<true, C> : (const void*)adjoint_whole_kernel<false, C>)
+                        : (exact ? (const void*)adjoint_kernel<true, C> : (const void*)adjoint_kernel<false, C>);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, f, kAdjWarps * 32, smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return r;
+}
+
+// Columns per warp for an adjoint launch: of 8, 4 and 2, the one whose grid
+// fills its last wave of resident CTAs best (a fuller wave by more than 2 %
+// wins; otherwise the larger group, which stages w fewer times).
+int pick_adjoint_cols(bool whole, bool exact, size_t smem, int max_cols, int nsets) {
+  static int sms = 0;
+  if (!sms && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0) != cudaSuccess) {
+    cudaGetLastError();
+    sms = 152;
+  }
+  const int cand[3] = {8, 4, 2};
+  const int res[3] = {adjoint_resident<8>(whole, exact, smem), adjoint_resident<4>(whole, exact, smem),
+                      adjoint_resident<2>(whole, exact, smem)};
+  int best = 8;
+  double best_eff = -1.0;
+  for (int c = 0; c < 3; ++c) {
+    if (res[c] <= 0) continue;
+    const long long blocks = (long long)div_up(max_cols, kAdjWarps * cand[c]) * nsets;
+    const long long wave = (long long)res[c] * sms;
+    const double eff = (double)blocks / (double)(div_up(blocks, wave) * wave);
+    if (eff > best_eff + 0.02) {
+      best_eff = eff;
+      best = cand[c];
+    }
+  }
+  return best;
+}
+
 int launch_adjoint(const AdjointSet* sets, int nsets, int KM, bool update, const SolverView& sv,
                    cudaStream_t st) {
   if (nsets <= 0) return SADMM_OK;
@@ -467,20 +519,28 @@ int launch_adjoint(const AdjointSet* sets, int nsets, int KM, bool update, const
   const size_t smem = (size_t)std::min(KM / 2, kAdjWChunk) * sizeof(float4);
   static bool configured = false;
   if (!configured) {
-    SADMM_CUDA_TRY(cudaFuncSetAttribute(adjoint_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        200 * 1024));
-    SADMM_CUDA_TRY(cudaFuncSetAttribute(adjoint_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        200 * 1024));
+    SADMM_TRY(configure_adjoint<8>());
+    SADMM_TRY(configure_adjoint<4>());
+    SADMM_TRY(configure_adjoint<2>());
     configured = true;
   }
-  dim3 grid(div_up(max_cols, kAdjWarps * kAdjColsPerWarp), nsets);
-  if (KM / 2 <= kAdjWChunk) {
-    if (exact) adjoint_whole_kernel<true><<<grid, kAdjWarps * 32, smem, st>>>(blk, KM, update, sv);
-    else adjoint_whole_kernel<false><<<grid, kAdjWarps * 32, smem, st>>>(blk, KM, update, sv);
-  } else {
-    if (exact) adjoint_kernel<true><<<grid, kAdjWarps * 32, smem, st>>>(blk, KM, update, sv);
-    else adjoint_kernel<false><<<grid, kAdjWarps * 32, smem, st>>>(blk, KM, update, sv);
+  const bool whole = KM / 2 <= kAdjWChunk;
+  // whole-w form: eight columns per warp (smaller groups re-stage w per CTA
+  // and measured slower at KM = 2048); chunked form: the fullest last wave
+  const int cols = whole ? 8 : pick_adjoint_cols(whole, exact, smem, max_cols, nsets);
+  dim3 grid(div_up(max_cols, kAdjWarps * cols), nsets);
+#define SADMM_ADJ_LAUNCH(C)                                                                              \
+  if (whole) {                                                                                           \
+    if (exact) adjoint_whole_kernel<true, C><<<grid, kAdjWarps * 32, smem, st>>>(blk, KM, update, sv);  \
+    else adjoint_whole_kernel<false, C><<<grid, kAdjWarps * 32, smem, st>>>(blk, KM, update, sv);       \
+  } else {                                                                                               \
+    if (exact) adjoint_kernel<true, C><<<grid, kAdjWarps * 32, smem, st>>>(blk, KM, update, sv);        \
+    else adjoint_kernel<false, C><<<grid, kAdjWarps * 32, smem, st>>>(blk, KM, update, sv);             \
   }
+  if (cols == 8) { SADMM_ADJ_LAUNCH(8) }
+  else if (cols == 4) { SADMM_ADJ_LAUNCH(4) }
+  else { SADMM_ADJ_LAUNCH(2) }
+#undef SADMM_ADJ_LAUNCH
   SADMM_LAUNCH_CHECK();
   return SADMM_OK;
 }
