@@ -158,7 +158,8 @@ int split_chunks(int nsets, int KM, int max_cols) {
 
 // ------------------------------------------------------------------ adjoint
 constexpr int kSaWarps = 8;
-constexpr int kSaColsPerWarp = 8;
+// columns per warp: a template parameter of split_adjoint_kernel (8, or 2
+// in the chunked form when that fills the last wave of CTAs better)
 constexpr int kSaUnroll = 4;
 constexpr int kSaChunk = 1024;        // uint4 of a column per staged chunk of w (4096 complex, 32 KB)
 
@@ -275,13 +276,13 @@ __device__ __forceinline__ void split_adj_finish(const SplitSet& as, const Solve
 // chunk and each column is summed in one pass; otherwise w is staged in
 // chunks and each warp keeps its columns' sums across them, so that large KM
 // keeps several CTAs per SM resident.
-template <int KIND, bool HI, bool LO, bool EXACT, bool WHOLE>
+template <int KIND, bool HI, bool LO, bool EXACT, bool WHOLE, int COLS>
 __global__ void __launch_bounds__(kSaWarps * 32)
 split_adjoint_kernel(const __grid_constant__ SetBlock<SplitSet> sets, int KM, bool update,
                      const __grid_constant__ SolverView sv) {
   extern __shared__ float4 s_w[];                    // one chunk of w: up to 2 kSaChunk float4
   const SplitSet& as = sets.v[blockIdx.y];
-  const int pbeg = blockIdx.x * kSaWarps * kSaColsPerWarp;
+  const int pbeg = blockIdx.x * kSaWarps * COLS;
   if (pbeg >= as.n) return;
   const float4* w4 = reinterpret_cast<const float4*>(as.w);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -291,8 +292,8 @@ split_adjoint_kernel(const __grid_constant__ SetBlock<SplitSet> sets, int KM, bo
   if constexpr (WHOLE) {
     for (int t = threadIdx.x; t < 2 * n4; t += blockDim.x) s_w[t] = w4[t];
     __syncthreads();
-    for (int cw = 0; cw < kSaColsPerWarp; ++cw) {
-      const int p = pbeg + warp * kSaColsPerWarp + cw;
+    for (int cw = 0; cw < COLS; ++cw) {
+      const int p = pbeg + warp * COLS + cw;
       if (p >= as.n) break;
       const int pix = as.idx[p];
       float g = 0.f, h_ = 0.f, l_ = 0.f;
@@ -301,12 +302,12 @@ split_adjoint_kernel(const __grid_constant__ SetBlock<SplitSet> sets, int KM, bo
     }
     return;
   }
-  float cs[kSaColsPerWarp], dh[kSaColsPerWarp], dl[kSaColsPerWarp];
-  int pixs[kSaColsPerWarp];
+  float cs[COLS], dh[COLS], dl[COLS];
+  int pixs[COLS];
 #pragma unroll
-  for (int cw = 0; cw < kSaColsPerWarp; ++cw) {
+  for (int cw = 0; cw < COLS; ++cw) {
     cs[cw] = 0.f; dh[cw] = 0.f; dl[cw] = 0.f;
-    const int p = pbeg + warp * kSaColsPerWarp + cw;
+    const int p = pbeg + warp * COLS + cw;
     pixs[cw] = p < as.n ? as.idx[p] : -1;
   }
   for (int c0 = 0; c0 < n4; c0 += kSaChunk) {
@@ -315,7 +316,7 @@ split_adjoint_kernel(const __grid_constant__ SetBlock<SplitSet> sets, int KM, bo
     for (int t = threadIdx.x; t < 2 * cn; t += blockDim.x) s_w[t] = w4[2 * c0 + t];
     __syncthreads();
 #pragma unroll 1
-    for (int cw = 0; cw < kSaColsPerWarp; ++cw) {
+    for (int cw = 0; cw < COLS; ++cw) {
       const int pix = pixs[cw];
       if (pix < 0) break;
       float g = cs[cw], h_ = dh[cw], l_ = dl[cw];
@@ -324,10 +325,10 @@ split_adjoint_kernel(const __grid_constant__ SetBlock<SplitSet> sets, int KM, bo
     }
   }
 #pragma unroll 1
-  for (int cw = 0; cw < kSaColsPerWarp; ++cw) {
+  for (int cw = 0; cw < COLS; ++cw) {
     const int pix = pixs[cw];
     if (pix < 0) break;
-    split_adj_finish<EXACT>(as, sv, update, pbeg + warp * kSaColsPerWarp + cw, pix, lane, cs[cw], dh[cw], dl[cw]);
+    split_adj_finish<EXACT>(as, sv, update, pbeg + warp * COLS + cw, pix, lane, cs[cw], dh[cw], dl[cw]);
   }
 }
 
@@ -369,21 +370,53 @@ int launch_split_forward_t(const SetBlock<SplitSet>& blk, int nsets, int KM, int
   return SADMM_OK;
 }
 
+// Fraction of the last wave that a grid of `blocks` CTAs fills, given the
+// resident CTAs per SM of its kernel (0 if the query fails).
+double last_wave_fill(const void* f, size_t smem, long long blocks) {
+  static int sms = 0;
+  if (!sms && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0) != cudaSuccess) {
+    cudaGetLastError();
+    sms = 152;
+  }
+  int r = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, f, kSaWarps * 32, smem) != cudaSuccess || r <= 0) {
+    cudaGetLastError();
+    return 0.0;
+  }
+  const long long wave = (long long)r * sms;
+  return (double)blocks / (double)(div_up(blocks, wave) * wave);
+}
+
+// The chunked form takes eight or two columns per warp, whichever fills the
+// last wave of resident CTAs better (by more than 2 %); the whole-w form eight.
 template <int KIND, bool HI, bool LO, bool EXACT>
 int launch_split_adjoint_e(const SetBlock<SplitSet>& blk, int nsets, int KM, int max_cols, bool update,
                            const SolverView& sv, cudaStream_t st) {
   static bool configured = false;
   if (!configured) {
-    SADMM_CUDA_TRY(cudaFuncSetAttribute(split_adjoint_kernel<KIND, HI, LO, EXACT, false>,
+    SADMM_CUDA_TRY(cudaFuncSetAttribute(split_adjoint_kernel<KIND, HI, LO, EXACT, false, 8>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    SADMM_CUDA_TRY(cudaFuncSetAttribute(split_adjoint_kernel<KIND, HI, LO, EXACT, false, 2>,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     configured = true;
   }
-  dim3 grid(div_up(max_cols, kSaWarps * kSaColsPerWarp), nsets);
   const size_t smem = (size_t)std::min(KM / 4, kSaChunk) * 2 * sizeof(float4);
-  if (KM / 4 <= kSaChunk)
-    split_adjoint_kernel<KIND, HI, LO, EXACT, true><<<grid, kSaWarps * 32, smem, st>>>(blk, KM, update, sv);
-  else
-    split_adjoint_kernel<KIND, HI, LO, EXACT, false><<<grid, kSaWarps * 32, smem, st>>>(blk, KM, update, sv);
+  if (KM / 4 <= kSaChunk) {
+    dim3 grid(div_up(max_cols, kSaWarps * 8), nsets);
+    split_adjoint_kernel<KIND, HI, LO, EXACT, true, 8><<<grid, kSaWarps * 32, smem, st>>>(blk, KM, update, sv);
+  } else {
+    const long long b8 = (long long)div_up(max_cols, kSaWarps * 8) * nsets;
+    const long long b2 = (long long)div_up(max_cols, kSaWarps * 2) * nsets;
+    const double f8 = last_wave_fill((const void*)split_adjoint_kernel<KIND, HI, LO, EXACT, false, 8>, smem, b8);
+    const double f2 = last_wave_fill((const void*)split_adjoint_kernel<KIND, HI, LO, EXACT, false, 2>, smem, b2);
+    if (f2 > f8 + 0.02) {
+      dim3 grid(div_up(max_cols, kSaWarps * 2), nsets);
+      split_adjoint_kernel<KIND, HI, LO, EXACT, false, 2><<<grid, kSaWarps * 32, smem, st>>>(blk, KM, update, sv);
+    } else {
+      dim3 grid(div_up(max_cols, kSaWarps * 8), nsets);
+      split_adjoint_kernel<KIND, HI, LO, EXACT, false, 8><<<grid, kSaWarps * 32, smem, st>>>(blk, KM, update, sv);
+    }
+  }
   SADMM_LAUNCH_CHECK();
   return SADMM_OK;
 }
