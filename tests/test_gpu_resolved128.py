@@ -59,7 +59,7 @@ def test_plain_fp32_converges_to_the_oracle_limit(solver):
     """Plain FP32 SADMM from zero: within 1e-3 of the limit by iteration 60
     (the oracle reaches it at 47 on this workload), and at the limit after 400
     iterations the image x_G and the per-sensor images X agree with the
-    oracle's within 1e-4 (the benchmark spec's FP32 bar), with the same support."""
+    oracle's within 1e-4 (the FP32 parity bar), with the same support."""
     s, y, d, meta = solver
     s.set_criterion(elim=0)
     xg, _ = s.solve(y, 60)
@@ -78,7 +78,7 @@ def test_plain_fp32_converges_to_the_oracle_limit(solver):
 def test_split_forms_reach_the_limit(solver, precision):
     """BF16 pairs (1) and the BF16 hi plane with lo refresh every 4 (3) solve
     Eq. 2 for the pair operator; on this well-posed workload their limit is
-    within the benchmark spec's 1e-3 of the FP64 oracle's limit on the complex64
+    within 1e-3 of the FP64 oracle's limit on the complex64
     operator after 400 iterations."""
     s, y, d, meta = solver
     s.set_criterion(elim=0, precision=precision, correct_every=4)
