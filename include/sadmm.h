@@ -201,12 +201,6 @@ int sadmm_set_operator(sadmm_t ctx, int q, const float* A_q);
  * 256 or 512 (SADMM_EINVAL otherwise); invalidates sensor q's factor. */
 int sadmm_set_operator_delays(sadmm_t ctx, int q, const double* tau, double f0, double df);
 
-/* Which operator representation the per-iteration products read:
- * SADMM_PRODUCTS_AUTO (default): the factored tables when every sensor's
- * operator came from sadmm_set_operator_delays and precision is 0, else the
- * stored operator; SADMM_PRODUCTS_STORED: always the stored operator;
- * SADMM_PRODUCTS_FACTORED: the tables (a solve returns SADMM_ENOTREADY if a
- * sensor has none, SADMM_EINVAL if precision > 0). */
 /* Composite back-projection image out[n] = sum_q |a_{q,n}^H y_q| (N floats,
  * host or device) from measurements y[0..Q-1] (K*M complex64 each, host or
  * device): the BP comparison images of Section IV (Fig. 1), read as each
@@ -216,6 +210,13 @@ int sadmm_set_operator_delays(sadmm_t ctx, int q, const double* tau, double f0, 
  * SADMM_ENOTREADY if an operator is missing. */
 int sadmm_backprojection(sadmm_t ctx, const float* const* y, float* out);
 
+/* Which operator representation the per-iteration products read:
+ * SADMM_PRODUCTS_AUTO (default): the factored tables when every sensor's
+ * operator came from sadmm_set_operator_delays and precision is 0, else the
+ * stored operator; SADMM_PRODUCTS_STORED: always the stored operator;
+ * SADMM_PRODUCTS_FACTORED: the tables (a solve returns SADMM_ENOTREADY if a
+ * sensor has none, SADMM_EINVAL if precision > 0).  SADMM_EINVAL for any
+ * other mode. */
 #define SADMM_PRODUCTS_AUTO 0
 #define SADMM_PRODUCTS_STORED 1
 #define SADMM_PRODUCTS_FACTORED 2
