@@ -58,3 +58,20 @@ def test_gpus_flag_starts_that_many_ranks(monkeypatch):
     monkeypatch.setenv("WORLD_SIZE", "2")
     with pytest.raises(SystemExit, match="--gpus 4 but the launcher started 2 ranks"):
         bench.main()
+
+
+def test_factor_order_follows_the_smaller_gram():
+    """The x-update factor of Eq. 3 is 2KM x 2KM (Woodbury) when N > 2KM and
+    N x N (primal) otherwise: the bytes the batched factor apply streams."""
+    import scenegen
+    g = scenegen.GEOMS["resolved_128"]              # KM = 16384, N = 128^2: primal
+    assert bench._factor_order(g) == g.N == 16384
+    p = scenegen.GEOMS["paper_scale"]               # KM = 2048, N = 128^2: Woodbury
+    assert bench._factor_order(p) == 2 * p.KM == 4096
+
+
+def test_the_committed_traffic_matches_the_current_kernels():
+    """profiles/traffic.json was captured on the current sources of the
+    single-scene kernels, so the bench reports their DRAM traffic."""
+    for k in ("forward", "adjoint_update", "spd_woodbury"):
+        assert bench.traffic_for(k) is not None, k
