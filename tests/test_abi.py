@@ -59,6 +59,23 @@ def test_invalid_sizes_rejected_before_any_device_work():
     assert b"invalid" in lib.sadmm_last_error()
 
 
+def test_kernel_entries_reject_bad_arguments_before_device_work():
+    """The kernel-level tensor-core entries check their arguments before any
+    allocation or launch (so these calls need no GPU)."""
+    lib = binding.load()
+    p = ctypes.c_void_p(16)                         # never dereferenced: rejected first
+    null = ctypes.c_void_p()
+    # digit apply: n <= 0, ld < n, missing pointers
+    assert lib.sadmm_digit_apply16(p, 8, 0, p, p, null) == binding.EINVAL
+    assert lib.sadmm_digit_apply16(p, 4, 8, p, p, null) == binding.EINVAL
+    assert lib.sadmm_digit_apply16(null, 8, 8, p, p, null) == binding.EINVAL
+    # batched forward / adjoint GEMMs: 2KM not a multiple of 16 (32), N <= 0
+    assert lib.sadmm_forward16_tc(p, 4, 10, p, p, null) == binding.EINVAL
+    assert lib.sadmm_forward16_tc(p, 8, 0, p, p, null) == binding.EINVAL
+    assert lib.sadmm_adjoint16_tc(p, 8, 10, p, p, null) == binding.EINVAL
+    assert b"bad arguments" in lib.sadmm_last_error()
+
+
 def test_default_criterion_matches_the_paper_setup(lib):
     """The library's Algorithm 1 defaults are the values Section IV prints
     (tests/golden/simulation_parameters.json)."""
