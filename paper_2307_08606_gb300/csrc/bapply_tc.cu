@@ -14,10 +14,10 @@
 // 256 values of j (at most four products per j) stays within 2^24, so each
 // chunk's order sums are exact in the FP32 accumulator; after each chunk the
 // four sums go into double-float running totals (orders 0..2 by error-free
-// two-sums, order 3 into the low word: about 2^-46 of the total per chunk).  The dropped orders (>= 4)
-// and the two slicing remainders contribute at most about 5 2^-32 per term
-// (of 2^(e_i + f_s)).  The factor digits take 8 bytes per entry, as the
-// double-float pair copy of the single-scene apply.
+// two-sums, order 3 into the low word: about 2^-46 of the total per chunk).
+// The dropped orders (>= 4) and the two slicing remainders contribute at most
+// about 5 2^-32 per term (of 2^(e_i + f_s)).  The factor digits take 8 bytes
+// per entry, as the double-float pair copy of the single-scene apply.
 //
 // bapply_tc_kernel is a persistent, warp-specialised pipeline over work items
 // (sensor q, block of 128 rows, range of k):
